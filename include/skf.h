@@ -1,0 +1,236 @@
+/*
+ * skf.h -- C ABI of the GB300 sketched-Krylov f(A)b library.
+ *
+ * Method: Guettel & Schweitzer, "Randomized sketching for Krylov
+ * approximations of large-scale matrix functions".  The library computes the
+ * sketched FOM approximant (Sec. 2, eq. (sFOM) / (sFOM''')) and the sketched
+ * GMRES approximant (Sec. 3, eq. (sGMRES)) of f(A)b for a sparse A in CSR
+ * form and a Stieltjes function f, with the basis generated by the
+ * k-truncated Arnoldi recurrence of Algorithm 2 and an s x N subspace
+ * embedding S (eq. (1.1)) applied on the fly.
+ *
+ * Conventions for every entry point
+ *   - Pointers are DEVICE pointers unless the argument says "host".
+ *   - Matrices are column-major with the given leading dimension.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) and performs no host synchronisation, except
+ *     skf_create_csr / skf_sketch_create, which may synchronise `stream`
+ *     once while building their handle.
+ *   - The return value reports argument validation and launch errors only.
+ *     Numerical outcomes that are known only on the device (breakdown,
+ *     branch cut, quadrature not converged, ill-conditioning) are written to
+ *     skf_info::status when the stream reaches them.
+ *   - On error the call returns a status != SKF_OK and skf_last_error()
+ *     returns a message (thread-local, valid until the next call on the
+ *     same thread).  No entry point throws across the ABI.
+ *   - Handles own their device allocations; outputs are caller-allocated.
+ *   - All device work runs in this library's CUDA kernels (sm_103a).  There
+ *     is no CPU fallback: without a usable GPU every call returns
+ *     SKF_ERR_CUDA.
+ */
+#ifndef SKF_H
+#define SKF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *skf_stream_t; /* == cudaStream_t */
+
+typedef enum {
+    SKF_OK = 0,
+    SKF_ERR_INVALID_ARG = 1,         /* bad size, null pointer, s <= m, zeta > s, ... */
+    SKF_ERR_CUDA = 2,                /* a CUDA call failed (message has the CUDA error) */
+    SKF_ERR_OOM = 3,                 /* device allocation failed */
+    SKF_ERR_ILL_CONDITIONED = 4,     /* R of the whitening QR is numerically singular */
+    SKF_ERR_BRANCH_CUT = 5,          /* a shifted system t I + M is singular for a node t */
+    SKF_ERR_QUAD_NOT_CONVERGED = 6,  /* adaptive quadrature passed ell_max */
+    SKF_ERR_SKETCH_TOO_SMALL = 7,    /* s < 2m is required by the GMRES reduction */
+    SKF_ERR_NOT_SUPPORTED = 8,       /* valid request this build does not implement */
+    SKF_ERR_ZERO_RHS = 9             /* ||b|| = 0: x is set to 0 */
+} skf_status;
+
+typedef enum { SKF_F64 = 0, SKF_F32 = 1, SKF_BF16 = 2 } skf_dtype;
+
+typedef enum {
+    /* zeta nonzeros +-1/sqrt(zeta) per column, one per row stripe, rows and
+       signs from SplitMix64 (see skf_sketch_create).  Not in the paper. */
+    SKF_SKETCH_SPARSE_SIGN = 0,
+    /* subsampled randomised Walsh-Hadamard transform (Sec. 2.2 and Sec. 5.1
+       use the Fourier/DCT members of this family) */
+    SKF_SKETCH_SRHT = 1,
+    /* S = I (requires s == N): turns sFOM into FOM (Sec. 2, comment 1) */
+    SKF_SKETCH_IDENTITY = 2
+} skf_sketch_kind;
+
+typedef enum { SKF_BORROW = 0, SKF_COPY = 1 } skf_copy_mode;
+
+typedef enum {
+    SKF_FUNC_INVSQRT = 0,       /* f(z) = z^(-1/2)                         */
+    SKF_FUNC_LOG1P_OVER_Z = 1,  /* f(z) = log(1 + z) / z                   */
+    SKF_FUNC_INV = 2,           /* f(z) = 1/z (single node t = 0): tests   */
+    SKF_FUNC_INVPOW = 3         /* f(z) = z^(-alpha), 0 < alpha < 1        */
+} skf_func_kind;
+
+typedef enum { SKF_METHOD_SFOM = 0, SKF_METHOD_SGMRES = 1 } skf_method;
+
+typedef struct skf_csr skf_csr;       /* opaque sparse operator handle */
+typedef struct skf_sketch skf_sketch; /* opaque embedding handle        */
+
+/* A Stieltjes function f(z) = int_0^inf (t + z)^-1 dmu(t) (Sec. 1) given by
+ * its quadrature family.  The rule for order ell (host-generated) is
+ *   INVSQRT / INVPOW: Gauss-Jacobi(-alpha, alpha-1) (Chebyshev for alpha =
+ *     1/2) in x, t = scale (1-x)/(1+x)  (Sec. 5.1 uses scale = 1),
+ *   LOG1P_OVER_Z: Gauss-Legendre in x, t = 1 + scale (1-x)/(1+x),
+ *   INV: t = 0, w = 1.
+ * If n_nodes > 0 the host arrays nodes/weights are used as the only rule
+ * (no adaptivity). */
+typedef struct {
+    skf_func_kind kind;
+    double alpha;           /* exponent for SKF_FUNC_INVPOW */
+    double scale;           /* c > 0 of the Moebius map      */
+    int32_t n_nodes;        /* explicit rule length, 0 = adaptive family */
+    const double *nodes;    /* host, n_nodes t_i >= 0 */
+    const double *weights;  /* host, n_nodes w_i      */
+} skf_func;
+
+/* Method parameters (inputs of Algorithms 1 and 2). */
+typedef struct {
+    int32_t m;              /* Krylov dimension, 1 <= m < s              */
+    int32_t k;              /* truncation length of MGS, 1 <= k <= 16    */
+    skf_dtype basis_dtype;  /* storage of V_m: F64 (also F32/BF16 later) */
+    int32_t ell1, ell2;     /* first two quadrature orders (Sec. 4.1)    */
+    int32_t ell_max;        /* give up past this order                   */
+    double tol;             /* relative tolerance ||q1-q2|| <= tol ||q2|| */
+} skf_params;
+
+/* Device-written result record.  Place it in memory the device can write
+ * (cudaMalloc, or cudaHostAlloc/cudaHostRegister'd host memory) and read it
+ * after synchronising the stream. */
+typedef struct {
+    int32_t status;         /* skf_status of the numerical outcome        */
+    int32_t m_eff;          /* basis columns built (< m after breakdown)  */
+    int32_t breakdown;      /* 1 if ||w|| <= 1e-12 ||A v_j|| stopped the recurrence */
+    int32_t ell;            /* accepted quadrature order                  */
+    double quad_err;        /* ||q_ell1 - q_ell2|| / ||q_ell2|| at acceptance */
+    double beta;            /* ||b||                                      */
+    double eps_est;         /* max_j | ||S v_j||^2 - 1 | (Sec. 4.3)       */
+    double rdiag_ratio;     /* min |R_jj| / max |R_jj| of the whitening QR */
+} skf_info;
+
+/* ---------------------------------------------------------------- misc */
+const char *skf_last_error(void);
+const char *skf_status_string(skf_status s);
+int32_t skf_version(void);     /* major*10000 + minor*100 + patch */
+
+/* ------------------------------------------------------------ operator */
+/* skf_create_csr: wrap or copy a CSR matrix A (Sec. 2.2 assumes a sparse A
+ * with O(N) nonzeros; the matrix-vector product is line "w <- A v" of
+ * Algorithm 2).
+ *   n       rows = columns, 1 <= n < 2^31
+ *   nnz     nonzeros, 0 <= nnz < 2^31
+ *   rowptr  device int64[n+1], rowptr[0] = 0, nondecreasing, rowptr[n] = nnz
+ *   colind  device int32[nnz], 0 <= colind < n (any order within a row)
+ *   values  device F64 or F32 array [nnz] (vdtype)
+ *   mode    SKF_BORROW keeps colind/values (they must outlive the handle);
+ *           SKF_COPY copies them.  The row pointer is always copied (as int32).
+ * Builds the row partition used by the kernels and max_i sum_j |a_ij|.
+ * May synchronise `stream`.  Errors: INVALID_ARG, OOM, CUDA. */
+skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
+                          const void *values, skf_dtype vdtype, skf_copy_mode mode,
+                          skf_stream_t stream, skf_csr **A_out);
+skf_status skf_destroy_csr(skf_csr *A);
+/* Host copy of the matrix's max absolute row sum (an upper bound for |lambda|). */
+skf_status skf_csr_norm_inf(const skf_csr *A, double *out_host);
+
+/* -------------------------------------------------------------- sketch */
+/* skf_sketch_create: draw the embedding S in R^{s x N} (Algorithm 1, line 1;
+ * eq. (1.1)).  O(s) storage; the sparse-sign pattern is recomputed from the
+ * seed on the fly.  Definitions (identical to the CPU oracle's):
+ *   word(seed, i) = mix64(seed + (i+1) * 0x9E3779B97F4A7C15) (SplitMix64,
+ *     Steele, Lea & Flood 2014), mix64 = xor-shift-multiply finaliser with
+ *     constants 0xBF58476D1CE4E5B9, 0x94D049BB133111EB, shifts 30, 27, 31.
+ *   SPARSE_SIGN: stripes q = 0..zeta-1 cover rows [floor(q s/zeta),
+ *     floor((q+1) s/zeta)); column c uses words c*W + w, W = ceil(zeta/4);
+ *     stripe q reads u = 16-bit chunk (q mod 4) of word (q div 4); sign is
+ *     negative iff u & 1; row = start_q + ((u >> 1) * size_q) >> 15.
+ *     Requires 1 <= zeta <= s, s/zeta <= 32768.
+ *   SRHT: S x = s^-1/2 (H E [x; 0])[P], N' = 2^ceil(log2 N), E_c = -1 iff
+ *     word(seed, c) & 1, P = first s entries of a partial Fisher-Yates
+ *     shuffle of [0, N') with word(mix64(seed), i).  Requires s <= N'.
+ *   IDENTITY: requires s == N.
+ * Errors: INVALID_ARG, OOM, CUDA, NOT_SUPPORTED. */
+skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t zeta, uint64_t seed,
+                             skf_stream_t stream, skf_sketch **S_out);
+skf_status skf_sketch_destroy(skf_sketch *S);
+
+/* skf_sketch_apply: SX = S X for X of N rows and ncols columns (xdtype F64
+ * or F32, leading dimension ldx >= N); SX is F64 s x ncols, leading
+ * dimension s.  The sparse-sign sum is accumulated in 64/128-bit fixed point
+ * scaled by each column's max |x|, so the result is independent of the
+ * launch configuration (deterministic) and exact up to one rounding per
+ * input entry at 2^-50 of the column max.  Errors: INVALID_ARG, OOM, CUDA. */
+skf_status skf_sketch_apply(const skf_sketch *S, const void *X, skf_dtype xdtype, int64_t ldx,
+                            int32_t ncols, double *SX, skf_stream_t stream);
+
+/* -------------------------------------------------------------- basis */
+/* skf_arnoldi_trunc: the basis generation of Algorithm 2 (k-truncated
+ * modified Gram-Schmidt, Sec. 2.2) with the sketches S V_m, S A V_m built on
+ * the fly (Sec. 2, comment 3).  Exactly m products with A are performed.
+ *   b          device F64 [N] (bdtype must be SKF_F64 in this build)
+ *   V, ldv     device basis storage, N x m, type basis_dtype (F64 here);
+ *              column j holds a positive multiple w_j of the basis vector:
+ *              v_j = vscale[j] * V[:, j], vscale[j] = 1 / ||V[:, j]||.
+ *   vscale     device F64 [m]
+ *   SV, SAV    device F64 s x m (ld = s): S v_j and S A v_j
+ *   H          device F64 (m+1) x m (ld = m+1), zero outside the band:
+ *              H[i, j] = MGS coefficient h_ij for i in the window,
+ *              H[j+1, j] = ||w||; the last column holds only the window
+ *              coefficients' slots as zero (no m+1-st vector is formed).
+ *   info       device skf_info (m_eff, breakdown, beta, eps_est) or NULL
+ * Requirements: 1 <= m < s, m <= N, 1 <= k <= 16.  Errors: INVALID_ARG, OOM, CUDA. */
+skf_status skf_arnoldi_trunc(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype,
+                             int32_t m, int32_t k, skf_dtype basis_dtype, void *V, int64_t ldv,
+                             double *vscale, double *SV, double *SAV, double *H, skf_info *info,
+                             skf_stream_t stream);
+
+/* ------------------------------------------------------------- solvers */
+/* skf_solve: the full approximant.
+ *   method SFOM:   f_hat = V_m R^{-1} sum_i w_i (t_i I + M)^{-1} c, the
+ *                  whitened form of eq. (sFOM) (equal to the closed form
+ *                  (sFOM''') up to the quadrature error, which the adaptive
+ *                  rule controls)
+ *   method SGMRES: f_tilde = V_m R^{-1} sum_i w_i (t_i Q + Z)^+ S b,
+ *                  eq. (sGMRES) with the quadrature (4.1)
+ * where S V_m = Q R (whitening, Sec. 2.1), Z = S A V_m R^{-1}, M = Q^T Z,
+ * c = Q^T S b.  Orders follow Sec. 4.1: ell1, ell2, then ell2 <-
+ * floor(sqrt(2) ell2) until ||q_ell1 - q_ell2|| <= tol ||q_ell2|| or
+ * ell_max is passed (info->status = QUAD_NOT_CONVERGED, x from the last
+ * order).  Requires s >= 2m for SGMRES.
+ *   b  device F64 [N];   x  device F64 [N] (output)
+ *   workspace is allocated stream-ordered (cudaMallocAsync) and released
+ *   before return, so the call can be captured into a CUDA graph.
+ * Errors: INVALID_ARG, OOM, CUDA, SKETCH_TOO_SMALL, NOT_SUPPORTED. */
+skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, const void *b,
+                     skf_dtype bdtype, const skf_func *f, const skf_params *p, void *x, skf_dtype xdtype,
+                     skf_info *info, skf_stream_t stream);
+
+/* Convenience forms of skf_solve. */
+skf_status skf_sfom(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype,
+                    const skf_func *f, const skf_params *p, void *x, skf_dtype xdtype, skf_info *info,
+                    skf_stream_t stream);
+skf_status skf_sgmres(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype,
+                      const skf_func *f, const skf_params *p, void *x, skf_dtype xdtype, skf_info *info,
+                      skf_stream_t stream);
+
+/* skf_quadrature_rule: host copy of the rule of order ell for f (the same
+ * nodes and weights the solvers use).  t_host, w_host: host double[ell]. */
+skf_status skf_quadrature_rule(const skf_func *f, int32_t ell, double *t_host, double *w_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKF_H */

@@ -1,0 +1,263 @@
+"""Python binding of the GB300 sketched-Krylov f(A)b library (include/skf.h).
+
+Argument marshalling only: every computation runs in the CUDA kernels of
+``libskf.so`` (built in-tree by ``paper_2208_11447_gb300.build``).  Tensors are
+torch CUDA tensors; the CUDA stream is torch's current stream unless one is
+given.  There is no CPU fallback: if the shared library is missing or cannot
+be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libskf.so")
+
+# enums of include/skf.h
+F64, F32, BF16 = 0, 1, 2
+SPARSE_SIGN, SRHT, IDENTITY = 0, 1, 2
+BORROW, COPY = 0, 1
+INVSQRT, LOG1P_OVER_Z, INV, INVPOW = 0, 1, 2, 3
+SFOM, SGMRES = 0, 1
+STATUS = {0: "SKF_OK", 1: "SKF_ERR_INVALID_ARG", 2: "SKF_ERR_CUDA", 3: "SKF_ERR_OOM",
+          4: "SKF_ERR_ILL_CONDITIONED", 5: "SKF_ERR_BRANCH_CUT", 6: "SKF_ERR_QUAD_NOT_CONVERGED",
+          7: "SKF_ERR_SKETCH_TOO_SMALL", 8: "SKF_ERR_NOT_SUPPORTED", 9: "SKF_ERR_ZERO_RHS"}
+FUNC_KIND = {"invsqrt": INVSQRT, "log1p_over_z": LOG1P_OVER_Z, "inv": INV, "invpow": INVPOW}
+_DTYPE = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
+
+
+class SkfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Func(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("alpha", ctypes.c_double), ("scale", ctypes.c_double),
+                ("n_nodes", ctypes.c_int32), ("nodes", ctypes.POINTER(ctypes.c_double)),
+                ("weights", ctypes.POINTER(ctypes.c_double))]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("k", ctypes.c_int32), ("basis_dtype", ctypes.c_int),
+                ("ell1", ctypes.c_int32), ("ell2", ctypes.c_int32), ("ell_max", ctypes.c_int32),
+                ("tol", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("m_eff", ctypes.c_int32), ("breakdown", ctypes.c_int32),
+                ("ell", ctypes.c_int32), ("quad_err", ctypes.c_double), ("beta", ctypes.c_double),
+                ("eps_est", ctypes.c_double), ("rdiag_ratio", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["status_name"] = STATUS.get(self.status, str(self.status))
+        return d
+
+
+_lib = None
+
+
+def lib():
+    """Load libskf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not found: run `python -m paper_2208_11447_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        L.skf_last_error.restype = ctypes.c_char_p
+        L.skf_status_string.restype = ctypes.c_char_p
+        L.skf_status_string.argtypes = [ctypes.c_int]
+        L.skf_version.restype = i32
+        L.skf_create_csr.argtypes = [i64, i64, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.skf_destroy_csr.argtypes = [vp]
+        L.skf_csr_norm_inf.argtypes = [vp, ctypes.POINTER(dbl)]
+        L.skf_sketch_create.argtypes = [ctypes.c_int, i64, i32, i32, u64, vp, ctypes.POINTER(vp)]
+        L.skf_sketch_destroy.argtypes = [vp]
+        L.skf_sketch_apply.argtypes = [vp, vp, ctypes.c_int, i64, i32, vp, vp]
+        L.skf_arnoldi_trunc.argtypes = [vp, vp, vp, ctypes.c_int, i32, i32, ctypes.c_int, vp, i64, vp, vp, vp, vp,
+                                        vp, vp]
+        L.skf_solve.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int, ctypes.POINTER(Func),
+                                ctypes.POINTER(Params), vp, ctypes.c_int, vp, vp]
+        L.skf_sfom.argtypes = L.skf_solve.argtypes[1:]
+        L.skf_sgmres.argtypes = L.skf_solve.argtypes[1:]
+        L.skf_quadrature_rule.argtypes = [ctypes.POINTER(Func), i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
+                     "skf_sketch_destroy", "skf_sketch_apply", "skf_arnoldi_trunc", "skf_solve", "skf_sfom",
+                     "skf_sgmres", "skf_quadrature_rule"]:
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise SkfError(st, lib().skf_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Csr:
+    """Handle of skf_create_csr; keeps the tensors it borrows alive."""
+
+    def __init__(self, rowptr: torch.Tensor, colind: torch.Tensor, values: torch.Tensor, copy: bool = False,
+                 stream=None):
+        assert rowptr.is_cuda and rowptr.dtype == torch.int64 and rowptr.is_contiguous()
+        assert colind.is_cuda and colind.dtype == torch.int32 and colind.is_contiguous()
+        assert values.is_cuda and values.dtype in _DTYPE and values.is_contiguous()
+        self.n = rowptr.numel() - 1
+        self.nnz = colind.numel()
+        self._keep = (rowptr, colind, values)
+        h = ctypes.c_void_p()
+        _check(lib().skf_create_csr(self.n, self.nnz, _ptr(rowptr), _ptr(colind), _ptr(values),
+                                    _DTYPE[values.dtype], COPY if copy else BORROW, _stream(stream),
+                                    ctypes.byref(h)))
+        self.handle = h
+
+    def norm_inf(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().skf_csr_norm_inf(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.skf_destroy_csr(self.handle)
+            self.handle = None
+
+
+def create_csr(rowptr, colind, values, copy=False, stream=None) -> Csr:
+    return Csr(rowptr, colind, values, copy, stream)
+
+
+class Sketch:
+    """Handle of skf_sketch_create."""
+
+    def __init__(self, kind: int, n: int, s: int, zeta: int = 8, seed: int = 13, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().skf_sketch_create(kind, n, s, zeta, seed & ((1 << 64) - 1), _stream(stream), ctypes.byref(h)))
+        self.handle, self.kind, self.n, self.s, self.zeta, self.seed = h, kind, n, s, zeta, seed
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.skf_sketch_destroy(self.handle)
+            self.handle = None
+
+
+def sketch_create(kind, n, s, zeta=8, seed=13, stream=None) -> Sketch:
+    return Sketch(kind, n, s, zeta, seed, stream)
+
+
+def sketch_apply(S: Sketch, X: torch.Tensor, SX: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """SX = S X for X of shape (N,) or (N, ncols) (column-major storage: X.T contiguous)."""
+    Xc = X.reshape(X.shape[0], -1)
+    ncols = Xc.shape[1]
+    Xcm = Xc.t().contiguous()           # column-major: column c at offset c*N
+    if SX is None:
+        SX = torch.empty((ncols, S.s), dtype=torch.float64, device=X.device)
+    _check(lib().skf_sketch_apply(S.handle, _ptr(Xcm), _DTYPE[X.dtype], X.shape[0], ncols, _ptr(SX),
+                                  _stream(stream)))
+    out = SX.t()
+    return out.reshape(S.s) if X.dim() == 1 else out
+
+
+def new_info(device="cuda") -> torch.Tensor:
+    return torch.zeros(ctypes.sizeof(Info), dtype=torch.uint8, device=device)
+
+
+def read_info(buf: torch.Tensor) -> dict:
+    raw = bytes(buf.cpu().numpy().tobytes())
+    return Info.from_buffer_copy(raw).as_dict()
+
+
+def arnoldi_trunc(A: Csr, S: Sketch, b: torch.Tensor, m: int, k: int, basis_dtype=torch.float64, info=None,
+                  stream=None):
+    """Returns V (m x N, row j = stored column w_j), vscale (m), SV, SAV (m x s,
+    row j = column j), H ((m) x (m+1): row j = column j of the (m+1) x m H)."""
+    N = A.n
+    dev = b.device
+    V = torch.empty((m, N), dtype=basis_dtype, device=dev)
+    vscale = torch.empty(m, dtype=torch.float64, device=dev)
+    SV = torch.empty((m, S.s), dtype=torch.float64, device=dev)
+    SAV = torch.empty((m, S.s), dtype=torch.float64, device=dev)
+    H = torch.empty((m, m + 1), dtype=torch.float64, device=dev)
+    _check(lib().skf_arnoldi_trunc(A.handle, S.handle, _ptr(b), _DTYPE[b.dtype], m, k, _DTYPE[basis_dtype],
+                                   _ptr(V), N, _ptr(vscale), _ptr(SV), _ptr(SAV), _ptr(H), _ptr(info),
+                                   _stream(stream)))
+    return V, vscale, SV, SAV, H
+
+
+def make_func(kind: str, scale: float = 1.0, alpha: float = 0.5, nodes=None, weights=None) -> Func:
+    f = Func()
+    f.kind = FUNC_KIND[kind]
+    f.alpha = alpha
+    f.scale = scale
+    if nodes is not None:
+        import numpy as np
+        t = np.ascontiguousarray(nodes, dtype=np.float64)
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        f.n_nodes = t.size
+        f._t, f._w = t, w        # keep alive
+        f.nodes = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        f.weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    else:
+        f.n_nodes = 0
+    return f
+
+
+def make_params(m: int, k: int, basis_dtype=torch.float64, ell1=16, ell2=22, ell_max=1024, tol=1e-10) -> Params:
+    return Params(m, k, _DTYPE[basis_dtype], ell1, ell2, ell_max, tol)
+
+
+def solve(method: int, A: Csr, S: Sketch, b: torch.Tensor, f: Func, p: Params, x: torch.Tensor | None = None,
+          info=None, stream=None) -> torch.Tensor:
+    if x is None:
+        x = torch.empty_like(b)
+    _check(lib().skf_solve(method, A.handle, S.handle, _ptr(b), _DTYPE[b.dtype], ctypes.byref(f), ctypes.byref(p),
+                           _ptr(x), _DTYPE[x.dtype], _ptr(info), _stream(stream)))
+    return x
+
+
+def sfom(A, S, b, f, p, x=None, info=None, stream=None):
+    return solve(SFOM, A, S, b, f, p, x, info, stream)
+
+
+def sgmres(A, S, b, f, p, x=None, info=None, stream=None):
+    return solve(SGMRES, A, S, b, f, p, x, info, stream)
+
+
+def quadrature_rule(f: Func, ell: int):
+    import numpy as np
+    t = np.empty(ell)
+    w = np.empty(ell)
+    _check(lib().skf_quadrature_rule(ctypes.byref(f), ell, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return t, w
+
+
+@dataclass
+class DeviceOperator:
+    """A CSR operator resident on the device plus its handle."""
+    rowptr: torch.Tensor
+    colind: torch.Tensor
+    values: torch.Tensor
+    csr: Csr
+
+
+def upload_csr(rowptr, colind, values, device="cuda") -> DeviceOperator:
+    rp = torch.as_tensor(rowptr, dtype=torch.int64).to(device)
+    ci = torch.as_tensor(colind, dtype=torch.int32).to(device)
+    va = torch.as_tensor(values).to(device)
+    return DeviceOperator(rp, ci, va, Csr(rp, ci, va))

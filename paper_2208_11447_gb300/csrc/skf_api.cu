@@ -1,0 +1,473 @@
+// C ABI entry points (include/skf.h): argument validation, handles, the
+// quadrature-rule cache and the orchestration of the device pipelines.
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "skf_internal.cuh"
+
+namespace skf {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+skf_status fail(skf_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+skf_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return SKF_ERR_OOM;
+    return SKF_ERR_CUDA;
+}
+
+int num_sms() {
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            cached = v;
+        else
+            return 1;
+    }
+    return cached;
+}
+
+skf_status dalloc(void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return cuda_fail(e, "cudaMallocAsync");
+    }
+    return SKF_OK;
+}
+void dfree(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+// ------------------------------------------------------- quadrature rules
+// Gauss-Legendre nodes by Newton's method on theta with x = cos(theta), so
+// that 1 + x = 2 cos^2(theta/2) and 1 - x = 2 sin^2(theta/2) are accurate near
+// the end points; the weights are 2 / (sin^2 theta P_n'(x)^2).
+static void gauss_legendre_theta(int n, std::vector<double> &theta, std::vector<double> &omega) {
+    theta.resize(n);
+    omega.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double th = M_PI * (i + 0.75) / (n + 0.5);
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            const double x = cos(th), st = sin(th);
+            double p0 = 1.0, p1 = x;
+            for (int kk = 2; kk <= n; ++kk) {
+                const double p2 = ((2.0 * kk - 1.0) * x * p1 - (kk - 1.0) * p0) / kk;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pn = (n == 0) ? 1.0 : (n == 1 ? x : p1);
+            const double pm = (n == 1) ? 1.0 : p0;
+            // d/dtheta P_n(cos theta) = n (x P_n - P_{n-1}) / sin(theta)
+            dp = n * (x * pn - pm) / st;
+            const double step = pn / dp;
+            th -= step;
+            if (fabs(step) < 1e-16 * (1.0 + fabs(th))) break;
+        }
+        theta[i] = th;
+        omega[i] = 2.0 / (dp * dp);   // = 2 / (sin^2 P_n'^2)
+    }
+}
+
+bool quadrature_rule(const skf_func &f, int ell, double *t, double *w) {
+    if (f.kind == SKF_FUNC_INV) {
+        t[0] = 0.0;
+        w[0] = 1.0;
+        return true;
+    }
+    const double c = f.scale;
+    if (f.kind == SKF_FUNC_INVSQRT || (f.kind == SKF_FUNC_INVPOW && f.alpha == 0.5)) {
+        // Gauss-Chebyshev: theta_i = (2i-1) pi / (2 ell), omega_i = pi / ell;
+        // t = c tan^2(theta/2), w = 2 sqrt(c) / (ell (1 + x)).
+        for (int i = 0; i < ell; ++i) {
+            const double th = (2.0 * i + 1.0) * M_PI / (2.0 * ell);
+            const double ch = cos(0.5 * th), sh = sin(0.5 * th);
+            t[i] = c * (sh * sh) / (ch * ch);
+            w[i] = sqrt(c) / (ell * ch * ch);
+        }
+        return true;
+    }
+    if (f.kind == SKF_FUNC_LOG1P_OVER_Z) {
+        std::vector<double> th, om;
+        gauss_legendre_theta(ell, th, om);
+        for (int i = 0; i < ell; ++i) {
+            const double ch = cos(0.5 * th[i]), sh = sin(0.5 * th[i]);
+            t[i] = 1.0 + c * (sh * sh) / (ch * ch);
+            // w = 2 c omega / ((1 + x)^2 t), 1 + x = 2 cos^2(theta/2)
+            w[i] = c * om[i] / (2.0 * ch * ch * ch * ch * t[i]);
+        }
+        return true;
+    }
+    return false;
+}
+
+// Device copies of the adaptive schedule, cached per (f, schedule).
+struct RuleCache {
+    std::mutex mu;
+    std::map<std::string, RuleDev *> tables;
+};
+static RuleCache &rule_cache() {
+    static RuleCache *rc = new RuleCache();
+    return *rc;
+}
+
+static skf_status get_rule(const skf_func &f, const skf_params &p, const RuleDev **out) {
+    char key[256];
+    snprintf(key, sizeof key, "%d|%.17g|%.17g|%d|%d|%d|%d", (int)f.kind, f.alpha, f.scale, p.ell1, p.ell2, p.ell_max,
+             f.n_nodes);
+    std::string k(key);
+    if (f.n_nodes > 0) {
+        for (int i = 0; i < f.n_nodes; ++i) {
+            char b[64];
+            snprintf(b, sizeof b, "|%a|%a", f.nodes[i], f.weights[i]);
+            k += b;
+        }
+    }
+    RuleCache &rc = rule_cache();
+    std::lock_guard<std::mutex> lk(rc.mu);
+    auto it = rc.tables.find(k);
+    if (it != rc.tables.end()) {
+        *out = it->second;
+        return SKF_OK;
+    }
+    std::vector<int> ells;
+    if (f.n_nodes > 0) {
+        ells.push_back(f.n_nodes);
+    } else if (f.kind == SKF_FUNC_INV) {
+        ells.push_back(1);
+    } else {
+        ells.push_back(p.ell1);
+        ells.push_back(p.ell2);
+        while (true) {
+            const int nx = (int)floor(sqrt(2.0) * ells.back());
+            if (nx > p.ell_max) break;
+            ells.push_back(nx);
+        }
+    }
+    std::vector<double> ht, hw;
+    std::vector<int> hs{0};
+    for (int ell : ells) {
+        const size_t o = ht.size();
+        ht.resize(o + ell);
+        hw.resize(o + ell);
+        if (f.n_nodes > 0) {
+            std::copy(f.nodes, f.nodes + ell, ht.begin() + o);
+            std::copy(f.weights, f.weights + ell, hw.begin() + o);
+        } else if (!quadrature_rule(f, ell, ht.data() + o, hw.data() + o)) {
+            return fail(SKF_ERR_NOT_SUPPORTED, "quadrature family not implemented for this function");
+        }
+        hs.push_back((int)ht.size());
+    }
+    RuleDev *r = new RuleDev();
+    r->nlevels = (int)ells.size();
+    r->h_start = hs;
+    r->h_ell = ells;
+    if (cudaMalloc(&r->t, sizeof(double) * ht.size()) != cudaSuccess ||
+        cudaMalloc(&r->w, sizeof(double) * hw.size()) != cudaSuccess ||
+        cudaMalloc(&r->lev_start, sizeof(int) * hs.size()) != cudaSuccess ||
+        cudaMalloc(&r->lev_ell, sizeof(int) * ells.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SKF_ERR_OOM, "rule table allocation failed");
+    }
+    if (cudaMemcpy(r->t, ht.data(), sizeof(double) * ht.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(r->w, hw.data(), sizeof(double) * hw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(r->lev_start, hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(r->lev_ell, ells.data(), sizeof(int) * ells.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "rule table upload");
+    rc.tables[k] = r;
+    *out = r;
+    return SKF_OK;
+}
+
+namespace {
+
+__global__ void k_rowptr32(const int64_t *__restrict__ in, int64_t n, int32_t *__restrict__ out, int *bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = in[i];
+        out[i] = (int32_t)v;
+        if (v < 0 || (i > 0 && in[i - 1] > v)) atomicExch(bad, 1);
+    }
+}
+
+__global__ void k_row_abs_sum(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
+                              int64_t n, int *bad, unsigned long long *maxbits) {
+    double mx = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int p = rp[r]; p < rp[r + 1]; ++p) {
+            acc += fabs(v[p]);
+            if (ci[p] < 0 || ci[p] >= n) atomicExch(bad, 1);
+        }
+        mx = fmax(mx, acc);
+    }
+    // non-negative doubles order like their bit patterns
+    atomicMax(maxbits, (unsigned long long)__double_as_longlong(mx));
+}
+
+}  // namespace
+}  // namespace skf
+
+using namespace skf;
+
+extern "C" {
+
+const char *skf_last_error(void) { return g_last_error.c_str(); }
+
+const char *skf_status_string(skf_status s) {
+    switch (s) {
+        case SKF_OK: return "ok";
+        case SKF_ERR_INVALID_ARG: return "invalid argument";
+        case SKF_ERR_CUDA: return "CUDA error";
+        case SKF_ERR_OOM: return "out of device memory";
+        case SKF_ERR_ILL_CONDITIONED: return "ill-conditioned";
+        case SKF_ERR_BRANCH_CUT: return "singular shifted system (branch cut)";
+        case SKF_ERR_QUAD_NOT_CONVERGED: return "quadrature not converged";
+        case SKF_ERR_SKETCH_TOO_SMALL: return "sketch too small";
+        case SKF_ERR_NOT_SUPPORTED: return "not supported";
+        case SKF_ERR_ZERO_RHS: return "zero right-hand side";
+    }
+    return "unknown status";
+}
+
+int32_t skf_version(void) { return 100; }
+
+skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind, const void *values,
+                          skf_dtype vdtype, skf_copy_mode mode, skf_stream_t stream, skf_csr **A_out) {
+    if (!A_out) return fail(SKF_ERR_INVALID_ARG, "A_out is NULL");
+    *A_out = nullptr;
+    if (n < 1 || n >= (1ll << 31)) return fail(SKF_ERR_INVALID_ARG, "n must be in [1, 2^31)");
+    if (nnz < 0 || nnz >= (1ll << 31)) return fail(SKF_ERR_INVALID_ARG, "nnz must be in [0, 2^31)");
+    if (!rowptr || (nnz > 0 && (!colind || !values))) return fail(SKF_ERR_INVALID_ARG, "NULL CSR array");
+    if (vdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "matrix values must be F64 in this build");
+    if (mode != SKF_BORROW && mode != SKF_COPY) return fail(SKF_ERR_INVALID_ARG, "bad copy mode");
+    cudaStream_t st = (cudaStream_t)stream;
+    skf_csr *A = new skf_csr();
+    A->n = n;
+    A->nnz = nnz;
+    A->vdtype = vdtype;
+    int *dbad = nullptr;
+    unsigned long long *dmax = nullptr;
+    auto cleanup = [&](skf_status s) {
+        if (dbad) cudaFree(dbad);
+        if (dmax) cudaFree(dmax);
+        skf_destroy_csr(A);
+        return s;
+    };
+    if (cudaMalloc(&A->rowptr, sizeof(int32_t) * (n + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(SKF_ERR_OOM, "rowptr allocation"));
+    }
+    if (mode == SKF_COPY && nnz > 0) {
+        if (cudaMalloc(&A->colind_own, sizeof(int32_t) * nnz) != cudaSuccess ||
+            cudaMalloc(&A->values_own, sizeof(double) * nnz) != cudaSuccess) {
+            cudaGetLastError();
+            return cleanup(fail(SKF_ERR_OOM, "CSR copy allocation"));
+        }
+        if (cudaMemcpyAsync(A->colind_own, colind, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(A->values_own, values, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return cleanup(cuda_fail(cudaGetLastError(), "CSR copy"));
+        A->colind = A->colind_own;
+        A->values = A->values_own;
+    } else {
+        A->colind = colind;
+        A->values = values;
+    }
+    if (cudaMalloc(&dbad, sizeof(int)) != cudaSuccess || cudaMalloc(&dmax, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(SKF_ERR_OOM, "scratch allocation"));
+    }
+    cudaMemsetAsync(dbad, 0, sizeof(int), st);
+    cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st);
+    const int blocks = (int)std::min<int64_t>((n + 256) / 256, 8 * num_sms());
+    k_rowptr32<<<blocks, 256, 0, st>>>(rowptr, n, A->rowptr, dbad);
+    int64_t last = 0, first = 0;
+    cudaMemcpyAsync(&last, rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&first, rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    int hbad = 0;
+    cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "skf_create_csr"));
+    if (hbad || first != 0 || last != nnz) return cleanup(fail(SKF_ERR_INVALID_ARG, "invalid row pointer"));
+    k_row_abs_sum<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, dbad, dmax);
+    unsigned long long hmax = 0;
+    cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "skf_create_csr"));
+    if (hbad) return cleanup(fail(SKF_ERR_INVALID_ARG, "column index out of range"));
+    memcpy(&A->norm_inf, &hmax, sizeof(double));
+    cudaFree(dbad);
+    cudaFree(dmax);
+    *A_out = A;
+    return SKF_OK;
+}
+
+skf_status skf_destroy_csr(skf_csr *A) {
+    if (!A) return SKF_OK;
+    if (A->rowptr) cudaFree(A->rowptr);
+    if (A->colind_own) cudaFree(A->colind_own);
+    if (A->values_own) cudaFree(A->values_own);
+    delete A;
+    return SKF_OK;
+}
+
+skf_status skf_csr_norm_inf(const skf_csr *A, double *out_host) {
+    if (!A || !out_host) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    *out_host = A->norm_inf;
+    return SKF_OK;
+}
+
+skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t zeta, uint64_t seed,
+                             skf_stream_t stream, skf_sketch **S_out) {
+    (void)stream;
+    if (!S_out) return fail(SKF_ERR_INVALID_ARG, "S_out is NULL");
+    *S_out = nullptr;
+    if (n < 1 || s < 1) return fail(SKF_ERR_INVALID_ARG, "n and s must be positive");
+    if (kind == SKF_SKETCH_SPARSE_SIGN) {
+        if (zeta < 1 || zeta > s || zeta > kMaxZeta) return fail(SKF_ERR_INVALID_ARG, "need 1 <= zeta <= min(s, 16)");
+        if (s / zeta > 32768) return fail(SKF_ERR_INVALID_ARG, "s / zeta must be <= 32768");
+    } else if (kind == SKF_SKETCH_IDENTITY) {
+        if (s != n) return fail(SKF_ERR_INVALID_ARG, "identity sketch needs s == n");
+        zeta = 1;
+    } else if (kind == SKF_SKETCH_SRHT) {
+        return fail(SKF_ERR_NOT_SUPPORTED, "SRHT sketch not implemented in this build");
+    } else {
+        return fail(SKF_ERR_INVALID_ARG, "unknown sketch kind");
+    }
+    skf_sketch *S = new skf_sketch();
+    S->kind = kind;
+    S->n = n;
+    S->s = s;
+    S->zeta = zeta;
+    S->seed = seed;
+    *S_out = S;
+    return SKF_OK;
+}
+
+skf_status skf_sketch_destroy(skf_sketch *S) {
+    if (!S) return SKF_OK;
+    if (S->P) cudaFree(S->P);
+    delete S;
+    return SKF_OK;
+}
+
+skf_status skf_sketch_apply(const skf_sketch *S, const void *X, skf_dtype xdtype, int64_t ldx, int32_t ncols,
+                            double *SX, skf_stream_t stream) {
+    if (!S || (!X && ncols > 0) || (!SX && ncols > 0)) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    if (ncols < 0 || ldx < S->n) return fail(SKF_ERR_INVALID_ARG, "ncols < 0 or ldx < n");
+    if (xdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "X must be F64 in this build");
+    return sketch_apply_f64(S, (const double *)X, ldx, ncols, SX, (cudaStream_t)stream);
+}
+
+static skf_status check_common(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, int m, int k,
+                               skf_dtype basis) {
+    if (!A || !S || !b) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    if (S->n != A->n) return fail(SKF_ERR_INVALID_ARG, "sketch and matrix sizes differ");
+    if (m < 1 || m >= S->s) return fail(SKF_ERR_INVALID_ARG, "need 1 <= m < s");
+    if (m > A->n) return fail(SKF_ERR_INVALID_ARG, "need m <= n");
+    if (k < 1 || k > kMaxK) return fail(SKF_ERR_INVALID_ARG, "need 1 <= k <= 16");
+    if (bdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "b must be F64 in this build");
+    if (basis != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "basis must be F64 in this build");
+    return SKF_OK;
+}
+
+skf_status skf_arnoldi_trunc(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, int32_t m,
+                             int32_t k, skf_dtype basis_dtype, void *V, int64_t ldv, double *vscale, double *SV,
+                             double *SAV, double *H, skf_info *info, skf_stream_t stream) {
+    skf_status st = check_common(A, S, b, bdtype, m, k, basis_dtype);
+    if (st != SKF_OK) return st;
+    if (!V || !vscale || !SV || !SAV || !H) return fail(SKF_ERR_INVALID_ARG, "NULL output");
+    if (ldv < A->n) return fail(SKF_ERR_INVALID_ARG, "ldv < n");
+    cudaStream_t cs = (cudaStream_t)stream;
+    int *iscal = nullptr;
+    st = dalloc((void **)&iscal, sizeof(int) * 4, cs);
+    if (st != SKF_OK) return st;
+    st = arnoldi_run(A, S, (const double *)b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+    dfree(iscal, cs);
+    return st;
+}
+
+skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype,
+                     const skf_func *f, const skf_params *p, void *x, skf_dtype xdtype, skf_info *info,
+                     skf_stream_t stream) {
+    if (!f || !p || !x) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    skf_status st = check_common(A, S, b, bdtype, p->m, p->k, p->basis_dtype);
+    if (st != SKF_OK) return st;
+    if (method != SKF_METHOD_SFOM && method != SKF_METHOD_SGMRES) return fail(SKF_ERR_INVALID_ARG, "bad method");
+    if (xdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "x must be F64 in this build");
+    if (method == SKF_METHOD_SGMRES && S->s < 2 * p->m)
+        return fail(SKF_ERR_SKETCH_TOO_SMALL, "sGMRES needs s >= 2m");
+    if (f->n_nodes < 0 || (f->n_nodes > 0 && (!f->nodes || !f->weights)))
+        return fail(SKF_ERR_INVALID_ARG, "bad explicit rule");
+    if (f->n_nodes == 0 && f->kind != SKF_FUNC_INV) {
+        if (!(f->scale > 0.0)) return fail(SKF_ERR_INVALID_ARG, "rule scale must be > 0");
+        if (p->ell1 < 1 || p->ell2 <= p->ell1 || p->ell2 < 3 || p->ell_max < p->ell2)
+            return fail(SKF_ERR_INVALID_ARG, "need 1 <= ell1 < ell2, ell2 >= 3, ell_max >= ell2");
+        if (!(p->tol > 0.0)) return fail(SKF_ERR_INVALID_ARG, "tol must be > 0");
+    }
+    if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5 && f->n_nodes == 0)
+        return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
+    const RuleDev *rule = nullptr;
+    st = get_rule(*f, *p, &rule);
+    if (st != SKF_OK) return st;
+
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int m = p->m;
+    const int64_t n = A->n;
+    const int s = S->s;
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t szV = sizeof(double) * (size_t)n * m;
+    const size_t szS = sizeof(double) * (size_t)s * m;
+    const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
+    const size_t total = al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4);
+    char *ws = nullptr;
+    st = dalloc((void **)&ws, total, cs);
+    if (st != SKF_OK) return st;
+    size_t off = 0;
+    double *V = (double *)(ws + off); off += al(szV);
+    double *SV = (double *)(ws + off); off += al(szS);
+    double *SAV = (double *)(ws + off); off += al(szS);
+    double *H = (double *)(ws + off); off += al(szH);
+    double *vscale = (double *)(ws + off); off += al(sizeof(double) * m);
+    int *iscal = (int *)(ws + off);
+    st = arnoldi_run(A, S, (const double *)b, m, p->k, V, n, vscale, SV, SAV, H, iscal, nullptr, cs);
+    if (st == SKF_OK)
+        st = tail_run(method, s, m, n, V, n, vscale, SV, SAV, iscal, *rule, p->tol, (double *)x, info, cs);
+    dfree(ws, cs);
+    return st;
+}
+
+skf_status skf_sfom(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, const skf_func *f,
+                    const skf_params *p, void *x, skf_dtype xdtype, skf_info *info, skf_stream_t stream) {
+    return skf_solve(SKF_METHOD_SFOM, A, S, b, bdtype, f, p, x, xdtype, info, stream);
+}
+
+skf_status skf_sgmres(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, const skf_func *f,
+                      const skf_params *p, void *x, skf_dtype xdtype, skf_info *info, skf_stream_t stream) {
+    return skf_solve(SKF_METHOD_SGMRES, A, S, b, bdtype, f, p, x, xdtype, info, stream);
+}
+
+skf_status skf_quadrature_rule(const skf_func *f, int32_t ell, double *t_host, double *w_host) {
+    if (!f || !t_host || !w_host || ell < 1) return fail(SKF_ERR_INVALID_ARG, "bad argument");
+    if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5)
+        return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
+    if (!quadrature_rule(*f, ell, t_host, w_host)) return fail(SKF_ERR_NOT_SUPPORTED, "unknown function");
+    return SKF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+"""CPU checks of the C ABI boundary: the shared library loads, exports every
+function include/skf.h declares, validates arguments on the host, and its
+host-side quadrature rules equal the oracle's rules (Sec. 4.1, Sec. 5.1)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def skf():
+    import paper_2208_11447_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_2208_11447_gb300 import build
+        build.build()
+    pkg.lib()
+    return pkg
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "skf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(skf_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(skf):
+    names = declared_functions()
+    assert len(names) >= 14
+    L = skf.lib()
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_version_and_status_strings(skf):
+    L = skf.lib()
+    assert L.skf_version() >= 100
+    for code in range(10):
+        assert L.skf_status_string(code)
+
+
+def test_host_side_validation(skf):
+    import ctypes
+    L = skf.lib()
+    h = ctypes.c_void_p()
+    # zeta > s, identity with s != n, unknown kind: rejected before any device work
+    assert L.skf_sketch_create(skf.SPARSE_SIGN, 100, 4, 8, 1, None, ctypes.byref(h)) == 1
+    assert L.skf_sketch_create(skf.IDENTITY, 100, 50, 1, 1, None, ctypes.byref(h)) == 1
+    assert L.skf_sketch_create(7, 100, 50, 1, 1, None, ctypes.byref(h)) == 1
+    assert L.skf_create_csr(0, 0, None, None, None, 0, 0, None, ctypes.byref(h)) == 1
+    assert b"n must be" in L.skf_last_error()
+    # a valid sparse-sign description needs no device memory
+    assert L.skf_sketch_create(skf.SPARSE_SIGN, 1000, 64, 8, 5, None, ctypes.byref(h)) == 0
+    assert L.skf_sketch_destroy(h) == 0
+
+
+@pytest.mark.parametrize("func,ell,c", [("invsqrt", 45, 1.0), ("invsqrt", 300, 1885.0),
+                                        ("log1p_over_z", 22, 346.4), ("log1p_over_z", 400, 30.0),
+                                        ("inv", 1, 1.0)])
+def test_quadrature_rule_matches_oracle(skf, func, ell, c):
+    from oracle import quadrature as oq
+    t, w = skf.quadrature_rule(skf.make_func(func, c), ell)
+    to, wo = oq.rule(func, ell, c)
+    o1, o2 = np.argsort(t), np.argsort(to)
+    # the oracle forms 1 + x from x; the library from theta (x = cos theta), so
+    # the nodes nearest x = +-1 differ by the oracle's rounding of 1 -+ x
+    np.testing.assert_allclose(t[o1], to[o2], rtol=1e-9, atol=0)
+    np.testing.assert_allclose(w[o1], wo[o2], rtol=1e-8, atol=0)
+    np.testing.assert_allclose(t[o1][5:-5], to[o2][5:-5], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("func,lo,hi,ell", [("invsqrt", 29.6, 1.2e5, 200), ("log1p_over_z", 1e-3, 1.2e5, 300)])
+def test_quadrature_rule_reproduces_f(skf, func, lo, hi, ell):
+    """Sum_i w_i / (t_i + z) equals the closed form f(z) on the interval."""
+    from oracle.quadrature import fscalar
+    c = math.sqrt(lo * hi) if func == "invsqrt" else math.sqrt(1 + hi)
+    t, w = skf.quadrature_rule(skf.make_func(func, c), ell)
+    z = np.geomspace(lo, hi, 60)
+    approx = (w[None, :] / (t[None, :] + z[:, None])).sum(1)
+    np.testing.assert_allclose(approx, np.real(fscalar(func, z)), rtol=2e-13)
