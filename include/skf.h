@@ -125,6 +125,10 @@ typedef struct {
 const char *skf_last_error(void);
 const char *skf_status_string(skf_status s);
 int32_t skf_version(void);     /* major*10000 + minor*100 + patch */
+/* Number of CUDA kernel launches this library has issued since it was
+ * loaded, counted on the host at launch time (a diagnostic for profilers and
+ * benchmarks; no device work). */
+int64_t skf_kernel_launch_count(void);
 
 /* ------------------------------------------------------------ operator */
 /* skf_create_csr: wrap or copy a CSR matrix A (Sec. 2.2 assumes a sparse A
@@ -148,8 +152,11 @@ skf_status skf_csr_norm_inf(const skf_csr *A, double *out_host);
 
 /* -------------------------------------------------------------- sketch */
 /* skf_sketch_create: draw the embedding S in R^{s x N} (Algorithm 1, line 1;
- * eq. (1.1)).  O(s) storage; the sparse-sign pattern is recomputed from the
- * seed on the fly.  Definitions (identical to the CPU oracle's):
+ * eq. (1.1)).  The sparse-sign pattern is expanded once on the device from
+ * its definition below (2 zeta bytes per column, plus the largest number of
+ * nonzeros one kernel row block puts into one row of S, which sizes the
+ * fixed-point accumulators); this call synchronises `stream`.  Definitions
+ * (identical to the CPU oracle's):
  *   word(seed, i) = mix64(seed + (i+1) * 0x9E3779B97F4A7C15) (SplitMix64,
  *     Steele, Lea & Flood 2014), mix64 = xor-shift-multiply finaliser with
  *     constants 0xBF58476D1CE4E5B9, 0x94D049BB133111EB, shifts 30, 27, 31.
@@ -209,7 +216,7 @@ skf_status skf_arnoldi_trunc(const skf_csr *A, const skf_sketch *S, const void *
  * c = Q^T S b.  Orders follow Sec. 4.1: ell1, ell2, then ell2 <-
  * floor(sqrt(2) ell2) until ||q_ell1 - q_ell2|| <= tol ||q_ell2|| or
  * ell_max is passed (info->status = QUAD_NOT_CONVERGED, x from the last
- * order).  Requires s >= 2m for SGMRES.
+ * order).  Requires s >= 2m for SGMRES and m <= 512 (dense tail).
  *   b  device F64 [N];   x  device F64 [N] (output)
  *   workspace is allocated stream-ordered (cudaMallocAsync) and released
  *   before return, so the call can be captured into a CUDA graph.

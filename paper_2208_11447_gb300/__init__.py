@@ -74,6 +74,7 @@ def lib():
         L.skf_status_string.restype = ctypes.c_char_p
         L.skf_status_string.argtypes = [ctypes.c_int]
         L.skf_version.restype = i32
+        L.skf_kernel_launch_count.restype = i64
         L.skf_create_csr.argtypes = [i64, i64, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
         L.skf_destroy_csr.argtypes = [vp]
         L.skf_csr_norm_inf.argtypes = [vp, ctypes.POINTER(dbl)]
@@ -236,6 +237,10 @@ def sfom(A, S, b, f, p, x=None, info=None, stream=None):
 
 def sgmres(A, S, b, f, p, x=None, info=None, stream=None):
     return solve(SGMRES, A, S, b, f, p, x, info, stream)
+
+
+def kernel_launch_count() -> int:
+    return int(lib().skf_kernel_launch_count())
 
 
 def quadrature_rule(f: Func, ell: int):

@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -24,6 +25,9 @@ skf_status cuda_fail(cudaError_t e, const char *what) {
     if (e == cudaErrorMemoryAllocation) return SKF_ERR_OOM;
     return SKF_ERR_CUDA;
 }
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int num_sms() {
     static int cached = 0;
@@ -219,6 +223,33 @@ __global__ void k_row_abs_sum(const int32_t *__restrict__ rp, const int32_t *__r
     atomicMax(maxbits, (unsigned long long)__double_as_longlong(mx));
 }
 
+// SELL-32 layout: slice widths, then entries (see skf_csr).
+__global__ void k_sell_width(const int32_t *__restrict__ rp, int64_t n, int64_t nslices, int32_t *__restrict__ w) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nslices; t += (int64_t)gridDim.x * blockDim.x) {
+        int mx = 0;
+        for (int64_t r = 32 * t; r < min(n, 32 * t + 32); ++r) mx = max(mx, rp[r + 1] - rp[r]);
+        w[t] = mx;
+    }
+}
+
+__global__ void k_sell_fill(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
+                            int64_t n, int64_t nslices, const int64_t *__restrict__ off, const int32_t *__restrict__ w,
+                            double *__restrict__ sv, int32_t *__restrict__ sc) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < 32 * nslices;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = r >> 5;
+        const int l = (int)(r & 31);
+        const int wt = w[t];
+        const int b = r < n ? rp[r] : 0, len = r < n ? rp[r + 1] - b : 0;
+        const int self = r < n ? (int)r : 0;
+        for (int p = 0; p < wt; ++p) {
+            const int64_t o = off[t] + 32ll * p + l;
+            sv[o] = p < len ? v[b + p] : 0.0;
+            sc[o] = p < len ? ci[b + p] : self;
+        }
+    }
+}
+
 }  // namespace
 }  // namespace skf
 
@@ -245,6 +276,8 @@ const char *skf_status_string(skf_status s) {
 }
 
 int32_t skf_version(void) { return 100; }
+
+int64_t skf_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
 
 skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind, const void *values,
                           skf_dtype vdtype, skf_copy_mode mode, skf_stream_t stream, skf_csr **A_out) {
@@ -295,6 +328,7 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
     cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st);
     const int blocks = (int)std::min<int64_t>((n + 256) / 256, 8 * num_sms());
     k_rowptr32<<<blocks, 256, 0, st>>>(rowptr, n, A->rowptr, dbad);
+    count_launches(1);
     int64_t last = 0, first = 0;
     cudaMemcpyAsync(&last, rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(&first, rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
@@ -304,6 +338,7 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "skf_create_csr"));
     if (hbad || first != 0 || last != nnz) return cleanup(fail(SKF_ERR_INVALID_ARG, "invalid row pointer"));
     k_row_abs_sum<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, dbad, dmax);
+    count_launches(1);
     unsigned long long hmax = 0;
     cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -311,6 +346,37 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "skf_create_csr"));
     if (hbad) return cleanup(fail(SKF_ERR_INVALID_ARG, "column index out of range"));
     memcpy(&A->norm_inf, &hmax, sizeof(double));
+    // SELL-32 copy for the kernels
+    A->nslices = (n + 31) / 32;
+    std::vector<int32_t> hw(A->nslices);
+    std::vector<int64_t> hoff(A->nslices + 1);
+    if (cudaMalloc(&A->sell_w, sizeof(int32_t) * A->nslices) != cudaSuccess ||
+        cudaMalloc(&A->sell_off, sizeof(int64_t) * (A->nslices + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(SKF_ERR_OOM, "SELL allocation"));
+    }
+    k_sell_width<<<blocks, 256, 0, st>>>(A->rowptr, n, A->nslices, A->sell_w);
+    count_launches(1);
+    cudaMemcpyAsync(hw.data(), A->sell_w, sizeof(int32_t) * A->nslices, cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "SELL widths"));
+    hoff[0] = 0;
+    for (int64_t t = 0; t < A->nslices; ++t) {
+        hoff[t + 1] = hoff[t] + 32ll * hw[t];
+        A->max_width = std::max(A->max_width, hw[t]);
+    }
+    const int64_t padded = hoff[A->nslices];
+    if (cudaMalloc(&A->sell_val, sizeof(double) * std::max<int64_t>(padded, 1)) != cudaSuccess ||
+        cudaMalloc(&A->sell_col, sizeof(int32_t) * std::max<int64_t>(padded, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(SKF_ERR_OOM, "SELL allocation"));
+    }
+    cudaMemcpyAsync(A->sell_off, hoff.data(), sizeof(int64_t) * (A->nslices + 1), cudaMemcpyHostToDevice, st);
+    k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, A->nslices, A->sell_off,
+                                        A->sell_w, A->sell_val, A->sell_col);
+    count_launches(1);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "SELL fill"));
     cudaFree(dbad);
     cudaFree(dmax);
     *A_out = A;
@@ -322,6 +388,10 @@ skf_status skf_destroy_csr(skf_csr *A) {
     if (A->rowptr) cudaFree(A->rowptr);
     if (A->colind_own) cudaFree(A->colind_own);
     if (A->values_own) cudaFree(A->values_own);
+    if (A->sell_off) cudaFree(A->sell_off);
+    if (A->sell_w) cudaFree(A->sell_w);
+    if (A->sell_val) cudaFree(A->sell_val);
+    if (A->sell_col) cudaFree(A->sell_col);
     delete A;
     return SKF_OK;
 }
@@ -334,7 +404,6 @@ skf_status skf_csr_norm_inf(const skf_csr *A, double *out_host) {
 
 skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t zeta, uint64_t seed,
                              skf_stream_t stream, skf_sketch **S_out) {
-    (void)stream;
     if (!S_out) return fail(SKF_ERR_INVALID_ARG, "S_out is NULL");
     *S_out = nullptr;
     if (n < 1 || s < 1) return fail(SKF_ERR_INVALID_ARG, "n and s must be positive");
@@ -355,6 +424,13 @@ skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t
     S->s = s;
     S->zeta = zeta;
     S->seed = seed;
+    if (kind == SKF_SKETCH_SPARSE_SIGN) {
+        const skf_status st = build_sparse_sign_tables(S, (cudaStream_t)stream);
+        if (st != SKF_OK) {
+            skf_sketch_destroy(S);
+            return st;
+        }
+    }
     *S_out = S;
     return SKF_OK;
 }
@@ -362,6 +438,8 @@ skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t
 skf_status skf_sketch_destroy(skf_sketch *S) {
     if (!S) return SKF_OK;
     if (S->P) cudaFree(S->P);
+    if (S->pattern) cudaFree(S->pattern);
+    if (S->binmax) cudaFree(S->binmax);
     delete S;
     return SKF_OK;
 }
@@ -410,6 +488,7 @@ skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, c
     if (st != SKF_OK) return st;
     if (method != SKF_METHOD_SFOM && method != SKF_METHOD_SGMRES) return fail(SKF_ERR_INVALID_ARG, "bad method");
     if (xdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "x must be F64 in this build");
+    if (p->m > 512) return fail(SKF_ERR_NOT_SUPPORTED, "m > 512 is not supported by the dense tail");
     if (method == SKF_METHOD_SGMRES && S->s < 2 * p->m)
         return fail(SKF_ERR_SKETCH_TOO_SMALL, "sGMRES needs s >= 2m");
     if (f->n_nodes < 0 || (f->n_nodes > 0 && (!f->nodes || !f->weights)))
@@ -445,7 +524,7 @@ skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, c
     double *H = (double *)(ws + off); off += al(szH);
     double *vscale = (double *)(ws + off); off += al(sizeof(double) * m);
     int *iscal = (int *)(ws + off);
-    st = arnoldi_run(A, S, (const double *)b, m, p->k, V, n, vscale, SV, SAV, H, iscal, nullptr, cs);
+    st = arnoldi_run(A, S, (const double *)b, m, p->k, V, n, vscale, SV, SAV, H, iscal, info, cs);
     if (st == SKF_OK)
         st = tail_run(method, s, m, n, V, n, vscale, SV, SAV, iscal, *rule, p->tol, (double *)x, info, cs);
     dfree(ws, cs);

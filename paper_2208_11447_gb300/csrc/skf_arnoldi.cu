@@ -8,28 +8,39 @@
 //   spmv   (step j): y~ = A w_j on the CTA's rows -> Y; partial dots
 //                    <w_i, y~> (i in the window), Gram <w_j, w_i>, max|y~|;
 //                    fixed-point sketch of w_j (-> S v_j).
-//   update (step j): every CTA reduces the partials in a fixed order, forms
-//                    the MGS coefficients from the dots and the window Gram
-//                    matrix (identical to MGS in exact arithmetic), writes
+//   update (step j): MGS coefficients from the reduced dots and the window
+//                    Gram matrix (identical to MGS in exact arithmetic),
 //                    w_{j+1} = sigma_j y~ - sum_i h_ij sigma_i w_i, partial
 //                    ||w_{j+1}||^2 and max|w_{j+1}|; fixed-point sketch of y~
 //                    (-> S A v_j).
 //
-// Cross-CTA reductions always run in CTA order, so the results do not depend
-// on scheduling.  Sketch partial sums are integers (exact), see skf_internal.
+// Cross-CTA reductions: every CTA writes its partials; the CTA that arrives
+// last (atomic ticket, no waiting) reduces them in a fixed order and publishes
+// the totals for the next launch.  Sketch partial sums are integers, reduced
+// exactly.  Results therefore do not depend on scheduling.
 #include <math.h>
+
+#include <algorithm>
 
 #include "skf_internal.cuh"
 
 namespace skf {
 
+constexpr int kP1 = kMaxK + 1;    // slots of one spmv partial: d[kMaxK], ymax
+constexpr int kP2 = kMaxK + 2;    // slots of one update partial: ||w||^2, max|w|, g[kMaxK]
+constexpr int kSpmvThreads = 1024; // threads per CTA of the SpMV kernel: one CTA per SM
+constexpr int kUpdThreads = 512;  // threads per CTA of the update kernel
+
 struct ArnCtx {
     int64_t n;
-    const int32_t *rowptr;
-    const int32_t *colind;
-    const double *vals;
+    const int64_t *sell_off;   // SELL-32 operator (see skf_csr)
+    const int32_t *sell_w;
+    const double *sell_val;
+    const int32_t *sell_col;
+    int max_width;             // widest SELL slice
     SparseSign sp;
-    int frac;          // fixed-point fraction bits
+    const uint16_t *pattern;   // expanded sparse-sign pattern [n][zeta]
+    const int *binmax;         // bin-load maximum of the row partition
     int identity;      // S = I
     int m, k;
     double *V;
@@ -38,27 +49,65 @@ struct ArnCtx {
     double *SV, *SAV;  // s x m
     double *H;         // (m+1) x m
     double *Y;         // [n]
-    double *p1;        // [G][2*kMaxK]: d[0..k-1], g[0..k-2], ymax at slot 2*kMaxK-1
-    double *p2;        // [2][G][2]: ||w||^2, max|w|
+    double *p1;        // [G][kP1] spmv partials
+    double *p2;        // [G][kP2] update partials: ||w||^2, max|w|, <w_{j+1}, w_{j+1-d}>
+    double *fin_d;     // [m][kP1] reduced spmv partials of step j
+    double *fin_w;     // [m+1][2] ||w_j||^2, max|w_j|
+    double *stepsc;    // [m+1][4] per-step scalars, computed once: 1/||w_j||, ||w_j||, stop flag
+    double inv_sqrt_zeta;
+    unsigned *cnt;     // [2] arrival tickets of the spmv / update launches
     long long *skSV;   // [G][s]
     long long *skSAV;  // [G][s]
-    double *gram;      // [m][kMaxK]: <w_j, w_{j-d}>, d = 1..k-1
-    int *eys;          // [m] exponent of max|y~_j| (INT_MIN if zero)
+    double *gram;      // [m][kMaxK]: <w_j, w_{j-d}>, d = 1..k-1 (reduced by the update kernel of step j-1)
+    int *eys;          // [m] exponent of max|y~_j| (kNoExp if zero)
+    int *ews;          // [m] exponent of max|w_j|
+    double *epscol;    // [m] | ||S v_j||^2 - 1 |
     int *iscal;        // [0] stopped, [1] m_eff, [2] status, [3] step that stopped
-    int64_t rows_per_cta;
+    int64_t rows_per_cta;      // row partition of the update kernel (sized the sketch tables)
+    int64_t spmv_rows;         // rows per CTA of the SpMV kernel (multiple of 32)
+    int G_upd;                 // CTAs of the update kernel = number of sketch partials
 };
 
 namespace {
 
-constexpr int kP1 = 2 * kMaxK;
 constexpr int kNoExp = -100000;
 
-// Sums (or maxes) of G per-CTA partials, computed by one warp in a fixed order.
+// Exact sum of G int64 partials by one warp (lanes strided over G, 128-bit
+// butterfly); every lane returns the same double.
+__device__ __forceinline__ double warp_sum_i64_exact(const long long *p, int G, size_t stride) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long lo = 0;
+    long long hi = 0;
+    for (int g = lane; g < G; g += 32) {
+        const long long v = __ldcg(p + (size_t)g * stride);
+        const unsigned long long nlo = lo + (unsigned long long)v;
+        hi += (v < 0 ? -1 : 0) + (nlo < lo ? 1 : 0);
+        lo = nlo;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        const long long ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const unsigned long long nlo = lo + olo;
+        hi += ohi + (nlo < lo ? 1 : 0);
+        lo = nlo;
+    }
+    const bool neg = hi < 0;
+    unsigned long long uhi = (unsigned long long)hi;
+    if (neg) {
+        lo = ~lo + 1ull;
+        uhi = ~uhi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const double r = (double)uhi * 18446744073709551616.0 + (double)lo;
+    return neg ? -r : r;
+}
+
+// Fixed-order reduction of G partials by one warp (sum or max).
 __device__ __forceinline__ double warp_reduce_partials(const double *p, int G, int stride, bool is_max) {
     const int lane = threadIdx.x & 31;
     double acc = 0.0;
     for (int g = lane; g < G; g += 32) {
-        const double v = p[(size_t)g * stride];
+        const double v = __ldcg(p + (size_t)g * stride);
         acc = is_max ? fmax(acc, v) : acc + v;
     }
 #pragma unroll
@@ -69,35 +118,48 @@ __device__ __forceinline__ double warp_reduce_partials(const double *p, int G, i
     return acc;
 }
 
-__device__ __forceinline__ void sketch_scatter(const SparseSign &sp, uint32_t *lo, uint32_t *hi, int64_t r,
-                                               long long v) {
-    if (v == 0) return;
-    uint64_t word = 0;
-    for (int q = 0; q < sp.zeta; ++q) {
-        if ((q & 3) == 0) word = splitmix_word(sp.seed, (uint64_t)r * sp.words + (q >> 2));
-        int row;
-        bool neg;
-        sparse_sign_entry(sp, word, q, row, neg);
-        atomic_add_i64_split(lo + row, hi + row, neg ? -v : v);
+// The zeta pattern entries of column r (one 16-byte load for zeta = 8).
+template <int ZCAP>
+__device__ __forceinline__ void load_pattern(const uint16_t *pattern, int zeta, int64_t r, uint16_t (&e)[ZCAP]) {
+    if (ZCAP == 8 && zeta == 8) {
+        const uint4 v = __ldg((const uint4 *)(pattern + r * 8));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) e[q] = (uint16_t)(w[q >> 1] >> (16 * (q & 1)));
+    } else {
+#pragma unroll
+        for (int q = 0; q < ZCAP; ++q) e[q] = q < zeta ? __ldg(pattern + r * zeta + q) : (uint16_t)0;
     }
 }
 
-// Finalise sketch column `col` from the integer partials for this CTA's
-// slice of the s rows.
+// Finalise a sketch column from the integer partials, for this CTA's slice of
+// the s rows: one warp per row of S.
 __device__ __forceinline__ void finalize_sketch(const long long *part, int G, int s, int E, int frac, double scale,
                                                 double *out_col) {
     const int per = (s + gridDim.x - 1) / gridDim.x;
     const int i0 = blockIdx.x * per;
     const int i1 = min(s, i0 + per);
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        if (E == kNoExp) {
-            out_col[i] = 0.0;
-        } else {
-            const double tot = sum_i64_exact(part + i, G, (size_t)s);
-            out_col[i] = ldexp(tot, E - frac) * scale;
-        }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = i0 + warp; i < i1; i += blockDim.x / 32) {
+        double v = 0.0;
+        if (E != kNoExp) v = ldexp(warp_sum_i64_exact(part + i, G, (size_t)s), E - frac) * scale;
+        if (lane == 0) out_col[i] = v;
     }
 }
+
+// Arrival ticket: true in exactly one CTA, the last to finish its partials.
+__device__ __forceinline__ bool last_to_arrive(unsigned *cnt) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
 
 __global__ void __launch_bounds__(kThreads) k_arnoldi_init(ArnCtx c, const double *__restrict__ b) {
     __shared__ double red[64];
@@ -108,14 +170,14 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_init(ArnCtx c, const doubl
     for (int64_t r = r0 + threadIdx.x; r < r1; r += kThreads) {
         const double x = b[r];
         c.V[r] = x;
-        nrm[0] += x * x;
+        nrm[0] = fma(x, x, nrm[0]);
         mx = fmax(mx, fabs(x));
     }
     block_sum<1>(nrm, red);
     mx = block_max(mx, red);
     if (threadIdx.x == 0) {
-        c.p2[(size_t)blockIdx.x * 2 + 0] = nrm[0];
-        c.p2[(size_t)blockIdx.x * 2 + 1] = mx;
+        c.p2[(size_t)blockIdx.x * kP2 + 0] = nrm[0];
+        c.p2[(size_t)blockIdx.x * kP2 + 1] = mx;
     }
     if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i < (c.m + 1) * c.m; i += kThreads) c.H[i] = 0.0;
@@ -126,133 +188,140 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_init(ArnCtx c, const doubl
             c.iscal[3] = c.m;
         }
     }
+    if (last_to_arrive(c.cnt + 1)) {
+        const int warp = threadIdx.x >> 5;
+        if (warp < 2) {
+            const double v = warp_reduce_partials(c.p2 + warp, gridDim.x, kP2, warp == 1);
+            if ((threadIdx.x & 31) == 0) c.fin_w[warp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double n2 = c.fin_w[0];
+            const double hn = sqrt(n2);
+            c.stepsc[0] = n2 > 0.0 ? 1.0 / hn : 0.0;
+            c.stepsc[1] = hn;
+            c.stepsc[2] = n2 > 0.0 ? 0.0 : 1.0;   // zero right-hand side
+            c.cnt[1] = 0u;
+        }
+    }
 }
 
-template <int KW>
-__global__ void __launch_bounds__(kThreads) k_arnoldi_spmv(ArnCtx c, int j) {
-    extern __shared__ uint32_t bins[];
-    __shared__ double red[32 * kP1];
-    __shared__ double sv[4];
+template <int KW, int WMAX>
+__global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int j) {
+    __shared__ double red[BlockSumTraits<KW, kSpmvThreads>::kSmem];
     // a stop decided by an earlier launch; a stop decided in this launch is
     // recomputed identically by every CTA below
     if (c.iscal[0] && c.iscal[3] < j) return;
     const int G = gridDim.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double *p2 = c.p2 + (size_t)(j & 1) * G * 2;
-    if (warp < 2) {
-        const double v = warp_reduce_partials(p2 + warp, G, 2, warp == 1);
-        if (lane == 0) sv[warp] = v;
-    }
-    __syncthreads();
-    const double wnorm2 = sv[0], wmax = sv[1];
     const int s = c.sp.s;
 
-    // S A v_{j-1} from the integer partials the previous update kernel wrote
-    if (j >= 1 && !c.identity)
-        finalize_sketch(c.skSAV, G, s, c.eys[j - 1], c.frac, c.vscale[j - 1] / sqrt((double)c.sp.zeta),
-                        c.SAV + (size_t)(j - 1) * s);
+    // S v_{j-1} and S A v_{j-1} from the integer partials of the previous update kernel
+    if (j >= 1 && !c.identity) {
+        const int frac = sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
+        const double sc = c.vscale[j - 1] * c.inv_sqrt_zeta;
+        finalize_sketch(c.skSV, c.G_upd, s, c.ews[j - 1], frac, sc, c.SV + (size_t)(j - 1) * s);
+        finalize_sketch(c.skSAV, c.G_upd, s, c.eys[j - 1], frac, sc, c.SAV + (size_t)(j - 1) * s);
+    }
 
-    // zero right-hand side / happy breakdown: ||w_j|| <= 1e-12 ||A v_{j-1}||
-    if (j == 0) {
-        if (!(wnorm2 > 0.0)) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                c.iscal[0] = 1;
-                c.iscal[1] = 0;
-                c.iscal[2] = SKF_ERR_ZERO_RHS;
-                c.iscal[3] = 0;
-            }
-            return;
+    // zero right-hand side (j = 0) or happy breakdown ||w_j|| <= 1e-12 ||A v_{j-1}||,
+    // decided once by the previous launch
+    const double *sc_j = c.stepsc + 4 * (size_t)j;
+    if (j >= 1 && blockIdx.x == 0 && threadIdx.x == 0) c.H[j + (size_t)(j - 1) * (c.m + 1)] = sc_j[1];
+    if (sc_j[2] != 0.0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c.iscal[0] = 1;
+            c.iscal[1] = j;
+            c.iscal[3] = j;
+            if (j == 0) c.iscal[2] = SKF_ERR_ZERO_RHS;
         }
-    } else {
-        const int i0p = max(0, j - c.k);
-        double hs = 0.0;
-        for (int i = i0p; i <= j - 1; ++i) {
-            const double h = c.H[i + (size_t)(j - 1) * (c.m + 1)];
-            hs += h * h;
-        }
-        const double hn = sqrt(wnorm2);
-        if (blockIdx.x == 0 && threadIdx.x == 0) c.H[j + (size_t)(j - 1) * (c.m + 1)] = hn;
-        if (!(hn > 1e-12 * sqrt(hs + wnorm2))) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                c.iscal[0] = 1;
-                c.iscal[1] = j;
-                c.iscal[3] = j;
-            }
-            return;
-        }
+        return;
     }
 
     const int i0 = max(0, j - c.k + 1);
     const int nw = j - i0 + 1;
-    uint32_t *lo = bins, *hi = bins + s;
-    if (!c.identity) {
-        for (int i = threadIdx.x; i < 2 * s; i += kThreads) bins[i] = 0u;
-    }
-    __syncthreads();
-    const int shift = c.frac - bound_exponent(wmax);
-
-    // acc[0..KW-1]: <w_i, y~>; acc[KW..2KW-2]: <w_j, w_i>
-    double acc[2 * KW];
+    // acc[a] = <w_{i0+a}, y~>
+    double acc[KW];
 #pragma unroll
-    for (int i = 0; i < 2 * KW; ++i) acc[i] = 0.0;
+    for (int i = 0; i < KW; ++i) acc[i] = 0.0;
     double ymax = 0.0;
     const double *wj = c.V + (size_t)j * c.ldv;
-    const int64_t r0 = (int64_t)blockIdx.x * c.rows_per_cta;
-    const int64_t r1 = min(c.n, r0 + c.rows_per_cta);
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += kThreads) {
-        const int p0 = c.rowptr[r], pe = c.rowptr[r + 1];
+    const int64_t r0 = (int64_t)blockIdx.x * c.spmv_rows;
+    const int64_t r1 = min(c.n, r0 + c.spmv_rows);
+    unsigned long long ykey = 0;
+    // rows_per_cta is a multiple of 32, so each warp works on whole slices;
+    // the slice width and offset are loaded once per warp, and for slices up
+    // to WMAX wide all value/column loads of a row are issued together
+    const int lane = threadIdx.x & 31;
+    for (int64_t rw = r0 + (threadIdx.x & ~31); rw < r1; rw += kSpmvThreads) {
+        const int64_t t = rw >> 5;
+        int wt = 0;
+        long long so = 0;
+        if (lane == 0) {
+            wt = __ldg(c.sell_w + t);
+            so = __ldg(c.sell_off + t);
+        }
+        wt = __shfl_sync(0xffffffffu, wt, 0);
+        so = __shfl_sync(0xffffffffu, so, 0);
+        const int64_t r = rw + lane;
+        if (r >= r1) continue;
+        const int64_t base = so + lane;
         double y = 0.0;
-        for (int p = p0; p < pe; ++p) y = fma(c.vals[p], wj[c.colind[p]], y);
-        c.Y[r] = y;
-        const double wjr = wj[r];
+        if (wt <= WMAX) {
+            double av[WMAX], xv[WMAX];
 #pragma unroll
-        for (int sl = 0; sl < KW; ++sl) {
-            if (sl < nw) {
-                const double wi = (sl == nw - 1) ? wjr : c.V[r + (size_t)(i0 + sl) * c.ldv];
-                acc[sl] = fma(wi, y, acc[sl]);
-                if (sl < nw - 1) acc[KW + sl] = fma(wjr, wi, acc[KW + sl]);
+            for (int p = 0; p < WMAX; ++p) {
+                if (p < wt) {
+                    const int64_t o = base + 32ll * p;
+                    av[p] = __ldg(c.sell_val + o);
+                    xv[p] = wj[__ldg(c.sell_col + o)];
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < WMAX; ++p)
+                if (p < wt) y = fma(av[p], xv[p], y);
+        } else {
+            for (int p = 0; p < wt; ++p) {
+                const int64_t o = base + 32ll * p;
+                y = fma(__ldg(c.sell_val + o), wj[__ldg(c.sell_col + o)], y);
             }
         }
-        ymax = fmax(ymax, fabs(y));
-        if (!c.identity) sketch_scatter(c.sp, lo, hi, r, fixed_point(wjr, shift));
+        c.Y[r] = y;
+#pragma unroll
+        for (int a = 0; a < KW; ++a)
+            if (a < nw) acc[a] = fma(c.V[r + (size_t)(i0 + a) * c.ldv], y, acc[a]);
+        ykey = max(ykey, abs_key(y));
     }
-    block_sum<2 * KW>(acc, red);
-    ymax = block_max(ymax, red);
+    block_sum_auto<KW, kSpmvThreads>(acc, red);
+    ymax = key_to_abs(block_max_key<kSpmvThreads>(ykey, (unsigned long long *)red));
     if (threadIdx.x == 0) {
         double *o = c.p1 + (size_t)blockIdx.x * kP1;
-        for (int i = 0; i < kP1 - 1; ++i) o[i] = 0.0;
         for (int i = 0; i < KW; ++i) o[i] = acc[i];
-        for (int i = 0; i < KW - 1; ++i) o[kMaxK + i] = acc[KW + i];
         o[kP1 - 1] = ymax;
     }
-    if (!c.identity) {
-        long long *o = c.skSV + (size_t)blockIdx.x * s;
-        for (int i = threadIdx.x; i < s; i += kThreads)
-            o[i] = (long long)(((unsigned long long)hi[i] << 32) | lo[i]);
+    if (last_to_arrive(c.cnt)) {
+        // reduce only the slots in use: d[0..nw-1], ymax
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int v = warp; v <= nw; v += kSpmvThreads / 32) {
+            const int slot = (v < nw) ? v : kP1 - 1;
+            const double r = warp_reduce_partials(c.p1 + slot, G, kP1, slot == kP1 - 1);
+            if (lane == 0) c.fin_d[(size_t)j * kP1 + slot] = r;
+        }
+        if (threadIdx.x == 0) c.cnt[0] = 0u;
     }
 }
 
-template <int KW>
-__global__ void __launch_bounds__(kThreads) k_arnoldi_update(ArnCtx c, int j) {
-    extern __shared__ uint32_t bins[];
-    __shared__ double red[64];
-    __shared__ double sd[kP1 + 2];
+template <int KW, int ZCAP>
+__global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j) {
+    extern __shared__ int bins[];
+    __shared__ double red[BlockSumTraits<KW + 1, kUpdThreads>::kSmem];
     __shared__ double sh[kMaxK];     // MGS coefficients h_ij
     __shared__ double scoef[kMaxK];  // h_ij * sigma_i
     if (c.iscal[0]) return;          // set at the latest by the spmv launch of this step
     const int G = gridDim.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double *p2 = c.p2 + (size_t)(j & 1) * G * 2;
-    for (int v = warp; v < kP1 + 2; v += kThreads / 32) {
-        double r;
-        if (v < kP1) r = warp_reduce_partials(c.p1 + v, G, kP1, v == kP1 - 1);
-        else r = warp_reduce_partials(p2 + (v - kP1), G, 2, v == kP1 + 1);
-        if (lane == 0) sd[v] = r;
-    }
-    __syncthreads();
-    const double sigma = 1.0 / sqrt(sd[kP1]);
-    const double wmax = sd[kP1 + 1];
-    const double ymax = sd[kP1 - 1];
+    const double *fd = c.fin_d + (size_t)j * kP1;
+    const double sigma = c.stepsc[4 * (size_t)j];
+    const double wmax = c.fin_w[2 * j + 1];
+    const double ymax = fd[kP1 - 1];
     const int s = c.sp.s;
     const int i0 = max(0, j - c.k + 1);
     const int nw = j - i0 + 1;
@@ -263,11 +332,11 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_update(ArnCtx c, int j) {
         for (int a = 0; a < nw; ++a) {
             const int ia = i0 + a;
             const double sa = (ia == j) ? sigma : c.vscale[ia];
-            double h = sa * sigma * sd[a];
+            double h = sa * sigma * fd[a];
             for (int b2 = 0; b2 < a; ++b2) {
                 const int ib = i0 + b2;
                 const double sb = c.vscale[ib];
-                const double gab = (ia == j) ? sd[kMaxK + b2] : c.gram[(size_t)ia * kMaxK + (ia - ib)];
+                const double gab = c.gram[(size_t)ia * kMaxK + (ia - ib)];
                 h -= sh[b2] * sa * sb * gab;
             }
             sh[a] = h;
@@ -281,81 +350,166 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_update(ArnCtx c, int j) {
         c.eys[j] = ey;
         if (j < c.m - 1)
             for (int a = 0; a < nw; ++a) c.H[(i0 + a) + (size_t)j * (c.m + 1)] = sh[a];
-        for (int d = 1; d < nw; ++d) c.gram[(size_t)j * kMaxK + d] = sd[kMaxK + (nw - 1 - d)];
     }
-    // S v_j from the integer partials of the spmv kernel
+    // fixed-point sketches of w_j (-> S v_j) and y~ (-> S A v_j), two limbs each
+    int *aw0 = bins, *aw1 = bins + s, *ay0 = bins + 2 * s, *ay1 = bins + 3 * s;
     if (!c.identity)
-        finalize_sketch(c.skSV, G, s, wmax > 0.0 ? bound_exponent(wmax) : kNoExp, c.frac,
-                        sigma / sqrt((double)c.sp.zeta), c.SV + (size_t)j * s);
-
-    uint32_t *lo = bins, *hi = bins + s;
-    if (!c.identity)
-        for (int i = threadIdx.x; i < 2 * s; i += kThreads) bins[i] = 0u;
+        for (int i = threadIdx.x; i < 4 * s; i += kUpdThreads) bins[i] = 0;
     __syncthreads();
-    const int shift = c.frac - (ey == kNoExp ? 0 : ey);
+    const int L = c.identity ? 0 : limb_bits(*c.binmax);
+    const int frac = sketch_fraction_bits_from_limb(L);
+    const long long lmask = (1ll << L) - 1;
+    const int ew = wmax > 0.0 ? bound_exponent(wmax) : kNoExp;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.ews[j] = ew;
+    const int shift_w = frac - (ew == kNoExp ? 0 : ew);
+    const int shift_y = frac - (ey == kNoExp ? 0 : ey);
     const bool do_update = j < c.m - 1;
-    double nrm[1] = {0.0};
-    double nmax = 0.0;
+    // part[0] = ||w_{j+1}||^2, part[1 + a] = <w_{j+1}, w_{i0+a}>; slot a is the
+    // Gram entry at distance d = nw - a of the next window when 1 <= d <= ng
+    const int ng = min(j + 1, c.k - 1);
+    double part[KW + 1];
+#pragma unroll
+    for (int i = 0; i <= KW; ++i) part[i] = 0.0;
+    unsigned long long nkey = 0;
     const int64_t r0 = (int64_t)blockIdx.x * c.rows_per_cta;
     const int64_t r1 = min(c.n, r0 + c.rows_per_cta);
     double *wn = c.V + (size_t)(j + 1) * c.ldv;
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += kThreads) {
-        const double y = c.Y[r];
-        if (do_update) {
-            double w = sigma * y;
+    // four rows per thread per iteration, all loads issued before the arithmetic
+    constexpr int U = 4;
+    for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += U * kUpdThreads) {
+        double yv[U], wv[U][KW];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = rb + (int64_t)u * kUpdThreads;
+            const bool ok = r < r1;
+            yv[u] = ok ? c.Y[r] : 0.0;
 #pragma unroll
             for (int a = 0; a < KW; ++a)
-                if (a < nw) w = fma(-scoef[a], c.V[r + (size_t)(i0 + a) * c.ldv], w);
-            wn[r] = w;
-            nrm[0] = fma(w, w, nrm[0]);
-            nmax = fmax(nmax, fabs(w));
+                wv[u][a] = (ok && a < nw) ? c.V[r + (size_t)(i0 + a) * c.ldv] : 0.0;
         }
-        if (c.identity) {
-            c.SV[r + (size_t)j * s] = sigma * c.V[r + (size_t)j * c.ldv];
-            c.SAV[r + (size_t)j * s] = sigma * y;
-        } else if (ey != kNoExp) {
-            sketch_scatter(c.sp, lo, hi, r, fixed_point(y, shift));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = rb + (int64_t)u * kUpdThreads;
+            if (r < r1) {
+                const double y = yv[u];
+                double wjr = wv[u][0];
+#pragma unroll
+                for (int a = 1; a < KW; ++a)
+                    if (a == nw - 1) wjr = wv[u][a];
+                if (do_update) {
+                    double w = sigma * y;
+#pragma unroll
+                    for (int a = 0; a < KW; ++a)
+                        if (a < nw) w = fma(-scoef[a], wv[u][a], w);
+                    wn[r] = w;
+                    part[0] = fma(w, w, part[0]);
+                    nkey = max(nkey, abs_key(w));
+#pragma unroll
+                    for (int a = 0; a < KW; ++a)
+                        if (a < nw && nw - a <= ng) part[1 + a] = fma(w, wv[u][a], part[1 + a]);
+                }
+                if (c.identity) {
+                    c.SV[r + (size_t)j * s] = sigma * wjr;
+                    c.SAV[r + (size_t)j * s] = sigma * y;
+                } else {
+                    uint16_t e[ZCAP];
+                    load_pattern<ZCAP>(c.pattern, c.sp.zeta, r, e);
+                    const long long vw = fixed_point(wjr, shift_w);
+                    const long long vy = ey == kNoExp ? 0 : fixed_point(y, shift_y);
+                    const int w0 = (int)(vw & lmask), w1 = (int)(vw >> L);
+                    const int y0 = (int)(vy & lmask), y1 = (int)(vy >> L);
+#pragma unroll
+                    for (int q = 0; q < ZCAP; ++q) {
+                        if (q < c.sp.zeta) {
+                            int row;
+                            bool neg;
+                            pattern_entry(c.sp, e[q], q, row, neg);
+                            red_limbs(aw0, aw1, row, w0, w1, neg);
+                            red_limbs(ay0, ay1, row, y0, y1, neg);
+                        }
+                    }
+                }
+            }
         }
     }
-    block_sum<1>(nrm, red);
-    nmax = block_max(nmax, red);
-    if (do_update && threadIdx.x == 0) {
-        double *o = c.p2 + (size_t)((j + 1) & 1) * G * 2 + (size_t)blockIdx.x * 2;
-        o[0] = nrm[0];
+    block_sum_auto<KW + 1, kUpdThreads>(part, red);
+    const double nmax = key_to_abs(block_max_key<kUpdThreads>(nkey, (unsigned long long *)red));
+    if (threadIdx.x == 0) {
+        double *o = c.p2 + (size_t)blockIdx.x * kP2;
+        o[0] = part[0];
         o[1] = nmax;
+        for (int a = 0; a < KW; ++a) o[2 + a] = part[1 + a];
     }
     if (!c.identity) {
-        long long *o = c.skSAV + (size_t)blockIdx.x * s;
-        for (int i = threadIdx.x; i < s; i += kThreads)
-            o[i] = (long long)(((unsigned long long)hi[i] << 32) | lo[i]);
+        __syncthreads();
+        long long *ow = c.skSV + (size_t)blockIdx.x * s, *oy = c.skSAV + (size_t)blockIdx.x * s;
+        for (int i = threadIdx.x; i < s; i += kUpdThreads) {
+            ow[i] = combine_limbs(aw0[i], aw1[i], L);
+            oy[i] = combine_limbs(ay0[i], ay1[i], L);
+        }
+    }
+    if (last_to_arrive(c.cnt + 1)) {
+        const int warp = threadIdx.x >> 5;
+        if (do_update)
+            for (int v = warp; v < 2 + nw; v += kUpdThreads / 32) {
+                const int d = nw - (v - 2);   // Gram distance of slot v - 2
+                if (v >= 2 && (d < 1 || d > ng)) continue;
+                const double r = warp_reduce_partials(c.p2 + v, G, kP2, v == 1);
+                if ((threadIdx.x & 31) == 0) {
+                    if (v < 2) c.fin_w[2 * (j + 1) + v] = r;
+                    else c.gram[(size_t)(j + 1) * kMaxK + d] = r;
+                }
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (do_update) {
+                // ||A v_j||^2 = sum_i h_ij^2 + ||w_{j+1}||^2 for the orthonormal window
+                const double n2 = c.fin_w[2 * (j + 1)];
+                double hs = 0.0;
+                for (int a = 0; a < nw; ++a) hs += sh[a] * sh[a];
+                const double hn = sqrt(n2);
+                double *o = c.stepsc + 4 * (size_t)(j + 1);
+                o[0] = hn > 0.0 ? 1.0 / hn : 0.0;
+                o[1] = hn;
+                o[2] = (hn > 1e-12 * sqrt(hs + n2)) ? 0.0 : 1.0;
+            }
+            c.cnt[1] = 0u;
+        }
     }
 }
 
-// After the loop: S A v_{m-1}, and the embedding-quality estimate of Sec. 4.3.
-__global__ void __launch_bounds__(kThreads) k_arnoldi_finish(ArnCtx c, skf_info *info) {
-    __shared__ double red[64];
+// After the loop: S v_{m-1} and S A v_{m-1}.
+__global__ void __launch_bounds__(kThreads) k_arnoldi_finish(ArnCtx c) {
     const int G = gridDim.x;
+    if (c.iscal[0] == 0 && !c.identity) {
+        const int frac = sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
+        const double sc = c.vscale[c.m - 1] * c.inv_sqrt_zeta;
+        finalize_sketch(c.skSV, c.G_upd, c.sp.s, c.ews[c.m - 1], frac, sc, c.SV + (size_t)(c.m - 1) * c.sp.s);
+        finalize_sketch(c.skSAV, c.G_upd, c.sp.s, c.eys[c.m - 1], frac, sc, c.SAV + (size_t)(c.m - 1) * c.sp.s);
+    }
+}
+
+// | ||S v_j||^2 - 1 | per column (the embedding-quality estimate of Sec. 4.3),
+// one warp per column.
+__global__ void __launch_bounds__(kThreads) k_arnoldi_eps(ArnCtx c) {
+    const int me = c.iscal[1];
+    const int j = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= me) return;
     const int s = c.sp.s;
-    const bool stopped = c.iscal[0] != 0;
-    if (!stopped && !c.identity)
-        finalize_sketch(c.skSAV, G, s, c.eys[c.m - 1], c.frac, c.vscale[c.m - 1] / sqrt((double)c.sp.zeta),
-                        c.SAV + (size_t)(c.m - 1) * s);
-    if (blockIdx.x != 0 || info == nullptr) return;
-    // block 0 finishes after its own slice; other slices are complete only
-    // after this kernel, so eps_est is computed by k_arnoldi_info below.
+    double acc = 0.0;
+    for (int i = lane; i < s; i += 32) acc = fma(c.SV[i + (size_t)j * s], c.SV[i + (size_t)j * s], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) c.epscol[j] = fabs(acc - 1.0);
 }
 
 __global__ void __launch_bounds__(kThreads) k_arnoldi_info(ArnCtx c, skf_info *info) {
     __shared__ double red[64];
     const int me = c.iscal[1];
-    const int s = c.sp.s;
     double eps = 0.0;
-    for (int j = 0; j < me; ++j) {
-        double acc[1] = {0.0};
-        for (int i = threadIdx.x; i < s; i += kThreads) acc[0] = fma(c.SV[i + (size_t)j * s], c.SV[i + (size_t)j * s], acc[0]);
-        block_sum<1>(acc, red);
-        eps = fmax(eps, fabs(acc[0] - 1.0));
-    }
+    for (int j = threadIdx.x; j < me; j += kThreads) eps = fmax(eps, c.epscol[j]);
+    eps = block_max(eps, red);
     if (threadIdx.x == 0 && info != nullptr) {
         info->status = c.iscal[2];
         info->m_eff = me;
@@ -363,6 +517,25 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_info(ArnCtx c, skf_info *i
         info->beta = me > 0 ? 1.0 / c.vscale[0] : 0.0;
         info->eps_est = eps;
     }
+}
+
+template <int KW, int ZCAP>
+void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, cudaStream_t st) {
+    auto spmv = c.max_width <= 8 ? k_arnoldi_spmv<KW, 8> : k_arnoldi_spmv<KW, 16>;
+    auto update = k_arnoldi_update<KW, ZCAP>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int j = 0; j < c.m; ++j) {
+        spmv<<<Gs, kSpmvThreads, 0, st>>>(c, j);
+        update<<<G, kUpdThreads, smem, st>>>(c, j);
+    }
+}
+
+template <int ZCAP>
+void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, cudaStream_t st) {
+    if (c.k <= 2) launch_steps<2, ZCAP>(c, G, Gs, smem, st);
+    else if (c.k <= 4) launch_steps<4, ZCAP>(c, G, Gs, smem, st);
+    else if (c.k <= 8) launch_steps<8, ZCAP>(c, G, Gs, smem, st);
+    else launch_steps<16, ZCAP>(c, G, Gs, smem, st);
 }
 
 }  // namespace
@@ -373,13 +546,20 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
                        cudaStream_t st) {
     ArnCtx c{};
     c.n = A->n;
-    c.rowptr = A->rowptr;
-    c.colind = A->colind;
-    c.vals = (const double *)A->values;
+    c.sell_off = A->sell_off;
+    c.sell_w = A->sell_w;
+    c.sell_val = A->sell_val;
+    c.sell_col = A->sell_col;
+    c.max_width = A->max_width;
     c.identity = S->kind == SKF_SKETCH_IDENTITY;
-    if (!c.identity) c.sp = make_sparse_sign(S);
+    if (!c.identity) {
+        c.sp = make_sparse_sign(S);
+        c.pattern = S->pattern;
+        c.binmax = S->binmax;
+    }
     c.sp.s = S->s;
     c.sp.zeta = c.identity ? 1 : S->zeta;
+    c.inv_sqrt_zeta = 1.0 / sqrt((double)c.sp.zeta);
     c.m = m;
     c.k = k;
     c.V = V;
@@ -389,51 +569,60 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     c.SAV = SAV;
     c.H = H;
     c.iscal = iscal;
-    int G = 2 * num_sms();
-    const int64_t min_rows = 512;
-    if ((A->n + min_rows - 1) / min_rows < G) G = (int)((A->n + min_rows - 1) / min_rows);
-    if (G < 1) G = 1;
-    c.rows_per_cta = (A->n + G - 1) / G;
-    c.frac = sketch_fraction_bits(c.rows_per_cta);
+    int G;
+    row_partition(A->n, &G, &c.rows_per_cta);   // the partition the sketch tables were sized for
+    int Gs = num_sms();
+    if ((A->n + 1023) / 1024 < Gs) Gs = (int)((A->n + 1023) / 1024);
+    if (Gs < 1) Gs = 1;
+    c.spmv_rows = ((A->n + Gs - 1) / Gs + 31) / 32 * 32;
+    c.G_upd = G;
 
     char *ws = nullptr;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t szY = sizeof(double) * A->n;
-    const size_t szP1 = sizeof(double) * (size_t)G * kP1;
-    const size_t szP2 = sizeof(double) * 2 * (size_t)G * 2;
+    const size_t szP1 = sizeof(double) * (size_t)std::max(G, Gs) * kP1;
+    const size_t szP2 = sizeof(double) * (size_t)G * kP2;
+    const size_t szFd = sizeof(double) * (size_t)m * kP1;
+    const size_t szFw = sizeof(double) * (size_t)(m + 1) * 2;
+    const size_t szSc = sizeof(double) * (size_t)(m + 1) * 4;
+    const size_t szCnt = sizeof(unsigned) * 4;
     const size_t szSk = c.identity ? 0 : sizeof(long long) * (size_t)G * S->s;
     const size_t szGram = sizeof(double) * (size_t)m * kMaxK;
     const size_t szE = sizeof(int) * (size_t)m;
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t total = al(szY) + al(szP1) + al(szP2) + 2 * al(szSk) + al(szGram) + al(szE);
+    const size_t szEps = sizeof(double) * (size_t)m;
+    const size_t total = al(szY) + al(szP1) + al(szP2) + al(szFd) + al(szFw) + al(szSc) + al(szCnt) + 2 * al(szSk) +
+                         al(szGram) + 2 * al(szE) + al(szEps);
     skf_status stt = dalloc((void **)&ws, total, st);
     if (stt != SKF_OK) return stt;
     size_t off = 0;
-    c.Y = (double *)(ws + off); off += al(szY);
-    c.p1 = (double *)(ws + off); off += al(szP1);
-    c.p2 = (double *)(ws + off); off += al(szP2);
-    c.skSV = (long long *)(ws + off); off += al(szSk);
-    c.skSAV = (long long *)(ws + off); off += al(szSk);
-    c.gram = (double *)(ws + off); off += al(szGram);
-    c.eys = (int *)(ws + off); off += al(szE);
-
-    const size_t smem = c.identity ? 0 : sizeof(uint32_t) * 2 * S->s;
-    k_arnoldi_init<<<G, kThreads, 0, st>>>(c, b);
-    auto loop = [&](auto spmv, auto update) {
-        if (smem > 48 * 1024) {
-            cudaFuncSetAttribute(spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        }
-        for (int j = 0; j < m; ++j) {
-            spmv<<<G, kThreads, smem, st>>>(c, j);
-            update<<<G, kThreads, smem, st>>>(c, j);
-        }
+    auto take = [&](size_t sz) {
+        char *p = ws + off;
+        off += al(sz);
+        return p;
     };
-    if (k <= 2) loop(k_arnoldi_spmv<2>, k_arnoldi_update<2>);
-    else if (k <= 4) loop(k_arnoldi_spmv<4>, k_arnoldi_update<4>);
-    else if (k <= 8) loop(k_arnoldi_spmv<8>, k_arnoldi_update<8>);
-    else loop(k_arnoldi_spmv<16>, k_arnoldi_update<16>);
-    k_arnoldi_finish<<<G, kThreads, 0, st>>>(c, info);
+    c.Y = (double *)take(szY);
+    c.p1 = (double *)take(szP1);
+    c.p2 = (double *)take(szP2);
+    c.fin_d = (double *)take(szFd);
+    c.fin_w = (double *)take(szFw);
+    c.stepsc = (double *)take(szSc);
+    c.cnt = (unsigned *)take(szCnt);
+    c.skSV = (long long *)take(szSk);
+    c.skSAV = (long long *)take(szSk);
+    c.gram = (double *)take(szGram);
+    c.eys = (int *)take(szE);
+    c.ews = (int *)take(szE);
+    c.epscol = (double *)take(szEps);
+    cudaMemsetAsync(c.cnt, 0, szCnt, st);
+
+    const size_t smem = c.identity ? 0 : sizeof(int) * 4 * S->s;   // two limbs for each of S v_j, S A v_j
+    k_arnoldi_init<<<G, kThreads, 0, st>>>(c, b);
+    if (c.sp.zeta <= 8) launch_steps_k<8>(c, G, Gs, smem, st);
+    else launch_steps_k<16>(c, G, Gs, smem, st);
+    k_arnoldi_finish<<<G, kThreads, 0, st>>>(c);
+    k_arnoldi_eps<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);
     k_arnoldi_info<<<1, kThreads, 0, st>>>(c, info);
+    count_launches(4 + 2ll * m);
     cudaError_t e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "arnoldi kernels");

@@ -34,6 +34,9 @@ skf_status cuda_fail(cudaError_t e, const char *what);
 
 int num_sms();
 
+// Number of kernel launches issued by the library (diagnostics).
+void count_launches(long long n);
+
 // ------------------------------------------------------------- handles
 }  // namespace skf
 
@@ -46,6 +49,16 @@ struct skf_csr {
     int32_t *colind_own = nullptr;
     void *values_own = nullptr;
     double norm_inf = 0.0;            // max_i sum_j |a_ij|
+    // SELL-32 copy used by the kernels: rows in slices of 32, slice t holds
+    // width[t] x 32 entries column-major (entry p of row 32t + l at
+    // off[t] + 32 p + l), rows padded with value 0 and their own column.
+    // Each row keeps the CSR order of its entries.
+    int64_t nslices = 0;
+    int64_t *sell_off = nullptr;      // [nslices + 1]
+    int32_t *sell_w = nullptr;        // [nslices]
+    double *sell_val = nullptr;
+    int32_t *sell_col = nullptr;
+    int max_width = 0;                // widest slice
 };
 
 struct skf_sketch {
@@ -55,6 +68,11 @@ struct skf_sketch {
     uint64_t seed = 0;
     int64_t np = 0;                   // SRHT: padded length N'
     int32_t *P = nullptr;             // SRHT: s sampled rows (device)
+    // Sparse-sign pattern, expanded once from the seed: entry [c * zeta + q]
+    // holds the row of nonzero q of column c inside stripe q (bits 0-14) and
+    // its sign (bit 15).  2 zeta bytes per column.
+    uint16_t *pattern = nullptr;
+    int *binmax = nullptr;            // device: most nonzeros one CTA row range puts in one row of S
 };
 
 namespace skf {
@@ -91,6 +109,13 @@ __device__ __forceinline__ void sparse_sign_entry(const SparseSign &sp, uint64_t
     neg = (u & 1u) != 0u;
     row = sp.start[q] + (int)(((u >> 1) * (uint32_t)sp.size[q]) >> 15);
 }
+
+// |x| as an ordered integer: for finite x, larger magnitudes give larger keys,
+// so max |x| can be taken with integer instructions.
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ double key_to_abs(unsigned long long k) { return __longlong_as_double((long long)k); }
 
 // Exponent E with |x| < 2^E for all |x| <= xmax (xmax > 0, finite).
 __host__ __device__ __forceinline__ int bound_exponent(double xmax) {
@@ -157,9 +182,9 @@ __device__ __forceinline__ double sum_i64_exact(const long long *p, int G, size_
     return neg ? -r : r;
 }
 
-// Block-wide reductions (blockDim.x == kThreads); the result is returned to
+// Block-wide reductions for blocks of NT threads; the result is returned to
 // every thread of the block.
-template <int NV>
+template <int NV, int NT = kThreads>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double *smem /* >= NV*32 */) {
 #pragma unroll
     for (int i = 0; i < NV; ++i)
@@ -174,7 +199,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *smem /* >= NV
     if (warp == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            double t = lane < (kThreads / 32) ? smem[i * 32 + lane] : 0.0;
+            double t = lane < (NT / 32) ? smem[i * 32 + lane] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             if (lane == 0) smem[i * 32] = t;
@@ -186,6 +211,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *smem /* >= NV
     __syncthreads();
 }
 
+template <int NT = kThreads>
 __device__ __forceinline__ double block_max(double v, double *smem /* >= 32 */) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -194,7 +220,7 @@ __device__ __forceinline__ double block_max(double v, double *smem /* >= 32 */) 
     if (lane == 0) smem[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        double t = lane < (kThreads / 32) ? smem[lane] : -INFINITY;
+        double t = lane < (NT / 32) ? smem[lane] : -INFINITY;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
         if (lane == 0) smem[0] = t;
@@ -205,13 +231,96 @@ __device__ __forceinline__ double block_max(double v, double *smem /* >= 32 */) 
     return v;
 }
 
-// Precision (fraction bits below the vector max) of the fixed-point sketch
-// accumulators, given the most rows one CTA contributes to a bin.
-__host__ __device__ __forceinline__ int sketch_fraction_bits(long long rows_per_cta) {
+// Block sum with few FP64 instructions (the FP64 pipe retires one warp
+// instruction per 16 SM cycles on this part, whatever the active lanes):
+// each thread parks its NV partials in shared memory and warp i alone adds
+// up value i (sequential per lane, then one butterfly).  Result in every
+// thread.  smem: NV * NT doubles.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_lowflop(double (&v)[NV], double *smem) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) smem[i * NT + threadIdx.x] = v[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < NV; i += NT / 32) {
+        double t = 0.0;
+#pragma unroll 4
+        for (int k = lane; k < NT; k += 32) t += smem[i * NT + k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        __syncwarp();
+        if (lane == 0) smem[i * NT] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = smem[i * NT];
+    __syncthreads();
+}
+
+// Shared-memory doubles a block reduction of NV values over NT threads needs,
+// and the variant used: the low-FP64 one when its buffer stays within 32 KB.
+template <int NV, int NT> struct BlockSumTraits {
+    static constexpr bool kLow = (size_t)NV * NT * sizeof(double) <= 32768;
+    static constexpr int kSmem = kLow ? NV * NT : 32 * NV;
+};
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_auto(double (&v)[NV], double *smem) {
+    if constexpr (BlockSumTraits<NV, NT>::kLow) block_sum_lowflop<NV, NT>(v, smem);
+    else block_sum<NV, NT>(v, smem);
+}
+
+// Block max of non-negative magnitude keys (integer instructions only).
+template <int NT>
+__device__ __forceinline__ unsigned long long block_max_key(unsigned long long k, unsigned long long *smem) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(0xffffffffu, k, o));
+    __syncthreads();
+    if (lane == 0) smem[warp] = k;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long t = lane < NT / 32 ? smem[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (lane == 0) smem[0] = t;
+    }
+    __syncthreads();
+    k = smem[0];
+    __syncthreads();
+    return k;
+}
+
+// Row partition shared by the streaming kernels and the sketch tables: G
+// CTAs, each owning `rows` consecutive rows.
+void row_partition(int64_t n, int *G, int64_t *rows);
+
+// Fixed-point sketch accumulation.  A value x is rounded to the integer
+// v = x 2^(P - E) (E: exponent bound of the vector, |v| < 2^P) and split into
+// two signed 32-bit limbs v = l1 2^L + l0, 0 <= l0 < 2^L, |l1| < 2^(P-L);
+// each limb is added with a native 32-bit shared-memory atomic.  With at most
+// `binmax` contributions per bin and CTA, L = 31 - ceil(log2(binmax + 1))
+// rules out overflow, and P = min(2L, 52) bits of the vector max are kept.
+__host__ __device__ __forceinline__ int limb_bits(int binmax) {
     int lg = 0;
-    while ((1ll << lg) < rows_per_cta + 1) ++lg;
-    int p = 62 - lg;
-    return p > 52 ? 52 : p;
+    while ((1 << lg) < binmax + 1) ++lg;
+    return 31 - lg;
+}
+__host__ __device__ __forceinline__ int sketch_fraction_bits_from_limb(int L) { return 2 * L > 52 ? 52 : 2 * L; }
+
+__device__ __forceinline__ void pattern_entry(const SparseSign &sp, uint16_t e, int q, int &row, bool &neg) {
+    row = sp.start[q] + (int)(e & 0x7FFFu);
+    neg = (e >> 15) != 0;
+}
+
+__device__ __forceinline__ void red_limbs(int *acc0, int *acc1, int row, int l0, int l1, bool neg) {
+    atomicAdd(acc0 + row, neg ? -l0 : l0);
+    atomicAdd(acc1 + row, neg ? -l1 : l1);
+}
+
+// int64 partial of one bin from its two limbs.
+__device__ __forceinline__ long long combine_limbs(int a0, int a1, int L) {
+    return ((long long)a1 << L) + (long long)a0;
 }
 
 // ------------------------------------------------------ host-side helpers
@@ -238,6 +347,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const double *V,
                     skf_info *info, cudaStream_t st);
 
 // Sketch-apply launcher shared by the API and the solvers.
+skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st);
 skf_status sketch_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX,
                             cudaStream_t st);
 

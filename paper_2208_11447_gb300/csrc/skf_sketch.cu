@@ -1,8 +1,11 @@
-// Application of the subspace embedding S (eq. (1.1)) to general vectors:
-// column maxima, fixed-point scatter into per-CTA shared-memory bins, and an
-// exact cross-CTA reduction.  The same device routines are used inside the
-// Arnoldi kernels.
+// The subspace embedding S (eq. (1.1)): expansion of the sparse-sign pattern
+// from its SplitMix64 definition, the per-partition bin-load maxima that
+// size the fixed-point limbs, and S X for general X (column maxima,
+// fixed-point scatter into per-CTA shared-memory bins, exact cross-CTA
+// reduction).  The Arnoldi kernels use the same pattern and accumulation.
 #include <math.h>
+
+#include <algorithm>
 
 #include "skf_internal.cuh"
 
@@ -23,7 +26,51 @@ SparseSign make_sparse_sign(const skf_sketch *S) {
     return sp;
 }
 
+void row_partition(int64_t n, int *G, int64_t *rows) {
+    int g = 2 * num_sms();
+    const int64_t min_rows = 512;
+    if ((n + min_rows - 1) / min_rows < g) g = (int)((n + min_rows - 1) / min_rows);
+    if (g < 1) g = 1;
+    *G = g;
+    *rows = ((n + g - 1) / g + 31) / 32 * 32;   // whole SELL slices per CTA
+}
+
 namespace {
+
+// pattern[c * zeta + q] = (row of nonzero q of column c within stripe q) | sign << 15
+__global__ void k_build_pattern(SparseSign sp, int64_t n, uint16_t *__restrict__ pattern) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t word = 0;
+        for (int q = 0; q < sp.zeta; ++q) {
+            if ((q & 3) == 0) word = splitmix_word(sp.seed, (uint64_t)c * sp.words + (q >> 2));
+            int row;
+            bool neg;
+            sparse_sign_entry(sp, word, q, row, neg);
+            pattern[c * sp.zeta + q] = (uint16_t)((row - sp.start[q]) | (neg ? 0x8000 : 0));
+        }
+    }
+}
+
+// Largest number of nonzeros that one CTA's row range puts into one row of S.
+__global__ void k_bin_max(SparseSign sp, int64_t n, int64_t rows_per_cta, const uint16_t *__restrict__ pattern,
+                          int *binmax) {
+    extern __shared__ int cnt[];
+    for (int i = threadIdx.x; i < sp.s; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+    const int64_t r1 = min(n, r0 + rows_per_cta);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+        for (int q = 0; q < sp.zeta; ++q) {
+            int row;
+            bool neg;
+            pattern_entry(sp, pattern[r * sp.zeta + q], q, row, neg);
+            atomicAdd(cnt + row, 1);
+        }
+    __syncthreads();
+    int mx = 0;
+    for (int i = threadIdx.x; i < sp.s; i += blockDim.x) mx = max(mx, cnt[i]);
+    atomicMax(binmax, mx);
+}
 
 // Per-CTA partial max |X[:, col]| for every column.
 __global__ void k_colmax(const double *__restrict__ X, int64_t ldx, int64_t n, int ncols, int64_t rows_per_cta,
@@ -39,52 +86,56 @@ __global__ void k_colmax(const double *__restrict__ X, int64_t ldx, int64_t n, i
     }
 }
 
-// Scatter of the rows of this CTA into fixed-point bins; writes the int64
-// partial sums [ncols][G][s].
+// Scatter of the rows of this CTA into fixed-point limb bins; writes the
+// int64 partial sums [ncols][G][s].
 __global__ void k_sparse_sign_scatter(const double *__restrict__ X, int64_t ldx, int64_t n, int ncols,
-                                      int64_t rows_per_cta, SparseSign sp, int frac_bits,
-                                      const double *__restrict__ maxpart, long long *__restrict__ out) {
-    extern __shared__ uint32_t bins[];   // lo[s], hi[s]
+                                      int64_t rows_per_cta, SparseSign sp, const uint16_t *__restrict__ pattern,
+                                      const int *__restrict__ binmax, const double *__restrict__ maxpart,
+                                      long long *__restrict__ out) {
+    extern __shared__ int bins[];   // acc0[s], acc1[s]
     __shared__ double red[32];
-    uint32_t *lo = bins, *hi = bins + sp.s;
+    int *acc0 = bins, *acc1 = bins + sp.s;
     const int G = gridDim.x;
+    const int L = limb_bits(*binmax);
+    const int frac = sketch_fraction_bits_from_limb(L);
+    const long long lmask = (1ll << L) - 1;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
     const int64_t r1 = min(n, r0 + rows_per_cta);
     for (int c = 0; c < ncols; ++c) {
         double mx = 0.0;
         for (int g = threadIdx.x; g < G; g += kThreads) mx = fmax(mx, maxpart[(size_t)c * G + g]);
         mx = block_max(mx, red);
-        for (int i = threadIdx.x; i < 2 * sp.s; i += kThreads) bins[i] = 0u;
+        for (int i = threadIdx.x; i < 2 * sp.s; i += kThreads) bins[i] = 0;
         __syncthreads();
         if (mx > 0.0) {
-            const int shift = frac_bits - bound_exponent(mx);
+            const int shift = frac - bound_exponent(mx);
             for (int64_t r = r0 + threadIdx.x; r < r1; r += kThreads) {
                 const long long v = fixed_point(X[r + c * ldx], shift);
                 if (v == 0) continue;
-                uint64_t word = 0;
+                const int l0 = (int)(v & lmask), l1 = (int)(v >> L);
                 for (int q = 0; q < sp.zeta; ++q) {
-                    if ((q & 3) == 0) word = splitmix_word(sp.seed, (uint64_t)r * sp.words + (q >> 2));
                     int row;
                     bool neg;
-                    sparse_sign_entry(sp, word, q, row, neg);
-                    atomic_add_i64_split(lo + row, hi + row, neg ? -v : v);
+                    pattern_entry(sp, pattern[r * sp.zeta + q], q, row, neg);
+                    red_limbs(acc0, acc1, row, l0, l1, neg);
                 }
             }
         }
         __syncthreads();
         long long *o = out + ((size_t)c * G + blockIdx.x) * sp.s;
-        for (int i = threadIdx.x; i < sp.s; i += kThreads)
-            o[i] = (long long)(((unsigned long long)hi[i] << 32) | lo[i]);
+        for (int i = threadIdx.x; i < sp.s; i += kThreads) o[i] = combine_limbs(acc0[i], acc1[i], L);
         __syncthreads();
     }
 }
 
-// SX[i, c] = 2^-frac * 2^E_c * zeta^-1/2 * sum_g partial[c][g][i].
+// SX[i, c] = 2^(E_c - frac) zeta^-1/2 sum_g partial[c][g][i].
 __global__ void k_sparse_sign_reduce(const long long *__restrict__ part, const double *__restrict__ maxpart, int G,
-                                     int s, int ncols, int zeta, int frac_bits, double *__restrict__ SX) {
+                                     int s, int ncols, int zeta, const int *__restrict__ binmax,
+                                     double *__restrict__ SX) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)s * ncols) return;
     const int c = (int)(idx / s), i = (int)(idx % s);
+    const int frac = sketch_fraction_bits_from_limb(limb_bits(*binmax));
     double mx = 0.0;
     for (int g = 0; g < G; ++g) mx = fmax(mx, maxpart[(size_t)c * G + g]);
     if (mx == 0.0) {
@@ -92,7 +143,7 @@ __global__ void k_sparse_sign_reduce(const long long *__restrict__ part, const d
         return;
     }
     const double tot = sum_i64_exact(part + (size_t)c * G * s + i, G, (size_t)s);
-    SX[idx] = ldexp(tot, bound_exponent(mx) - frac_bits) / sqrt((double)zeta);
+    SX[idx] = ldexp(tot, bound_exponent(mx) - frac) / sqrt((double)zeta);
 }
 
 __global__ void k_copy_cols(const double *__restrict__ X, int64_t ldx, int64_t n, int ncols, double *__restrict__ Y) {
@@ -104,6 +155,40 @@ __global__ void k_copy_cols(const double *__restrict__ X, int64_t ldx, int64_t n
 
 }  // namespace
 
+// Expand the sparse-sign pattern and its bin-load maximum (once per sketch).
+skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st) {
+    const SparseSign sp = make_sparse_sign(S);
+    const size_t bytes = sizeof(uint16_t) * (size_t)S->n * S->zeta;
+    cudaError_t e = cudaMalloc(&S->pattern, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        S->pattern = nullptr;
+        return fail(SKF_ERR_OOM, "sketch pattern allocation");
+    }
+    e = cudaMalloc(&S->binmax, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        S->binmax = nullptr;
+        return fail(SKF_ERR_OOM, "sketch table allocation");
+    }
+    int G;
+    int64_t rows;
+    row_partition(S->n, &G, &rows);
+    const int blocks = (int)std::min<int64_t>((S->n + 255) / 256, 16ll * num_sms());
+    k_build_pattern<<<blocks, 256, 0, st>>>(sp, S->n, S->pattern);
+    cudaMemsetAsync(S->binmax, 0, sizeof(int), st);
+    const size_t smem = sizeof(int) * S->s;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_bin_max, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bin_max<<<G, 256, smem, st>>>(sp, S->n, rows, S->pattern, S->binmax);
+    count_launches(2);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "sketch table build");
+    int hmax = 0;
+    cudaMemcpy(&hmax, S->binmax, sizeof(int), cudaMemcpyDeviceToHost);
+    if (limb_bits(hmax) < 13) return fail(SKF_ERR_NOT_SUPPORTED, "sketch too dense for the fixed-point accumulators");
+    return SKF_OK;
+}
+
 skf_status sketch_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX,
                             cudaStream_t st) {
     const int64_t n = S->n;
@@ -111,17 +196,15 @@ skf_status sketch_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, i
     if (S->kind == SKF_SKETCH_IDENTITY) {
         const int64_t tot = n * ncols;
         k_copy_cols<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, ldx, n, ncols, SX);
+        count_launches(1);
         SKF_LAUNCH_CHECK("k_copy_cols");
         return SKF_OK;
     }
     if (S->kind != SKF_SKETCH_SPARSE_SIGN) return fail(SKF_ERR_NOT_SUPPORTED, "sketch kind not implemented");
     const SparseSign sp = make_sparse_sign(S);
-    int G = 2 * num_sms();
-    const int64_t min_rows = 1024;
-    if ((n + min_rows - 1) / min_rows < G) G = (int)((n + min_rows - 1) / min_rows);
-    if (G < 1) G = 1;
-    const int64_t rows = (n + G - 1) / G;
-    const int frac = sketch_fraction_bits(rows);
+    int G;
+    int64_t rows;
+    row_partition(n, &G, &rows);
     double *maxpart = nullptr;
     long long *part = nullptr;
     skf_status stt = dalloc((void **)&maxpart, sizeof(double) * G * ncols, st);
@@ -132,13 +215,15 @@ skf_status sketch_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, i
         return stt;
     }
     k_colmax<<<G, kThreads, 0, st>>>(X, ldx, n, ncols, rows, maxpart);
-    const size_t smem = sizeof(uint32_t) * 2 * S->s;
+    const size_t smem = sizeof(int) * 2 * S->s;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_sparse_sign_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_sparse_sign_scatter<<<G, kThreads, smem, st>>>(X, ldx, n, ncols, rows, sp, frac, maxpart, part);
+    k_sparse_sign_scatter<<<G, kThreads, smem, st>>>(X, ldx, n, ncols, rows, sp, S->pattern, S->binmax, maxpart,
+                                                      part);
     const int64_t tot = (int64_t)S->s * ncols;
-    k_sparse_sign_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, maxpart, G, S->s, ncols, S->zeta, frac,
-                                                                        SX);
+    k_sparse_sign_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, maxpart, G, S->s, ncols, S->zeta,
+                                                                        S->binmax, SX);
+    count_launches(3);
     cudaError_t e = cudaGetLastError();
     dfree(part, st);
     dfree(maxpart, st);

@@ -29,10 +29,12 @@ struct TailCtx {
     double *Aw;        // s x 2m, ld s
     double *Rdiag;     // [2m]
     double *M, *R2;    // m x m, ld m
+    double *MT, *R2T;  // transposes, m x m, ld m
     double *B, *C;     // m x m, ld m (lower triangles used)
     double *cvec, *Mtc;  // [m]
     double *Nw;        // node workspace [batch][m*m]
     double *out;       // [batch][m] weighted node solutions
+    int *nodebad;      // [batch] 1 = the mixed-precision solve did not converge
     double *qbuf;      // [levels][m]
     double *qacc;      // [m]
     double *z;         // [m] coefficients for V (scaled by vscale)
@@ -58,59 +60,51 @@ __global__ void k_tail_copy(const double *__restrict__ SV, const double *__restr
     if (blockIdx.x == 0 && threadIdx.x < 4) c.qstate[threadIdx.x] = 0.0;
 }
 
-// Householder reflector for column jj, applied to the trailing columns.
-// Every CTA forms the reflector; trailing column cc belongs to CTA
-// (cc - jj - 1) mod G.  Column jj itself is not modified (its diagonal goes
-// to Rdiag), so no CTA reads data another CTA writes in this launch.
+// Householder reflector for column jj (LAPACK convention: beta = -sign(x0)
+// ||x||, v = [1; x(jj+1:)/(x0 - beta)], tau = (beta - x0)/beta), applied to
+// the trailing columns, one warp per trailing column.  Every warp forms the
+// reflector from column jj, which no warp modifies (its diagonal goes to
+// Rdiag), so the launch has no intra-launch dependencies.
 __global__ void __launch_bounds__(kThreads) k_householder(TailCtx c, int jj) {
-    __shared__ double red[64];
     const int me = c.iscal[1];
     const int ncols = 2 * me;
     const int nref = (c.method == SKF_METHOD_SGMRES) ? 2 * me : me;
     if (jj >= nref || jj >= c.s) return;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int ntrail = ncols - jj - 1;
+    if (gw >= ntrail && gw != 0) return;
     const double *x = c.Aw + (int64_t)jj * c.s;
-    double acc[1] = {0.0};
-    for (int i = jj + 1 + threadIdx.x; i < c.s; i += kThreads) acc[0] = fma(x[i], x[i], acc[0]);
-    block_sum<1>(acc, red);
-    __shared__ double sp[3];
-    if (threadIdx.x == 0) {
-        const double x0 = x[jj];
-        const double sig = acc[0];
-        double tau = 0.0, beta = x0, scale = 0.0;
-        if (sig > 0.0 || x0 == 0.0) {
-            const double nx = sqrt(x0 * x0 + sig);
-            beta = (x0 >= 0.0) ? -nx : nx;
-            if (nx > 0.0) {
-                tau = (beta - x0) / beta;
-                scale = 1.0 / (x0 - beta);
-            }
+    double sig = 0.0;
+    for (int i = jj + 1 + lane; i < c.s; i += 32) sig = fma(x[i], x[i], sig);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
+    const double x0 = x[jj];
+    double tau = 0.0, beta = x0, scale = 0.0;
+    if (sig > 0.0 || x0 == 0.0) {
+        const double nx = sqrt(x0 * x0 + sig);
+        beta = (x0 >= 0.0) ? -nx : nx;
+        if (nx > 0.0) {
+            tau = (beta - x0) / beta;
+            scale = 1.0 / (x0 - beta);
         }
-        sp[0] = tau;
-        sp[1] = beta;
-        sp[2] = scale;
-        if (blockIdx.x == 0) c.Rdiag[jj] = beta;
     }
-    __syncthreads();
-    const double tau = sp[0], scale = sp[2];
-    if (tau == 0.0) return;
-    for (int cc = jj + 1 + blockIdx.x; cc < ncols; cc += gridDim.x) {
-        double *y = c.Aw + (int64_t)cc * c.s;
-        double d[1] = {0.0};
-        for (int i = jj + threadIdx.x; i < c.s; i += kThreads) {
-            const double vi = (i == jj) ? 1.0 : x[i] * scale;
-            d[0] = fma(vi, y[i], d[0]);
-        }
-        block_sum<1>(d, red);
-        const double f = tau * d[0];
-        for (int i = jj + threadIdx.x; i < c.s; i += kThreads) {
-            const double vi = (i == jj) ? 1.0 : x[i] * scale;
-            y[i] = fma(-f, vi, y[i]);
-        }
-        __syncthreads();
-    }
+    if (gw == 0 && lane == 0) c.Rdiag[jj] = beta;
+    if (tau == 0.0 || gw >= ntrail) return;
+    double *y = c.Aw + (int64_t)(jj + 1 + gw) * c.s;
+    double d = (lane == 0) ? y[jj] : 0.0;
+    for (int i = jj + 1 + lane; i < c.s; i += 32) d = fma(x[i] * scale, y[i], d);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    const double f = tau * d;
+    if (lane == 0) y[jj] -= f;
+    for (int i = jj + 1 + lane; i < c.s; i += 32) y[i] = fma(-f, x[i] * scale, y[i]);
 }
 
+constexpr int kMaxRegCol = 16;    // register slots per lane for one column of R (m <= 512)
+
 // Rows of X R = T for T = R12 (-> M) and T = R22 (-> R2); one warp per row.
+// Column jcol+1 of R is loaded into registers while column jcol is reduced.
 __global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c) {
     extern __shared__ double xs[];   // [warps][m]
     const int me = c.iscal[1];
@@ -121,9 +115,25 @@ __global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c) {
     double *x = xs + (size_t)warp * c.m;
     const bool second = row >= me;
     const int a = second ? row - me : row;
+    double cur[kMaxRegCol], nxt[kMaxRegCol];
+#pragma unroll
+    for (int t = 0; t < kMaxRegCol; ++t) cur[t] = 0.0;   // column 0 has no entries above the diagonal
     for (int jcol = 0; jcol < me; ++jcol) {
+        const int jn = jcol + 1;
+#pragma unroll
+        for (int t = 0; t < kMaxRegCol; ++t) {
+            const int i = lane + 32 * t;
+            nxt[t] = (jn < me && i < jn) ? c.Aw[i + (int64_t)jn * c.s] : 0.0;
+        }
         double part = 0.0;
-        for (int i = lane; i < jcol; i += 32) part = fma(x[i], c.Aw[i + (int64_t)jcol * c.s], part);
+        const int nt = (jcol + 31) >> 5;   // warp-uniform: no predicated-off FP64 work
+#pragma unroll
+        for (int t = 0; t < kMaxRegCol; ++t) {
+            if (t < nt) {
+                const int i = lane + 32 * t;
+                part = fma(i < jcol ? x[i] : 0.0, cur[t], part);
+            }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         if (lane == 0) {
@@ -135,6 +145,8 @@ __global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c) {
             x[jcol] = (tv - part) / c.Rdiag[jcol];
         }
         __syncwarp();
+#pragma unroll
+        for (int t = 0; t < kMaxRegCol; ++t) cur[t] = nxt[t];
     }
     double *dst = second ? c.R2 : c.M;
     for (int jcol = lane; jcol < me; jcol += 32) dst[a + (int64_t)jcol * c.m] = x[jcol];
@@ -154,6 +166,12 @@ __global__ void __launch_bounds__(kThreads) k_tail_prep(TailCtx c) {
             for (int a = 0; a <= j; ++a) acc = fma(c.R2[a + (int64_t)i * c.m], c.R2[a + (int64_t)j * c.m], acc);
         c.C[i + (int64_t)j * c.m] = acc;
         c.B[i + (int64_t)j * c.m] = c.M[i + (int64_t)j * c.m] + c.M[j + (int64_t)i * c.m];
+    }
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % me), j = (int)(idx / me);
+        c.MT[j + (int64_t)i * c.m] = c.M[i + (int64_t)j * c.m];
+        if (c.method == SKF_METHOD_SGMRES) c.R2T[j + (int64_t)i * c.m] = c.R2[i + (int64_t)j * c.m];
     }
     if (blockIdx.x == 0) {
         const double c0 = (1.0 / c.vscale[0]) * c.Rdiag[0];
@@ -183,12 +201,14 @@ __device__ void chol_solve(const double *N, int me, int ld, double *y) {
     __syncthreads();
 }
 
-// One CTA per quadrature node: node n0 + off + blockIdx.x of the table,
-// result row off + blockIdx.x of `out`, workspace slot blockIdx.x.
+// FP64 fallback for the nodes k_nodes_mixed flagged: one CTA per node,
+// node n0 + off + blockIdx.x of the table, result row off + blockIdx.x of
+// `out`, workspace slot blockIdx.x.
 __global__ void __launch_bounds__(kThreads) k_nodes(TailCtx c, int n0, int off) {
     extern __shared__ double sm[];   // y[m], r[m], g[m], colp[m]
     const int me = c.iscal[1];
     if (c.qstate[0] != 0.0 || me == 0) return;
+    if (!c.nodebad[off + blockIdx.x]) return;   // solved by k_nodes_mixed
     const int m = c.m;
     double *y = sm, *r = sm + m, *g = sm + 2 * m, *colp = sm + 3 * m;
     const int nd = n0 + off + blockIdx.x;
@@ -258,6 +278,147 @@ __global__ void __launch_bounds__(kThreads) k_nodes(TailCtx c, int n0, int off) 
     for (int a = threadIdx.x; a < me; a += blockDim.x) outrow[a] = wt * (y[a] + g[a]);
 }
 
+
+constexpr int kMixedMaxM = 320;   // packed FP32 factor of order m must fit in shared memory
+
+__device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }   // packed lower, row-major
+
+// Solve L L^T z = z with the packed FP32 factor; one warp, z in FP64 shared
+// memory (the solve itself is in FP32).
+__device__ void packed_solve_warp(const float *L, int me, double *z) {
+    const int lane = threadIdx.x & 31;
+    for (int p = 0; p < me; ++p) {          // L u = z
+        float part = 0.f;
+        for (int q = lane; q < p; q += 32) part = fmaf(L[pk(p, q)], (float)z[q], part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) z[p] = (double)(((float)z[p] - part) / L[pk(p, p)]);
+        __syncwarp();
+    }
+    for (int p = me - 1; p >= 0; --p) {     // L^T x = u
+        float part = 0.f;
+        for (int i = p + 1 + lane; i < me; i += 32) part = fmaf(L[pk(i, p)], (float)z[i], part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) z[p] = (double)(((float)z[p] - part) / L[pk(p, p)]);
+        __syncwarp();
+    }
+}
+
+// One CTA per quadrature node.  The normal matrix N(t) = t^2 I + t (M + M^T)
+// + C is factored in FP32 (packed, in shared memory); the least-squares
+// solution is then refined in FP64 with the residual of the original problem
+// (semi-normal equations with iterative refinement), so the result has the
+// accuracy of an FP64 least-squares solve whenever cond(X)^2 u_fp32 < 1.
+// Nodes that do not converge are flagged for the FP64 kernel.
+__global__ void __launch_bounds__(kThreads) k_nodes_mixed(TailCtx c, int n0, int off) {
+    extern __shared__ double smd[];
+    const int me = c.iscal[1];
+    if (c.qstate[0] != 0.0 || me == 0) return;
+    const int m = c.m;
+    const int row = off + blockIdx.x;
+    if (me > kMixedMaxM) {
+        if (threadIdx.x == 0) c.nodebad[row] = 1;
+        return;
+    }
+    double *y = smd, *rt = smd + m, *rb = smd + 2 * m, *g = smd + 3 * m;
+    float *colp = (float *)(smd + 4 * m);
+    float *L = colp + m;
+    const int nd = n0 + row;
+    const double t = c.t[nd], wt = c.w[nd];
+    const bool gm = c.method == SKF_METHOD_SGMRES;
+    __shared__ int bad;
+    __shared__ double snorm[2];
+    if (threadIdx.x == 0) bad = 0;
+    for (int i = threadIdx.x; i < me; i += blockDim.x)
+        for (int j = 0; j <= i; ++j)
+            L[pk(i, j)] = (float)((i == j ? t * t : 0.0) + t * c.B[i + (int64_t)j * m] + c.C[i + (int64_t)j * m]);
+    // right-looking FP32 Cholesky
+    for (int p = 0; p < me; ++p) {
+        __syncthreads();
+        const float d = L[pk(p, p)];
+        if (!(d > 0.f)) {
+            if (threadIdx.x == 0) bad = 1;
+            break;
+        }
+        const float lpp = sqrtf(d);
+        for (int i = p + threadIdx.x; i < me; i += blockDim.x) colp[i] = (i == p) ? lpp : L[pk(i, p)] / lpp;
+        __syncthreads();
+        for (int i = p + threadIdx.x; i < me; i += blockDim.x) L[pk(i, p)] = colp[i];
+        // trailing update: one warp per row, lanes along the row
+        {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int i = p + 1 + warp; i < me; i += kThreads / 32) {
+                const float li = colp[i];
+                float *Li = L + pk(i, 0);
+                for (int q = p + 1 + lane; q <= i; q += 32) Li[q] = fmaf(-li, colp[q], Li[q]);
+            }
+        }
+    }
+    __syncthreads();
+    if (!bad) {
+        // y0 = N^{-1} (t c + M^T c)
+        for (int a = threadIdx.x; a < me; a += blockDim.x) y[a] = t * c.cvec[a] + c.Mtc[a];
+        __syncthreads();
+        if (threadIdx.x < 32) packed_solve_warp(L, me, y);
+        __syncthreads();
+        double prev = INFINITY;
+        bool conv = false;
+        for (int it = 0; it < 12; ++it) {
+            // r = [c; 0] - [t I + M; R2] y   (FP64)
+            for (int a = threadIdx.x; a < me; a += blockDim.x) {
+                double v = c.cvec[a] - t * y[a];
+                for (int j = 0; j < me; ++j) v = fma(-c.M[a + (int64_t)j * m], y[j], v);
+                rt[a] = v;
+                if (gm) {
+                    double u = 0.0;
+                    for (int j = a; j < me; ++j) u = fma(-c.R2[a + (int64_t)j * m], y[j], u);
+                    rb[a] = u;
+                }
+            }
+            __syncthreads();
+            // g = [t I + M; R2]^T r
+            for (int j = threadIdx.x; j < me; j += blockDim.x) {
+                double v = t * rt[j];
+                for (int a = 0; a < me; ++a) v = fma(c.MT[j + (int64_t)a * m], rt[a], v);
+                if (gm)
+                    for (int a = 0; a <= j; ++a) v = fma(c.R2T[j + (int64_t)a * m], rb[a], v);
+                g[j] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) packed_solve_warp(L, me, g);
+            __syncthreads();
+            double loc[2] = {0.0, 0.0};
+            for (int a = threadIdx.x; a < me; a += blockDim.x) {
+                loc[0] = fma(g[a], g[a], loc[0]);
+                y[a] += g[a];
+                loc[1] = fma(y[a], y[a], loc[1]);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                loc[0] += __shfl_xor_sync(0xffffffffu, loc[0], o);
+                loc[1] += __shfl_xor_sync(0xffffffffu, loc[1], o);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) { snorm[0] = 0.0; snorm[1] = 0.0; }
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(&snorm[0], loc[0]);
+                atomicAdd(&snorm[1], loc[1]);
+            }
+            __syncthreads();
+            const double dn = sqrt(snorm[0]), yn = sqrt(snorm[1]);
+            if (dn <= 1e-14 * yn) { conv = true; break; }
+            if (it >= 2 && dn > 0.5 * prev) { conv = dn <= 1e-12 * yn; break; }
+            prev = dn;
+        }
+        if (!conv && threadIdx.x == 0) bad = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) c.nodebad[row] = bad;
+    if (!bad)
+        for (int a = threadIdx.x; a < me; a += blockDim.x) c.out[(size_t)row * m + a] = wt * y[a];
+}
+
 // Sum the node solutions of each level of the batch, then run the
 // acceptance test of Sec. 4.1 level by level.  One CTA.
 __global__ void __launch_bounds__(kThreads) k_levels(TailCtx c, int lev0, int nlev, const int *lev_start,
@@ -310,18 +471,33 @@ __global__ void __launch_bounds__(kThreads) k_levels(TailCtx c, int lev0, int nl
     }
 }
 
-// y = R^{-1} q_acc, z = vscale .* y (single CTA, column-oriented back substitution).
+// y = R^{-1} q_acc, z = vscale .* y (single CTA, column-oriented back
+// substitution; column p-1 of R is prefetched while column p is applied).
 __global__ void __launch_bounds__(kThreads) k_coeffs(TailCtx c) {
     extern __shared__ double q[];
     __shared__ double red[64];
     const int me = c.iscal[1];
+    constexpr int kPer = 2;   // rows per thread: me <= 2 * kThreads
     for (int a = threadIdx.x; a < me; a += blockDim.x) q[a] = c.qacc[a];
+    double cur[kPer], nxt[kPer];
+    for (int u = 0; u < kPer; ++u) {
+        const int i = threadIdx.x + u * kThreads;
+        cur[u] = (me > 0 && i < me - 1) ? c.Aw[i + (int64_t)(me - 1) * c.s] : 0.0;
+    }
     for (int p = me - 1; p >= 0; --p) {
+        for (int u = 0; u < kPer; ++u) {
+            const int i = threadIdx.x + u * kThreads;
+            nxt[u] = (p >= 1 && i < p - 1) ? c.Aw[i + (int64_t)(p - 1) * c.s] : 0.0;
+        }
         __syncthreads();
         const double yp = q[p] / c.Rdiag[p];
         __syncthreads();
         if (threadIdx.x == 0) q[p] = yp;
-        for (int i = threadIdx.x; i < p; i += blockDim.x) q[i] = fma(-c.Aw[i + (int64_t)p * c.s], yp, q[i]);
+        for (int u = 0; u < kPer; ++u) {
+            const int i = threadIdx.x + u * kThreads;
+            if (i < p) q[i] = fma(-cur[u], yp, q[i]);
+            cur[u] = nxt[u];
+        }
     }
     __syncthreads();
     for (int a = threadIdx.x; a < me; a += blockDim.x) c.z[a] = c.vscale[a] * q[a];
@@ -380,14 +556,16 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const double *V,
     c.nlevels = rule.nlevels;
     int max_level = 0;
     for (int l = 0; l < rule.nlevels; ++l) max_level = std::max(max_level, rule.h_start[l + 1] - rule.h_start[l]);
-    const int cap = std::max(2 * num_sms(), max_level);
-    // batches of consecutive levels with at most `cap` nodes (a level never splits)
+    // batches of consecutive levels filling at most one wave of node CTAs
+    // (2 per SM); a larger level forms a batch of its own (never split)
+    const int wave = 2 * num_sms();
+    const int cap = std::max(wave, max_level);
     std::vector<std::pair<int, int>> batches;   // (first level, count)
     for (int l = 0; l < rule.nlevels;) {
         int cnt = 0, nodes = 0;
         while (l + cnt < rule.nlevels) {
             const int sz = rule.h_start[l + cnt + 1] - rule.h_start[l + cnt];
-            if (cnt > 0 && nodes + sz > cap) break;
+            if (cnt > 0 && nodes + sz > wave) break;
             nodes += sz;
             ++cnt;
         }
@@ -401,44 +579,61 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const double *V,
                             sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * m,
                             sizeof(double) * m, sizeof(double) * chunk * mm, sizeof(double) * (size_t)cap * m,
                             sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
-                            sizeof(double) * 4};
+                            sizeof(double) * 4, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap};
+    constexpr int kNbuf = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
     for (size_t v : sizes) total += al(v);
     char *ws = nullptr;
     skf_status stt = dalloc((void **)&ws, total, st);
     if (stt != SKF_OK) return stt;
-    double *ptrs[14];
+    double *ptrs[kNbuf];
     size_t off = 0;
-    for (int i = 0; i < 14; ++i) {
+    for (int i = 0; i < kNbuf; ++i) {
         ptrs[i] = (double *)(ws + off);
         off += al(sizes[i]);
     }
     c.Aw = ptrs[0]; c.Rdiag = ptrs[1]; c.M = ptrs[2]; c.R2 = ptrs[3]; c.B = ptrs[4]; c.C = ptrs[5];
     c.cvec = ptrs[6]; c.Mtc = ptrs[7]; c.Nw = ptrs[8]; c.out = ptrs[9]; c.qbuf = ptrs[10]; c.qacc = ptrs[11];
-    c.z = ptrs[12]; c.qstate = ptrs[13];
+    c.z = ptrs[12]; c.qstate = ptrs[13]; c.MT = ptrs[14]; c.R2T = ptrs[15]; c.nodebad = (int *)ptrs[16];
 
     const int G = std::min(2 * num_sms(), 1024);
+    long long nlaunch = 0;
     k_tail_copy<<<G, kThreads, 0, st>>>(SV, SAV, c);
-    const int hhG = std::max(1, std::min(num_sms(), 2 * m));
+    ++nlaunch;
     const int nref = (method == SKF_METHOD_SGMRES) ? 2 * m : m;
-    for (int jj = 0; jj < nref; ++jj) k_householder<<<hhG, kThreads, 0, st>>>(c, jj);
+    for (int jj = 0; jj < nref; ++jj) {
+        const int ntrail = std::max(1, 2 * m - jj - 1);
+        k_householder<<<(ntrail + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c, jj);
+    }
+    nlaunch += nref;
     {
         const int rows = (method == SKF_METHOD_SGMRES) ? 2 * m : m;
         const int blocks = (rows + (kThreads / 32) - 1) / (kThreads / 32);
         const size_t smem = sizeof(double) * (kThreads / 32) * m;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k_tri_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_tri_right<<<blocks, kThreads, smem, st>>>(c);
+        ++nlaunch;
     }
     k_tail_prep<<<G, kThreads, 0, st>>>(c);
+    ++nlaunch;
     const size_t nsmem = sizeof(double) * 4 * m;
     if (nsmem > 48 * 1024) cudaFuncSetAttribute(k_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsmem);
+    const int mm_mixed = std::min(m, kMixedMaxM);
+    const size_t msmem = sizeof(double) * 4 * m + sizeof(float) * ((size_t)m + (size_t)mm_mixed * (mm_mixed + 1) / 2);
+    if (msmem > 48 * 1024)
+        cudaFuncSetAttribute(k_nodes_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
     for (size_t bi = 0; bi < batches.size(); ++bi) {
         const int l0 = batches[bi].first, nl = batches[bi].second;
         const int n0 = rule.h_start[l0];
         const int nn = rule.h_start[l0 + nl] - n0;
-        for (int o = 0; o < nn; o += chunk) k_nodes<<<std::min(chunk, nn - o), kThreads, nsmem, st>>>(c, n0, o);
+        for (int o = 0; o < nn; o += chunk) {
+            k_nodes_mixed<<<std::min(chunk, nn - o), kThreads, msmem, st>>>(c, n0, o);
+            k_nodes<<<std::min(chunk, nn - o), kThreads, nsmem, st>>>(c, n0, o);
+            nlaunch += 2;
+        }
         k_levels<<<1, kThreads, 0, st>>>(c, l0, nl, rule.lev_start, rule.lev_ell, n0, tol,
                                          bi + 1 == batches.size() ? 1 : 0);
+        ++nlaunch;
     }
     const size_t qsm = sizeof(double) * m;
     if (qsm > 48 * 1024) cudaFuncSetAttribute(k_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
@@ -446,6 +641,8 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const double *V,
     const int64_t rb = std::min<int64_t>((n + kThreads - 1) / kThreads, 16 * num_sms());
     k_recombine<<<(unsigned)std::max<int64_t>(rb, 1), kThreads, 0, st>>>(V, ldv, n, c.z, iscal, x);
     k_write_info<<<1, 32, 0, st>>>(c, info);
+    nlaunch += 3;
+    count_launches(nlaunch);
     cudaError_t e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "tail kernels");
