@@ -183,6 +183,25 @@ skf_status skf_sketch_destroy(skf_sketch *S);
 skf_status skf_sketch_apply(const skf_sketch *S, const void *X, skf_dtype xdtype, int64_t ldx,
                             int32_t ncols, double *SX, skf_stream_t stream);
 
+/* skf_sketch_apply_noalloc: the same result as skf_sketch_apply for a
+ * sparse-sign sketch and F64 X, computed without allocating any device
+ * memory.  The paper has no counterpart; this entry point exists for callers
+ * that cannot call cudaMalloc/cudaMallocAsync at the point of use (a runtime
+ * that owns and budgets every device allocation, or a path that must not
+ * synchronise or touch the allocator).  Its scratch is a fixed 4 MiB array
+ * inside this library, which every GPU that loads the library keeps until
+ * the process exits; it must hold G * ncols * (s + 1) doubles, G being the
+ * kernels' CTA count (at most 2 per SM), otherwise the call returns
+ * SKF_ERR_INVALID_ARG and says how much it would need.  The first call on a
+ * device looks up that array's device address (once per device), so make the
+ * first call before capturing the stream into a CUDA graph.  All calls on a
+ * device share the array: calls whose kernels can overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Nothing needs clearing between calls: every scratch word a call reads is
+ * written by that call first.  Errors: INVALID_ARG, NOT_SUPPORTED, CUDA. */
+skf_status skf_sketch_apply_noalloc(const skf_sketch *S, const void *X, skf_dtype xdtype, int64_t ldx,
+                                    int32_t ncols, double *SX, skf_stream_t stream);
+
 /* -------------------------------------------------------------- basis */
 /* skf_arnoldi_trunc: the basis generation of Algorithm 2 (k-truncated
  * modified Gram-Schmidt, Sec. 2.2) with the sketches S V_m, S A V_m built on

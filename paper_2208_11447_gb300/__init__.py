@@ -81,6 +81,7 @@ def lib():
         L.skf_sketch_create.argtypes = [ctypes.c_int, i64, i32, i32, u64, vp, ctypes.POINTER(vp)]
         L.skf_sketch_destroy.argtypes = [vp]
         L.skf_sketch_apply.argtypes = [vp, vp, ctypes.c_int, i64, i32, vp, vp]
+        L.skf_sketch_apply_noalloc.argtypes = [vp, vp, ctypes.c_int, i64, i32, vp, vp]
         L.skf_arnoldi_trunc.argtypes = [vp, vp, vp, ctypes.c_int, i32, i32, ctypes.c_int, vp, i64, vp, vp, vp, vp,
                                         vp, vp]
         L.skf_solve.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int, ctypes.POINTER(Func),
@@ -89,7 +90,8 @@ def lib():
         L.skf_sgmres.argtypes = L.skf_solve.argtypes[1:]
         L.skf_quadrature_rule.argtypes = [ctypes.POINTER(Func), i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
-                     "skf_sketch_destroy", "skf_sketch_apply", "skf_arnoldi_trunc", "skf_solve", "skf_sfom",
+                     "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
+                     "skf_solve", "skf_sfom",
                      "skf_sgmres", "skf_quadrature_rule"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -170,6 +172,20 @@ def sketch_apply(S: Sketch, X: torch.Tensor, SX: torch.Tensor | None = None, str
         SX = torch.empty((ncols, S.s), dtype=torch.float64, device=X.device)
     _check(lib().skf_sketch_apply(S.handle, _ptr(Xcm), _DTYPE[X.dtype], X.shape[0], ncols, _ptr(SX),
                                   _stream(stream)))
+    out = SX.t()
+    return out.reshape(S.s) if X.dim() == 1 else out
+
+
+def sketch_apply_noalloc(S: Sketch, X: torch.Tensor, SX: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """As sketch_apply, through the allocation-free entry point (the output
+    tensor is allocated here, by the caller of the C ABI, as the ABI requires)."""
+    Xc = X.reshape(X.shape[0], -1)
+    ncols = Xc.shape[1]
+    Xcm = Xc.t().contiguous()
+    if SX is None:
+        SX = torch.empty((ncols, S.s), dtype=torch.float64, device=X.device)
+    _check(lib().skf_sketch_apply_noalloc(S.handle, _ptr(Xcm), _DTYPE[X.dtype], X.shape[0], ncols, _ptr(SX),
+                                          _stream(stream)))
     out = SX.t()
     return out.reshape(S.s) if X.dim() == 1 else out
 

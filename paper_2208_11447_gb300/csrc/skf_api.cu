@@ -452,6 +452,14 @@ skf_status skf_sketch_apply(const skf_sketch *S, const void *X, skf_dtype xdtype
     return sketch_apply_f64(S, (const double *)X, ldx, ncols, SX, (cudaStream_t)stream);
 }
 
+skf_status skf_sketch_apply_noalloc(const skf_sketch *S, const void *X, skf_dtype xdtype, int64_t ldx, int32_t ncols,
+                                    double *SX, skf_stream_t stream) {
+    if (!S || (!X && ncols > 0) || (!SX && ncols > 0)) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    if (ncols < 0 || ldx < S->n) return fail(SKF_ERR_INVALID_ARG, "ncols < 0 or ldx < n");
+    if (xdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "X must be F64 in this build");
+    return sketch_apply_f64_noalloc(S, (const double *)X, ldx, ncols, SX, (cudaStream_t)stream);
+}
+
 static skf_status check_common(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, int m, int k,
                                skf_dtype basis) {
     if (!A || !S || !b) return fail(SKF_ERR_INVALID_ARG, "NULL argument");

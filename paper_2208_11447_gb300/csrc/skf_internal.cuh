@@ -348,6 +348,8 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const double *V,
 
 // Sketch-apply launcher shared by the API and the solvers.
 skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st);
+skf_status sketch_apply_f64_noalloc(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX,
+                                    cudaStream_t st);
 skf_status sketch_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX,
                             cudaStream_t st);
 

@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "skf_internal.cuh"
 
@@ -228,6 +229,89 @@ skf_status sketch_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, i
     dfree(part, st);
     dfree(maxpart, st);
     if (e != cudaSuccess) return cuda_fail(e, "sketch_apply kernels");
+    return SKF_OK;
+}
+
+// ---------------------------------------------------------------------
+// Allocation-free variant of sketch_apply_f64.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// sketch: code running inside a memory-budgeted runtime that owns every
+// allocation, callers that must not synchronise (cudaMalloc/cudaFree can
+// synchronise the device), or code paths that are forbidden to change the
+// allocator's state.  For them the scratch of the column-max / scatter /
+// reduce pipeline (per-CTA column maxima and per-CTA integer partial sums)
+// lives in the fixed array below instead of coming from cudaMallocAsync.
+//
+// kNoAllocScratchBytes bounds G * ncols * (s + 1) * 8 bytes, where G is the
+// number of CTAs of the row partition (at most 2 per SM).  The array is a
+// module global: every GPU that loads this library keeps it for the life of
+// the process, and all calls on a device share it, so calls whose kernels
+// may overlap on the GPU (different streams, or different host threads)
+// race on it.  Every word a call reads is first written by the same call, so
+// nothing has to be cleared between calls.
+constexpr size_t kNoAllocScratchBytes = 4u << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (set-up once per
+// device; cudaGetSymbolAddress is not valid inside a stream capture).
+skf_status noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SKF_ERR_NOT_SUPPORTED, "device ordinal too large");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SKF_OK;
+}
+
+}  // namespace
+
+skf_status sketch_apply_f64_noalloc(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX,
+                                    cudaStream_t st) {
+    if (S->kind != SKF_SKETCH_SPARSE_SIGN)
+        return fail(SKF_ERR_NOT_SUPPORTED, "the allocation-free sketch apply supports the sparse-sign sketch only");
+    if (ncols <= 0) return SKF_OK;
+    const int64_t n = S->n;
+    int G;
+    int64_t rows;
+    row_partition(n, &G, &rows);
+    const size_t need = sizeof(long long) * (size_t)G * ncols * ((size_t)S->s + 1);
+    if (need > kNoAllocScratchBytes)
+        return fail(SKF_ERR_INVALID_ARG, "allocation-free sketch apply needs " + std::to_string(need) +
+                                             " bytes of scratch, more than its fixed " +
+                                             std::to_string(kNoAllocScratchBytes) +
+                                             " (reduce ncols or s, or use skf_sketch_apply)");
+    void *base = nullptr;
+    skf_status stt = noalloc_scratch(&base);
+    if (stt != SKF_OK) return stt;
+    double *maxpart = (double *)base;                                         // [ncols][G]
+    long long *part = (long long *)((char *)base + sizeof(double) * (size_t)G * ncols);   // [ncols][G][s]
+    const SparseSign sp = make_sparse_sign(S);
+    k_colmax<<<G, kThreads, 0, st>>>(X, ldx, n, ncols, rows, maxpart);
+    const size_t smem = sizeof(int) * 2 * S->s;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_sparse_sign_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_sparse_sign_scatter<<<G, kThreads, smem, st>>>(X, ldx, n, ncols, rows, sp, S->pattern, S->binmax, maxpart,
+                                                      part);
+    const int64_t tot = (int64_t)S->s * ncols;
+    k_sparse_sign_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, maxpart, G, S->s, ncols, S->zeta,
+                                                                        S->binmax, SX);
+    count_launches(3);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "allocation-free sketch_apply kernels");
     return SKF_OK;
 }
 
