@@ -175,6 +175,30 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def run_arnoldi_only(args, wl, A, b, op, dev, rank, world):
+    """Time skf_arnoldi_trunc alone (m steps of the two step kernels)."""
+    import torch
+    import paper_2208_11447_gb300 as skf
+    m = args.m or wl.m
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, wl.s, wl.zeta, 13)
+    b_dev = torch.as_tensor(b, device=dev)
+    for _ in range(args.warmup):
+        skf.arnoldi_trunc(op.csr, S, b_dev, m, wl.k)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(args.steps):
+        ev0.record()
+        skf.arnoldi_trunc(op.csr, S, b_dev, m, wl.k)
+        ev1.record()
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    if rank == 0:
+        us = statistics.median(times) * 1e3 / m
+        print(json.dumps({"mode": "arnoldi", "workload": args.workload, "m": m, "us_per_step": round(us, 2)}),
+              flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,6 +209,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--arnoldi-reps", type=int, default=5)
+    ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi"],
+                    help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu")
+    ap.add_argument("--m", type=int, default=None, help="override the Krylov dimension (arnoldi mode)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -218,6 +245,9 @@ def main():
 
     wl, A, b = build_inputs(args.workload)
     op = skf.upload_csr(A.rowptr, A.colind, A.values, device=dev)
+    if args.mode == "arnoldi":
+        run_arnoldi_only(args, wl, A, b, op, dev, rank, world)
+        return
     S = skf.Sketch(skf.SPARSE_SIGN, A.n, wl.s, wl.zeta, 13)
     c = quad_scale(wl.func, wl.lam_lo or 0.0, op.csr.norm_inf())
     f = skf.make_func(wl.func, c)
