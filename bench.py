@@ -33,6 +33,10 @@ HBM_PEAK_FALLBACK = 6800.0
 # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA
 # throughput on this part: 1.20 TFLOP/s, i.e. the same unit count).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# DRAM bytes (read + write) per Arnoldi step, summed over the spmv and update
+# kernels of one ncu capture of those kernels as they stand; keyed by workload
+# and basis dtype, and removed whenever those kernels change.
+NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64"): 146.4e6}
 
 
 def measured_peaks():
@@ -326,6 +330,7 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src}
+    roof["traffic"] = NCU_TRAFFIC_PER_STEP.get((args.workload, "f64"))
     roof.update({"kernel": "truncated-Arnoldi step (k_arnoldi_spmv + k_arnoldi_update)", "us_per_step": round(step_us, 2),
                  "alg_bytes_per_step": alg_bytes, "alg_flops_per_step": alg_flops,
                  "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak,
