@@ -39,6 +39,36 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64"): 146.4e6}
 
 
+BASIS_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "bf16": "bf16-storage/f32"}
+METRIC = {"f64": "f(A)b solves/s (sFOM + sGMRES, FP64)",
+          "f32": "f(A)b solves/s (sFOM + sGMRES, FP32 basis and arithmetic, FP64 tail)",
+          "bf16": "f(A)b solves/s (sFOM + sGMRES, BF16 basis, FP32 arithmetic, FP64 tail)"}
+
+
+def basis_torch(name: str):
+    import torch
+    return {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[name]
+
+
+def reference_error_fp64(skf, A, S, b_dev, f, wl, x_fom, x_gm, dev):
+    """Relative 2-norm error of the reduced-precision results against the FP64
+    GPU path on the same operator (values widened exactly), sketch and rule."""
+    import numpy as np
+    import torch
+    op64 = skf.upload_csr(A.rowptr, A.colind, A.values.astype(np.float64), device=dev)
+    p64 = skf.make_params(wl.m, wl.k, tol=1e-10)
+    r_f = skf.sfom(op64.csr, S, b_dev, f, p64)
+    r_g = skf.sgmres(op64.csr, S, b_dev, f, p64)
+    torch.cuda.synchronize()
+    e_f = float(torch.linalg.norm(x_fom - r_f) / torch.linalg.norm(r_f))
+    e_g = float(torch.linalg.norm(x_gm - r_g) / torch.linalg.norm(r_g))
+    del op64, r_f, r_g
+    torch.cuda.empty_cache()
+    return {"rel_err_vs_fp64_gpu": {"sfom": e_f, "sgmres": e_g}, "target": 1e-6,
+            "meets_target": bool(max(e_f, e_g) <= 1e-6)}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -184,23 +214,24 @@ def run_arnoldi_only(args, wl, A, b, op, dev, rank, world):
     import torch
     import paper_2208_11447_gb300 as skf
     m = args.m or wl.m
+    bdt = basis_torch(args.basis)
     S = skf.Sketch(skf.SPARSE_SIGN, A.n, wl.s, wl.zeta, 13)
     b_dev = torch.as_tensor(b, device=dev)
     for _ in range(args.warmup):
-        skf.arnoldi_trunc(op.csr, S, b_dev, m, wl.k)
+        skf.arnoldi_trunc(op.csr, S, b_dev, m, wl.k, basis_dtype=bdt)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = []
     for _ in range(args.steps):
         ev0.record()
-        skf.arnoldi_trunc(op.csr, S, b_dev, m, wl.k)
+        skf.arnoldi_trunc(op.csr, S, b_dev, m, wl.k, basis_dtype=bdt)
         ev1.record()
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1))
     if rank == 0:
         us = statistics.median(times) * 1e3 / m
-        print(json.dumps({"mode": "arnoldi", "workload": args.workload, "m": m, "us_per_step": round(us, 2)}),
-              flush=True)
+        print(json.dumps({"mode": "arnoldi", "workload": args.workload, "basis": args.basis, "m": m,
+                          "us_per_step": round(us, 2)}), flush=True)
 
 
 def main():
@@ -216,6 +247,8 @@ def main():
     ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi"],
                     help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu")
     ap.add_argument("--m", type=int, default=None, help="override the Krylov dimension (arnoldi mode)")
+    ap.add_argument("--basis", default=None, choices=["f64", "f32", "bf16"],
+                    help="basis storage (default: the workload's); f32/bf16 need an FP32 operator")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -248,6 +281,13 @@ def main():
         return float(t.item())
 
     wl, A, b = build_inputs(args.workload)
+    basis = args.basis or wl.basis_dtype
+    if basis != "f64" and A.values.dtype != np.float32:
+        A = A.astype(np.float32)
+    if basis == "f64" and A.values.dtype != np.float64:
+        A = A.astype(np.float64)
+    args.basis = basis
+    bdt = basis_torch(basis)
     op = skf.upload_csr(A.rowptr, A.colind, A.values, device=dev)
     if args.mode == "arnoldi":
         run_arnoldi_only(args, wl, A, b, op, dev, rank, world)
@@ -255,7 +295,7 @@ def main():
     S = skf.Sketch(skf.SPARSE_SIGN, A.n, wl.s, wl.zeta, 13)
     c = quad_scale(wl.func, wl.lam_lo or 0.0, op.csr.norm_inf())
     f = skf.make_func(wl.func, c)
-    p = skf.make_params(wl.m, wl.k, tol=1e-10)
+    p = skf.make_params(wl.m, wl.k, basis_dtype=bdt, tol=1e-10)
     b_dev = torch.as_tensor(b, device=dev)
     x_fom = torch.empty_like(b_dev)
     x_gm = torch.empty_like(b_dev)
@@ -272,6 +312,9 @@ def main():
         step()
     torch.cuda.synchronize()
     st_f, st_g = skf.read_info(info_f), skf.read_info(info_g)
+    accuracy = None
+    if basis != "f64":
+        accuracy = reference_error_fp64(skf, A, S, b_dev, f, wl, x_fom, x_gm, dev)
 
     # ---- timed region: device-resident inputs, L2 flushed between steps
     clocks = ClockSampler(local)
@@ -296,7 +339,7 @@ def main():
     value = world * 2 * args.steps / (t_max / 1e3)
 
     # ---- dominant kernels: the truncated-Arnoldi step (spmv + update launches)
-    V = torch.empty((wl.m, A.n), dtype=torch.float64, device=dev)
+    V = torch.empty((wl.m, A.n), dtype=bdt, device=dev)
     vsc = torch.empty(wl.m, dtype=torch.float64, device=dev)
     SV = torch.empty((wl.m, wl.s), dtype=torch.float64, device=dev)
     SAV = torch.empty_like(SV)
@@ -306,7 +349,8 @@ def main():
     for r in range(args.arnoldi_reps + 1):
         flush.zero_()
         ev0.record(stream)
-        skf._check(L.skf_arnoldi_trunc(op.csr.handle, S.handle, skf._ptr(b_dev), skf.F64, wl.m, wl.k, skf.F64,
+        skf._check(L.skf_arnoldi_trunc(op.csr.handle, S.handle, skf._ptr(b_dev), skf.F64, wl.m, wl.k,
+                                       skf._DTYPE[bdt],
                                        skf._ptr(V), A.n, skf._ptr(vsc), skf._ptr(SV), skf._ptr(SAV), skf._ptr(H),
                                        None, skf._stream(stream)))
         ev1.record(stream)
@@ -316,22 +360,24 @@ def main():
     step_us = statistics.median(arn_ms) * 1e3 / wl.m
     nnz, N, k = A.nnz, A.n, wl.k
     bv = 8 if A.values.dtype == np.float64 else 4
-    alg_bytes = nnz * (bv + 4) + 4 * (N + 1) + (k + 1) * N * 8       # per step: A once, window, new vector
+    bb = BASIS_BYTES[basis]
+    alg_bytes = nnz * (bv + 4) + 4 * (N + 1) + (k + 1) * N * bb      # per step: A once, window, new vector
     alg_flops = 2 * nnz + (4 * k + 3) * N                             # SpMV + k dots + k axpys + norm + scale
     hbm_peak, hbm_src = measured_peaks()
     achieved_gflops = alg_flops / (step_us * 1e-6) / 1e9
     achieved_gbs = alg_bytes / (step_us * 1e-6) / 1e9
     fp64_bound_us = alg_flops / (FP64_PEAK_GFLOPS * 1e9) * 1e6
     hbm_bound_us = alg_bytes / (hbm_peak * 1e9) * 1e6
-    if fp64_bound_us >= hbm_bound_us:
+    if basis == "f64" and fp64_bound_us >= hbm_bound_us:
         roof = {"bound": "alu", "achieved": round(achieved_gflops, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
                 "unit": "GFLOP/s", "frac": round(achieved_gflops / FP64_PEAK_GFLOPS, 4), "traffic": None,
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)"}
     else:
         roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src}
-    roof["traffic"] = NCU_TRAFFIC_PER_STEP.get((args.workload, "f64"))
-    roof.update({"kernel": "truncated-Arnoldi step (k_arnoldi_spmv + k_arnoldi_update)", "us_per_step": round(step_us, 2),
+    roof["traffic"] = NCU_TRAFFIC_PER_STEP.get((args.workload, basis))
+    kname = "k_arnoldi_spmv + k_arnoldi_update" if basis == "f64" else "k_arnoldi_spmv_lp + k_arnoldi_update_lp"
+    roof.update({"kernel": f"truncated-Arnoldi step ({kname})", "us_per_step": round(step_us, 2),
                  "alg_bytes_per_step": alg_bytes, "alg_flops_per_step": alg_flops,
                  "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak,
                          "frac": round(achieved_gbs / hbm_peak, 4), "of": hbm_src}})
@@ -364,15 +410,17 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "f(A)b solves/s (sFOM + sGMRES, FP64)", "value": round(value, 3), "unit": "solves/s",
+            "metric": METRIC[basis], "value": round(value, 3), "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[basis],
             "data": "synthetic",
             "config": {"workload": args.workload, "N": int(A.n), "nnz": int(A.nnz), "m": wl.m, "k": wl.k,
                        "s": wl.s, "zeta": wl.zeta, "sketch": "sparse_sign", "f": wl.func, "quad_scale": c,
                        "quad_tol": 1e-10, "parallelism": f"replicas x{world}", "l2": "flushed between steps",
                        "ell_sfom": st_f["ell"], "ell_sgmres": st_g["ell"], "status": [st_f["status_name"],
-                                                                                     st_g["status_name"]]},
+                                                                                     st_g["status_name"]],
+                       "basis": basis, "values": "f64" if A.values.dtype == np.float64 else "f32"},
+            "accuracy": accuracy,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": int(b.nbytes),

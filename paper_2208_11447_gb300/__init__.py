@@ -277,8 +277,10 @@ class DeviceOperator:
     csr: Csr
 
 
-def upload_csr(rowptr, colind, values, device="cuda") -> DeviceOperator:
+def upload_csr(rowptr, colind, values, device="cuda", dtype=None) -> DeviceOperator:
+    """dtype: torch.float64 or torch.float32 for the stored values (default:
+    that of `values`).  An F32 operator is what the FP32/BF16-basis path takes."""
     rp = torch.as_tensor(rowptr, dtype=torch.int64).to(device)
     ci = torch.as_tensor(colind, dtype=torch.int32).to(device)
-    va = torch.as_tensor(values).to(device)
+    va = torch.as_tensor(values, dtype=dtype).to(device)
     return DeviceOperator(rp, ci, va, Csr(rp, ci, va))

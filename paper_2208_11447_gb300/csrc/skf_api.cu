@@ -208,13 +208,14 @@ __global__ void k_rowptr32(const int64_t *__restrict__ in, int64_t n, int32_t *_
     }
 }
 
-__global__ void k_row_abs_sum(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
+template <typename TV>
+__global__ void k_row_abs_sum(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const TV *__restrict__ v,
                               int64_t n, int *bad, unsigned long long *maxbits) {
     double mx = 0.0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int p = rp[r]; p < rp[r + 1]; ++p) {
-            acc += fabs(v[p]);
+            acc += fabs((double)v[p]);
             if (ci[p] < 0 || ci[p] >= n) atomicExch(bad, 1);
         }
         mx = fmax(mx, acc);
@@ -232,9 +233,10 @@ __global__ void k_sell_width(const int32_t *__restrict__ rp, int64_t n, int64_t 
     }
 }
 
-__global__ void k_sell_fill(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
+template <typename TV>
+__global__ void k_sell_fill(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const TV *__restrict__ v,
                             int64_t n, int64_t nslices, const int64_t *__restrict__ off, const int32_t *__restrict__ w,
-                            double *__restrict__ sv, int32_t *__restrict__ sc) {
+                            TV *__restrict__ sv, int32_t *__restrict__ sc) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < 32 * nslices;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = r >> 5;
@@ -244,7 +246,7 @@ __global__ void k_sell_fill(const int32_t *__restrict__ rp, const int32_t *__res
         const int self = r < n ? (int)r : 0;
         for (int p = 0; p < wt; ++p) {
             const int64_t o = off[t] + 32ll * p + l;
-            sv[o] = p < len ? v[b + p] : 0.0;
+            sv[o] = p < len ? v[b + p] : (TV)0;
             sc[o] = p < len ? ci[b + p] : self;
         }
     }
@@ -286,7 +288,8 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
     if (n < 1 || n >= (1ll << 31)) return fail(SKF_ERR_INVALID_ARG, "n must be in [1, 2^31)");
     if (nnz < 0 || nnz >= (1ll << 31)) return fail(SKF_ERR_INVALID_ARG, "nnz must be in [0, 2^31)");
     if (!rowptr || (nnz > 0 && (!colind || !values))) return fail(SKF_ERR_INVALID_ARG, "NULL CSR array");
-    if (vdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "matrix values must be F64 in this build");
+    if (vdtype != SKF_F64 && vdtype != SKF_F32) return fail(SKF_ERR_NOT_SUPPORTED, "matrix values must be F64 or F32");
+    const size_t esz = vdtype == SKF_F64 ? sizeof(double) : sizeof(float);
     if (mode != SKF_BORROW && mode != SKF_COPY) return fail(SKF_ERR_INVALID_ARG, "bad copy mode");
     cudaStream_t st = (cudaStream_t)stream;
     skf_csr *A = new skf_csr();
@@ -307,12 +310,12 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
     }
     if (mode == SKF_COPY && nnz > 0) {
         if (cudaMalloc(&A->colind_own, sizeof(int32_t) * nnz) != cudaSuccess ||
-            cudaMalloc(&A->values_own, sizeof(double) * nnz) != cudaSuccess) {
+            cudaMalloc(&A->values_own, esz * nnz) != cudaSuccess) {
             cudaGetLastError();
             return cleanup(fail(SKF_ERR_OOM, "CSR copy allocation"));
         }
         if (cudaMemcpyAsync(A->colind_own, colind, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(A->values_own, values, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            cudaMemcpyAsync(A->values_own, values, esz * nnz, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return cleanup(cuda_fail(cudaGetLastError(), "CSR copy"));
         A->colind = A->colind_own;
         A->values = A->values_own;
@@ -337,7 +340,10 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "skf_create_csr"));
     if (hbad || first != 0 || last != nnz) return cleanup(fail(SKF_ERR_INVALID_ARG, "invalid row pointer"));
-    k_row_abs_sum<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, dbad, dmax);
+    if (vdtype == SKF_F64)
+        k_row_abs_sum<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, dbad, dmax);
+    else
+        k_row_abs_sum<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const float *)A->values, n, dbad, dmax);
     count_launches(1);
     unsigned long long hmax = 0;
     cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st);
@@ -366,14 +372,18 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
         A->max_width = std::max(A->max_width, hw[t]);
     }
     const int64_t padded = hoff[A->nslices];
-    if (cudaMalloc(&A->sell_val, sizeof(double) * std::max<int64_t>(padded, 1)) != cudaSuccess ||
+    if (cudaMalloc(&A->sell_val, esz * std::max<int64_t>(padded, 1)) != cudaSuccess ||
         cudaMalloc(&A->sell_col, sizeof(int32_t) * std::max<int64_t>(padded, 1)) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(fail(SKF_ERR_OOM, "SELL allocation"));
     }
     cudaMemcpyAsync(A->sell_off, hoff.data(), sizeof(int64_t) * (A->nslices + 1), cudaMemcpyHostToDevice, st);
-    k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, A->nslices, A->sell_off,
-                                        A->sell_w, A->sell_val, A->sell_col);
+    if (vdtype == SKF_F64)
+        k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, A->nslices,
+                                            A->sell_off, A->sell_w, (double *)A->sell_val, A->sell_col);
+    else
+        k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const float *)A->values, n, A->nslices,
+                                            A->sell_off, A->sell_w, (float *)A->sell_val, A->sell_col);
     count_launches(1);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "SELL fill"));
@@ -468,8 +478,26 @@ static skf_status check_common(const skf_csr *A, const skf_sketch *S, const void
     if (m > A->n) return fail(SKF_ERR_INVALID_ARG, "need m <= n");
     if (k < 1 || k > kMaxK) return fail(SKF_ERR_INVALID_ARG, "need 1 <= k <= 16");
     if (bdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "b must be F64 in this build");
-    if (basis != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "basis must be F64 in this build");
+    if (basis == SKF_F64) {
+        if (A->vdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "an F64 basis needs F64 matrix values");
+    } else if (basis == SKF_F32 || basis == SKF_BF16) {
+        if (A->vdtype != SKF_F32) return fail(SKF_ERR_NOT_SUPPORTED, "an F32 or BF16 basis needs F32 matrix values");
+        if (S->kind != SKF_SKETCH_SPARSE_SIGN && S->kind != SKF_SKETCH_IDENTITY)
+            return fail(SKF_ERR_NOT_SUPPORTED, "sketch kind not implemented");
+    } else {
+        return fail(SKF_ERR_INVALID_ARG, "unknown basis dtype");
+    }
     return SKF_OK;
+}
+
+static size_t dtype_size(skf_dtype d) { return d == SKF_F64 ? 8 : d == SKF_F32 ? 4 : 2; }
+
+static skf_status run_arnoldi(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, skf_dtype basis,
+                              void *V, int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
+                              skf_info *info, cudaStream_t cs) {
+    if (basis == SKF_F64) return arnoldi_run(A, S, b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+    if (basis == SKF_F32) return arnoldi_run_f32(A, S, b, m, k, (float *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+    return arnoldi_run_bf16(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, cs);
 }
 
 skf_status skf_arnoldi_trunc(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, int32_t m,
@@ -483,7 +511,7 @@ skf_status skf_arnoldi_trunc(const skf_csr *A, const skf_sketch *S, const void *
     int *iscal = nullptr;
     st = dalloc((void **)&iscal, sizeof(int) * 4, cs);
     if (st != SKF_OK) return st;
-    st = arnoldi_run(A, S, (const double *)b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+    st = run_arnoldi(A, S, (const double *)b, m, k, basis_dtype, V, ldv, vscale, SV, SAV, H, iscal, info, cs);
     dfree(iscal, cs);
     return st;
 }
@@ -518,7 +546,8 @@ skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, c
     const int64_t n = A->n;
     const int s = S->s;
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t szV = sizeof(double) * (size_t)n * m;
+    const skf_dtype bt = p->basis_dtype;
+    const size_t szV = dtype_size(bt) * (size_t)n * m;
     const size_t szS = sizeof(double) * (size_t)s * m;
     const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
     const size_t total = al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4);
@@ -526,15 +555,15 @@ skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, c
     st = dalloc((void **)&ws, total, cs);
     if (st != SKF_OK) return st;
     size_t off = 0;
-    double *V = (double *)(ws + off); off += al(szV);
+    void *V = (void *)(ws + off); off += al(szV);
     double *SV = (double *)(ws + off); off += al(szS);
     double *SAV = (double *)(ws + off); off += al(szS);
     double *H = (double *)(ws + off); off += al(szH);
     double *vscale = (double *)(ws + off); off += al(sizeof(double) * m);
     int *iscal = (int *)(ws + off);
-    st = arnoldi_run(A, S, (const double *)b, m, p->k, V, n, vscale, SV, SAV, H, iscal, info, cs);
+    st = run_arnoldi(A, S, (const double *)b, m, p->k, bt, V, n, vscale, SV, SAV, H, iscal, info, cs);
     if (st == SKF_OK)
-        st = tail_run(method, s, m, n, V, n, vscale, SV, SAV, iscal, *rule, p->tol, (double *)x, info, cs);
+        st = tail_run(method, s, m, n, V, bt, n, vscale, SV, SAV, iscal, *rule, p->tol, (double *)x, info, cs);
     dfree(ws, cs);
     return st;
 }

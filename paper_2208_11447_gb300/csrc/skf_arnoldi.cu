@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "skf_internal.cuh"
+#include "skf_step.cuh"
 
 namespace skf {
 
@@ -70,68 +71,6 @@ struct ArnCtx {
 
 namespace {
 
-constexpr int kNoExp = -100000;
-
-// Exact sum of G int64 partials by one warp (lanes strided over G, 128-bit
-// butterfly); every lane returns the same double.
-__device__ __forceinline__ double warp_sum_i64_exact(const long long *p, int G, size_t stride) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long lo = 0;
-    long long hi = 0;
-    for (int g = lane; g < G; g += 32) {
-        const long long v = __ldcg(p + (size_t)g * stride);
-        const unsigned long long nlo = lo + (unsigned long long)v;
-        hi += (v < 0 ? -1 : 0) + (nlo < lo ? 1 : 0);
-        lo = nlo;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long olo = __shfl_xor_sync(0xffffffffu, lo, o);
-        const long long ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-        const unsigned long long nlo = lo + olo;
-        hi += ohi + (nlo < lo ? 1 : 0);
-        lo = nlo;
-    }
-    const bool neg = hi < 0;
-    unsigned long long uhi = (unsigned long long)hi;
-    if (neg) {
-        lo = ~lo + 1ull;
-        uhi = ~uhi + (lo == 0ull ? 1ull : 0ull);
-    }
-    const double r = (double)uhi * 18446744073709551616.0 + (double)lo;
-    return neg ? -r : r;
-}
-
-// Fixed-order reduction of G partials by one warp (sum or max).
-__device__ __forceinline__ double warp_reduce_partials(const double *p, int G, int stride, bool is_max) {
-    const int lane = threadIdx.x & 31;
-    double acc = 0.0;
-    for (int g = lane; g < G; g += 32) {
-        const double v = __ldcg(p + (size_t)g * stride);
-        acc = is_max ? fmax(acc, v) : acc + v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double t = __shfl_xor_sync(0xffffffffu, acc, o);
-        acc = is_max ? fmax(acc, t) : acc + t;
-    }
-    return acc;
-}
-
-// The zeta pattern entries of column r (one 16-byte load for zeta = 8).
-template <int ZCAP>
-__device__ __forceinline__ void load_pattern(const uint16_t *pattern, int zeta, int64_t r, uint16_t (&e)[ZCAP]) {
-    if (ZCAP == 8 && zeta == 8) {
-        const uint4 v = __ldg((const uint4 *)(pattern + r * 8));
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) e[q] = (uint16_t)(w[q >> 1] >> (16 * (q & 1)));
-    } else {
-#pragma unroll
-        for (int q = 0; q < ZCAP; ++q) e[q] = q < zeta ? __ldg(pattern + r * zeta + q) : (uint16_t)0;
-    }
-}
-
 // Finalise a sketch column from the integer partials, for this CTA's slice of
 // the s rows: one warp per row of S.
 __device__ __forceinline__ void finalize_sketch(const long long *part, int G, int s, int E, int frac, double scale,
@@ -146,20 +85,6 @@ __device__ __forceinline__ void finalize_sketch(const long long *part, int G, in
         if (lane == 0) out_col[i] = v;
     }
 }
-
-// Arrival ticket: true in exactly one CTA, the last to finish its partials.
-__device__ __forceinline__ bool last_to_arrive(unsigned *cnt) {
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(cnt, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
-
 
 __global__ void __launch_bounds__(kThreads) k_arnoldi_init(ArnCtx c, const double *__restrict__ b) {
     __shared__ double red[64];
@@ -480,7 +405,6 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
 
 // After the loop: S v_{m-1} and S A v_{m-1}.
 __global__ void __launch_bounds__(kThreads) k_arnoldi_finish(ArnCtx c) {
-    const int G = gridDim.x;
     if (c.iscal[0] == 0 && !c.identity) {
         const int frac = sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
         const double sc = c.vscale[c.m - 1] * c.inv_sqrt_zeta;
@@ -548,7 +472,7 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     c.n = A->n;
     c.sell_off = A->sell_off;
     c.sell_w = A->sell_w;
-    c.sell_val = A->sell_val;
+    c.sell_val = (const double *)A->sell_val;
     c.sell_col = A->sell_col;
     c.max_width = A->max_width;
     c.identity = S->kind == SKF_SKETCH_IDENTITY;

@@ -53,10 +53,11 @@ struct skf_csr {
     // width[t] x 32 entries column-major (entry p of row 32t + l at
     // off[t] + 32 p + l), rows padded with value 0 and their own column.
     // Each row keeps the CSR order of its entries.
+    // Values keep the handle's dtype (vdtype: F64 or F32).
     int64_t nslices = 0;
     int64_t *sell_off = nullptr;      // [nslices + 1]
     int32_t *sell_w = nullptr;        // [nslices]
-    double *sell_val = nullptr;
+    void *sell_val = nullptr;
     int32_t *sell_col = nullptr;
     int max_width = 0;                // widest slice
 };
@@ -73,6 +74,7 @@ struct skf_sketch {
     // its sign (bit 15).  2 zeta bytes per column.
     uint16_t *pattern = nullptr;
     int *binmax = nullptr;            // device: most nonzeros one CTA row range puts in one row of S
+    int *binmax_chunk = nullptr;      // device: the same for the chunk-interleaved partition
 };
 
 namespace skf {
@@ -295,6 +297,13 @@ __device__ __forceinline__ unsigned long long block_max_key(unsigned long long k
 // CTAs, each owning `rows` consecutive rows.
 void row_partition(int64_t n, int *G, int64_t *rows);
 
+// Chunk-interleaved row partition of the reduced-precision SpMV kernel: rows
+// in chunks of kChunkRows, chunk c handled by CTA c mod G, G = min(SMs,
+// number of chunks).  All CTAs sweep the rows together, so the column
+// gathers of banded operators stay within a few MB of L2.
+constexpr int kChunkRows = 1024;
+void chunk_partition(int64_t n, int *G);
+
 // Fixed-point sketch accumulation.  A value x is rounded to the integer
 // v = x 2^(P - E) (E: exponent bound of the vector, |v| < 2^P) and split into
 // two signed 32-bit limbs v = l1 2^L + l0, 0 <= l0 < 2^L, |l1| < 2^(P-L);
@@ -342,9 +351,18 @@ struct RuleDev {
 skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V, int64_t ldv,
                        double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
                        cudaStream_t st);
-skf_status tail_run(skf_method method, int s, int m, int64_t n, const double *V, int64_t ldv, const double *vscale,
-                    const double *SV, const double *SAV, int *iscal, const RuleDev &rule, double tol, double *x,
-                    skf_info *info, cudaStream_t st);
+// Reduced-precision variants: FP32 matrix values, basis stored in FP32 or
+// BF16 (V of that type), FP32 SpMV and orthogonalisation, FP64 sketches.
+skf_status arnoldi_run_f32(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, float *V,
+                           int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
+                           skf_info *info, cudaStream_t st);
+skf_status arnoldi_run_bf16(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, void *V,
+                            int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
+                            skf_info *info, cudaStream_t st);
+// V has type vdt (F64, F32 or BF16).
+skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
+                    const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
+                    double tol, double *x, skf_info *info, cudaStream_t st);
 
 // Sketch-apply launcher shared by the API and the solvers.
 skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st);

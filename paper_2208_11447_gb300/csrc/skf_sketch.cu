@@ -36,6 +36,13 @@ void row_partition(int64_t n, int *G, int64_t *rows) {
     *rows = ((n + g - 1) / g + 31) / 32 * 32;   // whole SELL slices per CTA
 }
 
+void chunk_partition(int64_t n, int *G) {
+    const int64_t chunks = (n + kChunkRows - 1) / kChunkRows;
+    int g = num_sms();
+    if (chunks < g) g = (int)chunks;
+    *G = g < 1 ? 1 : g;
+}
+
 namespace {
 
 // pattern[c * zeta + q] = (row of nonzero q of column c within stripe q) | sign << 15
@@ -52,21 +59,24 @@ __global__ void k_build_pattern(SparseSign sp, int64_t n, uint16_t *__restrict__
     }
 }
 
-// Largest number of nonzeros that one CTA's row range puts into one row of S.
-__global__ void k_bin_max(SparseSign sp, int64_t n, int64_t rows_per_cta, const uint16_t *__restrict__ pattern,
+// Largest number of nonzeros that one CTA's rows put into one row of S.  CTA
+// g owns the chunks g, g + G, g + 2G, ... of `chunk` rows (one chunk per CTA
+// for the contiguous partition).
+__global__ void k_bin_max(SparseSign sp, int64_t n, int64_t chunk, const uint16_t *__restrict__ pattern,
                           int *binmax) {
     extern __shared__ int cnt[];
     for (int i = threadIdx.x; i < sp.s; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
-    const int64_t r1 = min(n, r0 + rows_per_cta);
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
-        for (int q = 0; q < sp.zeta; ++q) {
-            int row;
-            bool neg;
-            pattern_entry(sp, pattern[r * sp.zeta + q], q, row, neg);
-            atomicAdd(cnt + row, 1);
-        }
+    for (int64_t r0 = (int64_t)blockIdx.x * chunk; r0 < n; r0 += (int64_t)gridDim.x * chunk) {
+        const int64_t r1 = min(n, r0 + chunk);
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+            for (int q = 0; q < sp.zeta; ++q) {
+                int row;
+                bool neg;
+                pattern_entry(sp, pattern[r * sp.zeta + q], q, row, neg);
+                atomicAdd(cnt + row, 1);
+            }
+    }
     __syncthreads();
     int mx = 0;
     for (int i = threadIdx.x; i < sp.s; i += blockDim.x) mx = max(mx, cnt[i]);
@@ -166,27 +176,32 @@ skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st) {
         S->pattern = nullptr;
         return fail(SKF_ERR_OOM, "sketch pattern allocation");
     }
-    e = cudaMalloc(&S->binmax, sizeof(int));
+    e = cudaMalloc(&S->binmax, 2 * sizeof(int));
     if (e != cudaSuccess) {
         cudaGetLastError();
         S->binmax = nullptr;
         return fail(SKF_ERR_OOM, "sketch table allocation");
     }
+    S->binmax_chunk = S->binmax + 1;
     int G;
     int64_t rows;
     row_partition(S->n, &G, &rows);
     const int blocks = (int)std::min<int64_t>((S->n + 255) / 256, 16ll * num_sms());
     k_build_pattern<<<blocks, 256, 0, st>>>(sp, S->n, S->pattern);
-    cudaMemsetAsync(S->binmax, 0, sizeof(int), st);
+    cudaMemsetAsync(S->binmax, 0, 2 * sizeof(int), st);
     const size_t smem = sizeof(int) * S->s;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_bin_max, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_bin_max<<<G, 256, smem, st>>>(sp, S->n, rows, S->pattern, S->binmax);
-    count_launches(2);
+    int Gc;
+    chunk_partition(S->n, &Gc);
+    k_bin_max<<<Gc, 256, smem, st>>>(sp, S->n, kChunkRows, S->pattern, S->binmax_chunk);
+    count_launches(3);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "sketch table build");
-    int hmax = 0;
-    cudaMemcpy(&hmax, S->binmax, sizeof(int), cudaMemcpyDeviceToHost);
-    if (limb_bits(hmax) < 13) return fail(SKF_ERR_NOT_SUPPORTED, "sketch too dense for the fixed-point accumulators");
+    int hmax[2] = {0, 0};
+    cudaMemcpy(hmax, S->binmax, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+    if (limb_bits(hmax[0]) < 13 || limb_bits(hmax[1]) < 13)
+        return fail(SKF_ERR_NOT_SUPPORTED, "sketch too dense for the fixed-point accumulators");
     return SKF_OK;
 }
 

@@ -17,6 +17,8 @@
 #include <utility>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "skf_internal.cuh"
 
 namespace skf {
@@ -527,6 +529,42 @@ __global__ void __launch_bounds__(kThreads) k_recombine(const double *__restrict
     }
 }
 
+// f = V_m z for an FP32 or BF16 basis.  Each product v z_j is formed exactly
+// as a float pair (z_j = zh + zl, Dekker product through fmaf) and summed in
+// double-float arithmetic (Knuth's TwoSum), so the sum keeps about 44 bits
+// while running on the FP32 pipes; the pair is added in FP64 once per row.
+__device__ __forceinline__ float load_basis(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float load_basis(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+
+template <typename TB>
+__global__ void __launch_bounds__(kThreads) k_recombine_lp(const TB *__restrict__ V, int64_t ldv, int64_t n,
+                                                           const double *__restrict__ z, const int *iscal,
+                                                           double *__restrict__ x) {
+    extern __shared__ float zs[];   // [2 me]: hi and lo parts of z
+    const int me = iscal[1];
+    for (int j = threadIdx.x; j < me; j += blockDim.x) {
+        const float hi = (float)z[j];
+        zs[2 * j] = hi;
+        zs[2 * j + 1] = (float)(z[j] - (double)hi);
+    }
+    __syncthreads();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        float sh = 0.f, sl = 0.f;
+        for (int j = 0; j < me; ++j) {
+            const float v = load_basis(V + r + (int64_t)j * ldv);
+            const float zh = zs[2 * j], zl = zs[2 * j + 1];
+            const float ph = v * zh;
+            const float pe = fmaf(v, zl, fmaf(v, zh, -ph));
+            const float t = sh + ph;
+            const float bp = t - sh;
+            const float err = (sh - (t - bp)) + (ph - bp);
+            sh = t;
+            sl += err + pe;
+        }
+        x[r] = (double)sh + (double)sl;
+    }
+}
+
 __global__ void k_write_info(TailCtx c, skf_info *info) {
     if (threadIdx.x != 0 || info == nullptr) return;
     info->status = c.iscal[2];
@@ -542,9 +580,9 @@ __global__ void k_write_info(TailCtx c, skf_info *info) {
 // schedule; levels are evaluated in batches (speculatively, several levels per
 // launch) and accepted in schedule order, which gives the same accepted order
 // as evaluating one level at a time.
-skf_status tail_run(skf_method method, int s, int m, int64_t n, const double *V, int64_t ldv, const double *vscale,
-                    const double *SV, const double *SAV, int *iscal, const RuleDev &rule, double tol, double *x,
-                    skf_info *info, cudaStream_t st) {
+skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
+                    const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
+                    double tol, double *x, skf_info *info, cudaStream_t st) {
     TailCtx c{};
     c.s = s;
     c.m = m;
@@ -639,7 +677,15 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const double *V,
     if (qsm > 48 * 1024) cudaFuncSetAttribute(k_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
     k_coeffs<<<1, kThreads, qsm, st>>>(c);
     const int64_t rb = std::min<int64_t>((n + kThreads - 1) / kThreads, 16 * num_sms());
-    k_recombine<<<(unsigned)std::max<int64_t>(rb, 1), kThreads, 0, st>>>(V, ldv, n, c.z, iscal, x);
+    const unsigned rgrid = (unsigned)std::max<int64_t>(rb, 1);
+    const size_t zsm = sizeof(float) * 2 * (size_t)m;
+    if (vdt == SKF_F64) {
+        k_recombine<<<rgrid, kThreads, 0, st>>>((const double *)V, ldv, n, c.z, iscal, x);
+    } else if (vdt == SKF_F32) {
+        k_recombine_lp<float><<<rgrid, kThreads, zsm, st>>>((const float *)V, ldv, n, c.z, iscal, x);
+    } else {
+        k_recombine_lp<__nv_bfloat16><<<rgrid, kThreads, zsm, st>>>((const __nv_bfloat16 *)V, ldv, n, c.z, iscal, x);
+    }
     k_write_info<<<1, 32, 0, st>>>(c, info);
     nlaunch += 3;
     count_launches(nlaunch);

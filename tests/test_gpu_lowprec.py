@@ -1,0 +1,210 @@
+"""Reduced-precision path: FP32 matrix values, basis stored in FP32 or BF16,
+FP32 SpMV and orthogonalisation, FP64 sketches and tail (Algorithms 1 and 2).
+
+Two kinds of checks:
+* consistency of what the path returns with its own stored basis, against
+  the oracle's sketch.  S V_m is an exact fixed-point sketch of the stored
+  vectors (40 or more fraction bits below each column's maximum).  S A V_m
+  comes from the Arnoldi relation and the FP32 SpMV, so column j deviates from
+  S A v_j by the FP32 rounding of one SpMV row sum and one update: at most
+  about (w + k + 2) u_32 times the cancellation ratio || |A||v_j| || / ||A v_j||
+  (w = widest row, u_32 = 2^-24), checked per column with a factor 4;
+* the approximants against the FP64 oracle (O2, same S, m, k and rule): the
+  error there is the propagated FP32 / BF16 rounding of the basis.  The FP32
+  bound is the 1e-6 target of the workload; the BF16 bound is the observed
+  floor (about 4e-3, one BF16 unit roundoff) with a margin.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sketched as osk
+from oracle.sketch import Sketch as OSketch
+from workloads import convdiff_2d, convdiff_3d, csr_to_scipy, gaussian_rhs
+from workloads.configs import laplacian_lambda_min, quad_scale
+from workloads.operators import powerlaw_graph_operator
+from gpu_helpers import rel
+
+pytestmark = pytest.mark.gpu
+
+BASIS = {"f32": torch.float32, "bf16": torch.bfloat16}
+
+
+def upload32(skf, A):
+    return skf.upload_csr(A.rowptr, A.colind, A.values, device="cuda", dtype=torch.float32)
+
+
+def arnoldi_lp(skf, A, b, m, k, s, basis, zeta=8, seed=13, identity=False):
+    op = upload32(skf, A)
+    S = skf.Sketch(skf.IDENTITY if identity else skf.SPARSE_SIGN, A.n, s, zeta, seed)
+    info = skf.new_info()
+    V, vs, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, torch.as_tensor(b, device="cuda"), m, k,
+                                          basis_dtype=BASIS[basis], info=info)
+    torch.cuda.synchronize()
+    Vn = (V.double() * vs[:, None]).cpu().numpy().T      # stored basis, columns v_j = sigma_j w_j
+    return Vn, SV.cpu().numpy().T, SAV.cpu().numpy().T, H.cpu().numpy().T, skf.read_info(info)
+
+
+def a32(A):
+    """The operator with its values rounded to FP32 (what the path multiplies by)."""
+    M = csr_to_scipy(A).astype(np.float32).astype(np.float64)
+    return M
+
+
+U32 = 2.0 ** -24
+
+
+def check_sketches(A, V, SV, SAV, k, s, me):
+    S = OSketch("sparse_sign", A.n, s, 8, 13)
+    V = V[:, :me]
+    assert rel(SV[:, :me], S @ V) < 1e-9
+    M = a32(A)
+    AV = M @ V
+    absAV = abs(M) @ np.abs(V)
+    width = int(np.diff(A.rowptr).max())
+    SAVo = S @ AV
+    for j in range(me):
+        err = np.linalg.norm(SAV[:, j] - SAVo[:, j]) / np.linalg.norm(SAVo[:, j])
+        bound = 4 * (width + k + 2) * U32 * np.linalg.norm(absAV[:, j]) / np.linalg.norm(AV[:, j])
+        assert err <= bound, (j, err, bound)
+
+
+@pytest.mark.parametrize("basis", ["f32", "bf16"])
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_sketches_are_those_of_the_stored_basis(skf, basis, k):
+    A = convdiff_2d(97, (100.0, 50.0))          # N = 9409: ragged last chunk and slice
+    b = gaussian_rhs(A.n, 12)
+    m, s = 30, 120
+    V, SV, SAV, H, info = arnoldi_lp(skf, A, b, m, k, s, basis)
+    assert info["status"] == 0 and info["m_eff"] == m
+    check_sketches(A, V, SV, SAV, k, s, m)
+    # local orthogonality and unit norms of the stored basis, to FP32 accuracy
+    G = V.T @ V
+    tol = 1e-5 if basis == "f32" else 2e-2
+    assert np.abs(np.diag(G) - 1.0).max() < tol
+    for j in range(m):
+        for i in range(max(0, j - k + 1), j):
+            assert abs(G[i, j]) < tol, (i, j, G[i, j])
+
+
+def test_sketches_wide_rows_graph_operator(skf):
+    """Rows wider than eight entries (several passes of the SpMV row loop)."""
+    A = powerlaw_graph_operator(6000, seed=11)
+    widths = np.diff(A.rowptr)
+    assert widths.max() > 16
+    b = gaussian_rhs(A.n, 12)
+    m, s = 20, 80
+    for basis in ("f32", "bf16"):
+        V, SV, SAV, H, info = arnoldi_lp(skf, A, b, m, 3, s, basis)
+        assert info["status"] == 0 and info["m_eff"] == m
+        check_sketches(A, V, SV, SAV, 3, s, m)
+
+
+@pytest.mark.parametrize("m", [1, 2, 5])
+def test_short_bases(skf, m):
+    """m = 1 (the only column is the last: S y_0 scattered directly) and short
+    bases where the relation and the direct column meet."""
+    A = convdiff_2d(40)
+    b = gaussian_rhs(A.n, 12)
+    V, SV, SAV, H, info = arnoldi_lp(skf, A, b, m, 2, 4 * m + 8, "f32")
+    assert info["m_eff"] == m
+    check_sketches(A, V, SV, SAV, 2, 4 * m + 8, m)
+
+
+@pytest.mark.parametrize("basis", ["f32", "bf16"])
+def test_identity_sketch(skf, basis):
+    A = convdiff_2d(20)
+    b = gaussian_rhs(A.n, 3)
+    V, SV, SAV, H, info = arnoldi_lp(skf, A, b, 12, 2, A.n, basis, identity=True)
+    assert info["m_eff"] == 12
+    assert rel(SV, V) < 1e-15
+    assert rel(SAV, a32(A) @ V) < 2e-6
+
+
+def solve_lp(skf, A, b, func, m, k, s, c, method, basis, tol=1e-12):
+    op = upload32(skf, A)
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, s, 8, 13)
+    f = skf.make_func(func, c)
+    p = skf.make_params(m, k, basis_dtype=BASIS[basis], tol=tol)
+    info = skf.new_info()
+    x = skf.solve(method, op.csr, S, torch.as_tensor(b, device="cuda"), f, p, info=info)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), skf.read_info(info)
+
+
+# FP32: the 1e-6 target of the reduced-precision workload; BF16: the floor of
+# about one BF16 unit roundoff (3.9e-3) with a margin
+BOUND = {"f32": 1e-6, "bf16": 3e-2}
+
+
+@pytest.mark.parametrize("basis", ["f32", "bf16"])
+@pytest.mark.parametrize("method", ["sgmres", "sfom"])
+def test_config1_against_fp64_oracle(skf, basis, method):
+    """2D convection-diffusion N = 1e4, m = 40, k = 2, s = 160, z^{-1/2}."""
+    A = convdiff_2d(100, (100.0, 50.0))
+    b = gaussian_rhs(A.n, 12)
+    c = quad_scale("invsqrt", laplacian_lambda_min(100, 2), float(abs(csr_to_scipy(A)).sum(1).max()))
+    m, k, s = 40, 2, 160
+    x, info = solve_lp(skf, A, b, "invsqrt", m, k, s, c, skf.SGMRES if method == "sgmres" else skf.SFOM, basis)
+    xo, _ = osk.solve(csr_to_scipy(A), b, "invsqrt", m, k, OSketch("sparse_sign", A.n, s, 8, 13), c,
+                      method="sgmres" if method == "sgmres" else "sfom_quad", tol=1e-12)
+    assert info["status"] == 0 and info["m_eff"] == m
+    err = rel(x, xo)
+    print(f"{basis} {method}: rel err vs FP64 oracle {err:.3e}")
+    assert err <= BOUND[basis]
+
+
+@pytest.mark.parametrize("basis", ["f32", "bf16"])
+def test_3d_log1p_against_fp64_oracle(skf, basis):
+    A = convdiff_3d(24, (50.0, 50.0, 50.0))     # N = 13824
+    b = gaussian_rhs(A.n, 12)
+    c = quad_scale("log1p_over_z", 0.0, float(abs(csr_to_scipy(A)).sum(1).max()))
+    m, k, s = 50, 2, 200
+    x, info = solve_lp(skf, A, b, "log1p_over_z", m, k, s, c, skf.SGMRES, basis)
+    xo, _ = osk.solve(csr_to_scipy(A), b, "log1p_over_z", m, k, OSketch("sparse_sign", A.n, s, 8, 13), c,
+                      method="sgmres", tol=1e-12)
+    assert info["status"] == 0
+    err = rel(x, xo)
+    print(f"{basis} 3d log1p sgmres: rel err vs FP64 oracle {err:.3e}")
+    assert err <= BOUND[basis]
+
+
+@pytest.mark.parametrize("basis", ["f32", "bf16"])
+def test_zero_rhs(skf, basis):
+    A = convdiff_2d(16)
+    op = upload32(skf, A)
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, 64, 8, 13)
+    f = skf.make_func("invsqrt", 1.0)
+    p = skf.make_params(8, 2, basis_dtype=BASIS[basis])
+    info = skf.new_info()
+    x = skf.solve(skf.SGMRES, op.csr, S, torch.zeros(A.n, dtype=torch.float64, device="cuda"), f, p, info=info)
+    torch.cuda.synchronize()
+    st = skf.read_info(info)
+    assert st["status_name"] == "SKF_ERR_ZERO_RHS"
+    assert float(x.abs().max()) == 0.0
+
+
+def test_invariant_subspace_breakdown_fp32(skf):
+    """A = diag with 5 distinct values: the Krylov space is invariant after 5
+    steps, which the FP32 test (||w|| <= 2^-17 ||A v||) detects."""
+    from workloads.operators import CSR
+    N = 640
+    d = np.repeat(np.array([1.0, 2.0, 3.0, 5.0, 8.0]), N // 5)
+    A = CSR(N, np.arange(N + 1, dtype=np.int64), np.arange(N, dtype=np.int32), d)
+    b = gaussian_rhs(N, 12)
+    V, SV, SAV, H, info = arnoldi_lp(skf, A, b, 12, 12, 64, "f32")
+    assert info["breakdown"] == 1 and info["m_eff"] == 5
+    # the columns before the breakdown, including S A v_4 from the relation
+    check_sketches(A, V, SV, SAV, 12, 64, 5)
+
+
+def test_mixed_dtypes_rejected(skf):
+    A = convdiff_2d(16)
+    op64 = skf.upload_csr(A.rowptr, A.colind, A.values, device="cuda")
+    op32 = upload32(skf, A)
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, 64, 8, 13)
+    b = torch.as_tensor(gaussian_rhs(A.n, 12), device="cuda")
+    with pytest.raises(skf.SkfError):
+        skf.arnoldi_trunc(op64.csr, S, b, 8, 2, basis_dtype=torch.float32)
+    with pytest.raises(skf.SkfError):
+        skf.arnoldi_trunc(op32.csr, S, b, 8, 2, basis_dtype=torch.float64)
