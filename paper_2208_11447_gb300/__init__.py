@@ -200,18 +200,21 @@ def read_info(buf: torch.Tensor) -> dict:
 
 
 def arnoldi_trunc(A: Csr, S: Sketch, b: torch.Tensor, m: int, k: int, basis_dtype=torch.float64, info=None,
-                  stream=None):
-    """Returns V (m x N, row j = stored column w_j), vscale (m), SV, SAV (m x s,
-    row j = column j), H ((m) x (m+1): row j = column j of the (m+1) x m H)."""
+                  stream=None, ldv: int | None = None):
+    """Returns V (m x N, row j = stored column w_j; a view of an m x ldv buffer
+    when ldv is given), vscale (m), SV, SAV (m x s, row j = column j), H
+    ((m) x (m+1): row j = column j of the (m+1) x m H)."""
     N = A.n
     dev = b.device
-    V = torch.empty((m, N), dtype=basis_dtype, device=dev)
+    ldv = N if ldv is None else ldv
+    assert ldv >= N
+    V = torch.empty((m, ldv), dtype=basis_dtype, device=dev)[:, :N]
     vscale = torch.empty(m, dtype=torch.float64, device=dev)
     SV = torch.empty((m, S.s), dtype=torch.float64, device=dev)
     SAV = torch.empty((m, S.s), dtype=torch.float64, device=dev)
     H = torch.empty((m, m + 1), dtype=torch.float64, device=dev)
     _check(lib().skf_arnoldi_trunc(A.handle, S.handle, _ptr(b), _DTYPE[b.dtype], m, k, _DTYPE[basis_dtype],
-                                   _ptr(V), N, _ptr(vscale), _ptr(SV), _ptr(SAV), _ptr(H), _ptr(info),
+                                   _ptr(V), ldv, _ptr(vscale), _ptr(SV), _ptr(SAV), _ptr(H), _ptr(info),
                                    _stream(stream)))
     return V, vscale, SV, SAV, H
 

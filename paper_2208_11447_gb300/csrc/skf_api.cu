@@ -371,6 +371,10 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
         hoff[t + 1] = hoff[t] + 32ll * hw[t];
         A->max_width = std::max(A->max_width, hw[t]);
     }
+    for (int64_t t0 = 0; t0 < A->nslices; t0 += kChunkRows / 32) {
+        const int64_t t1 = std::min<int64_t>(A->nslices, t0 + kChunkRows / 32);
+        A->max_chunk_entries = std::max<int64_t>(A->max_chunk_entries, hoff[t1] - hoff[t0]);
+    }
     const int64_t padded = hoff[A->nslices];
     if (cudaMalloc(&A->sell_val, esz * std::max<int64_t>(padded, 1)) != cudaSuccess ||
         cudaMalloc(&A->sell_col, sizeof(int32_t) * std::max<int64_t>(padded, 1)) != cudaSuccess) {
@@ -450,6 +454,7 @@ skf_status skf_sketch_destroy(skf_sketch *S) {
     if (S->P) cudaFree(S->P);
     if (S->pattern) cudaFree(S->pattern);
     if (S->binmax) cudaFree(S->binmax);
+    if (S->pattern8) cudaFree(S->pattern8);
     delete S;
     return SKF_OK;
 }
@@ -547,7 +552,8 @@ skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, c
     const int s = S->s;
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const skf_dtype bt = p->basis_dtype;
-    const size_t szV = dtype_size(bt) * (size_t)n * m;
+    const int64_t ldv = (n + 63) / 64 * 64;   // 256-byte aligned columns
+    const size_t szV = dtype_size(bt) * (size_t)ldv * m;
     const size_t szS = sizeof(double) * (size_t)s * m;
     const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
     const size_t total = al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4);
@@ -561,9 +567,9 @@ skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, c
     double *H = (double *)(ws + off); off += al(szH);
     double *vscale = (double *)(ws + off); off += al(sizeof(double) * m);
     int *iscal = (int *)(ws + off);
-    st = run_arnoldi(A, S, (const double *)b, m, p->k, bt, V, n, vscale, SV, SAV, H, iscal, info, cs);
+    st = run_arnoldi(A, S, (const double *)b, m, p->k, bt, V, ldv, vscale, SV, SAV, H, iscal, info, cs);
     if (st == SKF_OK)
-        st = tail_run(method, s, m, n, V, bt, n, vscale, SV, SAV, iscal, *rule, p->tol, (double *)x, info, cs);
+        st = tail_run(method, s, m, n, V, bt, ldv, vscale, SV, SAV, iscal, *rule, p->tol, (double *)x, info, cs);
     dfree(ws, cs);
     return st;
 }

@@ -8,15 +8,23 @@
 // computed from the stored (rounded) vectors, so that SV = S V_m and
 // SAV = S A V_m hold for the basis the caller receives.
 //
+// Rows are dealt out in chunks of kChunkRows, chunk c to CTA c mod G (G = SMs,
+// one 1024-thread CTA per SM), in every kernel: all CTAs sweep the rows
+// together, so the stencil gathers of the SpMV stay within a few MB of L2, and
+// every kernel's fixed-point sketch partials share one bin-load bound.
+//
 // Two kernels per step:
-//   spmv   (step j): y_j = A w_j in FP32 on chunk-interleaved rows -> Y;
-//                    partial <w_i, y_j> for the window, max|y_j|; exact
-//                    fixed-point sketch of the stored w_j (two limbs; its
-//                    maximum is known from the previous step).
-//   update (step j): S w_j from the integer partials; MGS coefficients from
-//                    the dots and the window Gram matrix; w_{j+1} =
-//                    sigma_j y_j - sum_i h_ij sigma_i w_i in FP32, rounded and
-//                    stored; ||w_{j+1}||^2, Gram entries, max|w_{j+1}|.
+//   spmv   (step j): S w_{j-1} and S A v_{j-2} from the previous partials
+//                    (prologue); y_j = A w_j -> Y; partial <w_i, y_j> for the
+//                    window and max|y_j|.  For slices at most 8 wide the loads
+//                    are software-pipelined across chunks.
+//   update (step j): MGS coefficients from the dots and the window Gram
+//                    matrix; w_{j+1} = sigma_j y_j - sum_i h_ij sigma_i w_i in
+//                    FP32, rounded and stored; ||w_{j+1}||^2, Gram entries,
+//                    max|w_{j+1}|; exact two-limb fixed-point sketch of the
+//                    stored w_j (its maximum is known), in per-lane copies of
+//                    the shared-memory bins so that a warp's atomics do not
+//                    collide.
 // S y_j is not scattered: the update step is the Arnoldi relation
 //   sigma_j y_j = w_{j+1} + sum_i h_ij sigma_i w_i     (FP32 coefficients),
 // so S y_j follows from the sketches of stored vectors once S w_{j+1} is
@@ -44,7 +52,7 @@ namespace {   // internal linkage: each instantiating translation unit has its o
 constexpr int kP1 = kMaxK + 1;             // slots of one spmv partial: d[kMaxK], ymax
 constexpr int kP2 = kMaxK + 2;             // slots of one update partial: ||w||^2, max|w|, g[kMaxK]
 constexpr int kSpmvThreads = kChunkRows;   // one row per thread and chunk; one CTA per SM
-constexpr int kUpdThreads = 512;
+constexpr int kUpdThreads = kChunkRows;    // one row per thread and chunk; one CTA per SM
 constexpr int kCoef = kMaxK + 1;           // per step: sigma_j, then h_ij sigma_i of the window (FP32 values)
 // Happy breakdown in FP32 arithmetic: ||w_{j+1}|| <= 2^-17 ||A v_j|| (64 FP32
 // unit roundoffs; below that w_{j+1} is rounding noise).
@@ -94,16 +102,17 @@ struct LpCtx {
     const int32_t *sell_col;
     double norm_inf;           // ||A||_inf
     SparseSign sp;
-    const uint16_t *pattern;
-    const int *binmax;         // bin-load maximum of the update kernel's row partition
-    const int *binmax_chunk;   // bin-load maximum of the SpMV kernel's chunk partition
+    const uint16_t *pattern;   // 16-bit sparse-sign pattern
+    const uint8_t *pattern8;   // compact pattern (zeta <= 8, stripes <= 128 rows) or nullptr
+    const int *binmax_chunk;   // bin-load maximum of the chunk partition
     int identity;              // S = I
+    int split;                 // update bins laid out [stripe][sign][128] (compact pattern, zeta = 8)
     int m, k;
     void *V;                   // TB [m][ldv]
     int64_t ldv;
     double *vscale, *SV, *SAV, *H;
     float *Y;                  // [n] y_j = A w_j
-    double *p1;                // [Gs][kP1]
+    double *p1;                // [G][kP1]
     double *p2;                // [G][kP2]
     double *fin_d;             // [m][kP1] reduced dots of step j, max|y_j|
     double *fin_w;             // [m+1][2] ||w_j||^2, max|w_j|
@@ -111,40 +120,73 @@ struct LpCtx {
     double *gram;              // [m+1][kMaxK] <w_j, w_{j-d}>
     double *coef;              // [m][kCoef] the FP32 coefficients update j applied
     double *skw;               // [m][s] S w_j in units of the +-1 pattern
-    long long *skWp;           // [Gs][s] fixed-point partials of S w_j
-    long long *skYp;           // [Gs][s] fixed-point partials of S y_{m-1}
-    long long *skDp;           // [G][s]  fixed-point partials of the BF16 residual of w_{j+1}
+    double *sd;                // [s] S (residual of w_j), BF16 storage only
+    long long *skWp;           // [2][G][s] fixed-point partials of S w_j, by parity of j
+    long long *skYp;           // [G][s] fixed-point partials of S y_{m-1}
+    long long *skDp;           // [G][s] fixed-point partials of the BF16 residual of w_{j+1}
     int *ex;                   // exponents: [0, m) S w_j, [m, 2m) residual of w_j, [2m] S y_{m-1}
     double *epscol;            // [m]
     double inv_sqrt_zeta;
     unsigned *cnt;             // [2] arrival tickets
     int *iscal;                // [0] stopped, [1] m_eff, [2] status, [3] step that stopped
-    int64_t rows_per_cta;      // contiguous partition of the init and update kernels
-    int G_upd, G_spmv;
+    int G;                     // CTAs of every kernel (chunk partition)
+    int lc;                    // log2 of the per-lane bin copies of the update kernel
 };
 
+// (row of S, sign) of the zeta nonzeros of column r, from the compact or the
+// 16-bit pattern table.
+template <int ZCAP>
+__device__ __forceinline__ void pattern_row(const LpCtx &c, int64_t r, int (&row)[ZCAP], bool (&neg)[ZCAP]) {
+    if (ZCAP == 8 && c.pattern8 != nullptr) {
+        const uint2 v = __ldg((const uint2 *)(c.pattern8 + r * 8));
+#pragma unroll
+        for (int q = 0; q < ZCAP; ++q) {
+            const unsigned e = ((q < 4 ? v.x : v.y) >> (8 * (q & 3))) & 0xFFu;
+            row[q] = c.sp.start[q] + (int)(e & 0x7Fu);
+            neg[q] = (e & 0x80u) != 0u;
+        }
+    } else {
+        uint16_t e[ZCAP];
+        load_pattern<ZCAP>(c.pattern, c.sp.zeta, r, e);
+#pragma unroll
+        for (int q = 0; q < ZCAP; ++q) pattern_entry(c.sp, e[q], q, row[q], neg[q]);
+    }
+}
+
+// Chunk-partition row of thread `threadIdx.x` (< kChunkRows) in the i-th
+// chunk of this CTA, or -1; and the number of chunks of this CTA.
+__device__ __forceinline__ int64_t chunk_row(const LpCtx &c, int64_t i) {
+    const int64_t r = ((int64_t)blockIdx.x + i * c.G) * kChunkRows + threadIdx.x;
+    return r < c.n ? r : -1;
+}
+__device__ __forceinline__ int64_t chunks_of_cta(const LpCtx &c) {
+    const int64_t nch = (c.n + kChunkRows - 1) / kChunkRows;
+    return blockIdx.x < nch ? (nch - blockIdx.x + c.G - 1) / c.G : 0;
+}
+
 template <typename TB>
-__global__ void __launch_bounds__(kThreads) k_arnoldi_init_lp(LpCtx c, const double *__restrict__ b) {
+__global__ void __launch_bounds__(kChunkRows) k_arnoldi_init_lp(LpCtx c, const double *__restrict__ b) {
     __shared__ double red[64];
     TB *V = (TB *)c.V;
-    const int64_t r0 = (int64_t)blockIdx.x * c.rows_per_cta;
-    const int64_t r1 = min(c.n, r0 + c.rows_per_cta);
     double nrm[1] = {0.0};
     double mx = 0.0;
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += kThreads) {
+    const int64_t nc = chunks_of_cta(c);
+    for (int64_t i = 0; i < nc; ++i) {
+        const int64_t r = chunk_row(c, i);
+        if (r < 0) continue;
         const float x = Store<TB>::rnd((float)b[r]);   // b rounded to FP32, then to the storage type
         Store<TB>::st(V + r, x);
         nrm[0] = fma((double)x, (double)x, nrm[0]);
         mx = fmax(mx, fabs((double)x));
     }
-    block_sum<1>(nrm, red);
-    mx = block_max(mx, red);
+    block_sum<1, kChunkRows>(nrm, red);
+    mx = block_max<kChunkRows>(mx, red);
     if (threadIdx.x == 0) {
         c.p2[(size_t)blockIdx.x * kP2 + 0] = nrm[0];
         c.p2[(size_t)blockIdx.x * kP2 + 1] = mx;
     }
     if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < (c.m + 1) * c.m; i += kThreads) c.H[i] = 0.0;
+        for (int i = threadIdx.x; i < (c.m + 1) * c.m; i += kChunkRows) c.H[i] = 0.0;
         if (threadIdx.x == 0) {
             c.iscal[0] = 0;
             c.iscal[1] = c.m;
@@ -170,117 +212,203 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_init_lp(LpCtx c, const dou
     }
 }
 
-// Finalise S w_j for this CTA's slice of the rows of S (SV[:, j]); then, for
-// j >= 1, S y_{j-1} from the Arnoldi relation (SAV[:, j-1]); at the last step
-// also the directly scattered S y_{m-1} (SAV[:, m-1]).  Sketch values are in
-// units of the +-1 pattern; SV and SAV carry the 1/sqrt(zeta) scale.
+// S w_jw from the partials of the update kernel (or of a stopping SpMV) for
+// this CTA's slice of the rows of S; with `store`, skw and SV[:, jw].  Then,
+// for jw >= 1, S y_{jw-1} from the Arnoldi relation of update jw - 1:
+//   sigma_{jw-1} y_{jw-1} = (w_jw - residual_jw) + sum_i cf_i w_i,
+// SAV[:, jw-1] = sigma_{jw-1} S y_{jw-1} / sqrt(zeta).  With `next_resid`
+// (BF16 storage, called from SpMV jw + 1), sd <- S residual_{jw+1} afterwards.
+// With `ylast`, SAV[:, jw] from the directly scattered S y_jw.
 template <typename TB>
-__device__ __forceinline__ void finalize_sketches(const LpCtx &c, int j, bool last) {
+__device__ __forceinline__ void finalize_column(const LpCtx &c, int jw, bool store, bool next_resid, bool ylast) {
     const int s = c.sp.s;
     const int G = gridDim.x;
     const int L = limb_bits(*c.binmax_chunk);
     const int P = sketch_fraction_bits_from_limb(L);
-    const int Ld = Store<TB>::kExact ? 0 : limb_bits(*c.binmax);
-    const int ew = c.ex[j];
-    const int ed = j >= 1 ? c.ex[c.m + j] : kNoExp;
+    const int ew = c.ex[jw];
     const int ey = c.ex[2 * c.m];
-    const double sig_j = c.stepsc[4 * (size_t)j];
-    const int jm = j - 1;
+    const int edn = next_resid ? c.ex[c.m + jw + 1] : kNoExp;
+    const double sig = c.stepsc[4 * (size_t)jw];
+    const int jm = jw - 1;
     const int i0 = max(0, jm - c.k + 1);
     const int nw = jm - i0 + 1;
     const double *cf = c.coef + (size_t)max(jm, 0) * kCoef;
-    const double sig_jm = j >= 1 ? c.stepsc[4 * (size_t)jm] : 0.0;
+    const double sig_m = jw >= 1 ? c.stepsc[4 * (size_t)jm] : 0.0;
+    const long long *wp = c.skWp + (size_t)(jw & 1) * c.G * s;
     const int per = (s + G - 1) / G;
     const int b0 = blockIdx.x * per, b1 = min(s, b0 + per);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = b0 + warp; i < b1; i += blockDim.x / 32) {
         double sw = 0.0;
-        if (ew != kNoExp) sw = ldexp(warp_sum_i64_exact(c.skWp + i, c.G_spmv, (size_t)s), ew - P);
-        double sd = 0.0;
-        if (!Store<TB>::kExact && ed != kNoExp) sd = ldexp(warp_sum_i64_exact(c.skDp + i, c.G_upd, (size_t)s), ed - Ld);
+        if (ew != kNoExp) sw = ldexp(warp_sum_i64_exact(wp + i, c.G, (size_t)s), ew - P);
         double sy = 0.0;
-        if (last && ey != kNoExp) sy = ldexp(warp_sum_i64_exact(c.skYp + i, c.G_spmv, (size_t)s), ey - P);
+        if (ylast && ey != kNoExp) sy = ldexp(warp_sum_i64_exact(c.skYp + i, c.G, (size_t)s), ey - P);
+        double sdn = 0.0;
+        if (next_resid && edn != kNoExp) sdn = ldexp(warp_sum_i64_exact(c.skDp + i, c.G, (size_t)s), edn - L);
         if (lane == 0) {
-            c.skw[(size_t)j * s + i] = sw;
-            c.SV[i + (size_t)j * s] = sig_j * sw * c.inv_sqrt_zeta;
-            if (j >= 1) {
-                // sigma_{j-1} y_{j-1} = (w_j - residual) + sum_i h_i,j-1 sigma_i w_i, FP32 coefficients cf
-                double u = sw - sd;
-                for (int a = 0; a < nw; ++a) u += cf[1 + a] * c.skw[(size_t)(i0 + a) * s + i];
-                c.SAV[i + (size_t)jm * s] = (u / cf[0]) * sig_jm * c.inv_sqrt_zeta;
+            if (store) {
+                c.skw[(size_t)jw * s + i] = sw;
+                c.SV[i + (size_t)jw * s] = sig * sw * c.inv_sqrt_zeta;
             }
-            if (last) c.SAV[i + (size_t)j * s] = sig_j * sy * c.inv_sqrt_zeta;
+            if (jw >= 1) {
+                double u = sw - (Store<TB>::kExact ? 0.0 : c.sd[i]);
+                for (int a = 0; a < nw; ++a) u += cf[1 + a] * c.skw[(size_t)(i0 + a) * s + i];
+                c.SAV[i + (size_t)jm * s] = (u / cf[0]) * sig_m * c.inv_sqrt_zeta;
+            }
+            if (next_resid) c.sd[i] = sdn;
+            if (ylast) c.SAV[i + (size_t)jw * s] = sig * sy * c.inv_sqrt_zeta;
         }
     }
 }
 
-template <int KW, int ZCAP, typename TB>
-__global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, int j) {
-    extern __shared__ int bins[];   // [4 s]: two limbs of S w_j, then two limbs of S y_{m-1} (last step)
-    __shared__ double red[BlockSumTraits<KW, kSpmvThreads>::kSmem];
-    // stopped at an earlier step
-    if (c.iscal[0] && c.iscal[3] < j) return;
-    const int s = c.sp.s;
-    const TB *V = (const TB *)c.V;
+// Fixed-point sketch of one value into two-limb bins [2][s], signs selected.
+template <int ZCAP>
+__device__ __forceinline__ void scatter2(const LpCtx &c, int64_t r, long long v, int L, int *a0, int *a1) {
+    int row[ZCAP];
+    bool neg[ZCAP];
+    pattern_row<ZCAP>(c, r, row, neg);
+    const int l0 = (int)(v & ((1ll << L) - 1)), l1 = (int)(v >> L);
+#pragma unroll
+    for (int q = 0; q < ZCAP; ++q)
+        if (q < c.sp.zeta) red_limbs(a0, a1, row[q], l0, l1, neg[q]);
+}
+
+// Common start of the SpMV kernels: stop test, H subdiagonal, finalisation of
+// the previous column's sketches.  Returns false when nothing more is to be
+// done by this launch (stopped earlier, zero right-hand side, or S = I at a
+// stop); `stopping` = m_eff is j.
+template <typename TB>
+__device__ __forceinline__ bool spmv_begin(const LpCtx &c, int j, bool &stopping) {
+    if (c.iscal[0] && c.iscal[3] < j) return false;   // stopped at an earlier step
     const double *sc_j = c.stepsc + 4 * (size_t)j;
     if (j >= 1 && blockIdx.x == 0 && threadIdx.x == 0) c.H[j + (size_t)(j - 1) * (c.m + 1)] = sc_j[1];
     // zero right-hand side (j = 0) or happy breakdown, decided by the previous
     // launch: m_eff = j.  S w_j is still formed (S y_{j-1} needs it).
-    const bool stopping = sc_j[2] != 0.0;
-    if (stopping) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            c.iscal[0] = 1;
-            c.iscal[1] = j;
-            c.iscal[3] = j;
-            if (j == 0) c.iscal[2] = SKF_ERR_ZERO_RHS;
-        }
-        if (j == 0 || c.identity) return;
+    stopping = sc_j[2] != 0.0;
+    if (stopping && blockIdx.x == 0 && threadIdx.x == 0) {
+        c.iscal[0] = 1;
+        c.iscal[1] = j;
+        c.iscal[3] = j;
+        if (j == 0) c.iscal[2] = SKF_ERR_ZERO_RHS;
     }
-    const bool last = (j == c.m - 1) && !stopping;
+    if (stopping && (j == 0 || c.identity)) return false;
+    if (!c.identity && j >= 1) finalize_column<TB>(c, j - 1, true, !Store<TB>::kExact, false);
+    return true;
+}
 
-    const double sigma = sc_j[0];
+// At a stop (j >= 1, S sparse): S w_j into the partials of parity j & 1.
+// bins: [2 s] ints of shared memory.
+template <int ZCAP, typename TB>
+__device__ __forceinline__ void spmv_stop_sketch(const LpCtx &c, int j, int *bins) {
+    const int s = c.sp.s;
+    const int L = limb_bits(*c.binmax_chunk);
+    const int P = sketch_fraction_bits_from_limb(L);
+    const TB *wj = (const TB *)c.V + (size_t)j * c.ldv;
     const double wmax = c.fin_w[2 * (size_t)j + 1];
     const int ew = wmax > 0.0 ? bound_exponent(wmax) : kNoExp;
-    const double ybound = c.norm_inf * wmax * (1.0 + 1.0 / 1024.0);   // margin for the FP32 row sums
-    const int ey = (last && ybound > 0.0) ? bound_exponent(ybound) : kNoExp;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.ex[j] = ew;
+    for (int i = threadIdx.x; i < 2 * s; i += blockDim.x) bins[i] = 0;
+    __syncthreads();
+    const int64_t nc = chunks_of_cta(c);
+    for (int64_t i = 0; i < nc; ++i) {
+        const int64_t r = chunk_row(c, i);
+        if (r >= 0 && ew != kNoExp)
+            scatter2<ZCAP>(c, r, fixed_point_f32(Store<TB>::ld(wj + r), P - ew), L, bins, bins + s);
+    }
+    __syncthreads();
+    long long *ow = c.skWp + ((size_t)(j & 1) * c.G + blockIdx.x) * s;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) ow[i] = combine_limbs(bins[i], bins[s + i], L);
+}
+
+// Common end: sketch partials of S y_{m-1} (last step), dot/max partials and
+// the last-arriving CTA's fixed-order reduction.
+template <int KW>
+__device__ __forceinline__ void spmv_end(const LpCtx &c, int j, int nw, bool last, int L, const int *ybins,
+                                         float (&acc)[KW], unsigned ykey, double *red) {
+    const int s = c.sp.s;
+    if (last) {
+        __syncthreads();
+        long long *oy = c.skYp + (size_t)blockIdx.x * s;
+        for (int i = threadIdx.x; i < s; i += kSpmvThreads) oy[i] = combine_limbs(ybins[i], ybins[s + i], L);
+    }
+    double accd[KW];
+#pragma unroll
+    for (int a = 0; a < KW; ++a) accd[a] = (double)acc[a];
+    block_sum<KW, kSpmvThreads>(accd, red);
+    const unsigned ymk = (unsigned)block_max_key<kSpmvThreads>((unsigned long long)ykey, (unsigned long long *)red);
+    if (threadIdx.x == 0) {
+        double *o = c.p1 + (size_t)blockIdx.x * kP1;
+        for (int a = 0; a < KW; ++a) o[a] = accd[a];
+        o[kP1 - 1] = (double)__uint_as_float(ymk);
+    }
+    if (last_to_arrive(c.cnt)) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int v = warp; v <= nw; v += kSpmvThreads / 32) {
+            const int slot = (v < nw) ? v : kP1 - 1;
+            const double rr = warp_reduce_partials(c.p1 + slot, gridDim.x, kP1, slot == kP1 - 1);
+            if (lane == 0) c.fin_d[(size_t)j * kP1 + slot] = rr;
+        }
+        if (threadIdx.x == 0) c.cnt[0] = 0u;
+    }
+}
+
+// Scale of the directly scattered S y_{m-1}: |y_r| <= ||A||_inf max|w_{m-1}|.
+__device__ __forceinline__ int last_y_exponent(const LpCtx &c, int j) {
+    const double ybound = c.norm_inf * c.fin_w[2 * (size_t)j + 1] * (1.0 + 1.0 / 1024.0);   // FP32 row-sum margin
+    const int ey = ybound > 0.0 ? bound_exponent(ybound) : kNoExp;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.ex[2 * c.m] = ey;
+    return ey;
+}
+
+// SpMV with the SELL values and columns loaded per row (any slice width).
+template <int KW, int ZCAP, typename TB>
+__global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, int j) {
+    extern __shared__ int bins[];   // [2 s]: limbs of S w_j (stopping step) or of S y_{m-1} (last step)
+    __shared__ double red[32 * KW];
+    bool stopping;
+    if (!spmv_begin<TB>(c, j, stopping)) return;
+    if (stopping) {
+        spmv_stop_sketch<ZCAP, TB>(c, j, bins);
+        return;
+    }
+    const int s = c.sp.s;
+    const TB *V = (const TB *)c.V;
+    const TB *wj = V + (size_t)j * c.ldv;
     const int L = c.identity ? 0 : limb_bits(*c.binmax_chunk);
     const int P = sketch_fraction_bits_from_limb(L);
-    const long long lmask = (1ll << L) - 1;
-    const int shift_w = P - (ew == kNoExp ? 0 : ew);
-    const int shift_y = P - (ey == kNoExp ? 0 : ey);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        c.ex[j] = ew;
-        if (last) c.ex[2 * c.m] = ey;
-    }
-    int *aw0 = bins, *aw1 = bins + s, *ay0 = bins + 2 * s, *ay1 = bins + 3 * s;
-    if (!c.identity)
-        for (int i = threadIdx.x; i < (last ? 4 : 2) * s; i += kSpmvThreads) bins[i] = 0;
+    const bool last = (j == c.m - 1) && !c.identity;
+    const int ey = last ? last_y_exponent(c, j) : kNoExp;
+    if (last)
+        for (int i2 = threadIdx.x; i2 < 2 * s; i2 += kSpmvThreads) bins[i2] = 0;
     __syncthreads();
-
+    const int shift_y = P - (ey == kNoExp ? 0 : ey);
     const int i0 = max(0, j - c.k + 1);
     const int nw = j - i0 + 1;
     float acc[KW];
 #pragma unroll
     for (int a = 0; a < KW; ++a) acc[a] = 0.f;
     unsigned ykey = 0;
-    const TB *wj = V + (size_t)j * c.ldv;
     const int lane = threadIdx.x & 31;
-    const int64_t nch = (c.n + kChunkRows - 1) / kChunkRows;
-    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-        const int64_t rw = ch * kChunkRows + (threadIdx.x & ~31);   // first row of the warp's slice
-        if (rw >= c.n) continue;                                    // whole warp
-        const int64_t t = rw >> 5;
+    const int64_t nc = chunks_of_cta(c);
+    for (int64_t i = 0; i < nc; ++i) {
+        const int64_t rw = ((int64_t)blockIdx.x + i * c.G) * kChunkRows + (threadIdx.x & ~31);   // warp's slice
+        if (rw >= c.n) continue;                                                                // whole warp
         int wt = 0;
         long long so = 0;
-        if (lane == 0 && !stopping) {
-            wt = __ldg(c.sell_w + t);
-            so = __ldg(c.sell_off + t);
+        if (lane == 0) {
+            wt = __ldg(c.sell_w + (rw >> 5));
+            so = __ldg(c.sell_off + (rw >> 5));
         }
         wt = __shfl_sync(0xffffffffu, wt, 0);
         so = __shfl_sync(0xffffffffu, so, 0);
         const int64_t r = rw + lane;
         if (r >= c.n) continue;   // no warp-collective operation below
-        const int64_t base = so + lane;
+        // window values first: independent of the SpMV, their latency overlaps it
+        float wv[KW];
+#pragma unroll
+        for (int a = 0; a < KW; ++a) wv[a] = a < nw ? Store<TB>::ld(V + (size_t)(i0 + a) * c.ldv + r) : 0.f;
+        const float *pv = c.sell_val + so + lane;   // entry p at pv[32 p]
+        const int32_t *pc = c.sell_col + so + lane;
         float y = 0.f;
         // eight entries of the row in flight at a time
         for (int p0 = 0; p0 < wt; p0 += 8) {
@@ -289,9 +417,8 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, in
 #pragma unroll
             for (int p = 0; p < 8; ++p)
                 if (p0 + p < wt) {
-                    const int64_t o = base + 32ll * (p0 + p);
-                    av[p] = __ldcs(c.sell_val + o);
-                    cv[p] = __ldcs(c.sell_col + o);
+                    av[p] = __ldcs(pv + 32 * (p0 + p));
+                    cv[p] = __ldcs(pc + 32 * (p0 + p));
                 }
 #pragma unroll
             for (int p = 0; p < 8; ++p)
@@ -300,84 +427,164 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, in
             for (int p = 0; p < 8; ++p)
                 if (p0 + p < wt) y = fmaf(av[p], xv[p], y);
         }
-        float wv[KW];
+        c.Y[r] = y;
 #pragma unroll
         for (int a = 0; a < KW; ++a)
-            wv[a] = (a < nw && (!stopping || a == nw - 1)) ? Store<TB>::ld(V + (size_t)(i0 + a) * c.ldv + r) : 0.f;
-        float wjr = wv[0];
+            if (a < nw) acc[a] = fmaf(wv[a], y, acc[a]);
+        ykey = max(ykey, abs_key_f32(y));
+        if (last && ey != kNoExp) scatter2<ZCAP>(c, r, fixed_point_f32(y, shift_y), L, bins, bins + s);
+    }
+    spmv_end<KW>(c, j, nw, last, L, bins, acc, ykey, red);
+}
+
+// Pipelined SpMV for operators whose SELL slices are at most 8 wide.  Chunk i
+// of the CTA is in three stages at once: its values and gathers are loaded
+// (the gathers use column indices loaded one iteration earlier), the column
+// indices of chunk i + 1 are loaded, and the slice width and offset of chunk
+// i + 2 are loaded.  One memory round trip per chunk instead of two (column,
+// then gather), with 8 extra registers per thread.
+template <int KW, int ZCAP, typename TB>
+__global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp_pipe(LpCtx c, int j) {
+    extern __shared__ int bins[];   // [2 s]: limbs of S w_j (stopping step) or of S y_{m-1} (last step)
+    __shared__ double red[32 * KW];
+    bool stopping;
+    if (!spmv_begin<TB>(c, j, stopping)) return;
+    if (stopping) {
+        spmv_stop_sketch<ZCAP, TB>(c, j, bins);
+        return;
+    }
+    const int s = c.sp.s;
+    const TB *V = (const TB *)c.V;
+    const TB *wj = V + (size_t)j * c.ldv;
+    const int L = c.identity ? 0 : limb_bits(*c.binmax_chunk);
+    const int P = sketch_fraction_bits_from_limb(L);
+    const bool last = (j == c.m - 1) && !c.identity;
+    const int ey = last ? last_y_exponent(c, j) : kNoExp;
+    if (last)
+        for (int i2 = threadIdx.x; i2 < 2 * s; i2 += kSpmvThreads) bins[i2] = 0;
+    __syncthreads();
+    const int shift_y = P - (ey == kNoExp ? 0 : ey);
+    const int i0 = max(0, j - c.k + 1);
+    const int nw = j - i0 + 1;
+    float acc[KW];
 #pragma unroll
-        for (int a = 1; a < KW; ++a)
-            if (a == nw - 1) wjr = wv[a];
-        if (!stopping) {
+    for (int a = 0; a < KW; ++a) acc[a] = 0.f;
+    unsigned ykey = 0;
+    const int lane = threadIdx.x & 31;
+    const int64_t nc = chunks_of_cta(c);
+    const int64_t step = (int64_t)c.G * kChunkRows;
+    const int64_t rw0 = (int64_t)blockIdx.x * kChunkRows + (threadIdx.x & ~31);   // warp's slice in chunk 0
+
+    // slice metadata: chunk i (broadcast, wt_c / so_c) and chunk i + 1 (lane-0
+    // values, broadcast one iteration later)
+    int wt_c = 0, mw_raw = 0;
+    long long so_c = 0, mo_raw = 0;
+    if (lane == 0 && nc > 0 && rw0 < c.n) {
+        wt_c = __ldg(c.sell_w + (rw0 >> 5));
+        so_c = __ldg(c.sell_off + (rw0 >> 5));
+    }
+    wt_c = __shfl_sync(0xffffffffu, wt_c, 0);
+    so_c = __shfl_sync(0xffffffffu, so_c, 0);
+    if (lane == 0 && nc > 1 && rw0 + step < c.n) {
+        mw_raw = __ldg(c.sell_w + ((rw0 + step) >> 5));
+        mo_raw = __ldg(c.sell_off + ((rw0 + step) >> 5));
+    }
+    int cv[8];
+    {
+        const int32_t *pc = c.sell_col + so_c + lane;
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+            if (p < wt_c) cv[p] = __ldcs(pc + 32 * p);
+    }
+    for (int64_t i = 0; i < nc; ++i) {
+        const int64_t rw = rw0 + i * step;
+        const int64_t r = rw + lane;
+        const bool ok = rw < c.n && r < c.n;   // padded rows of the last slice do no work
+        // (1) values, gathers and window of chunk i
+        float av[8], xv[8], wv[KW];
+        {
+            const float *pv = c.sell_val + so_c + lane;
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < wt_c) {
+                    av[p] = __ldcs(pv + 32 * p);
+                    xv[p] = Store<TB>::ld(wj + cv[p]);
+                }
+#pragma unroll
+            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? Store<TB>::ld(V + (size_t)(i0 + a) * c.ldv + r) : 0.f;
+        }
+        // (2) metadata of chunk i + 1 (loaded one iteration ago) and its column indices
+        const int wt_n = __shfl_sync(0xffffffffu, mw_raw, 0);
+        const long long so_n = __shfl_sync(0xffffffffu, mo_raw, 0);
+        int cvn[8];
+        {
+            const int32_t *pc = c.sell_col + so_n + lane;
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < wt_n) cvn[p] = __ldcs(pc + 32 * p);
+        }
+        // (3) metadata of chunk i + 2
+        mw_raw = 0;
+        mo_raw = 0;
+        if (lane == 0 && i + 2 < nc && rw + 2 * step < c.n) {
+            mw_raw = __ldg(c.sell_w + ((rw + 2 * step) >> 5));
+            mo_raw = __ldg(c.sell_off + ((rw + 2 * step) >> 5));
+        }
+        // (4) y of chunk i
+        if (ok) {
+            float y = 0.f;
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < wt_c) y = fmaf(av[p], xv[p], y);
             c.Y[r] = y;
 #pragma unroll
             for (int a = 0; a < KW; ++a)
                 if (a < nw) acc[a] = fmaf(wv[a], y, acc[a]);
             ykey = max(ykey, abs_key_f32(y));
+            if (last && ey != kNoExp) scatter2<ZCAP>(c, r, fixed_point_f32(y, shift_y), L, bins, bins + s);
         }
-        if (c.identity) {
-            c.SV[r + (size_t)j * s] = sigma * (double)wjr;
-            c.SAV[r + (size_t)j * s] = sigma * (double)y;
-        } else {
-            uint16_t e[ZCAP];
-            load_pattern<ZCAP>(c.pattern, c.sp.zeta, r, e);
-            const long long vw = ew == kNoExp ? 0 : fixed_point_f32(wjr, shift_w);
-            const int w0 = (int)(vw & lmask), w1 = (int)(vw >> L);
-            const long long vy = last && ey != kNoExp ? fixed_point_f32(y, shift_y) : 0;
-            const int y0 = (int)(vy & lmask), y1 = (int)(vy >> L);
+        wt_c = wt_n;
+        so_c = so_n;
 #pragma unroll
-            for (int q = 0; q < ZCAP; ++q) {
-                if (q < c.sp.zeta) {
-                    int row;
-                    bool neg;
-                    pattern_entry(c.sp, e[q], q, row, neg);
-                    red_limbs(aw0, aw1, row, w0, w1, neg);
-                    if (last) red_limbs(ay0, ay1, row, y0, y1, neg);
-                }
-            }
-        }
+        for (int p = 0; p < 8; ++p) cv[p] = cvn[p];
     }
-    if (!c.identity) {
-        __syncthreads();
-        long long *ow = c.skWp + (size_t)blockIdx.x * s, *oy = c.skYp + (size_t)blockIdx.x * s;
-        for (int i = threadIdx.x; i < s; i += kSpmvThreads) {
-            ow[i] = combine_limbs(aw0[i], aw1[i], L);
-            if (last) oy[i] = combine_limbs(ay0[i], ay1[i], L);
-        }
-    }
-    if (stopping) return;
-    double accd[KW];
-#pragma unroll
-    for (int a = 0; a < KW; ++a) accd[a] = (double)acc[a];
-    block_sum_auto<KW, kSpmvThreads>(accd, red);
-    const unsigned ymk = (unsigned)block_max_key<kSpmvThreads>((unsigned long long)ykey, (unsigned long long *)red);
-    if (threadIdx.x == 0) {
-        double *o = c.p1 + (size_t)blockIdx.x * kP1;
-        for (int a = 0; a < KW; ++a) o[a] = accd[a];
-        o[kP1 - 1] = (double)__uint_as_float(ymk);
-    }
-    if (last_to_arrive(c.cnt)) {
-        const int warp = threadIdx.x >> 5, lane2 = threadIdx.x & 31;
-        for (int v = warp; v <= nw; v += kSpmvThreads / 32) {
-            const int slot = (v < nw) ? v : kP1 - 1;
-            const double r = warp_reduce_partials(c.p1 + slot, gridDim.x, kP1, slot == kP1 - 1);
-            if (lane2 == 0) c.fin_d[(size_t)j * kP1 + slot] = r;
-        }
-        if (threadIdx.x == 0) c.cnt[0] = 0u;
+    spmv_end<KW>(c, j, nw, last, L, bins, acc, ykey, red);
+}
+
+// S = I (tests): SV[:, j] = sigma_j w_j, SAV[:, j] = sigma_j y_j.
+template <typename TB>
+__global__ void __launch_bounds__(kThreads) k_identity_cols_lp(LpCtx c, int j) {
+    if (c.iscal[0] && c.iscal[3] <= j) return;
+    const TB *wj = (const TB *)c.V + (size_t)j * c.ldv;
+    const double sigma = c.stepsc[4 * (size_t)j];
+    const int s = c.sp.s;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < c.n; r += (int64_t)gridDim.x * blockDim.x) {
+        c.SV[r + (size_t)j * s] = sigma * (double)Store<TB>::ld(wj + r);
+        c.SAV[r + (size_t)j * s] = sigma * (double)c.Y[r];
     }
 }
 
+// Sum of the per-lane copies of bin i (C = 1 << lc copies, copy index in the
+// low bits) by one warp: exact in int32, since every copy holds a subset of
+// the bin's contributions and all of them together fit (limb width rule; a
+// split sign bin holds a subset too).
+__device__ __forceinline__ int sum_copies(const int *b, int i, int lc) {
+    const int lane = threadIdx.x & 31;
+    int v = lane < (1 << lc) ? b[(i << lc) + lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <int KW, int ZCAP, typename TB>
-__global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update_lp(LpCtx c, int j) {
-    extern __shared__ int bins[];   // [s]: one limb of the BF16 residual sketch
-    __shared__ double red[BlockSumTraits<KW + 1, kUpdThreads>::kSmem];
+__global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, int j) {
+    // per-lane copies of the bins: [limb 0 | limb 1 of S w_j | residual limb][nbin << lc]
+    extern __shared__ int bins[];
+    __shared__ double red[32 * (KW + 1)];
     __shared__ double sh[kMaxK];     // MGS coefficients h_ij
     __shared__ float scf[kMaxK];     // h_ij sigma_i in FP32, as applied
     __shared__ float sigf_s;
-    // stopped at an earlier step; at the stopping step only the sketches are finalised
-    if (c.iscal[0] && c.iscal[3] < j) return;
-    if (!c.identity) finalize_sketches<TB>(c, j, j == c.m - 1 && !c.iscal[0]);
-    if (c.iscal[0]) return;
+    if (c.iscal[0]) return;          // set at the latest by the spmv launch of this step
     TB *V = (TB *)c.V;
     const int G = gridDim.x;
     const double *fd = c.fin_d + (size_t)j * kP1;
@@ -405,6 +612,21 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update_lp(LpCtx c, int 
         }
         sigf_s = (float)sigma;
     }
+    const bool do_update = j < c.m - 1;
+    const bool sk = !c.identity;
+    const bool split = sk && c.split;
+    const bool resid = !Store<TB>::kExact && sk && do_update;
+    const int L = sk ? limb_bits(*c.binmax_chunk) : 0;
+    const int P = sketch_fraction_bits_from_limb(L);
+    const double wmax = c.fin_w[2 * (size_t)j + 1];
+    const int ew = (sk && wmax > 0.0) ? bound_exponent(wmax) : kNoExp;
+    const int shift_w = P - (ew == kNoExp ? 0 : ew);
+    const long long lmask = (1ll << L) - 1;
+    const int lc = c.lc, cm = (1 << lc) - 1;
+    const int ns = (split ? 8 * 256 : s) << lc;
+    int *wb0 = bins, *wb1 = bins + ns, *db = bins + 2 * ns;
+    if (sk)
+        for (int i = threadIdx.x; i < (resid ? 3 : 2) * ns; i += kUpdThreads) bins[i] = 0;
     __syncthreads();
     const float sigf = sigf_s;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -412,51 +634,80 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update_lp(LpCtx c, int 
         double *cf = c.coef + (size_t)j * kCoef;
         cf[0] = (double)sigf;
         for (int a = 0; a < nw; ++a) cf[1 + a] = (double)scf[a];
-        if (j < c.m - 1)
+        if (do_update)
             for (int a = 0; a < nw; ++a) c.H[(i0 + a) + (size_t)j * (c.m + 1)] = sh[a];
+        c.ex[j] = ew;
     }
-    const bool do_update = j < c.m - 1;
-    if (!do_update) return;
     // one-limb fixed point for the BF16 residual: |bf16(w) - w| <= 2^-8 |w|
     // and |w| <= sigma_j max|y_j| + sum_i |h_ij sigma_i| max|w_i|
-    const bool resid = !Store<TB>::kExact && !c.identity;
     int ed = kNoExp;
-    const int Ld = resid ? limb_bits(*c.binmax) : 0;
     if (resid) {
         double wb = (double)sigf * ymax;
         for (int a = 0; a < nw; ++a) wb += fabs((double)scf[a]) * c.fin_w[2 * (size_t)(i0 + a) + 1];
-        const double db = wb * (1.0 / 256.0) * (1.0 + 1.0 / 1024.0);
-        ed = db > 0.0 ? bound_exponent(db) : kNoExp;
-        for (int i = threadIdx.x; i < s; i += kUpdThreads) bins[i] = 0;
-        __syncthreads();
+        const double dbd = wb * (1.0 / 256.0) * (1.0 + 1.0 / 1024.0);
+        ed = dbd > 0.0 ? bound_exponent(dbd) : kNoExp;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) c.ex[c.m + j + 1] = ed;
-    const int shift_d = Ld - (ed == kNoExp ? 0 : ed);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && do_update) c.ex[c.m + j + 1] = ed;
+    const int shift_d = L - (ed == kNoExp ? 0 : ed);
 
     const int ng = min(j + 1, c.k - 1);
     float part[KW + 1];
 #pragma unroll
     for (int i = 0; i <= KW; ++i) part[i] = 0.f;
     unsigned nkey = 0;
-    const int64_t r0 = (int64_t)blockIdx.x * c.rows_per_cta;
-    const int64_t r1 = min(c.n, r0 + c.rows_per_cta);
     TB *wn = V + (size_t)(j + 1) * c.ldv;
-    constexpr int U = 4;
-    for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += U * kUpdThreads) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nc = chunks_of_cta(c);
+    constexpr int U = KW <= 2 ? 4 : (KW <= 4 ? 2 : 1);   // chunks in flight per thread
+    for (int64_t i = 0; i < nc; i += U) {
         float yv[U], wv[U][KW];
+        int64_t rr[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t r = rb + (int64_t)u * kUpdThreads;
-            const bool ok = r < r1;
-            yv[u] = ok ? c.Y[r] : 0.f;
+            rr[u] = i + u < nc ? chunk_row(c, i + u) : -1;
+            const bool ok = rr[u] >= 0;
+            yv[u] = (ok && do_update) ? c.Y[rr[u]] : 0.f;
 #pragma unroll
             for (int a = 0; a < KW; ++a)
-                wv[u][a] = (ok && a < nw) ? Store<TB>::ld(V + (size_t)(i0 + a) * c.ldv + r) : 0.f;
+                wv[u][a] = (ok && a < nw) ? Store<TB>::ld(V + (size_t)(i0 + a) * c.ldv + rr[u]) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t r = rb + (int64_t)u * kUpdThreads;
-            if (r < r1) {
+            const int64_t r = rr[u];
+            if (r < 0) continue;
+            float wjr = wv[u][0];
+#pragma unroll
+            for (int a = 1; a < KW; ++a)
+                if (a == nw - 1) wjr = wv[u][a];
+            int row[ZCAP];
+            bool neg[ZCAP];
+            uint2 pv = make_uint2(0u, 0u);
+            if (split) pv = __ldg((const uint2 *)(c.pattern8 + r * 8));
+            else if (sk) pattern_row<ZCAP>(c, r, row, neg);
+            if (sk && ew != kNoExp) {
+                // exact sketch of the stored w_j, per-lane bin copies
+                const long long vw = fixed_point_f32(wjr, shift_w);
+                const int l0 = (int)(vw & lmask), l1 = (int)(vw >> L);
+                if (split) {
+                    // bin (stripe << 8) | pattern byte: signs in separate bins
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int e = (int)__byte_perm(q < 4 ? pv.x : pv.y, 0u, 0x4440u + (q & 3));
+                        const int bi = (((q << 8) | e) << lc) | (lane & cm);
+                        atomicAdd(wb0 + bi, l0);
+                        atomicAdd(wb1 + bi, l1);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < ZCAP; ++q)
+                        if (q < c.sp.zeta) {
+                            const int bi = (row[q] << lc) | (lane & cm);
+                            atomicAdd(wb0 + bi, neg[q] ? -l0 : l0);
+                            atomicAdd(wb1 + bi, neg[q] ? -l1 : l1);
+                        }
+                }
+            }
+            if (do_update) {
                 float w = sigf * yv[u];
 #pragma unroll
                 for (int a = 0; a < KW; ++a)
@@ -470,25 +721,53 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update_lp(LpCtx c, int 
                     if (a < nw && nw - a <= ng) part[1 + a] = fmaf(wr, wv[u][a], part[1 + a]);
                 if (resid && ed != kNoExp) {
                     // wr - w is exact in FP32 (Sterbenz: wr and w lie within a factor 2)
-                    const long long vd = fixed_point_f32(wr - w, shift_d);
-                    uint16_t e[ZCAP];
-                    load_pattern<ZCAP>(c.pattern, c.sp.zeta, r, e);
+                    const int vd = (int)fixed_point_f32(wr - w, shift_d);
+                    if (split) {
 #pragma unroll
-                    for (int q = 0; q < ZCAP; ++q)
-                        if (q < c.sp.zeta) {
-                            int row;
-                            bool neg;
-                            pattern_entry(c.sp, e[q], q, row, neg);
-                            atomicAdd(bins + row, neg ? -(int)vd : (int)vd);
+                        for (int q = 0; q < 8; ++q) {
+                            const int e = (int)__byte_perm(q < 4 ? pv.x : pv.y, 0u, 0x4440u + (q & 3));
+                            atomicAdd(db + ((((q << 8) | e) << lc) | (lane & cm)), vd);
                         }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < ZCAP; ++q)
+                            if (q < c.sp.zeta) atomicAdd(db + ((row[q] << lc) | (lane & cm)), neg[q] ? -vd : vd);
+                    }
                 }
             }
         }
     }
+    __syncthreads();
+    if (sk) {
+        // per-CTA partials: copies summed by one warp per bin
+        const int warp = threadIdx.x >> 5;
+        long long *ow = c.skWp + ((size_t)(j & 1) * G + blockIdx.x) * s;
+        long long *od = c.skDp + (size_t)blockIdx.x * s;
+        for (int i = warp; i < s; i += kUpdThreads / 32) {
+            long long v0, v1, vd = 0;
+            if (split) {
+                int q = 0;
+                while (q + 1 < 8 && i >= c.sp.start[q + 1]) ++q;
+                const int bp = (q << 8) + (i - c.sp.start[q]), bn = bp + 128;   // positive and negative bins
+                v0 = (long long)sum_copies(wb0, bp, lc) - sum_copies(wb0, bn, lc);
+                v1 = (long long)sum_copies(wb1, bp, lc) - sum_copies(wb1, bn, lc);
+                if (resid) vd = (long long)sum_copies(db, bp, lc) - sum_copies(db, bn, lc);
+            } else {
+                v0 = sum_copies(wb0, i, lc);
+                v1 = sum_copies(wb1, i, lc);
+                if (resid) vd = sum_copies(db, i, lc);
+            }
+            if (lane == 0) {
+                ow[i] = (v1 << L) + v0;
+                if (resid) od[i] = vd;
+            }
+        }
+    }
+    if (!do_update) return;
     double partd[KW + 1];
 #pragma unroll
     for (int i = 0; i <= KW; ++i) partd[i] = (double)part[i];
-    block_sum_auto<KW + 1, kUpdThreads>(partd, red);
+    block_sum<KW + 1, kUpdThreads>(partd, red);
     const unsigned nmk = (unsigned)block_max_key<kUpdThreads>((unsigned long long)nkey, (unsigned long long *)red);
     if (threadIdx.x == 0) {
         double *o = c.p2 + (size_t)blockIdx.x * kP2;
@@ -496,20 +775,15 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update_lp(LpCtx c, int 
         o[1] = (double)__uint_as_float(nmk);
         for (int a = 0; a < KW; ++a) o[2 + a] = partd[1 + a];
     }
-    if (resid) {
-        __syncthreads();
-        long long *od = c.skDp + (size_t)blockIdx.x * s;
-        for (int i = threadIdx.x; i < s; i += kUpdThreads) od[i] = (long long)bins[i];
-    }
     if (last_to_arrive(c.cnt + 1)) {
         const int warp = threadIdx.x >> 5;
         for (int v = warp; v < 2 + nw; v += kUpdThreads / 32) {
             const int d = nw - (v - 2);   // Gram distance of slot v - 2
             if (v >= 2 && (d < 1 || d > ng)) continue;
-            const double r = warp_reduce_partials(c.p2 + v, G, kP2, v == 1);
+            const double rv = warp_reduce_partials(c.p2 + v, G, kP2, v == 1);
             if ((threadIdx.x & 31) == 0) {
-                if (v < 2) c.fin_w[2 * (size_t)(j + 1) + v] = r;
-                else c.gram[(size_t)(j + 1) * kMaxK + d] = r;
+                if (v < 2) c.fin_w[2 * (size_t)(j + 1) + v] = rv;
+                else c.gram[(size_t)(j + 1) * kMaxK + d] = rv;
             }
         }
         __syncthreads();
@@ -526,6 +800,18 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update_lp(LpCtx c, int 
             c.cnt[1] = 0u;
         }
     }
+}
+
+// After the loop: the pending column.  Ran to the end: S w_{m-1} (SV), S y_{m-2}
+// by the relation and the scattered S y_{m-1} (SAV).  Stopped at step me: S w_me
+// (not a basis column) gives S y_{me-1} by the relation.
+template <typename TB>
+__global__ void __launch_bounds__(kThreads) k_arnoldi_finish_lp(LpCtx c) {
+    const int me = c.iscal[1];
+    if (me == 0 || c.identity) return;
+    const bool stopped = c.iscal[0] != 0;
+    if (stopped) finalize_column<TB>(c, me, false, false, false);
+    else finalize_column<TB>(c, c.m - 1, true, false, true);
 }
 
 // | ||S v_j||^2 - 1 | per column (the embedding-quality estimate of Sec. 4.3).
@@ -558,28 +844,30 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_info_lp(LpCtx c, skf_info 
 }
 
 template <int KW, int ZCAP, typename TB>
-void launch_steps(const LpCtx &c, size_t smem_spmv, size_t smem_upd, cudaStream_t st) {
-    auto spmv = k_arnoldi_spmv_lp<KW, ZCAP, TB>;
+void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, cudaStream_t st) {
+    auto spmv = pipe ? k_arnoldi_spmv_lp_pipe<KW, ZCAP, TB> : k_arnoldi_spmv_lp<KW, ZCAP, TB>;
     auto update = k_arnoldi_update_lp<KW, ZCAP, TB>;
     if (smem_spmv > 48 * 1024)
         cudaFuncSetAttribute(spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_spmv);
     if (smem_upd > 48 * 1024)
         cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_upd);
+    const unsigned gid = (unsigned)std::min<int64_t>((c.n + kThreads - 1) / kThreads, 8ll * c.G);
     for (int j = 0; j < c.m; ++j) {
-        spmv<<<c.G_spmv, kSpmvThreads, smem_spmv, st>>>(c, j);
-        update<<<c.G_upd, kUpdThreads, smem_upd, st>>>(c, j);
+        spmv<<<c.G, kSpmvThreads, smem_spmv, st>>>(c, j);
+        if (c.identity) k_identity_cols_lp<TB><<<gid, kThreads, 0, st>>>(c, j);
+        update<<<c.G, kUpdThreads, smem_upd, st>>>(c, j);
     }
 }
 
 template <int ZCAP, typename TB>
-void launch_steps_k(const LpCtx &c, size_t s1, size_t s2, cudaStream_t st) {
-    if (c.k <= 2) launch_steps<2, ZCAP, TB>(c, s1, s2, st);
-    else if (c.k <= 4) launch_steps<4, ZCAP, TB>(c, s1, s2, st);
-    else if (c.k <= 8) launch_steps<8, ZCAP, TB>(c, s1, s2, st);
-    else launch_steps<16, ZCAP, TB>(c, s1, s2, st);
+void launch_steps_k(const LpCtx &c, bool pipe, size_t s1, size_t s2, cudaStream_t st) {
+    if (c.k <= 2) launch_steps<2, ZCAP, TB>(c, pipe, s1, s2, st);
+    else if (c.k <= 4) launch_steps<4, ZCAP, TB>(c, pipe, s1, s2, st);
+    else if (c.k <= 8) launch_steps<8, ZCAP, TB>(c, pipe, s1, s2, st);
+    else launch_steps<16, ZCAP, TB>(c, pipe, s1, s2, st);
 }
 
-// Host driver: init, m x (spmv, update), eps, info on `st`.
+// Host driver: init, m x (spmv, update), finish, eps, info on `st`.
 template <typename TB>
 skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, TB *V, int64_t ldv,
                           double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
@@ -595,7 +883,7 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     if (!c.identity) {
         c.sp = make_sparse_sign(S);
         c.pattern = S->pattern;
-        c.binmax = S->binmax;
+        c.pattern8 = S->pattern8;
         c.binmax_chunk = S->binmax_chunk;
     }
     c.sp.s = S->s;
@@ -610,14 +898,32 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     c.SAV = SAV;
     c.H = H;
     c.iscal = iscal;
-    row_partition(A->n, &c.G_upd, &c.rows_per_cta);
-    chunk_partition(A->n, &c.G_spmv);
-    const int G = c.G_upd, Gs = c.G_spmv;
+    chunk_partition(A->n, &c.G);
+    const int G = c.G;
     const int s = S->s;
+    const bool bf = !Store<TB>::kExact;
+
+    // per-lane bin copies of the update kernel: as many (up to 32) as fit;
+    // bins [stripe][sign][128] with the compact pattern and zeta = 8
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    c.split = (!c.identity && S->pattern8 != nullptr && S->zeta == 8) ? 1 : 0;
+    const int nlimb = bf ? 3 : 2;
+    const size_t nbin = c.split ? 8 * 256 : (size_t)s;
+    const size_t static_upd = sizeof(double) * 32 * (kMaxK + 1) + sizeof(double) * kMaxK + sizeof(float) * (kMaxK + 1) +
+                              256;
+    c.lc = 5;
+    while (c.lc > 0 && sizeof(int) * (size_t)nlimb * (nbin << c.lc) + static_upd > (size_t)optin) --c.lc;
+    const size_t smem_upd = c.identity ? 0 : sizeof(int) * (size_t)nlimb * (nbin << c.lc);
+    const size_t smem_spmv = c.identity ? 0 : sizeof(int) * 2 * (size_t)s;
+    if (smem_upd + static_upd > (size_t)optin || smem_spmv > (size_t)optin)
+        return fail(SKF_ERR_NOT_SUPPORTED, "sketch size s too large for the shared-memory bins");
+    const bool pipe = A->max_width <= 8;   // slices at most 8 wide: the pipelined SpMV
 
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t szY = sizeof(float) * A->n;
-    const size_t szP1 = sizeof(double) * (size_t)Gs * kP1;
+    const size_t szP1 = sizeof(double) * (size_t)G * kP1;
     const size_t szP2 = sizeof(double) * (size_t)G * kP2;
     const size_t szFd = sizeof(double) * (size_t)m * kP1;
     const size_t szFw = sizeof(double) * (size_t)(m + 1) * 2;
@@ -625,13 +931,14 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     const size_t szGram = sizeof(double) * (size_t)(m + 1) * kMaxK;
     const size_t szCoef = sizeof(double) * (size_t)m * kCoef;
     const size_t szSk = c.identity ? 0 : sizeof(double) * (size_t)m * s;
-    const size_t szSkYp = c.identity ? 0 : sizeof(long long) * (size_t)Gs * s;   // also S w_j partials
-    const size_t szSkDp = (c.identity || Store<TB>::kExact) ? 0 : sizeof(long long) * (size_t)G * s;
+    const size_t szSd = (c.identity || !bf) ? 0 : sizeof(double) * (size_t)s;
+    const size_t szPart = c.identity ? 0 : sizeof(long long) * (size_t)G * s;
     const size_t szEx = sizeof(int) * (size_t)(2 * m + 1);
     const size_t szEps = sizeof(double) * (size_t)m;
     const size_t szCnt = sizeof(unsigned) * 4;
     const size_t total = al(szY) + al(szP1) + al(szP2) + al(szFd) + al(szFw) + al(szSc) + al(szGram) + al(szCoef) +
-                         al(szSk) + 2 * al(szSkYp) + al(szSkDp) + al(szEx) + al(szEps) + al(szCnt);
+                         al(szSk) + al(szSd) + al(2 * szPart) + al(szPart) + (bf ? al(szPart) : 0) + al(szEx) +
+                         al(szEps) + al(szCnt);
     char *ws = nullptr;
     skf_status stt = dalloc((void **)&ws, total, st);
     if (stt != SKF_OK) return stt;
@@ -650,22 +957,22 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     c.gram = (double *)take(szGram);
     c.coef = (double *)take(szCoef);
     c.skw = (double *)take(szSk);
-    c.skWp = (long long *)take(szSkYp);
-    c.skYp = (long long *)take(szSkYp);
-    c.skDp = (long long *)take(szSkDp);
+    c.sd = (double *)take(szSd);
+    c.skWp = (long long *)take(2 * szPart);
+    c.skYp = (long long *)take(szPart);
+    c.skDp = bf ? (long long *)take(szPart) : nullptr;
     c.ex = (int *)take(szEx);
     c.epscol = (double *)take(szEps);
     c.cnt = (unsigned *)take(szCnt);
     cudaMemsetAsync(c.cnt, 0, szCnt, st);
 
-    const size_t smem_spmv = c.identity ? 0 : sizeof(int) * 4 * (size_t)s;
-    const size_t smem_upd = (c.identity || Store<TB>::kExact) ? 0 : sizeof(int) * (size_t)s;
-    k_arnoldi_init_lp<TB><<<G, kThreads, 0, st>>>(c, b);
-    if (c.sp.zeta <= 8) launch_steps_k<8, TB>(c, smem_spmv, smem_upd, st);
-    else launch_steps_k<16, TB>(c, smem_spmv, smem_upd, st);
+    k_arnoldi_init_lp<TB><<<G, kChunkRows, 0, st>>>(c, b);
+    if (c.sp.zeta <= 8) launch_steps_k<8, TB>(c, pipe, smem_spmv, smem_upd, st);
+    else launch_steps_k<16, TB>(c, pipe, smem_spmv, smem_upd, st);
+    k_arnoldi_finish_lp<TB><<<G, kThreads, 0, st>>>(c);
     k_arnoldi_eps_lp<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);
     k_arnoldi_info_lp<<<1, kThreads, 0, st>>>(c, info);
-    count_launches(3 + 2ll * m);
+    count_launches(4 + (c.identity ? 3ll : 2ll) * m);
     cudaError_t e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "reduced-precision Arnoldi kernels");

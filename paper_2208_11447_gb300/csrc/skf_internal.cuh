@@ -60,6 +60,7 @@ struct skf_csr {
     void *sell_val = nullptr;
     int32_t *sell_col = nullptr;
     int max_width = 0;                // widest slice
+    int64_t max_chunk_entries = 0;    // most SELL entries in one chunk of 1024 rows (32 slices)
 };
 
 struct skf_sketch {
@@ -75,6 +76,10 @@ struct skf_sketch {
     uint16_t *pattern = nullptr;
     int *binmax = nullptr;            // device: most nonzeros one CTA row range puts in one row of S
     int *binmax_chunk = nullptr;      // device: the same for the chunk-interleaved partition
+    // Compact pattern when every stripe has at most 128 rows and zeta <= 8:
+    // byte [c * 8 + q] = (row of nonzero q within stripe q) | sign << 7, zero
+    // bytes beyond zeta; nullptr otherwise.
+    uint8_t *pattern8 = nullptr;
 };
 
 namespace skf {

@@ -59,6 +59,20 @@ __global__ void k_build_pattern(SparseSign sp, int64_t n, uint16_t *__restrict__
     }
 }
 
+// The same pattern in bytes (row within stripe | sign << 7), eight per column.
+__global__ void k_build_pattern8(SparseSign sp, int64_t n, const uint16_t *__restrict__ pattern,
+                                 uint8_t *__restrict__ p8) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        for (int q = 0; q < 8; ++q) {
+            uint8_t v = 0;
+            if (q < sp.zeta) {
+                const uint16_t e = pattern[c * sp.zeta + q];
+                v = (uint8_t)((e & 0x7Fu) | ((e >> 8) & 0x80u));
+            }
+            p8[c * 8 + q] = v;
+        }
+}
+
 // Largest number of nonzeros that one CTA's rows put into one row of S.  CTA
 // g owns the chunks g, g + G, g + 2G, ... of `chunk` rows (one chunk per CTA
 // for the contiguous partition).
@@ -202,6 +216,19 @@ skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st) {
     cudaMemcpy(hmax, S->binmax, 2 * sizeof(int), cudaMemcpyDeviceToHost);
     if (limb_bits(hmax[0]) < 13 || limb_bits(hmax[1]) < 13)
         return fail(SKF_ERR_NOT_SUPPORTED, "sketch too dense for the fixed-point accumulators");
+    int max_stripe = 0;
+    for (int q = 0; q < sp.zeta; ++q) max_stripe = std::max(max_stripe, sp.size[q]);
+    if (max_stripe <= 128 && S->zeta <= 8) {
+        if (cudaMalloc(&S->pattern8, (size_t)S->n * 8) == cudaSuccess) {
+            k_build_pattern8<<<blocks, 256, 0, st>>>(sp, S->n, S->pattern, S->pattern8);
+            count_launches(1);
+            e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "sketch table build");
+        } else {
+            cudaGetLastError();   // no compact table: the kernels read the 16-bit one
+            S->pattern8 = nullptr;
+        }
+    }
     return SKF_OK;
 }
 

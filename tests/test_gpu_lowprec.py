@@ -34,12 +34,12 @@ def upload32(skf, A):
     return skf.upload_csr(A.rowptr, A.colind, A.values, device="cuda", dtype=torch.float32)
 
 
-def arnoldi_lp(skf, A, b, m, k, s, basis, zeta=8, seed=13, identity=False):
+def arnoldi_lp(skf, A, b, m, k, s, basis, zeta=8, seed=13, identity=False, ldv=None):
     op = upload32(skf, A)
     S = skf.Sketch(skf.IDENTITY if identity else skf.SPARSE_SIGN, A.n, s, zeta, seed)
     info = skf.new_info()
     V, vs, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, torch.as_tensor(b, device="cuda"), m, k,
-                                          basis_dtype=BASIS[basis], info=info)
+                                          basis_dtype=BASIS[basis], info=info, ldv=ldv)
     torch.cuda.synchronize()
     Vn = (V.double() * vs[:, None]).cpu().numpy().T      # stored basis, columns v_j = sigma_j w_j
     return Vn, SV.cpu().numpy().T, SAV.cpu().numpy().T, H.cpu().numpy().T, skf.read_info(info)
@@ -208,3 +208,41 @@ def test_mixed_dtypes_rejected(skf):
         skf.arnoldi_trunc(op64.csr, S, b, 8, 2, basis_dtype=torch.float32)
     with pytest.raises(skf.SkfError):
         skf.arnoldi_trunc(op32.csr, S, b, 8, 2, basis_dtype=torch.float64)
+
+
+@pytest.mark.parametrize("basis", ["f32", "bf16"])
+@pytest.mark.parametrize("n,ldv", [(90, None), (1010, 1020160)])
+def test_many_chunks_per_cta(skf, basis, n, ldv):
+    """Five or more 1024-row chunks per CTA (the pipelined SpMV carries column
+    indices and slice metadata from chunk to chunk): 3D n = 90 (N = 729000)
+    and 2D n = 1010 (N = 1020100, ragged last chunk) with a padded leading
+    dimension.  Basis and sketches against the oracle."""
+    from oracle.arnoldi import arnoldi_trunc as o_arnoldi
+    A = convdiff_3d(n, (50.0, 50.0, 50.0)) if n == 90 else convdiff_2d(n, (100.0, 50.0))
+    b = gaussian_rhs(A.n, 12)
+    m, k, s = 8, 2, 48
+    V, SV, SAV, H, info = arnoldi_lp(skf, A, b, m, k, s, basis, ldv=ldv)
+    assert info["status"] == 0 and info["m_eff"] == m
+    check_sketches(A, V, SV, SAV, k, s, m)
+    if basis == "f32":
+        ar = o_arnoldi(a32(A), b, m, k, OSketch("sparse_sign", A.n, s, 8, 13))
+        for j in range(m):   # FP32 recurrence against the FP64 one: a few hundred u_32 after 8 steps
+            assert rel(V[:, j], ar["V"][:, j]) < 1e-4, j
+
+
+@pytest.mark.parametrize("zeta", [4, 8, 12])
+def test_sketch_sparsity_variants(skf, zeta):
+    """zeta = 8 takes the compact-pattern split bins; 4 and 12 the general ones."""
+    A = convdiff_2d(60)
+    b = gaussian_rhs(A.n, 12)
+    m, s = 12, 96
+    op = upload32(skf, A)
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, s, zeta, 13)
+    info = skf.new_info()
+    V, vs, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, torch.as_tensor(b, device="cuda"), m, 2,
+                                          basis_dtype=torch.float32, info=info)
+    torch.cuda.synchronize()
+    Vn = (V.double() * vs[:, None]).cpu().numpy().T
+    So = OSketch("sparse_sign", A.n, s, zeta, 13)
+    assert rel(SV.cpu().numpy().T, So @ Vn) < 1e-9
+    assert rel(SAV.cpu().numpy().T, So @ (a32(A) @ Vn)) < 1e-5
