@@ -104,9 +104,10 @@ struct LpCtx {
     SparseSign sp;
     const uint16_t *pattern;   // 16-bit sparse-sign pattern
     const uint8_t *pattern8;   // compact pattern (zeta <= 8, stripes <= 128 rows) or nullptr
+    int p8_block;              // its sign offset: 64 or 128
     const int *binmax_chunk;   // bin-load maximum of the chunk partition
     int identity;              // S = I
-    int split;                 // update bins laid out [stripe][sign][128] (compact pattern, zeta = 8)
+    int split;                 // update bins laid out [stripe][sign][p8_block] (compact pattern, zeta = 8)
     int m, k;
     void *V;                   // TB [m][ldv]
     int64_t ldv;
@@ -141,9 +142,9 @@ __device__ __forceinline__ void pattern_row(const LpCtx &c, int64_t r, int (&row
         const uint2 v = __ldg((const uint2 *)(c.pattern8 + r * 8));
 #pragma unroll
         for (int q = 0; q < ZCAP; ++q) {
-            const unsigned e = ((q < 4 ? v.x : v.y) >> (8 * (q & 3))) & 0xFFu;
-            row[q] = c.sp.start[q] + (int)(e & 0x7Fu);
-            neg[q] = (e & 0x80u) != 0u;
+            const int e = (int)(((q < 4 ? v.x : v.y) >> (8 * (q & 3))) & 0xFFu);
+            neg[q] = e >= c.p8_block;
+            row[q] = c.sp.start[q] + (neg[q] ? e - c.p8_block : e);
         }
     } else {
         uint16_t e[ZCAP];
@@ -576,7 +577,16 @@ __device__ __forceinline__ int sum_copies(const int *b, int i, int lc) {
     return v;
 }
 
-template <int KW, int ZCAP, typename TB>
+// Per-lane bin copies of the split layout: 2 * SB * 8 bins per limb, C copies,
+// 64 KB per limb either way.
+template <int SB> struct SplitGeom {
+    static constexpr int kLc = SB == 64 ? 4 : 3;
+    static constexpr int kBins = 8 * 2 * SB;
+};
+
+// SB = 0: general bins [s] per limb (signs selected), lc per-lane copies;
+// SB = 64 or 128: split bins [stripe][sign][SB] (compact pattern, zeta = 8).
+template <int KW, int ZCAP, typename TB, int SB>
 __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, int j) {
     // per-lane copies of the bins: [limb 0 | limb 1 of S w_j | residual limb][nbin << lc]
     extern __shared__ int bins[];
@@ -614,7 +624,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
     }
     const bool do_update = j < c.m - 1;
     const bool sk = !c.identity;
-    const bool split = sk && c.split;
+    constexpr bool split = SB != 0;
     const bool resid = !Store<TB>::kExact && sk && do_update;
     const int L = sk ? limb_bits(*c.binmax_chunk) : 0;
     const int P = sketch_fraction_bits_from_limb(L);
@@ -622,8 +632,8 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
     const int ew = (sk && wmax > 0.0) ? bound_exponent(wmax) : kNoExp;
     const int shift_w = P - (ew == kNoExp ? 0 : ew);
     const long long lmask = (1ll << L) - 1;
-    const int lc = c.lc, cm = (1 << lc) - 1;
-    const int ns = (split ? 8 * 256 : s) << lc;
+    const int lc = split ? SplitGeom<SB>::kLc : c.lc, cm = (1 << lc) - 1;
+    const int ns = split ? (SplitGeom<SB>::kBins << SplitGeom<SB>::kLc) : (s << lc);
     int *wb0 = bins, *wb1 = bins + ns, *db = bins + 2 * ns;
     if (sk)
         for (int i = threadIdx.x; i < (resid ? 3 : 2) * ns; i += kUpdThreads) bins[i] = 0;
@@ -682,20 +692,22 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
             int row[ZCAP];
             bool neg[ZCAP];
             uint2 pv = make_uint2(0u, 0u);
-            if (split) pv = __ldg((const uint2 *)(c.pattern8 + r * 8));
+            if constexpr (split) pv = __ldg((const uint2 *)(c.pattern8 + r * 8));
             else if (sk) pattern_row<ZCAP>(c, r, row, neg);
             if (sk && ew != kNoExp) {
                 // exact sketch of the stored w_j, per-lane bin copies
                 const long long vw = fixed_point_f32(wjr, shift_w);
                 const int l0 = (int)(vw & lmask), l1 = (int)(vw >> L);
-                if (split) {
-                    // bin (stripe << 8) | pattern byte: signs in separate bins
+                if constexpr (split) {
+                    // bin 2 SB stripe + pattern byte: signs in separate bins
+                    constexpr int LC = SplitGeom<SB>::kLc;
+                    int *b0l = wb0 + (lane & ((1 << LC) - 1)), *b1l = wb1 + (lane & ((1 << LC) - 1));
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int e = (int)__byte_perm(q < 4 ? pv.x : pv.y, 0u, 0x4440u + (q & 3));
-                        const int bi = (((q << 8) | e) << lc) | (lane & cm);
-                        atomicAdd(wb0 + bi, l0);
-                        atomicAdd(wb1 + bi, l1);
+                        const int bi = ((2 * SB * q) | e) << LC;
+                        atomicAdd(b0l + bi, l0);
+                        atomicAdd(b1l + bi, l1);
                     }
                 } else {
 #pragma unroll
@@ -722,11 +734,13 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
                 if (resid && ed != kNoExp) {
                     // wr - w is exact in FP32 (Sterbenz: wr and w lie within a factor 2)
                     const int vd = (int)fixed_point_f32(wr - w, shift_d);
-                    if (split) {
+                    if constexpr (split) {
+                        constexpr int LC = SplitGeom<SB>::kLc;
+                        int *dl = db + (lane & ((1 << LC) - 1));
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const int e = (int)__byte_perm(q < 4 ? pv.x : pv.y, 0u, 0x4440u + (q & 3));
-                            atomicAdd(db + ((((q << 8) | e) << lc) | (lane & cm)), vd);
+                            atomicAdd(dl + (((2 * SB * q) | e) << LC), vd);
                         }
                     } else {
 #pragma unroll
@@ -745,10 +759,10 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
         long long *od = c.skDp + (size_t)blockIdx.x * s;
         for (int i = warp; i < s; i += kUpdThreads / 32) {
             long long v0, v1, vd = 0;
-            if (split) {
+            if constexpr (split) {
                 int q = 0;
                 while (q + 1 < 8 && i >= c.sp.start[q + 1]) ++q;
-                const int bp = (q << 8) + (i - c.sp.start[q]), bn = bp + 128;   // positive and negative bins
+                const int bp = 2 * SB * q + (i - c.sp.start[q]), bn = bp + SB;   // positive and negative bins
                 v0 = (long long)sum_copies(wb0, bp, lc) - sum_copies(wb0, bn, lc);
                 v1 = (long long)sum_copies(wb1, bp, lc) - sum_copies(wb1, bn, lc);
                 if (resid) vd = (long long)sum_copies(db, bp, lc) - sum_copies(db, bn, lc);
@@ -846,7 +860,10 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_info_lp(LpCtx c, skf_info 
 template <int KW, int ZCAP, typename TB>
 void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, cudaStream_t st) {
     auto spmv = pipe ? k_arnoldi_spmv_lp_pipe<KW, ZCAP, TB> : k_arnoldi_spmv_lp<KW, ZCAP, TB>;
-    auto update = k_arnoldi_update_lp<KW, ZCAP, TB>;
+    auto update = k_arnoldi_update_lp<KW, ZCAP, TB, 0>;
+    if constexpr (ZCAP == 8) {
+        if (c.split) update = c.p8_block == 64 ? k_arnoldi_update_lp<KW, 8, TB, 64> : k_arnoldi_update_lp<KW, 8, TB, 128>;
+    }
     if (smem_spmv > 48 * 1024)
         cudaFuncSetAttribute(spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_spmv);
     if (smem_upd > 48 * 1024)
@@ -884,6 +901,7 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
         c.sp = make_sparse_sign(S);
         c.pattern = S->pattern;
         c.pattern8 = S->pattern8;
+        c.p8_block = S->p8_block;
         c.binmax_chunk = S->binmax_chunk;
     }
     c.sp.s = S->s;
@@ -910,12 +928,13 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     c.split = (!c.identity && S->pattern8 != nullptr && S->zeta == 8) ? 1 : 0;
     const int nlimb = bf ? 3 : 2;
-    const size_t nbin = c.split ? 8 * 256 : (size_t)s;
     const size_t static_upd = sizeof(double) * 32 * (kMaxK + 1) + sizeof(double) * kMaxK + sizeof(float) * (kMaxK + 1) +
                               256;
     c.lc = 5;
-    while (c.lc > 0 && sizeof(int) * (size_t)nlimb * (nbin << c.lc) + static_upd > (size_t)optin) --c.lc;
-    const size_t smem_upd = c.identity ? 0 : sizeof(int) * (size_t)nlimb * (nbin << c.lc);
+    while (c.lc > 0 && sizeof(int) * (size_t)nlimb * ((size_t)s << c.lc) + static_upd > (size_t)optin) --c.lc;
+    // split layout: 16 * block bins per limb, 64 / block * 128 copies: 64 KB per limb
+    const size_t per_limb = c.split ? (size_t)16 * c.p8_block * (c.p8_block == 64 ? 16 : 8) : ((size_t)s << c.lc);
+    const size_t smem_upd = c.identity ? 0 : sizeof(int) * (size_t)nlimb * per_limb;
     const size_t smem_spmv = c.identity ? 0 : sizeof(int) * 2 * (size_t)s;
     if (smem_upd + static_upd > (size_t)optin || smem_spmv > (size_t)optin)
         return fail(SKF_ERR_NOT_SUPPORTED, "sketch size s too large for the shared-memory bins");

@@ -77,9 +77,11 @@ struct skf_sketch {
     int *binmax = nullptr;            // device: most nonzeros one CTA row range puts in one row of S
     int *binmax_chunk = nullptr;      // device: the same for the chunk-interleaved partition
     // Compact pattern when every stripe has at most 128 rows and zeta <= 8:
-    // byte [c * 8 + q] = (row of nonzero q within stripe q) | sign << 7, zero
+    // byte [c * 8 + q] = (row of nonzero q within stripe q) + p8_block * sign,
+    // with p8_block = 64 if every stripe has at most 64 rows, else 128; zero
     // bytes beyond zeta; nullptr otherwise.
     uint8_t *pattern8 = nullptr;
+    int p8_block = 0;
 };
 
 namespace skf {

@@ -59,15 +59,16 @@ __global__ void k_build_pattern(SparseSign sp, int64_t n, uint16_t *__restrict__
     }
 }
 
-// The same pattern in bytes (row within stripe | sign << 7), eight per column.
-__global__ void k_build_pattern8(SparseSign sp, int64_t n, const uint16_t *__restrict__ pattern,
+// The same pattern in bytes (row within stripe + block * sign, block = 64 or
+// 128), eight per column.
+__global__ void k_build_pattern8(SparseSign sp, int64_t n, int block, const uint16_t *__restrict__ pattern,
                                  uint8_t *__restrict__ p8) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
         for (int q = 0; q < 8; ++q) {
             uint8_t v = 0;
             if (q < sp.zeta) {
                 const uint16_t e = pattern[c * sp.zeta + q];
-                v = (uint8_t)((e & 0x7Fu) | ((e >> 8) & 0x80u));
+                v = (uint8_t)((e & 0x7FFFu) + ((e >> 15) ? block : 0));
             }
             p8[c * 8 + q] = v;
         }
@@ -220,7 +221,8 @@ skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st) {
     for (int q = 0; q < sp.zeta; ++q) max_stripe = std::max(max_stripe, sp.size[q]);
     if (max_stripe <= 128 && S->zeta <= 8) {
         if (cudaMalloc(&S->pattern8, (size_t)S->n * 8) == cudaSuccess) {
-            k_build_pattern8<<<blocks, 256, 0, st>>>(sp, S->n, S->pattern, S->pattern8);
+            S->p8_block = max_stripe <= 64 ? 64 : 128;
+            k_build_pattern8<<<blocks, 256, 0, st>>>(sp, S->n, S->p8_block, S->pattern, S->pattern8);
             count_launches(1);
             e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return cuda_fail(e, "sketch table build");
