@@ -672,6 +672,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
     for (int64_t i = 0; i < nc; i += U) {
         float yv[U], wv[U][KW];
         int64_t rr[U];
+        uint2 pvu[U];   // compact pattern words (split layout), loaded with the rest
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             rr[u] = i + u < nc ? chunk_row(c, i + u) : -1;
@@ -680,6 +681,9 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
 #pragma unroll
             for (int a = 0; a < KW; ++a)
                 wv[u][a] = (ok && a < nw) ? Store<TB>::ld(V + (size_t)(i0 + a) * c.ldv + rr[u]) : 0.f;
+            pvu[u] = make_uint2(0u, 0u);
+            if constexpr (split)
+                if (ok) pvu[u] = __ldg((const uint2 *)(c.pattern8 + rr[u] * 8));
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -691,9 +695,9 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
                 if (a == nw - 1) wjr = wv[u][a];
             int row[ZCAP];
             bool neg[ZCAP];
-            uint2 pv = make_uint2(0u, 0u);
-            if constexpr (split) pv = __ldg((const uint2 *)(c.pattern8 + r * 8));
-            else if (sk) pattern_row<ZCAP>(c, r, row, neg);
+            const uint2 pv = pvu[u];
+            if constexpr (!split)
+                if (sk) pattern_row<ZCAP>(c, r, row, neg);
             if (sk && ew != kNoExp) {
                 // exact sketch of the stored w_j, per-lane bin copies
                 const long long vw = fixed_point_f32(wjr, shift_w);
