@@ -94,6 +94,31 @@ __device__ __forceinline__ long long fixed_point_f32(float x, int shift) {
 
 __device__ __forceinline__ unsigned abs_key_f32(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
 
+// The two limbs (l0, l1) of round(x 2^shift) = l1 2^L + l0, from FP32
+// operations on |x|: t = |x| 2^(shift - L) (exact scaling), l1 = floor(t), and
+// l0 = rint((t - l1) 2^L) (the fractional part of a non-negative float is
+// exact); both limbs carry the sign of x.  0 <= |l0| <= 2^L, which keeps the
+// bin sums within the limb-width rule.  Requires |x| 2^shift < 2^(2L).  The
+// scales come from LimbScale, set once per kernel.
+struct LimbScale {
+    float hi, lo;   // 2^(shift - L) (0 if outside the float range), 2^L
+    int k;          // shift - L
+    __device__ __forceinline__ LimbScale(int shift, int L) {
+        k = shift - L;
+        hi = (k >= -126 && k <= 127) ? __int_as_float((127 + k) << 23) : 0.f;
+        lo = __int_as_float((127 + L) << 23);
+    }
+};
+__device__ __forceinline__ void limbs_f32(float x, const LimbScale &ls, int &l0, int &l1) {
+    const float t = ls.hi != 0.f ? fabsf(x) * ls.hi : ldexpf(fabsf(x), ls.k);
+    const float fl = floorf(t);
+    const int h = __float2int_rz(fl);
+    const int lo = __float2int_rn((t - fl) * ls.lo);
+    const bool ng = x < 0.f;
+    l1 = ng ? -h : h;
+    l0 = ng ? -lo : lo;
+}
+
 struct LpCtx {
     int64_t n;
     const int64_t *sell_off;   // SELL-32 operator with FP32 values (see skf_csr)
@@ -631,7 +656,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
     const double wmax = c.fin_w[2 * (size_t)j + 1];
     const int ew = (sk && wmax > 0.0) ? bound_exponent(wmax) : kNoExp;
     const int shift_w = P - (ew == kNoExp ? 0 : ew);
-    const long long lmask = (1ll << L) - 1;
+    const LimbScale lsw(shift_w, L);
     const int lc = split ? SplitGeom<SB>::kLc : c.lc, cm = (1 << lc) - 1;
     const int ns = split ? (SplitGeom<SB>::kBins << SplitGeom<SB>::kLc) : (s << lc);
     int *wb0 = bins, *wb1 = bins + ns, *db = bins + 2 * ns;
@@ -700,8 +725,8 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
                 if (sk) pattern_row<ZCAP>(c, r, row, neg);
             if (sk && ew != kNoExp) {
                 // exact sketch of the stored w_j, per-lane bin copies
-                const long long vw = fixed_point_f32(wjr, shift_w);
-                const int l0 = (int)(vw & lmask), l1 = (int)(vw >> L);
+                int l0, l1;
+                limbs_f32(wjr, lsw, l0, l1);
                 if constexpr (split) {
                     // bin 2 SB stripe + pattern byte: signs in separate bins
                     constexpr int LC = SplitGeom<SB>::kLc;
