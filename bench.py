@@ -168,8 +168,9 @@ def cpu_baseline_sample(name: str, budget_s: float = 20.0):
     t_arn = time.perf_counter() - t0
     W = osk.whiten(ar["SV"], ar["SAV"], S @ b)
     t0 = time.perf_counter()
-    osk.sgmres_quadrature(W, wl.func, c, tol=1e-10)
-    osk.sfom_quadrature(W, wl.func, c, tol=1e-10)
+    ell = wl.extra.get("ell")
+    osk.sgmres_quadrature(W, wl.func, c, ell=ell, tol=1e-10)
+    osk.sfom_quadrature(W, wl.func, c, ell=ell, tol=1e-10)
     t_tail = time.perf_counter() - t0
     per_pair = t_arn * (wl.m / js) * 2 + t_tail * (wl.m / js) ** 2
     cores = len(os.sched_getaffinity(0))
@@ -295,6 +296,10 @@ def main():
     S = skf.Sketch(skf.SPARSE_SIGN, A.n, wl.s, wl.zeta, 13)
     c = quad_scale(wl.func, wl.lam_lo or 0.0, op.csr.norm_inf())
     f = skf.make_func(wl.func, c)
+    if wl.extra.get("ell"):
+        # fixed rule: every node solved in one batch
+        t_nodes, w_nodes = skf.quadrature_rule(f, int(wl.extra["ell"]))
+        f = skf.make_func(wl.func, c, nodes=t_nodes, weights=w_nodes)
     p = skf.make_params(wl.m, wl.k, basis_dtype=bdt, tol=1e-10)
     b_dev = torch.as_tensor(b, device=dev)
     x_fom = torch.empty_like(b_dev)
@@ -416,7 +421,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "N": int(A.n), "nnz": int(A.nnz), "m": wl.m, "k": wl.k,
                        "s": wl.s, "zeta": wl.zeta, "sketch": "sparse_sign", "f": wl.func, "quad_scale": c,
-                       "quad_tol": 1e-10, "parallelism": f"replicas x{world}", "l2": "flushed between steps",
+                       "quad_tol": 1e-10, "quad_rule": (f"fixed {wl.extra['ell']} nodes" if wl.extra.get("ell")
+                                                        else "adaptive"),
+                       "parallelism": f"replicas x{world}", "l2": "flushed between steps",
                        "ell_sfom": st_f["ell"], "ell_sgmres": st_g["ell"], "status": [st_f["status_name"],
                                                                                      st_g["status_name"]],
                        "basis": basis, "values": "f64" if A.values.dtype == np.float64 else "f32"},
