@@ -69,6 +69,32 @@ def reference_error_fp64(skf, A, S, b_dev, f, wl, x_fom, x_gm, dev):
             "meets_target": bool(max(e_f, e_g) <= 1e-6)}
 
 
+# ---- replicas: one independent solve stream per GPU, no data-path collective.
+# The timed region is bracketed by barriers; the job's time is the slowest
+# rank's, and its throughput counts every rank's solves.
+def replica_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def replica_max(v: float, world: int, device) -> float:
+    """Max of a per-rank value over the ranks (device: where the process
+    group's tensors live: cuda under NCCL, cpu under gloo)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, solves_per_rank: int, t_max_ms: float) -> float:
+    """Whole-job solves/s: every rank's solves over the slowest rank's time."""
+    return world * solves_per_rank / (t_max_ms / 1e3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -271,15 +297,10 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replica_barrier(world)
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, world, dev)
 
     wl, A, b = build_inputs(args.workload)
     basis = args.basis or wl.basis_dtype
@@ -341,7 +362,7 @@ def main():
     launches = skf.kernel_launch_count() - launches0
     clk = clocks.stop()
     t_max = max_over_ranks(total_ms)
-    value = world * 2 * args.steps / (t_max / 1e3)
+    value = replica_value(world, 2 * args.steps, t_max)
 
     # ---- dominant kernels: the truncated-Arnoldi step (spmv + update launches)
     V = torch.empty((wl.m, A.n), dtype=bdt, device=dev)
@@ -406,7 +427,7 @@ def main():
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_max = max_over_ranks(e2e_ms)
-    e2e_value = world * 2 * args.steps / (e2e_max / 1e3)
+    e2e_value = replica_value(world, 2 * args.steps, e2e_max)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
