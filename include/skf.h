@@ -179,7 +179,12 @@ skf_status skf_sketch_destroy(skf_sketch *S);
  * dimension s.  The sparse-sign sum is accumulated in 64/128-bit fixed point
  * scaled by each column's max |x|, so the result is independent of the
  * launch configuration (deterministic) and exact up to one rounding per
- * input entry at 2^-50 of the column max.  Errors: INVALID_ARG, OOM, CUDA. */
+ * input entry at 2^-50 of the column max.  SRHT is computed the same way:
+ * the Walsh-Hadamard transform runs exactly in int64 on blocks of up to 4096
+ * entries (H_{N'} = H_{N'/B} (x) H_B), inputs rounded at 2^-(62 - log2 B) of
+ * the column max, and the block contributions to each sampled row are summed
+ * exactly.  The SRHT is available for F64 X and, in the Arnoldi process and
+ * the solvers, for an F64 basis.  Errors: INVALID_ARG, OOM, CUDA. */
 skf_status skf_sketch_apply(const skf_sketch *S, const void *X, skf_dtype xdtype, int64_t ldx,
                             int32_t ncols, double *SX, skf_stream_t stream);
 

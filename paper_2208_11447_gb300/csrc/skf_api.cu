@@ -428,7 +428,7 @@ skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t
         if (s != n) return fail(SKF_ERR_INVALID_ARG, "identity sketch needs s == n");
         zeta = 1;
     } else if (kind == SKF_SKETCH_SRHT) {
-        return fail(SKF_ERR_NOT_SUPPORTED, "SRHT sketch not implemented in this build");
+        zeta = 0;
     } else {
         return fail(SKF_ERR_INVALID_ARG, "unknown sketch kind");
     }
@@ -438,8 +438,9 @@ skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t
     S->s = s;
     S->zeta = zeta;
     S->seed = seed;
-    if (kind == SKF_SKETCH_SPARSE_SIGN) {
-        const skf_status st = build_sparse_sign_tables(S, (cudaStream_t)stream);
+    if (kind == SKF_SKETCH_SPARSE_SIGN || kind == SKF_SKETCH_SRHT) {
+        const skf_status st =
+            kind == SKF_SKETCH_SRHT ? build_srht_tables(S) : build_sparse_sign_tables(S, (cudaStream_t)stream);
         if (st != SKF_OK) {
             skf_sketch_destroy(S);
             return st;

@@ -43,6 +43,11 @@ struct ArnCtx {
     const uint16_t *pattern;   // expanded sparse-sign pattern [n][zeta]
     const int *binmax;         // bin-load maximum of the row partition
     int identity;      // S = I
+    int sparse;        // sparse-sign S (scattered by the update kernel)
+    int srht;          // SRHT S (separate block-transform kernels after each update)
+    int sk_parts;      // integer partials per sketch column (update CTAs or SRHT blocks)
+    int srht_frac;     // SRHT fixed-point fraction bits
+    double sk_scale;   // scale of the integer sums: 1/sqrt(zeta) or 1/sqrt(s)
     int m, k;
     double *V;
     int64_t ldv;
@@ -140,12 +145,12 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
     const int G = gridDim.x;
     const int s = c.sp.s;
 
-    // S v_{j-1} and S A v_{j-1} from the integer partials of the previous update kernel
+    // S v_{j-1} and S A v_{j-1} from the integer partials of the previous step
     if (j >= 1 && !c.identity) {
-        const int frac = sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
-        const double sc = c.vscale[j - 1] * c.inv_sqrt_zeta;
-        finalize_sketch(c.skSV, c.G_upd, s, c.ews[j - 1], frac, sc, c.SV + (size_t)(j - 1) * s);
-        finalize_sketch(c.skSAV, c.G_upd, s, c.eys[j - 1], frac, sc, c.SAV + (size_t)(j - 1) * s);
+        const int frac = c.srht ? c.srht_frac : sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
+        const double sc = c.vscale[j - 1] * c.sk_scale;
+        finalize_sketch(c.skSV, c.sk_parts, s, c.ews[j - 1], frac, sc, c.SV + (size_t)(j - 1) * s);
+        finalize_sketch(c.skSAV, c.sk_parts, s, c.eys[j - 1], frac, sc, c.SAV + (size_t)(j - 1) * s);
     }
 
     // zero right-hand side (j = 0) or happy breakdown ||w_j|| <= 1e-12 ||A v_{j-1}||,
@@ -278,10 +283,10 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
     }
     // fixed-point sketches of w_j (-> S v_j) and y~ (-> S A v_j), two limbs each
     int *aw0 = bins, *aw1 = bins + s, *ay0 = bins + 2 * s, *ay1 = bins + 3 * s;
-    if (!c.identity)
+    if (c.sparse)
         for (int i = threadIdx.x; i < 4 * s; i += kUpdThreads) bins[i] = 0;
     __syncthreads();
-    const int L = c.identity ? 0 : limb_bits(*c.binmax);
+    const int L = c.sparse ? limb_bits(*c.binmax) : 0;
     const int frac = sketch_fraction_bits_from_limb(L);
     const long long lmask = (1ll << L) - 1;
     const int ew = wmax > 0.0 ? bound_exponent(wmax) : kNoExp;
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
                 if (c.identity) {
                     c.SV[r + (size_t)j * s] = sigma * wjr;
                     c.SAV[r + (size_t)j * s] = sigma * y;
-                } else {
+                } else if (c.sparse) {
                     uint16_t e[ZCAP];
                     load_pattern<ZCAP>(c.pattern, c.sp.zeta, r, e);
                     const long long vw = fixed_point(wjr, shift_w);
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
         o[1] = nmax;
         for (int a = 0; a < KW; ++a) o[2 + a] = part[1 + a];
     }
-    if (!c.identity) {
+    if (c.sparse) {
         __syncthreads();
         long long *ow = c.skSV + (size_t)blockIdx.x * s, *oy = c.skSAV + (size_t)blockIdx.x * s;
         for (int i = threadIdx.x; i < s; i += kUpdThreads) {
@@ -406,10 +411,10 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
 // After the loop: S v_{m-1} and S A v_{m-1}.
 __global__ void __launch_bounds__(kThreads) k_arnoldi_finish(ArnCtx c) {
     if (c.iscal[0] == 0 && !c.identity) {
-        const int frac = sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
-        const double sc = c.vscale[c.m - 1] * c.inv_sqrt_zeta;
-        finalize_sketch(c.skSV, c.G_upd, c.sp.s, c.ews[c.m - 1], frac, sc, c.SV + (size_t)(c.m - 1) * c.sp.s);
-        finalize_sketch(c.skSAV, c.G_upd, c.sp.s, c.eys[c.m - 1], frac, sc, c.SAV + (size_t)(c.m - 1) * c.sp.s);
+        const int frac = c.srht ? c.srht_frac : sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
+        const double sc = c.vscale[c.m - 1] * c.sk_scale;
+        finalize_sketch(c.skSV, c.sk_parts, c.sp.s, c.ews[c.m - 1], frac, sc, c.SV + (size_t)(c.m - 1) * c.sp.s);
+        finalize_sketch(c.skSAV, c.sk_parts, c.sp.s, c.eys[c.m - 1], frac, sc, c.SAV + (size_t)(c.m - 1) * c.sp.s);
     }
 }
 
@@ -444,22 +449,35 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_info(ArnCtx c, skf_info *i
 }
 
 template <int KW, int ZCAP>
-void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, cudaStream_t st) {
+void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, cudaStream_t st) {
     auto spmv = c.max_width <= 8 ? k_arnoldi_spmv<KW, 8> : k_arnoldi_spmv<KW, 16>;
     auto update = k_arnoldi_update<KW, ZCAP>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int j = 0; j < c.m; ++j) {
         spmv<<<Gs, kSpmvThreads, 0, st>>>(c, j);
         update<<<G, kUpdThreads, smem, st>>>(c, j);
+        if (sd) {   // S w_j and S y_j (exponents written by the update kernel)
+            SrhtCols cols{};
+            cols.ncols = 2;
+            cols.x[0] = c.V + (size_t)j * c.ldv;
+            cols.e[0] = c.ews + j;
+            cols.part[0] = c.skSV;
+            cols.x[1] = c.Y;
+            cols.e[1] = c.eys + j;
+            cols.part[1] = c.skSAV;
+            cols.iscal = c.iscal;
+            cols.step = j;
+            srht_launch(*sd, cols, st);
+        }
     }
 }
 
 template <int ZCAP>
-void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, cudaStream_t st) {
-    if (c.k <= 2) launch_steps<2, ZCAP>(c, G, Gs, smem, st);
-    else if (c.k <= 4) launch_steps<4, ZCAP>(c, G, Gs, smem, st);
-    else if (c.k <= 8) launch_steps<8, ZCAP>(c, G, Gs, smem, st);
-    else launch_steps<16, ZCAP>(c, G, Gs, smem, st);
+void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, cudaStream_t st) {
+    if (c.k <= 2) launch_steps<2, ZCAP>(c, G, Gs, smem, sd, st);
+    else if (c.k <= 4) launch_steps<4, ZCAP>(c, G, Gs, smem, sd, st);
+    else if (c.k <= 8) launch_steps<8, ZCAP>(c, G, Gs, smem, sd, st);
+    else launch_steps<16, ZCAP>(c, G, Gs, smem, sd, st);
 }
 
 }  // namespace
@@ -476,14 +494,22 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     c.sell_col = A->sell_col;
     c.max_width = A->max_width;
     c.identity = S->kind == SKF_SKETCH_IDENTITY;
-    if (!c.identity) {
+    c.sparse = S->kind == SKF_SKETCH_SPARSE_SIGN;
+    c.srht = S->kind == SKF_SKETCH_SRHT;
+    SrhtDev sd{};
+    if (c.sparse) {
         c.sp = make_sparse_sign(S);
         c.pattern = S->pattern;
         c.binmax = S->binmax;
     }
+    if (c.srht) {
+        sd = make_srht(S);
+        c.srht_frac = sd.frac;
+    }
     c.sp.s = S->s;
-    c.sp.zeta = c.identity ? 1 : S->zeta;
+    c.sp.zeta = c.sparse ? S->zeta : 1;
     c.inv_sqrt_zeta = 1.0 / sqrt((double)c.sp.zeta);
+    c.sk_scale = c.srht ? 1.0 / sqrt((double)S->s) : c.inv_sqrt_zeta;
     c.m = m;
     c.k = k;
     c.V = V;
@@ -500,6 +526,7 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     if (Gs < 1) Gs = 1;
     c.spmv_rows = ((A->n + Gs - 1) / Gs + 31) / 32 * 32;
     c.G_upd = G;
+    c.sk_parts = c.srht ? sd.nblk : G;
 
     char *ws = nullptr;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -510,7 +537,7 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     const size_t szFw = sizeof(double) * (size_t)(m + 1) * 2;
     const size_t szSc = sizeof(double) * (size_t)(m + 1) * 4;
     const size_t szCnt = sizeof(unsigned) * 4;
-    const size_t szSk = c.identity ? 0 : sizeof(long long) * (size_t)G * S->s;
+    const size_t szSk = c.identity ? 0 : sizeof(long long) * (size_t)c.sk_parts * S->s;
     const size_t szGram = sizeof(double) * (size_t)m * kMaxK;
     const size_t szE = sizeof(int) * (size_t)m;
     const size_t szEps = sizeof(double) * (size_t)m;
@@ -539,10 +566,11 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     c.epscol = (double *)take(szEps);
     cudaMemsetAsync(c.cnt, 0, szCnt, st);
 
-    const size_t smem = c.identity ? 0 : sizeof(int) * 4 * S->s;   // two limbs for each of S v_j, S A v_j
+    const size_t smem = c.sparse ? sizeof(int) * 4 * S->s : 0;   // two limbs for each of S v_j, S A v_j
     k_arnoldi_init<<<G, kThreads, 0, st>>>(c, b);
-    if (c.sp.zeta <= 8) launch_steps_k<8>(c, G, Gs, smem, st);
-    else launch_steps_k<16>(c, G, Gs, smem, st);
+    const SrhtDev *sdp = c.srht ? &sd : nullptr;
+    if (c.sp.zeta <= 8) launch_steps_k<8>(c, G, Gs, smem, sdp, st);
+    else launch_steps_k<16>(c, G, Gs, smem, sdp, st);
     k_arnoldi_finish<<<G, kThreads, 0, st>>>(c);
     k_arnoldi_eps<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);
     k_arnoldi_info<<<1, kThreads, 0, st>>>(c, info);

@@ -371,6 +371,33 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
                     double tol, double *x, skf_info *info, cudaStream_t st);
 
+// SRHT sketch (see skf_srht.cu): blocks of 2^b entries transformed exactly in
+// integers, b = min(kSrhtBlockLog2, log2 N').
+constexpr int kSrhtBlockLog2 = 12;
+struct SrhtDev {
+    int64_t n, np;       // N, N' = 2^ceil(log2 N)
+    int s, b, nblk;      // rows, block log2, N' / 2^b
+    int frac;            // fraction bits of the fixed-point input, 62 - b
+    uint64_t seed;
+    const int32_t *P;    // [s] sampled rows
+};
+// Up to two columns per launch: x[c] (device, N entries), the exponent bound
+// of its maximum (device int, kNoExp for a zero column) and its block
+// partials part[c][nblk][s]; with iscal non-null the launch does nothing once
+// the Arnoldi process has stopped at or before `step`.
+struct SrhtCols {
+    const double *x[2];
+    const int *e[2];
+    long long *part[2];
+    int ncols;
+    const int *iscal;
+    int step;
+};
+SrhtDev make_srht(const skf_sketch *S);
+skf_status build_srht_tables(skf_sketch *S);
+void srht_launch(const SrhtDev &d, const SrhtCols &cols, cudaStream_t st);
+skf_status srht_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX, cudaStream_t st);
+
 // Sketch-apply launcher shared by the API and the solvers.
 skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st);
 skf_status sketch_apply_f64_noalloc(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX,

@@ -245,6 +245,7 @@ skf_status sketch_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, i
         SKF_LAUNCH_CHECK("k_copy_cols");
         return SKF_OK;
     }
+    if (S->kind == SKF_SKETCH_SRHT) return srht_apply_f64(S, X, ldx, ncols, SX, st);
     if (S->kind != SKF_SKETCH_SPARSE_SIGN) return fail(SKF_ERR_NOT_SUPPORTED, "sketch kind not implemented");
     const SparseSign sp = make_sparse_sign(S);
     int G;

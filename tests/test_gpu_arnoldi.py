@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 def run_both(skf, Acsr, b, m, k, s, zeta=8, seed=13, kind="sparse_sign"):
     op = upload(skf, Acsr)
-    S = skf.Sketch(skf.SPARSE_SIGN if kind == "sparse_sign" else skf.IDENTITY, Acsr.n, s, zeta, seed)
+    S = skf.Sketch({"sparse_sign": skf.SPARSE_SIGN, "identity": skf.IDENTITY, "srht": skf.SRHT}[kind], Acsr.n, s,
+                   zeta, seed)
     info = skf.new_info()
     bt = torch.as_tensor(b, device="cuda")
     V, vs, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, bt, m, k, info=info)
@@ -98,3 +99,18 @@ def test_arnoldi_rejects_bad_arguments(skf):
         skf.arnoldi_trunc(op.csr, S, b, 10, 2)         # m >= s
     with pytest.raises(skf.SkfError):
         skf.arnoldi_trunc(op.csr, S, b, 4, 17)         # k > 16
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_arnoldi_srht_matches_oracle(skf, k):
+    """SRHT sketches of w_j and A w_j, one block-transform launch per step
+    (N = 9409, N' = 16384: four 4096-entry blocks)."""
+    A = convdiff_2d(97, (100.0, 50.0))
+    b = gaussian_rhs(A.n, 12)
+    m, s = 30, 120
+    g, ar = run_both(skf, A, b, m, k, s, kind="srht")
+    assert g["info"]["m_eff"] == m and g["info"]["status"] == 0
+    for j in range(m):
+        assert rel(g["V"][:, j], ar["V"][:, j]) < 1e-11, j
+    assert rel(g["SV"], ar["SV"]) < 1e-11
+    assert rel(g["SAV"], ar["SAV"]) < 1e-11

@@ -257,11 +257,11 @@ def test_graph_fixed_rule_128_nodes(skf):
     rounding of each new basis vector is amplified by its conditioning, so the
     FP32 result differs from the FP64 approximant by far more than on the
     convection-diffusion operators.  The check is therefore against the exact
-    f(A)b of the same rule (shifted sparse solves): the FP32 approximant may
-    be at most twice as far from it as the FP64 one (measured: 6.0e-3 against
-    3.8e-3 at m = 30)."""
+    f(A)b (dense, N = 2000; the 128-node rule's own error is far below the
+    Krylov errors compared): the FP32 approximant may be at most twice as far
+    from it as the FP64 one."""
     from oracle.quadrature import rule
-    A = powerlaw_graph_operator(6000, seed=11)
+    A = powerlaw_graph_operator(2000, seed=11)
     b = gaussian_rhs(A.n, 12)
     c = quad_scale("invsqrt", 0.1, float(abs(csr_to_scipy(A)).sum(1).max()))
     m, k, s = 30, 3, 120
@@ -277,8 +277,8 @@ def test_graph_fixed_rule_128_nodes(skf):
     xo, _ = osk.solve(csr_to_scipy(A), b, "invsqrt", m, k, OSketch("sparse_sign", A.n, s, 8, 13), c,
                       method="sgmres", ell=128)
     assert st["status"] == 0 and st["m_eff"] == m
-    from oracle.exact import fAb_shifted
-    xq = fAb_shifted(csr_to_scipy(A), b, "invsqrt", c, 128)   # same rule, exact shifted solves
+    from oracle.exact import fAb_dense
+    xq = fAb_dense(csr_to_scipy(A).toarray(), b, "invsqrt")   # exact f(A) b (dense Schur-based)
     x32 = x.cpu().numpy()
     e32, e64, d = rel(x32, xq), rel(xo, xq), rel(x32, xo)
     print(f"graph 128-node sgmres: err f32 {e32:.3e}, err f64 {e64:.3e}, f32 vs f64 {d:.3e}, "

@@ -127,3 +127,16 @@ def test_quadrature_not_converged_reported(skf):
     x, info = gpu_solve(skf, A, b, "invsqrt", 10, 2, 40, 1e-6 * c, skf.SGMRES, tol=1e-14, ell=(16, 22, 40))
     assert info["status_name"] == "SKF_ERR_QUAD_NOT_CONVERGED" and info["ell"] == 31
     assert np.all(np.isfinite(x))
+
+
+@pytest.mark.parametrize("method", ["sgmres", "sfom"])
+def test_config1_srht(skf, method):
+    """Config-1 operator with the SRHT sketch (s = 160, N' = 16384)."""
+    A, b, c = config1()
+    m, k, s = 40, 2, 160
+    x, info = gpu_solve(skf, A, b, "invsqrt", m, k, s, c, skf.SGMRES if method == "sgmres" else skf.SFOM,
+                        kind=skf.SRHT, zeta=0)
+    xo, oi = osk.solve(csr_to_scipy(A), b, "invsqrt", m, k, OSketch("srht", A.n, s, 0, 13), c,
+                       method="sgmres" if method == "sgmres" else "sfom_quad", tol=1e-12)
+    assert info["status"] == 0 and info["m_eff"] == m
+    assert rel(x, xo) <= TOL
