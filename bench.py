@@ -34,9 +34,9 @@ HBM_PEAK_FALLBACK = 6800.0
 # throughput on this part: 1.20 TFLOP/s, i.e. the same unit count).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes (read + write) per Arnoldi step, summed over the spmv and update
-# kernels of one ncu capture of those kernels as they stand; keyed by workload
-# and basis dtype, and removed whenever those kernels change.
-NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64"): 146.4e6, ("cd3d_n256_fp32", "f32"): 1515.9e6}
+# kernels of one ncu capture of those kernels as they stand; keyed by workload,
+# basis dtype and sketch, and removed whenever those kernels change.
+NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64", "sparse_sign"): 146.4e6, ("cd3d_n256_fp32", "f32", "sparse_sign"): 1515.9e6}
 
 
 BASIS_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
@@ -44,6 +44,9 @@ DTYPE_NAME = {"f64": "f64", "f32": "f32", "bf16": "bf16-storage/f32"}
 METRIC = {"f64": "f(A)b solves/s (sFOM + sGMRES, FP64)",
           "f32": "f(A)b solves/s (sFOM + sGMRES, FP32 basis and arithmetic, FP64 tail)",
           "bf16": "f(A)b solves/s (sFOM + sGMRES, BF16 basis, FP32 arithmetic, FP64 tail)"}
+
+
+SKETCH_KIND = {"sparse_sign": lambda skf: skf.SPARSE_SIGN, "srht": lambda skf: skf.SRHT}
 
 
 def basis_torch(name: str):
@@ -170,7 +173,7 @@ class ClockSampler:
         return out
 
 
-def cpu_baseline_sample(name: str, budget_s: float = 20.0):
+def cpu_baseline_sample(name: str, budget_s: float = 20.0, sketch: str = "sparse_sign"):
     """The oracle, as it stands, on a bounded sample of the workload: the
     first j_s Arnoldi steps at full N (scaled to m linearly) and both tails
     (sFOM by quadrature, sGMRES) on the j_s-column sample, scaled by (m/j_s)^2
@@ -183,7 +186,7 @@ def cpu_baseline_sample(name: str, budget_s: float = 20.0):
     from workloads.configs import quad_scale
     wl, A, b = build_inputs(name)
     As = csr_to_scipy(A.astype(np.float64))
-    S = Sketch("sparse_sign", A.n, wl.s, wl.zeta, 13)
+    S = Sketch(sketch, A.n, wl.s, wl.zeta, 13)
     c = quad_scale(wl.func, wl.lam_lo or 0.0, float(abs(As).sum(1).max()))
     t0 = time.perf_counter()
     ar = arnoldi_trunc(As, b, 2, wl.k, S)
@@ -214,12 +217,12 @@ def run_reference(args, rank: int):
         return
     wl, A, _ = build_inputs(args.workload)
     for _ in range(args.warmup):
-        cpu_baseline_sample(args.workload, budget_s=1.0)
+        cpu_baseline_sample(args.workload, budget_s=1.0, sketch=args.sketch)
     budget = min(args.ref_budget, 150.0 / max(1, args.steps))
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        cb = cpu_baseline_sample(args.workload, budget_s=budget)
+        cb = cpu_baseline_sample(args.workload, budget_s=budget, sketch=args.sketch)
         vals.append(cb["value"])
     wall = time.perf_counter() - t0
     value = statistics.mean(vals)
@@ -228,7 +231,7 @@ def run_reference(args, rank: int):
             "ms_per_step": 2000.0 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "N": int(A.n), "nnz": int(A.nnz), "m": wl.m, "k": wl.k,
-                       "s": wl.s, "zeta": wl.zeta, "sketch": "sparse_sign", "f": wl.func},
+                       "s": wl.s, "zeta": wl.zeta, "sketch": args.sketch, "f": wl.func},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -242,7 +245,7 @@ def run_arnoldi_only(args, wl, A, b, op, dev, rank, world):
     import paper_2208_11447_gb300 as skf
     m = args.m or wl.m
     bdt = basis_torch(args.basis)
-    S = skf.Sketch(skf.SPARSE_SIGN, A.n, wl.s, wl.zeta, 13)
+    S = skf.Sketch(SKETCH_KIND[args.sketch](skf), A.n, wl.s, wl.zeta, 13)
     b_dev = torch.as_tensor(b, device=dev)
     for _ in range(args.warmup):
         skf.arnoldi_trunc(op.csr, S, b_dev, m, wl.k, basis_dtype=bdt)
@@ -274,6 +277,8 @@ def main():
     ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi"],
                     help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu")
     ap.add_argument("--m", type=int, default=None, help="override the Krylov dimension (arnoldi mode)")
+    ap.add_argument("--sketch", default="sparse_sign", choices=["sparse_sign", "srht"],
+                    help="subspace embedding: sparse-sign (zeta nonzeros per column) or SRHT")
     ap.add_argument("--basis", default=None, choices=["f64", "f32", "bf16"],
                     help="basis storage (default: the workload's); f32/bf16 need an FP32 operator")
     args = ap.parse_args()
@@ -314,7 +319,7 @@ def main():
     if args.mode == "arnoldi":
         run_arnoldi_only(args, wl, A, b, op, dev, rank, world)
         return
-    S = skf.Sketch(skf.SPARSE_SIGN, A.n, wl.s, wl.zeta, 13)
+    S = skf.Sketch(SKETCH_KIND[args.sketch](skf), A.n, wl.s, wl.zeta, 13)
     c = quad_scale(wl.func, wl.lam_lo or 0.0, op.csr.norm_inf())
     f = skf.make_func(wl.func, c)
     if wl.extra.get("ell"):
@@ -401,8 +406,10 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src}
-    roof["traffic"] = NCU_TRAFFIC_PER_STEP.get((args.workload, basis))
+    roof["traffic"] = NCU_TRAFFIC_PER_STEP.get((args.workload, basis, args.sketch))
     kname = "k_arnoldi_spmv + k_arnoldi_update" if basis == "f64" else "k_arnoldi_spmv_lp + k_arnoldi_update_lp"
+    if args.sketch == "srht":
+        kname += " + k_srht_blocks"
     roof.update({"kernel": f"truncated-Arnoldi step ({kname})", "us_per_step": round(step_us, 2),
                  "alg_bytes_per_step": alg_bytes, "alg_flops_per_step": alg_flops,
                  "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak,
@@ -431,7 +438,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline_sample(args.workload, budget_s=args.ref_budget)
+        cb = cpu_baseline_sample(args.workload, budget_s=args.ref_budget, sketch=args.sketch)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if rank == 0:
@@ -441,7 +448,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[basis],
             "data": "synthetic",
             "config": {"workload": args.workload, "N": int(A.n), "nnz": int(A.nnz), "m": wl.m, "k": wl.k,
-                       "s": wl.s, "zeta": wl.zeta, "sketch": "sparse_sign", "f": wl.func, "quad_scale": c,
+                       "s": wl.s, "zeta": wl.zeta, "sketch": args.sketch, "f": wl.func, "quad_scale": c,
                        "quad_tol": 1e-10, "quad_rule": (f"fixed {wl.extra['ell']} nodes" if wl.extra.get("ell")
                                                         else "adaptive"),
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps",
