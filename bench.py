@@ -264,6 +264,232 @@ def run_arnoldi_only(args, wl, A, b, op, dev, rank, world):
                           "us_per_step": round(us, 2)}), flush=True)
 
 
+
+# ----------------------------------------------------------------- batched workload
+BATCH_TOL = 1e-6          # error gate of a batched FP32-basis solve against the FP64 one
+BATCH_FUNC = "invsqrt"
+
+
+def batch_inputs(n_rhs: int):
+    """Host inputs of the batched workload: the seeded layout, its operators
+    (FP32-rounded values), quadrature scales and right-hand sides."""
+    from workloads.batch import batch_layout, quad_scale_invsqrt
+    layout = batch_layout(n_rhs=n_rhs)
+    ops = []
+    for M in layout.mats:
+        A = M.operator()
+        ops.append((A, quad_scale_invsqrt(A, M.lam_lo())))
+    rhs = [r.rhs(layout.mats[r.mat].N) for r in layout.rhs]
+    return layout, ops, rhs
+
+
+def cpu_batch_sample(layout, ops, rhs, budget_s: float = 20.0):
+    """The oracle, as it stands, on a bounded sample of the batched workload:
+    a few Arnoldi steps of one right-hand side on each operator (per-step
+    time per operator), and the sGMRES tail on a j_t-column basis of the
+    smallest operator (its cost depends on m and s = 4m only); scaled to the
+    batch as sum_r (m_r t_step(A_r) + (m_r / j_t)^3 t_tail)."""
+    import numpy as np
+    from oracle import sketched as osk
+    from oracle.arnoldi import arnoldi_trunc
+    from oracle.sketch import Sketch
+    from workloads import csr_to_scipy
+    per_op = max(0.5, 0.5 * budget_s / len(ops))
+    t_step = []
+    spent = 0.0
+    for i, (A, c) in enumerate(ops):
+        r = next(j for j, q in enumerate(layout.rhs) if q.mat == i)
+        q = layout.rhs[r]
+        As = csr_to_scipy(A.astype(np.float64))
+        S = Sketch("sparse_sign", A.n, q.s, 8, q.sketch_seed)
+        t0 = time.perf_counter()
+        arnoldi_trunc(As, rhs[r], 2, 2, S)
+        probe = (time.perf_counter() - t0) / 2
+        js = int(max(2, min(q.m, per_op // max(probe, 1e-6))))
+        t0 = time.perf_counter()
+        arnoldi_trunc(As, rhs[r], js, 2, S)
+        dt = time.perf_counter() - t0
+        spent += dt
+        t_step.append(dt / js)
+    i0 = min(range(len(ops)), key=lambda i: ops[i][0].n)
+    A, c = ops[i0]
+    r = next(j for j, q in enumerate(layout.rhs) if q.mat == i0)
+    jt = 48
+    As = csr_to_scipy(A.astype(np.float64))
+    S = Sketch("sparse_sign", A.n, 4 * jt, 8, layout.rhs[r].sketch_seed)
+    ar = arnoldi_trunc(As, rhs[r], jt, 2, S)
+    W = osk.whiten(ar["SV"], ar["SAV"], S @ rhs[r])
+    t0 = time.perf_counter()
+    osk.sgmres_quadrature(W, BATCH_FUNC, c, tol=1e-10)
+    t_tail = time.perf_counter() - t0
+    spent += t_tail
+    total = sum(q.m * t_step[q.mat] + (q.m / jt) ** 3 * t_tail for q in layout.rhs)
+    return {"value": len(layout.rhs) / total, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle",
+            "sample": f"per operator a few Arnoldi steps of one right-hand side at full N (per-step time x m_r "
+                      f"for each of its right-hand sides) + one sGMRES tail on a {jt}-column basis, s = {4 * jt} "
+                      f"(x (m_r/{jt})^3); SciPy CSR matvec single-threaded",
+            "seconds": round(spent, 2)}
+
+
+def run_reference_batch(args, rank: int):
+    if rank != 0:
+        return
+    layout, ops, rhs = batch_inputs(args.batch_rhs)
+    for _ in range(args.warmup):
+        cpu_batch_sample(layout, ops, rhs, budget_s=1.0)
+    budget = min(args.ref_budget, 150.0 / max(1, args.steps))
+    vals = [cpu_batch_sample(layout, ops, rhs, budget_s=budget) for _ in range(args.steps)]
+    value = statistics.mean(v["value"] for v in vals)
+    cb = vals[-1]
+    print(json.dumps({
+        "metric": "f(A)b solves/s at rel err <= 1e-6 (batched sGMRES)", "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": len(layout.rhs) * 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "batch_cd_8x64", **layout.summary()},
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+        flush=True)
+
+
+def run_batch(args, rank, world, local, dev):
+    """Batched workload: the FP32-basis batch (skf_solve_batched captured
+    into one CUDA graph, replayed once per step) against the plain FP64 path
+    solving the same problems one at a time (skf_sgmres per problem, same
+    operators, sketches, right-hand sides and rule)."""
+    import numpy as np
+    import torch
+    import paper_2208_11447_gb300 as skf
+
+    layout, ops, rhs = batch_inputs(args.batch_rhs)
+    nprob = len(layout.rhs)
+    op32, op64 = [], []
+    for A, c in ops:
+        op32.append(skf.upload_csr(A.rowptr, A.colind, A.values, device=dev))
+        op64.append(skf.upload_csr(A.rowptr, A.colind, A.values.astype(np.float64), device=dev))
+    sketches, funcs, b_dev = [], [], []
+    for q, b in zip(layout.rhs, rhs):
+        sketches.append(skf.Sketch(skf.SPARSE_SIGN, layout.mats[q.mat].N, q.s, 8, q.sketch_seed))
+        funcs.append(skf.make_func(BATCH_FUNC, ops[q.mat][1]))
+        b_dev.append(torch.as_tensor(b, device=dev))
+    p32 = [skf.make_params(q.m, 2, basis_dtype=torch.float32, tol=1e-10) for q in layout.rhs]
+    p64 = [skf.make_params(q.m, 2, basis_dtype=torch.float64, tol=1e-10) for q in layout.rhs]
+    x32 = [torch.empty_like(b) for b in b_dev]
+    x64 = [torch.empty_like(b) for b in b_dev]
+    inf32 = [skf.new_info(dev) for _ in range(nprob)]
+    inf64 = [skf.new_info(dev) for _ in range(nprob)]
+    probs32 = [(skf.SGMRES, op32[q.mat].csr, sketches[r], b_dev[r], funcs[r], p32[r], x32[r], inf32[r])
+               for r, q in enumerate(layout.rhs)]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def fp64_one_at_a_time():
+        for r, q in enumerate(layout.rhs):
+            skf.sgmres(op64[q.mat].csr, sketches[r], b_dev[r], funcs[r], p64[r], x=x64[r], info=inf64[r])
+
+    def timed(fn, steps):
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            fn()
+            ev1.record(stream)
+            ev1.synchronize()
+            tot += ev0.elapsed_time(ev1)
+        return tot
+
+    # plain FP64 path, one problem at a time
+    for _ in range(args.warmup):
+        fp64_one_at_a_time()
+    torch.cuda.synchronize()
+    replica_barrier(world)
+    t64 = replica_max(timed(fp64_one_at_a_time, args.steps), world, dev)
+
+    # FP32-basis batch as one CUDA graph
+    l0 = skf.kernel_launch_count()
+    graph = skf.BatchGraph(probs32, lanes=args.lanes)     # one eager run + capture
+    launches_per_batch = (skf.kernel_launch_count() - l0) // 2
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    replica_barrier(world)
+    torch.cuda.synchronize()
+    t32 = replica_max(timed(graph.replay, args.steps), world, dev)
+    replica_barrier(world)
+    clk = clocks.stop()
+
+    # accuracy: FP32-basis batch against the FP64 path, per problem
+    errs = []
+    for a, b in zip(x32, x64):
+        errs.append(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)))
+    st32 = [skf.read_info(i)["status_name"] for i in inf32]
+    st64 = [skf.read_info(i)["status_name"] for i in inf64]
+    n_ok = sum(1 for e in errs if e <= BATCH_TOL)
+
+    # end to end: right-hand sides from pinned host memory, results back
+    b_host = [torch.as_tensor(b).pin_memory() for b in rhs]
+    x_host = [torch.empty(b.numel(), dtype=torch.float64).pin_memory() for b in b_dev]
+    e2e_ms = 0.0
+    replica_barrier(world)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for bd, bh in zip(b_dev, b_host):
+            bd.copy_(bh, non_blocking=True)
+        graph.replay()
+        for xh, xd in zip(x_host, x32):
+            xh.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_ms = replica_max(e2e_ms, world, dev)
+
+    value = replica_value(world, nprob * args.steps, t32)
+    v64 = replica_value(world, nprob * args.steps, t64)
+    e2e_value = replica_value(world, nprob * args.steps, e2e_ms)
+    # whole-batch effective bandwidth over the algorithmic Arnoldi bytes
+    alg = 0
+    for q in layout.rhs:
+        A = ops[q.mat][0]
+        alg += q.m * (A.nnz * 8 + 4 * (A.n + 1) + 3 * A.n * 4)
+    hbm_peak, hbm_src = measured_peaks()
+    gbs = alg / (t32 / args.steps * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_batch_sample(layout, ops, rhs, budget_s=args.ref_budget)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        nbytes_b = int(sum(b.nbytes for b in rhs))
+        print(json.dumps({
+            "metric": "f(A)b solves/s at rel err <= 1e-6 (batched sGMRES, FP32 basis)",
+            "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t32 / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch_cd_8x64", **layout.summary(), "k": 2, "s": "4 m_r", "zeta": 8,
+                       "f": BATCH_FUNC, "method": "sgmres", "quad_tol": 1e-10, "basis": "f32", "values": "f32",
+                       "lanes": args.lanes, "graph": "one CUDA graph per batch",
+                       "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
+            "fp64_one_at_a_time": {"value": round(v64, 3), "unit": "solves/s",
+                                   "ms_per_batch": round(t64 / args.steps, 3)},
+            "speedup_vs_fp64_one_at_a_time": round(value / v64, 3),
+            "accuracy": {"vs": "FP64 GPU path, same problems", "max_rel_err": max(errs),
+                         "median_rel_err": statistics.median(errs), "within_1e-6": n_ok, "of": nprob,
+                         "status_f32": sorted(set(st32)), "status_f64": sorted(set(st64))},
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src,
+                         "kernel": "whole batch: algorithmic Arnoldi bytes (sum_r m_r (B_A + 3 N 4)) over the "
+                                   "batch time, tails included"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": nbytes_b,
+                    "d2h_bytes_per_step": nbytes_b},
+            "gpu_launches": int(launches_per_batch * args.steps),
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+        }), flush=True)
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,8 +500,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--arnoldi-reps", type=int, default=5)
-    ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi"],
-                    help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu")
+    ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi", "batch"],
+                    help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu; "
+                         "batch: the batched workload (8 operators, 64 right-hand sides) as one CUDA graph")
+    ap.add_argument("--lanes", type=int, default=4, help="concurrent streams of the batched solve (batch mode)")
+    ap.add_argument("--batch-rhs", type=int, default=64, help="right-hand sides of the batched workload")
     ap.add_argument("--m", type=int, default=None, help="override the Krylov dimension (arnoldi mode)")
     ap.add_argument("--sketch", default="sparse_sign", choices=["sparse_sign", "srht"],
                     help="subspace embedding: sparse-sign (zeta nonzeros per column) or SRHT")
@@ -287,7 +516,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        run_reference(args, rank)
+        if args.mode == "batch":
+            run_reference_batch(args, rank)
+        else:
+            run_reference(args, rank)
         return
 
     import numpy as np
@@ -306,6 +538,12 @@ def main():
 
     def max_over_ranks(v: float) -> float:
         return replica_max(v, world, dev)
+
+    if args.mode == "batch":
+        run_batch(args, rank, world, local, dev)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     wl, A, b = build_inputs(args.workload)
     basis = args.basis or wl.basis_dtype

@@ -257,6 +257,46 @@ skf_status skf_sgmres(const skf_csr *A, const skf_sketch *S, const void *b, skf_
                       const skf_func *f, const skf_params *p, void *x, skf_dtype xdtype, skf_info *info,
                       skf_stream_t stream);
 
+/* ------------------------------------------------------------- batches */
+/* One independent problem of a batch: the arguments of one skf_solve call. */
+typedef struct {
+    skf_method method;
+    const skf_csr *A;
+    const skf_sketch *S;
+    const void *b;          /* device F64 [N] */
+    skf_dtype bdtype;
+    const skf_func *f;      /* host; read during the call only */
+    const skf_params *p;    /* host; read during the call only */
+    void *x;                /* device F64 [N] (output) */
+    skf_dtype xdtype;
+    skf_info *info;         /* device-writable, or NULL */
+} skf_problem;
+
+/* skf_solve_batched: nprob independent f(A)b problems (each one exactly the
+ * approximant skf_solve computes for its arguments; the paper solves one
+ * f(A)b at a time, batching is a throughput form of the same computation).
+ * Problems may share operators and sketches and may differ in N, m, k, s,
+ * f and method.  The problems are spread over `lanes` (1..16) internal CUDA
+ * streams that fork from `stream` and join it again, longest estimated work
+ * first onto the least-loaded lane, so that the kernels of small problems
+ * and the latency-bound tails run side by side on the GPU.  Every problem's
+ * result is bit-identical to the result of its own skf_solve call (the
+ * kernels' reductions have a fixed order).
+ *   All problems are validated before anything is enqueued: on an argument
+ *   error nothing runs and the message names the problem's index.
+ *   Work is ordered after earlier work on `stream`, and later work on
+ *   `stream` waits for all of it, so the whole call can be captured into
+ *   one CUDA graph and replayed as one launch.  The first call on a device
+ *   creates the lane streams and the first use of a quadrature rule uploads
+ *   it (both synchronous, host-side): make one call outside capture first.
+ *   Calls from several host threads are serialised inside the library.
+ *   Outputs x must not alias each other or any input.
+ *   Device memory: each running problem holds the workspace of its
+ *   skf_solve (V_m and the sketches), so up to `lanes` of them are live.
+ * Errors: INVALID_ARG (also nprob < 0, lanes outside 1..16), OOM, CUDA,
+ *   SKETCH_TOO_SMALL, NOT_SUPPORTED. */
+skf_status skf_solve_batched(int32_t nprob, const skf_problem *probs, int32_t lanes, skf_stream_t stream);
+
 /* skf_quadrature_rule: host copy of the rule of order ell for f (the same
  * nodes and weights the solvers use).  t_host, w_host: host double[ell]. */
 skf_status skf_quadrature_rule(const skf_func *f, int32_t ell, double *t_host, double *w_host);

@@ -59,6 +59,13 @@ class Info(ctypes.Structure):
         return d
 
 
+class Problem(ctypes.Structure):
+    """skf_problem: the arguments of one skf_solve call inside a batch."""
+    _fields_ = [("method", ctypes.c_int), ("A", ctypes.c_void_p), ("S", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("bdtype", ctypes.c_int), ("f", ctypes.POINTER(Func)), ("p", ctypes.POINTER(Params)),
+                ("x", ctypes.c_void_p), ("xdtype", ctypes.c_int), ("info", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -89,9 +96,10 @@ def lib():
         L.skf_sfom.argtypes = L.skf_solve.argtypes[1:]
         L.skf_sgmres.argtypes = L.skf_solve.argtypes[1:]
         L.skf_quadrature_rule.argtypes = [ctypes.POINTER(Func), i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        L.skf_solve_batched.argtypes = [i32, ctypes.POINTER(Problem), i32, vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
-                     "skf_solve", "skf_sfom",
+                     "skf_solve", "skf_solve_batched", "skf_sfom",
                      "skf_sgmres", "skf_quadrature_rule"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -256,6 +264,41 @@ def sfom(A, S, b, f, p, x=None, info=None, stream=None):
 
 def sgmres(A, S, b, f, p, x=None, info=None, stream=None):
     return solve(SGMRES, A, S, b, f, p, x, info, stream)
+
+
+def solve_batched(problems, lanes: int = 4, stream=None):
+    """skf_solve_batched.  problems: sequence of (method, A, S, b, f, p, x,
+    info) with x a preallocated F64 tensor and info a buffer from new_info()
+    or None.  Returns the list of x."""
+    arr = (Problem * len(problems))()
+    for i, (method, A, S, b, f, p, x, info) in enumerate(problems):
+        arr[i] = Problem(method, A.handle, S.handle, b.data_ptr(), _DTYPE[b.dtype], ctypes.pointer(f),
+                         ctypes.pointer(p), x.data_ptr(), _DTYPE[x.dtype], info.data_ptr() if info is not None else 0)
+    _check(lib().skf_solve_batched(len(problems), arr, lanes, _stream(stream)))
+    return [q[6] for q in problems]
+
+
+class BatchGraph:
+    """A fixed batch of problems captured once into a CUDA graph.
+
+    The constructor runs the batch once outside capture (this creates the
+    library's lane streams and uploads the quadrature rules), then captures
+    one skf_solve_batched call; replay() enqueues the whole batch as one
+    graph launch on the current stream.  The tensors of `problems` must stay
+    alive and in place: replays read b and write x where capture found them."""
+
+    def __init__(self, problems, lanes: int = 4):
+        self.problems = list(problems)
+        self.lanes = lanes
+        solve_batched(self.problems, lanes)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            solve_batched(self.problems, lanes)
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()
 
 
 def kernel_launch_count() -> int:

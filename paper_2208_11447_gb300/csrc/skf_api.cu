@@ -252,6 +252,163 @@ __global__ void k_sell_fill(const int32_t *__restrict__ rp, const int32_t *__res
     }
 }
 
+
+static skf_status check_common(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, int m, int k,
+                               skf_dtype basis) {
+    if (!A || !S || !b) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    if (S->n != A->n) return fail(SKF_ERR_INVALID_ARG, "sketch and matrix sizes differ");
+    if (m < 1 || m >= S->s) return fail(SKF_ERR_INVALID_ARG, "need 1 <= m < s");
+    if (m > A->n) return fail(SKF_ERR_INVALID_ARG, "need m <= n");
+    if (k < 1 || k > kMaxK) return fail(SKF_ERR_INVALID_ARG, "need 1 <= k <= 16");
+    if (bdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "b must be F64 in this build");
+    if (basis == SKF_F64) {
+        if (A->vdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "an F64 basis needs F64 matrix values");
+    } else if (basis == SKF_F32 || basis == SKF_BF16) {
+        if (A->vdtype != SKF_F32) return fail(SKF_ERR_NOT_SUPPORTED, "an F32 or BF16 basis needs F32 matrix values");
+        if (S->kind != SKF_SKETCH_SPARSE_SIGN && S->kind != SKF_SKETCH_IDENTITY)
+            return fail(SKF_ERR_NOT_SUPPORTED, "sketch kind not implemented");
+    } else {
+        return fail(SKF_ERR_INVALID_ARG, "unknown basis dtype");
+    }
+    return SKF_OK;
+}
+
+static size_t dtype_size(skf_dtype d) { return d == SKF_F64 ? 8 : d == SKF_F32 ? 4 : 2; }
+
+static skf_status run_arnoldi(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, skf_dtype basis,
+                              void *V, int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
+                              skf_info *info, cudaStream_t cs) {
+    if (basis == SKF_F64) return arnoldi_run(A, S, b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+    if (basis == SKF_F32) return arnoldi_run_f32(A, S, b, m, k, (float *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+    return arnoldi_run_bf16(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+}
+
+// ------------------------------------------------------------ solve parts
+// Argument validation of one skf_solve call and its quadrature rule (host
+// work only; may upload a new rule synchronously).
+static skf_status solve_check(skf_method method, const skf_csr *A, const skf_sketch *S, const void *b,
+                              skf_dtype bdtype, const skf_func *f, const skf_params *p, const void *x,
+                              skf_dtype xdtype, const RuleDev **rule) {
+    if (!f || !p || !x) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    skf_status st = check_common(A, S, b, bdtype, p->m, p->k, p->basis_dtype);
+    if (st != SKF_OK) return st;
+    if (method != SKF_METHOD_SFOM && method != SKF_METHOD_SGMRES) return fail(SKF_ERR_INVALID_ARG, "bad method");
+    if (xdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "x must be F64 in this build");
+    if (p->m > 512) return fail(SKF_ERR_NOT_SUPPORTED, "m > 512 is not supported by the dense tail");
+    if (method == SKF_METHOD_SGMRES && S->s < 2 * p->m)
+        return fail(SKF_ERR_SKETCH_TOO_SMALL, "sGMRES needs s >= 2m");
+    if (f->n_nodes < 0 || (f->n_nodes > 0 && (!f->nodes || !f->weights)))
+        return fail(SKF_ERR_INVALID_ARG, "bad explicit rule");
+    if (f->n_nodes == 0 && f->kind != SKF_FUNC_INV) {
+        if (!(f->scale > 0.0)) return fail(SKF_ERR_INVALID_ARG, "rule scale must be > 0");
+        if (p->ell1 < 1 || p->ell2 <= p->ell1 || p->ell2 < 3 || p->ell_max < p->ell2)
+            return fail(SKF_ERR_INVALID_ARG, "need 1 <= ell1 < ell2, ell2 >= 3, ell_max >= ell2");
+        if (!(p->tol > 0.0)) return fail(SKF_ERR_INVALID_ARG, "tol must be > 0");
+    }
+    if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5 && f->n_nodes == 0)
+        return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
+    return get_rule(*f, *p, rule);
+}
+
+// Enqueue one validated solve on `cs`: stream-ordered workspace, the
+// Arnoldi process, the tail, release of the workspace.
+static skf_status solve_enqueue(skf_method method, const skf_csr *A, const skf_sketch *S, const void *b,
+                                const skf_params &p, void *x, skf_info *info, const RuleDev &rule, cudaStream_t cs) {
+    const int m = p.m;
+    const int64_t n = A->n;
+    const int s = S->s;
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const skf_dtype bt = p.basis_dtype;
+    const int64_t ldv = (n + 63) / 64 * 64;   // 256-byte aligned columns
+    const size_t szV = dtype_size(bt) * (size_t)ldv * m;
+    const size_t szS = sizeof(double) * (size_t)s * m;
+    const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
+    const size_t total = al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4);
+    char *ws = nullptr;
+    skf_status st = dalloc((void **)&ws, total, cs);
+    if (st != SKF_OK) return st;
+    size_t off = 0;
+    void *V = (void *)(ws + off); off += al(szV);
+    double *SV = (double *)(ws + off); off += al(szS);
+    double *SAV = (double *)(ws + off); off += al(szS);
+    double *H = (double *)(ws + off); off += al(szH);
+    double *vscale = (double *)(ws + off); off += al(sizeof(double) * m);
+    int *iscal = (int *)(ws + off);
+    st = run_arnoldi(A, S, (const double *)b, m, p.k, bt, V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+    if (st == SKF_OK)
+        st = tail_run(method, s, m, n, V, bt, ldv, vscale, SV, SAV, iscal, rule, p.tol, (double *)x, info, cs);
+    dfree(ws, cs);
+    return st;
+}
+
+// ---------------------------------------------------------------- lanes
+constexpr int kMaxLanes = 16;
+
+// Non-blocking streams and fork/join events of skf_solve_batched, created
+// once per device and kept until the process exits.
+struct LanePool {
+    cudaStream_t s[kMaxLanes];
+    cudaEvent_t join[kMaxLanes];
+    cudaEvent_t fork;
+};
+
+static std::mutex &lane_mutex() {
+    static std::mutex *mu = new std::mutex();
+    return *mu;
+}
+
+// Caller holds lane_mutex().
+static skf_status lane_pool(LanePool **out) {
+    static std::map<int, LanePool *> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    auto it = pools.find(dev);
+    if (it != pools.end()) {
+        *out = it->second;
+        return SKF_OK;
+    }
+    LanePool *p = new LanePool();
+    e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    for (int l = 0; l < kMaxLanes && e == cudaSuccess; ++l) {
+        e = cudaStreamCreateWithFlags(&p->s[l], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[l], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "lane stream creation");   // partial pool leaks; rare
+    pools[dev] = p;
+    *out = p;
+    return SKF_OK;
+}
+
+// Estimated device seconds of one problem: m steps, each the larger of its
+// streamed bytes at HBM speed and a launch-latency floor, plus a tail that
+// grows with m (Householder columns and quadrature nodes).
+static double solve_cost(const skf_problem &q) {
+    const double vb = (double)dtype_size(q.p->basis_dtype);
+    const double ab = (double)dtype_size(q.A->vdtype) + 4.0;
+    const double bytes = (double)q.A->nnz * ab + 3.0 * (double)q.A->n * vb;
+    const double step = std::max(bytes / 6.0e12, 12.0e-6);
+    return q.p->m * (step + 40.0e-6);
+}
+
+// Longest-processing-time-first: problems by decreasing cost, each onto the
+// lane with the least work so far (ties: lowest lane, then lowest index).
+static void assign_lanes(int n, const skf_problem *probs, int L, int *lane_of, int *order) {
+    std::vector<double> cost((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        cost[i] = solve_cost(probs[i]);
+        order[i] = i;
+    }
+    std::stable_sort(order, order + n, [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load((size_t)L, 0.0);
+    for (int t = 0; t < n; ++t) {
+        const int i = order[t];
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lane_of[i] = l;
+        load[l] += cost[i];
+    }
+}
+
 }  // namespace
 }  // namespace skf
 
@@ -476,36 +633,6 @@ skf_status skf_sketch_apply_noalloc(const skf_sketch *S, const void *X, skf_dtyp
     return sketch_apply_f64_noalloc(S, (const double *)X, ldx, ncols, SX, (cudaStream_t)stream);
 }
 
-static skf_status check_common(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, int m, int k,
-                               skf_dtype basis) {
-    if (!A || !S || !b) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
-    if (S->n != A->n) return fail(SKF_ERR_INVALID_ARG, "sketch and matrix sizes differ");
-    if (m < 1 || m >= S->s) return fail(SKF_ERR_INVALID_ARG, "need 1 <= m < s");
-    if (m > A->n) return fail(SKF_ERR_INVALID_ARG, "need m <= n");
-    if (k < 1 || k > kMaxK) return fail(SKF_ERR_INVALID_ARG, "need 1 <= k <= 16");
-    if (bdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "b must be F64 in this build");
-    if (basis == SKF_F64) {
-        if (A->vdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "an F64 basis needs F64 matrix values");
-    } else if (basis == SKF_F32 || basis == SKF_BF16) {
-        if (A->vdtype != SKF_F32) return fail(SKF_ERR_NOT_SUPPORTED, "an F32 or BF16 basis needs F32 matrix values");
-        if (S->kind != SKF_SKETCH_SPARSE_SIGN && S->kind != SKF_SKETCH_IDENTITY)
-            return fail(SKF_ERR_NOT_SUPPORTED, "sketch kind not implemented");
-    } else {
-        return fail(SKF_ERR_INVALID_ARG, "unknown basis dtype");
-    }
-    return SKF_OK;
-}
-
-static size_t dtype_size(skf_dtype d) { return d == SKF_F64 ? 8 : d == SKF_F32 ? 4 : 2; }
-
-static skf_status run_arnoldi(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, skf_dtype basis,
-                              void *V, int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                              skf_info *info, cudaStream_t cs) {
-    if (basis == SKF_F64) return arnoldi_run(A, S, b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
-    if (basis == SKF_F32) return arnoldi_run_f32(A, S, b, m, k, (float *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
-    return arnoldi_run_bf16(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, cs);
-}
-
 skf_status skf_arnoldi_trunc(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, int32_t m,
                              int32_t k, skf_dtype basis_dtype, void *V, int64_t ldv, double *vscale, double *SV,
                              double *SAV, double *H, skf_info *info, skf_stream_t stream) {
@@ -525,54 +652,57 @@ skf_status skf_arnoldi_trunc(const skf_csr *A, const skf_sketch *S, const void *
 skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype,
                      const skf_func *f, const skf_params *p, void *x, skf_dtype xdtype, skf_info *info,
                      skf_stream_t stream) {
-    if (!f || !p || !x) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
-    skf_status st = check_common(A, S, b, bdtype, p->m, p->k, p->basis_dtype);
-    if (st != SKF_OK) return st;
-    if (method != SKF_METHOD_SFOM && method != SKF_METHOD_SGMRES) return fail(SKF_ERR_INVALID_ARG, "bad method");
-    if (xdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "x must be F64 in this build");
-    if (p->m > 512) return fail(SKF_ERR_NOT_SUPPORTED, "m > 512 is not supported by the dense tail");
-    if (method == SKF_METHOD_SGMRES && S->s < 2 * p->m)
-        return fail(SKF_ERR_SKETCH_TOO_SMALL, "sGMRES needs s >= 2m");
-    if (f->n_nodes < 0 || (f->n_nodes > 0 && (!f->nodes || !f->weights)))
-        return fail(SKF_ERR_INVALID_ARG, "bad explicit rule");
-    if (f->n_nodes == 0 && f->kind != SKF_FUNC_INV) {
-        if (!(f->scale > 0.0)) return fail(SKF_ERR_INVALID_ARG, "rule scale must be > 0");
-        if (p->ell1 < 1 || p->ell2 <= p->ell1 || p->ell2 < 3 || p->ell_max < p->ell2)
-            return fail(SKF_ERR_INVALID_ARG, "need 1 <= ell1 < ell2, ell2 >= 3, ell_max >= ell2");
-        if (!(p->tol > 0.0)) return fail(SKF_ERR_INVALID_ARG, "tol must be > 0");
-    }
-    if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5 && f->n_nodes == 0)
-        return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
     const RuleDev *rule = nullptr;
-    st = get_rule(*f, *p, &rule);
+    skf_status st = solve_check(method, A, S, b, bdtype, f, p, x, xdtype, &rule);
     if (st != SKF_OK) return st;
+    return solve_enqueue(method, A, S, b, *p, x, info, *rule, (cudaStream_t)stream);
+}
 
+skf_status skf_solve_batched(int32_t nprob, const skf_problem *probs, int32_t lanes, skf_stream_t stream) {
+    if (nprob < 0 || (nprob > 0 && !probs)) return fail(SKF_ERR_INVALID_ARG, "bad problem array");
+    if (lanes < 1 || lanes > kMaxLanes) return fail(SKF_ERR_INVALID_ARG, "lanes must be in 1..16");
+    std::vector<const RuleDev *> rules((size_t)nprob, nullptr);
+    for (int i = 0; i < nprob; ++i) {
+        const skf_problem &q = probs[i];
+        const skf_status st = solve_check(q.method, q.A, q.S, q.b, q.bdtype, q.f, q.p, q.x, q.xdtype, &rules[i]);
+        if (st != SKF_OK) return fail(st, "problem " + std::to_string(i) + ": " + skf_last_error());
+    }
+    if (nprob == 0) return SKF_OK;
     cudaStream_t cs = (cudaStream_t)stream;
-    const int m = p->m;
-    const int64_t n = A->n;
-    const int s = S->s;
-    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const skf_dtype bt = p->basis_dtype;
-    const int64_t ldv = (n + 63) / 64 * 64;   // 256-byte aligned columns
-    const size_t szV = dtype_size(bt) * (size_t)ldv * m;
-    const size_t szS = sizeof(double) * (size_t)s * m;
-    const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
-    const size_t total = al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4);
-    char *ws = nullptr;
-    st = dalloc((void **)&ws, total, cs);
+    const int L = std::min<int>(lanes, nprob);
+    std::vector<int> lane_of((size_t)nprob, 0), order((size_t)nprob);
+    assign_lanes(nprob, probs, L, lane_of.data(), order.data());
+    if (L == 1) {
+        for (int i : order) {
+            const skf_problem &q = probs[i];
+            const skf_status st = solve_enqueue(q.method, q.A, q.S, q.b, *q.p, q.x, q.info, *rules[i], cs);
+            if (st != SKF_OK) return fail(st, "problem " + std::to_string(i) + ": " + skf_last_error());
+        }
+        return SKF_OK;
+    }
+    std::lock_guard<std::mutex> lk(lane_mutex());
+    LanePool *pool = nullptr;
+    skf_status st = lane_pool(&pool);
     if (st != SKF_OK) return st;
-    size_t off = 0;
-    void *V = (void *)(ws + off); off += al(szV);
-    double *SV = (double *)(ws + off); off += al(szS);
-    double *SAV = (double *)(ws + off); off += al(szS);
-    double *H = (double *)(ws + off); off += al(szH);
-    double *vscale = (double *)(ws + off); off += al(sizeof(double) * m);
-    int *iscal = (int *)(ws + off);
-    st = run_arnoldi(A, S, (const double *)b, m, p->k, bt, V, ldv, vscale, SV, SAV, H, iscal, info, cs);
-    if (st == SKF_OK)
-        st = tail_run(method, s, m, n, V, bt, ldv, vscale, SV, SAV, iscal, *rule, p->tol, (double *)x, info, cs);
-    dfree(ws, cs);
-    return st;
+    cudaError_t e = cudaEventRecord(pool->fork, cs);
+    for (int l = 0; l < L && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(pool->s[l], pool->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "lane fork");
+    // enqueue in order; on a failure stop enqueuing but still join every lane
+    std::string err;
+    for (int i : order) {
+        if (st != SKF_OK) break;
+        const skf_problem &q = probs[i];
+        st = solve_enqueue(q.method, q.A, q.S, q.b, *q.p, q.x, q.info, *rules[i], pool->s[lane_of[i]]);
+        if (st != SKF_OK) err = "problem " + std::to_string(i) + ": " + skf_last_error();
+    }
+    for (int l = 0; l < L; ++l) {
+        cudaError_t ej = cudaEventRecord(pool->join[l], pool->s[l]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(cs, pool->join[l], 0);
+        if (ej != cudaSuccess && e == cudaSuccess) e = ej;
+    }
+    if (st != SKF_OK) return fail(st, err);
+    if (e != cudaSuccess) return cuda_fail(e, "lane join");
+    return SKF_OK;
 }
 
 skf_status skf_sfom(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, const skf_func *f,
