@@ -119,6 +119,10 @@ typedef struct {
     double beta;            /* ||b||                                      */
     double eps_est;         /* max_j | ||S v_j||^2 - 1 | (Sec. 4.3)       */
     double rdiag_ratio;     /* min |R_jj| / max |R_jj| of the whitening QR */
+    int32_t nodes_fp64;     /* quadrature-node solves that needed the FP64
+                               Cholesky factor (the FP32 factor with FP64
+                               refinement did not converge for them)      */
+    int32_t reserved;
 } skf_info;
 
 /* ---------------------------------------------------------------- misc */

@@ -51,7 +51,8 @@ class Params(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("m_eff", ctypes.c_int32), ("breakdown", ctypes.c_int32),
                 ("ell", ctypes.c_int32), ("quad_err", ctypes.c_double), ("beta", ctypes.c_double),
-                ("eps_est", ctypes.c_double), ("rdiag_ratio", ctypes.c_double)]
+                ("eps_est", ctypes.c_double), ("rdiag_ratio", ctypes.c_double),
+                ("nodes_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -40,7 +40,7 @@ struct TailCtx {
     double *qbuf;      // [levels][m]
     double *qacc;      // [m]
     double *z;         // [m] coefficients for V (scaled by vscale)
-    double *qstate;    // [0] converged, [1] ell, [2] quad_err, [3] rdiag_ratio
+    double *qstate;    // [0] converged, [1] ell, [2] quad_err, [3] rdiag_ratio, [4] FP64 node solves
     const double *t, *w;      // node table
     int nlevels;
 };
@@ -59,7 +59,7 @@ __global__ void k_tail_copy(const double *__restrict__ SV, const double *__restr
         else if (col < 2 * me) v = SAV[r + (int64_t)(col - me) * c.s];
         c.Aw[idx] = v;
     }
-    if (blockIdx.x == 0 && threadIdx.x < 4) c.qstate[threadIdx.x] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x < 5) c.qstate[threadIdx.x] = 0.0;
 }
 
 // Householder reflector for column jj (LAPACK convention: beta = -sign(x0)
@@ -183,103 +183,6 @@ __global__ void __launch_bounds__(kThreads) k_tail_prep(TailCtx c) {
         }
     }
 }
-
-// Cholesky solve L L^T y = y in place (L in the lower triangle of N, ld m).
-__device__ void chol_solve(const double *N, int me, int ld, double *y) {
-    for (int p = 0; p < me; ++p) {
-        __syncthreads();
-        const double yp = y[p] / N[p + (int64_t)p * ld];
-        __syncthreads();
-        if (threadIdx.x == 0) y[p] = yp;
-        for (int i = p + 1 + threadIdx.x; i < me; i += blockDim.x) y[i] = fma(-N[i + (int64_t)p * ld], yp, y[i]);
-    }
-    for (int p = me - 1; p >= 0; --p) {
-        __syncthreads();
-        const double yp = y[p] / N[p + (int64_t)p * ld];
-        __syncthreads();
-        if (threadIdx.x == 0) y[p] = yp;
-        for (int i = threadIdx.x; i < p; i += blockDim.x) y[i] = fma(-N[p + (int64_t)i * ld], yp, y[i]);
-    }
-    __syncthreads();
-}
-
-// FP64 fallback for the nodes k_nodes_mixed flagged: one CTA per node,
-// node n0 + off + blockIdx.x of the table, result row off + blockIdx.x of
-// `out`, workspace slot blockIdx.x.
-__global__ void __launch_bounds__(kThreads) k_nodes(TailCtx c, int n0, int off) {
-    extern __shared__ double sm[];   // y[m], r[m], g[m], colp[m]
-    const int me = c.iscal[1];
-    if (c.qstate[0] != 0.0 || me == 0) return;
-    if (!c.nodebad[off + blockIdx.x]) return;   // solved by k_nodes_mixed
-    const int m = c.m;
-    double *y = sm, *r = sm + m, *g = sm + 2 * m, *colp = sm + 3 * m;
-    const int nd = n0 + off + blockIdx.x;
-    const double t = c.t[nd], wt = c.w[nd];
-    double *outrow = c.out + (size_t)(off + blockIdx.x) * c.m;
-    double *N = c.Nw + (size_t)blockIdx.x * m * m;
-    const bool gm = c.method == SKF_METHOD_SGMRES;
-    // N(t) = t^2 I + t (M + M^T) + C, lower triangle
-    for (int64_t idx = threadIdx.x; idx < (int64_t)me * me; idx += blockDim.x) {
-        const int i = (int)(idx % me), j = (int)(idx / me);
-        if (j > i) continue;
-        N[i + (int64_t)j * m] = (i == j ? t * t : 0.0) + t * c.B[i + (int64_t)j * m] + c.C[i + (int64_t)j * m];
-    }
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    // right-looking Cholesky
-    for (int p = 0; p < me; ++p) {
-        __syncthreads();
-        const double d = N[p + (int64_t)p * m];
-        if (!(d > 0.0)) {
-            if (threadIdx.x == 0) bad = 1;
-            break;
-        }
-        const double lpp = sqrt(d);
-        for (int i = p + threadIdx.x; i < me; i += blockDim.x) {
-            const double v = (i == p) ? lpp : N[i + (int64_t)p * m] / lpp;
-            colp[i] = v;
-        }
-        __syncthreads();
-        for (int i = p + threadIdx.x; i < me; i += blockDim.x) N[i + (int64_t)p * m] = colp[i];
-        for (int i = p + 1 + threadIdx.x; i < me; i += blockDim.x) {
-            const double lip = colp[i];
-            for (int q = p + 1; q <= i; ++q) N[i + (int64_t)q * m] = fma(-lip, colp[q], N[i + (int64_t)q * m]);
-        }
-    }
-    __syncthreads();
-    if (bad) {
-        for (int a = threadIdx.x; a < me; a += blockDim.x) outrow[a] = 0.0;
-        if (threadIdx.x == 0) atomicExch(&c.iscal[2], gm ? (int)SKF_ERR_ILL_CONDITIONED : (int)SKF_ERR_BRANCH_CUT);
-        return;
-    }
-    // y = N^{-1} (t c + M^T c)
-    for (int a = threadIdx.x; a < me; a += blockDim.x) y[a] = t * c.cvec[a] + c.Mtc[a];
-    chol_solve(N, me, m, y);
-    // one refinement step on the original residual
-    for (int a = threadIdx.x; a < me; a += blockDim.x) {
-        double v = c.cvec[a] - t * y[a];
-        for (int j = 0; j < me; ++j) v = fma(-c.M[a + (int64_t)j * m], y[j], v);
-        r[a] = v;
-    }
-    if (gm) {
-        for (int a = threadIdx.x; a < me; a += blockDim.x) {
-            double v = 0.0;
-            for (int j = a; j < me; ++j) v = fma(-c.R2[a + (int64_t)j * m], y[j], v);
-            colp[a] = v;   // bottom residual
-        }
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < me; j += blockDim.x) {
-        double v = t * r[j];
-        for (int a = 0; a < me; ++a) v = fma(c.M[a + (int64_t)j * m], r[a], v);
-        if (gm)
-            for (int a = 0; a <= j; ++a) v = fma(c.R2[a + (int64_t)j * m], colp[a], v);
-        g[j] = v;
-    }
-    chol_solve(N, me, m, g);
-    for (int a = threadIdx.x; a < me; a += blockDim.x) outrow[a] = wt * (y[a] + g[a]);
-}
-
 
 constexpr int kMixedMaxM = 320;   // packed FP32 factor of order m must fit in shared memory
 
@@ -418,6 +321,260 @@ __global__ void __launch_bounds__(kThreads) k_nodes_mixed(TailCtx c, int n0, int
     __syncthreads();
     if (threadIdx.x == 0) c.nodebad[row] = bad;
     if (!bad)
+        for (int a = threadIdx.x; a < me; a += blockDim.x) c.out[(size_t)row * m + a] = wt * y[a];
+}
+
+// ---------------------------------------------------------------------------
+// Node solves with the Cholesky factor in global memory (one slot of m x m
+// per CTA): FP32 factor + FP64 refinement for m above the shared-memory limit
+// of k_nodes_mixed, and the FP64 factor for the nodes that the FP32 factor
+// cannot resolve (any m).
+constexpr int kNodeThreads = 512;   // one thread per row of a panel (m <= 512)
+constexpr int kNB = 32;             // panel width of the blocked Cholesky
+constexpr int kKC = 64;             // factored columns staged per pass of the panel update
+
+template <typename T> struct NodeSmem {
+    double *y, *rt, *rb, *g;   // [m] each
+    T *P;                      // panel [mp x kNB], ld mp
+    T *Lt;                     // [kKC x kNB]: rows c0.. of staged factored columns
+    T *D;                      // [32 x 32] diagonal block for the triangular solves
+    T *sd;                     // [kNB] pivots of the panel
+    int mp;
+};
+
+template <typename T> __device__ NodeSmem<T> node_smem(unsigned char *base, int m) {
+    NodeSmem<T> s;
+    s.mp = (m + 31) & ~31;
+    double *d = (double *)base;
+    s.y = d; s.rt = d + m; s.rb = d + 2 * m; s.g = d + 3 * m;
+    T *t = (T *)(d + 4 * m);
+    s.P = t; s.Lt = t + (size_t)s.mp * kNB; s.D = s.Lt + kKC * kNB; s.sd = s.D + 32 * 32;
+    return s;
+}
+
+template <typename T> size_t node_smem_bytes(int m) {
+    const int mp = (m + 31) & ~31;
+    return sizeof(double) * 4 * (size_t)m + sizeof(T) * ((size_t)mp * kNB + kKC * kNB + 32 * 32 + kNB);
+}
+
+// Blocked left-looking Cholesky N(t) = L L^T, N(t) = t^2 I + t B + C (B, C:
+// lower triangles, ld m), L lower in global memory (column-major, ld m), in
+// precision T.  Each panel of kNB columns is formed as N(t) minus the product
+// of the already factored rows (register tiles, one row per thread), then
+// factored in shared memory (right-looking, pivot division deferred to a final
+// scaling).  Returns false on a nonpositive pivot (uniform over the CTA).
+template <typename T>
+__device__ bool chol_blocked(const TailCtx &c, double t, int me, T *L, const NodeSmem<T> &sm) {
+    const int m = c.m, mp = sm.mp, tid = threadIdx.x;
+    for (int c0 = 0; c0 < me; c0 += kNB) {
+        const int nb = min(kNB, me - c0), rows = me - c0;
+        T acc[kNB];
+#pragma unroll
+        for (int u = 0; u < kNB; ++u) acc[u] = (T)0;
+        for (int pk = 0; pk < c0; pk += kKC) {
+            const int kc = min(kKC, c0 - pk);
+            __syncthreads();
+            for (int idx = tid; idx < kc * kNB; idx += blockDim.x) {
+                const int q = idx / kNB, jj = idx % kNB;
+                sm.Lt[idx] = jj < nb ? L[(c0 + jj) + (int64_t)(pk + q) * m] : (T)0;
+            }
+            __syncthreads();
+            if (tid < rows) {
+                const T *lrow = L + (c0 + tid) + (int64_t)pk * m;
+                for (int q = 0; q < kc; ++q) {
+                    const T a = lrow[(int64_t)q * m];
+                    const T *lt = sm.Lt + q * kNB;
+#pragma unroll
+                    for (int u = 0; u < kNB; ++u) acc[u] = fma(a, lt[u], acc[u]);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < rows) {
+            const int i = c0 + tid;
+#pragma unroll
+            for (int u = 0; u < kNB; ++u) {
+                const int j = c0 + u;
+                T v = (T)0;
+                if (u < nb && i >= j)
+                    v = (T)((i == j ? t * t : 0.0) + t * c.B[i + (int64_t)j * m] + c.C[i + (int64_t)j * m]) - acc[u];
+                sm.P[tid + u * mp] = v;
+            }
+        }
+        for (int k = 0; k < nb; ++k) {
+            __syncthreads();
+            const T d = sm.P[k + k * mp];
+            if (!(d > (T)0)) return false;
+            const T inv = (T)1 / d;
+            const int w = nb - k - 1;
+            for (int idx = tid; idx < (rows - k - 1) * w; idx += blockDim.x) {
+                const int r = k + 1 + idx / w, jj = k + 1 + idx % w;
+                if (jj <= r) sm.P[r + jj * mp] -= sm.P[r + k * mp] * sm.P[jj + k * mp] * inv;
+            }
+        }
+        __syncthreads();
+        if (tid < nb) sm.sd[tid] = sqrt(sm.P[tid + tid * mp]);
+        __syncthreads();
+        for (int idx = tid; idx < rows * nb; idx += blockDim.x) {
+            const int r = idx % rows, k = idx / rows;
+            if (r >= k) L[(c0 + r) + (int64_t)(c0 + k) * m] = (r == k) ? sm.sd[k] : sm.P[r + k * mp] / sm.sd[k];
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// z <- (L L^T)^{-1} z with the global factor of chol_blocked; z is FP64 in
+// shared memory, the arithmetic is in T.  Blocks of 32 rows: the diagonal
+// block is solved by one warp from shared memory, the rest of the rows are
+// updated by all threads.
+template <typename T>
+__device__ void chol_solve_g(const T *L, int me, int m, double *z, const NodeSmem<T> &sm) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    auto load_diag = [&](int b0, int nb) {
+        __syncthreads();
+        for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
+            const int q = idx >> 5, r = idx & 31;
+            sm.D[idx] = (r < nb && q < nb && r >= q) ? L[(b0 + r) + (int64_t)(b0 + q) * m] : (T)0;
+        }
+        __syncthreads();
+    };
+    for (int b0 = 0; b0 < me; b0 += 32) {               // L u = z
+        const int nb = min(32, me - b0);
+        load_diag(b0, nb);
+        if (tid < 32) {
+            T zr = lane < nb ? (T)z[b0 + lane] : (T)0;
+            for (int q = 0; q < nb; ++q) {
+                if (lane == q) zr = zr / sm.D[q * 33];
+                const T uq = __shfl_sync(0xffffffffu, zr, q);
+                if (lane > q) zr = fma(-sm.D[lane + q * 32], uq, zr);
+            }
+            if (lane < nb) z[b0 + lane] = (double)zr;
+        }
+        __syncthreads();
+        for (int r = b0 + nb + tid; r < me; r += blockDim.x) {
+            T acc = (T)0;
+            for (int q = 0; q < nb; ++q) acc = fma(L[r + (int64_t)(b0 + q) * m], (T)z[b0 + q], acc);
+            z[r] -= (double)acc;
+        }
+    }
+    for (int b0 = ((me - 1) / 32) * 32; b0 >= 0; b0 -= 32) {   // L^T x = u
+        const int nb = min(32, me - b0);
+        load_diag(b0, nb);
+        if (tid < 32) {
+            T xr = lane < nb ? (T)z[b0 + lane] : (T)0;
+            for (int q = nb - 1; q >= 0; --q) {
+                if (lane == q) xr = xr / sm.D[q * 33];
+                const T xq = __shfl_sync(0xffffffffu, xr, q);
+                if (lane < q) xr = fma(-sm.D[q + lane * 32], xq, xr);
+            }
+            if (lane < nb) z[b0 + lane] = (double)xr;
+        }
+        __syncthreads();
+        for (int r = tid; r < b0; r += blockDim.x) {
+            const T *col = L + (b0) + (int64_t)r * m;
+            T acc = (T)0;
+            for (int q = 0; q < nb; ++q) acc = fma(col[q], (T)z[b0 + q], acc);
+            z[r] -= (double)acc;
+        }
+    }
+    __syncthreads();
+}
+
+// r = [c; 0] - [t I + M; R2] y  (FP64; rb only for sGMRES), then
+// g = [t I + M; R2]^T r.  Threads over rows / columns.
+__device__ void node_residual(const TailCtx &c, double t, int me, const double *y, double *rt, double *rb, double *g,
+                              bool gm) {
+    const int m = c.m;
+    __syncthreads();
+    for (int a = threadIdx.x; a < me; a += blockDim.x) {
+        double v = c.cvec[a] - t * y[a];
+        for (int j = 0; j < me; ++j) v = fma(-c.M[a + (int64_t)j * m], y[j], v);
+        rt[a] = v;
+        if (gm) {
+            double u = 0.0;
+            for (int j = a; j < me; ++j) u = fma(-c.R2[a + (int64_t)j * m], y[j], u);
+            rb[a] = u;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < me; j += blockDim.x) {
+        double v = t * rt[j];
+        for (int a = 0; a < me; ++a) v = fma(c.MT[j + (int64_t)a * m], rt[a], v);
+        if (gm)
+            for (int a = 0; a <= j; ++a) v = fma(c.R2T[j + (int64_t)a * m], rb[a], v);
+        g[j] = v;
+    }
+    __syncthreads();
+}
+
+// One CTA per node (node n0 + off + blockIdx.x, workspace slot blockIdx.x).
+// MIXED: FP32 factor, then FP64 iterative refinement on the original
+// least-squares residual (semi-normal equations); a node that does not
+// converge is flagged for the FP64 variant.  !MIXED (T = double): runs only
+// for flagged nodes: FP64 factor, solve, one refinement step.
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(kNodeThreads) k_nodes_g(TailCtx c, int n0, int off) {
+    extern __shared__ __align__(16) unsigned char nsm_raw[];
+    const int me = c.iscal[1];
+    if (c.qstate[0] != 0.0 || me == 0) return;
+    const int row = off + blockIdx.x;
+    if (!MIXED && !c.nodebad[row]) return;
+    if (!MIXED && threadIdx.x == 0) atomicAdd(&c.qstate[4], 1.0);
+    const int m = c.m;
+    const NodeSmem<T> sm = node_smem<T>(nsm_raw, m);
+    T *L = (T *)(c.Nw + (size_t)blockIdx.x * m * m);
+    const int nd = n0 + row;
+    const double t = c.t[nd], wt = c.w[nd];
+    const bool gm = c.method == SKF_METHOD_SGMRES;
+    double *y = sm.y, *rt = sm.rt, *rb = sm.rb, *g = sm.g;
+    __shared__ double snorm[2];
+    bool ok = chol_blocked<T>(c, t, me, L, sm);
+    if (!ok) {
+        if (MIXED) {
+            if (threadIdx.x == 0) c.nodebad[row] = 1;
+        } else {
+            for (int a = threadIdx.x; a < me; a += blockDim.x) c.out[(size_t)row * m + a] = 0.0;
+            if (threadIdx.x == 0)
+                atomicExch(&c.iscal[2], gm ? (int)SKF_ERR_ILL_CONDITIONED : (int)SKF_ERR_BRANCH_CUT);
+        }
+        return;
+    }
+    for (int a = threadIdx.x; a < me; a += blockDim.x) y[a] = t * c.cvec[a] + c.Mtc[a];
+    chol_solve_g<T>(L, me, m, y, sm);
+    bool conv = !MIXED;
+    const int iters = MIXED ? 12 : 1;
+    double prev = INFINITY;
+    for (int it = 0; it < iters; ++it) {
+        node_residual(c, t, me, y, rt, rb, g, gm);
+        chol_solve_g<T>(L, me, m, g, sm);
+        double loc[2] = {0.0, 0.0};
+        for (int a = threadIdx.x; a < me; a += blockDim.x) {
+            loc[0] = fma(g[a], g[a], loc[0]);
+            y[a] += g[a];
+            loc[1] = fma(y[a], y[a], loc[1]);
+        }
+        if constexpr (MIXED) {
+            for (int o = 16; o > 0; o >>= 1) {
+                loc[0] += __shfl_xor_sync(0xffffffffu, loc[0], o);
+                loc[1] += __shfl_xor_sync(0xffffffffu, loc[1], o);
+            }
+            if (threadIdx.x == 0) { snorm[0] = 0.0; snorm[1] = 0.0; }
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(&snorm[0], loc[0]);
+                atomicAdd(&snorm[1], loc[1]);
+            }
+            __syncthreads();
+            const double dn = sqrt(snorm[0]), yn = sqrt(snorm[1]);
+            if (dn <= 1e-14 * yn) { conv = true; break; }
+            if (it >= 2 && dn > 0.5 * prev) { conv = dn <= 1e-12 * yn; break; }
+            prev = dn;
+        }
+    }
+    __syncthreads();
+    if (MIXED && threadIdx.x == 0) c.nodebad[row] = conv ? 0 : 1;
+    if (conv)
         for (int a = threadIdx.x; a < me; a += blockDim.x) c.out[(size_t)row * m + a] = wt * y[a];
 }
 
@@ -572,6 +729,7 @@ __global__ void k_write_info(TailCtx c, skf_info *info) {
     info->ell = (int)c.qstate[1];
     info->quad_err = c.qstate[2];
     info->rdiag_ratio = c.qstate[3];
+    info->nodes_fp64 = (int)c.qstate[4];
 }
 
 }  // namespace
@@ -617,7 +775,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                             sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * m,
                             sizeof(double) * m, sizeof(double) * chunk * mm, sizeof(double) * (size_t)cap * m,
                             sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
-                            sizeof(double) * 4, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap};
+                            sizeof(double) * 5, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap};
     constexpr int kNbuf = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
     for (size_t v : sizes) total += al(v);
@@ -654,19 +812,25 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     }
     k_tail_prep<<<G, kThreads, 0, st>>>(c);
     ++nlaunch;
-    const size_t nsmem = sizeof(double) * 4 * m;
-    if (nsmem > 48 * 1024) cudaFuncSetAttribute(k_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsmem);
-    const int mm_mixed = std::min(m, kMixedMaxM);
-    const size_t msmem = sizeof(double) * 4 * m + sizeof(float) * ((size_t)m + (size_t)mm_mixed * (mm_mixed + 1) / 2);
-    if (msmem > 48 * 1024)
+    // FP32 factor: packed in shared memory up to kMixedMaxM, else a global slot
+    const bool packed = m <= kMixedMaxM;
+    const size_t msmem = sizeof(double) * 4 * m + sizeof(float) * ((size_t)m + (size_t)m * (m + 1) / 2);
+    const size_t gsm32 = node_smem_bytes<float>(m), gsm64 = node_smem_bytes<double>(m);
+    if (packed && msmem > 48 * 1024)
         cudaFuncSetAttribute(k_nodes_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+    if (!packed && gsm32 > 48 * 1024)
+        cudaFuncSetAttribute(k_nodes_g<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm32);
+    if (gsm64 > 48 * 1024)
+        cudaFuncSetAttribute(k_nodes_g<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm64);
     for (size_t bi = 0; bi < batches.size(); ++bi) {
         const int l0 = batches[bi].first, nl = batches[bi].second;
         const int n0 = rule.h_start[l0];
         const int nn = rule.h_start[l0 + nl] - n0;
         for (int o = 0; o < nn; o += chunk) {
-            k_nodes_mixed<<<std::min(chunk, nn - o), kThreads, msmem, st>>>(c, n0, o);
-            k_nodes<<<std::min(chunk, nn - o), kThreads, nsmem, st>>>(c, n0, o);
+            const int nb = std::min(chunk, nn - o);
+            if (packed) k_nodes_mixed<<<nb, kThreads, msmem, st>>>(c, n0, o);
+            else k_nodes_g<float, true><<<nb, kNodeThreads, gsm32, st>>>(c, n0, o);
+            k_nodes_g<double, false><<<nb, kNodeThreads, gsm64, st>>>(c, n0, o);
             nlaunch += 2;
         }
         k_levels<<<1, kThreads, 0, st>>>(c, l0, nl, rule.lev_start, rule.lev_ell, n0, tol,

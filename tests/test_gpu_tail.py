@@ -1,0 +1,89 @@
+"""The dense FP64 tail of sFOM / sGMRES at large m and on ill-conditioned
+node systems, checked against the oracle's tail (whitening QR of S V_m,
+Sec. 2.1; shifted sketched least-squares solves of eq. (sGMRES) and shifted
+solves of eq. (sFOM) over the adaptive quadrature of Sec. 4.1) applied to the
+same basis and sketches the GPU Arnoldi process produced.  Fixing the basis
+isolates the tail: the node solves (FP32 Cholesky factor with FP64 iterative
+refinement, FP64 factor where that does not converge) must agree with the
+oracle's dense least-squares solutions to 1e-10."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sketched as osk
+from workloads import convdiff_2d, csr_to_scipy, gaussian_rhs
+from workloads.configs import laplacian_lambda_min, quad_scale
+from gpu_helpers import rel
+
+pytestmark = pytest.mark.gpu
+
+
+def tail_case(skf, A, lam_lo, m, s, basis, method, seed=7, ell=None):
+    from oracle import quadrature as oq
+    vals = A.values.astype(np.float32 if basis == torch.float32 else np.float64)
+    op = skf.upload_csr(A.rowptr, A.colind, vals, device="cuda")
+    b = torch.as_tensor(gaussian_rhs(A.n, seed), device="cuda")
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, s, 8, 13)
+    c = quad_scale("invsqrt", lam_lo, float(abs(csr_to_scipy(A)).sum(1).max()))
+    if ell is None:
+        f = skf.make_func("invsqrt", c)
+    else:          # one fixed rule, the oracle's nodes on both sides
+        t_, w_ = oq.rule("invsqrt", ell, c)
+        f = skf.make_func("invsqrt", c, nodes=t_, weights=w_)
+    p = skf.make_params(m, 2, basis_dtype=basis, tol=1e-10)
+    info = skf.new_info()
+    x = skf.solve(method, op.csr, S, b, f, p, info=info)
+    V, vsc, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, b, m, 2, basis_dtype=basis)
+    torch.cuda.synchronize()
+    inf = skf.read_info(info)
+    # the oracle's tail on the GPU's basis: S b is the sketch of the stored
+    # first column, rescaled to b (the tail's c = ||w_1|| R_11 e_1)
+    SVn = SV.cpu().numpy().T
+    SAVn = SAV.cpu().numpy().T
+    vs = vsc.cpu().numpy()
+    Sb = SVn[:, 0] / vs[0]
+    W = osk.whiten(SVn, SAVn, Sb)
+    if method == skf.SGMRES:
+        y, used = osk.sgmres_quadrature(W, "invsqrt", c, ell=ell, tol=1e-10)
+    else:
+        y, used = osk.sfom_quadrature(W, "invsqrt", c, ell=ell, tol=1e-10)
+    Vd = V.double().cpu().numpy() * vs[:, None]       # rows: v_j
+    xo = Vd.T @ y
+    # conditioning of the worst (smallest-shift) node system of the method
+    t_min = oq.rule("invsqrt", ell or 64, c)[0].min()
+    if method == skf.SGMRES:
+        kappa = float(np.linalg.cond(t_min * W["Q"] + W["Z"]))
+    else:
+        kappa = float(np.linalg.cond(t_min * np.eye(W["M"].shape[0]) + W["M"]))
+    return x.cpu().numpy(), xo, inf, used, kappa
+
+
+@pytest.mark.parametrize("m,method", [(352, "sgmres"), (448, "sgmres"), (352, "sfom")])
+def test_tail_above_shared_memory_factor_limit(skf, m, method):
+    """m > 320: the FP32 factor lives in a global slot (blocked Cholesky).
+    2D grid n = 250 (m < 2n: the basis stays well conditioned), fixed
+    64-node rule."""
+    n = 250
+    A = convdiff_2d(n, (100.0, 50.0))
+    meth = skf.SGMRES if method == "sgmres" else skf.SFOM
+    x, xo, inf, ell, kappa = tail_case(skf, A, laplacian_lambda_min(n, 2), m, 4 * m, torch.float32, meth, ell=64)
+    assert inf["status"] == 0 and inf["m_eff"] == m
+    # the FP32 factor resolved most nodes (a broken factor sends all 64 to FP64)
+    assert inf["nodes_fp64"] < 32
+    # least-squares forward error: two backward-stable FP64 solvers agree to
+    # about kappa^2 u for the worst-conditioned node (smallest shift)
+    assert rel(x, xo) <= max(1e-10, kappa ** 2 * 2.0 ** -52)
+
+
+@pytest.mark.parametrize("n,m", [(400, 300), (600, 400)])
+def test_tail_ill_conditioned_nodes_use_fp64_factor(skf, n, m):
+    """2D operators with m large enough that the smallest shifts give node
+    systems whose normal matrices are beyond the FP32 factor; those nodes are
+    solved with the FP64 factor.  m = 300 pairs it with the shared-memory
+    FP32 kernel, m = 400 with the global-slot one.  Fixed 64-node rule."""
+    A = convdiff_2d(n, (100.0, 50.0))
+    x, xo, inf, ell, kappa = tail_case(skf, A, laplacian_lambda_min(n, 2), m, 4 * m, torch.float32, skf.SGMRES,
+                                       ell=64)
+    assert inf["status"] == 0 and inf["m_eff"] == m
+    assert 1 <= inf["nodes_fp64"] < 32
+    assert rel(x, xo) <= max(1e-10, kappa ** 2 * 2.0 ** -52)
