@@ -17,6 +17,7 @@ Rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -354,10 +355,16 @@ def run_reference_batch(args, rank: int):
 
 
 def run_batch(args, rank, world, local, dev):
-    """Batched workload: the FP32-basis batch (skf_solve_batched captured
-    into one CUDA graph, replayed once per step) against the plain FP64 path
-    solving the same problems one at a time (skf_sgmres per problem, same
-    operators, sketches, right-hand sides and rule)."""
+    """Batched workload.  Arms, all through the public API on the same
+    operators, sketches, right-hand sides and rules:
+      * FP64 basis, one problem at a time (skf_sgmres per problem);
+      * FP64 basis as one batch (skf_solve_batched captured into one CUDA
+        graph, replayed once per step): the headline, since its results are
+        bit-identical to the one-at-a-time path (error 0 <= 1e-6);
+      * FP32 basis as one batch: faster, and its error against the FP64
+        results is reported per problem (the 1e-6 gate holds for part of the
+        batch only), with how well the solve's own flag (nodes needing the
+        FP64 factor) predicts a miss."""
     import numpy as np
     import torch
     import paper_2208_11447_gb300 as skf
@@ -375,10 +382,15 @@ def run_batch(args, rank, world, local, dev):
         b_dev.append(torch.as_tensor(b, device=dev))
     p32 = [skf.make_params(q.m, 2, basis_dtype=torch.float32, tol=1e-10) for q in layout.rhs]
     p64 = [skf.make_params(q.m, 2, basis_dtype=torch.float64, tol=1e-10) for q in layout.rhs]
-    x32 = [torch.empty_like(b) for b in b_dev]
+    info_sz = ctypes.sizeof(skf.Info)
     x64 = [torch.empty_like(b) for b in b_dev]
-    inf32 = [skf.new_info(dev) for _ in range(nprob)]
-    inf64 = [skf.new_info(dev) for _ in range(nprob)]
+    x64b = [torch.empty_like(b) for b in b_dev]
+    x32 = [torch.empty_like(b) for b in b_dev]
+    inf64 = torch.zeros((nprob, info_sz), dtype=torch.uint8, device=dev)
+    inf64b = torch.zeros_like(inf64)
+    inf32 = torch.zeros_like(inf64)
+    probs64 = [(skf.SGMRES, op64[q.mat].csr, sketches[r], b_dev[r], funcs[r], p64[r], x64b[r], inf64b[r])
+               for r, q in enumerate(layout.rhs)]
     probs32 = [(skf.SGMRES, op32[q.mat].csr, sketches[r], b_dev[r], funcs[r], p32[r], x32[r], inf32[r])
                for r, q in enumerate(layout.rhs)]
     stream = torch.cuda.current_stream(dev)
@@ -400,6 +412,9 @@ def run_batch(args, rank, world, local, dev):
             tot += ev0.elapsed_time(ev1)
         return tot
 
+    def statuses(buf):
+        return sorted({skf.read_info(buf[r])["status_name"] for r in range(nprob)})
+
     # plain FP64 path, one problem at a time
     for _ in range(args.warmup):
         fp64_one_at_a_time()
@@ -407,28 +422,22 @@ def run_batch(args, rank, world, local, dev):
     replica_barrier(world)
     t64 = replica_max(timed(fp64_one_at_a_time, args.steps), world, dev)
 
-    # FP32-basis batch as one CUDA graph
+    # FP64 batch as one CUDA graph: the headline
     l0 = skf.kernel_launch_count()
-    graph = skf.BatchGraph(probs32, lanes=args.lanes)     # one eager run + capture
+    graph64 = skf.BatchGraph(probs64, lanes=args.lanes)     # one eager run + capture
     launches_per_batch = (skf.kernel_launch_count() - l0) // 2
     for _ in range(args.warmup):
-        graph.replay()
+        graph64.replay()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     replica_barrier(world)
     torch.cuda.synchronize()
-    t32 = replica_max(timed(graph.replay, args.steps), world, dev)
+    t64b = replica_max(timed(graph64.replay, args.steps), world, dev)
     replica_barrier(world)
     clk = clocks.stop()
-
-    # accuracy: FP32-basis batch against the FP64 path, per problem
-    errs = []
-    for a, b in zip(x32, x64):
-        errs.append(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)))
-    st32 = [skf.read_info(i)["status_name"] for i in inf32]
-    st64 = [skf.read_info(i)["status_name"] for i in inf64]
-    n_ok = sum(1 for e in errs if e <= BATCH_TOL)
+    equal64 = all(bool(torch.equal(a, b)) for a, b in zip(x64b, x64))
+    errs64b = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(x64b, x64)]
 
     # end to end: right-hand sides from pinned host memory, results back
     b_host = [torch.as_tensor(b).pin_memory() for b in rhs]
@@ -441,23 +450,36 @@ def run_batch(args, rank, world, local, dev):
         t0 = time.perf_counter()
         for bd, bh in zip(b_dev, b_host):
             bd.copy_(bh, non_blocking=True)
-        graph.replay()
-        for xh, xd in zip(x_host, x32):
+        graph64.replay()
+        for xh, xd in zip(x_host, x64b):
             xh.copy_(xd, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_ms = replica_max(e2e_ms, world, dev)
+    del graph64
 
-    value = replica_value(world, nprob * args.steps, t32)
+    # FP32-basis batch as one CUDA graph
+    graph32 = skf.BatchGraph(probs32, lanes=args.lanes)
+    for _ in range(args.warmup):
+        graph32.replay()
+    torch.cuda.synchronize()
+    replica_barrier(world)
+    t32 = replica_max(timed(graph32.replay, args.steps), world, dev)
+    errs = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(x32, x64)]
+    flags = [skf.read_info(inf32[r])["nodes_fp64"] > 0 for r in range(nprob)]
+    tol = BATCH_TOL
+
+    value = replica_value(world, nprob * args.steps, t64b)
     v64 = replica_value(world, nprob * args.steps, t64)
+    v32 = replica_value(world, nprob * args.steps, t32)
     e2e_value = replica_value(world, nprob * args.steps, e2e_ms)
-    # whole-batch effective bandwidth over the algorithmic Arnoldi bytes
+    # whole-batch effective bandwidth over the algorithmic Arnoldi bytes (FP64)
     alg = 0
     for q in layout.rhs:
         A = ops[q.mat][0]
-        alg += q.m * (A.nnz * 8 + 4 * (A.n + 1) + 3 * A.n * 4)
+        alg += q.m * (A.nnz * 12 + 4 * (A.n + 1) + 3 * A.n * 8)
     hbm_peak, hbm_src = measured_peaks()
-    gbs = alg / (t32 / args.steps * 1e-3) / 1e9
+    gbs = alg / (t64b / args.steps * 1e-3) / 1e9
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_batch_sample(layout, ops, rhs, budget_s=args.ref_budget)
@@ -465,23 +487,33 @@ def run_batch(args, rank, world, local, dev):
     if rank == 0:
         nbytes_b = int(sum(b.nbytes for b in rhs))
         print(json.dumps({
-            "metric": "f(A)b solves/s at rel err <= 1e-6 (batched sGMRES, FP32 basis)",
+            "metric": "f(A)b solves/s at rel err <= 1e-6 (batched sGMRES)",
             "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(t32 / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": round(t64b / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batch_cd_8x64", **layout.summary(), "k": 2, "s": "4 m_r", "zeta": 8,
-                       "f": BATCH_FUNC, "method": "sgmres", "quad_tol": 1e-10, "basis": "f32", "values": "f32",
+                       "f": BATCH_FUNC, "method": "sgmres", "quad_tol": 1e-10, "basis": "f64", "values": "f32-rounded",
                        "lanes": args.lanes, "graph": "one CUDA graph per batch",
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
+            "accuracy": {"vs": "FP64 one-at-a-time GPU path, same problems", "max_rel_err": max(errs64b),
+                         "bitwise_equal": equal64, "within_1e-6": sum(1 for e in errs64b if e <= tol), "of": nprob,
+                         "status": statuses(inf64b)},
             "fp64_one_at_a_time": {"value": round(v64, 3), "unit": "solves/s",
-                                   "ms_per_batch": round(t64 / args.steps, 3)},
+                                   "ms_per_batch": round(t64 / args.steps, 3), "status": statuses(inf64)},
             "speedup_vs_fp64_one_at_a_time": round(value / v64, 3),
-            "accuracy": {"vs": "FP64 GPU path, same problems", "max_rel_err": max(errs),
-                         "median_rel_err": statistics.median(errs), "within_1e-6": n_ok, "of": nprob,
-                         "status_f32": sorted(set(st32)), "status_f64": sorted(set(st64))},
+            "fp32_batched": {"value": round(v32, 3), "unit": "solves/s", "ms_per_batch": round(t32 / args.steps, 3),
+                             "speedup_vs_fp64_one_at_a_time": round(v32 / v64, 3),
+                             "max_rel_err": max(errs), "median_rel_err": statistics.median(errs),
+                             "within_1e-6": sum(1 for e in errs if e <= tol), "of": nprob,
+                             "status": statuses(inf32),
+                             "flag_nodes_fp64": {
+                                 "flagged_err_gt_tol": sum(1 for f, e in zip(flags, errs) if f and e > tol),
+                                 "flagged_err_le_tol": sum(1 for f, e in zip(flags, errs) if f and e <= tol),
+                                 "unflagged_err_gt_tol": sum(1 for f, e in zip(flags, errs) if not f and e > tol),
+                                 "unflagged_err_le_tol": sum(1 for f, e in zip(flags, errs) if not f and e <= tol)}},
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src,
-                         "kernel": "whole batch: algorithmic Arnoldi bytes (sum_r m_r (B_A + 3 N 4)) over the "
+                         "kernel": "whole FP64 batch: algorithmic Arnoldi bytes (sum_r m_r (B_A + 3 N 8)) over the "
                                    "batch time, tails included"},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": nbytes_b,
@@ -489,6 +521,7 @@ def run_batch(args, rank, world, local, dev):
             "gpu_launches": int(launches_per_batch * args.steps),
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
         }), flush=True)
+
 
 def main():
     ap = argparse.ArgumentParser()
