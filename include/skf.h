@@ -105,6 +105,19 @@ typedef struct {
     int32_t ell1, ell2;     /* first two quadrature orders (Sec. 4.1)    */
     int32_t ell_max;        /* give up past this order                   */
     double tol;             /* relative tolerance ||q1-q2|| <= tol ||q2|| */
+    /* Sketched stopping criterion (Sec. 4.3), off when check_every = 0.
+     * At every p = d, 2d, ... < m (d = check_every) the approximant f_p of
+     * the leading p basis columns is formed in sketched form only (S f_p =
+     * S V_p y_p, no N-vector) and compared with the previous checkpoint:
+     *   est_p = ||S V_p (y_p - [y_{p-d}; 0])|| / sqrt(1 - eps)
+     *           / (||S V_p y_p|| / sqrt(1 + eps)),
+     * eps = max_{j<p} | ||S v_j||^2 - 1 |.  The first p with est_p <= stop_tol
+     * ends the Arnoldi process there (m_eff = p) and f_p is returned; the
+     * decision is taken on the device, so the call still needs no host
+     * synchronisation.  Each checkpoint costs one dense tail (whitening QR
+     * and quadrature) of order p. */
+    int32_t check_every;
+    double stop_tol;
 } skf_params;
 
 /* Device-written result record.  Place it in memory the device can write
@@ -122,7 +135,10 @@ typedef struct {
     int32_t nodes_fp64;     /* quadrature-node solves that needed the FP64
                                Cholesky factor (the FP32 factor with FP64
                                refinement did not converge for them)      */
-    int32_t reserved;
+    int32_t stop_m;         /* p at which the stopping criterion ended the
+                               process, 0 if it did not (or was off)      */
+    double err_est;         /* last relative estimate est_p (Sec. 4.3), 0
+                               if no two checkpoints were compared        */
 } skf_info;
 
 /* ---------------------------------------------------------------- misc */

@@ -45,14 +45,14 @@ class Func(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("k", ctypes.c_int32), ("basis_dtype", ctypes.c_int),
                 ("ell1", ctypes.c_int32), ("ell2", ctypes.c_int32), ("ell_max", ctypes.c_int32),
-                ("tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("check_every", ctypes.c_int32), ("stop_tol", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("m_eff", ctypes.c_int32), ("breakdown", ctypes.c_int32),
                 ("ell", ctypes.c_int32), ("quad_err", ctypes.c_double), ("beta", ctypes.c_double),
                 ("eps_est", ctypes.c_double), ("rdiag_ratio", ctypes.c_double),
-                ("nodes_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("nodes_fp64", ctypes.c_int32), ("stop_m", ctypes.c_int32), ("err_est", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -246,8 +246,11 @@ def make_func(kind: str, scale: float = 1.0, alpha: float = 0.5, nodes=None, wei
     return f
 
 
-def make_params(m: int, k: int, basis_dtype=torch.float64, ell1=16, ell2=22, ell_max=1024, tol=1e-10) -> Params:
-    return Params(m, k, _DTYPE[basis_dtype], ell1, ell2, ell_max, tol)
+def make_params(m: int, k: int, basis_dtype=torch.float64, ell1=16, ell2=22, ell_max=1024, tol=1e-10,
+                check_every: int = 0, stop_tol: float = 0.0) -> Params:
+    """check_every = d > 0 turns on the sketched stopping criterion (Sec. 4.3)
+    with relative tolerance stop_tol; m is then the largest dimension."""
+    return Params(m, k, _DTYPE[basis_dtype], ell1, ell2, ell_max, tol, check_every, stop_tol)
 
 
 def solve(method: int, A: Csr, S: Sketch, b: torch.Tensor, f: Func, p: Params, x: torch.Tensor | None = None,

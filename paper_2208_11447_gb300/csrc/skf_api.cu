@@ -277,10 +277,35 @@ static size_t dtype_size(skf_dtype d) { return d == SKF_F64 ? 8 : d == SKF_F32 ?
 
 static skf_status run_arnoldi(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, skf_dtype basis,
                               void *V, int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                              skf_info *info, cudaStream_t cs) {
-    if (basis == SKF_F64) return arnoldi_run(A, S, b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
-    if (basis == SKF_F32) return arnoldi_run_f32(A, S, b, m, k, (float *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
-    return arnoldi_run_bf16(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+                              skf_info *info, cudaStream_t cs, const StepHook *hook = nullptr) {
+    if (basis == SKF_F64)
+        return arnoldi_run(A, S, b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook);
+    if (basis == SKF_F32)
+        return arnoldi_run_f32(A, S, b, m, k, (float *)V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook);
+    return arnoldi_run_bf16(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook);
+}
+
+// Checkpoints of the stopping criterion, enqueued from the Arnoldi drivers'
+// hook at p = d, 2d, ... < m as soon as the leading p columns are final.
+struct StopCtx {
+    skf_method method;
+    int s, m, d, next_p;
+    const double *vscale, *SV, *SAV;
+    int *iscal, *iscal_chk;
+    double *sf_prev, *sf_cur, *state;
+    const RuleDev *rule;
+    double tol_quad, stop_tol;
+    skf_status err;
+};
+
+static void stop_hook(void *ctx, int done, cudaStream_t st) {
+    StopCtx *k = (StopCtx *)ctx;
+    while (k->err == SKF_OK && k->next_p <= done && k->next_p < k->m) {
+        const int p = k->next_p;
+        k->next_p += k->d;
+        k->err = stop_check(k->method, k->s, p, k->vscale, k->SV, k->SAV, k->iscal, k->iscal_chk, k->sf_prev,
+                            k->sf_cur, k->state, *k->rule, k->tol_quad, k->stop_tol, st);
+    }
 }
 
 // ------------------------------------------------------------ solve parts
@@ -307,6 +332,8 @@ static skf_status solve_check(skf_method method, const skf_csr *A, const skf_ske
     }
     if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5 && f->n_nodes == 0)
         return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
+    if (p->check_every < 0 || !(p->stop_tol >= 0.0))
+        return fail(SKF_ERR_INVALID_ARG, "need check_every >= 0 and stop_tol >= 0");
     return get_rule(*f, *p, rule);
 }
 
@@ -323,7 +350,11 @@ static skf_status solve_enqueue(skf_method method, const skf_csr *A, const skf_s
     const size_t szV = dtype_size(bt) * (size_t)ldv * m;
     const size_t szS = sizeof(double) * (size_t)s * m;
     const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
-    const size_t total = al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4);
+    const bool stopping = p.check_every > 0 && p.check_every < m;
+    // stopping criterion: iscal_chk[4] | state[4] | sf_prev[s] | sf_cur[s]
+    const size_t szStop = stopping ? al(sizeof(int) * 4) + al(sizeof(double) * (4 + 2 * (size_t)s)) : 0;
+    const size_t total =
+        al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4) + szStop;
     char *ws = nullptr;
     skf_status st = dalloc((void **)&ws, total, cs);
     if (st != SKF_OK) return st;
@@ -333,10 +364,37 @@ static skf_status solve_enqueue(skf_method method, const skf_csr *A, const skf_s
     double *SAV = (double *)(ws + off); off += al(szS);
     double *H = (double *)(ws + off); off += al(szH);
     double *vscale = (double *)(ws + off); off += al(sizeof(double) * m);
-    int *iscal = (int *)(ws + off);
-    st = run_arnoldi(A, S, (const double *)b, m, p.k, bt, V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+    int *iscal = (int *)(ws + off); off += al(sizeof(int) * 4);
+    StopCtx sc{};
+    StepHook hook{};
+    if (stopping) {
+        sc.iscal_chk = (int *)(ws + off); off += al(sizeof(int) * 4);
+        sc.state = (double *)(ws + off);
+        sc.sf_prev = sc.state + 4;
+        sc.sf_cur = sc.sf_prev + s;
+        cudaMemsetAsync(sc.state, 0, sizeof(double) * (4 + 2 * (size_t)s), cs);
+        sc.method = method;
+        sc.s = s;
+        sc.m = m;
+        sc.d = p.check_every;
+        sc.next_p = p.check_every;
+        sc.vscale = vscale;
+        sc.SV = SV;
+        sc.SAV = SAV;
+        sc.iscal = iscal;
+        sc.rule = &rule;
+        sc.tol_quad = p.tol;
+        sc.stop_tol = p.stop_tol;
+        sc.err = SKF_OK;
+        hook.fn = stop_hook;
+        hook.ctx = &sc;
+    }
+    st = run_arnoldi(A, S, (const double *)b, m, p.k, bt, V, ldv, vscale, SV, SAV, H, iscal, info, cs,
+                     stopping ? &hook : nullptr);
+    if (st == SKF_OK && sc.err != SKF_OK) st = sc.err;
     if (st == SKF_OK)
-        st = tail_run(method, s, m, n, V, bt, ldv, vscale, SV, SAV, iscal, rule, p.tol, (double *)x, info, cs);
+        st = tail_run(method, s, m, n, V, bt, ldv, vscale, SV, SAV, iscal, rule, p.tol, (double *)x, info, cs,
+                      nullptr, stopping ? sc.state : nullptr);
     dfree(ws, cs);
     return st;
 }

@@ -442,19 +442,21 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_info(ArnCtx c, skf_info *i
     if (threadIdx.x == 0 && info != nullptr) {
         info->status = c.iscal[2];
         info->m_eff = me;
-        info->breakdown = (c.iscal[0] != 0 && me > 0) ? 1 : 0;
+        info->breakdown = (c.iscal[0] == 1 && me > 0) ? 1 : 0;
         info->beta = me > 0 ? 1.0 / c.vscale[0] : 0.0;
         info->eps_est = eps;
     }
 }
 
 template <int KW, int ZCAP>
-void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, cudaStream_t st) {
+void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, cudaStream_t st,
+                  const StepHook *hook) {
     auto spmv = c.max_width <= 8 ? k_arnoldi_spmv<KW, 8> : k_arnoldi_spmv<KW, 16>;
     auto update = k_arnoldi_update<KW, ZCAP>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int j = 0; j < c.m; ++j) {
         spmv<<<Gs, kSpmvThreads, 0, st>>>(c, j);
+        call_hook(hook, j, st);   // S v_i, S A v_i final for i < j
         update<<<G, kUpdThreads, smem, st>>>(c, j);
         if (sd) {   // S w_j and S y_j (exponents written by the update kernel)
             SrhtCols cols{};
@@ -473,11 +475,12 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
 }
 
 template <int ZCAP>
-void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, cudaStream_t st) {
-    if (c.k <= 2) launch_steps<2, ZCAP>(c, G, Gs, smem, sd, st);
-    else if (c.k <= 4) launch_steps<4, ZCAP>(c, G, Gs, smem, sd, st);
-    else if (c.k <= 8) launch_steps<8, ZCAP>(c, G, Gs, smem, sd, st);
-    else launch_steps<16, ZCAP>(c, G, Gs, smem, sd, st);
+void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, cudaStream_t st,
+                    const StepHook *hook) {
+    if (c.k <= 2) launch_steps<2, ZCAP>(c, G, Gs, smem, sd, st, hook);
+    else if (c.k <= 4) launch_steps<4, ZCAP>(c, G, Gs, smem, sd, st, hook);
+    else if (c.k <= 8) launch_steps<8, ZCAP>(c, G, Gs, smem, sd, st, hook);
+    else launch_steps<16, ZCAP>(c, G, Gs, smem, sd, st, hook);
 }
 
 }  // namespace
@@ -485,7 +488,7 @@ void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *
 // Host driver: launches init, m x (spmv, update), finish on `st`.
 skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V, int64_t ldv,
                        double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
-                       cudaStream_t st) {
+                       cudaStream_t st, const StepHook *hook) {
     ArnCtx c{};
     c.n = A->n;
     c.sell_off = A->sell_off;
@@ -569,9 +572,10 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     const size_t smem = c.sparse ? sizeof(int) * 4 * S->s : 0;   // two limbs for each of S v_j, S A v_j
     k_arnoldi_init<<<G, kThreads, 0, st>>>(c, b);
     const SrhtDev *sdp = c.srht ? &sd : nullptr;
-    if (c.sp.zeta <= 8) launch_steps_k<8>(c, G, Gs, smem, sdp, st);
-    else launch_steps_k<16>(c, G, Gs, smem, sdp, st);
+    if (c.sp.zeta <= 8) launch_steps_k<8>(c, G, Gs, smem, sdp, st, hook);
+    else launch_steps_k<16>(c, G, Gs, smem, sdp, st, hook);
     k_arnoldi_finish<<<G, kThreads, 0, st>>>(c);
+    call_hook(hook, m, st);
     k_arnoldi_eps<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);
     k_arnoldi_info<<<1, kThreads, 0, st>>>(c, info);
     count_launches(4 + 2ll * m);

@@ -852,6 +852,7 @@ template <typename TB>
 __global__ void __launch_bounds__(kThreads) k_arnoldi_finish_lp(LpCtx c) {
     const int me = c.iscal[1];
     if (me == 0 || c.identity) return;
+    if (c.iscal[0] == 2) return;   // stopped by the criterion: columns < me already final
     const bool stopped = c.iscal[0] != 0;
     if (stopped) finalize_column<TB>(c, me, false, false, false);
     else finalize_column<TB>(c, c.m - 1, true, false, true);
@@ -880,14 +881,15 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_info_lp(LpCtx c, skf_info 
     if (threadIdx.x == 0 && info != nullptr) {
         info->status = c.iscal[2];
         info->m_eff = me;
-        info->breakdown = (c.iscal[0] != 0 && me > 0) ? 1 : 0;
+        info->breakdown = (c.iscal[0] == 1 && me > 0) ? 1 : 0;
         info->beta = me > 0 ? 1.0 / c.vscale[0] : 0.0;
         info->eps_est = eps;
     }
 }
 
 template <int KW, int ZCAP, typename TB>
-void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, cudaStream_t st) {
+void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, cudaStream_t st,
+                  const StepHook *hook) {
     auto spmv = pipe ? k_arnoldi_spmv_lp_pipe<KW, ZCAP, TB> : k_arnoldi_spmv_lp<KW, ZCAP, TB>;
     auto update = k_arnoldi_update_lp<KW, ZCAP, TB, 0>;
     if constexpr (ZCAP == 8) {
@@ -900,24 +902,25 @@ void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, 
     const unsigned gid = (unsigned)std::min<int64_t>((c.n + kThreads - 1) / kThreads, 8ll * c.G);
     for (int j = 0; j < c.m; ++j) {
         spmv<<<c.G, kSpmvThreads, smem_spmv, st>>>(c, j);
+        if (j >= 1) call_hook(hook, j - 1, st);   // S v_i, S A v_i final for i < j - 1
         if (c.identity) k_identity_cols_lp<TB><<<gid, kThreads, 0, st>>>(c, j);
         update<<<c.G, kUpdThreads, smem_upd, st>>>(c, j);
     }
 }
 
 template <int ZCAP, typename TB>
-void launch_steps_k(const LpCtx &c, bool pipe, size_t s1, size_t s2, cudaStream_t st) {
-    if (c.k <= 2) launch_steps<2, ZCAP, TB>(c, pipe, s1, s2, st);
-    else if (c.k <= 4) launch_steps<4, ZCAP, TB>(c, pipe, s1, s2, st);
-    else if (c.k <= 8) launch_steps<8, ZCAP, TB>(c, pipe, s1, s2, st);
-    else launch_steps<16, ZCAP, TB>(c, pipe, s1, s2, st);
+void launch_steps_k(const LpCtx &c, bool pipe, size_t s1, size_t s2, cudaStream_t st, const StepHook *hook) {
+    if (c.k <= 2) launch_steps<2, ZCAP, TB>(c, pipe, s1, s2, st, hook);
+    else if (c.k <= 4) launch_steps<4, ZCAP, TB>(c, pipe, s1, s2, st, hook);
+    else if (c.k <= 8) launch_steps<8, ZCAP, TB>(c, pipe, s1, s2, st, hook);
+    else launch_steps<16, ZCAP, TB>(c, pipe, s1, s2, st, hook);
 }
 
 // Host driver: init, m x (spmv, update), finish, eps, info on `st`.
 template <typename TB>
 skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, TB *V, int64_t ldv,
                           double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
-                          cudaStream_t st) {
+                          cudaStream_t st, const StepHook *hook = nullptr) {
     LpCtx c{};
     c.n = A->n;
     c.sell_off = A->sell_off;
@@ -1015,9 +1018,10 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     cudaMemsetAsync(c.cnt, 0, szCnt, st);
 
     k_arnoldi_init_lp<TB><<<G, kChunkRows, 0, st>>>(c, b);
-    if (c.sp.zeta <= 8) launch_steps_k<8, TB>(c, pipe, smem_spmv, smem_upd, st);
-    else launch_steps_k<16, TB>(c, pipe, smem_spmv, smem_upd, st);
+    if (c.sp.zeta <= 8) launch_steps_k<8, TB>(c, pipe, smem_spmv, smem_upd, st, hook);
+    else launch_steps_k<16, TB>(c, pipe, smem_spmv, smem_upd, st, hook);
     k_arnoldi_finish_lp<TB><<<G, kThreads, 0, st>>>(c);
+    call_hook(hook, m, st);
     k_arnoldi_eps_lp<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);
     k_arnoldi_info_lp<<<1, kThreads, 0, st>>>(c, info);
     count_launches(4 + (c.identity ? 3ll : 2ll) * m);

@@ -355,21 +355,46 @@ struct RuleDev {
     int nlevels = 0;
 };
 
+// Called by the Arnoldi host drivers while they enqueue the steps: once the
+// work enqueued so far has run, columns 0 .. done-1 of S V and S A V are final
+// (done = m after the last step).  The stopping criterion enqueues its
+// checkpoints from here.  iscal[0] = 2 marks a stop by the criterion (the
+// recurrence ends at m_eff = iscal[1] with those columns already final).
+struct StepHook {
+    void (*fn)(void *ctx, int done, cudaStream_t st) = nullptr;
+    void *ctx = nullptr;
+};
+inline void call_hook(const StepHook *h, int done, cudaStream_t st) {
+    if (h && h->fn) h->fn(h->ctx, done, st);
+}
+
 skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V, int64_t ldv,
                        double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
-                       cudaStream_t st);
+                       cudaStream_t st, const StepHook *hook = nullptr);
 // Reduced-precision variants: FP32 matrix values, basis stored in FP32 or
 // BF16 (V of that type), FP32 SpMV and orthogonalisation, FP64 sketches.
 skf_status arnoldi_run_f32(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, float *V,
                            int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                           skf_info *info, cudaStream_t st);
+                           skf_info *info, cudaStream_t st, const StepHook *hook = nullptr);
 skf_status arnoldi_run_bf16(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, void *V,
                             int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                            skf_info *info, cudaStream_t st);
-// V has type vdt (F64, F32 or BF16).
+                            skf_info *info, cudaStream_t st, const StepHook *hook = nullptr);
+// V has type vdt (F64, F32 or BF16).  With sketch_out != nullptr the tail
+// writes S f = S V y (s doubles) there instead of recombining x = V y (x
+// unused).  stop_state (nullable): [1] last estimate, [2] stop step of the
+// stopping criterion, copied into info.
 skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
-                    double tol, double *x, skf_info *info, cudaStream_t st);
+                    double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out = nullptr,
+                    const double *stop_state = nullptr);
+// One checkpoint of the stopping criterion at prefix p (see skf_params):
+// the tail of the leading p columns in sketched form, then the comparison
+// with the previous checkpoint; on success sets iscal to stop at m_eff = p.
+// Work buffers: iscal_chk[4], sf_prev[s], sf_cur[s], state[4] ([0] previous
+// checkpoint valid, [1] last estimate, [2] stop step), zeroed by the caller.
+skf_status stop_check(skf_method method, int s, int p, const double *vscale, const double *SV, const double *SAV,
+                      int *iscal, int *iscal_chk, double *sf_prev, double *sf_cur, double *state, const RuleDev &rule,
+                      double tol_quad, double stop_tol, cudaStream_t st);
 
 // SRHT sketch (see skf_srht.cu): blocks of 2^b entries transformed exactly in
 // integers, b = min(kSrhtBlockLog2, log2 N').

@@ -722,8 +722,79 @@ __global__ void __launch_bounds__(kThreads) k_recombine_lp(const TB *__restrict_
     }
 }
 
-__global__ void k_write_info(TailCtx c, skf_info *info) {
+// S f = S V y = sum_j S v_j y_j with y_j = z_j / vscale_j (sketched form of
+// the approximant, for the stopping criterion); one thread per row of S.
+__global__ void __launch_bounds__(kThreads) k_sketch_f(TailCtx c, const double *__restrict__ SV, double *__restrict__ sf) {
+    const int me = c.iscal[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.s; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < me; ++j) acc = fma(SV[i + (size_t)j * c.s], c.z[j] / c.vscale[j], acc);
+        sf[i] = acc;
+    }
+}
+
+// Checkpoint p of the stopping criterion: skipped (m_eff 0 for the tail)
+// once the recurrence has stopped.
+__global__ void k_check_begin(const int *__restrict__ iscal, int *__restrict__ iscal_chk, int p) {
+    if (threadIdx.x != 0) return;
+    iscal_chk[0] = 0;
+    iscal_chk[1] = iscal[0] != 0 ? 0 : p;
+    iscal_chk[2] = SKF_OK;
+    iscal_chk[3] = p;
+}
+
+// est_p = ||S f_p - S f_{p-d}|| / sqrt(1 - eps) / (||S f_p|| / sqrt(1 + eps)),
+// eps = max_{j<p} | ||S v_j||^2 - 1 | (Sec. 4.3); on est_p <= stop_tol the
+// recurrence stops at m_eff = p.  One CTA.
+__global__ void __launch_bounds__(kThreads) k_check_end(const double *__restrict__ SV, int s, int p, int *iscal,
+                                                        const int *__restrict__ iscal_chk, double *sf_prev,
+                                                        const double *__restrict__ sf_cur, double *state,
+                                                        double stop_tol) {
+    __shared__ double red[64];
+    if (iscal_chk[1] == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double eps = 0.0;
+    for (int j = warp; j < p; j += kThreads / 32) {
+        double a = 0.0;
+        for (int i = lane; i < s; i += 32) a = fma(SV[i + (size_t)j * s], SV[i + (size_t)j * s], a);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        eps = fmax(eps, fabs(a - 1.0));
+    }
+    eps = block_max(eps, red);
+    __syncthreads();
+    double v[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+        const double d = sf_cur[i] - sf_prev[i];
+        v[0] = fma(d, d, v[0]);
+        v[1] = fma(sf_cur[i], sf_cur[i], v[1]);
+    }
+    block_sum<2>(v, red);
+    __shared__ double sv2[2];
+    if (threadIdx.x == 0) { sv2[0] = v[0]; sv2[1] = v[1]; }
+    __syncthreads();
+    const bool ok = iscal_chk[2] == SKF_OK;
+    if (threadIdx.x == 0) {
+        if (ok && state[0] != 0.0 && eps < 1.0 && sv2[1] > 0.0) {
+            const double rel = sqrt(sv2[0] / (1.0 - eps)) / sqrt(sv2[1] / (1.0 + eps));
+            state[1] = rel;
+            if (rel <= stop_tol && iscal[0] == 0) {
+                iscal[0] = 2;
+                iscal[1] = p;
+                iscal[3] = p;
+                state[2] = (double)p;
+            }
+        }
+        state[0] = ok ? 1.0 : 0.0;
+    }
+    if (ok)
+        for (int i = threadIdx.x; i < s; i += blockDim.x) sf_prev[i] = sf_cur[i];
+}
+
+__global__ void k_write_info(TailCtx c, skf_info *info, const double *stop_state) {
     if (threadIdx.x != 0 || info == nullptr) return;
+    info->stop_m = stop_state ? (int)stop_state[2] : 0;
+    info->err_est = stop_state ? stop_state[1] : 0.0;
     info->status = c.iscal[2];
     info->m_eff = c.iscal[1];
     info->ell = (int)c.qstate[1];
@@ -740,7 +811,8 @@ __global__ void k_write_info(TailCtx c, skf_info *info) {
 // as evaluating one level at a time.
 skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
-                    double tol, double *x, skf_info *info, cudaStream_t st) {
+                    double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out,
+                    const double *stop_state) {
     TailCtx c{};
     c.s = s;
     c.m = m;
@@ -843,19 +915,36 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     const int64_t rb = std::min<int64_t>((n + kThreads - 1) / kThreads, 16 * num_sms());
     const unsigned rgrid = (unsigned)std::max<int64_t>(rb, 1);
     const size_t zsm = sizeof(float) * 2 * (size_t)m;
-    if (vdt == SKF_F64) {
+    if (sketch_out) {
+        k_sketch_f<<<(s + kThreads - 1) / kThreads, kThreads, 0, st>>>(c, SV, sketch_out);
+    } else if (vdt == SKF_F64) {
         k_recombine<<<rgrid, kThreads, 0, st>>>((const double *)V, ldv, n, c.z, iscal, x);
     } else if (vdt == SKF_F32) {
         k_recombine_lp<float><<<rgrid, kThreads, zsm, st>>>((const float *)V, ldv, n, c.z, iscal, x);
     } else {
         k_recombine_lp<__nv_bfloat16><<<rgrid, kThreads, zsm, st>>>((const __nv_bfloat16 *)V, ldv, n, c.z, iscal, x);
     }
-    k_write_info<<<1, 32, 0, st>>>(c, info);
+    k_write_info<<<1, 32, 0, st>>>(c, info, stop_state);
     nlaunch += 3;
     count_launches(nlaunch);
     cudaError_t e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "tail kernels");
+    return SKF_OK;
+}
+
+skf_status stop_check(skf_method method, int s, int p, const double *vscale, const double *SV, const double *SAV,
+                      int *iscal, int *iscal_chk, double *sf_prev, double *sf_cur, double *state, const RuleDev &rule,
+                      double tol_quad, double stop_tol, cudaStream_t st) {
+    k_check_begin<<<1, 32, 0, st>>>(iscal, iscal_chk, p);
+    count_launches(1);
+    skf_status e = tail_run(method, s, p, 0, nullptr, SKF_F64, 0, vscale, SV, SAV, iscal_chk, rule, tol_quad, nullptr,
+                            nullptr, st, sf_cur, nullptr);
+    if (e != SKF_OK) return e;
+    k_check_end<<<1, kThreads, 0, st>>>(SV, s, p, iscal, iscal_chk, sf_prev, sf_cur, state, stop_tol);
+    count_launches(1);
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(ce, "stopping-criterion kernels");
     return SKF_OK;
 }
 
