@@ -37,7 +37,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes (read + write) per Arnoldi step, summed over the spmv and update
 # kernels of one ncu capture of those kernels as they stand; keyed by workload,
 # basis dtype and sketch, and removed whenever those kernels change.
-NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64", "sparse_sign"): 146.4e6, ("cd3d_n256_fp32", "f32", "sparse_sign"): 1515.9e6}
+NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64", "sparse_sign"): 143.3e6, ("cd3d_n256_fp32", "f32", "sparse_sign"): 1515.9e6}
 
 
 BASIS_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
@@ -678,7 +678,7 @@ def main():
         roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src}
     roof["traffic"] = NCU_TRAFFIC_PER_STEP.get((args.workload, basis, args.sketch))
-    kname = "k_arnoldi_spmv + k_arnoldi_update" if basis == "f64" else "k_arnoldi_spmv_lp + k_arnoldi_update_lp"
+    kname = "k_arnoldi_spmv_pipe + k_arnoldi_update" if basis == "f64" else "k_arnoldi_spmv_lp + k_arnoldi_update_lp"
     if args.sketch == "srht":
         kname += " + k_srht_blocks"
     roof.update({"kernel": f"truncated-Arnoldi step ({kname})", "us_per_step": round(step_us, 2),

@@ -240,6 +240,147 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
     }
 }
 
+// Pipelined variant of k_arnoldi_spmv for operators whose SELL slices are at
+// most 8 wide.  Rows are dealt out in chunks of kPipeRows (one row per
+// thread), chunk c to CTA c mod gridDim.x, so all CTAs sweep the rows
+// together and the stencil gathers of neighbouring chunks meet in L2.  Within
+// a CTA the loads are software-pipelined: the values, gathers and window
+// entries of chunk i, the column indices of chunk i + 1 and the slice
+// metadata of chunk i + 2 are in flight together, so a chunk costs one memory
+// round trip instead of two (column index, then gather).  Prologue and
+// epilogue are those of k_arnoldi_spmv.
+constexpr int kPipeRows = 512;
+
+// CTAs of the pipelined SpMV: one per SM, at most one per chunk.
+inline int pipe_ctas(int64_t n) {
+    const int64_t chunks = (n + kPipeRows - 1) / kPipeRows;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, num_sms()));
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, int j) {
+    __shared__ double red[BlockSumTraits<KW, kPipeRows>::kSmem];
+    if (c.iscal[0] && c.iscal[3] < j) return;
+    const int G = gridDim.x;
+    const int s = c.sp.s;
+    if (j >= 1 && !c.identity) {
+        const int frac = c.srht ? c.srht_frac : sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
+        const double sc = c.vscale[j - 1] * c.sk_scale;
+        finalize_sketch(c.skSV, c.sk_parts, s, c.ews[j - 1], frac, sc, c.SV + (size_t)(j - 1) * s);
+        finalize_sketch(c.skSAV, c.sk_parts, s, c.eys[j - 1], frac, sc, c.SAV + (size_t)(j - 1) * s);
+    }
+    const double *sc_j = c.stepsc + 4 * (size_t)j;
+    if (j >= 1 && blockIdx.x == 0 && threadIdx.x == 0) c.H[j + (size_t)(j - 1) * (c.m + 1)] = sc_j[1];
+    if (sc_j[2] != 0.0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c.iscal[0] = 1;
+            c.iscal[1] = j;
+            c.iscal[3] = j;
+            if (j == 0) c.iscal[2] = SKF_ERR_ZERO_RHS;
+        }
+        return;
+    }
+    const int i0 = max(0, j - c.k + 1);
+    const int nw = j - i0 + 1;
+    double acc[KW];
+#pragma unroll
+    for (int a = 0; a < KW; ++a) acc[a] = 0.0;
+    unsigned long long ykey = 0;
+    const double *wj = c.V + (size_t)j * c.ldv;
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (c.n + kPipeRows - 1) / kPipeRows;
+    const int64_t nc = nchunks > blockIdx.x ? (nchunks - 1 - blockIdx.x) / G + 1 : 0;
+    const int64_t step = (int64_t)G * kPipeRows;
+    const int64_t rw0 = (int64_t)blockIdx.x * kPipeRows + (threadIdx.x & ~31);   // warp's slice in chunk 0
+
+    int wt_c = 0, mw_raw = 0;
+    long long so_c = 0, mo_raw = 0;
+    if (lane == 0 && nc > 0 && rw0 < c.n) {
+        wt_c = __ldg(c.sell_w + (rw0 >> 5));
+        so_c = __ldg(c.sell_off + (rw0 >> 5));
+    }
+    wt_c = __shfl_sync(0xffffffffu, wt_c, 0);
+    so_c = __shfl_sync(0xffffffffu, so_c, 0);
+    if (lane == 0 && nc > 1 && rw0 + step < c.n) {
+        mw_raw = __ldg(c.sell_w + ((rw0 + step) >> 5));
+        mo_raw = __ldg(c.sell_off + ((rw0 + step) >> 5));
+    }
+    int cv[8];
+    {
+        const int32_t *pc = c.sell_col + so_c + lane;
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+            if (p < wt_c) cv[p] = __ldcs(pc + 32 * p);
+    }
+    for (int64_t i = 0; i < nc; ++i) {
+        const int64_t rw = rw0 + i * step;
+        const int64_t r = rw + lane;
+        const bool ok = rw < c.n && r < c.n;   // padded rows of the last slice do no work
+        // (1) values, gathers and window of chunk i
+        double av[8], xv[8], wv[KW];
+        {
+            const double *pv = c.sell_val + so_c + lane;
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < wt_c) {
+                    av[p] = __ldcs(pv + 32 * p);
+                    xv[p] = wj[cv[p]];
+                }
+#pragma unroll
+            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? c.V[r + (size_t)(i0 + a) * c.ldv] : 0.0;
+        }
+        // (2) metadata of chunk i + 1 (loaded one iteration ago) and its column indices
+        const int wt_n = __shfl_sync(0xffffffffu, mw_raw, 0);
+        const long long so_n = __shfl_sync(0xffffffffu, mo_raw, 0);
+        int cvn[8];
+        {
+            const int32_t *pc = c.sell_col + so_n + lane;
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < wt_n) cvn[p] = __ldcs(pc + 32 * p);
+        }
+        // (3) metadata of chunk i + 2
+        mw_raw = 0;
+        mo_raw = 0;
+        if (lane == 0 && i + 2 < nc && rw + 2 * step < c.n) {
+            mw_raw = __ldg(c.sell_w + ((rw + 2 * step) >> 5));
+            mo_raw = __ldg(c.sell_off + ((rw + 2 * step) >> 5));
+        }
+        // (4) y~ of chunk i
+        if (ok) {
+            double y = 0.0;
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < wt_c) y = fma(av[p], xv[p], y);
+            c.Y[r] = y;
+#pragma unroll
+            for (int a = 0; a < KW; ++a)
+                if (a < nw) acc[a] = fma(wv[a], y, acc[a]);
+            ykey = max(ykey, abs_key(y));
+        }
+        wt_c = wt_n;
+        so_c = so_n;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) cv[p] = cvn[p];
+    }
+    block_sum_auto<KW, kPipeRows>(acc, red);
+    const double ymax = key_to_abs(block_max_key<kPipeRows>(ykey, (unsigned long long *)red));
+    if (threadIdx.x == 0) {
+        double *o = c.p1 + (size_t)blockIdx.x * kP1;
+        for (int i = 0; i < KW; ++i) o[i] = acc[i];
+        o[kP1 - 1] = ymax;
+    }
+    if (last_to_arrive(c.cnt)) {
+        const int warp = threadIdx.x >> 5;
+        for (int v = warp; v <= nw; v += kPipeRows / 32) {
+            const int slot = (v < nw) ? v : kP1 - 1;
+            const double r = warp_reduce_partials(c.p1 + slot, G, kP1, slot == kP1 - 1);
+            if (lane == 0) c.fin_d[(size_t)j * kP1 + slot] = r;
+        }
+        if (threadIdx.x == 0) c.cnt[0] = 0u;
+    }
+}
+
 template <int KW, int ZCAP>
 __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j) {
     extern __shared__ int bins[];
@@ -452,10 +593,13 @@ template <int KW, int ZCAP>
 void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, cudaStream_t st,
                   const StepHook *hook) {
     auto spmv = c.max_width <= 8 ? k_arnoldi_spmv<KW, 8> : k_arnoldi_spmv<KW, 16>;
+    const bool pipe = c.max_width <= 8;
+    const int Gp = pipe_ctas(c.n);
     auto update = k_arnoldi_update<KW, ZCAP>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int j = 0; j < c.m; ++j) {
-        spmv<<<Gs, kSpmvThreads, 0, st>>>(c, j);
+        if (pipe) k_arnoldi_spmv_pipe<KW><<<Gp, kPipeRows, 0, st>>>(c, j);
+        else spmv<<<Gs, kSpmvThreads, 0, st>>>(c, j);
         call_hook(hook, j, st);   // S v_i, S A v_i final for i < j
         update<<<G, kUpdThreads, smem, st>>>(c, j);
         if (sd) {   // S w_j and S y_j (exponents written by the update kernel)
@@ -534,7 +678,7 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     char *ws = nullptr;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t szY = sizeof(double) * A->n;
-    const size_t szP1 = sizeof(double) * (size_t)std::max(G, Gs) * kP1;
+    const size_t szP1 = sizeof(double) * (size_t)std::max(std::max(G, Gs), pipe_ctas(A->n)) * kP1;
     const size_t szP2 = sizeof(double) * (size_t)G * kP2;
     const size_t szFd = sizeof(double) * (size_t)m * kP1;
     const size_t szFw = sizeof(double) * (size_t)(m + 1) * 2;
