@@ -118,6 +118,15 @@ typedef struct {
      * and quadrature) of order p. */
     int32_t check_every;
     double stop_tol;
+    /* Two-pass truncated Arnoldi (Sec. 4.2) when nonzero: the first pass
+     * keeps only the k + 2 most recent basis vectors (a ring; memory
+     * N (k + 2) instead of N m) while it builds S V_m and S A V_m; after the
+     * tail, a second pass repeats the same recurrence and accumulates
+     * f = sum_j y_j v_j as each vector appears.  Twice the products with A.
+     * The recurrence is deterministic, so the result equals the one-pass
+     * result (bit for bit with an F64 basis; for F32/BF16 the one-pass
+     * recombination sums in double-float, this one in FP64). */
+    int32_t two_pass;
 } skf_params;
 
 /* Device-written result record.  Place it in memory the device can write

@@ -45,7 +45,8 @@ class Func(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("k", ctypes.c_int32), ("basis_dtype", ctypes.c_int),
                 ("ell1", ctypes.c_int32), ("ell2", ctypes.c_int32), ("ell_max", ctypes.c_int32),
-                ("tol", ctypes.c_double), ("check_every", ctypes.c_int32), ("stop_tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("check_every", ctypes.c_int32), ("stop_tol", ctypes.c_double),
+                ("two_pass", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -247,10 +248,12 @@ def make_func(kind: str, scale: float = 1.0, alpha: float = 0.5, nodes=None, wei
 
 
 def make_params(m: int, k: int, basis_dtype=torch.float64, ell1=16, ell2=22, ell_max=1024, tol=1e-10,
-                check_every: int = 0, stop_tol: float = 0.0) -> Params:
+                check_every: int = 0, stop_tol: float = 0.0, two_pass: bool = False) -> Params:
     """check_every = d > 0 turns on the sketched stopping criterion (Sec. 4.3)
-    with relative tolerance stop_tol; m is then the largest dimension."""
-    return Params(m, k, _DTYPE[basis_dtype], ell1, ell2, ell_max, tol, check_every, stop_tol)
+    with relative tolerance stop_tol; m is then the largest dimension.
+    two_pass: the two-pass truncated Arnoldi of Sec. 4.2 (basis memory
+    N (k + 2) instead of N m, twice the products with A)."""
+    return Params(m, k, _DTYPE[basis_dtype], ell1, ell2, ell_max, tol, check_every, stop_tol, 1 if two_pass else 0)
 
 
 def solve(method: int, A: Csr, S: Sketch, b: torch.Tensor, f: Func, p: Params, x: torch.Tensor | None = None,

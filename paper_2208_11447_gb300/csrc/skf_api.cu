@@ -277,12 +277,12 @@ static size_t dtype_size(skf_dtype d) { return d == SKF_F64 ? 8 : d == SKF_F32 ?
 
 static skf_status run_arnoldi(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, skf_dtype basis,
                               void *V, int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                              skf_info *info, cudaStream_t cs, const StepHook *hook = nullptr) {
+                              skf_info *info, cudaStream_t cs, const StepHook *hook = nullptr, int vring = 0) {
     if (basis == SKF_F64)
-        return arnoldi_run(A, S, b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook);
+        return arnoldi_run(A, S, b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook, vring);
     if (basis == SKF_F32)
-        return arnoldi_run_f32(A, S, b, m, k, (float *)V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook);
-    return arnoldi_run_bf16(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook);
+        return arnoldi_run_f32(A, S, b, m, k, (float *)V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook, vring);
+    return arnoldi_run_bf16(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook, vring);
 }
 
 // Checkpoints of the stopping criterion, enqueued from the Arnoldi drivers'
@@ -297,6 +297,40 @@ struct StopCtx {
     double tol_quad, stop_tol;
     skf_status err;
 };
+
+// Second pass of the two-pass mode: x (+)= z_j w_j as each column appears;
+// a stop of the first pass by the criterion is copied to the second pass's
+// state right after its start kernel (same columns, same m_eff).
+struct AccCtx {
+    const void *V;
+    skf_dtype vdt;
+    int64_t ldv, n;
+    int vring;
+    const double *z;
+    const int *iscal1;
+    int *iscal2;
+    double *x;
+    skf_status err;
+};
+
+__global__ void k_copy_stop(const int *__restrict__ iscal1, int *__restrict__ iscal2) {
+    if (threadIdx.x == 0 && iscal1[0] == 2) {
+        iscal2[0] = 2;
+        iscal2[1] = iscal1[1];
+        iscal2[3] = iscal1[3];
+    }
+}
+
+static void acc_hook(void *ctx, int j, cudaStream_t st) {
+    AccCtx *a = (AccCtx *)ctx;
+    if (a->err != SKF_OK) return;
+    if (j == 0) {
+        k_copy_stop<<<1, 32, 0, st>>>(a->iscal1, a->iscal2);
+        count_launches(1);
+    }
+    const char *w = (const char *)a->V + (size_t)(j % a->vring) * a->ldv * dtype_size(a->vdt);
+    a->err = accumulate_column(w, a->vdt, a->z, a->iscal1, j, a->n, a->x, st);
+}
 
 static void stop_hook(void *ctx, int done, cudaStream_t st) {
     StopCtx *k = (StopCtx *)ctx;
@@ -347,14 +381,18 @@ static skf_status solve_enqueue(skf_method method, const skf_csr *A, const skf_s
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const skf_dtype bt = p.basis_dtype;
     const int64_t ldv = (n + 63) / 64 * 64;   // 256-byte aligned columns
-    const size_t szV = dtype_size(bt) * (size_t)ldv * m;
+    const bool two = p.two_pass != 0;
+    const int vring = two ? std::min(m, p.k + 2) : 0;   // ring slots of the two-pass mode
+    const size_t szV = dtype_size(bt) * (size_t)ldv * (two ? vring : m);
     const size_t szS = sizeof(double) * (size_t)s * m;
     const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
     const bool stopping = p.check_every > 0 && p.check_every < m;
     // stopping criterion: iscal_chk[4] | state[4] | sf_prev[s] | sf_cur[s]
     const size_t szStop = stopping ? al(sizeof(int) * 4) + al(sizeof(double) * (4 + 2 * (size_t)s)) : 0;
+    // two-pass: coefficients z[m] and the second pass's iscal[4]
+    const size_t szTwo = two ? al(sizeof(double) * m) + al(sizeof(int) * 4) : 0;
     const size_t total =
-        al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4) + szStop;
+        al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4) + szStop + szTwo;
     char *ws = nullptr;
     skf_status st = dalloc((void **)&ws, total, cs);
     if (st != SKF_OK) return st;
@@ -389,12 +427,29 @@ static skf_status solve_enqueue(skf_method method, const skf_csr *A, const skf_s
         hook.fn = stop_hook;
         hook.ctx = &sc;
     }
+    double *z = nullptr;
+    int *iscal2 = nullptr;
+    if (two) {
+        z = (double *)(ws + off); off += al(sizeof(double) * m);
+        iscal2 = (int *)(ws + off); off += al(sizeof(int) * 4);
+    }
     st = run_arnoldi(A, S, (const double *)b, m, p.k, bt, V, ldv, vscale, SV, SAV, H, iscal, info, cs,
-                     stopping ? &hook : nullptr);
+                     stopping ? &hook : nullptr, vring);
     if (st == SKF_OK && sc.err != SKF_OK) st = sc.err;
     if (st == SKF_OK)
-        st = tail_run(method, s, m, n, V, bt, ldv, vscale, SV, SAV, iscal, rule, p.tol, (double *)x, info, cs,
-                      nullptr, stopping ? sc.state : nullptr);
+        st = tail_run(method, s, m, n, V, bt, ldv, vscale, SV, SAV, iscal, rule, p.tol, two ? nullptr : (double *)x,
+                      info, cs, nullptr, stopping ? sc.state : nullptr, z);
+    if (st == SKF_OK && two) {
+        // second pass: the same recurrence (same sketches, H, vscale rewritten
+        // with identical values), accumulating x column by column
+        AccCtx ac{V, bt, ldv, n, vring, z, iscal, iscal2, (double *)x, SKF_OK};
+        StepHook h2{};
+        h2.col_fn = acc_hook;
+        h2.col_ctx = &ac;
+        st = run_arnoldi(A, S, (const double *)b, m, p.k, bt, V, ldv, vscale, SV, SAV, H, iscal2, nullptr, cs, &h2,
+                         vring);
+        if (st == SKF_OK) st = ac.err;
+    }
     dfree(ws, cs);
     return st;
 }

@@ -51,6 +51,7 @@ struct ArnCtx {
     int m, k;
     double *V;
     int64_t ldv;
+    int vring;         // 0: V holds all m columns; > 0: a ring of vring slots (two-pass)
     double *vscale;    // [m]
     double *SV, *SAV;  // s x m
     double *H;         // (m+1) x m
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
 #pragma unroll
     for (int i = 0; i < KW; ++i) acc[i] = 0.0;
     double ymax = 0.0;
-    const double *wj = c.V + (size_t)j * c.ldv;
+    const double *wj = c.V + vcol(c, j);
     const int64_t r0 = (int64_t)blockIdx.x * c.spmv_rows;
     const int64_t r1 = min(c.n, r0 + c.spmv_rows);
     unsigned long long ykey = 0;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
         c.Y[r] = y;
 #pragma unroll
         for (int a = 0; a < KW; ++a)
-            if (a < nw) acc[a] = fma(c.V[r + (size_t)(i0 + a) * c.ldv], y, acc[a]);
+            if (a < nw) acc[a] = fma(c.V[r + vcol(c, i0 + a)], y, acc[a]);
         ykey = max(ykey, abs_key(y));
     }
     block_sum_auto<KW, kSpmvThreads>(acc, red);
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
 #pragma unroll
     for (int a = 0; a < KW; ++a) acc[a] = 0.0;
     unsigned long long ykey = 0;
-    const double *wj = c.V + (size_t)j * c.ldv;
+    const double *wj = c.V + vcol(c, j);
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (c.n + kPipeRows - 1) / kPipeRows;
     const int64_t nc = nchunks > blockIdx.x ? (nchunks - 1 - blockIdx.x) / G + 1 : 0;
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
                     xv[p] = wj[cv[p]];
                 }
 #pragma unroll
-            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? c.V[r + (size_t)(i0 + a) * c.ldv] : 0.0;
+            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? c.V[r + vcol(c, i0 + a)] : 0.0;
         }
         // (2) metadata of chunk i + 1 (loaded one iteration ago) and its column indices
         const int wt_n = __shfl_sync(0xffffffffu, mw_raw, 0);
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
     unsigned long long nkey = 0;
     const int64_t r0 = (int64_t)blockIdx.x * c.rows_per_cta;
     const int64_t r1 = min(c.n, r0 + c.rows_per_cta);
-    double *wn = c.V + (size_t)(j + 1) * c.ldv;
+    double *wn = c.V + vcol(c, j + 1);
     // four rows per thread per iteration, all loads issued before the arithmetic
     constexpr int U = 4;
     for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += U * kUpdThreads) {
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
             yv[u] = ok ? c.Y[r] : 0.0;
 #pragma unroll
             for (int a = 0; a < KW; ++a)
-                wv[u][a] = (ok && a < nw) ? c.V[r + (size_t)(i0 + a) * c.ldv] : 0.0;
+                wv[u][a] = (ok && a < nw) ? c.V[r + vcol(c, i0 + a)] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -602,10 +603,11 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
         else spmv<<<Gs, kSpmvThreads, 0, st>>>(c, j);
         call_hook(hook, j, st);   // S v_i, S A v_i final for i < j
         update<<<G, kUpdThreads, smem, st>>>(c, j);
+        if (j + 1 < c.m) call_col_hook(hook, j + 1, st);
         if (sd) {   // S w_j and S y_j (exponents written by the update kernel)
             SrhtCols cols{};
             cols.ncols = 2;
-            cols.x[0] = c.V + (size_t)j * c.ldv;
+            cols.x[0] = c.V + (size_t)(c.vring ? j % c.vring : j) * c.ldv;
             cols.e[0] = c.ews + j;
             cols.part[0] = c.skSV;
             cols.x[1] = c.Y;
@@ -632,7 +634,7 @@ void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *
 // Host driver: launches init, m x (spmv, update), finish on `st`.
 skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V, int64_t ldv,
                        double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
-                       cudaStream_t st, const StepHook *hook) {
+                       cudaStream_t st, const StepHook *hook, int vring) {
     ArnCtx c{};
     c.n = A->n;
     c.sell_off = A->sell_off;
@@ -661,6 +663,7 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     c.k = k;
     c.V = V;
     c.ldv = ldv;
+    c.vring = vring;
     c.vscale = vscale;
     c.SV = SV;
     c.SAV = SAV;
@@ -715,6 +718,7 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
 
     const size_t smem = c.sparse ? sizeof(int) * 4 * S->s : 0;   // two limbs for each of S v_j, S A v_j
     k_arnoldi_init<<<G, kThreads, 0, st>>>(c, b);
+    call_col_hook(hook, 0, st);
     const SrhtDev *sdp = c.srht ? &sd : nullptr;
     if (c.sp.zeta <= 8) launch_steps_k<8>(c, G, Gs, smem, sdp, st, hook);
     else launch_steps_k<16>(c, G, Gs, smem, sdp, st, hook);

@@ -6,9 +6,9 @@ namespace skf {
 
 skf_status arnoldi_run_bf16(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, void *V,
                             int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                            skf_info *info, cudaStream_t st, const StepHook *hook) {
+                            skf_info *info, cudaStream_t st, const StepHook *hook, int vring) {
     return lp::arnoldi_run_lp<__nv_bfloat16>(A, S, b, m, k, (__nv_bfloat16 *)V, ldv, vscale, SV, SAV, H, iscal,
-                                             info, st, hook);
+                                             info, st, hook, vring);
 }
 
 }  // namespace skf

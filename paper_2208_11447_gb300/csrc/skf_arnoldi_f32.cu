@@ -6,8 +6,8 @@ namespace skf {
 
 skf_status arnoldi_run_f32(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, float *V,
                            int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                           skf_info *info, cudaStream_t st, const StepHook *hook) {
-    return lp::arnoldi_run_lp<float>(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, st, hook);
+                           skf_info *info, cudaStream_t st, const StepHook *hook, int vring) {
+    return lp::arnoldi_run_lp<float>(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, st, hook, vring);
 }
 
 }  // namespace skf

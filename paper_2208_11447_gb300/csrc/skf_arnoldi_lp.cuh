@@ -134,8 +134,9 @@ struct LpCtx {
     int identity;              // S = I
     int split;                 // update bins laid out [stripe][sign][p8_block] (compact pattern, zeta = 8)
     int m, k;
-    void *V;                   // TB [m][ldv]
+    void *V;                   // TB [m][ldv] (or [vring][ldv], see vcol)
     int64_t ldv;
+    int vring;                 // 0: all m columns stored; > 0: ring of vring slots (two-pass)
     double *vscale, *SV, *SAV, *H;
     float *Y;                  // [n] y_j = A w_j
     double *p1;                // [G][kP1]
@@ -329,7 +330,7 @@ __device__ __forceinline__ void spmv_stop_sketch(const LpCtx &c, int j, int *bin
     const int s = c.sp.s;
     const int L = limb_bits(*c.binmax_chunk);
     const int P = sketch_fraction_bits_from_limb(L);
-    const TB *wj = (const TB *)c.V + (size_t)j * c.ldv;
+    const TB *wj = (const TB *)c.V + vcol(c, j);
     const double wmax = c.fin_w[2 * (size_t)j + 1];
     const int ew = wmax > 0.0 ? bound_exponent(wmax) : kNoExp;
     if (blockIdx.x == 0 && threadIdx.x == 0) c.ex[j] = ew;
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, in
     }
     const int s = c.sp.s;
     const TB *V = (const TB *)c.V;
-    const TB *wj = V + (size_t)j * c.ldv;
+    const TB *wj = V + vcol(c, j);
     const int L = c.identity ? 0 : limb_bits(*c.binmax_chunk);
     const int P = sketch_fraction_bits_from_limb(L);
     const bool last = (j == c.m - 1) && !c.identity;
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, in
         // window values first: independent of the SpMV, their latency overlaps it
         float wv[KW];
 #pragma unroll
-        for (int a = 0; a < KW; ++a) wv[a] = a < nw ? Store<TB>::ld(V + (size_t)(i0 + a) * c.ldv + r) : 0.f;
+        for (int a = 0; a < KW; ++a) wv[a] = a < nw ? Store<TB>::ld(V + vcol(c, i0 + a) + r) : 0.f;
         const float *pv = c.sell_val + so + lane;   // entry p at pv[32 p]
         const int32_t *pc = c.sell_col + so + lane;
         float y = 0.f;
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp_pipe(LpCtx 
     }
     const int s = c.sp.s;
     const TB *V = (const TB *)c.V;
-    const TB *wj = V + (size_t)j * c.ldv;
+    const TB *wj = V + vcol(c, j);
     const int L = c.identity ? 0 : limb_bits(*c.binmax_chunk);
     const int P = sketch_fraction_bits_from_limb(L);
     const bool last = (j == c.m - 1) && !c.identity;
@@ -537,7 +538,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp_pipe(LpCtx 
                     xv[p] = Store<TB>::ld(wj + cv[p]);
                 }
 #pragma unroll
-            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? Store<TB>::ld(V + (size_t)(i0 + a) * c.ldv + r) : 0.f;
+            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? Store<TB>::ld(V + vcol(c, i0 + a) + r) : 0.f;
         }
         // (2) metadata of chunk i + 1 (loaded one iteration ago) and its column indices
         const int wt_n = __shfl_sync(0xffffffffu, mw_raw, 0);
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp_pipe(LpCtx 
 template <typename TB>
 __global__ void __launch_bounds__(kThreads) k_identity_cols_lp(LpCtx c, int j) {
     if (c.iscal[0] && c.iscal[3] <= j) return;
-    const TB *wj = (const TB *)c.V + (size_t)j * c.ldv;
+    const TB *wj = (const TB *)c.V + vcol(c, j);
     const double sigma = c.stepsc[4 * (size_t)j];
     const int s = c.sp.s;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < c.n; r += (int64_t)gridDim.x * blockDim.x) {
@@ -690,7 +691,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
 #pragma unroll
     for (int i = 0; i <= KW; ++i) part[i] = 0.f;
     unsigned nkey = 0;
-    TB *wn = V + (size_t)(j + 1) * c.ldv;
+    TB *wn = V + vcol(c, j + 1);
     const int lane = threadIdx.x & 31;
     const int64_t nc = chunks_of_cta(c);
     constexpr int U = KW <= 2 ? 4 : (KW <= 4 ? 2 : 1);   // chunks in flight per thread
@@ -705,7 +706,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
             yv[u] = (ok && do_update) ? c.Y[rr[u]] : 0.f;
 #pragma unroll
             for (int a = 0; a < KW; ++a)
-                wv[u][a] = (ok && a < nw) ? Store<TB>::ld(V + (size_t)(i0 + a) * c.ldv + rr[u]) : 0.f;
+                wv[u][a] = (ok && a < nw) ? Store<TB>::ld(V + vcol(c, i0 + a) + rr[u]) : 0.f;
             pvu[u] = make_uint2(0u, 0u);
             if constexpr (split)
                 if (ok) pvu[u] = __ldg((const uint2 *)(c.pattern8 + rr[u] * 8));
@@ -905,6 +906,7 @@ void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, 
         if (j >= 1) call_hook(hook, j - 1, st);   // S v_i, S A v_i final for i < j - 1
         if (c.identity) k_identity_cols_lp<TB><<<gid, kThreads, 0, st>>>(c, j);
         update<<<c.G, kUpdThreads, smem_upd, st>>>(c, j);
+        if (j + 1 < c.m) call_col_hook(hook, j + 1, st);
     }
 }
 
@@ -920,7 +922,7 @@ void launch_steps_k(const LpCtx &c, bool pipe, size_t s1, size_t s2, cudaStream_
 template <typename TB>
 skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, TB *V, int64_t ldv,
                           double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
-                          cudaStream_t st, const StepHook *hook = nullptr) {
+                          cudaStream_t st, const StepHook *hook = nullptr, int vring = 0) {
     LpCtx c{};
     c.n = A->n;
     c.sell_off = A->sell_off;
@@ -943,6 +945,7 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     c.k = k;
     c.V = V;
     c.ldv = ldv;
+    c.vring = vring;
     c.vscale = vscale;
     c.SV = SV;
     c.SAV = SAV;
@@ -1018,6 +1021,7 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     cudaMemsetAsync(c.cnt, 0, szCnt, st);
 
     k_arnoldi_init_lp<TB><<<G, kChunkRows, 0, st>>>(c, b);
+    call_col_hook(hook, 0, st);
     if (c.sp.zeta <= 8) launch_steps_k<8, TB>(c, pipe, smem_spmv, smem_upd, st, hook);
     else launch_steps_k<16, TB>(c, pipe, smem_spmv, smem_upd, st, hook);
     k_arnoldi_finish_lp<TB><<<G, kThreads, 0, st>>>(c);

@@ -360,33 +360,48 @@ struct RuleDev {
 // (done = m after the last step).  The stopping criterion enqueues its
 // checkpoints from here.  iscal[0] = 2 marks a stop by the criterion (the
 // recurrence ends at m_eff = iscal[1] with those columns already final).
+// col_fn(ctx, j, st) is called once column j of V (w_j) is written: j = 0
+// after the start kernel, j + 1 after the update of step j (the two-pass
+// mode accumulates f there before the ring slot is reused).
 struct StepHook {
     void (*fn)(void *ctx, int done, cudaStream_t st) = nullptr;
     void *ctx = nullptr;
+    void (*col_fn)(void *ctx, int j, cudaStream_t st) = nullptr;
+    void *col_ctx = nullptr;
 };
 inline void call_hook(const StepHook *h, int done, cudaStream_t st) {
     if (h && h->fn) h->fn(h->ctx, done, st);
 }
+inline void call_col_hook(const StepHook *h, int j, cudaStream_t st) {
+    if (h && h->col_fn) h->col_fn(h->col_ctx, j, st);
+}
 
 skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V, int64_t ldv,
                        double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
-                       cudaStream_t st, const StepHook *hook = nullptr);
+                       cudaStream_t st, const StepHook *hook = nullptr, int vring = 0);
 // Reduced-precision variants: FP32 matrix values, basis stored in FP32 or
 // BF16 (V of that type), FP32 SpMV and orthogonalisation, FP64 sketches.
 skf_status arnoldi_run_f32(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, float *V,
                            int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                           skf_info *info, cudaStream_t st, const StepHook *hook = nullptr);
+                           skf_info *info, cudaStream_t st, const StepHook *hook = nullptr, int vring = 0);
 skf_status arnoldi_run_bf16(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, void *V,
                             int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                            skf_info *info, cudaStream_t st, const StepHook *hook = nullptr);
+                            skf_info *info, cudaStream_t st, const StepHook *hook = nullptr, int vring = 0);
 // V has type vdt (F64, F32 or BF16).  With sketch_out != nullptr the tail
 // writes S f = S V y (s doubles) there instead of recombining x = V y (x
-// unused).  stop_state (nullable): [1] last estimate, [2] stop step of the
+// unused); with x == nullptr and no sketch_out it only forms the
+// coefficients.  z_out (nullable, m doubles): the coefficients z_j of the
+// stored columns (x = sum_j z_j w_j), zero for j >= m_eff.  stop_state (nullable): [1] last estimate, [2] stop step of the
 // stopping criterion, copied into info.
 skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
                     double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out = nullptr,
-                    const double *stop_state = nullptr);
+                    const double *stop_state = nullptr, double *z_out = nullptr);
+// Two-pass mode: x (+)= z_j w_j for basis column w_j (type vdt), j < m_eff =
+// iscal[1]; j = 0 starts x (x = 0 when m_eff = 0).  The FMA sequence per row
+// is that of the one-pass FP64 recombination.
+skf_status accumulate_column(const void *w, skf_dtype vdt, const double *z, const int *iscal, int j, int64_t n,
+                             double *x, cudaStream_t st);
 // One checkpoint of the stopping criterion at prefix p (see skf_params):
 // the tail of the leading p columns in sketched form, then the comparison
 // with the previous checkpoint; on success sets iscal to stop at m_eff = p.

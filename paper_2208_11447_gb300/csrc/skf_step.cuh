@@ -82,4 +82,12 @@ __device__ __forceinline__ bool last_to_arrive(unsigned *cnt) {
     return last;
 }
 
+// Offset of basis column j in V: column-major with leading dimension ldv,
+// or, when the basis is kept as a ring of vring slots (two-pass mode, only
+// the columns the recurrence still reads are alive), slot j mod vring.
+template <class Ctx>
+__device__ __forceinline__ size_t vcol(const Ctx &c, int j) {
+    return (size_t)(c.vring ? j % c.vring : j) * (size_t)c.ldv;
+}
+
 }  // namespace skf

@@ -692,6 +692,9 @@ __global__ void __launch_bounds__(kThreads) k_recombine(const double *__restrict
 // while running on the FP32 pipes; the pair is added in FP64 once per row.
 __device__ __forceinline__ float load_basis(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float load_basis(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ double load_basis_any(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float load_basis_any(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float load_basis_any(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
 
 template <typename TB>
 __global__ void __launch_bounds__(kThreads) k_recombine_lp(const TB *__restrict__ V, int64_t ldv, int64_t n,
@@ -730,6 +733,27 @@ __global__ void __launch_bounds__(kThreads) k_sketch_f(TailCtx c, const double *
         double acc = 0.0;
         for (int j = 0; j < me; ++j) acc = fma(SV[i + (size_t)j * c.s], c.z[j] / c.vscale[j], acc);
         sf[i] = acc;
+    }
+}
+
+// z_out[j] = z_j for j < m_eff, 0 beyond.
+__global__ void k_copy_z(TailCtx c, double *__restrict__ z_out) {
+    const int me = c.iscal[1];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < c.m) z_out[j] = j < me ? c.z[j] : 0.0;
+}
+
+// Two-pass recombination, one column at a time: x (+)= z_j w_j.
+template <typename TB>
+__global__ void __launch_bounds__(kThreads) k_accum(const TB *__restrict__ w, const double *__restrict__ z,
+                                                    const int *__restrict__ iscal, int j, int64_t n,
+                                                    double *__restrict__ x) {
+    const int me = iscal[1];
+    if (j > 0 && j >= me) return;
+    const double zj = j < me ? z[j] : 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const double wr = (double)load_basis_any(w + r);
+        x[r] = j == 0 ? fma(wr, zj, 0.0) : fma(wr, zj, x[r]);
     }
 }
 
@@ -812,7 +836,7 @@ __global__ void k_write_info(TailCtx c, skf_info *info, const double *stop_state
 skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
                     double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out,
-                    const double *stop_state) {
+                    const double *stop_state, double *z_out) {
     TailCtx c{};
     c.s = s;
     c.m = m;
@@ -915,8 +939,11 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     const int64_t rb = std::min<int64_t>((n + kThreads - 1) / kThreads, 16 * num_sms());
     const unsigned rgrid = (unsigned)std::max<int64_t>(rb, 1);
     const size_t zsm = sizeof(float) * 2 * (size_t)m;
+    if (z_out) k_copy_z<<<(m + kThreads - 1) / kThreads, kThreads, 0, st>>>(c, z_out);
     if (sketch_out) {
         k_sketch_f<<<(s + kThreads - 1) / kThreads, kThreads, 0, st>>>(c, SV, sketch_out);
+    } else if (x == nullptr) {
+        // coefficients only (two-pass mode)
     } else if (vdt == SKF_F64) {
         k_recombine<<<rgrid, kThreads, 0, st>>>((const double *)V, ldv, n, c.z, iscal, x);
     } else if (vdt == SKF_F32) {
@@ -945,6 +972,17 @@ skf_status stop_check(skf_method method, int s, int p, const double *vscale, con
     count_launches(1);
     const cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return cuda_fail(ce, "stopping-criterion kernels");
+    return SKF_OK;
+}
+
+skf_status accumulate_column(const void *w, skf_dtype vdt, const double *z, const int *iscal, int j, int64_t n,
+                             double *x, cudaStream_t st) {
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads,
+                                                                          16ll * num_sms()));
+    if (vdt == SKF_F64) k_accum<double><<<grid, kThreads, 0, st>>>((const double *)w, z, iscal, j, n, x);
+    else if (vdt == SKF_F32) k_accum<float><<<grid, kThreads, 0, st>>>((const float *)w, z, iscal, j, n, x);
+    else k_accum<__nv_bfloat16><<<grid, kThreads, 0, st>>>((const __nv_bfloat16 *)w, z, iscal, j, n, x);
+    count_launches(1);
     return SKF_OK;
 }
 
