@@ -407,7 +407,7 @@ static skf_status solve_enqueue(skf_method method, const skf_csr *A, const skf_s
     StepHook hook{};
     if (stopping) {
         sc.iscal_chk = (int *)(ws + off); off += al(sizeof(int) * 4);
-        sc.state = (double *)(ws + off);
+        sc.state = (double *)(ws + off); off += al(sizeof(double) * (4 + 2 * (size_t)s));
         sc.sf_prev = sc.state + 4;
         sc.sf_cur = sc.sf_prev + s;
         cudaMemsetAsync(sc.state, 0, sizeof(double) * (4 + 2 * (size_t)s), cs);

@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
     __shared__ double red[BlockSumTraits<KW + 1, kUpdThreads>::kSmem];
     __shared__ double sh[kMaxK];     // MGS coefficients h_ij
     __shared__ double scoef[kMaxK];  // h_ij * sigma_i
-    if (c.iscal[0]) return;          // set at the latest by the spmv launch of this step
+    if (c.iscal[0] && c.iscal[3] <= j) return;   // stopped at this step (set by its spmv launch) or earlier
     const int G = gridDim.x;
     const double *fd = c.fin_d + (size_t)j * kP1;
     const double sigma = c.stepsc[4 * (size_t)j];

@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
     __shared__ double sh[kMaxK];     // MGS coefficients h_ij
     __shared__ float scf[kMaxK];     // h_ij sigma_i in FP32, as applied
     __shared__ float sigf_s;
-    if (c.iscal[0]) return;          // set at the latest by the spmv launch of this step
+    if (c.iscal[0] && c.iscal[3] <= j) return;   // stopped at this step (set by its spmv launch) or earlier
     TB *V = (TB *)c.V;
     const int G = gridDim.x;
     const double *fd = c.fin_d + (size_t)j * kP1;
