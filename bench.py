@@ -537,6 +537,8 @@ def main():
                     help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu; "
                          "batch: the batched workload (8 operators, 64 right-hand sides) as one CUDA graph")
     ap.add_argument("--lanes", type=int, default=4, help="concurrent streams of the batched solve (batch mode)")
+    ap.add_argument("--two-pass", action="store_true",
+                    help="two-pass truncated Arnoldi (Sec. 4.2): basis ring of k + 2 vectors, twice the SpMVs")
     ap.add_argument("--batch-rhs", type=int, default=64, help="right-hand sides of the batched workload")
     ap.add_argument("--m", type=int, default=None, help="override the Krylov dimension (arnoldi mode)")
     ap.add_argument("--sketch", default="sparse_sign", choices=["sparse_sign", "srht"],
@@ -597,7 +599,7 @@ def main():
         # fixed rule: every node solved in one batch
         t_nodes, w_nodes = skf.quadrature_rule(f, int(wl.extra["ell"]))
         f = skf.make_func(wl.func, c, nodes=t_nodes, weights=w_nodes)
-    p = skf.make_params(wl.m, wl.k, basis_dtype=bdt, tol=1e-10)
+    p = skf.make_params(wl.m, wl.k, basis_dtype=bdt, tol=1e-10, two_pass=args.two_pass)
     b_dev = torch.as_tensor(b, device=dev)
     x_fom = torch.empty_like(b_dev)
     x_gm = torch.empty_like(b_dev)
@@ -725,7 +727,10 @@ def main():
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps",
                        "ell_sfom": st_f["ell"], "ell_sgmres": st_g["ell"], "status": [st_f["status_name"],
                                                                                      st_g["status_name"]],
-                       "basis": basis, "values": "f64" if A.values.dtype == np.float64 else "f32"},
+                       "basis": basis, "values": "f64" if A.values.dtype == np.float64 else "f32",
+                       "two_pass": bool(args.two_pass),
+                       "basis_bytes": int(BASIS_BYTES[basis] * ((A.n + 63) // 64 * 64)
+                                          * (min(wl.m, wl.k + 2) if args.two_pass else wl.m))},
             "accuracy": accuracy,
             "roofline": roof,
             "cpu_baseline": cpu,
