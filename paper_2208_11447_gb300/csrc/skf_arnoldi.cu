@@ -52,6 +52,7 @@ struct ArnCtx {
     double *V;
     int64_t ldv;
     int vring;         // 0: V holds all m columns; > 0: a ring of vring slots (two-pass)
+    int64_t woff[kMaxK];   // element offsets of the window columns i0 .. j of this launch's step (host-filled)
     double *vscale;    // [m]
     double *SV, *SAV;  // s x m
     double *H;         // (m+1) x m
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
         c.Y[r] = y;
 #pragma unroll
         for (int a = 0; a < KW; ++a)
-            if (a < nw) acc[a] = fma(c.V[r + vcol(c, i0 + a)], y, acc[a]);
+            if (a < nw) acc[a] = fma(c.V[r + c.woff[a]], y, acc[a]);
         ykey = max(ykey, abs_key(y));
     }
     block_sum_auto<KW, kSpmvThreads>(acc, red);
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
                     xv[p] = wj[cv[p]];
                 }
 #pragma unroll
-            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? c.V[r + vcol(c, i0 + a)] : 0.0;
+            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? c.V[r + c.woff[a]] : 0.0;
         }
         // (2) metadata of chunk i + 1 (loaded one iteration ago) and its column indices
         const int wt_n = __shfl_sync(0xffffffffu, mw_raw, 0);
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
             yv[u] = ok ? c.Y[r] : 0.0;
 #pragma unroll
             for (int a = 0; a < KW; ++a)
-                wv[u][a] = (ok && a < nw) ? c.V[r + vcol(c, i0 + a)] : 0.0;
+                wv[u][a] = (ok && a < nw) ? c.V[r + c.woff[a]] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -599,10 +600,12 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
     auto update = k_arnoldi_update<KW, ZCAP>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int j = 0; j < c.m; ++j) {
-        if (pipe) k_arnoldi_spmv_pipe<KW><<<Gp, kPipeRows, 0, st>>>(c, j);
-        else spmv<<<Gs, kSpmvThreads, 0, st>>>(c, j);
+        ArnCtx cj = c;
+        window_offsets(cj, j);
+        if (pipe) k_arnoldi_spmv_pipe<KW><<<Gp, kPipeRows, 0, st>>>(cj, j);
+        else spmv<<<Gs, kSpmvThreads, 0, st>>>(cj, j);
         call_hook(hook, j, st);   // S v_i, S A v_i final for i < j
-        update<<<G, kUpdThreads, smem, st>>>(c, j);
+        update<<<G, kUpdThreads, smem, st>>>(cj, j);
         if (j + 1 < c.m) call_col_hook(hook, j + 1, st);
         if (sd) {   // S w_j and S y_j (exponents written by the update kernel)
             SrhtCols cols{};

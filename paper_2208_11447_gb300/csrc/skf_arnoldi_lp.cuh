@@ -137,6 +137,8 @@ struct LpCtx {
     void *V;                   // TB [m][ldv] (or [vring][ldv], see vcol)
     int64_t ldv;
     int vring;                 // 0: all m columns stored; > 0: ring of vring slots (two-pass)
+    int64_t woff[kMaxK];       // element offsets of the window columns i0 .. j of this launch's step
+                               // (filled on the host per launch, so no kernel computes ring slots)
     double *vscale, *SV, *SAV, *H;
     float *Y;                  // [n] y_j = A w_j
     double *p1;                // [G][kP1]
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, in
         // window values first: independent of the SpMV, their latency overlaps it
         float wv[KW];
 #pragma unroll
-        for (int a = 0; a < KW; ++a) wv[a] = a < nw ? Store<TB>::ld(V + vcol(c, i0 + a) + r) : 0.f;
+        for (int a = 0; a < KW; ++a) wv[a] = a < nw ? Store<TB>::ld(V + c.woff[a] + r) : 0.f;
         const float *pv = c.sell_val + so + lane;   // entry p at pv[32 p]
         const int32_t *pc = c.sell_col + so + lane;
         float y = 0.f;
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp_pipe(LpCtx 
                     xv[p] = Store<TB>::ld(wj + cv[p]);
                 }
 #pragma unroll
-            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? Store<TB>::ld(V + vcol(c, i0 + a) + r) : 0.f;
+            for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? Store<TB>::ld(V + c.woff[a] + r) : 0.f;
         }
         // (2) metadata of chunk i + 1 (loaded one iteration ago) and its column indices
         const int wt_n = __shfl_sync(0xffffffffu, mw_raw, 0);
@@ -706,7 +708,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
             yv[u] = (ok && do_update) ? c.Y[rr[u]] : 0.f;
 #pragma unroll
             for (int a = 0; a < KW; ++a)
-                wv[u][a] = (ok && a < nw) ? Store<TB>::ld(V + vcol(c, i0 + a) + rr[u]) : 0.f;
+                wv[u][a] = (ok && a < nw) ? Store<TB>::ld(V + c.woff[a] + rr[u]) : 0.f;
             pvu[u] = make_uint2(0u, 0u);
             if constexpr (split)
                 if (ok) pvu[u] = __ldg((const uint2 *)(c.pattern8 + rr[u] * 8));
@@ -902,10 +904,12 @@ void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, 
         cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_upd);
     const unsigned gid = (unsigned)std::min<int64_t>((c.n + kThreads - 1) / kThreads, 8ll * c.G);
     for (int j = 0; j < c.m; ++j) {
-        spmv<<<c.G, kSpmvThreads, smem_spmv, st>>>(c, j);
+        LpCtx cj = c;
+        window_offsets(cj, j);
+        spmv<<<c.G, kSpmvThreads, smem_spmv, st>>>(cj, j);
         if (j >= 1) call_hook(hook, j - 1, st);   // S v_i, S A v_i final for i < j - 1
-        if (c.identity) k_identity_cols_lp<TB><<<gid, kThreads, 0, st>>>(c, j);
-        update<<<c.G, kUpdThreads, smem_upd, st>>>(c, j);
+        if (c.identity) k_identity_cols_lp<TB><<<gid, kThreads, 0, st>>>(cj, j);
+        update<<<c.G, kUpdThreads, smem_upd, st>>>(cj, j);
         if (j + 1 < c.m) call_col_hook(hook, j + 1, st);
     }
 }

@@ -90,4 +90,15 @@ __device__ __forceinline__ size_t vcol(const Ctx &c, int j) {
     return (size_t)(c.vring ? j % c.vring : j) * (size_t)c.ldv;
 }
 
+// Host: the window columns i0 .. j of step j (i0 = max(0, j - k + 1)) as
+// element offsets into V, in the launch's copy of the context.
+template <class Ctx>
+inline void window_offsets(Ctx &c, int j) {
+    const int i0 = j - c.k + 1 > 0 ? j - c.k + 1 : 0;
+    for (int a = 0; a < kMaxK; ++a) {
+        const int col = i0 + a <= j ? i0 + a : j;
+        c.woff[a] = (int64_t)(c.vring ? col % c.vring : col) * c.ldv;
+    }
+}
+
 }  // namespace skf
