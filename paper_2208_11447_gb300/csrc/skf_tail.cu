@@ -41,6 +41,7 @@ struct TailCtx {
     double *qacc;      // [m]
     double *z;         // [m] coefficients for V (scaled by vscale)
     double *qstate;    // [0] converged, [1] ell, [2] quad_err, [3] rdiag_ratio, [4] FP64 node solves
+    double *hsig;      // [2m] ||x(jj+1:)||^2 of each pivot column, from the previous reflector launch
     const double *t, *w;      // node table
     int nlevels;
 };
@@ -64,23 +65,46 @@ __global__ void k_tail_copy(const double *__restrict__ SV, const double *__restr
 
 // Householder reflector for column jj (LAPACK convention: beta = -sign(x0)
 // ||x||, v = [1; x(jj+1:)/(x0 - beta)], tau = (beta - x0)/beta), applied to
-// the trailing columns, one warp per trailing column.  Every warp forms the
-// reflector from column jj, which no warp modifies (its diagonal goes to
-// Rdiag), so the launch has no intra-launch dependencies.
-__global__ void __launch_bounds__(kThreads) k_householder(TailCtx c, int jj) {
+// the trailing columns, one CTA of kHhThreads per trailing column, so a
+// launch spreads over all SMs and each column's rows are read by four warps
+// at once.  Every CTA forms the reflector from column jj, which no CTA
+// modifies (its diagonal goes to Rdiag), so the launch has no intra-launch
+// dependencies.  sig = ||x(jj+1:)||^2 comes from the previous launch: the
+// CTA that updates column jj+1 sums its squares below the next diagonal right
+// after its update (hsig[jj+1]); launch 0 sums it itself.
+constexpr int kHhThreads = 128;
+
+__device__ __forceinline__ double hh_sum(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kHhThreads / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(kHhThreads) k_householder(TailCtx c, int jj) {
+    __shared__ double red[kHhThreads / 32];
     const int me = c.iscal[1];
     const int ncols = 2 * me;
     const int nref = (c.method == SKF_METHOD_SGMRES) ? 2 * me : me;
     if (jj >= nref || jj >= c.s) return;
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int tid = threadIdx.x;
+    const int gw = blockIdx.x;
     const int ntrail = ncols - jj - 1;
     if (gw >= ntrail && gw != 0) return;
     const double *x = c.Aw + (int64_t)jj * c.s;
-    double sig = 0.0;
-    for (int i = jj + 1 + lane; i < c.s; i += 32) sig = fma(x[i], x[i], sig);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
+    double sig;
+    if (jj == 0) {
+        double p = 0.0;
+        for (int i = jj + 1 + tid; i < c.s; i += kHhThreads) p = fma(x[i], x[i], p);
+        sig = hh_sum(p, red);
+    } else {
+        sig = c.hsig[jj];
+    }
     const double x0 = x[jj];
     double tau = 0.0, beta = x0, scale = 0.0;
     if (sig > 0.0 || x0 == 0.0) {
@@ -91,16 +115,24 @@ __global__ void __launch_bounds__(kThreads) k_householder(TailCtx c, int jj) {
             scale = 1.0 / (x0 - beta);
         }
     }
-    if (gw == 0 && lane == 0) c.Rdiag[jj] = beta;
-    if (tau == 0.0 || gw >= ntrail) return;
+    if (gw == 0 && tid == 0) c.Rdiag[jj] = beta;
+    if (gw >= ntrail) return;
     double *y = c.Aw + (int64_t)(jj + 1 + gw) * c.s;
-    double d = (lane == 0) ? y[jj] : 0.0;
-    for (int i = jj + 1 + lane; i < c.s; i += 32) d = fma(x[i] * scale, y[i], d);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    const double f = tau * d;
-    if (lane == 0) y[jj] -= f;
-    for (int i = jj + 1 + lane; i < c.s; i += 32) y[i] = fma(-f, x[i] * scale, y[i]);
+    if (tau != 0.0) {
+        double p = (tid == 0) ? y[jj] : 0.0;
+        for (int i = jj + 1 + tid; i < c.s; i += kHhThreads) p = fma(x[i] * scale, y[i], p);
+        const double f = tau * hh_sum(p, red);
+        if (tid == 0) y[jj] -= f;
+        for (int i = jj + 1 + tid; i < c.s; i += kHhThreads) y[i] = fma(-f, x[i] * scale, y[i]);
+    }
+    if (gw == 0 && jj + 1 < nref) {
+        // sig of the next pivot column, from the entries the CTA just wrote
+        __syncthreads();
+        double p = 0.0;
+        for (int i = jj + 2 + tid; i < c.s; i += kHhThreads) p = fma(y[i], y[i], p);
+        const double sn = hh_sum(p, red);
+        if (tid == 0) c.hsig[jj + 1] = sn;
+    }
 }
 
 constexpr int kMaxRegCol = 16;    // register slots per lane for one column of R (m <= 512)
@@ -871,7 +903,8 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                             sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * m,
                             sizeof(double) * m, sizeof(double) * chunk * mm, sizeof(double) * (size_t)cap * m,
                             sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
-                            sizeof(double) * 5, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap};
+                            sizeof(double) * 5, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
+                            sizeof(double) * 2 * (size_t)m};
     constexpr int kNbuf = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
     for (size_t v : sizes) total += al(v);
@@ -887,6 +920,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     c.Aw = ptrs[0]; c.Rdiag = ptrs[1]; c.M = ptrs[2]; c.R2 = ptrs[3]; c.B = ptrs[4]; c.C = ptrs[5];
     c.cvec = ptrs[6]; c.Mtc = ptrs[7]; c.Nw = ptrs[8]; c.out = ptrs[9]; c.qbuf = ptrs[10]; c.qacc = ptrs[11];
     c.z = ptrs[12]; c.qstate = ptrs[13]; c.MT = ptrs[14]; c.R2T = ptrs[15]; c.nodebad = (int *)ptrs[16];
+    c.hsig = ptrs[17];
 
     const int G = std::min(2 * num_sms(), 1024);
     long long nlaunch = 0;
@@ -895,7 +929,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     const int nref = (method == SKF_METHOD_SGMRES) ? 2 * m : m;
     for (int jj = 0; jj < nref; ++jj) {
         const int ntrail = std::max(1, 2 * m - jj - 1);
-        k_householder<<<(ntrail + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c, jj);
+        k_householder<<<ntrail, kHhThreads, 0, st>>>(c, jj);
     }
     nlaunch += nref;
     {
