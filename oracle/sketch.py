@@ -22,6 +22,13 @@ the diagonal of signs (-1 iff bit 0 of word(seed, c) is set) and P the first
 s entries of a partial Fisher-Yates shuffle of [0, N') driven by
 word(mix64(seed), i): position i swaps with i + (word mod (N' - i)).
 The scale makes S orthogonal when s = N' = N.
+
+SRDCT (the sketch of the paper's experiments, Sec. 5.1: S = P F E with F a
+discrete cosine transform): S x = sqrt(N/s) * (F E x)[P], F the orthonormal
+DCT-II of order N, (F y)_k = a_k sum_n y_n cos(pi k (2n + 1) / (2N)) with
+a_0 = sqrt(1/N), a_k = sqrt(2/N); E as for the SRHT, and P the first s entries
+of the same partial Fisher-Yates shuffle, of [0, N) (no padding).  The scale
+makes S orthogonal when s = N.
 """
 from __future__ import annotations
 
@@ -145,6 +152,9 @@ class Sketch:
             self.Np = 1 << max(0, math.ceil(math.log2(N)))
             self.E = srht_signs(N, seed)
             self.P = srht_rows(self.Np, s, seed)
+        elif kind == "srdct":
+            self.E = srht_signs(N, seed)
+            self.P = srht_rows(N, s, seed)
         elif kind == "identity":
             if s != N:
                 raise ValueError("identity sketch needs s == N")
@@ -157,6 +167,10 @@ class Sketch:
             return self.mat @ X
         if self.kind == "identity":
             return X.copy()
+        if self.kind == "srdct":
+            import scipy.fft
+            y = self.E.reshape((-1,) + (1,) * (X.ndim - 1)) * X
+            return scipy.fft.dct(y, type=2, norm="ortho", axis=0)[self.P] * math.sqrt(self.N / self.s)
         z = np.zeros((self.Np,) + X.shape[1:])
         z[: self.N] = (self.E.reshape((-1,) + (1,) * (X.ndim - 1)) * X)
         return fwht(z)[self.P] / math.sqrt(self.s)

@@ -93,3 +93,36 @@ def test_srht_unbiased_norm_and_padding():
     X = rng.standard_normal((100, 3))
     S = sk.Sketch("srht", 100, 32, seed=4)
     np.testing.assert_allclose(S @ X, np.column_stack([S @ X[:, i] for i in range(3)]), atol=1e-13)
+
+
+# ---- SRDCT (Sec. 5.1: S = P F E with a discrete cosine transform)
+@pytest.mark.parametrize("N", [1, 7, 12, 33])
+def test_srdct_transform_is_the_textbook_dct2(N):
+    """s = N, E and P undone: S equals sqrt(N/s) times the orthonormal DCT-II
+    written out from its cosine sum."""
+    S = sk.Sketch("srdct", N, N, seed=5)
+    D = S.dense()
+    F = np.empty((N, N))
+    for k in range(N):
+        a = math.sqrt((1.0 if k == 0 else 2.0) / N)
+        for n in range(N):
+            F[k, n] = a * math.cos(math.pi * k * (2 * n + 1) / (2 * N))
+    expect = (F * S.E[None, :])[S.P]
+    np.testing.assert_allclose(D, expect, rtol=0, atol=1e-13)
+
+
+def test_srdct_orthogonal_when_full():
+    S = sk.Sketch("srdct", 40, 40, seed=9)
+    D = S.dense()
+    np.testing.assert_allclose(D.T @ D, np.eye(40), atol=1e-13)
+
+
+def test_srdct_unbiased_norm_and_rows():
+    N, s = 300, 60
+    x = np.random.default_rng(3).standard_normal(N)
+    vals = []
+    for seed in range(200):
+        S = sk.Sketch("srdct", N, s, seed=seed)
+        assert len(set(S.P.tolist())) == s and S.P.min() >= 0 and S.P.max() < N
+        vals.append(np.sum((S @ x) ** 2))
+    assert abs(np.mean(vals) / np.sum(x ** 2) - 1.0) < 0.05
