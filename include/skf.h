@@ -63,7 +63,10 @@ typedef enum {
        use the Fourier/DCT members of this family) */
     SKF_SKETCH_SRHT = 1,
     /* S = I (requires s == N): turns sFOM into FOM (Sec. 2, comment 1) */
-    SKF_SKETCH_IDENTITY = 2
+    SKF_SKETCH_IDENTITY = 2,
+    /* subsampled randomised discrete cosine transform, the sketch of the
+       paper's experiments (Sec. 5.1, S = P F E with F a DCT) */
+    SKF_SKETCH_SRDCT = 3
 } skf_sketch_kind;
 
 typedef enum { SKF_BORROW = 0, SKF_COPY = 1 } skf_copy_mode;
@@ -197,6 +200,12 @@ skf_status skf_csr_norm_inf(const skf_csr *A, double *out_host);
  *   SRHT: S x = s^-1/2 (H E [x; 0])[P], N' = 2^ceil(log2 N), E_c = -1 iff
  *     word(seed, c) & 1, P = first s entries of a partial Fisher-Yates
  *     shuffle of [0, N') with word(mix64(seed), i).  Requires s <= N'.
+ *   SRDCT: S x = sqrt(N/s) (F E x)[P], F the orthonormal DCT-II of order N
+ *     ((F y)_k = a_k sum_n y_n cos(pi k (2n+1) / (2N)), a_0 = sqrt(1/N),
+ *     a_k = sqrt(2/N)), E as for SRHT, P the first s entries of the same
+ *     partial Fisher-Yates shuffle, of [0, N).  Requires s <= N.  Applied as
+ *     s direct dot products against a table of cos(pi j / (2N)), j < 4N
+ *     (O(s N) work per vector: meant for the paper's N ~ 1e4 examples).
  *   IDENTITY: requires s == N.
  * Errors: INVALID_ARG, OOM, CUDA, NOT_SUPPORTED. */
 skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t zeta, uint64_t seed,
@@ -213,7 +222,9 @@ skf_status skf_sketch_destroy(skf_sketch *S);
  * entries (H_{N'} = H_{N'/B} (x) H_B), inputs rounded at 2^-(62 - log2 B) of
  * the column max, and the block contributions to each sampled row are summed
  * exactly.  The SRHT is available for F64 X and, in the Arnoldi process and
- * the solvers, for an F64 basis.  Errors: INVALID_ARG, OOM, CUDA. */
+ * the solvers, for an F64 basis.  SRDCT sums in FP64 in a fixed order
+ * (deterministic, not exact); F64 X and an F64 basis, like the SRHT.
+ * Errors: INVALID_ARG, OOM, CUDA. */
 skf_status skf_sketch_apply(const skf_sketch *S, const void *X, skf_dtype xdtype, int64_t ldx,
                             int32_t ncols, double *SX, skf_stream_t stream);
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libskf.so")
 
 # enums of include/skf.h
 F64, F32, BF16 = 0, 1, 2
-SPARSE_SIGN, SRHT, IDENTITY = 0, 1, 2
+SPARSE_SIGN, SRHT, IDENTITY, SRDCT = 0, 1, 2, 3
 BORROW, COPY = 0, 1
 INVSQRT, LOG1P_OVER_Z, INV, INVPOW = 0, 1, 2, 3
 SFOM, SGMRES = 0, 1

@@ -697,7 +697,7 @@ skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t
     } else if (kind == SKF_SKETCH_IDENTITY) {
         if (s != n) return fail(SKF_ERR_INVALID_ARG, "identity sketch needs s == n");
         zeta = 1;
-    } else if (kind == SKF_SKETCH_SRHT) {
+    } else if (kind == SKF_SKETCH_SRHT || kind == SKF_SKETCH_SRDCT) {
         zeta = 0;
     } else {
         return fail(SKF_ERR_INVALID_ARG, "unknown sketch kind");
@@ -708,9 +708,10 @@ skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t
     S->s = s;
     S->zeta = zeta;
     S->seed = seed;
-    if (kind == SKF_SKETCH_SPARSE_SIGN || kind == SKF_SKETCH_SRHT) {
-        const skf_status st =
-            kind == SKF_SKETCH_SRHT ? build_srht_tables(S) : build_sparse_sign_tables(S, (cudaStream_t)stream);
+    if (kind != SKF_SKETCH_IDENTITY) {
+        const skf_status st = kind == SKF_SKETCH_SRHT    ? build_srht_tables(S)
+                              : kind == SKF_SKETCH_SRDCT ? build_srdct_tables(S)
+                                                         : build_sparse_sign_tables(S, (cudaStream_t)stream);
         if (st != SKF_OK) {
             skf_sketch_destroy(S);
             return st;
@@ -726,6 +727,8 @@ skf_status skf_sketch_destroy(skf_sketch *S) {
     if (S->pattern) cudaFree(S->pattern);
     if (S->binmax) cudaFree(S->binmax);
     if (S->pattern8) cudaFree(S->pattern8);
+    if (S->E) cudaFree(S->E);
+    if (S->costab) cudaFree(S->costab);
     delete S;
     return SKF_OK;
 }

@@ -45,6 +45,7 @@ struct ArnCtx {
     int identity;      // S = I
     int sparse;        // sparse-sign S (scattered by the update kernel)
     int srht;          // SRHT S (separate block-transform kernels after each update)
+    int direct;        // SRDCT S: S v_j, S A v_j written directly by a kernel after each update
     int sk_parts;      // integer partials per sketch column (update CTAs or SRHT blocks)
     int srht_frac;     // SRHT fixed-point fraction bits
     double sk_scale;   // scale of the integer sums: 1/sqrt(zeta) or 1/sqrt(s)
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
     const int s = c.sp.s;
 
     // S v_{j-1} and S A v_{j-1} from the integer partials of the previous step
-    if (j >= 1 && !c.identity) {
+    if (j >= 1 && !c.identity && !c.direct) {
         const int frac = c.srht ? c.srht_frac : sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
         const double sc = c.vscale[j - 1] * c.sk_scale;
         finalize_sketch(c.skSV, c.sk_parts, s, c.ews[j - 1], frac, sc, c.SV + (size_t)(j - 1) * s);
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
     if (c.iscal[0] && c.iscal[3] < j) return;
     const int G = gridDim.x;
     const int s = c.sp.s;
-    if (j >= 1 && !c.identity) {
+    if (j >= 1 && !c.identity && !c.direct) {
         const int frac = c.srht ? c.srht_frac : sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
         const double sc = c.vscale[j - 1] * c.sk_scale;
         finalize_sketch(c.skSV, c.sk_parts, s, c.ews[j - 1], frac, sc, c.SV + (size_t)(j - 1) * s);
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
 
 // After the loop: S v_{m-1} and S A v_{m-1}.
 __global__ void __launch_bounds__(kThreads) k_arnoldi_finish(ArnCtx c) {
-    if (c.iscal[0] == 0 && !c.identity) {
+    if (c.iscal[0] == 0 && !c.identity && !c.direct) {
         const int frac = c.srht ? c.srht_frac : sketch_fraction_bits_from_limb(limb_bits(*c.binmax));
         const double sc = c.vscale[c.m - 1] * c.sk_scale;
         finalize_sketch(c.skSV, c.sk_parts, c.sp.s, c.ews[c.m - 1], frac, sc, c.SV + (size_t)(c.m - 1) * c.sp.s);
@@ -592,8 +593,8 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_info(ArnCtx c, skf_info *i
 }
 
 template <int KW, int ZCAP>
-void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, cudaStream_t st,
-                  const StepHook *hook) {
+void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, const SrdctDev *dd,
+                  cudaStream_t st, const StepHook *hook) {
     auto spmv = c.max_width <= 8 ? k_arnoldi_spmv<KW, 8> : k_arnoldi_spmv<KW, 16>;
     const bool pipe = c.max_width <= 8;
     const int Gp = pipe_ctas(c.n);
@@ -607,6 +608,18 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
         call_hook(hook, j, st);   // S v_i, S A v_i final for i < j
         update<<<G, kUpdThreads, smem, st>>>(cj, j);
         if (j + 1 < c.m) call_col_hook(hook, j + 1, st);
+        if (dd) {   // SV[:, j] = sigma_j S w_j, SAV[:, j] = sigma_j S y_j
+            SrdctCols cols{};
+            cols.ncols = 2;
+            cols.x[0] = c.V + (size_t)(c.vring ? j % c.vring : j) * c.ldv;
+            cols.x[1] = c.Y;
+            cols.out[0] = c.SV + (size_t)j * c.sp.s;
+            cols.out[1] = c.SAV + (size_t)j * c.sp.s;
+            cols.colscale = c.stepsc + 4 * (size_t)j;
+            cols.iscal = c.iscal;
+            cols.step = j;
+            srdct_launch(*dd, cols, st);
+        }
         if (sd) {   // S w_j and S y_j (exponents written by the update kernel)
             SrhtCols cols{};
             cols.ncols = 2;
@@ -624,12 +637,12 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
 }
 
 template <int ZCAP>
-void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, cudaStream_t st,
-                    const StepHook *hook) {
-    if (c.k <= 2) launch_steps<2, ZCAP>(c, G, Gs, smem, sd, st, hook);
-    else if (c.k <= 4) launch_steps<4, ZCAP>(c, G, Gs, smem, sd, st, hook);
-    else if (c.k <= 8) launch_steps<8, ZCAP>(c, G, Gs, smem, sd, st, hook);
-    else launch_steps<16, ZCAP>(c, G, Gs, smem, sd, st, hook);
+void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, const SrdctDev *dd,
+                    cudaStream_t st, const StepHook *hook) {
+    if (c.k <= 2) launch_steps<2, ZCAP>(c, G, Gs, smem, sd, dd, st, hook);
+    else if (c.k <= 4) launch_steps<4, ZCAP>(c, G, Gs, smem, sd, dd, st, hook);
+    else if (c.k <= 8) launch_steps<8, ZCAP>(c, G, Gs, smem, sd, dd, st, hook);
+    else launch_steps<16, ZCAP>(c, G, Gs, smem, sd, dd, st, hook);
 }
 
 }  // namespace
@@ -648,7 +661,10 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     c.identity = S->kind == SKF_SKETCH_IDENTITY;
     c.sparse = S->kind == SKF_SKETCH_SPARSE_SIGN;
     c.srht = S->kind == SKF_SKETCH_SRHT;
+    c.direct = S->kind == SKF_SKETCH_SRDCT;
     SrhtDev sd{};
+    SrdctDev dd{};
+    if (c.direct) dd = make_srdct(S);
     if (c.sparse) {
         c.sp = make_sparse_sign(S);
         c.pattern = S->pattern;
@@ -723,8 +739,9 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     k_arnoldi_init<<<G, kThreads, 0, st>>>(c, b);
     call_col_hook(hook, 0, st);
     const SrhtDev *sdp = c.srht ? &sd : nullptr;
-    if (c.sp.zeta <= 8) launch_steps_k<8>(c, G, Gs, smem, sdp, st, hook);
-    else launch_steps_k<16>(c, G, Gs, smem, sdp, st, hook);
+    const SrdctDev *ddp = c.direct ? &dd : nullptr;
+    if (c.sp.zeta <= 8) launch_steps_k<8>(c, G, Gs, smem, sdp, ddp, st, hook);
+    else launch_steps_k<16>(c, G, Gs, smem, sdp, ddp, st, hook);
     k_arnoldi_finish<<<G, kThreads, 0, st>>>(c);
     call_hook(hook, m, st);
     k_arnoldi_eps<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);

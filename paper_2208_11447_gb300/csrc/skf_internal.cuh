@@ -68,8 +68,10 @@ struct skf_sketch {
     int64_t n = 0;
     int32_t s = 0, zeta = 0;
     uint64_t seed = 0;
-    int64_t np = 0;                   // SRHT: padded length N'
-    int32_t *P = nullptr;             // SRHT: s sampled rows (device)
+    int64_t np = 0;                   // SRHT: padded length N' (SRDCT: N)
+    int32_t *P = nullptr;             // SRHT, SRDCT: s sampled rows (device)
+    double *E = nullptr;              // SRDCT: the N signs (device)
+    double *costab = nullptr;         // SRDCT: cos(pi j / (2N)), j = 0 .. 4N-1 (device)
     // Sparse-sign pattern, expanded once from the seed: entry [c * zeta + q]
     // holds the row of nonzero q of column c inside stripe q (bits 0-14) and
     // its sign (bit 15).  2 zeta bytes per column.
@@ -437,6 +439,32 @@ SrhtDev make_srht(const skf_sketch *S);
 skf_status build_srht_tables(skf_sketch *S);
 void srht_launch(const SrhtDev &d, const SrhtCols &cols, cudaStream_t st);
 skf_status srht_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX, cudaStream_t st);
+
+// SRDCT sketch (see skf_srdct.cu): direct O(sN) evaluation of the sampled
+// rows of the orthonormal DCT-II.
+struct SrdctDev {
+    int64_t n;
+    int s;
+    const int32_t *P;       // [s] sampled rows
+    const double *E;        // [n] signs
+    const double *costab;   // [4n] cos(pi j / (2n))
+};
+// Up to two columns: out[q][i] = colscale * (S x[q])_i (colscale a device
+// scalar or nullptr for 1); iscal/step as for SrhtCols.
+struct SrdctCols {
+    const double *x[2];
+    double *out[2];
+    const double *colscale;
+    int ncols;
+    const int *iscal;
+    int step;
+};
+SrdctDev make_srdct(const skf_sketch *S);
+skf_status build_srdct_tables(skf_sketch *S);
+void srdct_launch(const SrdctDev &d, const SrdctCols &cols, cudaStream_t st);
+skf_status srdct_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX, cudaStream_t st);
+// P: the first s entries of the partial Fisher-Yates shuffle of [0, np) (device).
+skf_status build_sampled_rows(skf_sketch *S, int64_t np);
 
 // Sketch-apply launcher shared by the API and the solvers.
 skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st);

@@ -246,6 +246,7 @@ skf_status sketch_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, i
         return SKF_OK;
     }
     if (S->kind == SKF_SKETCH_SRHT) return srht_apply_f64(S, X, ldx, ncols, SX, st);
+    if (S->kind == SKF_SKETCH_SRDCT) return srdct_apply_f64(S, X, ldx, ncols, SX, st);
     if (S->kind != SKF_SKETCH_SPARSE_SIGN) return fail(SKF_ERR_NOT_SUPPORTED, "sketch kind not implemented");
     const SparseSign sp = make_sparse_sign(S);
     int G;

@@ -130,7 +130,11 @@ skf_status build_srht_tables(skf_sketch *S) {
     while (np < S->n) np <<= 1;
     if ((int64_t)S->s > np) return fail(SKF_ERR_INVALID_ARG, "SRHT needs s <= N' = 2^ceil(log2 N)");
     S->np = np;
-    // P: first s entries of a partial Fisher-Yates shuffle of 0..N'-1
+    return build_sampled_rows(S, np);
+}
+
+skf_status build_sampled_rows(skf_sketch *S, int64_t np) {
+    // P: first s entries of a partial Fisher-Yates shuffle of 0..np-1
     const uint64_t seed2 = mix64(S->seed);
     std::unordered_map<int64_t, int64_t> swapped;
     std::vector<int32_t> P(S->s);
