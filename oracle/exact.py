@@ -26,6 +26,8 @@ def fAb_dense(A: np.ndarray, b: np.ndarray, func: str, alpha: float = 0.5) -> np
         return np.real(np.linalg.solve(A, L @ b))
     if func == "inv":
         return np.linalg.solve(A, b)
+    if func == "exp_neg":
+        return sla.expm(-A) @ b
     raise ValueError(func)
 
 

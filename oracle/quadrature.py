@@ -12,6 +12,19 @@ weights w_i with f(z) ~= sum_i w_i / (t_i + z).
   integrand becomes 2c / ([(1+x) + c(1-x)] [(1+z)(1+x) + c(1-x)]), integrated
   by Gauss-Legendre.
 * 1/z: the single node t = 0 with weight 1.
+* e^{-z} (not a Stieltjes function; the contour form of Algorithm 2): by
+  Cauchy's formula in the pole variable t = -z,
+  f(A) b = (1/(2 pi i)) oint f(-t) (t I + A)^{-1} b dt, on a contour that
+  winds once counterclockwise around the points -lambda(A).  The contour is
+  the parabola t(zeta) = a - c zeta^2 + i zeta (Sec. 5.2), zeta in R, along
+  which e^{t} decays like e^{-c zeta^2}; the trapezoidal rule in zeta with
+  step h on [-L, L], c L^2 = 37, converges exponentially.  For real A and b
+  the terms at zeta and -zeta are complex conjugates, so the rule keeps the
+  nodes zeta_k = k h, k = 0 .. ell-1 (h = L / (ell - 1)), doubles the weights
+  of k >= 1, and f(A) b is the real part of the sum:
+      t_k = a - c zeta_k^2 + i zeta_k,
+      w_k = (2 - [k = 0]) h e^{t_k} (i - 2 c zeta_k) / (2 pi i).
+  Here `alpha` carries the vertex a and `c` the width parameter.
 
 The scale c > 0 is an input (chosen from a spectral interval by the caller).
 """
@@ -76,7 +89,21 @@ def rule_log1p_over_z(ell: int, c: float):
     return t, w
 
 
+def rule_exp_neg(ell: int, c: float, a: float):
+    if ell < 2:
+        raise ValueError("the contour rule needs ell >= 2")
+    L = math.sqrt(37.0 / c)
+    h = L / (ell - 1)
+    zeta = h * np.arange(ell)
+    t = a - c * zeta ** 2 + 1j * zeta
+    w = h * np.exp(t) * (1j - 2.0 * c * zeta) / (2j * math.pi)
+    w[1:] *= 2.0
+    return t, w
+
+
 def rule(func: str, ell: int, c: float, alpha: float = 0.5):
+    if func == "exp_neg":
+        return rule_exp_neg(ell, c, alpha)
     if func == "invsqrt":
         return rule_invpow(ell, c, 0.5)
     if func == "invpow":
@@ -104,6 +131,8 @@ def fscalar(func: str, z, alpha: float = 0.5):
         return out
     if func == "inv":
         return 1.0 / z
+    if func == "exp_neg":
+        return np.exp(-z)
     raise ValueError(func)
 
 

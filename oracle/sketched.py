@@ -44,6 +44,8 @@ def whiten(SV: np.ndarray, SAV: np.ndarray, Sb: np.ndarray):
 def matfunc_apply(func: str, M: np.ndarray, c: np.ndarray, alpha: float = 0.5) -> np.ndarray:
     """f(M) c for the principal branch, by Schur-based dense routines."""
     ev = np.linalg.eigvals(M)
+    if func == "exp_neg":
+        return sla.expm(-M) @ c
     if func in ("invsqrt", "invpow", "inv"):
         cut = -0.0
     elif func == "log1p_over_z":
@@ -84,16 +86,16 @@ def sfom_closed(W: dict, func: str, alpha: float = 0.5) -> np.ndarray:
 
 
 def sfom_quadrature(W: dict, func: str, c_scale: float, ell=None, ell1=16, ell2=22,
-                    tol=1e-10, ell_max=1024):
+                    tol=1e-10, ell_max=1024, alpha: float = 0.5):
     M, cvec = W["M"], W["c"]
     m = M.shape[0]
 
     def q(ell_):
-        t, w = quad.rule(func, ell_, c_scale)
-        acc = np.zeros(m)
+        t, w = quad.rule(func, ell_, c_scale, alpha)
+        acc = np.zeros(m, dtype=np.result_type(t, w, np.float64))
         for ti, wi in zip(t, w):
             acc += wi * np.linalg.solve(ti * np.eye(m) + M, cvec)
-        return acc
+        return acc.real   # complex contour nodes: the rule's real part (see quadrature)
 
     if func == "inv":
         ell = 1
@@ -105,15 +107,15 @@ def sfom_quadrature(W: dict, func: str, c_scale: float, ell=None, ell1=16, ell2=
 
 
 def sgmres_quadrature(W: dict, func: str, c_scale: float, ell=None, ell1=16, ell2=22,
-                      tol=1e-10, ell_max=1024):
+                      tol=1e-10, ell_max=1024, alpha: float = 0.5):
     Q, Z, Sb = W["Q"], W["Z"], W["Sb"]
 
     def q(ell_):
-        t, w = quad.rule(func, ell_, c_scale)
-        acc = np.zeros(Q.shape[1])
+        t, w = quad.rule(func, ell_, c_scale, alpha)
+        acc = np.zeros(Q.shape[1], dtype=np.result_type(t, w, np.float64))
         for ti, wi in zip(t, w):
             acc += wi * np.linalg.lstsq(ti * Q + Z, Sb, rcond=None)[0]
-        return acc
+        return acc.real   # complex contour nodes: the rule's real part (see quadrature)
 
     if func == "inv":
         ell = 1
@@ -136,9 +138,9 @@ def solve(A, b, func: str, m: int, k: int, S, c_scale: float, method: str = "sgm
     if method == "sfom":
         y = sfom_closed(W, func, alpha)
     elif method == "sfom_quad":
-        y, info["ell"] = sfom_quadrature(W, func, c_scale, ell, ell1, ell2, tol, ell_max)
+        y, info["ell"] = sfom_quadrature(W, func, c_scale, ell, ell1, ell2, tol, ell_max, alpha)
     elif method == "sgmres":
-        y, info["ell"] = sgmres_quadrature(W, func, c_scale, ell, ell1, ell2, tol, ell_max)
+        y, info["ell"] = sgmres_quadrature(W, func, c_scale, ell, ell1, ell2, tol, ell_max, alpha)
     else:
         raise ValueError(method)
     info["arnoldi"] = ar
