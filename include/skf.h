@@ -75,7 +75,8 @@ typedef enum {
     SKF_FUNC_INVSQRT = 0,       /* f(z) = z^(-1/2)                         */
     SKF_FUNC_LOG1P_OVER_Z = 1,  /* f(z) = log(1 + z) / z                   */
     SKF_FUNC_INV = 2,           /* f(z) = 1/z (single node t = 0): tests   */
-    SKF_FUNC_INVPOW = 3         /* f(z) = z^(-alpha), 0 < alpha < 1        */
+    SKF_FUNC_INVPOW = 3,        /* f(z) = z^(-alpha), 0 < alpha < 1        */
+    SKF_FUNC_EXP_NEG = 4        /* f(z) = exp(-z): contour rule, see skf_func */
 } skf_func_kind;
 
 typedef enum { SKF_METHOD_SFOM = 0, SKF_METHOD_SGMRES = 1 } skf_method;
@@ -89,8 +90,19 @@ typedef struct skf_sketch skf_sketch; /* opaque embedding handle        */
  *     1/2) in x, t = scale (1-x)/(1+x)  (Sec. 5.1 uses scale = 1),
  *   LOG1P_OVER_Z: Gauss-Legendre in x, t = 1 + scale (1-x)/(1+x),
  *   INV: t = 0, w = 1.
+ *   EXP_NEG (not a Stieltjes function; Algorithm 2 with a fixed contour):
+ *     Cauchy's formula in the pole variable t = -z, f(A) b =
+ *     (1/(2 pi i)) oint f(-t) (t I + A)^{-1} b dt, on the parabola
+ *     t(zeta) = a - c zeta^2 + i zeta (Sec. 5.2) with a = alpha and
+ *     c = scale; it must enclose -Lambda (the negated spectrum and Ritz
+ *     values: every -lambda left of the parabola).  Trapezoidal rule in zeta
+ *     on [0, L], c L^2 = 37, h = L / (ell - 1), weights of zeta > 0 doubled
+ *     (the conjugate half, real A and b), f(A) b = Re sum_k w_k (t_k I +
+ *     A)^{-1} b with t_k = t(k h), w_k = (2 - [k = 0]) h e^{t_k}
+ *     (i - 2 c k h) / (2 pi i).  Complex nodes: the node systems are solved
+ *     through their real 2m x 2m form (requires m <= 256, ell1 >= 2).
  * If n_nodes > 0 the host arrays nodes/weights are used as the only rule
- * (no adaptivity). */
+ * (no adaptivity; real rules only). */
 typedef struct {
     skf_func_kind kind;
     double alpha;           /* exponent for SKF_FUNC_INVPOW */
@@ -338,8 +350,13 @@ typedef struct {
 skf_status skf_solve_batched(int32_t nprob, const skf_problem *probs, int32_t lanes, skf_stream_t stream);
 
 /* skf_quadrature_rule: host copy of the rule of order ell for f (the same
- * nodes and weights the solvers use).  t_host, w_host: host double[ell]. */
+ * nodes and weights the solvers use).  t_host, w_host: host double[ell].
+ * NOT_SUPPORTED for EXP_NEG (complex rule: skf_quadrature_rule_c). */
 skf_status skf_quadrature_rule(const skf_func *f, int32_t ell, double *t_host, double *w_host);
+/* skf_quadrature_rule_c: the same with real and imaginary parts (host
+ * double[ell] each); for the real rules the imaginary parts are zero. */
+skf_status skf_quadrature_rule_c(const skf_func *f, int32_t ell, double *t_re, double *t_im, double *w_re,
+                                 double *w_im);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,8 @@ SFOM, SGMRES = 0, 1
 STATUS = {0: "SKF_OK", 1: "SKF_ERR_INVALID_ARG", 2: "SKF_ERR_CUDA", 3: "SKF_ERR_OOM",
           4: "SKF_ERR_ILL_CONDITIONED", 5: "SKF_ERR_BRANCH_CUT", 6: "SKF_ERR_QUAD_NOT_CONVERGED",
           7: "SKF_ERR_SKETCH_TOO_SMALL", 8: "SKF_ERR_NOT_SUPPORTED", 9: "SKF_ERR_ZERO_RHS"}
-FUNC_KIND = {"invsqrt": INVSQRT, "log1p_over_z": LOG1P_OVER_Z, "inv": INV, "invpow": INVPOW}
+EXP_NEG = 4
+FUNC_KIND = {"invsqrt": INVSQRT, "log1p_over_z": LOG1P_OVER_Z, "inv": INV, "invpow": INVPOW, "exp_neg": EXP_NEG}
 _DTYPE = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 
 
@@ -98,11 +99,12 @@ def lib():
         L.skf_sfom.argtypes = L.skf_solve.argtypes[1:]
         L.skf_sgmres.argtypes = L.skf_solve.argtypes[1:]
         L.skf_quadrature_rule.argtypes = [ctypes.POINTER(Func), i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        L.skf_quadrature_rule_c.argtypes = [ctypes.POINTER(Func), i32] + [ctypes.POINTER(dbl)] * 4
         L.skf_solve_batched.argtypes = [i32, ctypes.POINTER(Problem), i32, vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
                      "skf_solve", "skf_solve_batched", "skf_sfom",
-                     "skf_sgmres", "skf_quadrature_rule"]:
+                     "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -319,6 +321,15 @@ def quadrature_rule(f: Func, ell: int):
     _check(lib().skf_quadrature_rule(ctypes.byref(f), ell, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                      w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return t, w
+
+
+def quadrature_rule_c(f: Func, ell: int):
+    """Complex nodes and weights (t, w) of the rule of order ell (numpy complex)."""
+    import numpy as np
+    arrs = [np.empty(ell) for _ in range(4)]
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(lib().skf_quadrature_rule_c(ctypes.byref(f), ell, *[ptr(a) for a in arrs]))
+    return arrs[0] + 1j * arrs[1], arrs[2] + 1j * arrs[3]
 
 
 @dataclass

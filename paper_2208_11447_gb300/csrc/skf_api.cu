@@ -88,6 +88,26 @@ static void gauss_legendre_theta(int n, std::vector<double> &theta, std::vector<
     }
 }
 
+// Contour rule for f(z) = exp(-z) on the parabola t(zeta) = a - c zeta^2 +
+// i zeta (a = f.alpha, c = f.scale): trapezoidal rule in zeta on [0, L],
+// c L^2 = 37, step h = L / (ell - 1), weights of zeta > 0 doubled (the
+// conjugate half of the contour): w = h e^t (i - 2 c zeta) / (2 pi i).
+static bool contour_rule(const skf_func &f, int ell, double *tr, double *ti, double *wr, double *wi) {
+    if (f.kind != SKF_FUNC_EXP_NEG || ell < 2 || !(f.scale > 0.0)) return false;
+    const double c = f.scale, a = f.alpha;
+    const double L = sqrt(37.0 / c), h = L / (ell - 1);
+    for (int k = 0; k < ell; ++k) {
+        const double z = k * h;
+        const double mag = (k == 0 ? 1.0 : 2.0) * h * exp(a - c * z * z) / (2.0 * M_PI);
+        const double cs = cos(z), sn = sin(z);
+        tr[k] = a - c * z * z;
+        ti[k] = z;
+        wr[k] = mag * (cs - 2.0 * c * z * sn);
+        wi[k] = mag * (sn + 2.0 * c * z * cs);
+    }
+    return true;
+}
+
 bool quadrature_rule(const skf_func &f, int ell, double *t, double *w) {
     if (f.kind == SKF_FUNC_INV) {
         t[0] = 0.0;
@@ -163,21 +183,38 @@ static skf_status get_rule(const skf_func &f, const skf_params &p, const RuleDev
             ells.push_back(nx);
         }
     }
-    std::vector<double> ht, hw;
+    std::vector<double> ht, hw, hti, hwi;
     std::vector<int> hs{0};
+    const bool cplx = f.n_nodes == 0 && f.kind == SKF_FUNC_EXP_NEG;
     for (int ell : ells) {
         const size_t o = ht.size();
         ht.resize(o + ell);
         hw.resize(o + ell);
+        hti.resize(o + ell);
+        hwi.resize(o + ell);
         if (f.n_nodes > 0) {
             std::copy(f.nodes, f.nodes + ell, ht.begin() + o);
             std::copy(f.weights, f.weights + ell, hw.begin() + o);
+        } else if (cplx) {
+            if (!contour_rule(f, ell, ht.data() + o, hti.data() + o, hw.data() + o, hwi.data() + o))
+                return fail(SKF_ERR_INVALID_ARG, "contour rule needs ell >= 2 and scale > 0");
         } else if (!quadrature_rule(f, ell, ht.data() + o, hw.data() + o)) {
             return fail(SKF_ERR_NOT_SUPPORTED, "quadrature family not implemented for this function");
         }
         hs.push_back((int)ht.size());
     }
     RuleDev *r = new RuleDev();
+    r->cplx = cplx;
+    if (cplx) {
+        if (cudaMalloc(&r->t_im, sizeof(double) * hti.size()) != cudaSuccess ||
+            cudaMalloc(&r->w_im, sizeof(double) * hwi.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SKF_ERR_OOM, "rule table allocation failed");
+        }
+        if (cudaMemcpy(r->t_im, hti.data(), sizeof(double) * hti.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(r->w_im, hwi.data(), sizeof(double) * hwi.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "rule table upload");
+    }
     r->nlevels = (int)ells.size();
     r->h_start = hs;
     r->h_ell = ells;
@@ -366,6 +403,11 @@ static skf_status solve_check(skf_method method, const skf_csr *A, const skf_ske
     }
     if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5 && f->n_nodes == 0)
         return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
+    if (f->kind == SKF_FUNC_EXP_NEG) {
+        if (f->n_nodes > 0) return fail(SKF_ERR_NOT_SUPPORTED, "explicit rules are real; exp(-z) uses the contour");
+        if (p->ell1 < 2) return fail(SKF_ERR_INVALID_ARG, "the contour rule needs ell1 >= 2");
+        if (p->m > 256) return fail(SKF_ERR_NOT_SUPPORTED, "complex quadrature nodes need m <= 256");
+    }
     if (p->check_every < 0 || !(p->stop_tol >= 0.0))
         return fail(SKF_ERR_INVALID_ARG, "need check_every >= 0 and stop_tol >= 0");
     return get_rule(*f, *p, rule);
@@ -831,8 +873,25 @@ skf_status skf_sgmres(const skf_csr *A, const skf_sketch *S, const void *b, skf_
     return skf_solve(SKF_METHOD_SGMRES, A, S, b, bdtype, f, p, x, xdtype, info, stream);
 }
 
+skf_status skf_quadrature_rule_c(const skf_func *f, int32_t ell, double *t_re, double *t_im, double *w_re,
+                                 double *w_im) {
+    if (!f || !t_re || !t_im || !w_re || !w_im || ell < 1) return fail(SKF_ERR_INVALID_ARG, "bad argument");
+    if (f->kind != SKF_FUNC_EXP_NEG) {
+        if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5)
+            return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
+        if (!quadrature_rule(*f, ell, t_re, w_re)) return fail(SKF_ERR_NOT_SUPPORTED, "unknown function");
+        for (int i = 0; i < ell; ++i) t_im[i] = w_im[i] = 0.0;
+        return SKF_OK;
+    }
+    if (!contour_rule(*f, ell, t_re, t_im, w_re, w_im))
+        return fail(SKF_ERR_INVALID_ARG, "the contour rule needs ell >= 2 and scale > 0");
+    return SKF_OK;
+}
+
 skf_status skf_quadrature_rule(const skf_func *f, int32_t ell, double *t_host, double *w_host) {
     if (!f || !t_host || !w_host || ell < 1) return fail(SKF_ERR_INVALID_ARG, "bad argument");
+    if (f->kind == SKF_FUNC_EXP_NEG)
+        return fail(SKF_ERR_NOT_SUPPORTED, "exp(-z) has a complex contour rule: skf_quadrature_rule_c");
     if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5)
         return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
     if (!quadrature_rule(*f, ell, t_host, w_host)) return fail(SKF_ERR_NOT_SUPPORTED, "unknown function");

@@ -351,7 +351,9 @@ void dfree(void *p, cudaStream_t st);
 
 // Quadrature levels of the adaptive schedule on the device.
 struct RuleDev {
-    double *t = nullptr, *w = nullptr;               // all nodes, level after level
+    double *t = nullptr, *w = nullptr;               // all nodes, level after level (real parts)
+    double *t_im = nullptr, *w_im = nullptr;         // imaginary parts (contour rules), else nullptr
+    bool cplx = false;
     int *lev_start = nullptr, *lev_ell = nullptr;    // device [nlevels+1], [nlevels]
     std::vector<int> h_start, h_ell;                 // host copies
     int nlevels = 0;

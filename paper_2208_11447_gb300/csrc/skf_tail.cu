@@ -43,6 +43,7 @@ struct TailCtx {
     double *qstate;    // [0] converged, [1] ell, [2] quad_err, [3] rdiag_ratio, [4] FP64 node solves
     double *hsig;      // [2m] ||x(jj+1:)||^2 of each pivot column, from the previous reflector launch
     const double *t, *w;      // node table
+    const double *ti, *wi;    // imaginary parts of complex (contour) nodes and weights, or nullptr
     int nlevels;
 };
 
@@ -389,15 +390,16 @@ template <typename T> size_t node_smem_bytes(int m) {
     return sizeof(double) * 4 * (size_t)m + sizeof(T) * ((size_t)mp * kNB + kKC * kNB + 32 * 32 + kNB);
 }
 
-// Blocked left-looking Cholesky N(t) = L L^T, N(t) = t^2 I + t B + C (B, C:
-// lower triangles, ld m), L lower in global memory (column-major, ld m), in
-// precision T.  Each panel of kNB columns is formed as N(t) minus the product
-// of the already factored rows (register tiles, one row per thread), then
-// factored in shared memory (right-looking, pivot division deferred to a final
-// scaling).  Returns false on a nonpositive pivot (uniform over the CTA).
-template <typename T>
-__device__ bool chol_blocked(const TailCtx &c, double t, int me, T *L, const NodeSmem<T> &sm) {
-    const int m = c.m, mp = sm.mp, tid = threadIdx.x;
+// Blocked left-looking Cholesky of a symmetric positive definite matrix N
+// of order me, N_ij (i >= j) given by the functor nval, into L lower in
+// global memory (column-major, leading dimension ld), in precision T.  Each
+// panel of kNB columns is formed as N minus the product of the already
+// factored rows (register tiles, one row per thread), then factored in shared
+// memory (right-looking, pivot division deferred to a final scaling).
+// Returns false on a nonpositive pivot (uniform over the CTA).
+template <typename T, class NF>
+__device__ bool chol_blocked_f(NF nval, int me, int ld, T *L, const NodeSmem<T> &sm) {
+    const int mp = sm.mp, tid = threadIdx.x;
     for (int c0 = 0; c0 < me; c0 += kNB) {
         const int nb = min(kNB, me - c0), rows = me - c0;
         T acc[kNB];
@@ -408,13 +410,13 @@ __device__ bool chol_blocked(const TailCtx &c, double t, int me, T *L, const Nod
             __syncthreads();
             for (int idx = tid; idx < kc * kNB; idx += blockDim.x) {
                 const int q = idx / kNB, jj = idx % kNB;
-                sm.Lt[idx] = jj < nb ? L[(c0 + jj) + (int64_t)(pk + q) * m] : (T)0;
+                sm.Lt[idx] = jj < nb ? L[(c0 + jj) + (int64_t)(pk + q) * ld] : (T)0;
             }
             __syncthreads();
             if (tid < rows) {
-                const T *lrow = L + (c0 + tid) + (int64_t)pk * m;
+                const T *lrow = L + (c0 + tid) + (int64_t)pk * ld;
                 for (int q = 0; q < kc; ++q) {
-                    const T a = lrow[(int64_t)q * m];
+                    const T a = lrow[(int64_t)q * ld];
                     const T *lt = sm.Lt + q * kNB;
 #pragma unroll
                     for (int u = 0; u < kNB; ++u) acc[u] = fma(a, lt[u], acc[u]);
@@ -428,8 +430,7 @@ __device__ bool chol_blocked(const TailCtx &c, double t, int me, T *L, const Nod
             for (int u = 0; u < kNB; ++u) {
                 const int j = c0 + u;
                 T v = (T)0;
-                if (u < nb && i >= j)
-                    v = (T)((i == j ? t * t : 0.0) + t * c.B[i + (int64_t)j * m] + c.C[i + (int64_t)j * m]) - acc[u];
+                if (u < nb && i >= j) v = (T)nval(i, j) - acc[u];
                 sm.P[tid + u * mp] = v;
             }
         }
@@ -449,11 +450,22 @@ __device__ bool chol_blocked(const TailCtx &c, double t, int me, T *L, const Nod
         __syncthreads();
         for (int idx = tid; idx < rows * nb; idx += blockDim.x) {
             const int r = idx % rows, k = idx / rows;
-            if (r >= k) L[(c0 + r) + (int64_t)(c0 + k) * m] = (r == k) ? sm.sd[k] : sm.P[r + k * mp] / sm.sd[k];
+            if (r >= k) L[(c0 + r) + (int64_t)(c0 + k) * ld] = (r == k) ? sm.sd[k] : sm.P[r + k * mp] / sm.sd[k];
         }
         __syncthreads();
     }
     return true;
+}
+
+// The normal matrix of a real node t, N(t) = t^2 I + t B + C (B, C: lower
+// triangles, ld m), factored as above with ld = m.
+template <typename T>
+__device__ bool chol_blocked(const TailCtx &c, double t, int me, T *L, const NodeSmem<T> &sm) {
+    const int m = c.m;
+    const double *B = c.B, *C = c.C;
+    return chol_blocked_f<T>(
+        [=](int i, int j) { return (i == j ? t * t : 0.0) + t * B[i + (int64_t)j * m] + C[i + (int64_t)j * m]; },
+        me, m, L, sm);
 }
 
 // z <- (L L^T)^{-1} z with the global factor of chol_blocked; z is FP64 in
@@ -608,6 +620,99 @@ __global__ void __launch_bounds__(kNodeThreads) k_nodes_g(TailCtx c, int n0, int
     if (MIXED && threadIdx.x == 0) c.nodebad[row] = conv ? 0 : 1;
     if (conv)
         for (int a = threadIdx.x; a < me; a += blockDim.x) c.out[(size_t)row * m + a] = wt * y[a];
+}
+
+// Complex nodes (contour rules for a non-Stieltjes f, Algorithm 2): for
+// t = alpha + i beta the node problem min || [t I + M; R2] y - [c; 0] || (or
+// (t I + M) y = c for sFOM) is solved in real arithmetic for y = u + i v:
+// the normal matrix of the real 4m x 2m least-squares problem
+//   [[A1, -beta I], [beta I, A1], [R2, 0], [0, R2]] [u; v] ~ [c; 0; 0; 0],
+// A1 = alpha I + M, is the 2m x 2m symmetric positive definite
+//   [[N(alpha) + beta^2 I, beta (M - M^T)], [beta (M^T - M), N(alpha) + beta^2 I]]
+// with N(alpha) = alpha^2 I + alpha B + C, and the right-hand side
+// [alpha c + M^T c; -beta c].  FP64 factor (blocked, global slot of order
+// 2 m_eff), solve, one refinement step on the residual of the original
+// problem; the node contributes Re(w y) = Re(w) u - Im(w) v.
+__device__ void node_residual_cplx(const TailCtx &c, double al, double be, int me, const double *y, double *rt,
+                                   double *rb, double *g, bool gm) {
+    const int m = c.m;
+    const double *u = y, *v = y + me;
+    __syncthreads();
+    for (int a = threadIdx.x; a < me; a += blockDim.x) {
+        double mu = 0.0, mv = 0.0;
+        for (int j = 0; j < me; ++j) {
+            const double mij = c.M[a + (int64_t)j * m];
+            mu = fma(mij, u[j], mu);
+            mv = fma(mij, v[j], mv);
+        }
+        rt[a] = c.cvec[a] - al * u[a] - mu + be * v[a];      // r1
+        rt[me + a] = -be * u[a] - al * v[a] - mv;            // r2
+        if (gm) {
+            double ru = 0.0, rv = 0.0;
+            for (int j = a; j < me; ++j) {
+                ru = fma(-c.R2[a + (int64_t)j * m], u[j], ru);
+                rv = fma(-c.R2[a + (int64_t)j * m], v[j], rv);
+            }
+            rb[a] = ru;        // r3
+            rb[me + a] = rv;   // r4
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < me; j += blockDim.x) {
+        double g1 = al * rt[j] + be * rt[me + j], g2 = -be * rt[j] + al * rt[me + j];
+        for (int a = 0; a < me; ++a) {
+            const double mt = c.MT[j + (int64_t)a * m];
+            g1 = fma(mt, rt[a], g1);
+            g2 = fma(mt, rt[me + a], g2);
+        }
+        if (gm)
+            for (int a = 0; a <= j; ++a) {
+                const double r2t = c.R2T[j + (int64_t)a * m];
+                g1 = fma(r2t, rb[a], g1);
+                g2 = fma(r2t, rb[me + a], g2);
+            }
+        g[j] = g1;
+        g[me + j] = g2;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kNodeThreads) k_nodes_cplx(TailCtx c, int n0, int off) {
+    extern __shared__ __align__(16) unsigned char nsm_raw[];
+    const int me = c.iscal[1];
+    if (c.qstate[0] != 0.0 || me == 0) return;
+    const int m = c.m, m2 = 2 * me, ld = 2 * m;
+    const NodeSmem<double> sm = node_smem<double>(nsm_raw, 2 * m);
+    const int row = off + blockIdx.x;
+    double *L = c.Nw + (size_t)blockIdx.x * 4 * (size_t)m * m;
+    const int nd = n0 + row;
+    const double al = c.t[nd], be = c.ti[nd], wr = c.w[nd], wim = c.wi[nd];
+    const bool gm = c.method == SKF_METHOD_SGMRES;
+    const double *B = c.B, *C = c.C, *Mm = c.M;
+    const bool ok = chol_blocked_f<double>(
+        [=](int i, int j) {
+            const int bi = i >= me, bj = j >= me;
+            const int ii = i - bi * me, jj = j - bj * me;
+            if (bi == bj)
+                return (ii == jj ? al * al + be * be : 0.0) + al * B[ii + (int64_t)jj * m] + C[ii + (int64_t)jj * m];
+            return be * (Mm[jj + (int64_t)ii * m] - Mm[ii + (int64_t)jj * m]);   // block (2,1) = beta (M^T - M)
+        },
+        m2, ld, L, sm);
+    if (!ok) {
+        for (int a = threadIdx.x; a < me; a += blockDim.x) c.out[(size_t)row * m + a] = 0.0;
+        if (threadIdx.x == 0) atomicExch(&c.iscal[2], gm ? (int)SKF_ERR_ILL_CONDITIONED : (int)SKF_ERR_BRANCH_CUT);
+        return;
+    }
+    double *y = sm.y, *rt = sm.rt, *rb = sm.rb, *g = sm.g;
+    for (int a = threadIdx.x; a < me; a += blockDim.x) {
+        y[a] = al * c.cvec[a] + c.Mtc[a];
+        y[me + a] = -be * c.cvec[a];
+    }
+    chol_solve_g<double>(L, m2, ld, y, sm);
+    node_residual_cplx(c, al, be, me, y, rt, rb, g, gm);
+    chol_solve_g<double>(L, m2, ld, g, sm);
+    for (int a = threadIdx.x; a < me; a += blockDim.x)
+        c.out[(size_t)row * m + a] = wr * (y[a] + g[a]) - wim * (y[me + a] + g[me + a]);
 }
 
 // Sum the node solutions of each level of the batch, then run the
@@ -876,6 +981,8 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     c.iscal = iscal;
     c.vscale = vscale;
     c.t = rule.t;
+    c.ti = rule.t_im;
+    c.wi = rule.w_im;
     c.w = rule.w;
     c.nlevels = rule.nlevels;
     int max_level = 0;
@@ -901,7 +1008,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     const size_t mm = (size_t)m * m;
     const size_t sizes[] = {sizeof(double) * (size_t)s * 2 * m, sizeof(double) * 2 * m, sizeof(double) * mm,
                             sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * m,
-                            sizeof(double) * m, sizeof(double) * chunk * mm, sizeof(double) * (size_t)cap * m,
+                            sizeof(double) * m, sizeof(double) * chunk * mm * (rule.cplx ? 4 : 1), sizeof(double) * (size_t)cap * m,
                             sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
                             sizeof(double) * 5, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
                             sizeof(double) * 2 * (size_t)m};
@@ -946,6 +1053,9 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     const bool packed = m <= kMixedMaxM;
     const size_t msmem = sizeof(double) * 4 * m + sizeof(float) * ((size_t)m + (size_t)m * (m + 1) / 2);
     const size_t gsm32 = node_smem_bytes<float>(m), gsm64 = node_smem_bytes<double>(m);
+    const size_t gsmC = node_smem_bytes<double>(2 * m);
+    if (rule.cplx && gsmC > 48 * 1024)
+        cudaFuncSetAttribute(k_nodes_cplx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmC);
     if (packed && msmem > 48 * 1024)
         cudaFuncSetAttribute(k_nodes_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
     if (!packed && gsm32 > 48 * 1024)
@@ -958,9 +1068,13 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
         const int nn = rule.h_start[l0 + nl] - n0;
         for (int o = 0; o < nn; o += chunk) {
             const int nb = std::min(chunk, nn - o);
-            if (packed) k_nodes_mixed<<<nb, kThreads, msmem, st>>>(c, n0, o);
-            else k_nodes_g<float, true><<<nb, kNodeThreads, gsm32, st>>>(c, n0, o);
-            k_nodes_g<double, false><<<nb, kNodeThreads, gsm64, st>>>(c, n0, o);
+            if (rule.cplx) {
+                k_nodes_cplx<<<nb, kNodeThreads, gsmC, st>>>(c, n0, o);
+            } else {
+                if (packed) k_nodes_mixed<<<nb, kThreads, msmem, st>>>(c, n0, o);
+                else k_nodes_g<float, true><<<nb, kNodeThreads, gsm32, st>>>(c, n0, o);
+                k_nodes_g<double, false><<<nb, kNodeThreads, gsm64, st>>>(c, n0, o);
+            }
             nlaunch += 2;
         }
         k_levels<<<1, kThreads, 0, st>>>(c, l0, nl, rule.lev_start, rule.lev_ell, n0, tol,

@@ -80,3 +80,14 @@ def test_quadrature_rule_reproduces_f(skf, func, lo, hi, ell):
     z = np.geomspace(lo, hi, 60)
     approx = (w[None, :] / (t[None, :] + z[:, None])).sum(1)
     np.testing.assert_allclose(approx, np.real(fscalar(func, z)), rtol=2e-13)
+
+
+@pytest.mark.parametrize("ell,c,a", [(2, 1.0, 0.0), (64, 0.1, 0.5), (200, 0.02, -0.3)])
+def test_contour_rule_matches_oracle(skf, ell, c, a):
+    """exp(-z) contour rule (parabola of Sec. 5.2, trapezoidal in its
+    parameter): the library's host rule equals the oracle's."""
+    from oracle import quadrature as oq
+    t, w = skf.quadrature_rule_c(skf.make_func("exp_neg", c, alpha=a), ell)
+    to, wo = oq.rule("exp_neg", ell, c, a)
+    np.testing.assert_allclose(t, to, rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(w, wo, rtol=1e-12, atol=1e-300)
