@@ -37,7 +37,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes (read + write) per Arnoldi step, summed over the spmv and update
 # kernels of one ncu capture of those kernels as they stand; keyed by workload,
 # basis dtype and sketch, and removed whenever those kernels change.
-NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64", "sparse_sign"): 143.3e6, ("cd3d_n256_fp32", "f32", "sparse_sign"): 1516.3e6}
+NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64", "sparse_sign"): 143.5e6, ("cd3d_n256_fp32", "f32", "sparse_sign"): 1516.3e6}
 
 
 BASIS_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
@@ -423,8 +423,14 @@ def run_batch(args, rank, world, local, dev):
     t64 = replica_max(timed(fp64_one_at_a_time, args.steps), world, dev)
 
     # FP64 batch as one CUDA graph: the headline
+    lane_times = None
+    if args.lanes == "auto":
+        graph64, lane_times = skf.BatchGraph.autotune(probs64)
+        lanes = graph64.lanes
+    else:
+        lanes = int(args.lanes)
     l0 = skf.kernel_launch_count()
-    graph64 = skf.BatchGraph(probs64, lanes=args.lanes)     # one eager run + capture
+    graph64 = skf.BatchGraph(probs64, lanes=lanes)          # one eager run + capture
     launches_per_batch = (skf.kernel_launch_count() - l0) // 2
     for _ in range(args.warmup):
         graph64.replay()
@@ -459,7 +465,7 @@ def run_batch(args, rank, world, local, dev):
     del graph64
 
     # FP32-basis batch as one CUDA graph
-    graph32 = skf.BatchGraph(probs32, lanes=args.lanes)
+    graph32 = skf.BatchGraph(probs32, lanes=lanes)
     for _ in range(args.warmup):
         graph32.replay()
     torch.cuda.synchronize()
@@ -493,7 +499,7 @@ def run_batch(args, rank, world, local, dev):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batch_cd_8x64", **layout.summary(), "k": 2, "s": "4 m_r", "zeta": 8,
                        "f": BATCH_FUNC, "method": "sgmres", "quad_tol": 1e-10, "basis": "f64", "values": "f32-rounded",
-                       "lanes": args.lanes, "graph": "one CUDA graph per batch",
+                       "lanes": lanes, "lane_autotune_ms": lane_times, "graph": "one CUDA graph per batch",
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
             "accuracy": {"vs": "FP64 one-at-a-time GPU path, same problems", "max_rel_err": max(errs64b),
                          "bitwise_equal": equal64, "within_1e-6": sum(1 for e in errs64b if e <= tol), "of": nprob,
@@ -536,7 +542,8 @@ def main():
     ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi", "batch"],
                     help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu; "
                          "batch: the batched workload (8 operators, 64 right-hand sides) as one CUDA graph")
-    ap.add_argument("--lanes", type=int, default=4, help="concurrent streams of the batched solve (batch mode)")
+    ap.add_argument("--lanes", default="auto",
+                    help="concurrent streams of the batched solve (batch mode): a count, or auto (timed choice of 4/8/16)")
     ap.add_argument("--two-pass", action="store_true",
                     help="two-pass truncated Arnoldi (Sec. 4.2): basis ring of k + 2 vectors, twice the SpMVs")
     ap.add_argument("--batch-rhs", type=int, default=64, help="right-hand sides of the batched workload")

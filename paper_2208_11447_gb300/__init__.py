@@ -309,6 +309,27 @@ class BatchGraph:
     def replay(self):
         self.graph.replay()
 
+    @classmethod
+    def autotune(cls, problems, candidates=(4, 8, 16)):
+        """Capture the batch once per lane count, time one replay of each
+        (after a warm one) with CUDA events, and keep the fastest.  Returns
+        (graph, {lanes: ms})."""
+        times, best = {}, None
+        for lanes in candidates:
+            g = cls(problems, lanes)
+            g.replay()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            g.replay()
+            ev1.record()
+            ev1.synchronize()
+            times[lanes] = ev0.elapsed_time(ev1)
+            if best is None or times[lanes] < times[best.lanes]:
+                best = g
+            else:
+                del g
+        return best, times
+
 
 def kernel_launch_count() -> int:
     return int(lib().skf_kernel_launch_count())
