@@ -41,6 +41,8 @@ struct ArnCtx {
     int max_width;             // widest SELL slice
     SparseSign sp;
     const uint16_t *pattern;   // expanded sparse-sign pattern [n][zeta]
+    const uint8_t *pattern8;   // compact pattern [n][8] when zeta = 8 (row in stripe + p8_block * sign), or nullptr
+    int p8_block;              // its sign offset: 64 or 128
     const int *binmax;         // bin-load maximum of the row partition
     int identity;      // S = I
     int sparse;        // sparse-sign S (scattered by the update kernel)
@@ -247,11 +249,12 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
 // most 8 wide.  Rows are dealt out in chunks of kPipeRows (one row per
 // thread), chunk c to CTA c mod gridDim.x, so all CTAs sweep the rows
 // together and the stencil gathers of neighbouring chunks meet in L2.  Within
-// a CTA the loads are software-pipelined: the values, gathers and window
-// entries of chunk i, the column indices of chunk i + 1 and the slice
-// metadata of chunk i + 2 are in flight together, so a chunk costs one memory
-// round trip instead of two (column index, then gather).  Prologue and
-// epilogue are those of k_arnoldi_spmv.
+// a CTA the loads are software-pipelined four deep: while the FP64 products
+// of chunk i run, the values, gathers and window entries of chunk i + 1, the
+// column indices of chunk i + 2 and the slice metadata of chunk i + 3 are in
+// flight, so a chunk costs the longer of its arithmetic and one memory round
+// trip rather than their sum.  Prologue and epilogue are those of
+// k_arnoldi_spmv.
 constexpr int kPipeRows = 512;
 
 // CTAs of the pipelined SpMV: one per SM, at most one per chunk.
@@ -296,60 +299,108 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
     const int64_t step = (int64_t)G * kPipeRows;
     const int64_t rw0 = (int64_t)blockIdx.x * kPipeRows + (threadIdx.x & ~31);   // warp's slice in chunk 0
 
-    int wt_c = 0, mw_raw = 0;
-    long long so_c = 0, mo_raw = 0;
-    if (lane == 0 && nc > 0 && rw0 < c.n) {
-        wt_c = __ldg(c.sell_w + (rw0 >> 5));
-        so_c = __ldg(c.sell_off + (rw0 >> 5));
+    // Stage state at the top of iteration i: values, gathers and window of
+    // chunk i (in flight since iteration i - 1), slice metadata and column
+    // indices of chunk i + 1, lane 0's raw metadata of chunk i + 2.  Wide
+    // windows (KW > 4) are loaded in their own iteration: two sets of them
+    // would not fit in the registers.
+    constexpr bool kWinAhead = KW <= 4;
+    int wr0 = 0, wr1 = 0;
+    long long or0 = 0, or1 = 0;
+    if (lane == 0) {
+        if (nc > 0 && rw0 < c.n) {
+            wr0 = __ldg(c.sell_w + (rw0 >> 5));
+            or0 = __ldg(c.sell_off + (rw0 >> 5));
+        }
+        if (nc > 1 && rw0 + step < c.n) {
+            wr1 = __ldg(c.sell_w + ((rw0 + step) >> 5));
+            or1 = __ldg(c.sell_off + ((rw0 + step) >> 5));
+        }
     }
-    wt_c = __shfl_sync(0xffffffffu, wt_c, 0);
-    so_c = __shfl_sync(0xffffffffu, so_c, 0);
-    if (lane == 0 && nc > 1 && rw0 + step < c.n) {
-        mw_raw = __ldg(c.sell_w + ((rw0 + step) >> 5));
-        mo_raw = __ldg(c.sell_off + ((rw0 + step) >> 5));
-    }
-    int cv[8];
+    int wt_c = __shfl_sync(0xffffffffu, wr0, 0);
+    const long long so_c = __shfl_sync(0xffffffffu, or0, 0);
+    int wt_n = __shfl_sync(0xffffffffu, wr1, 0);
+    long long so_n = __shfl_sync(0xffffffffu, or1, 0);
+    int cv[8], cvn[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) cv[p] = cvn[p] = 0;
     {
         const int32_t *pc = c.sell_col + so_c + lane;
+        const int32_t *pn = c.sell_col + so_n + lane;
 #pragma unroll
-        for (int p = 0; p < 8; ++p)
+        for (int p = 0; p < 8; ++p) {
             if (p < wt_c) cv[p] = __ldcs(pc + 32 * p);
+            if (p < wt_n) cvn[p] = __ldcs(pn + 32 * p);
+        }
+    }
+    int mw_raw = 0;
+    long long mo_raw = 0;
+    if (lane == 0 && nc > 2 && rw0 + 2 * step < c.n) {
+        mw_raw = __ldg(c.sell_w + ((rw0 + 2 * step) >> 5));
+        mo_raw = __ldg(c.sell_off + ((rw0 + 2 * step) >> 5));
+    }
+    double av[8], xv[8], wv[KW];
+    {
+        const double *pv = c.sell_val + so_c + lane;
+        const bool ok = nc > 0 && rw0 < c.n && rw0 + lane < c.n;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            av[p] = 0.0;
+            xv[p] = 0.0;
+            if (p < wt_c) {
+                av[p] = __ldcs(pv + 32 * p);
+                xv[p] = wj[cv[p]];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < KW; ++a) wv[a] = (kWinAhead && ok && a < nw) ? c.V[rw0 + lane + c.woff[a]] : 0.0;
     }
     for (int64_t i = 0; i < nc; ++i) {
         const int64_t rw = rw0 + i * step;
         const int64_t r = rw + lane;
         const bool ok = rw < c.n && r < c.n;   // padded rows of the last slice do no work
-        // (1) values, gathers and window of chunk i
-        double av[8], xv[8], wv[KW];
+        // (1) values, gathers and window of chunk i + 1 (wt_n = 0 past the end)
+        double avn[8], xvn[8], wvn[KW];
         {
-            const double *pv = c.sell_val + so_c + lane;
+            const double *pv = c.sell_val + so_n + lane;
+            const int64_t rn = r + step;
+            const bool okn = i + 1 < nc && rw + step < c.n && rn < c.n;
 #pragma unroll
-            for (int p = 0; p < 8; ++p)
-                if (p < wt_c) {
-                    av[p] = __ldcs(pv + 32 * p);
-                    xv[p] = wj[cv[p]];
+            for (int p = 0; p < 8; ++p) {
+                avn[p] = 0.0;
+                xvn[p] = 0.0;
+                if (p < wt_n) {
+                    avn[p] = __ldcs(pv + 32 * p);
+                    xvn[p] = wj[cvn[p]];
                 }
+            }
+#pragma unroll
+            for (int a = 0; a < KW; ++a) wvn[a] = (kWinAhead && okn && a < nw) ? c.V[rn + c.woff[a]] : 0.0;
+        }
+        if constexpr (!kWinAhead) {
 #pragma unroll
             for (int a = 0; a < KW; ++a) wv[a] = (ok && a < nw) ? c.V[r + c.woff[a]] : 0.0;
         }
-        // (2) metadata of chunk i + 1 (loaded one iteration ago) and its column indices
-        const int wt_n = __shfl_sync(0xffffffffu, mw_raw, 0);
-        const long long so_n = __shfl_sync(0xffffffffu, mo_raw, 0);
-        int cvn[8];
+        // (2) metadata of chunk i + 2 (loaded one iteration ago) and its column indices
+        const int wt_nn = __shfl_sync(0xffffffffu, mw_raw, 0);
+        const long long so_nn = __shfl_sync(0xffffffffu, mo_raw, 0);
+        int cvnn[8];
         {
-            const int32_t *pc = c.sell_col + so_n + lane;
+            const int32_t *pc = c.sell_col + so_nn + lane;
 #pragma unroll
-            for (int p = 0; p < 8; ++p)
-                if (p < wt_n) cvn[p] = __ldcs(pc + 32 * p);
+            for (int p = 0; p < 8; ++p) {
+                cvnn[p] = 0;
+                if (p < wt_nn) cvnn[p] = __ldcs(pc + 32 * p);
+            }
         }
-        // (3) metadata of chunk i + 2
+        // (3) metadata of chunk i + 3
         mw_raw = 0;
         mo_raw = 0;
-        if (lane == 0 && i + 2 < nc && rw + 2 * step < c.n) {
-            mw_raw = __ldg(c.sell_w + ((rw + 2 * step) >> 5));
-            mo_raw = __ldg(c.sell_off + ((rw + 2 * step) >> 5));
+        if (lane == 0 && i + 3 < nc && rw + 3 * step < c.n) {
+            mw_raw = __ldg(c.sell_w + ((rw + 3 * step) >> 5));
+            mo_raw = __ldg(c.sell_off + ((rw + 3 * step) >> 5));
         }
-        // (4) y~ of chunk i
+        // (4) y~ of chunk i, from the loads issued one iteration ago
         if (ok) {
             double y = 0.0;
 #pragma unroll
@@ -362,9 +413,16 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
             ykey = max(ykey, abs_key(y));
         }
         wt_c = wt_n;
-        so_c = so_n;
+        wt_n = wt_nn;
+        so_n = so_nn;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) cv[p] = cvn[p];
+        for (int p = 0; p < 8; ++p) {
+            av[p] = avn[p];
+            xv[p] = xvn[p];
+            cvn[p] = cvnn[p];
+        }
+#pragma unroll
+        for (int a = 0; a < KW; ++a) wv[a] = wvn[a];
     }
     block_sum_auto<KW, kPipeRows>(acc, red);
     const double ymax = key_to_abs(block_max_key<kPipeRows>(ykey, (unsigned long long *)red));
@@ -385,7 +443,7 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
 }
 
 template <int KW, int ZCAP>
-__global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j) {
+__global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update(ArnCtx c, int j) {
     extern __shared__ int bins[];
     __shared__ double red[BlockSumTraits<KW + 1, kUpdThreads>::kSmem];
     __shared__ double sh[kMaxK];     // MGS coefficients h_ij
@@ -448,10 +506,13 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
     const int64_t r0 = (int64_t)blockIdx.x * c.rows_per_cta;
     const int64_t r1 = min(c.n, r0 + c.rows_per_cta);
     double *wn = c.V + vcol(c, j + 1);
-    // four rows per thread per iteration, all loads issued before the arithmetic
+    // four rows per thread per iteration, all loads (with the compact sketch
+    // pattern, where there is one) issued before the arithmetic
     constexpr int U = 4;
+    const bool p8 = ZCAP == 8 && c.sparse && c.pattern8 != nullptr;
     for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += U * kUpdThreads) {
         double yv[U], wv[U][KW];
+        uint2 pvu[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t r = rb + (int64_t)u * kUpdThreads;
@@ -460,6 +521,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
 #pragma unroll
             for (int a = 0; a < KW; ++a)
                 wv[u][a] = (ok && a < nw) ? c.V[r + c.woff[a]] : 0.0;
+            pvu[u] = (ok && p8) ? __ldg((const uint2 *)(c.pattern8 + r * 8)) : make_uint2(0u, 0u);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -486,20 +548,32 @@ __global__ void __launch_bounds__(kUpdThreads) k_arnoldi_update(ArnCtx c, int j)
                     c.SV[r + (size_t)j * s] = sigma * wjr;
                     c.SAV[r + (size_t)j * s] = sigma * y;
                 } else if (c.sparse) {
-                    uint16_t e[ZCAP];
-                    load_pattern<ZCAP>(c.pattern, c.sp.zeta, r, e);
                     const long long vw = fixed_point(wjr, shift_w);
                     const long long vy = ey == kNoExp ? 0 : fixed_point(y, shift_y);
                     const int w0 = (int)(vw & lmask), w1 = (int)(vw >> L);
                     const int y0 = (int)(vy & lmask), y1 = (int)(vy >> L);
+                    if (p8) {
+                        const uint2 pv = pvu[u];
 #pragma unroll
-                    for (int q = 0; q < ZCAP; ++q) {
-                        if (q < c.sp.zeta) {
-                            int row;
-                            bool neg;
-                            pattern_entry(c.sp, e[q], q, row, neg);
+                        for (int q = 0; q < 8; ++q) {
+                            const int e = (int)__byte_perm(q < 4 ? pv.x : pv.y, 0u, 0x4440u + (q & 3));
+                            const bool neg = e >= c.p8_block;
+                            const int row = c.sp.start[q] + (neg ? e - c.p8_block : e);
                             red_limbs(aw0, aw1, row, w0, w1, neg);
                             red_limbs(ay0, ay1, row, y0, y1, neg);
+                        }
+                    } else {
+                        uint16_t e[ZCAP];
+                        load_pattern<ZCAP>(c.pattern, c.sp.zeta, r, e);
+#pragma unroll
+                        for (int q = 0; q < ZCAP; ++q) {
+                            if (q < c.sp.zeta) {
+                                int row;
+                                bool neg;
+                                pattern_entry(c.sp, e[q], q, row, neg);
+                                red_limbs(aw0, aw1, row, w0, w1, neg);
+                                red_limbs(ay0, ay1, row, y0, y1, neg);
+                            }
                         }
                     }
                 }
@@ -669,6 +743,10 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
         c.sp = make_sparse_sign(S);
         c.pattern = S->pattern;
         c.binmax = S->binmax;
+        if (S->zeta == 8 && S->pattern8 != nullptr) {
+            c.pattern8 = S->pattern8;
+            c.p8_block = S->p8_block;
+        }
     }
     if (c.srht) {
         sd = make_srht(S);
