@@ -91,7 +91,7 @@ __device__ __forceinline__ void finalize_sketch(const long long *part, int G, in
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = i0 + warp; i < i1; i += blockDim.x / 32) {
         double v = 0.0;
-        if (E != kNoExp) v = ldexp(warp_sum_i64_exact(part + i, G, (size_t)s), E - frac) * scale;
+        if (E != kNoExp) v = scale_pow2(warp_sum_i64_exact(part + i, G, (size_t)s), E - frac) * scale;
         if (lane == 0) out_col[i] = v;
     }
 }
@@ -246,7 +246,8 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
 }
 
 // Pipelined variant of k_arnoldi_spmv for operators whose SELL slices are at
-// most 8 wide.  Rows are dealt out in chunks of kPipeRows (one row per
+// most W <= 8 wide (W product slots per row, so that no predicated-off DFMA
+// takes FP64 pipe time on narrow stencils).  Rows are dealt out in chunks of kPipeRows (one row per
 // thread), chunk c to CTA c mod gridDim.x, so all CTAs sweep the rows
 // together and the stencil gathers of neighbouring chunks meet in L2.  Within
 // a CTA the loads are software-pipelined four deep: while the FP64 products
@@ -263,7 +264,7 @@ inline int pipe_ctas(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, num_sms()));
 }
 
-template <int KW>
+template <int KW, int W>
 __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, int j) {
     __shared__ double red[BlockSumTraits<KW, kPipeRows>::kSmem];
     if (c.iscal[0] && c.iscal[3] < j) return;
@@ -321,14 +322,14 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
     const long long so_c = __shfl_sync(0xffffffffu, or0, 0);
     int wt_n = __shfl_sync(0xffffffffu, wr1, 0);
     long long so_n = __shfl_sync(0xffffffffu, or1, 0);
-    int cv[8], cvn[8];
+    int cv[W], cvn[W];
 #pragma unroll
-    for (int p = 0; p < 8; ++p) cv[p] = cvn[p] = 0;
+    for (int p = 0; p < W; ++p) cv[p] = cvn[p] = 0;
     {
         const int32_t *pc = c.sell_col + so_c + lane;
         const int32_t *pn = c.sell_col + so_n + lane;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
+        for (int p = 0; p < W; ++p) {
             if (p < wt_c) cv[p] = __ldcs(pc + 32 * p);
             if (p < wt_n) cvn[p] = __ldcs(pn + 32 * p);
         }
@@ -339,12 +340,12 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
         mw_raw = __ldg(c.sell_w + ((rw0 + 2 * step) >> 5));
         mo_raw = __ldg(c.sell_off + ((rw0 + 2 * step) >> 5));
     }
-    double av[8], xv[8], wv[KW];
+    double av[W], xv[W], wv[KW];
     {
         const double *pv = c.sell_val + so_c + lane;
         const bool ok = nc > 0 && rw0 < c.n && rw0 + lane < c.n;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
+        for (int p = 0; p < W; ++p) {
             av[p] = 0.0;
             xv[p] = 0.0;
             if (p < wt_c) {
@@ -360,13 +361,13 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
         const int64_t r = rw + lane;
         const bool ok = rw < c.n && r < c.n;   // padded rows of the last slice do no work
         // (1) values, gathers and window of chunk i + 1 (wt_n = 0 past the end)
-        double avn[8], xvn[8], wvn[KW];
+        double avn[W], xvn[W], wvn[KW];
         {
             const double *pv = c.sell_val + so_n + lane;
             const int64_t rn = r + step;
             const bool okn = i + 1 < nc && rw + step < c.n && rn < c.n;
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
+            for (int p = 0; p < W; ++p) {
                 avn[p] = 0.0;
                 xvn[p] = 0.0;
                 if (p < wt_n) {
@@ -384,11 +385,11 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
         // (2) metadata of chunk i + 2 (loaded one iteration ago) and its column indices
         const int wt_nn = __shfl_sync(0xffffffffu, mw_raw, 0);
         const long long so_nn = __shfl_sync(0xffffffffu, mo_raw, 0);
-        int cvnn[8];
+        int cvnn[W];
         {
             const int32_t *pc = c.sell_col + so_nn + lane;
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
+            for (int p = 0; p < W; ++p) {
                 cvnn[p] = 0;
                 if (p < wt_nn) cvnn[p] = __ldcs(pc + 32 * p);
             }
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
         if (ok) {
             double y = 0.0;
 #pragma unroll
-            for (int p = 0; p < 8; ++p)
+            for (int p = 0; p < W; ++p)
                 if (p < wt_c) y = fma(av[p], xv[p], y);
             c.Y[r] = y;
 #pragma unroll
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
         wt_n = wt_nn;
         so_n = so_nn;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
+        for (int p = 0; p < W; ++p) {
             av[p] = avn[p];
             xv[p] = xvn[p];
             cvn[p] = cvnn[p];
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update
         }
     }
     __syncthreads();
-    const int ey = ymax > 0.0 ? bound_exponent(ymax) : kNoExp;
+    const int ey = positive_finite(ymax) ? bound_exponent(ymax) : kNoExp;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c.vscale[j] = sigma;
         c.eys[j] = ey;
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update
     const int L = c.sparse ? limb_bits(*c.binmax) : 0;
     const int frac = sketch_fraction_bits_from_limb(L);
     const long long lmask = (1ll << L) - 1;
-    const int ew = wmax > 0.0 ? bound_exponent(wmax) : kNoExp;
+    const int ew = positive_finite(wmax) ? bound_exponent(wmax) : kNoExp;
     if (blockIdx.x == 0 && threadIdx.x == 0) c.ews[j] = ew;
     const int shift_w = frac - (ew == kNoExp ? 0 : ew);
     const int shift_y = frac - (ey == kNoExp ? 0 : ey);
@@ -671,13 +672,17 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
                   cudaStream_t st, const StepHook *hook) {
     auto spmv = c.max_width <= 8 ? k_arnoldi_spmv<KW, 8> : k_arnoldi_spmv<KW, 16>;
     const bool pipe = c.max_width <= 8;
+    // product slots of the pipelined SpMV: the widest slice rounded up to 5, 7
+    // or 8 (a slot past a slice's width is a predicated-off FP64 instruction)
+    auto spmv_pipe = c.max_width <= 5 ? k_arnoldi_spmv_pipe<KW, 5>
+                   : c.max_width <= 7 ? k_arnoldi_spmv_pipe<KW, 7> : k_arnoldi_spmv_pipe<KW, 8>;
     const int Gp = pipe_ctas(c.n);
     auto update = k_arnoldi_update<KW, ZCAP>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int j = 0; j < c.m; ++j) {
         ArnCtx cj = c;
         window_offsets(cj, j);
-        if (pipe) k_arnoldi_spmv_pipe<KW><<<Gp, kPipeRows, 0, st>>>(cj, j);
+        if (pipe) spmv_pipe<<<Gp, kPipeRows, 0, st>>>(cj, j);
         else spmv<<<Gs, kSpmvThreads, 0, st>>>(cj, j);
         call_hook(hook, j, st);   // S v_i, S A v_i final for i < j
         update<<<G, kUpdThreads, smem, st>>>(cj, j);

@@ -269,11 +269,11 @@ __device__ __forceinline__ void finalize_column(const LpCtx &c, int jw, bool sto
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = b0 + warp; i < b1; i += blockDim.x / 32) {
         double sw = 0.0;
-        if (ew != kNoExp) sw = ldexp(warp_sum_i64_exact(wp + i, c.G, (size_t)s), ew - P);
+        if (ew != kNoExp) sw = scale_pow2(warp_sum_i64_exact(wp + i, c.G, (size_t)s), ew - P);
         double sy = 0.0;
-        if (ylast && ey != kNoExp) sy = ldexp(warp_sum_i64_exact(c.skYp + i, c.G, (size_t)s), ey - P);
+        if (ylast && ey != kNoExp) sy = scale_pow2(warp_sum_i64_exact(c.skYp + i, c.G, (size_t)s), ey - P);
         double sdn = 0.0;
-        if (next_resid && edn != kNoExp) sdn = ldexp(warp_sum_i64_exact(c.skDp + i, c.G, (size_t)s), edn - L);
+        if (next_resid && edn != kNoExp) sdn = scale_pow2(warp_sum_i64_exact(c.skDp + i, c.G, (size_t)s), edn - L);
         if (lane == 0) {
             if (store) {
                 c.skw[(size_t)jw * s + i] = sw;
@@ -334,7 +334,7 @@ __device__ __forceinline__ void spmv_stop_sketch(const LpCtx &c, int j, int *bin
     const int P = sketch_fraction_bits_from_limb(L);
     const TB *wj = (const TB *)c.V + vcol(c, j);
     const double wmax = c.fin_w[2 * (size_t)j + 1];
-    const int ew = wmax > 0.0 ? bound_exponent(wmax) : kNoExp;
+    const int ew = positive_finite(wmax) ? bound_exponent(wmax) : kNoExp;
     if (blockIdx.x == 0 && threadIdx.x == 0) c.ex[j] = ew;
     for (int i = threadIdx.x; i < 2 * s; i += blockDim.x) bins[i] = 0;
     __syncthreads();
@@ -384,7 +384,7 @@ __device__ __forceinline__ void spmv_end(const LpCtx &c, int j, int nw, bool las
 // Scale of the directly scattered S y_{m-1}: |y_r| <= ||A||_inf max|w_{m-1}|.
 __device__ __forceinline__ int last_y_exponent(const LpCtx &c, int j) {
     const double ybound = c.norm_inf * c.fin_w[2 * (size_t)j + 1] * (1.0 + 1.0 / 1024.0);   // FP32 row-sum margin
-    const int ey = ybound > 0.0 ? bound_exponent(ybound) : kNoExp;
+    const int ey = positive_finite(ybound) ? bound_exponent(ybound) : kNoExp;
     if (blockIdx.x == 0 && threadIdx.x == 0) c.ex[2 * c.m] = ey;
     return ey;
 }
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
     const int L = sk ? limb_bits(*c.binmax_chunk) : 0;
     const int P = sketch_fraction_bits_from_limb(L);
     const double wmax = c.fin_w[2 * (size_t)j + 1];
-    const int ew = (sk && wmax > 0.0) ? bound_exponent(wmax) : kNoExp;
+    const int ew = (sk && positive_finite(wmax)) ? bound_exponent(wmax) : kNoExp;
     const int shift_w = P - (ew == kNoExp ? 0 : ew);
     const LimbScale lsw(shift_w, L);
     const int lc = split ? SplitGeom<SB>::kLc : c.lc, cm = (1 << lc) - 1;
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
         double wb = (double)sigf * ymax;
         for (int a = 0; a < nw; ++a) wb += fabs((double)scf[a]) * c.fin_w[2 * (size_t)(i0 + a) + 1];
         const double dbd = wb * (1.0 / 256.0) * (1.0 + 1.0 / 1024.0);
-        ed = dbd > 0.0 ? bound_exponent(dbd) : kNoExp;
+        ed = positive_finite(dbd) ? bound_exponent(dbd) : kNoExp;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && do_update) c.ex[c.m + j + 1] = ed;
     const int shift_d = L - (ed == kNoExp ? 0 : ed);

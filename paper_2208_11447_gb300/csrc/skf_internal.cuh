@@ -2,7 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <string>
 #include <vector>
@@ -128,11 +130,57 @@ __device__ __forceinline__ unsigned long long abs_key(double x) {
 }
 __device__ __forceinline__ double key_to_abs(unsigned long long k) { return __longlong_as_double((long long)k); }
 
-// Exponent E with |x| < 2^E for all |x| <= xmax (xmax > 0, finite).
+// Exponent E with |x| < 2^E for all |x| <= xmax (xmax > 0, finite): the
+// exponent e of xmax = f 2^e, 0.5 <= f < 1, read from the bit pattern with
+// integer instructions (the FP64 pipe retires one warp instruction per 16 SM
+// cycles on this part, so per-thread scalar FP64 work is not free).  Normal
+// xmax: biased exponent - 1022; subnormal xmax = mant 2^-1074: e = hb - 1073
+// with hb the highest set bit of mant.
 __host__ __device__ __forceinline__ int bound_exponent(double xmax) {
-    int e;
-    (void)frexp(xmax, &e);   // xmax = f 2^e, 0.5 <= f < 1  =>  xmax < 2^e
-    return e;
+#ifdef __CUDA_ARCH__
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(xmax);
+#else
+    unsigned long long bits;
+    memcpy(&bits, &xmax, sizeof bits);
+#endif
+    const int be = (int)((bits >> 52) & 0x7FFull);
+    if (be != 0) return be - 1022;
+    const unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+#ifdef __CUDA_ARCH__
+    const int hb = 63 - __clzll((long long)mant);
+#else
+    const int hb = 63 - __builtin_clzll(mant);
+#endif
+    return hb - 1073;
+}
+
+// x 2^k, equal to ldexp(x, k): one multiplication by the exact power of two
+// when 2^k is a normal double (a product with a power of two is rounded once,
+// as ldexp rounds), ldexp otherwise.
+__host__ __device__ __forceinline__ double scale_pow2(double x, int k) {
+    if (k >= -1022 && k <= 1023) {
+        const unsigned long long b = (unsigned long long)(k + 1023) << 52;
+#ifdef __CUDA_ARCH__
+        return x * __longlong_as_double((long long)b);
+#else
+        double p;
+        memcpy(&p, &b, sizeof p);
+        return x * p;
+#endif
+    }
+    return ldexp(x, k);
+}
+
+// 0 < xmax < inf (false for zero, negative, infinite and NaN xmax), with
+// integer instructions.
+__host__ __device__ __forceinline__ bool positive_finite(double xmax) {
+#ifdef __CUDA_ARCH__
+    const long long b = __double_as_longlong(xmax);
+#else
+    long long b;
+    memcpy(&b, &xmax, sizeof b);
+#endif
+    return b > 0 && b < 0x7FF0000000000000ll;
 }
 
 // Round x * 2^shift to the nearest integer, using only integer operations

@@ -169,7 +169,7 @@ __global__ void k_sparse_sign_reduce(const long long *__restrict__ part, const d
         return;
     }
     const double tot = sum_i64_exact(part + (size_t)c * G * s + i, G, (size_t)s);
-    SX[idx] = ldexp(tot, bound_exponent(mx) - frac) / sqrt((double)zeta);
+    SX[idx] = scale_pow2(tot, bound_exponent(mx) - frac) / sqrt((double)zeta);
 }
 
 __global__ void k_copy_cols(const double *__restrict__ X, int64_t ldx, int64_t n, int ncols, double *__restrict__ Y) {

@@ -92,7 +92,7 @@ __global__ void k_srht_reduce(SrhtDev d, const long long *__restrict__ part, con
         return;
     }
     const double tot = sum_i64_exact(part + (size_t)c * d.nblk * d.s + o, d.nblk, (size_t)d.s);
-    SX[idx] = ldexp(tot, E[c] - d.frac) * scale;
+    SX[idx] = scale_pow2(tot, E[c] - d.frac) * scale;
 }
 
 // Per-CTA partial max |X[:, c]| (rows of CTA g: g, g + G, ...).
