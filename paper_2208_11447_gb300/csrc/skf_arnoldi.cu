@@ -446,9 +446,9 @@ __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, in
 template <int KW, int ZCAP>
 __global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update(ArnCtx c, int j) {
     extern __shared__ int bins[];
-    __shared__ double red[BlockSumTraits<KW + 1, kUpdThreads>::kSmem];
+    __shared__ double red[BlockSumTraits<KW, kUpdThreads>::kSmem];
     __shared__ double sh[kMaxK];     // MGS coefficients h_ij
-    __shared__ double scoef[kMaxK];  // h_ij * sigma_i
+    __shared__ double scoef[kMaxK];  // h_ij * sigma_i, newest window vector first: scoef[b] for w_{j-b}
     if (c.iscal[0] && c.iscal[3] <= j) return;   // stopped at this step (set by its spmv launch) or earlier
     const int G = gridDim.x;
     const double *fd = c.fin_d + (size_t)j * kP1;
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update
                 h -= sh[b2] * sa * sb * gab;
             }
             sh[a] = h;
-            scoef[a] = h * sa;
+            scoef[nw - 1 - a] = h * sa;
         }
     }
     __syncthreads();
@@ -497,22 +497,27 @@ __global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update
     const int shift_w = frac - (ew == kNoExp ? 0 : ew);
     const int shift_y = frac - (ey == kNoExp ? 0 : ey);
     const bool do_update = j < c.m - 1;
-    // part[0] = ||w_{j+1}||^2, part[1 + a] = <w_{j+1}, w_{i0+a}>; slot a is the
-    // Gram entry at distance d = nw - a of the next window when 1 <= d <= ng
+    // part[0] = ||w_{j+1}||^2, part[d] = <w_{j+1}, w_{j+1-d}> for the Gram
+    // distances d = 1 .. ng of the next window (ng <= KW - 1): only the live
+    // products are issued (a predicated-off DFMA still takes FP64 pipe time)
     const int ng = min(j + 1, c.k - 1);
-    double part[KW + 1];
+    double part[KW];
 #pragma unroll
-    for (int i = 0; i <= KW; ++i) part[i] = 0.0;
+    for (int i = 0; i < KW; ++i) part[i] = 0.0;
     unsigned long long nkey = 0;
     const int64_t r0 = (int64_t)blockIdx.x * c.rows_per_cta;
     const int64_t r1 = min(c.n, r0 + c.rows_per_cta);
     double *wn = c.V + vcol(c, j + 1);
+    // window offsets newest first: woffr[b] locates w_{j-b}
+    int64_t woffr[KW];
+#pragma unroll
+    for (int b = 0; b < KW; ++b) woffr[b] = b < nw ? c.woff[nw - 1 - b] : 0;
     // four rows per thread per iteration, all loads (with the compact sketch
     // pattern, where there is one) issued before the arithmetic
     constexpr int U = 4;
     const bool p8 = ZCAP == 8 && c.sparse && c.pattern8 != nullptr;
     for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += U * kUpdThreads) {
-        double yv[U], wv[U][KW];
+        double yv[U], wv[U][KW];   // wv[u][b] = w_{j-b}: newest first
         uint2 pvu[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -521,7 +526,7 @@ __global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update
             yv[u] = ok ? c.Y[r] : 0.0;
 #pragma unroll
             for (int a = 0; a < KW; ++a)
-                wv[u][a] = (ok && a < nw) ? c.V[r + c.woff[a]] : 0.0;
+                wv[u][a] = (ok && a < nw) ? c.V[r + woffr[a]] : 0.0;
             pvu[u] = (ok && p8) ? __ldg((const uint2 *)(c.pattern8 + r * 8)) : make_uint2(0u, 0u);
         }
 #pragma unroll
@@ -529,21 +534,19 @@ __global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update
             const int64_t r = rb + (int64_t)u * kUpdThreads;
             if (r < r1) {
                 const double y = yv[u];
-                double wjr = wv[u][0];
-#pragma unroll
-                for (int a = 1; a < KW; ++a)
-                    if (a == nw - 1) wjr = wv[u][a];
+                const double wjr = wv[u][0];
                 if (do_update) {
                     double w = sigma * y;
 #pragma unroll
                     for (int a = 0; a < KW; ++a)
-                        if (a < nw) w = fma(-scoef[a], wv[u][a], w);
+                        if (KW - 1 - a < nw) w = fma(-scoef[KW - 1 - a], wv[u][KW - 1 - a], w);   // oldest first
                     wn[r] = w;
                     part[0] = fma(w, w, part[0]);
                     nkey = max(nkey, abs_key(w));
 #pragma unroll
-                    for (int a = 0; a < KW; ++a)
-                        if (a < nw && nw - a <= ng) part[1 + a] = fma(w, wv[u][a], part[1 + a]);
+                    for (int d = 1; d < KW; ++d) {
+                        if (d <= ng) part[d] = fma(w, wv[u][d - 1], part[d]);   // w_{j+1-d}
+                    }
                 }
                 if (c.identity) {
                     c.SV[r + (size_t)j * s] = sigma * wjr;
@@ -581,13 +584,16 @@ __global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update
             }
         }
     }
-    block_sum_auto<KW + 1, kUpdThreads>(part, red);
+    block_sum_auto<KW, kUpdThreads>(part, red);
     const double nmax = key_to_abs(block_max_key<kUpdThreads>(nkey, (unsigned long long *)red));
     if (threadIdx.x == 0) {
+        // partial layout: slot 2 + a holds the Gram entry at distance d = nw - a
         double *o = c.p2 + (size_t)blockIdx.x * kP2;
         o[0] = part[0];
         o[1] = nmax;
-        for (int a = 0; a < KW; ++a) o[2 + a] = part[1 + a];
+#pragma unroll
+        for (int d = 1; d < KW; ++d)
+            if (d <= ng) o[2 + nw - d] = part[d];
     }
     if (c.sparse) {
         __syncthreads();
