@@ -89,6 +89,12 @@ __device__ __forceinline__ double hh_sum(double v, double *red) {
 
 __global__ void __launch_bounds__(kHhThreads) k_householder(TailCtx c, int jj) {
     __shared__ double red[kHhThreads / 32];
+    // Launched as a programmatic dependent of the previous reflector: wait for
+    // it to finish (every CTA, before any exit, so that no launch can finish
+    // ahead of its predecessor), then let the next reflector's CTAs be placed
+    // while this one runs.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int me = c.iscal[1];
     const int ncols = 2 * me;
     const int nref = (c.method == SKF_METHOD_SGMRES) ? 2 * me : me;
@@ -222,25 +228,56 @@ constexpr int kMixedMaxM = 320;   // packed FP32 factor of order m must fit in s
 __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }   // packed lower, row-major
 
 // Solve L L^T z = z with the packed FP32 factor; one warp, z in FP64 shared
-// memory (the solve itself is in FP32).
-__device__ void packed_solve_warp(const float *L, int me, double *z) {
+// memory, the solve itself in FP32 (the factor only preconditions the FP64
+// refinement).  Column-oriented: lane l keeps rows l, l + 32, ... of z in
+// registers; at step p the lane owning row p scales it by rinv[p] = 1/L_pp
+// and broadcasts it, and every lane updates its own unsolved rows.  One
+// shuffle per row instead of a reduction tree, and no FP64 conversions
+// inside the recurrence.
+constexpr int kSolveRegs = (kMixedMaxM + 31) / 32;
+__device__ void packed_solve_warp(const float *L, const float *rinv, int me, double *z) {
     const int lane = threadIdx.x & 31;
-    for (int p = 0; p < me; ++p) {          // L u = z
-        float part = 0.f;
-        for (int q = lane; q < p; q += 32) part = fmaf(L[pk(p, q)], (float)z[q], part);
+    float zr[kSolveRegs];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) z[p] = (double)(((float)z[p] - part) / L[pk(p, p)]);
-        __syncwarp();
+    for (int k = 0; k < kSolveRegs; ++k) {
+        const int i = lane + 32 * k;
+        zr[k] = i < me ? (float)z[i] : 0.f;
+    }
+    for (int p = 0; p < me; ++p) {          // L u = z
+        const int kp = p >> 5, lp = p & 31;
+        float zp = zr[0];
+#pragma unroll
+        for (int k = 1; k < kSolveRegs; ++k)
+            if (k == kp) zp = zr[k];
+        const float up = __shfl_sync(0xffffffffu, zp * rinv[p], lp);
+#pragma unroll
+        for (int k = 0; k < kSolveRegs; ++k) {
+            const int i = lane + 32 * k;
+            if (i == p) zr[k] = up;
+            else if (i > p && i < me) zr[k] = fmaf(-L[pk(i, p)], up, zr[k]);
+        }
     }
     for (int p = me - 1; p >= 0; --p) {     // L^T x = u
-        float part = 0.f;
-        for (int i = p + 1 + lane; i < me; i += 32) part = fmaf(L[pk(i, p)], (float)z[i], part);
+        const int kp = p >> 5, lp = p & 31;
+        float zp = zr[0];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) z[p] = (double)(((float)z[p] - part) / L[pk(p, p)]);
-        __syncwarp();
+        for (int k = 1; k < kSolveRegs; ++k)
+            if (k == kp) zp = zr[k];
+        const float xp = __shfl_sync(0xffffffffu, zp * rinv[p], lp);
+        const float *Lp = L + pk(p, 0);
+#pragma unroll
+        for (int k = 0; k < kSolveRegs; ++k) {
+            const int i = lane + 32 * k;
+            if (i == p) zr[k] = xp;
+            else if (i < p) zr[k] = fmaf(-Lp[i], xp, zr[k]);
+        }
     }
+#pragma unroll
+    for (int k = 0; k < kSolveRegs; ++k) {
+        const int i = lane + 32 * k;
+        if (i < me) z[i] = (double)zr[k];
+    }
+    __syncwarp();
 }
 
 // One CTA per quadrature node.  The normal matrix N(t) = t^2 I + t (M + M^T)
@@ -280,25 +317,39 @@ __global__ void __launch_bounds__(kThreads) k_nodes_mixed(TailCtx c, int n0, int
             break;
         }
         const float lpp = sqrtf(d);
-        for (int i = p + threadIdx.x; i < me; i += blockDim.x) colp[i] = (i == p) ? lpp : L[pk(i, p)] / lpp;
+        const float rl = 1.f / lpp;
+        for (int i = p + threadIdx.x; i < me; i += blockDim.x) colp[i] = (i == p) ? lpp : L[pk(i, p)] * rl;
         __syncthreads();
         for (int i = p + threadIdx.x; i < me; i += blockDim.x) L[pk(i, p)] = colp[i];
-        // trailing update: one warp per row, lanes along the row
+        // trailing update: one warp per row, lanes along the row; rows i and
+        // i + 8 of a warp in the same pass, so their loads overlap
         {
+            constexpr int kW = kThreads / 32;
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            for (int i = p + 1 + warp; i < me; i += kThreads / 32) {
-                const float li = colp[i];
+            for (int i = p + 1 + warp; i < me; i += 2 * kW) {
+                const int i2 = i + kW;
+                const bool two = i2 < me;
+                const float li = colp[i], li2 = two ? colp[i2] : 0.f;
                 float *Li = L + pk(i, 0);
-                for (int q = p + 1 + lane; q <= i; q += 32) Li[q] = fmaf(-li, colp[q], Li[q]);
+                float *Li2 = L + pk(two ? i2 : i, 0);
+                const int qe = two ? i2 : i;
+                for (int q = p + 1 + lane; q <= qe; q += 32) {
+                    const float cq = colp[q];
+                    if (q <= i) Li[q] = fmaf(-li, cq, Li[q]);
+                    if (two) Li2[q] = fmaf(-li2, cq, Li2[q]);
+                }
             }
         }
     }
     __syncthreads();
     if (!bad) {
-        // y0 = N^{-1} (t c + M^T c)
-        for (int a = threadIdx.x; a < me; a += blockDim.x) y[a] = t * c.cvec[a] + c.Mtc[a];
+        // y0 = N^{-1} (t c + M^T c); colp <- 1/L_pp for the solves
+        for (int a = threadIdx.x; a < me; a += blockDim.x) {
+            y[a] = t * c.cvec[a] + c.Mtc[a];
+            colp[a] = 1.f / L[pk(a, a)];
+        }
         __syncthreads();
-        if (threadIdx.x < 32) packed_solve_warp(L, me, y);
+        if (threadIdx.x < 32) packed_solve_warp(L, colp, me, y);
         __syncthreads();
         double prev = INFINITY;
         bool conv = false;
@@ -324,7 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_nodes_mixed(TailCtx c, int n0, int
                 g[j] = v;
             }
             __syncthreads();
-            if (threadIdx.x < 32) packed_solve_warp(L, me, g);
+            if (threadIdx.x < 32) packed_solve_warp(L, colp, me, g);
             __syncthreads();
             double loc[2] = {0.0, 0.0};
             for (int a = threadIdx.x; a < me; a += blockDim.x) {
@@ -1034,9 +1085,22 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     k_tail_copy<<<G, kThreads, 0, st>>>(SV, SAV, c);
     ++nlaunch;
     const int nref = (method == SKF_METHOD_SGMRES) ? 2 * m : m;
+    // the 2m (sGMRES) or m (sFOM) reflector launches, each a programmatic
+    // dependent of the one before, so that launch latency overlaps the
+    // previous reflector
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
     for (int jj = 0; jj < nref; ++jj) {
         const int ntrail = std::max(1, 2 * m - jj - 1);
-        k_householder<<<ntrail, kHhThreads, 0, st>>>(c, jj);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)ntrail);
+        cfg.blockDim = dim3(kHhThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cfg.attrs = pdl;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_householder, c, jj);
     }
     nlaunch += nref;
     {
