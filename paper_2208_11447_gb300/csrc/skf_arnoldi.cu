@@ -267,6 +267,11 @@ inline int pipe_ctas(int64_t n) {
 template <int KW, int W>
 __global__ void __launch_bounds__(kPipeRows, 1) k_arnoldi_spmv_pipe(ArnCtx c, int j) {
     __shared__ double red[BlockSumTraits<KW, kPipeRows>::kSmem];
+    // programmatic dependent of the previous launch: every CTA waits for it
+    // before reading anything (and before any exit), then releases the next
+    // launch so that its placement overlaps this one
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (c.iscal[0] && c.iscal[3] < j) return;
     const int G = gridDim.x;
     const int s = c.sp.s;
@@ -449,6 +454,9 @@ __global__ void __launch_bounds__(kUpdThreads, KW <= 2 ? 2 : 1) k_arnoldi_update
     __shared__ double red[BlockSumTraits<KW, kUpdThreads>::kSmem];
     __shared__ double sh[kMaxK];     // MGS coefficients h_ij
     __shared__ double scoef[kMaxK];  // h_ij * sigma_i, newest window vector first: scoef[b] for w_{j-b}
+    // programmatic dependent of the SpMV launch (see k_arnoldi_spmv_pipe)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (c.iscal[0] && c.iscal[3] <= j) return;   // stopped at this step (set by its spmv launch) or earlier
     const int G = gridDim.x;
     const double *fd = c.fin_d + (size_t)j * kP1;
@@ -685,13 +693,30 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
     const int Gp = pipe_ctas(c.n);
     auto update = k_arnoldi_update<KW, ZCAP>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the pipelined SpMV and the update are launched as programmatic
+    // dependents of the launch before them (each waits for it in full)
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg_s = {}, cfg_u = {};
+    cfg_s.gridDim = dim3((unsigned)Gp);
+    cfg_s.blockDim = dim3(kPipeRows);
+    cfg_s.stream = st;
+    cfg_s.attrs = pdl;
+    cfg_s.numAttrs = 1;
+    cfg_u.gridDim = dim3((unsigned)G);
+    cfg_u.blockDim = dim3(kUpdThreads);
+    cfg_u.dynamicSmemBytes = smem;
+    cfg_u.stream = st;
+    cfg_u.attrs = pdl;
+    cfg_u.numAttrs = 1;
     for (int j = 0; j < c.m; ++j) {
         ArnCtx cj = c;
         window_offsets(cj, j);
-        if (pipe) spmv_pipe<<<Gp, kPipeRows, 0, st>>>(cj, j);
+        if (pipe) cudaLaunchKernelEx(&cfg_s, spmv_pipe, cj, j);
         else spmv<<<Gs, kSpmvThreads, 0, st>>>(cj, j);
         call_hook(hook, j, st);   // S v_i, S A v_i final for i < j
-        update<<<G, kUpdThreads, smem, st>>>(cj, j);
+        cudaLaunchKernelEx(&cfg_u, update, cj, j);
         if (j + 1 < c.m) call_col_hook(hook, j + 1, st);
         if (dd) {   // SV[:, j] = sigma_j S w_j, SAV[:, j] = sigma_j S y_j
             SrdctCols cols{};
