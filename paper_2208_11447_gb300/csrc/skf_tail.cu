@@ -235,41 +235,44 @@ __device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; } 
 // shuffle per row instead of a reduction tree, and no FP64 conversions
 // inside the recurrence.
 constexpr int kSolveRegs = (kMixedMaxM + 31) / 32;
-__device__ void packed_solve_warp(const float *L, const float *rinv, int me, double *z) {
+__device__ __forceinline__ void packed_solve_warp(const float *L, const float *rinv, int me, double *z) {
     const int lane = threadIdx.x & 31;
     float zr[kSolveRegs];
+    int rowb[kSolveRegs];   // packed offset of row min(i, me - 1)
 #pragma unroll
     for (int k = 0; k < kSolveRegs; ++k) {
         const int i = lane + 32 * k;
         zr[k] = i < me ? (float)z[i] : 0.f;
+        rowb[k] = pk(min(i, me - 1), 0);
     }
+    // Branch-free per register: every lane loads an in-range entry (rows past
+    // me - 1 read row me - 1; entries right of the diagonal belong to later
+    // rows of the packed array) and keeps or replaces its value by selects.
     for (int p = 0; p < me; ++p) {          // L u = z
         const int kp = p >> 5, lp = p & 31;
         float zp = zr[0];
 #pragma unroll
-        for (int k = 1; k < kSolveRegs; ++k)
-            if (k == kp) zp = zr[k];
+        for (int k = 1; k < kSolveRegs; ++k) zp = (k == kp) ? zr[k] : zp;
         const float up = __shfl_sync(0xffffffffu, zp * rinv[p], lp);
 #pragma unroll
         for (int k = 0; k < kSolveRegs; ++k) {
             const int i = lane + 32 * k;
-            if (i == p) zr[k] = up;
-            else if (i > p && i < me) zr[k] = fmaf(-L[pk(i, p)], up, zr[k]);
+            const float nz = fmaf(-L[rowb[k] + p], up, zr[k]);
+            zr[k] = (i == p) ? up : ((i > p) ? nz : zr[k]);
         }
     }
     for (int p = me - 1; p >= 0; --p) {     // L^T x = u
         const int kp = p >> 5, lp = p & 31;
         float zp = zr[0];
 #pragma unroll
-        for (int k = 1; k < kSolveRegs; ++k)
-            if (k == kp) zp = zr[k];
+        for (int k = 1; k < kSolveRegs; ++k) zp = (k == kp) ? zr[k] : zp;
         const float xp = __shfl_sync(0xffffffffu, zp * rinv[p], lp);
         const float *Lp = L + pk(p, 0);
 #pragma unroll
         for (int k = 0; k < kSolveRegs; ++k) {
             const int i = lane + 32 * k;
-            if (i == p) zr[k] = xp;
-            else if (i < p) zr[k] = fmaf(-Lp[i], xp, zr[k]);
+            const float nz = fmaf(-Lp[min(i, p)], xp, zr[k]);
+            zr[k] = (i == p) ? xp : ((i < p) ? nz : zr[k]);
         }
     }
 #pragma unroll
