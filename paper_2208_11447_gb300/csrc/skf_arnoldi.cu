@@ -6,13 +6,15 @@
 // products before the update, and the new vector before the next SpMV):
 //
 //   spmv   (step j): y~ = A w_j on the CTA's rows -> Y; partial dots
-//                    <w_i, y~> (i in the window), Gram <w_j, w_i>, max|y~|;
-//                    fixed-point sketch of w_j (-> S v_j).
+//                    <w_i, y~> (i in the window) and max|y~|; in its
+//                    prologue, S v_{j-1} and S A v_{j-1} from the update's
+//                    integer partials.
 //   update (step j): MGS coefficients from the reduced dots and the window
 //                    Gram matrix (identical to MGS in exact arithmetic),
 //                    w_{j+1} = sigma_j y~ - sum_i h_ij sigma_i w_i, partial
-//                    ||w_{j+1}||^2 and max|w_{j+1}|; fixed-point sketch of y~
-//                    (-> S A v_j).
+//                    ||w_{j+1}||^2, max|w_{j+1}| and the Gram entries
+//                    <w_{j+1}, w_i> of the next window; fixed-point sketches
+//                    of w_j (-> S v_j) and of y~ (-> S A v_j).
 //
 // Cross-CTA reductions: every CTA writes its partials; the CTA that arrives
 // last (atomic ticket, no waiting) reduces them in a fixed order and publishes
