@@ -541,6 +541,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--arnoldi-reps", type=int, default=5)
+    ap.add_argument("--arnoldi-form", default="auto", choices=["auto", "persistent", "two_kernel"],
+                    help="form of the FP64 Arnoldi process (skf_set_arnoldi_mode)")
     ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi", "batch"],
                     help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu; "
                          "batch: the batched workload (8 operators, 64 right-hand sides) as one CUDA graph")
@@ -576,6 +578,8 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    skf.set_arnoldi_mode({"auto": skf.ARNOLDI_AUTO, "persistent": skf.ARNOLDI_PERSISTENT,
+                          "two_kernel": skf.ARNOLDI_TWO_KERNEL}[args.arnoldi_form])
 
     def barrier():
         replica_barrier(world)

@@ -50,7 +50,9 @@ typedef enum {
     SKF_ERR_QUAD_NOT_CONVERGED = 6,  /* adaptive quadrature passed ell_max */
     SKF_ERR_SKETCH_TOO_SMALL = 7,    /* s < 2m is required by the GMRES reduction */
     SKF_ERR_NOT_SUPPORTED = 8,       /* valid request this build does not implement */
-    SKF_ERR_ZERO_RHS = 9             /* ||b|| = 0: x is set to 0 */
+    SKF_ERR_ZERO_RHS = 9,            /* ||b|| = 0: x is set to 0 */
+    SKF_ERR_TIMEOUT = 10             /* a bounded device-side wait (grid barrier of the
+                                        persistent Arnoldi kernel) ran out; results invalid */
 } skf_status;
 
 typedef enum { SKF_F64 = 0, SKF_F32 = 1, SKF_BF16 = 2 } skf_dtype;
@@ -173,6 +175,34 @@ int32_t skf_version(void);     /* major*10000 + minor*100 + patch */
  * loaded, counted on the host at launch time (a diagnostic for profilers and
  * benchmarks; no device work). */
 int64_t skf_kernel_launch_count(void);
+
+/* skf_set_arnoldi_mode: which form of the FP64 Arnoldi process the library
+ * launches (process-wide; a tuning and testing switch, results agree to
+ * rounding between the forms):
+ *   0  automatic (default): the persistent form where it applies, else the
+ *      two-kernel form;
+ *   1  the two-kernel form only: per step one SpMV launch and one update
+ *      launch (programmatic dependents), any k, sketch kind and size;
+ *   2  the persistent form only, SKF_ERR_NOT_SUPPORTED where it does not
+ *      apply.
+ * The persistent form runs all m steps of Algorithm 2 in one cooperative
+ * launch, one CTA per SM, each CTA keeping its rows of the window vectors
+ * and of A v_j in shared memory.  It applies to an F64 basis with a
+ * sparse-sign sketch, k <= 4, one-pass storage without the stopping
+ * criterion, and (k + 1) * ceil(N / SMs) * 8 bytes (plus the sketch bins)
+ * within the per-CTA shared memory (N up to about 1e6 at k = 2 on a
+ * 152-SM GB300).  Its grid barriers wait at most about one second each and
+ * then report SKF_ERR_TIMEOUT in skf_info::status.
+ * Returns INVALID_ARG for another mode. */
+skf_status skf_set_arnoldi_mode(int32_t mode);
+
+/* skf_barrier_selftest: failure-detection check of the bounded grid wait
+ * used by the persistent Arnoldi kernel.  Launches `ctas` co-resident CTAs
+ * (1 <= ctas <= SMs) that wait at a barrier no CTA can complete, giving up
+ * after budget_cycles SM clock cycles (1e3 .. 1e10); the kernel then writes
+ * SKF_ERR_TIMEOUT to *status_device (device int) and returns, leaving the
+ * context usable.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+skf_status skf_barrier_selftest(int32_t ctas, int64_t budget_cycles, int32_t *status_device, skf_stream_t stream);
 
 /* ------------------------------------------------------------ operator */
 /* skf_create_csr: wrap or copy a CSR matrix A (Sec. 2.2 assumes a sparse A

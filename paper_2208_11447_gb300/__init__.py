@@ -25,7 +25,10 @@ INVSQRT, LOG1P_OVER_Z, INV, INVPOW = 0, 1, 2, 3
 SFOM, SGMRES = 0, 1
 STATUS = {0: "SKF_OK", 1: "SKF_ERR_INVALID_ARG", 2: "SKF_ERR_CUDA", 3: "SKF_ERR_OOM",
           4: "SKF_ERR_ILL_CONDITIONED", 5: "SKF_ERR_BRANCH_CUT", 6: "SKF_ERR_QUAD_NOT_CONVERGED",
-          7: "SKF_ERR_SKETCH_TOO_SMALL", 8: "SKF_ERR_NOT_SUPPORTED", 9: "SKF_ERR_ZERO_RHS"}
+          7: "SKF_ERR_SKETCH_TOO_SMALL", 8: "SKF_ERR_NOT_SUPPORTED", 9: "SKF_ERR_ZERO_RHS",
+          10: "SKF_ERR_TIMEOUT"}
+# Arnoldi forms of skf_set_arnoldi_mode
+ARNOLDI_AUTO, ARNOLDI_TWO_KERNEL, ARNOLDI_PERSISTENT = 0, 1, 2
 EXP_NEG = 4
 FUNC_KIND = {"invsqrt": INVSQRT, "log1p_over_z": LOG1P_OVER_Z, "inv": INV, "invpow": INVPOW, "exp_neg": EXP_NEG}
 _DTYPE = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
@@ -101,10 +104,13 @@ def lib():
         L.skf_quadrature_rule.argtypes = [ctypes.POINTER(Func), i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
         L.skf_quadrature_rule_c.argtypes = [ctypes.POINTER(Func), i32] + [ctypes.POINTER(dbl)] * 4
         L.skf_solve_batched.argtypes = [i32, ctypes.POINTER(Problem), i32, vp]
+        L.skf_set_arnoldi_mode.argtypes = [i32]
+        L.skf_barrier_selftest.argtypes = [i32, i64, vp, vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
                      "skf_solve", "skf_solve_batched", "skf_sfom",
-                     "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c"]:
+                     "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c", "skf_set_arnoldi_mode",
+                     "skf_barrier_selftest"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -329,6 +335,35 @@ class BatchGraph:
             else:
                 del g
         return best, times
+
+
+def set_arnoldi_mode(mode: int) -> None:
+    """skf_set_arnoldi_mode: ARNOLDI_AUTO, ARNOLDI_TWO_KERNEL or ARNOLDI_PERSISTENT."""
+    _check(lib().skf_set_arnoldi_mode(mode))
+
+
+class arnoldi_mode:
+    """Context manager: run the enclosed calls with the given Arnoldi form,
+    then return to the automatic choice."""
+
+    def __init__(self, mode: int):
+        self.mode = mode
+
+    def __enter__(self):
+        set_arnoldi_mode(self.mode)
+        return self
+
+    def __exit__(self, *exc):
+        set_arnoldi_mode(ARNOLDI_AUTO)
+        return False
+
+
+def barrier_selftest(ctas: int, budget_cycles: int, stream=None) -> int:
+    """skf_barrier_selftest: returns the status the kernel wrote (after a
+    stream synchronisation)."""
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    _check(lib().skf_barrier_selftest(ctas, budget_cycles, _ptr(st), _stream(stream)))
+    return int(st.item())
 
 
 def kernel_launch_count() -> int:

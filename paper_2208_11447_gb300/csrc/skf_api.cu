@@ -585,6 +585,7 @@ const char *skf_status_string(skf_status s) {
         case SKF_ERR_SKETCH_TOO_SMALL: return "sketch too small";
         case SKF_ERR_NOT_SUPPORTED: return "not supported";
         case SKF_ERR_ZERO_RHS: return "zero right-hand side";
+        case SKF_ERR_TIMEOUT: return "device-side wait timed out";
     }
     return "unknown status";
 }
@@ -592,6 +593,20 @@ const char *skf_status_string(skf_status s) {
 int32_t skf_version(void) { return 100; }
 
 int64_t skf_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
+
+skf_status skf_set_arnoldi_mode(int32_t mode) {
+    if (mode < 0 || mode > 2) return fail(SKF_ERR_INVALID_ARG, "Arnoldi mode must be 0, 1 or 2");
+    set_step_mode(mode);
+    return SKF_OK;
+}
+
+skf_status skf_barrier_selftest(int32_t ctas, int64_t budget_cycles, int32_t *status_device, skf_stream_t stream) {
+    if (!status_device) return fail(SKF_ERR_INVALID_ARG, "status_device is NULL");
+    if (ctas < 1 || ctas > num_sms()) return fail(SKF_ERR_INVALID_ARG, "need 1 <= ctas <= number of SMs");
+    if (budget_cycles < 1000 || budget_cycles > 10000000000ll)
+        return fail(SKF_ERR_INVALID_ARG, "budget_cycles must be in [1e3, 1e10]");
+    return barrier_selftest(ctas, budget_cycles, (int *)status_device, (cudaStream_t)stream);
+}
 
 skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind, const void *values,
                           skf_dtype vdtype, skf_copy_mode mode, skf_stream_t stream, skf_csr **A_out) {

@@ -686,7 +686,9 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_info(ArnCtx c, skf_info *i
 template <int KW, int ZCAP>
 void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd, const SrdctDev *dd,
                   cudaStream_t st, const StepHook *hook) {
-    auto spmv = c.max_width <= 8 ? k_arnoldi_spmv<KW, 8> : k_arnoldi_spmv<KW, 16>;
+    // slices up to 8 wide take the pipelined SpMV; wider ones the generic
+    // kernel (16 unrolled product slots, an entry loop past 16)
+    auto spmv = k_arnoldi_spmv<KW, 16>;
     const bool pipe = c.max_width <= 8;
     // product slots of the pipelined SpMV: the widest slice rounded up to 5, 7
     // or 8 (a slot past a slice's width is a predicated-off FP64 instruction)
@@ -763,6 +765,13 @@ void launch_steps_k(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *
 skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V, int64_t ldv,
                        double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
                        cudaStream_t st, const StepHook *hook, int vring) {
+    // the persistent single-launch form where it applies (no per-step host
+    // hooks, one-pass storage, sparse-sign S, k <= 4, rows fit in shared memory)
+    if (step_mode() != 1 && hook == nullptr && vring == 0) {
+        const skf_status ps = arnoldi_run_persistent(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, st);
+        if (ps != SKF_ERR_NOT_SUPPORTED) return ps;
+        if (step_mode() == 2) return fail(SKF_ERR_NOT_SUPPORTED, "persistent Arnoldi form does not apply here");
+    }
     ArnCtx c{};
     c.n = A->n;
     c.sell_off = A->sell_off;

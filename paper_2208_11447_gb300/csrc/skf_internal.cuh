@@ -80,6 +80,8 @@ struct skf_sketch {
     uint16_t *pattern = nullptr;
     int *binmax = nullptr;            // device: most nonzeros one CTA row range puts in one row of S
     int *binmax_chunk = nullptr;      // device: the same for the chunk-interleaved partition
+    int *binmax_persist = nullptr;    // device: the same for the persistent partition (persist_partition)
+    int binmax_persist_host = 0;      // host copy of *binmax_persist
     // Compact pattern when every stripe has at most 128 rows and zeta <= 8:
     // byte [c * 8 + q] = (row of nonzero q within stripe q) + p8_block * sign,
     // with p8_block = 64 if every stripe has at most 64 rows, else 128; zero
@@ -361,6 +363,10 @@ void row_partition(int64_t n, int *G, int64_t *rows);
 constexpr int kChunkRows = 1024;
 void chunk_partition(int64_t n, int *G);
 
+// Row partition of the persistent FP64 Arnoldi kernel: G <= SMs CTAs of
+// `rows` consecutive rows each (whole SELL slices), every CTA non-empty.
+void persist_partition(int64_t n, int *G, int64_t *rows);
+
 // Fixed-point sketch accumulation.  A value x is rounded to the integer
 // v = x 2^(P - E) (E: exponent bound of the vector, |v| < 2^P) and split into
 // two signed 32-bit limbs v = l1 2^L + l0, 0 <= l0 < 2^L, |l1| < 2^(P-L);
@@ -427,6 +433,21 @@ inline void call_hook(const StepHook *h, int done, cudaStream_t st) {
 inline void call_col_hook(const StepHook *h, int j, cudaStream_t st) {
     if (h && h->col_fn) h->col_fn(h->col_ctx, j, st);
 }
+
+// Persistent single-launch FP64 Arnoldi process (skf_arnoldi_persist.cu):
+// SKF_ERR_NOT_SUPPORTED, with nothing left enqueued, when the case does not
+// fit it (sketch kind, k > 4, shared memory, cooperative launch).
+skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V,
+                                  int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
+                                  skf_info *info, cudaStream_t st);
+// Which FP64 step form arnoldi_run uses: 0 automatic (persistent where it
+// fits), 1 the two-kernel form only, 2 the persistent form or
+// SKF_ERR_NOT_SUPPORTED.
+void set_step_mode(int mode);
+int step_mode();
+// Bounded-wait self-test: `ctas` co-resident CTAs wait at a barrier that
+// cannot complete; *status_out (device) becomes SKF_ERR_TIMEOUT.
+skf_status barrier_selftest(int ctas, long long budget, int *status_out, cudaStream_t st);
 
 skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V, int64_t ldv,
                        double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,

@@ -191,32 +191,40 @@ skf_status build_sparse_sign_tables(skf_sketch *S, cudaStream_t st) {
         S->pattern = nullptr;
         return fail(SKF_ERR_OOM, "sketch pattern allocation");
     }
-    e = cudaMalloc(&S->binmax, 2 * sizeof(int));
+    e = cudaMalloc(&S->binmax, 3 * sizeof(int));
     if (e != cudaSuccess) {
         cudaGetLastError();
         S->binmax = nullptr;
         return fail(SKF_ERR_OOM, "sketch table allocation");
     }
     S->binmax_chunk = S->binmax + 1;
+    S->binmax_persist = S->binmax + 2;
     int G;
     int64_t rows;
     row_partition(S->n, &G, &rows);
     const int blocks = (int)std::min<int64_t>((S->n + 255) / 256, 16ll * num_sms());
     k_build_pattern<<<blocks, 256, 0, st>>>(sp, S->n, S->pattern);
-    cudaMemsetAsync(S->binmax, 0, 2 * sizeof(int), st);
+    cudaMemsetAsync(S->binmax, 0, 3 * sizeof(int), st);
     const size_t smem = sizeof(int) * S->s;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_bin_max, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_bin_max<<<G, 256, smem, st>>>(sp, S->n, rows, S->pattern, S->binmax);
     int Gc;
     chunk_partition(S->n, &Gc);
     k_bin_max<<<Gc, 256, smem, st>>>(sp, S->n, kChunkRows, S->pattern, S->binmax_chunk);
-    count_launches(3);
+    int Gp;
+    int64_t rows_p;
+    persist_partition(S->n, &Gp, &rows_p);
+    k_bin_max<<<Gp, 256, smem, st>>>(sp, S->n, rows_p, S->pattern, S->binmax_persist);
+    count_launches(4);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "sketch table build");
-    int hmax[2] = {0, 0};
-    cudaMemcpy(hmax, S->binmax, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+    int hmax[3] = {0, 0, 0};
+    cudaMemcpy(hmax, S->binmax, 3 * sizeof(int), cudaMemcpyDeviceToHost);
     if (limb_bits(hmax[0]) < 13 || limb_bits(hmax[1]) < 13)
         return fail(SKF_ERR_NOT_SUPPORTED, "sketch too dense for the fixed-point accumulators");
+    // the persistent Arnoldi kernel is simply not used for a denser partition
+    S->binmax_persist_host = hmax[2];
+    if (limb_bits(hmax[2]) < 13) S->binmax_persist = nullptr;
     int max_stripe = 0;
     for (int q = 0; q < sp.zeta; ++q) max_stripe = std::max(max_stripe, sp.size[q]);
     if (max_stripe <= 128 && S->zeta <= 8) {

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(skf):
 def test_version_and_status_strings(skf):
     L = skf.lib()
     assert L.skf_version() >= 100
-    for code in range(10):
+    for code in range(11):
         assert L.skf_status_string(code)
 
 
@@ -54,6 +54,9 @@ def test_host_side_validation(skf):
     assert b"n must be" in L.skf_last_error()
     assert L.skf_sketch_destroy(None) == 0
     assert L.skf_destroy_csr(None) == 0
+    assert L.skf_set_arnoldi_mode(3) == 1 and L.skf_set_arnoldi_mode(-1) == 1
+    assert L.skf_set_arnoldi_mode(0) == 0
+    assert L.skf_barrier_selftest(1, 10**6, None, None) == 1          # NULL status pointer
 
 
 @pytest.mark.parametrize("func,ell,c", [("invsqrt", 45, 1.0), ("invsqrt", 300, 1885.0),

@@ -109,6 +109,36 @@ def upwind_2d(n: int, D: float = 1e-3) -> CSR:
     return _stencil(n, 2, diag, off)
 
 
+def ninepoint_2d(n: int, nu=(100.0, 50.0), drop_corner: bool = False) -> CSR:
+    """-Delta u + nu . grad u on an n x n grid with the compact nine-point
+    (Mehrstellen) Laplacian (diagonal 20, edges -4, corners -1, over 6 h^2)
+    and centred first differences.  Its symmetric part is the nine-point
+    Laplacian (positive definite), so the operator is positive real.  With
+    ``drop_corner`` the (+1, +1) corner coupling is left out (eight entries
+    per interior row); its symmetric part keeps the diagonal 20 against
+    off-diagonal magnitudes 16 + 2 + 1 = 19 (over 6 h^2), so it is strictly
+    diagonally dominant and the operator stays positive real."""
+    h = 1.0 / (n + 1)
+    N = n * n
+    idx = np.arange(N, dtype=np.int64)
+    x, y = idx % n, idx // n
+    e, c0 = -4.0 / (6 * h * h), -1.0 / (6 * h * h)
+    cx, cy = nu[0] / (2 * h), nu[1] / (2 * h)
+    offs = [(-1, -1, c0), (0, -1, e - cy), (1, -1, c0), (-1, 0, e - cx), (0, 0, 20.0 / (6 * h * h)),
+            (1, 0, e + cx), (-1, 1, c0), (0, 1, e + cy)]
+    if not drop_corner:
+        offs.append((1, 1, c0))
+    width = len(offs)
+    cols = np.empty((N, width), dtype=np.int64)
+    vals = np.empty((N, width), dtype=np.float64)
+    valid = np.empty((N, width), dtype=bool)
+    for slot, (dx, dy, v) in enumerate(offs):       # ascending column order
+        cols[:, slot] = idx + dx + n * dy
+        vals[:, slot] = v
+        valid[:, slot] = (x + dx >= 0) & (x + dx < n) & (y + dy >= 0) & (y + dy < n)
+    return _assemble(N, cols, vals, valid)
+
+
 def powerlaw_graph_operator(N: int, alpha: float = 2.1, mean_degree: float = 10.0,
                             seed: int = 11, d_max: int = 100_000,
                             transpose: bool = False) -> CSR:
