@@ -45,7 +45,9 @@ typedef enum {
     SKF_ERR_INVALID_ARG = 1,         /* bad size, null pointer, s <= m, zeta > s, ... */
     SKF_ERR_CUDA = 2,                /* a CUDA call failed (message has the CUDA error) */
     SKF_ERR_OOM = 3,                 /* device allocation failed */
-    SKF_ERR_ILL_CONDITIONED = 4,     /* R of the whitening QR is numerically singular */
+    SKF_ERR_ILL_CONDITIONED = 4,     /* the estimate of cond(R) of the whitening QR passed
+                                        skf_params::cond_max, or R is singular; x is still
+                                        computed and written */
     SKF_ERR_BRANCH_CUT = 5,          /* a shifted system t I + M is singular for a node t */
     SKF_ERR_QUAD_NOT_CONVERGED = 6,  /* adaptive quadrature passed ell_max */
     SKF_ERR_SKETCH_TOO_SMALL = 7,    /* s < 2m is required by the GMRES reduction */
@@ -78,7 +80,8 @@ typedef enum {
     SKF_FUNC_LOG1P_OVER_Z = 1,  /* f(z) = log(1 + z) / z                   */
     SKF_FUNC_INV = 2,           /* f(z) = 1/z (single node t = 0): tests   */
     SKF_FUNC_INVPOW = 3,        /* f(z) = z^(-alpha), 0 < alpha < 1        */
-    SKF_FUNC_EXP_NEG = 4        /* f(z) = exp(-z): contour rule, see skf_func */
+    SKF_FUNC_EXP_NEG = 4,       /* f(z) = exp(-z): contour rule, see skf_func */
+    SKF_FUNC_CUSTOM = 5         /* any Stieltjes measure: rules from skf_func::rule */
 } skf_func_kind;
 
 typedef enum { SKF_METHOD_SFOM = 0, SKF_METHOD_SGMRES = 1 } skf_method;
@@ -90,6 +93,10 @@ typedef struct skf_sketch skf_sketch; /* opaque embedding handle        */
  * its quadrature family.  The rule for order ell (host-generated) is
  *   INVSQRT / INVPOW: Gauss-Jacobi(-alpha, alpha-1) (Chebyshev for alpha =
  *     1/2) in x, t = scale (1-x)/(1+x)  (Sec. 5.1 uses scale = 1),
+ *     w = (sin(alpha pi)/pi) 2 scale^(1-alpha) omega / (1+x) with the
+ *     Gauss-Jacobi weights omega (for alpha != 1/2: Golub-Welsch, nodes by
+ *     Sturm bisection of the Jacobi matrix, weights from its eigenvectors'
+ *     first components; orders up to 1024),
  *   LOG1P_OVER_Z: Gauss-Legendre in x, t = 1 + scale (1-x)/(1+x),
  *   INV: t = 0, w = 1.
  *   EXP_NEG (not a Stieltjes function; Algorithm 2 with a fixed contour):
@@ -103,22 +110,37 @@ typedef struct skf_sketch skf_sketch; /* opaque embedding handle        */
  *     A)^{-1} b with t_k = t(k h), w_k = (2 - [k = 0]) h e^{t_k}
  *     (i - 2 c k h) / (2 pi i).  Complex nodes: the node systems are solved
  *     through their real 2m x 2m form (requires m <= 256, ell1 >= 2).
+ *   CUSTOM: the measure is the caller's, passed as a closure: for each order
+ *     ell of the adaptive schedule (Sec. 4.1) the library calls
+ *     rule(ell, t, w, ctx) on the calling host thread, during skf_solve and
+ *     before any of its work is enqueued; the callback fills the host arrays
+ *     t[ell] (nodes, t_i >= 0) and w[ell] (weights) of a rule with
+ *     f(z) ~= sum_i w_i / (t_i + z) and returns 0 (nonzero: the call fails
+ *     with SKF_ERR_NOT_SUPPORTED).  The rules of a (rule, ctx, schedule)
+ *     triple are generated once and kept on the device for the life of the
+ *     process: a different measure needs a different rule function or ctx
+ *     pointer.  The library evaluates sFOM through the whitened quadrature
+ *     form (eq. (sFOM) with the nodes), so no scalar f is needed.
  * If n_nodes > 0 the host arrays nodes/weights are used as the only rule
  * (no adaptivity; real rules only). */
 typedef struct {
     skf_func_kind kind;
-    double alpha;           /* exponent for SKF_FUNC_INVPOW */
+    double alpha;           /* exponent for SKF_FUNC_INVPOW (0 < alpha < 1); vertex a for EXP_NEG */
     double scale;           /* c > 0 of the Moebius map      */
     int32_t n_nodes;        /* explicit rule length, 0 = adaptive family */
     const double *nodes;    /* host, n_nodes t_i >= 0 */
     const double *weights;  /* host, n_nodes w_i      */
+    int (*rule)(int32_t ell, double *t, double *w, void *ctx);   /* CUSTOM only */
+    void *ctx;              /* passed to rule unchanged */
 } skf_func;
 
 /* Method parameters (inputs of Algorithms 1 and 2). */
 typedef struct {
     int32_t m;              /* Krylov dimension, 1 <= m < s              */
     int32_t k;              /* truncation length of MGS, 1 <= k <= 16    */
-    skf_dtype basis_dtype;  /* storage of V_m: F64 (also F32/BF16 later) */
+    skf_dtype basis_dtype;  /* storage of V_m: F64 (F64 matrix values), or F32
+                               or BF16 (F32 matrix values; FP32 arithmetic in
+                               the Arnoldi process, FP64 tail)              */
     int32_t ell1, ell2;     /* first two quadrature orders (Sec. 4.1)    */
     int32_t ell_max;        /* give up past this order                   */
     double tol;             /* relative tolerance ||q1-q2|| <= tol ||q2|| */
@@ -141,9 +163,18 @@ typedef struct {
      * tail, a second pass repeats the same recurrence and accumulates
      * f = sum_j y_j v_j as each vector appears.  Twice the products with A.
      * The recurrence is deterministic, so the result equals the one-pass
-     * result (bit for bit with an F64 basis; for F32/BF16 the one-pass
-     * recombination sums in double-float, this one in FP64). */
+     * result of the two-kernel form of the Arnoldi process (bit for bit with
+     * an F64 basis; for F32/BF16 the one-pass recombination sums in
+     * double-float, this one in FP64); the two-pass and stopping modes run
+     * that form, and the persistent form that a plain F64 solve takes (see
+     * skf_set_arnoldi_mode) gives the same approximant to rounding. */
     int32_t two_pass;
+    /* Whitening check (Sec. 2.1 uses R^{-1}; reading of the survey: beyond
+     * cond(R) ~ 1e12 in FP64 report ill-conditioning): info->status becomes
+     * SKF_ERR_ILL_CONDITIONED when the estimate of cond(R) (skf_info::cond_est)
+     * exceeds cond_max; x is still computed.  0 selects 1e12; a negative value
+     * (or +inf) turns the test off (an exactly singular R is still reported). */
+    double cond_max;
 } skf_params;
 
 /* Device-written result record.  Place it in memory the device can write
@@ -165,6 +196,10 @@ typedef struct {
                                process, 0 if it did not (or was off)      */
     double err_est;         /* last relative estimate est_p (Sec. 4.3), 0
                                if no two checkpoints were compared        */
+    double cond_est;        /* estimate of cond(R) = ||R|| ||R^{-1}|| of the
+                               whitening factor: largest column norm times a
+                               LINPACK-style ||R^{-1}|| estimate, at least
+                               max|R_jj| / min|R_jj|                       */
 } skf_info;
 
 /* ---------------------------------------------------------------- misc */
@@ -294,7 +329,8 @@ skf_status skf_sketch_apply_noalloc(const skf_sketch *S, const void *X, skf_dtyp
  * modified Gram-Schmidt, Sec. 2.2) with the sketches S V_m, S A V_m built on
  * the fly (Sec. 2, comment 3).  Exactly m products with A are performed.
  *   b          device F64 [N] (bdtype must be SKF_F64 in this build)
- *   V, ldv     device basis storage, N x m, type basis_dtype (F64 here);
+ *   V, ldv     device basis storage, N x m, type basis_dtype (F64, or F32
+ *              and BF16 with F32 matrix values);
  *              column j holds a positive multiple w_j of the basis vector:
  *              v_j = vscale[j] * V[:, j], vscale[j] = 1 / ||V[:, j]||.
  *   vscale     device F64 [m]
@@ -323,6 +359,13 @@ skf_status skf_arnoldi_trunc(const skf_csr *A, const skf_sketch *S, const void *
  * floor(sqrt(2) ell2) until ||q_ell1 - q_ell2|| <= tol ||q_ell2|| or
  * ell_max is passed (info->status = QUAD_NOT_CONVERGED, x from the last
  * order).  Requires s >= 2m for SGMRES and m <= 512 (dense tail).
+ * Branch cut (Sec. 2.3, Sec. 5.4): when M has an eigenvalue on the branch
+ * cut of f (real and <= 0 for z^-alpha, <= -1 for log(1+z)/z) the sFOM
+ * approximant (sFOM''') is undefined; its quadrature form then has a pole of
+ * the integrand on the integration path, which info->status reports as
+ * SKF_ERR_BRANCH_CUT (a node system singular to working precision) or
+ * SKF_ERR_QUAD_NOT_CONVERGED (the rule does not settle), with x from the
+ * last order.  sGMRES solves least-squares problems, which stay defined.
  *   b  device F64 [N];   x  device F64 [N] (output)
  *   workspace is allocated stream-ordered (cudaMallocAsync) and released
  *   before return, so the call can be captured into a CUDA graph.

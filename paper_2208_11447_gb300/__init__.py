@@ -29,8 +29,9 @@ STATUS = {0: "SKF_OK", 1: "SKF_ERR_INVALID_ARG", 2: "SKF_ERR_CUDA", 3: "SKF_ERR_
           10: "SKF_ERR_TIMEOUT"}
 # Arnoldi forms of skf_set_arnoldi_mode
 ARNOLDI_AUTO, ARNOLDI_TWO_KERNEL, ARNOLDI_PERSISTENT = 0, 1, 2
-EXP_NEG = 4
-FUNC_KIND = {"invsqrt": INVSQRT, "log1p_over_z": LOG1P_OVER_Z, "inv": INV, "invpow": INVPOW, "exp_neg": EXP_NEG}
+EXP_NEG, CUSTOM = 4, 5
+FUNC_KIND = {"invsqrt": INVSQRT, "log1p_over_z": LOG1P_OVER_Z, "inv": INV, "invpow": INVPOW, "exp_neg": EXP_NEG,
+             "custom": CUSTOM}
 _DTYPE = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 
 
@@ -40,24 +41,30 @@ class SkfError(RuntimeError):
         self.status = status
 
 
+# int rule(int32_t ell, double *t, double *w, void *ctx) of a custom Stieltjes measure
+RULE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+
+
 class Func(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("alpha", ctypes.c_double), ("scale", ctypes.c_double),
                 ("n_nodes", ctypes.c_int32), ("nodes", ctypes.POINTER(ctypes.c_double)),
-                ("weights", ctypes.POINTER(ctypes.c_double))]
+                ("weights", ctypes.POINTER(ctypes.c_double)), ("rule", RULE_FN), ("ctx", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("k", ctypes.c_int32), ("basis_dtype", ctypes.c_int),
                 ("ell1", ctypes.c_int32), ("ell2", ctypes.c_int32), ("ell_max", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("check_every", ctypes.c_int32), ("stop_tol", ctypes.c_double),
-                ("two_pass", ctypes.c_int32)]
+                ("two_pass", ctypes.c_int32), ("cond_max", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("m_eff", ctypes.c_int32), ("breakdown", ctypes.c_int32),
                 ("ell", ctypes.c_int32), ("quad_err", ctypes.c_double), ("beta", ctypes.c_double),
                 ("eps_est", ctypes.c_double), ("rdiag_ratio", ctypes.c_double),
-                ("nodes_fp64", ctypes.c_int32), ("stop_m", ctypes.c_int32), ("err_est", ctypes.c_double)]
+                ("nodes_fp64", ctypes.c_int32), ("stop_m", ctypes.c_int32), ("err_est", ctypes.c_double),
+                ("cond_est", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -237,11 +244,32 @@ def arnoldi_trunc(A: Csr, S: Sketch, b: torch.Tensor, m: int, k: int, basis_dtyp
     return V, vscale, SV, SAV, H
 
 
-def make_func(kind: str, scale: float = 1.0, alpha: float = 0.5, nodes=None, weights=None) -> Func:
+def make_func(kind: str, scale: float = 1.0, alpha: float = 0.5, nodes=None, weights=None, rule=None,
+              ctx: int = 0) -> Func:
+    """rule (kind "custom"): a Python callable rule(ell) -> (t, w), two
+    sequences of ell floats with f(z) ~= sum_i w_i / (t_i + z); it is passed
+    to the library as the skf_func::rule closure (kept alive by the Func).
+    The library keeps the rules it generated per (rule, ctx) pointer pair:
+    give a different measure a distinct ctx (any nonzero integer tag)."""
     f = Func()
     f.kind = FUNC_KIND[kind]
     f.alpha = alpha
     f.scale = scale
+    if rule is not None:
+        def _cb(ell, tp, wp, ctx):
+            try:
+                t, w = rule(int(ell))
+                if len(t) != ell or len(w) != ell:
+                    return 1
+                for i in range(ell):
+                    tp[i] = float(t[i])
+                    wp[i] = float(w[i])
+                return 0
+            except Exception:
+                return 1
+        f._cb = RULE_FN(_cb)     # keep alive
+        f.rule = f._cb
+        f.ctx = ctx or None
     if nodes is not None:
         import numpy as np
         t = np.ascontiguousarray(nodes, dtype=np.float64)
@@ -256,12 +284,15 @@ def make_func(kind: str, scale: float = 1.0, alpha: float = 0.5, nodes=None, wei
 
 
 def make_params(m: int, k: int, basis_dtype=torch.float64, ell1=16, ell2=22, ell_max=1024, tol=1e-10,
-                check_every: int = 0, stop_tol: float = 0.0, two_pass: bool = False) -> Params:
+                check_every: int = 0, stop_tol: float = 0.0, two_pass: bool = False, cond_max: float = 0.0) -> Params:
     """check_every = d > 0 turns on the sketched stopping criterion (Sec. 4.3)
     with relative tolerance stop_tol; m is then the largest dimension.
     two_pass: the two-pass truncated Arnoldi of Sec. 4.2 (basis memory
-    N (k + 2) instead of N m, twice the products with A)."""
-    return Params(m, k, _DTYPE[basis_dtype], ell1, ell2, ell_max, tol, check_every, stop_tol, 1 if two_pass else 0)
+    N (k + 2) instead of N m, twice the products with A).
+    cond_max: ILL_CONDITIONED above this estimate of cond(R) (0: 1e12,
+    negative: no test)."""
+    return Params(m, k, _DTYPE[basis_dtype], ell1, ell2, ell_max, tol, check_every, stop_tol, 1 if two_pass else 0,
+                  cond_max)
 
 
 def solve(method: int, A: Csr, S: Sketch, b: torch.Tensor, f: Func, p: Params, x: torch.Tensor | None = None,

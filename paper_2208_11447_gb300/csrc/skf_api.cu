@@ -88,6 +88,83 @@ static void gauss_legendre_theta(int n, std::vector<double> &theta, std::vector<
     }
 }
 
+// Gauss-Jacobi rule for the weight (1-x)^a (1+x)^b (a, b > -1): the nodes
+// are the eigenvalues of the symmetric tridiagonal Jacobi matrix of the
+// orthonormal recurrence (Golub-Welsch), each found by bisection on Sturm
+// counts (negative pivots of T - lambda I = L D L^T); the weights are
+// mu_0 times the squared first component of the normalised eigenvector,
+// obtained by inverse iteration at the computed eigenvalue.  The diagonal
+// entry k = 0 and the off-diagonal entry k = 1 are used in their cancelled
+// forms, so a + b = -1 (the z^-alpha weight) is well defined.  Returns false
+// unless the nodes are distinct and ordered and the weights add up to mu_0.
+static bool gauss_jacobi(int n, double a, double b, std::vector<double> &x, std::vector<double> &omega) {
+    if (n < 1 || !(a > -1.0) || !(b > -1.0)) return false;
+    const double ab = a + b;
+    std::vector<double> dg(n), of2(n, 0.0);
+    dg[0] = (b - a) / (ab + 2.0);
+    for (int k = 1; k < n; ++k) dg[k] = (b * b - a * a) / ((2.0 * k + ab) * (2.0 * k + ab + 2.0));
+    if (n > 1) of2[1] = 4.0 * (1.0 + a) * (1.0 + b) / ((2.0 + ab) * (2.0 + ab) * (3.0 + ab));
+    for (int k = 2; k < n; ++k) {
+        const double k2 = 2.0 * k + ab;
+        of2[k] = 4.0 * k * (k + a) * (k + b) * (k + ab) / (k2 * k2 * (k2 + 1.0) * (k2 - 1.0));
+    }
+    auto below = [&](double lam) {
+        int cnt = 0;
+        double d = 1.0;
+        for (int k = 0; k < n; ++k) {
+            d = (dg[k] - lam) - (k > 0 ? of2[k] / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0.0) ++cnt;
+        }
+        return cnt;
+    };
+    const double mu0 = pow(2.0, ab + 1.0) * tgamma(a + 1.0) * tgamma(b + 1.0) / tgamma(ab + 2.0);
+    std::vector<double> of(n, 0.0), v(n), dd(n), ll(n);
+    for (int k = 1; k < n; ++k) of[k] = sqrt(of2[k]);
+    x.assign(n, 0.0);
+    omega.assign(n, 0.0);
+    double sum = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double lo = -1.0, hi = 1.0;
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (!(mid > lo && mid < hi)) break;
+            if (below(mid) > k) hi = mid;
+            else lo = mid;
+        }
+        const double xk = 0.5 * (lo + hi);
+        // normalised eigenvector by two steps of inverse iteration on the
+        // tridiagonal T - x I (elimination without pivoting; a zero pivot is
+        // replaced by a tiny one, which only sharpens the iteration)
+        for (int j = 0; j < n; ++j) v[j] = 1.0;
+        for (int it = 0; it < 2; ++it) {
+            double piv = dg[0] - xk;
+            if (piv == 0.0) piv = 1e-300;
+            dd[0] = piv;
+            for (int j = 1; j < n; ++j) {
+                const double l = of[j] / dd[j - 1];
+                ll[j] = l;
+                piv = (dg[j] - xk) - l * of[j];
+                if (piv == 0.0) piv = 1e-300;
+                dd[j] = piv;
+                v[j] -= l * v[j - 1];
+            }
+            v[n - 1] /= dd[n - 1];
+            for (int j = n - 2; j >= 0; --j) v[j] = (v[j] - of[j + 1] * v[j + 1]) / dd[j];
+            double mx = 0.0;
+            for (int j = 0; j < n; ++j) mx = std::max(mx, fabs(v[j]));
+            for (int j = 0; j < n; ++j) v[j] /= mx;
+        }
+        double ss = 0.0;
+        for (int j = 0; j < n; ++j) ss += v[j] * v[j];
+        x[k] = xk;
+        omega[k] = mu0 * v[0] * v[0] / ss;
+        sum += omega[k];
+        if (!(xk > -1.0 && xk < 1.0) || (k > 0 && !(xk > x[k - 1]))) return false;
+    }
+    return fabs(sum - mu0) <= 1e-11 * mu0;
+}
+
 // Contour rule for f(z) = exp(-z) on the parabola t(zeta) = a - c zeta^2 +
 // i zeta (a = f.alpha, c = f.scale): trapezoidal rule in zeta on [0, L],
 // c L^2 = 37, step h = L / (ell - 1), weights of zeta > 0 doubled (the
@@ -114,7 +191,21 @@ bool quadrature_rule(const skf_func &f, int ell, double *t, double *w) {
         w[0] = 1.0;
         return true;
     }
+    if (f.kind == SKF_FUNC_CUSTOM) return f.rule != nullptr && f.rule(ell, t, w, f.ctx) == 0;
     const double c = f.scale;
+    if (f.kind == SKF_FUNC_INVPOW && f.alpha != 0.5) {
+        // z^-alpha = (sin(alpha pi)/pi) int t^-alpha (t+z)^-1 dt with t = c (1-x)/(1+x):
+        // Gauss-Jacobi(-alpha, alpha-1) in x, w = (sin(alpha pi)/pi) 2 c^(1-alpha) omega / (1+x)
+        if (!(f.alpha > 0.0 && f.alpha < 1.0)) return false;
+        std::vector<double> xs, om;
+        if (!gauss_jacobi(ell, -f.alpha, f.alpha - 1.0, xs, om)) return false;
+        const double k = sin(f.alpha * M_PI) / M_PI * 2.0 * pow(c, 1.0 - f.alpha);
+        for (int i = 0; i < ell; ++i) {
+            t[i] = c * (1.0 - xs[i]) / (1.0 + xs[i]);
+            w[i] = k * om[i] / (1.0 + xs[i]);
+        }
+        return true;
+    }
     if (f.kind == SKF_FUNC_INVSQRT || (f.kind == SKF_FUNC_INVPOW && f.alpha == 0.5)) {
         // Gauss-Chebyshev: theta_i = (2i-1) pi / (2 ell), omega_i = pi / ell;
         // t = c tan^2(theta/2), w = 2 sqrt(c) / (ell (1 + x)).
@@ -152,8 +243,9 @@ static RuleCache &rule_cache() {
 
 static skf_status get_rule(const skf_func &f, const skf_params &p, const RuleDev **out) {
     char key[256];
-    snprintf(key, sizeof key, "%d|%.17g|%.17g|%d|%d|%d|%d", (int)f.kind, f.alpha, f.scale, p.ell1, p.ell2, p.ell_max,
-             f.n_nodes);
+    snprintf(key, sizeof key, "%d|%.17g|%.17g|%d|%d|%d|%d|%p|%p", (int)f.kind, f.alpha, f.scale, p.ell1, p.ell2,
+             p.ell_max, f.n_nodes, f.kind == SKF_FUNC_CUSTOM ? (void *)f.rule : nullptr,
+             f.kind == SKF_FUNC_CUSTOM ? f.ctx : nullptr);
     std::string k(key);
     if (f.n_nodes > 0) {
         for (int i = 0; i < f.n_nodes; ++i) {
@@ -199,7 +291,10 @@ static skf_status get_rule(const skf_func &f, const skf_params &p, const RuleDev
             if (!contour_rule(f, ell, ht.data() + o, hti.data() + o, hw.data() + o, hwi.data() + o))
                 return fail(SKF_ERR_INVALID_ARG, "contour rule needs ell >= 2 and scale > 0");
         } else if (!quadrature_rule(f, ell, ht.data() + o, hw.data() + o)) {
-            return fail(SKF_ERR_NOT_SUPPORTED, "quadrature family not implemented for this function");
+            return fail(SKF_ERR_NOT_SUPPORTED, f.kind == SKF_FUNC_CUSTOM
+                                                   ? "the custom rule callback failed for order " + std::to_string(ell)
+                                                   : "quadrature rule of order " + std::to_string(ell) +
+                                                         " not available for this function");
         }
         hs.push_back((int)ht.size());
     }
@@ -401,8 +496,11 @@ static skf_status solve_check(skf_method method, const skf_csr *A, const skf_ske
             return fail(SKF_ERR_INVALID_ARG, "need 1 <= ell1 < ell2, ell2 >= 3, ell_max >= ell2");
         if (!(p->tol > 0.0)) return fail(SKF_ERR_INVALID_ARG, "tol must be > 0");
     }
-    if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5 && f->n_nodes == 0)
-        return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
+    if (f->kind == SKF_FUNC_INVPOW && f->n_nodes == 0 && !(f->alpha > 0.0 && f->alpha < 1.0))
+        return fail(SKF_ERR_INVALID_ARG, "z^-alpha needs 0 < alpha < 1");
+    if (f->kind == SKF_FUNC_CUSTOM && f->n_nodes == 0 && f->rule == nullptr)
+        return fail(SKF_ERR_INVALID_ARG, "a custom function needs a rule callback or explicit nodes");
+    if (f->kind < SKF_FUNC_INVSQRT || f->kind > SKF_FUNC_CUSTOM) return fail(SKF_ERR_INVALID_ARG, "unknown function kind");
     if (f->kind == SKF_FUNC_EXP_NEG) {
         if (f->n_nodes > 0) return fail(SKF_ERR_NOT_SUPPORTED, "explicit rules are real; exp(-z) uses the contour");
         if (p->ell1 < 2) return fail(SKF_ERR_INVALID_ARG, "the contour rule needs ell1 >= 2");
@@ -480,7 +578,8 @@ static skf_status solve_enqueue(skf_method method, const skf_csr *A, const skf_s
     if (st == SKF_OK && sc.err != SKF_OK) st = sc.err;
     if (st == SKF_OK)
         st = tail_run(method, s, m, n, V, bt, ldv, vscale, SV, SAV, iscal, rule, p.tol, two ? nullptr : (double *)x,
-                      info, cs, nullptr, stopping ? sc.state : nullptr, z);
+                      info, cs, nullptr, stopping ? sc.state : nullptr, z,
+                      p.cond_max == 0.0 ? 1e12 : (p.cond_max < 0.0 ? 0.0 : p.cond_max));
     if (st == SKF_OK && two) {
         // second pass: the same recurrence (same sketches, H, vscale rewritten
         // with identical values), accumulating x column by column
@@ -892,9 +991,8 @@ skf_status skf_quadrature_rule_c(const skf_func *f, int32_t ell, double *t_re, d
                                  double *w_im) {
     if (!f || !t_re || !t_im || !w_re || !w_im || ell < 1) return fail(SKF_ERR_INVALID_ARG, "bad argument");
     if (f->kind != SKF_FUNC_EXP_NEG) {
-        if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5)
-            return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
-        if (!quadrature_rule(*f, ell, t_re, w_re)) return fail(SKF_ERR_NOT_SUPPORTED, "unknown function");
+        if (!quadrature_rule(*f, ell, t_re, w_re))
+            return fail(SKF_ERR_NOT_SUPPORTED, "no quadrature rule of this order for this function");
         for (int i = 0; i < ell; ++i) t_im[i] = w_im[i] = 0.0;
         return SKF_OK;
     }
@@ -907,9 +1005,8 @@ skf_status skf_quadrature_rule(const skf_func *f, int32_t ell, double *t_host, d
     if (!f || !t_host || !w_host || ell < 1) return fail(SKF_ERR_INVALID_ARG, "bad argument");
     if (f->kind == SKF_FUNC_EXP_NEG)
         return fail(SKF_ERR_NOT_SUPPORTED, "exp(-z) has a complex contour rule: skf_quadrature_rule_c");
-    if (f->kind == SKF_FUNC_INVPOW && f->alpha != 0.5)
-        return fail(SKF_ERR_NOT_SUPPORTED, "z^-alpha rule implemented for alpha = 1/2 only");
-    if (!quadrature_rule(*f, ell, t_host, w_host)) return fail(SKF_ERR_NOT_SUPPORTED, "unknown function");
+    if (!quadrature_rule(*f, ell, t_host, w_host))
+        return fail(SKF_ERR_NOT_SUPPORTED, "no quadrature rule of this order for this function");
     return SKF_OK;
 }
 

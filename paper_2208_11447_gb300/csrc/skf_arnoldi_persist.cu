@@ -218,22 +218,24 @@ __device__ __forceinline__ void scatter_row(const PCtx &c, int64_t r, uint2 pv, 
     }
 }
 
-// y~ = A w on this CTA's rows into ys[] (slices handed out dynamically to
-// the warps through *ctr, so a warp that starts late takes fewer), with the
-// window dots acc[a] = <w_{i0+a}, y~> (soff: slot offsets of the window in
-// win[], nw of them) and the magnitude key of max|y~|.  Entries of one row
-// are summed in their SELL (= CSR) order, so y~ does not depend on which
-// warp computes the row.
+// y~ = A w on this CTA's rows into ys[] by the kSpmvWarps SpMV warps, warp
+// w taking slices w, w + kSpmvWarps, ... (a fixed assignment, so every lane
+// accumulates the same rows in every run: the dot products are bitwise
+// reproducible), with the window dots acc[a] = <w_{i0+a}, y~> (soff: slot
+// offsets of the window in win[], nw of them) and the magnitude key of
+// max|y~|.  Entries of one row are summed in their SELL (= CSR) order.
+constexpr int kSpmvWarps = kPNW - 1;   // the last warp serves the reductions
 template <int KW, int W>
 __device__ __forceinline__ void spmv_rows(const PCtx &c, const double *__restrict__ wsrc, const double *win,
                                           const int (&soff)[KW], int nw, double *ys, const long long *meta_o,
-                                          const int *meta_w, int nsl, int nr, int *ctr, double (&acc)[KW],
+                                          const int *meta_w, int nsl, int nr, double (&acc)[KW],
                                           unsigned long long &ykey) {
     const int lane = threadIdx.x & 31;
+    int next_t = threadIdx.x >> 5;
     auto grab = [&]() {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(ctr, 1);
-        return __shfl_sync(0xffffffffu, t, 0);
+        const int t = next_t;
+        next_t += kSpmvWarps;
+        return t;
     };
     if constexpr (W > 0) {
         // three-stage pipeline: values and gathers of slice tn and column
@@ -358,7 +360,6 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
     __shared__ double sd[KW + 1];            // reduced dots and max|y~| of the current step
     __shared__ double sb[KW + 1];            // reduced ||w_j||^2, max|w_j|, Gram entries
     __shared__ int sbreak;                   // w_j is a happy breakdown
-    __shared__ int slice_ctr;                // dynamic slice counter of the SpMV
     unsigned nb = 0;                         // barriers passed
 
     // Column i of S V and column i-1 of S A V from the integer sums of S w_i
@@ -425,10 +426,7 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
         c.iscal[2] = SKF_OK;
         c.iscal[3] = m;
     }
-    if (tid == 0) {
-        slice_ctr = 0;
-        sbreak = 0;
-    }
+    if (tid == 0) sbreak = 0;
     {
         double nrm[1] = {0.0};
         unsigned long long key = 0;
@@ -472,12 +470,12 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
         const int nw = j - i0 + 1;
         const bool last = j == m - 1;
         const int ngj = min(j, k - 1);       // Gram distances of w_j
-        // ---- phase A: y~ = A w_j and the window dots.  Meanwhile the service
-        // warp reduces this CTA's partial norms of w_j (left by phase B of the
-        // previous step), adds the CTA's S w_{j-1} bins to the global sums and
-        // finalises the sketch columns of step j - 2: none of it is needed
-        // before the barrier, and phase A does not need the norm of w_j
-        // (stored unnormalised).
+        // ---- phase A: y~ = A w_j and the window dots (kSpmvWarps warps).
+        // Meanwhile the service warp reduces this CTA's partial norms of w_j
+        // (left by phase B of the previous step), adds the CTA's S w_{j-1}
+        // bins to the global sums and finalises the sketch columns of step
+        // j - 2: none of it is needed before the barrier, and phase A does not
+        // need the norm of w_j (stored unnormalised).
         double acc[KW];
 #pragma unroll
         for (int a = 0; a < KW; ++a) acc[a] = 0.0;
@@ -514,8 +512,8 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
             int soff[KW];   // window slot offsets, oldest first
 #pragma unroll
             for (int a = 0; a < KW; ++a) soff[a] = a < nw ? ((i0 + a) % k) * R : 0;
-            spmv_rows<KW, W>(c, c.V + (size_t)j * c.ldv, win, soff, nw, ys, meta_o, meta_w, nsl, nr, &slice_ctr, acc,
-                             ykey);
+            if (warp < kSpmvWarps)
+                spmv_rows<KW, W>(c, c.V + (size_t)j * c.ldv, win, soff, nw, ys, meta_o, meta_w, nsl, nr, acc, ykey);
         }
         ykey = block_reduce_t0<KW>(acc, ykey, red);
         if (tid == 0) {
@@ -539,7 +537,6 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
         }
         __syncthreads();
         if (tid == 0) {
-            slice_ctr = 0;
             if (j >= 1) {
                 // ||A v_{j-1}||^2 = sum_i h_i^2 + ||w_j||^2 for the orthonormal window;
                 // happy breakdown when ||w_j|| <= 1e-12 ||A v_{j-1}||
@@ -593,8 +590,8 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
 #pragma unroll
             for (int a = 0; a < KW; ++a) accb[a] = 0.0;
             unsigned long long kb = 0;
-            spmv_rows<KW, W>(c, c.V + (size_t)jb * c.ldv, win, soff, 0, ys, meta_o, meta_w, nsl, nr, &slice_ctr, accb,
-                             kb);
+            if (warp < kSpmvWarps)
+                spmv_rows<KW, W>(c, c.V + (size_t)jb * c.ldv, win, soff, 0, ys, meta_o, meta_w, nsl, nr, accb, kb);
             __syncthreads();
             const int ey = eys[jb & 3];
             const int shift_y = c.frac - (ey == kNoExp ? 0 : ey);
@@ -702,29 +699,35 @@ timeout:
     }
 }
 
-// | ||S v_j||^2 - 1 | maximum over the built columns and the info record.
-__global__ void __launch_bounds__(kThreads) k_persist_info(const double *__restrict__ SV, int s,
-                                                           const double *__restrict__ vscale,
-                                                           const int *__restrict__ iscal, skf_info *info) {
-    __shared__ double red[64];
-    const int me = iscal[1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double eps = 0.0;
-    for (int j = warp; j < me; j += kThreads / 32) {
-        double acc = 0.0;
-        for (int i = lane; i < s; i += 32) acc = fma(SV[i + (size_t)j * s], SV[i + (size_t)j * s], acc);
+// | ||S v_j||^2 - 1 | for column j (one CTA per column), folded into a
+// maximum with an integer atomic on the bit pattern (non-negative doubles
+// order like their bits, so the result does not depend on the order).
+__global__ void __launch_bounds__(128) k_persist_eps(const double *__restrict__ SV, int s,
+                                                    const int *__restrict__ iscal, unsigned long long *epsmax) {
+    __shared__ double red[4];
+    const int j = blockIdx.x;
+    if (j >= iscal[1]) return;
+    double a = 0.0;
+    for (int i = threadIdx.x; i < s; i += 128) a = fma(SV[i + (size_t)j * s], SV[i + (size_t)j * s], a);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        eps = fmax(eps, fabs(acc - 1.0));
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double e = fabs(((red[0] + red[1]) + red[2]) + red[3] - 1.0);
+        atomicMax(epsmax, (unsigned long long)__double_as_longlong(e));
     }
-    eps = block_max(eps, red);
-    if (threadIdx.x == 0 && info != nullptr) {
-        info->status = iscal[2];
-        info->m_eff = me;
-        info->breakdown = (iscal[0] == 1 && me > 0) ? 1 : 0;
-        info->beta = me > 0 ? 1.0 / vscale[0] : 0.0;
-        info->eps_est = eps;
-    }
+}
+
+__global__ void k_persist_info(const double *__restrict__ vscale, const int *__restrict__ iscal,
+                               const unsigned long long *epsmax, skf_info *info) {
+    if (threadIdx.x != 0 || info == nullptr) return;
+    const int me = iscal[1];
+    info->status = iscal[2];
+    info->m_eff = me;
+    info->breakdown = (iscal[0] == 1 && me > 0) ? 1 : 0;
+    info->beta = me > 0 ? 1.0 / vscale[0] : 0.0;
+    info->eps_est = __longlong_as_double((long long)*epsmax);
 }
 
 // A barrier that can never complete (it waits for one CTA more than the
@@ -855,7 +858,7 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     const size_t szAw = sizeof(unsigned long long) * (size_t)m * 2 * s;
     const size_t szAy = sizeof(unsigned long long) * 2 * (size_t)s;
     const size_t szSw = sizeof(double) * (size_t)s * m;
-    const size_t szBar = 2 * sizeof(int);
+    const size_t szBar = 2 * sizeof(int) + sizeof(unsigned long long);   // counter, flag, eps maximum
     const size_t total = 2 * al(szP) + al(szAw) + al(szAy) + al(szSw) + al(szBar);
     char *ws = nullptr;
     skf_status stt = dalloc((void **)&ws, total, st);
@@ -873,6 +876,7 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     c.Sw = (double *)take(szSw);
     c.bar = (unsigned *)take(szBar);
     c.flag = (int *)(c.bar + 1);
+    unsigned long long *epsmax = (unsigned long long *)(c.bar + 2);
     // accumulators and the barrier start at zero (one memset: they are adjacent)
     cudaMemsetAsync(c.accw, 0, (size_t)((char *)c.Sw - (char *)c.accw), st);
     cudaMemsetAsync(c.bar, 0, szBar, st);
@@ -885,8 +889,9 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
         if (e == cudaErrorCooperativeLaunchTooLarge) return SKF_ERR_NOT_SUPPORTED;
         return cuda_fail(e, "persistent Arnoldi launch");
     }
-    k_persist_info<<<1, kThreads, 0, st>>>(SV, s, vscale, iscal, info);
-    count_launches(2);
+    k_persist_eps<<<m, 128, 0, st>>>(SV, s, iscal, epsmax);
+    k_persist_info<<<1, 32, 0, st>>>(vscale, iscal, epsmax, info);
+    count_launches(3);
     e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "persistent Arnoldi kernels");

@@ -469,7 +469,7 @@ skf_status arnoldi_run_bf16(const skf_csr *A, const skf_sketch *S, const double 
 skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
                     double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out = nullptr,
-                    const double *stop_state = nullptr, double *z_out = nullptr);
+                    const double *stop_state = nullptr, double *z_out = nullptr, double cond_max = 0.0);
 // Two-pass mode: x (+)= z_j w_j for basis column w_j (type vdt), j < m_eff =
 // iscal[1]; j = 0 starts x (x = 0 when m_eff = 0).  The FMA sequence per row
 // is that of the one-pass FP64 recombination.

@@ -40,7 +40,8 @@ struct TailCtx {
     double *qbuf;      // [levels][m]
     double *qacc;      // [m]
     double *z;         // [m] coefficients for V (scaled by vscale)
-    double *qstate;    // [0] converged, [1] ell, [2] quad_err, [3] rdiag_ratio, [4] FP64 node solves
+    double *qstate;    // [0] converged, [1] ell, [2] quad_err, [3] rdiag_ratio, [4] FP64 node solves, [5] cond(R) estimate
+    double cond_max;   // ILL_CONDITIONED above this cond(R) estimate (0: no test)
     double *hsig;      // [2m] ||x(jj+1:)||^2 of each pivot column, from the previous reflector launch
     const double *t, *w;      // node table
     const double *ti, *wi;    // imaginary parts of complex (contour) nodes and weights, or nullptr
@@ -61,7 +62,7 @@ __global__ void k_tail_copy(const double *__restrict__ SV, const double *__restr
         else if (col < 2 * me) v = SAV[r + (int64_t)(col - me) * c.s];
         c.Aw[idx] = v;
     }
-    if (blockIdx.x == 0 && threadIdx.x < 5) c.qstate[threadIdx.x] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x < 6) c.qstate[threadIdx.x] = 0.0;
 }
 
 // Householder reflector for column jj (LAPACK convention: beta = -sign(x0)
@@ -821,47 +822,130 @@ __global__ void __launch_bounds__(kThreads) k_levels(TailCtx c, int lev0, int nl
     }
 }
 
-// y = R^{-1} q_acc, z = vscale .* y (single CTA, column-oriented back
-// substitution; column p-1 of R is prefetched while column p is applied).
-__global__ void __launch_bounds__(kThreads) k_coeffs(TailCtx c) {
-    extern __shared__ double q[];
-    __shared__ double red[64];
-    const int me = c.iscal[1];
-    constexpr int kPer = 2;   // rows per thread: me <= 2 * kThreads
-    for (int a = threadIdx.x; a < me; a += blockDim.x) q[a] = c.qacc[a];
-    double cur[kPer], nxt[kPer];
-    for (int u = 0; u < kPer; ++u) {
-        const int i = threadIdx.x + u * kThreads;
-        cur[u] = (me > 0 && i < me - 1) ? c.Aw[i + (int64_t)(me - 1) * c.s] : 0.0;
-    }
+// Triangular solves with the whitening factor R (upper; R_ij = Aw[i + j s]
+// for i < j, R_jj = Rdiag[j]) by one warp, vectors of length me <= 32 kRv
+// held in registers (lane l: entries l, l + 32, ...).  rinv: 1 / R_jj.
+constexpr int kRv = 16;   // m <= 512
+
+__device__ __forceinline__ double warp_pick(const double (&x)[kRv], int p) {
+    const int kp = p >> 5;
+    double v = x[0];
+#pragma unroll
+    for (int k = 1; k < kRv; ++k) v = (k == kp) ? x[k] : v;
+    return __shfl_sync(0xffffffffu, v, p & 31);
+}
+
+// back substitution R z = x in place, column-oriented: step p reads column p
+// of R (contiguous) and updates the rows above it
+__device__ void warp_back_subst(const double *Aw, int s, const double *rinv, int me, double (&x)[kRv]) {
+    const int lane = threadIdx.x & 31;
     for (int p = me - 1; p >= 0; --p) {
-        for (int u = 0; u < kPer; ++u) {
-            const int i = threadIdx.x + u * kThreads;
-            nxt[u] = (p >= 1 && i < p - 1) ? c.Aw[i + (int64_t)(p - 1) * c.s] : 0.0;
+        const double zp = warp_pick(x, p) * rinv[p];
+        const int nk = (p >> 5) + 1;   // warp-uniform: registers that hold rows <= p
+#pragma unroll
+        for (int k = 0; k < kRv; ++k) {
+            if (k < nk) {
+                const int i = lane + 32 * k;
+                if (i < p) x[k] = fma(-Aw[i + (int64_t)p * s], zp, x[k]);
+                else if (i == p) x[k] = zp;
+            }
         }
-        __syncthreads();
-        const double yp = q[p] / c.Rdiag[p];
-        __syncthreads();
-        if (threadIdx.x == 0) q[p] = yp;
-        for (int u = 0; u < kPer; ++u) {
-            const int i = threadIdx.x + u * kThreads;
-            if (i < p) q[i] = fma(-cur[u], yp, q[i]);
-            cur[u] = nxt[u];
+    }
+}
+
+// Estimate of ||R^{-1}||_2 in the manner of the LINPACK condition estimator:
+// solve R^T z = b with b_p = +-1 chosen, step by step, to make |z_p| as large
+// as possible, then R y = z; ||y|| / ||z|| approximates ||R^{-1}|| (from
+// below, usually within a small factor).  Returns the estimate in every lane.
+__device__ double warp_rinv_norm_est(const double *Aw, int s, const double *rinv, int me) {
+    const int lane = threadIdx.x & 31;
+    double z[kRv];
+#pragma unroll
+    for (int k = 0; k < kRv; ++k) z[k] = 0.0;
+    for (int p = 0; p < me; ++p) {   // R^T z = b: z_p = (b_p - sum_{i<p} R_ip z_i) / R_pp
+        const int nk = (p >> 5) + 1;
+        double part = 0.0;
+#pragma unroll
+        for (int k = 0; k < kRv; ++k) {
+            if (k < nk) {
+                const int i = lane + 32 * k;
+                if (i < p) part = fma(Aw[i + (int64_t)p * s], z[k], part);
+            }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const double bp = part > 0.0 ? -1.0 : 1.0;
+        const double zp = (bp - part) * rinv[p];
+        if (lane == (p & 31)) z[p >> 5] = zp;
+    }
+    double zn = 0.0;
+#pragma unroll
+    for (int k = 0; k < kRv; ++k) zn = fma(z[k], z[k], zn);
+    warp_back_subst(Aw, s, rinv, me, z);
+    double yn = 0.0;
+#pragma unroll
+    for (int k = 0; k < kRv; ++k) yn = fma(z[k], z[k], yn);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        zn += __shfl_xor_sync(0xffffffffu, zn, o);
+        yn += __shfl_xor_sync(0xffffffffu, yn, o);
+    }
+    return zn > 0.0 ? sqrt(yn / zn) : 0.0;
+}
+
+// y = R^{-1} q_acc, z = vscale .* y (warp 0); the estimate of cond(R) =
+// ||R|| ||R^{-1}|| (warp 1: LINPACK-style ||R^{-1}||; warp 2: the largest
+// column norm of R, which is within a factor sqrt(m) of ||R||).
+__global__ void __launch_bounds__(kThreads) k_coeffs(TailCtx c) {
+    extern __shared__ double rinv[];   // [me]
+    __shared__ double res[2];
+    const int me = c.iscal[1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bool zero_pivot = false;
+    for (int a = threadIdx.x; a < me; a += blockDim.x) {
+        const double d = c.Rdiag[a];
+        rinv[a] = d != 0.0 ? 1.0 / d : 0.0;
     }
     __syncthreads();
-    for (int a = threadIdx.x; a < me; a += blockDim.x) c.z[a] = c.vscale[a] * q[a];
-    // min |R_jj| / max |R_jj| over the whitening factor
-    double mn = INFINITY, mx = 0.0;
-    for (int a = threadIdx.x; a < me; a += blockDim.x) {
-        mn = fmin(mn, fabs(c.Rdiag[a]));
-        mx = fmax(mx, fabs(c.Rdiag[a]));
+    for (int a = threadIdx.x; a < me; a += blockDim.x) zero_pivot |= !(c.Rdiag[a] != 0.0);
+    zero_pivot = __syncthreads_or(zero_pivot);
+    if (warp == 0) {
+        double x[kRv];
+#pragma unroll
+        for (int k = 0; k < kRv; ++k) x[k] = (lane + 32 * k < me) ? c.qacc[lane + 32 * k] : 0.0;
+        if (!zero_pivot) warp_back_subst(c.Aw, c.s, rinv, me, x);
+#pragma unroll
+        for (int k = 0; k < kRv; ++k) {
+            const int i = lane + 32 * k;
+            if (i < me) c.z[i] = zero_pivot ? 0.0 : c.vscale[i] * x[k];
+        }
+    } else if (warp == 1) {
+        const double r = zero_pivot ? INFINITY : warp_rinv_norm_est(c.Aw, c.s, rinv, me);
+        if (lane == 0) res[0] = r;
+    } else if (warp == 2) {
+        double mx = 0.0;
+        for (int j = 0; j < me; ++j) {
+            double a = (lane == 0) ? c.Rdiag[j] * c.Rdiag[j] : 0.0;
+            for (int i = lane; i < j; i += 32) a = fma(c.Aw[i + (int64_t)j * c.s], c.Aw[i + (int64_t)j * c.s], a);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            mx = fmax(mx, a);
+        }
+        if (lane == 0) res[1] = sqrt(mx);
     }
-    mx = block_max(mx, red);
-    mn = -block_max(-mn, red);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        c.qstate[3] = mx > 0.0 ? mn / mx : 0.0;
-        if (!(mn > 0.0) && me > 0 && c.iscal[2] == SKF_OK) c.iscal[2] = SKF_ERR_ILL_CONDITIONED;
+        double mn = INFINITY, mxd = 0.0;
+        for (int a = 0; a < me; ++a) {
+            mn = fmin(mn, fabs(c.Rdiag[a]));
+            mxd = fmax(mxd, fabs(c.Rdiag[a]));
+        }
+        c.qstate[3] = mxd > 0.0 ? mn / mxd : 0.0;
+        // the estimate never reports less than the diagonal ratio, a lower bound of cond(R)
+        const double est = me == 0 ? 0.0 : fmax(res[0] * res[1], mn > 0.0 ? mxd / mn : INFINITY);
+        c.qstate[5] = est;
+        if (me > 0 && c.iscal[2] == SKF_OK && (zero_pivot || (c.cond_max > 0.0 && est > c.cond_max)))
+            c.iscal[2] = SKF_ERR_ILL_CONDITIONED;
     }
 }
 
@@ -1016,6 +1100,7 @@ __global__ void k_write_info(TailCtx c, skf_info *info, const double *stop_state
     info->quad_err = c.qstate[2];
     info->rdiag_ratio = c.qstate[3];
     info->nodes_fp64 = (int)c.qstate[4];
+    info->cond_est = c.qstate[5];
 }
 
 }  // namespace
@@ -1027,8 +1112,9 @@ __global__ void k_write_info(TailCtx c, skf_info *info, const double *stop_state
 skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
                     double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out,
-                    const double *stop_state, double *z_out) {
+                    const double *stop_state, double *z_out, double cond_max) {
     TailCtx c{};
+    c.cond_max = cond_max;
     c.s = s;
     c.m = m;
     c.method = method;
@@ -1064,7 +1150,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                             sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * m,
                             sizeof(double) * m, sizeof(double) * chunk * mm * (rule.cplx ? 4 : 1), sizeof(double) * (size_t)cap * m,
                             sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
-                            sizeof(double) * 5, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
+                            sizeof(double) * 6, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
                             sizeof(double) * 2 * (size_t)m};
     constexpr int kNbuf = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
@@ -1148,9 +1234,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                                          bi + 1 == batches.size() ? 1 : 0);
         ++nlaunch;
     }
-    const size_t qsm = sizeof(double) * m;
-    if (qsm > 48 * 1024) cudaFuncSetAttribute(k_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
-    k_coeffs<<<1, kThreads, qsm, st>>>(c);
+    k_coeffs<<<1, kThreads, sizeof(double) * m, st>>>(c);
     const int64_t rb = std::min<int64_t>((n + kThreads - 1) / kThreads, 16 * num_sms());
     const unsigned rgrid = (unsigned)std::max<int64_t>(rb, 1);
     const size_t zsm = sizeof(float) * 2 * (size_t)m;

@@ -94,3 +94,61 @@ def test_contour_rule_matches_oracle(skf, ell, c, a):
     to, wo = oq.rule("exp_neg", ell, c, a)
     np.testing.assert_allclose(t, to, rtol=1e-14, atol=1e-15)
     np.testing.assert_allclose(w, wo, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("alpha,ell", [(0.3, 16), (0.3, 150), (0.7, 60), (0.1, 400), (0.9, 1024)])
+def test_invpow_gauss_jacobi_rule(skf, alpha, ell):
+    """z^-alpha, alpha != 1/2: the host Gauss-Jacobi(-alpha, alpha-1) rule
+    (bisection on the Jacobi matrix, eigenvector weights) against the
+    oracle's (SciPy's tridiagonal eigensolver): nodes agree away from the end
+    points (both round 1 + x there), and the quadrature sums agree."""
+    from oracle import quadrature as oq
+    c = 7.0
+    t, w = skf.quadrature_rule(skf.make_func("invpow", c, alpha=alpha), ell)
+    to, wo = oq.rule("invpow", ell, c, alpha)
+    o1, o2 = np.argsort(t), np.argsort(to)
+    assert np.all(t > 0) and np.all(w > 0)
+    # both sides form 1 -+ x from x: the nodes nearest x = +-1 carry that rounding
+    np.testing.assert_allclose(t[o1], to[o2], rtol=1e-8, atol=0)
+    np.testing.assert_allclose(t[o1][5:-5], to[o2][5:-5], rtol=1e-11, atol=0)
+    z = np.geomspace(1e-2, 1e4, 40)
+    s1 = (w[None, :] / (t[None, :] + z[:, None])).sum(1)
+    s2 = (wo[None, :] / (to[None, :] + z[:, None])).sum(1)
+    np.testing.assert_allclose(s1, s2, rtol=1e-11)
+
+
+@pytest.mark.parametrize("alpha", [0.25, 0.6, 0.85])
+def test_invpow_rule_reproduces_z_power(skf, alpha):
+    """Pin to the closed form: sum_i w_i / (t_i + z) = z^-alpha on a spectral
+    interval, with the scale c = sqrt(lo hi) (Sec. 4.1's rules converge
+    geometrically in ell)."""
+    lo, hi = 30.0, 6e4
+    t, w = skf.quadrature_rule(skf.make_func("invpow", math.sqrt(lo * hi), alpha=alpha), 400)
+    z = np.geomspace(lo, hi, 50)
+    approx = (w[None, :] / (t[None, :] + z[:, None])).sum(1)
+    np.testing.assert_allclose(approx, z ** -alpha, rtol=1e-12)
+
+
+def test_invpow_rejects_alpha_outside_unit_interval(skf):
+    with pytest.raises(skf.SkfError):
+        skf.quadrature_rule(skf.make_func("invpow", 1.0, alpha=1.5), 10)
+
+
+def test_custom_rule_closure(skf):
+    """SKF_FUNC_CUSTOM: the library obtains the rule of each order from the
+    caller's rule(ell, t, w, ctx) closure and uses it unchanged; a failing
+    callback is reported as NOT_SUPPORTED."""
+    calls = []
+
+    def rule(ell):
+        calls.append(ell)
+        return np.arange(1, ell + 1, dtype=float), 1.0 / np.arange(1, ell + 1, dtype=float)
+
+    f = skf.make_func("custom", rule=rule)
+    t, w = skf.quadrature_rule(f, 7)
+    assert calls == [7]
+    np.testing.assert_array_equal(t, np.arange(1, 8, dtype=float))
+    np.testing.assert_array_equal(w, 1.0 / np.arange(1, 8, dtype=float))
+    bad = skf.make_func("custom", rule=lambda ell: ([1.0], [1.0]))      # wrong length
+    with pytest.raises(skf.SkfError, match="NOT_SUPPORTED"):
+        skf.quadrature_rule(bad, 3)

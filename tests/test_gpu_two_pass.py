@@ -2,7 +2,8 @@
 k + 2 basis vectors while it builds S V_m and S A V_m, the second repeats the
 recurrence and accumulates f = sum_j y_j v_j.  The recurrence is
 deterministic, so with an FP64 basis the result must equal the one-pass
-result bit for bit (and the oracle's approximant to 1e-10); with an FP32 or
+result of the same (two-kernel) form of the Arnoldi process bit for bit, the
+persistent form's to rounding, and the oracle's approximant to 1e-10; with an FP32 or
 BF16 basis the two differ only in the recombination's summation (FP64 here,
 double-float in the one-pass kernel)."""
 import numpy as np
@@ -42,10 +43,14 @@ def solve(skf, op, S, b, c, m, k, basis, method, two_pass, **kw):
 def test_fp64_two_pass_equals_one_pass_bitwise(skf, dims, n, m, k, method):
     A, op, b, c, S = setup(skf, dims, n, torch.float64, s=4 * m)
     meth = skf.SGMRES if method == "sgmres" else skf.SFOM
-    x1, i1 = solve(skf, op, S, b, c, m, k, torch.float64, meth, False)
+    with skf.arnoldi_mode(skf.ARNOLDI_TWO_KERNEL):
+        x1, i1 = solve(skf, op, S, b, c, m, k, torch.float64, meth, False)
     x2, i2 = solve(skf, op, S, b, c, m, k, torch.float64, meth, True)
     assert torch.equal(x1, x2)
     assert i1 == i2
+    # the default (persistent) one-pass form: the same approximant to rounding
+    xp, ip = solve(skf, op, S, b, c, m, k, torch.float64, meth, False)
+    assert rel(xp.cpu().numpy(), x2.cpu().numpy()) <= 1e-12 and ip["ell"] == i2["ell"]
     xo, _ = osk.solve(csr_to_scipy(A), b.cpu().numpy(), "invsqrt", m, k, OSketch("sparse_sign", A.n, 4 * m, 8, 13), c,
                       method=method if method == "sgmres" else "sfom_quad", tol=1e-10)
     assert rel(x2.cpu().numpy(), xo) <= 1e-10
