@@ -231,6 +231,16 @@ int64_t skf_kernel_launch_count(void);
  * Returns INVALID_ARG for another mode. */
 skf_status skf_set_arnoldi_mode(int32_t mode);
 
+/* skf_set_qr_mode: form of the whitening QR of [S V_m, S A V_m] in the tail
+ * (process-wide; results agree to rounding):
+ *   0  automatic (default): one cooperative launch, column q updated by CTA
+ *      q mod G throughout, each step starting as soon as the owner of its
+ *      pivot column has published it (bounded wait: SKF_ERR_TIMEOUT in
+ *      skf_info::status if it runs out);
+ *   1  one launch per Householder reflector.
+ * Returns INVALID_ARG for another mode. */
+skf_status skf_set_qr_mode(int32_t mode);
+
 /* skf_barrier_selftest: failure-detection check of the bounded grid wait
  * used by the persistent Arnoldi kernel.  Launches `ctas` co-resident CTAs
  * (1 <= ctas <= SMs) that wait at a barrier no CTA can complete, giving up

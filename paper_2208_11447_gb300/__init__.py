@@ -112,12 +112,13 @@ def lib():
         L.skf_quadrature_rule_c.argtypes = [ctypes.POINTER(Func), i32] + [ctypes.POINTER(dbl)] * 4
         L.skf_solve_batched.argtypes = [i32, ctypes.POINTER(Problem), i32, vp]
         L.skf_set_arnoldi_mode.argtypes = [i32]
+        L.skf_set_qr_mode.argtypes = [i32]
         L.skf_barrier_selftest.argtypes = [i32, i64, vp, vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
                      "skf_solve", "skf_solve_batched", "skf_sfom",
                      "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c", "skf_set_arnoldi_mode",
-                     "skf_barrier_selftest"]:
+                     "skf_set_qr_mode", "skf_barrier_selftest"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -386,6 +387,27 @@ class arnoldi_mode:
 
     def __exit__(self, *exc):
         set_arnoldi_mode(ARNOLDI_AUTO)
+        return False
+
+
+def set_qr_mode(mode: int) -> None:
+    """skf_set_qr_mode: 0 one cooperative launch (default), 1 one launch per reflector."""
+    _check(lib().skf_set_qr_mode(mode))
+
+
+class qr_mode:
+    """Context manager: run the enclosed calls with the given QR form, then
+    return to the default."""
+
+    def __init__(self, mode: int):
+        self.mode = mode
+
+    def __enter__(self):
+        set_qr_mode(self.mode)
+        return self
+
+    def __exit__(self, *exc):
+        set_qr_mode(0)
         return False
 
 

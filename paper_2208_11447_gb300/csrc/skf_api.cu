@@ -699,6 +699,12 @@ skf_status skf_set_arnoldi_mode(int32_t mode) {
     return SKF_OK;
 }
 
+skf_status skf_set_qr_mode(int32_t mode) {
+    if (mode < 0 || mode > 1) return fail(SKF_ERR_INVALID_ARG, "QR mode must be 0 or 1");
+    set_qr_mode(mode);
+    return SKF_OK;
+}
+
 skf_status skf_barrier_selftest(int32_t ctas, int64_t budget_cycles, int32_t *status_device, skf_stream_t stream) {
     if (!status_device) return fail(SKF_ERR_INVALID_ARG, "status_device is NULL");
     if (ctas < 1 || ctas > num_sms()) return fail(SKF_ERR_INVALID_ARG, "need 1 <= ctas <= number of SMs");

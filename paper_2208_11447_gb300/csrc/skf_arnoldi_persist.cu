@@ -104,7 +104,7 @@ __device__ bool grid_barrier(unsigned *bar, int *flag, unsigned nb, long long bu
                 good = 0;
                 break;
             }
-            __nanosleep(32);
+            // spin: one thread per CTA polls one L2 line
         }
         if (!good) atomicExch(flag, 1);
         __threadfence();
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
         return;
     }
     if (tid == 0) {
-        sig[0] = 1.0 / sqrt(sb[0]);
+        sig[0] = rsqrt(sb[0]);
         ews[0] = positive_finite(sb[1]) ? bound_exponent(sb[1]) : kNoExp;
         if (g == 0) c.vscale[0] = sig[0];
     }
@@ -540,19 +540,22 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
             if (j >= 1) {
                 // ||A v_{j-1}||^2 = sum_i h_i^2 + ||w_j||^2 for the orthonormal window;
                 // happy breakdown when ||w_j|| <= 1e-12 ||A v_{j-1}||
+                // (compared in squares, and sigma = 1/||w_j|| from one rsqrt: an FP64
+                // square root or division is ~650 dependent cycles on this part)
                 const double n2 = sb[0];
                 double hs = 0.0;
-                for (int a = 0; a < cnw[(j - 1) & 3]; ++a) hs += sh[a] * sh[a];
-                const double hn = sqrt(n2);
-                sbreak = (hn > 1e-12 * sqrt(hs + n2)) ? 0 : 1;
+                for (int a = 0; a < cnw[(j - 1) & 3]; ++a) hs = fma(sh[a], sh[a], hs);
+                sbreak = (n2 > 1e-24 * (hs + n2)) ? 0 : 1;
+                const double sgm = n2 > 0.0 ? rsqrt(n2) : 0.0;
+                const double hn = n2 * sgm;
                 if (!sbreak) {   // w_j enters the window
-                    sig[j & 3] = 1.0 / hn;
+                    sig[j & 3] = sgm;
                     for (int d = 1; d <= ngj; ++d) grm[j & 3][d] = sb[1 + d];
                     ews[j & 3] = positive_finite(sb[1]) ? bound_exponent(sb[1]) : kNoExp;
                 }
                 if (g == 0) {
                     c.H[j + (size_t)(j - 1) * (m + 1)] = hn;
-                    if (!sbreak) c.vscale[j] = 1.0 / hn;
+                    if (!sbreak) c.vscale[j] = sgm;
                 }
             }
             if (!sbreak) {

@@ -445,6 +445,10 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
 // SKF_ERR_NOT_SUPPORTED.
 void set_step_mode(int mode);
 int step_mode();
+// Form of the whitening QR in the tail: 0 one cooperative launch where it
+// fits, 1 one launch per Householder reflector.
+void set_qr_mode(int mode);
+int qr_mode();
 // Bounded-wait self-test: `ctas` co-resident CTAs wait at a barrier that
 // cannot complete; *status_out (device) becomes SKF_ERR_TIMEOUT.
 skf_status barrier_selftest(int ctas, long long budget, int *status_out, cudaStream_t st);

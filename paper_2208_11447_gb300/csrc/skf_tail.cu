@@ -143,20 +143,268 @@ __global__ void __launch_bounds__(kHhThreads) k_householder(TailCtx c, int jj) {
     }
 }
 
+// The whole Householder QR of [S V_m, S A V_m] in one cooperative launch.
+// Column q belongs to CTA q mod G for the whole factorisation and stays in
+// that CTA's shared memory until the end, so a CTA's trailing columns are
+// only ever read and updated on chip.  The only data a step needs from
+// another CTA is its pivot column: the owner of column jj + 1 updates that
+// column first at step jj, writes it to global memory and publishes it (a
+// release store of jj + 1 to a step counter); every other CTA starts step
+// jj + 1 as soon as the counter reaches jj + 1 (bounded wait), so the updates
+// of the remaining columns overlap the next steps instead of meeting at a
+// grid barrier.  Each step is one pass over the pivot column per CTA:
+// ||x(jj+1:)||^2 and the products x(jj+1:)^T y for the CTA's columns, summed
+// in one block reduction; the reflector (LAPACK convention, as
+// k_householder) is formed identically by every CTA.
+constexpr int kQrThreads = 256;
+constexpr int kQrOwn = 7;            // columns per CTA (at most)
+constexpr long long kQrBudget = 1ll << 31;
+
+__device__ __forceinline__ unsigned qr_ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// sums over the CTA of nv <= kQrOwn + 1 per-thread values, in a fixed order,
+// into tot[] (visible to every thread on return)
+__device__ __forceinline__ void qr_block_sums(const double (&v)[kQrOwn + 1], int nv, double *sm, double *tot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < kQrOwn + 1; ++k)
+        if (k < nv) sm[k * kQrThreads + tid] = v[k];
+    __syncthreads();
+    if (warp < nv) {
+        double a = 0.0;
+#pragma unroll
+        for (int r = 0; r < kQrThreads / 32; ++r) a += sm[warp * kQrThreads + lane + 32 * r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) tot[warp] = a;
+    }
+    __syncthreads();
+}
+
+size_t qr_smem_bytes(int s) {
+    return sizeof(double) * ((size_t)kQrOwn * s + s + (size_t)(kQrOwn + 1) * kQrThreads + kQrOwn + 1);
+}
+
+__global__ void __launch_bounds__(kQrThreads) k_qr_persist(TailCtx c, unsigned *ready, int *flag) {
+    extern __shared__ double qsm[];
+    __shared__ int ok;
+    const int me = c.iscal[1];
+    const int ncols = 2 * me;
+    const int s = c.s;
+    const int nref = min((c.method == SKF_METHOD_SGMRES) ? 2 * me : me, s);
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+    double *cols = qsm;                                   // [kQrOwn][s]: columns g, g + G, ...
+    double *xs = cols + (size_t)kQrOwn * s;               // [s] pivot column
+    double *sm = xs + s;                                  // reduction scratch
+    double *tot = sm + (kQrOwn + 1) * kQrThreads;
+    int nq = 0;
+    for (int q = g; q < ncols; q += G) ++nq;
+    for (int k = 0; k < nq; ++k)
+        for (int i = tid; i < s; i += kQrThreads) cols[(size_t)k * s + i] = c.Aw[i + (int64_t)(g + k * G) * s];
+    __syncthreads();
+    for (int jj = 0; jj < nref; ++jj) {
+        // own columns that trail the pivot: k >= kf (column g + k G > jj)
+        const int kf = jj < g ? 0 : (jj - g) / G + 1;
+        const bool writer = (jj % G) == g;                 // owns the pivot column
+        if (kf >= nq && !writer) continue;
+        // pivot column jj, rows jj .. s-1
+        if (writer) {
+            const double *xc = cols + (size_t)((jj - g) / G) * s;
+            for (int i = jj + tid; i < s; i += kQrThreads) xs[i] = xc[i];
+        } else {
+            if (tid == 0) {
+                const long long t0 = clock64();
+                int good = 1;
+                while (qr_ld_acquire(ready) < (unsigned)jj) {
+                    if (*(volatile int *)flag != 0 || clock64() - t0 > kQrBudget) {
+                        good = 0;
+                        break;
+                    }
+                }
+                if (!good) atomicExch(flag, 1);
+                ok = good;
+            }
+            __syncthreads();
+            if (!ok) {
+                if (tid == 0) atomicExch(&c.iscal[2], (int)SKF_ERR_TIMEOUT);
+                return;
+            }
+            const double *x = c.Aw + (int64_t)jj * s;
+            for (int i = jj + tid; i < s; i += kQrThreads) xs[i] = __ldcg(x + i);
+        }
+        __syncthreads();
+        const double x0 = xs[jj];
+        // the next pivot column (jj + 1) is this CTA's first trailing one:
+        // update and publish it before the others
+        const bool pivot_owner = kf < nq && g + kf * G == jj + 1;
+        const int n1 = pivot_owner ? 1 : nq - kf;
+        double loc[kQrOwn + 1];
+#pragma unroll
+        for (int k = 0; k < kQrOwn + 1; ++k) loc[k] = 0.0;
+        for (int i = jj + 1 + tid; i < s; i += kQrThreads) {
+            const double xi = xs[i];
+            loc[0] = fma(xi, xi, loc[0]);
+#pragma unroll
+            for (int k = 0; k < kQrOwn; ++k)
+                if (k < n1) loc[1 + k] = fma(xi, cols[(size_t)(kf + k) * s + i], loc[1 + k]);
+        }
+        qr_block_sums(loc, 1 + (kf < nq ? n1 : 0), sm, tot);
+        // reflector from one rsqrt and one reciprocal (an FP64 square root or
+        // division is ~650 dependent cycles on this part): with
+        // r = (x0^2 + sig)^-1/2, ||x|| = (x0^2 + sig) r, beta = -sign(x0) ||x||,
+        // tau = (beta - x0) / beta = 1 + |x0| r, 1 / (x0 - beta) = sign(x0) / (|x0| + ||x||)
+        const double sig = tot[0];
+        double tau = 0.0, beta = x0, scale = 0.0;
+        if (sig > 0.0 || x0 == 0.0) {
+            const double q2 = fma(x0, x0, sig);
+            if (q2 > 0.0) {
+                const double r = rsqrt(q2);
+                const double nx = q2 * r;
+                const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
+                beta = -sgn * nx;
+                tau = fma(fabs(x0), r, 1.0);
+                scale = sgn / (fabs(x0) + nx);
+            }
+        }
+        if (writer && tid == 0) c.Rdiag[jj] = beta;
+        if (kf >= nq) {
+            __syncthreads();
+            continue;
+        }
+        // y(jj) -= f, y(i) -= f scale x_i, f = tau (y(jj) + scale x^T y); every
+        // thread forms f from y(jj) before thread 0 changes it
+        double f1[kQrOwn];
+#pragma unroll
+        for (int k = 0; k < kQrOwn; ++k) f1[k] = k < n1 ? tau * (cols[(size_t)(kf + k) * s + jj] + scale * tot[1 + k]) : 0.0;
+        __syncthreads();
+        if (tau != 0.0) {
+#pragma unroll
+            for (int k = 0; k < kQrOwn; ++k) {
+                if (k < n1) {
+                    double *y = cols + (size_t)(kf + k) * s;
+                    const double fs = f1[k] * scale;
+                    for (int i = jj + 1 + tid; i < s; i += kQrThreads) y[i] = fma(-fs, xs[i], y[i]);
+                    if (tid == 0) y[jj] -= f1[k];
+                }
+            }
+        }
+        if (pivot_owner) {
+            // publish column jj + 1 (rows jj + 1 .. s - 1: what the next reflector reads)
+            __syncthreads();
+            double *yg = c.Aw + (int64_t)(jj + 1) * s;
+            const double *y = cols + (size_t)kf * s;
+            for (int i = jj + 1 + tid; i < s; i += kQrThreads) yg[i] = y[i];
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ready), "r"((unsigned)(jj + 1)) : "memory");
+            }
+            const int n2 = nq - kf - 1;
+            if (n2 > 0) {   // the rest of this CTA's trailing columns
+#pragma unroll
+                for (int k = 0; k < kQrOwn + 1; ++k) loc[k] = 0.0;
+                for (int i = jj + 1 + tid; i < s; i += kQrThreads) {
+                    const double xi = xs[i];
+#pragma unroll
+                    for (int k = 0; k < kQrOwn; ++k)
+                        if (k < n2) loc[k] = fma(xi, cols[(size_t)(kf + 1 + k) * s + i], loc[k]);
+                }
+                qr_block_sums(loc, n2, sm, tot);
+                double f2[kQrOwn];
+#pragma unroll
+                for (int k = 0; k < kQrOwn; ++k)
+                    f2[k] = k < n2 ? tau * (cols[(size_t)(kf + 1 + k) * s + jj] + scale * tot[k]) : 0.0;
+                __syncthreads();
+                if (tau != 0.0) {
+#pragma unroll
+                    for (int k = 0; k < kQrOwn; ++k) {
+                        if (k < n2) {
+                            double *y = cols + (size_t)(kf + 1 + k) * s;
+                            const double fs = f2[k] * scale;
+                            for (int i = jj + 1 + tid; i < s; i += kQrThreads) y[i] = fma(-fs, xs[i], y[i]);
+                            if (tid == 0) y[jj] -= f2[k];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // the factored columns back to global memory (R above the diagonal, the
+    // reflectors below it are not used later)
+    for (int k = 0; k < nq; ++k)
+        for (int i = tid; i < s; i += kQrThreads) c.Aw[i + (int64_t)(g + k * G) * s] = cols[(size_t)k * s + i];
+}
+
 constexpr int kMaxRegCol = 16;    // register slots per lane for one column of R (m <= 512)
 
-// Rows of X R = T for T = R12 (-> M) and T = R22 (-> R2); one warp per row.
-// Column jcol+1 of R is loaded into registers while column jcol is reduced.
-__global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c) {
-    extern __shared__ double xs[];   // [warps][m]
+__device__ double warp_rinv_norm_est(const double *Aw, int s, const double *rinv, int me);
+
+// Rows of X R = T for T = R12 (-> M) and T = R22 (-> R2); one warp per row,
+// x_j = (t_j - sum_{i<j} x_i R_ij) / R_jj.  The row of T and the reciprocals
+// 1 / R_jj are staged in shared memory first, and column j + 1 of R is
+// loaded into registers while column j is reduced, so a step waits on no
+// global load.  The last CTA computes the estimate of cond(R) (qstate[5])
+// meanwhile: ||R^{-1}|| LINPACK-style times the largest column norm of R.
+__global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c, int nblk_rows) {
+    extern __shared__ double xs[];   // [warps][m] solutions, [warps][m] rows of T, [m] 1 / R_jj
     const int me = c.iscal[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *rinv = xs + (size_t)2 * (kThreads / 32) * c.m;
+    for (int j = threadIdx.x; j < me; j += blockDim.x) rinv[j] = c.Rdiag[j] != 0.0 ? 1.0 / c.Rdiag[j] : 0.0;
+    __syncthreads();
+    if ((int)blockIdx.x == nblk_rows) {   // the cond(R) estimate
+        __shared__ double res[2];
+        if (warp == 0) {
+            bool zp = false;
+            for (int j = lane; j < me; j += 32) zp |= !(c.Rdiag[j] != 0.0);
+            zp = __any_sync(0xffffffffu, zp);
+            const double r = zp ? INFINITY : warp_rinv_norm_est(c.Aw, c.s, rinv, me);
+            if (lane == 0) res[0] = r;
+        } else if (warp == 1) {
+            double mx = 0.0;
+            for (int j = 0; j < me; ++j) {
+                double a2 = (lane == 0) ? c.Rdiag[j] * c.Rdiag[j] : 0.0;
+                for (int i = lane; i < j; i += 32) a2 = fma(c.Aw[i + (int64_t)j * c.s], c.Aw[i + (int64_t)j * c.s], a2);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                mx = fmax(mx, a2);
+            }
+            if (lane == 0) res[1] = sqrt(mx);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double mn = INFINITY, mxd = 0.0;
+            for (int a2 = 0; a2 < me; ++a2) {
+                mn = fmin(mn, fabs(c.Rdiag[a2]));
+                mxd = fmax(mxd, fabs(c.Rdiag[a2]));
+            }
+            c.qstate[3] = mxd > 0.0 ? mn / mxd : 0.0;
+            // never less than the diagonal ratio, a lower bound of cond(R)
+            c.qstate[5] = me == 0 ? 0.0 : fmax(res[0] * res[1], mn > 0.0 ? mxd / mn : INFINITY);
+        }
+        return;
+    }
     const int row = blockIdx.x * (kThreads / 32) + warp;
     const int nrows = (c.method == SKF_METHOD_SGMRES) ? 2 * me : me;
     if (row >= nrows) return;
     double *x = xs + (size_t)warp * c.m;
+    double *tr = xs + (size_t)((kThreads / 32) + warp) * c.m;
     const bool second = row >= me;
     const int a = second ? row - me : row;
+    for (int j = lane; j < me; j += 32) {
+        double tv;
+        if (!second) tv = c.Aw[a + (int64_t)(me + j) * c.s];
+        else if (j < a) tv = 0.0;
+        else if (j == a) tv = c.Rdiag[me + a];
+        else tv = c.Aw[(me + a) + (int64_t)(me + j) * c.s];
+        tr[j] = tv;
+    }
+    __syncwarp();
     double cur[kMaxRegCol], nxt[kMaxRegCol];
 #pragma unroll
     for (int t = 0; t < kMaxRegCol; ++t) cur[t] = 0.0;   // column 0 has no entries above the diagonal
@@ -178,14 +426,7 @@ __global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c) {
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) {
-            double tv;
-            if (!second) tv = c.Aw[a + (int64_t)(me + jcol) * c.s];
-            else if (jcol < a) tv = 0.0;
-            else if (jcol == a) tv = c.Rdiag[me + a];
-            else tv = c.Aw[(me + a) + (int64_t)(me + jcol) * c.s];
-            x[jcol] = (tv - part) / c.Rdiag[jcol];
-        }
+        if (lane == 0) x[jcol] = (tr[jcol] - part) * rinv[jcol];
         __syncwarp();
 #pragma unroll
         for (int t = 0; t < kMaxRegCol; ++t) cur[t] = nxt[t];
@@ -839,17 +1080,30 @@ __device__ __forceinline__ double warp_pick(const double (&x)[kRv], int p) {
 // of R (contiguous) and updates the rows above it
 __device__ void warp_back_subst(const double *Aw, int s, const double *rinv, int me, double (&x)[kRv]) {
     const int lane = threadIdx.x & 31;
+    double cur[kRv], nxt[kRv];   // column p of R (rows < p), column p - 1 prefetched
+#pragma unroll
+    for (int k = 0; k < kRv; ++k) {
+        const int i = lane + 32 * k;
+        cur[k] = (me > 0 && i < me - 1) ? Aw[i + (int64_t)(me - 1) * s] : 0.0;
+    }
     for (int p = me - 1; p >= 0; --p) {
+#pragma unroll
+        for (int k = 0; k < kRv; ++k) {
+            const int i = lane + 32 * k;
+            nxt[k] = (p >= 1 && i < p - 1) ? Aw[i + (int64_t)(p - 1) * s] : 0.0;
+        }
         const double zp = warp_pick(x, p) * rinv[p];
         const int nk = (p >> 5) + 1;   // warp-uniform: registers that hold rows <= p
 #pragma unroll
         for (int k = 0; k < kRv; ++k) {
             if (k < nk) {
                 const int i = lane + 32 * k;
-                if (i < p) x[k] = fma(-Aw[i + (int64_t)p * s], zp, x[k]);
+                if (i < p) x[k] = fma(-cur[k], zp, x[k]);
                 else if (i == p) x[k] = zp;
             }
         }
+#pragma unroll
+        for (int k = 0; k < kRv; ++k) cur[k] = nxt[k];
     }
 }
 
@@ -859,24 +1113,36 @@ __device__ void warp_back_subst(const double *Aw, int s, const double *rinv, int
 // below, usually within a small factor).  Returns the estimate in every lane.
 __device__ double warp_rinv_norm_est(const double *Aw, int s, const double *rinv, int me) {
     const int lane = threadIdx.x & 31;
-    double z[kRv];
+    double z[kRv], cur[kRv], nxt[kRv];   // column p of R, column p + 1 prefetched
 #pragma unroll
-    for (int k = 0; k < kRv; ++k) z[k] = 0.0;
+    for (int k = 0; k < kRv; ++k) {
+        z[k] = 0.0;
+        cur[k] = 0.0;   // column 0 has no entries above the diagonal
+    }
     for (int p = 0; p < me; ++p) {   // R^T z = b: z_p = (b_p - sum_{i<p} R_ip z_i) / R_pp
+#pragma unroll
+        for (int k = 0; k < kRv; ++k) {
+            const int i = lane + 32 * k;
+            nxt[k] = (p + 1 < me && i < p + 1) ? Aw[i + (int64_t)(p + 1) * s] : 0.0;
+        }
         const int nk = (p >> 5) + 1;
         double part = 0.0;
 #pragma unroll
         for (int k = 0; k < kRv; ++k) {
             if (k < nk) {
                 const int i = lane + 32 * k;
-                if (i < p) part = fma(Aw[i + (int64_t)p * s], z[k], part);
+                if (i < p) part = fma(cur[k], z[k], part);
             }
         }
+#pragma unroll
+        for (int k = 0; k < kRv; ++k) cur[k] = nxt[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         const double bp = part > 0.0 ? -1.0 : 1.0;
         const double zp = (bp - part) * rinv[p];
-        if (lane == (p & 31)) z[p >> 5] = zp;
+#pragma unroll
+        for (int k = 0; k < kRv; ++k)
+            if (k == (p >> 5) && lane == (p & 31)) z[k] = zp;
     }
     double zn = 0.0;
 #pragma unroll
@@ -893,60 +1159,33 @@ __device__ double warp_rinv_norm_est(const double *Aw, int s, const double *rinv
     return zn > 0.0 ? sqrt(yn / zn) : 0.0;
 }
 
-// y = R^{-1} q_acc, z = vscale .* y (warp 0); the estimate of cond(R) =
-// ||R|| ||R^{-1}|| (warp 1: LINPACK-style ||R^{-1}||; warp 2: the largest
-// column norm of R, which is within a factor sqrt(m) of ||R||).
-__global__ void __launch_bounds__(kThreads) k_coeffs(TailCtx c) {
+// y = R^{-1} q_acc, z = vscale .* y: one warp, back substitution with the
+// column of R prefetched (warp_back_subst); ILL_CONDITIONED when R has a zero
+// pivot or the estimate of cond(R) (k_tri_right) exceeds cond_max.
+__global__ void __launch_bounds__(32) k_coeffs(TailCtx c) {
     extern __shared__ double rinv[];   // [me]
-    __shared__ double res[2];
     const int me = c.iscal[1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     bool zero_pivot = false;
-    for (int a = threadIdx.x; a < me; a += blockDim.x) {
+    for (int a = lane; a < me; a += 32) {
         const double d = c.Rdiag[a];
+        zero_pivot |= !(d != 0.0);
         rinv[a] = d != 0.0 ? 1.0 / d : 0.0;
     }
-    __syncthreads();
-    for (int a = threadIdx.x; a < me; a += blockDim.x) zero_pivot |= !(c.Rdiag[a] != 0.0);
-    zero_pivot = __syncthreads_or(zero_pivot);
-    if (warp == 0) {
-        double x[kRv];
+    zero_pivot = __any_sync(0xffffffffu, zero_pivot);
+    __syncwarp();
+    double x[kRv];
 #pragma unroll
-        for (int k = 0; k < kRv; ++k) x[k] = (lane + 32 * k < me) ? c.qacc[lane + 32 * k] : 0.0;
-        if (!zero_pivot) warp_back_subst(c.Aw, c.s, rinv, me, x);
+    for (int k = 0; k < kRv; ++k) x[k] = (lane + 32 * k < me) ? c.qacc[lane + 32 * k] : 0.0;
+    if (!zero_pivot) warp_back_subst(c.Aw, c.s, rinv, me, x);
 #pragma unroll
-        for (int k = 0; k < kRv; ++k) {
-            const int i = lane + 32 * k;
-            if (i < me) c.z[i] = zero_pivot ? 0.0 : c.vscale[i] * x[k];
-        }
-    } else if (warp == 1) {
-        const double r = zero_pivot ? INFINITY : warp_rinv_norm_est(c.Aw, c.s, rinv, me);
-        if (lane == 0) res[0] = r;
-    } else if (warp == 2) {
-        double mx = 0.0;
-        for (int j = 0; j < me; ++j) {
-            double a = (lane == 0) ? c.Rdiag[j] * c.Rdiag[j] : 0.0;
-            for (int i = lane; i < j; i += 32) a = fma(c.Aw[i + (int64_t)j * c.s], c.Aw[i + (int64_t)j * c.s], a);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            mx = fmax(mx, a);
-        }
-        if (lane == 0) res[1] = sqrt(mx);
+    for (int k = 0; k < kRv; ++k) {
+        const int i = lane + 32 * k;
+        if (i < me) c.z[i] = zero_pivot ? 0.0 : c.vscale[i] * x[k];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double mn = INFINITY, mxd = 0.0;
-        for (int a = 0; a < me; ++a) {
-            mn = fmin(mn, fabs(c.Rdiag[a]));
-            mxd = fmax(mxd, fabs(c.Rdiag[a]));
-        }
-        c.qstate[3] = mxd > 0.0 ? mn / mxd : 0.0;
-        // the estimate never reports less than the diagonal ratio, a lower bound of cond(R)
-        const double est = me == 0 ? 0.0 : fmax(res[0] * res[1], mn > 0.0 ? mxd / mn : INFINITY);
-        c.qstate[5] = est;
-        if (me > 0 && c.iscal[2] == SKF_OK && (zero_pivot || (c.cond_max > 0.0 && est > c.cond_max)))
-            c.iscal[2] = SKF_ERR_ILL_CONDITIONED;
-    }
+    if (lane == 0 && me > 0 && c.iscal[2] == SKF_OK &&
+        (zero_pivot || (c.cond_max > 0.0 && c.qstate[5] > c.cond_max)))
+        c.iscal[2] = SKF_ERR_ILL_CONDITIONED;
 }
 
 // x = V z (tall-skinny GEMV over the stored basis).
@@ -1109,6 +1348,10 @@ __global__ void k_write_info(TailCtx c, skf_info *info, const double *stop_state
 // schedule; levels are evaluated in batches (speculatively, several levels per
 // launch) and accepted in schedule order, which gives the same accepted order
 // as evaluating one level at a time.
+static int g_qr_mode = 0;   // 0 automatic (cooperative QR where it fits), 1 per-reflector launches
+void set_qr_mode(int mode) { g_qr_mode = mode; }
+int qr_mode() { return g_qr_mode; }
+
 skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
                     double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out,
@@ -1151,7 +1394,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                             sizeof(double) * m, sizeof(double) * chunk * mm * (rule.cplx ? 4 : 1), sizeof(double) * (size_t)cap * m,
                             sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
                             sizeof(double) * 6, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
-                            sizeof(double) * 2 * (size_t)m};
+                            sizeof(double) * 2 * (size_t)m, sizeof(unsigned) * 4};
     constexpr int kNbuf = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
     for (size_t v : sizes) total += al(v);
@@ -1168,19 +1411,53 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     c.cvec = ptrs[6]; c.Mtc = ptrs[7]; c.Nw = ptrs[8]; c.out = ptrs[9]; c.qbuf = ptrs[10]; c.qacc = ptrs[11];
     c.z = ptrs[12]; c.qstate = ptrs[13]; c.MT = ptrs[14]; c.R2T = ptrs[15]; c.nodebad = (int *)ptrs[16];
     c.hsig = ptrs[17];
+    unsigned *qr_ready = (unsigned *)ptrs[18];   // [0] published pivot columns, [1] timeout flag
 
     const int G = std::min(2 * num_sms(), 1024);
     long long nlaunch = 0;
     k_tail_copy<<<G, kThreads, 0, st>>>(SV, SAV, c);
     ++nlaunch;
     const int nref = (method == SKF_METHOD_SGMRES) ? 2 * m : m;
-    // the 2m (sGMRES) or m (sFOM) reflector launches, each a programmatic
-    // dependent of the one before, so that launch latency overlaps the
-    // previous reflector
+    // the QR in one cooperative launch (k_qr_persist): every column's owner
+    // CTA must be resident, with at most kQrOwn columns per CTA
+    bool qr_done = false;
+    if (qr_mode() != 1) {
+        const int cols = std::max(1, 2 * m);   // every column has an owner CTA holding it
+        int Gq = std::min(cols, num_sms());
+        if ((cols + kQrOwn - 1) / kQrOwn > Gq) Gq = (cols + kQrOwn - 1) / kQrOwn;
+        int dev = 0, per_sm = 0, coop = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+            cudaFuncSetAttribute(k_qr_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)qr_smem_bytes(s)) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_persist, kQrThreads, qr_smem_bytes(s)) ==
+                cudaSuccess &&
+            Gq <= per_sm * num_sms()) {
+            cudaMemsetAsync(qr_ready, 0, sizeof(unsigned) * 4, st);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeCooperative;
+            at[0].val.cooperative = 1;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)Gq);
+            cfg.blockDim = dim3(kQrThreads);
+            cfg.dynamicSmemBytes = qr_smem_bytes(s);
+            cfg.stream = st;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            qr_done = cudaLaunchKernelEx(&cfg, k_qr_persist, c, qr_ready, (int *)(qr_ready + 1)) == cudaSuccess;
+            if (!qr_done) cudaGetLastError();
+            else ++nlaunch;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    // otherwise the 2m (sGMRES) or m (sFOM) reflector launches, each a
+    // programmatic dependent of the one before, so that launch latency
+    // overlaps the previous reflector
     cudaLaunchAttribute pdl[1];
     pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     pdl[0].val.programmaticStreamSerializationAllowed = 1;
-    for (int jj = 0; jj < nref; ++jj) {
+    for (int jj = 0; !qr_done && jj < nref; ++jj) {
         const int ntrail = std::max(1, 2 * m - jj - 1);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)ntrail);
@@ -1191,13 +1468,13 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
         cfg.numAttrs = 1;
         cudaLaunchKernelEx(&cfg, k_householder, c, jj);
     }
-    nlaunch += nref;
+    if (!qr_done) nlaunch += nref;
     {
         const int rows = (method == SKF_METHOD_SGMRES) ? 2 * m : m;
         const int blocks = (rows + (kThreads / 32) - 1) / (kThreads / 32);
-        const size_t smem = sizeof(double) * (kThreads / 32) * m;
+        const size_t smem = sizeof(double) * (2 * (kThreads / 32) + 1) * (size_t)m;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k_tri_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_tri_right<<<blocks, kThreads, smem, st>>>(c);
+        k_tri_right<<<blocks + 1, kThreads, smem, st>>>(c, blocks);   // + 1: the cond(R) estimate
         ++nlaunch;
     }
     k_tail_prep<<<G, kThreads, 0, st>>>(c);
@@ -1234,7 +1511,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                                          bi + 1 == batches.size() ? 1 : 0);
         ++nlaunch;
     }
-    k_coeffs<<<1, kThreads, sizeof(double) * m, st>>>(c);
+    k_coeffs<<<1, 32, sizeof(double) * m, st>>>(c);
     const int64_t rb = std::min<int64_t>((n + kThreads - 1) / kThreads, 16 * num_sms());
     const unsigned rgrid = (unsigned)std::max<int64_t>(rb, 1);
     const size_t zsm = sizeof(float) * 2 * (size_t)m;

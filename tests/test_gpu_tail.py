@@ -79,12 +79,14 @@ def test_tail_above_shared_memory_factor_limit(skf, m, method):
     assert rel(x, xo) <= gate
 
 
-@pytest.mark.parametrize("n,m", [(400, 300), (600, 400)])
+@pytest.mark.parametrize("n,m", [(400, 300), (800, 480)])
 def test_tail_ill_conditioned_nodes_use_fp64_factor(skf, n, m):
     """2D operators with m large enough that the smallest shifts give node
     systems whose normal matrices are beyond the FP32 factor; those nodes are
     solved with the FP64 factor.  m = 300 pairs it with the shared-memory
-    FP32 kernel, m = 400 with the global-slot one.  Fixed 64-node rule."""
+    FP32 kernel, m = 480 with the global-slot one (kappa^2 u_fp32 > 1 for the
+    smallest shifts, so the FP32 factor cannot resolve them).  Fixed 64-node
+    rule."""
     A = convdiff_2d(n, (100.0, 50.0))
     x, xo, inf, ell, kappa = tail_case(skf, A, laplacian_lambda_min(n, 2), m, 4 * m, torch.float32, skf.SGMRES,
                                        ell=64)
