@@ -553,35 +553,76 @@ __global__ void __launch_bounds__(kThreads) k_nodes_mixed(TailCtx c, int n0, int
     for (int i = threadIdx.x; i < me; i += blockDim.x)
         for (int j = 0; j <= i; ++j)
             L[pk(i, j)] = (float)((i == j ? t * t : 0.0) + t * c.B[i + (int64_t)j * m] + c.C[i + (int64_t)j * m]);
-    // right-looking FP32 Cholesky
-    for (int p = 0; p < me; ++p) {
-        __syncthreads();
-        const float d = L[pk(p, p)];
-        if (!(d > 0.f)) {
-            if (threadIdx.x == 0) bad = 1;
-            break;
-        }
-        const float lpp = sqrtf(d);
-        const float rl = 1.f / lpp;
-        for (int i = p + threadIdx.x; i < me; i += blockDim.x) colp[i] = (i == p) ? lpp : L[pk(i, p)] * rl;
-        __syncthreads();
-        for (int i = p + threadIdx.x; i < me; i += blockDim.x) L[pk(i, p)] = colp[i];
-        // trailing update: one warp per row, lanes along the row; rows i and
-        // i + 8 of a warp in the same pass, so their loads overlap
-        {
+    // blocked right-looking FP32 Cholesky, 32-column panels: the diagonal
+    // block by one warp (lane = row, the pivot column passed through shared
+    // memory), the rows below it solved against that block (one row per
+    // thread, in registers), then the rank-32 update of the trailing matrix
+    // by all warps (one warp per row, lanes along the row).  Three block
+    // barriers per panel instead of two per column.
+    {
+        constexpr int kPB = 32;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int k0 = 0; k0 < me; k0 += kPB) {
+            __syncthreads();
+            const int kb = min(kPB, me - k0), k1 = k0 + kb;
+            if (warp == 0) {
+                for (int p = 0; p < kb; ++p) {
+                    const float d = L[pk(k0 + p, k0 + p)];
+                    if (!(d > 0.f)) {
+                        if (lane == 0) bad = 1;
+                        break;
+                    }
+                    const float lpp = sqrtf(d), rl = 1.f / lpp;
+                    const bool below = lane > p && lane < kb;
+                    const float lip = below ? L[pk(k0 + lane, k0 + p)] * rl : 0.f;
+                    if (below) L[pk(k0 + lane, k0 + p)] = lip;
+                    if (lane == p) L[pk(k0 + p, k0 + p)] = lpp;
+                    if (lane < kb) colp[k0 + lane] = lip;
+                    __syncwarp();
+                    if (below)
+                        for (int q = p + 1; q <= lane; ++q) L[pk(k0 + lane, k0 + q)] -= lip * colp[k0 + q];
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            if (bad) break;
+            // rows below the block: x D^T = row, D the factored diagonal block
+            for (int i = k1 + threadIdx.x; i < me; i += blockDim.x) {
+                float r[kPB];
+                float *Li = L + pk(i, k0);
+#pragma unroll
+                for (int p = 0; p < kPB; ++p) r[p] = p < kb ? Li[p] : 0.f;
+#pragma unroll
+                for (int p = 0; p < kPB; ++p) {
+                    if (p < kb) {
+                        float v = r[p];
+                        const float *Dp = L + pk(k0 + p, k0);
+#pragma unroll
+                        for (int q = 0; q < kPB; ++q)
+                            if (q < p) v = fmaf(-r[q], Dp[q], v);
+                        r[p] = v / Dp[p];
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < kPB; ++p)
+                    if (p < kb) Li[p] = r[p];
+            }
+            __syncthreads();
+            // trailing update: L[i][q] -= sum_p L[i][k0+p] L[q][k0+p], k1 <= q <= i
             constexpr int kW = kThreads / 32;
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            for (int i = p + 1 + warp; i < me; i += 2 * kW) {
-                const int i2 = i + kW;
-                const bool two = i2 < me;
-                const float li = colp[i], li2 = two ? colp[i2] : 0.f;
-                float *Li = L + pk(i, 0);
-                float *Li2 = L + pk(two ? i2 : i, 0);
-                const int qe = two ? i2 : i;
-                for (int q = p + 1 + lane; q <= qe; q += 32) {
-                    const float cq = colp[q];
-                    if (q <= i) Li[q] = fmaf(-li, cq, Li[q]);
-                    if (two) Li2[q] = fmaf(-li2, cq, Li2[q]);
+            for (int i = k1 + warp; i < me; i += kW) {
+                const float *Li = L + pk(i, k0);
+                float ri[kPB];
+#pragma unroll
+                for (int p = 0; p < kPB; ++p) ri[p] = p < kb ? Li[p] : 0.f;
+                float *Lrow = L + pk(i, 0);
+                for (int q = k1 + lane; q <= i; q += 32) {
+                    const float *Lq = L + pk(q, k0);
+                    float acc = 0.f;
+#pragma unroll
+                    for (int p = 0; p < kPB; ++p)
+                        if (p < kb) acc = fmaf(ri[p], Lq[p], acc);
+                    Lrow[q] -= acc;
                 }
             }
         }

@@ -6,6 +6,8 @@ same basis and sketches the GPU Arnoldi process produced.  Fixing the basis
 isolates the tail: the node solves (FP32 Cholesky factor with FP64 iterative
 refinement, FP64 factor where that does not converge) must agree with the
 oracle's dense least-squares solutions to 1e-10."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -79,19 +81,55 @@ def test_tail_above_shared_memory_factor_limit(skf, m, method):
     assert rel(x, xo) <= gate
 
 
-@pytest.mark.parametrize("n,m", [(400, 300), (800, 480)])
+@pytest.mark.parametrize("n,m", [(1400, 320), (1400, 480)])
 def test_tail_ill_conditioned_nodes_use_fp64_factor(skf, n, m):
-    """2D operators with m large enough that the smallest shifts give node
-    systems whose normal matrices are beyond the FP32 factor; those nodes are
-    solved with the FP64 factor.  m = 300 pairs it with the shared-memory
-    FP32 kernel, m = 480 with the global-slot one (kappa^2 u_fp32 > 1 for the
-    smallest shifts, so the FP32 factor cannot resolve them).  Fixed 64-node
-    rule."""
+    """Node systems beyond the FP32 factor are solved with the FP64 factor.
+    The fixed 64-node rule is extended by one shift t* chosen on the GPU's
+    own basis (with the oracle's whitening) so that the node system has
+    kappa ~ 5000: kappa^2 u_fp32 ~ 1.5 (the FP32 factor with FP64 refinement
+    cannot resolve it) while kappa^2 u_fp64 ~ 3e-9 keeps the comparison with
+    the oracle meaningful.  The 2D operator with n = 1400 makes such shifts
+    exist (cond(Z) = 4.6e3 at n = 1000, m = 320 on the FP32 basis, growing
+    with n).  m = 320 pairs the fallback
+    with the shared-memory FP32 kernel, m = 480 with the global-slot one."""
+    from oracle import quadrature as oq
     A = convdiff_2d(n, (100.0, 50.0))
-    x, xo, inf, ell, kappa = tail_case(skf, A, laplacian_lambda_min(n, 2), m, 4 * m, torch.float32, skf.SGMRES,
-                                       ell=64)
+    s = 4 * m
+    vals = A.values.astype(np.float32)
+    op = skf.upload_csr(A.rowptr, A.colind, vals, device="cuda")
+    b = torch.as_tensor(gaussian_rhs(A.n, 7), device="cuda")
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, s, 8, 13)
+    c = quad_scale("invsqrt", laplacian_lambda_min(n, 2), float(abs(csr_to_scipy(A)).sum(1).max()))
+    V, vsc, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, b, m, 2, basis_dtype=torch.float32)
+    torch.cuda.synchronize()
+    SVn, SAVn, vs = SV.cpu().numpy().T, SAV.cpu().numpy().T, vsc.cpu().numpy()
+    W = osk.whiten(SVn, SAVn, SVn[:, 0] / vs[0])
+    kappa_of = lambda t: float(np.linalg.cond(t * W["Q"] + W["Z"]))
+    print(f"n {n} m {m}: cond(Z) {kappa_of(0.0):.3e}")
+    assert kappa_of(0.0) > 5000.0
+    lo, hi = 1e-12 * c, 1e3 * c          # kappa decreases as the shift grows
+    for _ in range(60):
+        mid = math.sqrt(lo * hi)
+        lo, hi = (mid, hi) if kappa_of(mid) > 5000.0 else (lo, mid)
+    t_star = math.sqrt(lo * hi)
+    kappa = kappa_of(t_star)
+    t_, w_ = oq.rule("invsqrt", 64, c)
+    t_ = np.append(t_, t_star)
+    w_ = np.append(w_, w_.max())
+    f = skf.make_func("invsqrt", c, nodes=t_, weights=w_)
+    p = skf.make_params(m, 2, basis_dtype=torch.float32, tol=1e-10)
+    info = skf.new_info()
+    x = skf.solve(skf.SGMRES, op.csr, S, b, f, p, info=info)
+    torch.cuda.synchronize()
+    inf = skf.read_info(info)
+    q = sum(wi * np.linalg.lstsq(ti * W["Q"] + W["Z"], W["Sb"], rcond=None)[0] for ti, wi in zip(t_, w_))
+    import scipy.linalg as sla
+    y = sla.solve_triangular(W["R"], q, lower=False)
+    xo = (V.double().cpu().numpy() * vs[:, None]).T @ y
+    err = rel(x.cpu().numpy(), xo)
+    print(f"n {n} m {m}: t* {t_star:.3e}, kappa {kappa:.3e}, kappa^2 u {kappa ** 2 * 2.0 ** -52:.2e}, "
+          f"nodes_fp64 {inf['nodes_fp64']}, err {err:.2e}")
     assert inf["status"] == 0 and inf["m_eff"] == m
-    assert 1 <= inf["nodes_fp64"] < 32
-    print(f"n {n} m {m}: kappa {kappa:.3e}, kappa^2 u {kappa ** 2 * 2.0 ** -52:.2e}, err {rel(x, xo):.2e}")
+    assert 1 <= inf["nodes_fp64"] <= 32     # the small shifts of the rule and t*; most nodes stay FP32
     assert kappa ** 2 * 2.0 ** -52 <= 1e-8
-    assert rel(x, xo) <= max(1e-10, kappa ** 2 * 2.0 ** -52)
+    assert err <= max(1e-10, kappa ** 2 * 2.0 ** -52)
