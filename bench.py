@@ -39,7 +39,11 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # basis dtype and sketch, and removed whenever those kernels change.
 # ncu dram bytes per Arnoldi step, for step kernels unchanged since their capture;
 # the FP32 kernels changed after theirs (1516.3 MB per step), so their entry is null
-NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64", "sparse_sign"): 139.8e6, ("cd3d_n256_fp32", "f32", "sparse_sign"): None}
+# k_arnoldi_persist is one launch for all m steps: per-step bytes are the
+# difference of two captures (m = 40 and m = 12) over 28 steps
+NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64", "sparse_sign", True): 91.7e6,
+                        ("cd3d_n100", "f64", "sparse_sign", False): None,
+                        ("cd3d_n256_fp32", "f32", "sparse_sign", False): None}
 
 
 BASIS_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
@@ -213,32 +217,60 @@ def cpu_baseline_sample(name: str, budget_s: float = 20.0, sketch: str = "sparse
             "seconds": round(t_arn + t_tail, 2)}
 
 
+def oracle_pair(name: str, sketch: str = "sparse_sign", m: int | None = None):
+    """One sFOM + sGMRES pair of the workload by the oracle as it stands, on the
+    full operator: one truncated Arnoldi process (the basis both methods
+    use), both tails (adaptive quadrature, tol 1e-10) and both
+    recombinations; m < wl.m gives a bounded prefix (the warm-up)."""
+    import numpy as np
+    from oracle import sketched as osk
+    from oracle.arnoldi import arnoldi_trunc
+    from oracle.sketch import Sketch
+    from workloads import csr_to_scipy
+    from workloads.configs import quad_scale
+    wl, A, b = build_inputs(name)
+    As = csr_to_scipy(A.astype(np.float64))
+    S = Sketch(sketch, A.n, wl.s, wl.zeta, 13)
+    c = quad_scale(wl.func, wl.lam_lo or 0.0, float(abs(As).sum(1).max()))
+    mm = m or wl.m
+    ell = wl.extra.get("ell")
+    t0 = time.perf_counter()
+    ar = arnoldi_trunc(As, b, mm, wl.k, S)
+    W = osk.whiten(ar["SV"], ar["SAV"], S @ b)
+    yg, _ = osk.sgmres_quadrature(W, wl.func, c, ell=ell, tol=1e-10)
+    yf, _ = osk.sfom_quadrature(W, wl.func, c, ell=ell, tol=1e-10)
+    xg, xf = ar["V"] @ yg, ar["V"] @ yf
+    return time.perf_counter() - t0, wl, A
+
+
 def run_reference(args, rank: int):
-    """The oracle as it stands on the host cores; each step is one bounded
-    sample of the workload (see cpu_baseline_sample).  Rank 0 only."""
+    """The oracle as it stands on the host cores, rank 0 only.  Each timed
+    step is one whole pair of the workload (nothing extrapolated): one
+    Arnoldi process shared by the two methods, both tails, both
+    recombinations.  Warm-up steps run a short prefix (untimed)."""
     if rank != 0:
         return
-    wl, A, _ = build_inputs(args.workload)
     for _ in range(args.warmup):
-        cpu_baseline_sample(args.workload, budget_s=1.0, sketch=args.sketch)
-    budget = min(args.ref_budget, 150.0 / max(1, args.steps))
-    vals = []
-    t0 = time.perf_counter()
+        oracle_pair(args.workload, args.sketch, m=4)
+    times = []
     for _ in range(args.steps):
-        cb = cpu_baseline_sample(args.workload, budget_s=budget, sketch=args.sketch)
-        vals.append(cb["value"])
-    wall = time.perf_counter() - t0
-    value = statistics.mean(vals)
+        dt, wl, A = oracle_pair(args.workload, args.sketch)
+        times.append(dt)
+    total = sum(times)
+    value = 2.0 * args.steps / total
+    cores = len(os.sched_getaffinity(0))
+    sample = (f"whole sFOM + sGMRES pairs on the full workload (N = {A.n}, m = {wl.m}): one truncated Arnoldi "
+              f"process shared by both methods, both tails, both recombinations; BLAS threads "
+              f"{os.environ.get('OMP_NUM_THREADS', 'default')}, SciPy CSR matvec single-threaded")
     line = {"metric": "f(A)b solves/s (sFOM + sGMRES, FP64)", "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 2000.0 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "ms_per_step": total * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "N": int(A.n), "nnz": int(A.nnz), "m": wl.m, "k": wl.k,
                        "s": wl.s, "zeta": wl.zeta, "sketch": args.sketch, "f": wl.func},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
-                             "sample": cb["sample"]},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": round(wall, 1)}
+            "timed_s": round(total, 1)}
     print(json.dumps(line), flush=True)
 
 
@@ -356,22 +388,23 @@ def run_reference_batch(args, rank: int):
         flush=True)
 
 
-def run_batch(args, rank, world, local, dev):
-    """Batched workload.  Arms, all through the public API on the same
+def batch_arms(dev, steps: int, warmup: int, lanes_arg, world: int = 1, n_rhs: int = 64, with_e2e: bool = False,
+               clocks=None):
+    """The batched workload's arms, all through the public API on the same
     operators, sketches, right-hand sides and rules:
       * FP64 basis, one problem at a time (skf_sgmres per problem);
       * FP64 basis as one batch (skf_solve_batched captured into one CUDA
-        graph, replayed once per step): the headline, since its results are
-        bit-identical to the one-at-a-time path (error 0 <= 1e-6);
-      * FP32 basis as one batch: faster, and its error against the FP64
-        results is reported per problem (the 1e-6 gate holds for part of the
-        batch only), with how well the solve's own flag (nodes needing the
-        FP64 factor) predicts a miss."""
+        graph, replayed once per step): bit-identical to the one-at-a-time
+        results (error 0 <= 1e-6);
+      * FP32 basis as one batch: its error against the FP64 results per
+        problem, and how well the solve's own flag (nodes needing the FP64
+        factor) predicts a miss of 1e-6.
+    Returns the timings (ms, summed over steps) and per-problem errors."""
     import numpy as np
     import torch
     import paper_2208_11447_gb300 as skf
 
-    layout, ops, rhs = batch_inputs(args.batch_rhs)
+    layout, ops, rhs = batch_inputs(n_rhs)
     nprob = len(layout.rhs)
     op32, op64 = [], []
     for A, c in ops:
@@ -403,9 +436,9 @@ def run_batch(args, rank, world, local, dev):
         for r, q in enumerate(layout.rhs):
             skf.sgmres(op64[q.mat].csr, sketches[r], b_dev[r], funcs[r], p64[r], x=x64[r], info=inf64[r])
 
-    def timed(fn, steps):
+    def timed(fn, k):
         tot = 0.0
-        for _ in range(steps):
+        for _ in range(k):
             flush.zero_()
             ev0.record(stream)
             fn()
@@ -417,108 +450,141 @@ def run_batch(args, rank, world, local, dev):
     def statuses(buf):
         return sorted({skf.read_info(buf[r])["status_name"] for r in range(nprob)})
 
+    out = {"layout": layout, "ops": ops, "rhs": rhs, "nprob": nprob}
     # plain FP64 path, one problem at a time
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         fp64_one_at_a_time()
     torch.cuda.synchronize()
     replica_barrier(world)
-    t64 = replica_max(timed(fp64_one_at_a_time, args.steps), world, dev)
-
-    # FP64 batch as one CUDA graph: the headline
+    out["t64"] = replica_max(timed(fp64_one_at_a_time, steps), world, dev)
+    out["status64"] = statuses(inf64)
+    # FP64 batch as one CUDA graph
     lane_times = None
-    if args.lanes == "auto":
+    if lanes_arg == "auto":
         graph64, lane_times = skf.BatchGraph.autotune(probs64)
         lanes = graph64.lanes
+        del graph64
     else:
-        lanes = int(args.lanes)
+        lanes = int(lanes_arg)
     l0 = skf.kernel_launch_count()
     graph64 = skf.BatchGraph(probs64, lanes=lanes)          # one eager run + capture
-    launches_per_batch = (skf.kernel_launch_count() - l0) // 2
-    for _ in range(args.warmup):
+    out["launches_per_batch"] = (skf.kernel_launch_count() - l0) // 2
+    for _ in range(warmup):
         graph64.replay()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
+    if clocks is not None:
+        clocks.start()
     replica_barrier(world)
     torch.cuda.synchronize()
-    t64b = replica_max(timed(graph64.replay, args.steps), world, dev)
+    out["t64b"] = replica_max(timed(graph64.replay, steps), world, dev)
     replica_barrier(world)
-    clk = clocks.stop()
-    equal64 = all(bool(torch.equal(a, b)) for a, b in zip(x64b, x64))
-    errs64b = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(x64b, x64)]
-
-    # end to end: right-hand sides from pinned host memory, results back
-    b_host = [torch.as_tensor(b).pin_memory() for b in rhs]
-    x_host = [torch.empty(b.numel(), dtype=torch.float64).pin_memory() for b in b_dev]
-    e2e_ms = 0.0
-    replica_barrier(world)
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for bd, bh in zip(b_dev, b_host):
-            bd.copy_(bh, non_blocking=True)
-        graph64.replay()
-        for xh, xd in zip(x_host, x64b):
-            xh.copy_(xd, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_ms += (time.perf_counter() - t0) * 1e3
-    e2e_ms = replica_max(e2e_ms, world, dev)
+    if clocks is not None:
+        out["clk"] = clocks.stop()
+    out["equal64"] = all(bool(torch.equal(a, b)) for a, b in zip(x64b, x64))
+    out["errs64b"] = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(x64b, x64)]
+    out["status64b"] = statuses(inf64b)
+    out["lanes"], out["lane_times"] = lanes, lane_times
+    if with_e2e:
+        # right-hand sides from pinned host memory, results back
+        b_host = [torch.as_tensor(b).pin_memory() for b in rhs]
+        x_host = [torch.empty(b.numel(), dtype=torch.float64).pin_memory() for b in b_dev]
+        e2e_ms = 0.0
+        replica_barrier(world)
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for bd, bh in zip(b_dev, b_host):
+                bd.copy_(bh, non_blocking=True)
+            graph64.replay()
+            for xh, xd in zip(x_host, x64b):
+                xh.copy_(xd, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+        out["e2e_ms"] = replica_max(e2e_ms, world, dev)
     del graph64
-
     # FP32-basis batch as one CUDA graph
     graph32 = skf.BatchGraph(probs32, lanes=lanes)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph32.replay()
     torch.cuda.synchronize()
     replica_barrier(world)
-    t32 = replica_max(timed(graph32.replay, args.steps), world, dev)
-    errs = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(x32, x64)]
-    flags = [skf.read_info(inf32[r])["nodes_fp64"] > 0 for r in range(nprob)]
-    tol = BATCH_TOL
+    out["t32"] = replica_max(timed(graph32.replay, steps), world, dev)
+    del graph32
+    out["errs32"] = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(x32, x64)]
+    out["flags32"] = [skf.read_info(inf32[r])["nodes_fp64"] > 0 for r in range(nprob)]
+    out["status32"] = statuses(inf32)
+    return out
 
-    value = replica_value(world, nprob * args.steps, t64b)
-    v64 = replica_value(world, nprob * args.steps, t64)
-    v32 = replica_value(world, nprob * args.steps, t32)
-    e2e_value = replica_value(world, nprob * args.steps, e2e_ms)
+
+def batch_summary(o, steps: int, world: int = 1):
+    """The three arms as JSON-ready numbers (solves/s, errors against the FP64
+    one-at-a-time results, counts within the 1e-6 gate)."""
+    nprob, tol = o["nprob"], BATCH_TOL
+    v64b = replica_value(world, nprob * steps, o["t64b"])
+    v64 = replica_value(world, nprob * steps, o["t64"])
+    v32 = replica_value(world, nprob * steps, o["t32"])
+    errs, flags = o["errs32"], o["flags32"]
+    return {
+        "fp64_one_at_a_time": {"value": round(v64, 3), "unit": "solves/s",
+                               "ms_per_batch": round(o["t64"] / steps, 3), "status": o["status64"]},
+        "fp64_batched": {"value": round(v64b, 3), "unit": "solves/s", "ms_per_batch": round(o["t64b"] / steps, 3),
+                         "speedup_vs_fp64_one_at_a_time": round(v64b / v64, 3),
+                         "max_rel_err": max(o["errs64b"]), "bitwise_equal": o["equal64"],
+                         "within_1e-6": sum(1 for e in o["errs64b"] if e <= tol), "of": nprob,
+                         "status": o["status64b"], "lanes": o["lanes"]},
+        "fp32_batched": {"value": round(v32, 3), "unit": "solves/s", "ms_per_batch": round(o["t32"] / steps, 3),
+                         "speedup_vs_fp64_one_at_a_time": round(v32 / v64, 3),
+                         "max_rel_err": max(errs), "median_rel_err": statistics.median(errs),
+                         "within_1e-6": sum(1 for e in errs if e <= tol), "of": nprob, "status": o["status32"],
+                         "flag_nodes_fp64": {
+                             "flagged_err_gt_tol": sum(1 for f, e in zip(flags, errs) if f and e > tol),
+                             "flagged_err_le_tol": sum(1 for f, e in zip(flags, errs) if f and e <= tol),
+                             "unflagged_err_gt_tol": sum(1 for f, e in zip(flags, errs) if not f and e > tol),
+                             "unflagged_err_le_tol": sum(1 for f, e in zip(flags, errs) if not f and e <= tol)}},
+        "errors_vs": "FP64 one-at-a-time GPU path, same problems; gate 1e-6",
+    }
+
+
+def run_batch(args, rank, world, local, dev):
+    """Batched workload (bench.py --mode batch): the FP64 batch is the
+    headline (the fastest arm that meets 1e-6 on every problem)."""
+    clocks = ClockSampler(local)
+    o = batch_arms(dev, args.steps, args.warmup, args.lanes, world, args.batch_rhs, with_e2e=True, clocks=clocks)
+    layout, ops, rhs, nprob = o["layout"], o["ops"], o["rhs"], o["nprob"]
+    summ = batch_summary(o, args.steps, world)
+    value = replica_value(world, nprob * args.steps, o["t64b"])
+    e2e_value = replica_value(world, nprob * args.steps, o["e2e_ms"])
     # whole-batch effective bandwidth over the algorithmic Arnoldi bytes (FP64)
     alg = 0
     for q in layout.rhs:
         A = ops[q.mat][0]
         alg += q.m * (A.nnz * 12 + 4 * (A.n + 1) + 3 * A.n * 8)
     hbm_peak, hbm_src = measured_peaks()
-    gbs = alg / (t64b / args.steps * 1e-3) / 1e9
+    gbs = alg / (o["t64b"] / args.steps * 1e-3) / 1e9
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_batch_sample(layout, ops, rhs, budget_s=args.ref_budget)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    clk = o["clk"]
     if rank == 0:
         nbytes_b = int(sum(b.nbytes for b in rhs))
         print(json.dumps({
             "metric": "f(A)b solves/s at rel err <= 1e-6 (batched sGMRES)",
             "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(t64b / args.steps, 3), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": round(o["t64b"] / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batch_cd_8x64", **layout.summary(), "k": 2, "s": "4 m_r", "zeta": 8,
                        "f": BATCH_FUNC, "method": "sgmres", "quad_tol": 1e-10, "basis": "f64", "values": "f32-rounded",
-                       "lanes": lanes, "lane_autotune_ms": lane_times, "graph": "one CUDA graph per batch",
+                       "lanes": o["lanes"], "lane_autotune_ms": o["lane_times"], "graph": "one CUDA graph per batch",
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
-            "accuracy": {"vs": "FP64 one-at-a-time GPU path, same problems", "max_rel_err": max(errs64b),
-                         "bitwise_equal": equal64, "within_1e-6": sum(1 for e in errs64b if e <= tol), "of": nprob,
-                         "status": statuses(inf64b)},
-            "fp64_one_at_a_time": {"value": round(v64, 3), "unit": "solves/s",
-                                   "ms_per_batch": round(t64 / args.steps, 3), "status": statuses(inf64)},
-            "speedup_vs_fp64_one_at_a_time": round(value / v64, 3),
-            "fp32_batched": {"value": round(v32, 3), "unit": "solves/s", "ms_per_batch": round(t32 / args.steps, 3),
-                             "speedup_vs_fp64_one_at_a_time": round(v32 / v64, 3),
-                             "max_rel_err": max(errs), "median_rel_err": statistics.median(errs),
-                             "within_1e-6": sum(1 for e in errs if e <= tol), "of": nprob,
-                             "status": statuses(inf32),
-                             "flag_nodes_fp64": {
-                                 "flagged_err_gt_tol": sum(1 for f, e in zip(flags, errs) if f and e > tol),
-                                 "flagged_err_le_tol": sum(1 for f, e in zip(flags, errs) if f and e <= tol),
-                                 "unflagged_err_gt_tol": sum(1 for f, e in zip(flags, errs) if not f and e > tol),
-                                 "unflagged_err_le_tol": sum(1 for f, e in zip(flags, errs) if not f and e <= tol)}},
+            "accuracy": {"vs": "FP64 one-at-a-time GPU path, same problems",
+                         "max_rel_err": summ["fp64_batched"]["max_rel_err"],
+                         "bitwise_equal": o["equal64"], "within_1e-6": summ["fp64_batched"]["within_1e-6"],
+                         "of": nprob, "status": o["status64b"]},
+            "fp64_one_at_a_time": summ["fp64_one_at_a_time"],
+            "speedup_vs_fp64_one_at_a_time": summ["fp64_batched"]["speedup_vs_fp64_one_at_a_time"],
+            "fp32_batched": summ["fp32_batched"],
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src,
                          "kernel": "whole FP64 batch: algorithmic Arnoldi bytes (sum_r m_r (B_A + 3 N 8)) over the "
@@ -526,9 +592,66 @@ def run_batch(args, rank, world, local, dev):
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": nbytes_b,
                     "d2h_bytes_per_step": nbytes_b},
-            "gpu_launches": int(launches_per_batch * args.steps),
+            "gpu_launches": int(o["launches_per_batch"] * args.steps),
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
         }), flush=True)
+
+
+def precision_extras(dev, reps: int = 3):
+    """The reduced-precision workload (3D n = 256, N = 16.8M, m = 120,
+    z^-1/2): per basis type (FP32, BF16) the truncated-Arnoldi step time
+    (CUDA events around skf_arnoldi_trunc, median of reps, L2 flushed), its
+    fraction of the measured HBM copy rate for the algorithmic bytes, and the
+    relative error of both solves against the FP64 GPU path on the same
+    operator (values widened exactly), sketch and rule."""
+    import numpy as np
+    import torch
+    import paper_2208_11447_gb300 as skf
+    from workloads.configs import quad_scale
+    wl, A, b = build_inputs("cd3d_n256_fp32")
+    A32 = A.astype(np.float32)
+    op32 = skf.upload_csr(A32.rowptr, A32.colind, A32.values, device=dev)
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, wl.s, wl.zeta, 13)
+    c = quad_scale(wl.func, wl.lam_lo or 0.0, op32.csr.norm_inf())
+    f = skf.make_func(wl.func, c)
+    b_dev = torch.as_tensor(b, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hbm_peak, hbm_src = measured_peaks()
+    res = {"workload": "cd3d_n256 (N = 16,777,216, nnz = 117,047,296, m = 120, k = 2, s = 480, zeta = 8, z^-1/2)"}
+    xs = {}
+    for name, bdt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        ts = []
+        for r in range(reps + 1):
+            flush.zero_()
+            ev0.record(stream)
+            skf.arnoldi_trunc(op32.csr, S, b_dev, wl.m, wl.k, basis_dtype=bdt)
+            ev1.record(stream)
+            ev1.synchronize()
+            if r > 0:
+                ts.append(ev0.elapsed_time(ev1))
+        us = statistics.median(ts) * 1e3 / wl.m
+        alg = A.nnz * 8 + 4 * (A.n + 1) + (wl.k + 1) * A.n * BASIS_BYTES[name]
+        p = skf.make_params(wl.m, wl.k, basis_dtype=bdt, tol=1e-10)
+        xs[name] = (skf.sfom(op32.csr, S, b_dev, f, p), skf.sgmres(op32.csr, S, b_dev, f, p))
+        res[name] = {"us_per_step": round(us, 2), "alg_bytes_per_step": int(alg),
+                     "hbm_frac": round(alg / (us * 1e-6) / 1e9 / hbm_peak, 4), "of": hbm_src}
+    torch.cuda.synchronize()
+    del op32
+    op64 = skf.upload_csr(A.rowptr, A.colind, A.values.astype(np.float64), device=dev)
+    p64 = skf.make_params(wl.m, wl.k, tol=1e-10)
+    r_f = skf.sfom(op64.csr, S, b_dev, f, p64)
+    r_g = skf.sgmres(op64.csr, S, b_dev, f, p64)
+    torch.cuda.synchronize()
+    for name in ("f32", "bf16"):
+        xf, xg = xs[name]
+        res[name]["rel_err_vs_fp64_gpu"] = {
+            "sfom": float(torch.linalg.vector_norm(xf - r_f) / torch.linalg.vector_norm(r_f)),
+            "sgmres": float(torch.linalg.vector_norm(xg - r_g) / torch.linalg.vector_norm(r_g))}
+    del op64, xs, r_f, r_g
+    torch.cuda.empty_cache()
+    return res
 
 
 def main():
@@ -543,6 +666,8 @@ def main():
     ap.add_argument("--arnoldi-reps", type=int, default=5)
     ap.add_argument("--arnoldi-form", default="auto", choices=["auto", "persistent", "two_kernel"],
                     help="form of the FP64 Arnoldi process (skf_set_arnoldi_mode)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra keys of the default line (reduced-precision workload, batch arms)")
     ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi", "batch"],
                     help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu; "
                          "batch: the batched workload (8 operators, 64 right-hand sides) as one CUDA graph")
@@ -692,8 +817,12 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src}
-    roof["traffic"] = NCU_TRAFFIC_PER_STEP.get((args.workload, basis, args.sketch))
-    kname = "k_arnoldi_spmv_pipe + k_arnoldi_update" if basis == "f64" else "k_arnoldi_spmv_lp + k_arnoldi_update_lp"
+    persistent = basis == "f64" and args.sketch == "sparse_sign" and args.arnoldi_form != "two_kernel" and wl.k <= 4
+    roof["traffic"] = NCU_TRAFFIC_PER_STEP.get((args.workload, basis, args.sketch, persistent))
+    if persistent:
+        kname = "k_arnoldi_persist: all m steps in one cooperative launch"
+    else:
+        kname = "k_arnoldi_spmv_pipe + k_arnoldi_update" if basis == "f64" else "k_arnoldi_spmv_lp + k_arnoldi_update_lp"
     if args.sketch == "srht":
         kname += " + k_srht_blocks"
     roof.update({"kernel": f"truncated-Arnoldi step ({kname})", "us_per_step": round(step_us, 2),
@@ -727,6 +856,22 @@ def main():
         cb = cpu_baseline_sample(args.workload, budget_s=args.ref_budget, sketch=args.sketch)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
+    # extra keys (single GPU, outside the timed region): the reduced-precision
+    # workload's step and accuracy, and the three arms of the batched workload
+    extras = None
+    if world == 1 and not args.no_extras and args.workload == "cd3d_n100" and basis == "f64":
+        del V, SV, SAV, H
+        torch.cuda.empty_cache()
+        t_ex = time.perf_counter()
+        extras = {"precision": precision_extras(dev)}
+        bo = batch_arms(dev, 1, 1, "16")
+        extras["batch"] = {"workload": "batch_cd_8x64 (8 operators, 64 right-hand sides, m_r in [50, 400], "
+                                       "sGMRES z^-1/2; one replay per arm after one warm-up)",
+                           **batch_summary(bo, 1)}
+        del bo
+        torch.cuda.empty_cache()
+        extras["seconds"] = round(time.perf_counter() - t_ex, 1)
+
     if rank == 0:
         line = {
             "metric": METRIC[basis], "value": round(value, 3), "unit": "solves/s",
@@ -752,6 +897,8 @@ def main():
             "gpu_launches": int(launches),
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
         }
+        if extras is not None:
+            line["extras"] = extras
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
