@@ -192,11 +192,15 @@ size_t qr_smem_bytes(int s) {
 __global__ void __launch_bounds__(kQrThreads) k_qr_persist(TailCtx c, unsigned *ready, int *flag) {
     extern __shared__ double qsm[];
     __shared__ int ok;
+    __shared__ double qsc[2];                     // tau, scale of the current reflector
+    __shared__ double qf[kQrOwn], qfs[kQrOwn];    // f and f scale of the columns being updated
     const int me = c.iscal[1];
     const int ncols = 2 * me;
     const int s = c.s;
     const int nref = min((c.method == SKF_METHOD_SGMRES) ? 2 * me : me, s);
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31;
+    const bool warp0 = tid < 32;
     double *cols = qsm;                                   // [kQrOwn][s]: columns g, g + G, ...
     double *xs = cols + (size_t)kQrOwn * s;               // [s] pivot column
     double *sm = xs + s;                                  // reduction scratch
@@ -253,42 +257,50 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_persist(TailCtx c, unsigned *
                 if (k < n1) loc[1 + k] = fma(xi, cols[(size_t)(kf + k) * s + i], loc[1 + k]);
         }
         qr_block_sums(loc, 1 + (kf < nq ? n1 : 0), sm, tot);
-        // reflector from one rsqrt and one reciprocal (an FP64 square root or
-        // division is ~650 dependent cycles on this part): with
+        // The reflector (from one rsqrt and one reciprocal: with
         // r = (x0^2 + sig)^-1/2, ||x|| = (x0^2 + sig) r, beta = -sign(x0) ||x||,
-        // tau = (beta - x0) / beta = 1 + |x0| r, 1 / (x0 - beta) = sign(x0) / (|x0| + ||x||)
-        const double sig = tot[0];
-        double tau = 0.0, beta = x0, scale = 0.0;
-        if (sig > 0.0 || x0 == 0.0) {
-            const double q2 = fma(x0, x0, sig);
-            if (q2 > 0.0) {
-                const double r = rsqrt(q2);
-                const double nx = q2 * r;
-                const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
-                beta = -sgn * nx;
-                tau = fma(fabs(x0), r, 1.0);
-                scale = sgn / (fabs(x0) + nx);
+        // tau = (beta - x0) / beta = 1 + |x0| r, 1 / (x0 - beta) =
+        // sign(x0) / (|x0| + ||x||)) and the factors f = tau (y(jj) + scale x^T y)
+        // of the columns, by warp 0 only: a warp instruction occupies the FP64
+        // pipe for 16 cycles whatever its active lanes, so scalar FP64 work
+        // repeated by every warp costs eight times the pipe time.
+        if (warp0) {
+            const double sig = tot[0];
+            double tau = 0.0, beta = x0, scale = 0.0;
+            if (sig > 0.0 || x0 == 0.0) {
+                const double q2 = fma(x0, x0, sig);
+                if (q2 > 0.0) {
+                    const double r = rsqrt(q2);
+                    const double nx = q2 * r;
+                    const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
+                    beta = -sgn * nx;
+                    tau = fma(fabs(x0), r, 1.0);
+                    scale = sgn / (fabs(x0) + nx);
+                }
+            }
+            if (lane == 0) {
+                qsc[0] = tau;
+                qsc[1] = scale;
+                if (writer) c.Rdiag[jj] = beta;
+            }
+            if (lane < n1 && kf < nq) {
+                const double f = tau * (cols[(size_t)(kf + lane) * s + jj] + scale * tot[1 + lane]);
+                qf[lane] = f;
+                qfs[lane] = f * scale;
             }
         }
-        if (writer && tid == 0) c.Rdiag[jj] = beta;
-        if (kf >= nq) {
-            __syncthreads();
-            continue;
-        }
-        // y(jj) -= f, y(i) -= f scale x_i, f = tau (y(jj) + scale x^T y); every
-        // thread forms f from y(jj) before thread 0 changes it
-        double f1[kQrOwn];
-#pragma unroll
-        for (int k = 0; k < kQrOwn; ++k) f1[k] = k < n1 ? tau * (cols[(size_t)(kf + k) * s + jj] + scale * tot[1 + k]) : 0.0;
         __syncthreads();
+        if (kf >= nq) continue;
+        const double tau = qsc[0];
+        // y(jj) -= f, y(i) -= f scale x_i
         if (tau != 0.0) {
 #pragma unroll
             for (int k = 0; k < kQrOwn; ++k) {
                 if (k < n1) {
                     double *y = cols + (size_t)(kf + k) * s;
-                    const double fs = f1[k] * scale;
+                    const double fs = qfs[k];
                     for (int i = jj + 1 + tid; i < s; i += kQrThreads) y[i] = fma(-fs, xs[i], y[i]);
-                    if (tid == 0) y[jj] -= f1[k];
+                    if (tid == 0) y[jj] -= qf[k];
                 }
             }
         }
@@ -314,19 +326,20 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_persist(TailCtx c, unsigned *
                         if (k < n2) loc[k] = fma(xi, cols[(size_t)(kf + 1 + k) * s + i], loc[k]);
                 }
                 qr_block_sums(loc, n2, sm, tot);
-                double f2[kQrOwn];
-#pragma unroll
-                for (int k = 0; k < kQrOwn; ++k)
-                    f2[k] = k < n2 ? tau * (cols[(size_t)(kf + 1 + k) * s + jj] + scale * tot[k]) : 0.0;
+                if (warp0 && lane < n2) {
+                    const double f = tau * (cols[(size_t)(kf + 1 + lane) * s + jj] + qsc[1] * tot[lane]);
+                    qf[lane] = f;
+                    qfs[lane] = f * qsc[1];
+                }
                 __syncthreads();
                 if (tau != 0.0) {
 #pragma unroll
                     for (int k = 0; k < kQrOwn; ++k) {
                         if (k < n2) {
                             double *y = cols + (size_t)(kf + 1 + k) * s;
-                            const double fs = f2[k] * scale;
+                            const double fs = qfs[k];
                             for (int i = jj + 1 + tid; i < s; i += kQrThreads) y[i] = fma(-fs, xs[i], y[i]);
-                            if (tid == 0) y[jj] -= f2[k];
+                            if (tid == 0) y[jj] -= qf[k];
                         }
                     }
                 }
@@ -531,6 +544,44 @@ __device__ __forceinline__ void packed_solve_warp(const float *L, const float *r
 // (semi-normal equations with iterative refinement), so the result has the
 // accuracy of an FP64 least-squares solve whenever cond(X)^2 u_fp32 < 1.
 // Nodes that do not converge are flagged for the FP64 kernel.
+// Stopping test of the FP64 refinement of a node solve, on the squared norms
+// of the correction d and the iterate y (partials loc[0], loc[1] of each of
+// the NT threads): converged when ||d|| <= 1e-14 ||y||; given up when, from
+// the third step on, ||d|| no longer halves (then converged only if
+// ||d|| <= 1e-12 ||y||).  The warps' partials are added by thread 0 in warp
+// order, so the decision is the same on every run.  snorm holds
+// 2 NT / 32 + 2 doubles of scratch.  Returns 0 to go on, 1 converged, -1 not
+// converged; prev2 is the previous ||d||^2 (start at +inf).
+template <int NT>
+__device__ __forceinline__ int refine_stop(double loc[2], int it, double &prev2, double *snorm) {
+    constexpr int kW = NT / 32;
+    for (int o = 16; o > 0; o >>= 1) {
+        loc[0] += __shfl_xor_sync(0xffffffffu, loc[0], o);
+        loc[1] += __shfl_xor_sync(0xffffffffu, loc[1], o);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        snorm[warp] = loc[0];
+        snorm[kW + warp] = loc[1];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double d2 = 0.0, y2 = 0.0;
+        for (int w = 0; w < kW; ++w) {
+            d2 += snorm[w];
+            y2 += snorm[kW + w];
+        }
+        int st = 0;
+        if (d2 <= 1e-28 * y2) st = 1;
+        else if (it >= 2 && d2 > 0.25 * prev2) st = d2 <= 1e-24 * y2 ? 1 : -1;
+        snorm[2 * kW] = (double)st;
+        snorm[2 * kW + 1] = d2;
+    }
+    __syncthreads();
+    prev2 = snorm[2 * kW + 1];   // rewritten only after the next call's first barrier
+    return (int)snorm[2 * kW];
+}
+
 __global__ void __launch_bounds__(kThreads) k_nodes_mixed(TailCtx c, int n0, int off) {
     extern __shared__ double smd[];
     const int me = c.iscal[1];
@@ -548,7 +599,7 @@ __global__ void __launch_bounds__(kThreads) k_nodes_mixed(TailCtx c, int n0, int
     const double t = c.t[nd], wt = c.w[nd];
     const bool gm = c.method == SKF_METHOD_SGMRES;
     __shared__ int bad;
-    __shared__ double snorm[2];
+    __shared__ double snorm[2 * kThreads / 32 + 2];
     if (threadIdx.x == 0) bad = 0;
     for (int i = threadIdx.x; i < me; i += blockDim.x)
         for (int j = 0; j <= i; ++j)
@@ -669,22 +720,8 @@ __global__ void __launch_bounds__(kThreads) k_nodes_mixed(TailCtx c, int n0, int
                 y[a] += g[a];
                 loc[1] = fma(y[a], y[a], loc[1]);
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                loc[0] += __shfl_xor_sync(0xffffffffu, loc[0], o);
-                loc[1] += __shfl_xor_sync(0xffffffffu, loc[1], o);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) { snorm[0] = 0.0; snorm[1] = 0.0; }
-            __syncthreads();
-            if ((threadIdx.x & 31) == 0) {
-                atomicAdd(&snorm[0], loc[0]);
-                atomicAdd(&snorm[1], loc[1]);
-            }
-            __syncthreads();
-            const double dn = sqrt(snorm[0]), yn = sqrt(snorm[1]);
-            if (dn <= 1e-14 * yn) { conv = true; break; }
-            if (it >= 2 && dn > 0.5 * prev) { conv = dn <= 1e-12 * yn; break; }
-            prev = dn;
+            const int st = refine_stop<kThreads>(loc, it, prev, snorm);
+            if (st != 0) { conv = st > 0; break; }
         }
         if (!conv && threadIdx.x == 0) bad = 1;
     }
@@ -909,7 +946,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_nodes_g(TailCtx c, int n0, int
     const double t = c.t[nd], wt = c.w[nd];
     const bool gm = c.method == SKF_METHOD_SGMRES;
     double *y = sm.y, *rt = sm.rt, *rb = sm.rb, *g = sm.g;
-    __shared__ double snorm[2];
+    __shared__ double snorm[2 * kNodeThreads / 32 + 2];
     bool ok = chol_blocked<T>(c, t, me, L, sm);
     if (!ok) {
         if (MIXED) {
@@ -936,21 +973,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_nodes_g(TailCtx c, int n0, int
             loc[1] = fma(y[a], y[a], loc[1]);
         }
         if constexpr (MIXED) {
-            for (int o = 16; o > 0; o >>= 1) {
-                loc[0] += __shfl_xor_sync(0xffffffffu, loc[0], o);
-                loc[1] += __shfl_xor_sync(0xffffffffu, loc[1], o);
-            }
-            if (threadIdx.x == 0) { snorm[0] = 0.0; snorm[1] = 0.0; }
-            __syncthreads();
-            if ((threadIdx.x & 31) == 0) {
-                atomicAdd(&snorm[0], loc[0]);
-                atomicAdd(&snorm[1], loc[1]);
-            }
-            __syncthreads();
-            const double dn = sqrt(snorm[0]), yn = sqrt(snorm[1]);
-            if (dn <= 1e-14 * yn) { conv = true; break; }
-            if (it >= 2 && dn > 0.5 * prev) { conv = dn <= 1e-12 * yn; break; }
-            prev = dn;
+            const int st = refine_stop<kNodeThreads>(loc, it, prev, snorm);
+            if (st != 0) { conv = st > 0; break; }
         }
     }
     __syncthreads();
