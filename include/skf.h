@@ -241,6 +241,20 @@ skf_status skf_set_arnoldi_mode(int32_t mode);
  * Returns INVALID_ARG for another mode. */
 skf_status skf_set_qr_mode(int32_t mode);
 
+/* skf_set_tail_form: what the tail factors to whiten the sketched problem
+ * (Sec. 3; process-wide; results agree to rounding):
+ *   0  automatic (default): with an F64 basis the relation form, the QR of
+ *      the s x (m+1) matrix [S V_m, S A v_m]: the sketched Arnoldi relation
+ *      S A v_j = S V_m H(1:m, j) (j < m, eq. (2.1)) gives
+ *      M = [R_11 H(1:m, 1:m-1), R(1:m, m+1)] R_11^{-1} and the sGMRES term
+ *      orthogonal to S V_m, R(m+1, m+1) / R(m, m) e_m^T; with an F32 or BF16
+ *      basis (whose stored columns satisfy the relation only to their own
+ *      precision) the full form;
+ *   1  the full form: the QR of the s x 2m matrix [S V_m, S A V_m].
+ * The stopping criterion's checkpoints always take the full form.
+ * Returns INVALID_ARG for another form. */
+skf_status skf_set_tail_form(int32_t form);
+
 /* skf_barrier_selftest: failure-detection check of the bounded grid wait
  * used by the persistent Arnoldi kernel.  Launches `ctas` co-resident CTAs
  * (1 <= ctas <= SMs) that wait at a barrier no CTA can complete, giving up

@@ -113,12 +113,13 @@ def lib():
         L.skf_solve_batched.argtypes = [i32, ctypes.POINTER(Problem), i32, vp]
         L.skf_set_arnoldi_mode.argtypes = [i32]
         L.skf_set_qr_mode.argtypes = [i32]
+        L.skf_set_tail_form.argtypes = [i32]
         L.skf_barrier_selftest.argtypes = [i32, i64, vp, vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
                      "skf_solve", "skf_solve_batched", "skf_sfom",
                      "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c", "skf_set_arnoldi_mode",
-                     "skf_set_qr_mode", "skf_barrier_selftest"]:
+                     "skf_set_qr_mode", "skf_set_tail_form", "skf_barrier_selftest"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -408,6 +409,31 @@ class qr_mode:
 
     def __exit__(self, *exc):
         set_qr_mode(0)
+        return False
+
+
+TAIL_AUTO, TAIL_FULL = 0, 1
+
+
+def set_tail_form(form: int) -> None:
+    """skf_set_tail_form: 0 automatic (relation form with an F64 basis), 1 the
+    QR of [S V_m, S A V_m]."""
+    _check(lib().skf_set_tail_form(form))
+
+
+class tail_form:
+    """Context manager: run the enclosed calls with the given tail form, then
+    return to the default."""
+
+    def __init__(self, form: int):
+        self.form = form
+
+    def __enter__(self):
+        set_tail_form(self.form)
+        return self
+
+    def __exit__(self, *exc):
+        set_tail_form(TAIL_AUTO)
         return False
 
 

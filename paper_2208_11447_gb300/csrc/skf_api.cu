@@ -579,7 +579,7 @@ static skf_status solve_enqueue(skf_method method, const skf_csr *A, const skf_s
     if (st == SKF_OK)
         st = tail_run(method, s, m, n, V, bt, ldv, vscale, SV, SAV, iscal, rule, p.tol, two ? nullptr : (double *)x,
                       info, cs, nullptr, stopping ? sc.state : nullptr, z,
-                      p.cond_max == 0.0 ? 1e12 : (p.cond_max < 0.0 ? 0.0 : p.cond_max));
+                      p.cond_max == 0.0 ? 1e12 : (p.cond_max < 0.0 ? 0.0 : p.cond_max), H, m + 1, p.k);
     if (st == SKF_OK && two) {
         // second pass: the same recurrence (same sketches, H, vscale rewritten
         // with identical values), accumulating x column by column
@@ -702,6 +702,12 @@ skf_status skf_set_arnoldi_mode(int32_t mode) {
 skf_status skf_set_qr_mode(int32_t mode) {
     if (mode < 0 || mode > 1) return fail(SKF_ERR_INVALID_ARG, "QR mode must be 0 or 1");
     set_qr_mode(mode);
+    return SKF_OK;
+}
+
+skf_status skf_set_tail_form(int32_t form) {
+    if (form < 0 || form > 1) return fail(SKF_ERR_INVALID_ARG, "tail form must be 0 or 1");
+    set_tail_form(form);
     return SKF_OK;
 }
 

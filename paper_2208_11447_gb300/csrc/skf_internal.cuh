@@ -449,6 +449,9 @@ int step_mode();
 // fits, 1 one launch per Householder reflector.
 void set_qr_mode(int mode);
 int qr_mode();
+// what the tail factors (skf_set_tail_form)
+void set_tail_form(int form);
+int tail_form();
 // Bounded-wait self-test: `ctas` co-resident CTAs wait at a barrier that
 // cannot complete; *status_out (device) becomes SKF_ERR_TIMEOUT.
 skf_status barrier_selftest(int ctas, long long budget, int *status_out, cudaStream_t st);
@@ -469,11 +472,14 @@ skf_status arnoldi_run_bf16(const skf_csr *A, const skf_sketch *S, const double 
 // unused); with x == nullptr and no sketch_out it only forms the
 // coefficients.  z_out (nullable, m doubles): the coefficients z_j of the
 // stored columns (x = sum_j z_j w_j), zero for j >= m_eff.  stop_state (nullable): [1] last estimate, [2] stop step of the
-// stopping criterion, copied into info.
+// stopping criterion, copied into info.  H (nullable; ld ldh, truncation kt):
+// the Arnoldi coefficients; with H and an FP64 basis the tail uses the
+// relation form (QR of [S V_m, S A v_m], S A v_j = S V_m H(:, j) for j < m).
 skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
                     double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out = nullptr,
-                    const double *stop_state = nullptr, double *z_out = nullptr, double cond_max = 0.0);
+                    const double *stop_state = nullptr, double *z_out = nullptr, double cond_max = 0.0,
+                    const double *H = nullptr, int ldh = 0, int kt = 0);
 // Two-pass mode: x (+)= z_j w_j for basis column w_j (type vdt), j < m_eff =
 // iscal[1]; j = 0 starts x (x = 0 when m_eff = 0).  The FMA sequence per row
 // is that of the one-pass FP64 recombination.

@@ -11,6 +11,18 @@
 //           independent of s, equal to min ||(t Q + Z) y - S b||).
 // Each node is solved from its normal equations by Cholesky with one step of
 // FP64 iterative refinement on the original residual.
+//
+// With an FP64 basis the tail factors only the s x (m+1) matrix
+// [S V_m, S A v_m] instead (relation form): the Arnoldi relation
+// A v_j = sum_i h_ij v_i (i <= j + 1, eq. (2.1)) sketched gives
+// S A v_j = S V_m H(1:m, j) for j < m, so with [S V_m, S A v_m] = Q R,
+//   Q^T S A V_m = [R_11 H(1:m, 1:m-1), R(1:m, m+1)],
+// and the part of S A V_m orthogonal to S V_m is R(m+1, m+1) q_{m+1} e_m^T:
+// M = [R_11 H(1:m, 1:m-1), R(1:m, m+1)] R_11^{-1} and R2 is the single row
+// gamma e_m^T, gamma = R(m+1, m+1) / R(m, m) (the last row of R_11^{-1} is
+// e_m^T / R(m, m)).  Same M and ||R2 y|| as the 2m-column QR (S A V_m enters
+// only through the relation, which both Arnoldi forms satisfy to rounding),
+// half the reflectors for sGMRES, and rank-one R2 terms in the node solves.
 #include <math.h>
 
 #include <algorithm>
@@ -40,7 +52,11 @@ struct TailCtx {
     double *qbuf;      // [levels][m]
     double *qacc;      // [m]
     double *z;         // [m] coefficients for V (scaled by vscale)
-    double *qstate;    // [0] converged, [1] ell, [2] quad_err, [3] rdiag_ratio, [4] FP64 node solves, [5] cond(R) estimate
+    double *qstate;    // [0] converged, [1] ell, [2] quad_err, [3] rdiag_ratio, [4] FP64 node solves, [5] cond(R) estimate,
+                       // [6] gamma of the relation form (R2 = gamma e_m^T)
+    const double *H;   // relation form: Arnoldi coefficients h_ij = H[i + j ldh]
+    int ldh, kt;       // leading dimension of H, truncation length k
+    int rel;           // 1: relation form (QR of [S V_m, S A v_m]), 0: QR of [S V_m, S A V_m]
     double cond_max;   // ILL_CONDITIONED above this cond(R) estimate (0: no test)
     double *hsig;      // [2m] ||x(jj+1:)||^2 of each pivot column, from the previous reflector launch
     const double *t, *w;      // node table
@@ -52,17 +68,17 @@ namespace {
 
 __global__ void k_tail_copy(const double *__restrict__ SV, const double *__restrict__ SAV, TailCtx c) {
     const int me = c.iscal[1];
-    const int64_t tot = (int64_t)c.s * 2 * c.m;
+    const int64_t tot = (int64_t)c.s * (c.rel ? c.m + 1 : 2 * c.m);
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int col = (int)(idx / c.s);
         const int64_t r = idx % c.s;
         double v = 0.0;
         if (col < me) v = SV[r + (int64_t)col * c.s];
-        else if (col < 2 * me) v = SAV[r + (int64_t)(col - me) * c.s];
+        else if (c.rel ? col == me : col < 2 * me) v = SAV[r + (int64_t)(c.rel ? me - 1 : col - me) * c.s];
         c.Aw[idx] = v;
     }
-    if (blockIdx.x == 0 && threadIdx.x < 6) c.qstate[threadIdx.x] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x < 8) c.qstate[threadIdx.x] = 0.0;
 }
 
 // Householder reflector for column jj (LAPACK convention: beta = -sign(x0)
@@ -97,8 +113,8 @@ __global__ void __launch_bounds__(kHhThreads) k_householder(TailCtx c, int jj) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int me = c.iscal[1];
-    const int ncols = 2 * me;
-    const int nref = (c.method == SKF_METHOD_SGMRES) ? 2 * me : me;
+    const int ncols = c.rel ? me + 1 : 2 * me;
+    const int nref = (c.method == SKF_METHOD_SGMRES) ? ncols : me;
     if (jj >= nref || jj >= c.s) return;
     const int tid = threadIdx.x;
     const int gw = blockIdx.x;
@@ -195,9 +211,9 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_persist(TailCtx c, unsigned *
     __shared__ double qsc[2];                     // tau, scale of the current reflector
     __shared__ double qf[kQrOwn], qfs[kQrOwn];    // f and f scale of the columns being updated
     const int me = c.iscal[1];
-    const int ncols = 2 * me;
+    const int ncols = c.rel ? me + 1 : 2 * me;
     const int s = c.s;
-    const int nref = min((c.method == SKF_METHOD_SGMRES) ? 2 * me : me, s);
+    const int nref = min((c.method == SKF_METHOD_SGMRES) ? ncols : me, s);
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31;
     const bool warp0 = tid < 32;
@@ -358,6 +374,8 @@ constexpr int kMaxRegCol = 16;    // register slots per lane for one column of R
 __device__ double warp_rinv_norm_est(const double *Aw, int s, const double *rinv, int me);
 
 // Rows of X R = T for T = R12 (-> M) and T = R22 (-> R2); one warp per row,
+// (relation form: T = [R_11 H(1:m, 1:m-1), R(1:m, m+1)] -> M only, and
+// gamma = R(m+1, m+1) / R(m, m) by the cond(R) CTA)
 // x_j = (t_j - sum_{i<j} x_i R_ij) / R_jj.  The row of T and the reciprocals
 // 1 / R_jj are staged in shared memory first, and column j + 1 of R is
 // loaded into registers while column j is reduced, so a step waits on no
@@ -399,11 +417,13 @@ __global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c, int nblk_rows
             c.qstate[3] = mxd > 0.0 ? mn / mxd : 0.0;
             // never less than the diagonal ratio, a lower bound of cond(R)
             c.qstate[5] = me == 0 ? 0.0 : fmax(res[0] * res[1], mn > 0.0 ? mxd / mn : INFINITY);
+            c.qstate[6] = (c.rel && c.method == SKF_METHOD_SGMRES && me > 0 && c.Rdiag[me - 1] != 0.0)
+                              ? c.Rdiag[me] / c.Rdiag[me - 1] : 0.0;
         }
         return;
     }
     const int row = blockIdx.x * (kThreads / 32) + warp;
-    const int nrows = (c.method == SKF_METHOD_SGMRES) ? 2 * me : me;
+    const int nrows = (c.method == SKF_METHOD_SGMRES && !c.rel) ? 2 * me : me;
     if (row >= nrows) return;
     double *x = xs + (size_t)warp * c.m;
     double *tr = xs + (size_t)((kThreads / 32) + warp) * c.m;
@@ -411,7 +431,16 @@ __global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c, int nblk_rows
     const int a = second ? row - me : row;
     for (int j = lane; j < me; j += 32) {
         double tv;
-        if (!second) tv = c.Aw[a + (int64_t)(me + j) * c.s];
+        if (c.rel) {
+            if (j == me - 1) {
+                tv = c.Aw[a + (int64_t)me * c.s];   // R(a, m+1)
+            } else {                                // (R_11 H)(a, j): rows max(a, j-k+1) .. j+1 of column j of H
+                tv = 0.0;
+                const int i1 = min(j + 1, me - 1);
+                for (int i = max(a, j - c.kt + 1); i <= i1; ++i)
+                    tv = fma(i == a ? c.Rdiag[a] : c.Aw[a + (int64_t)i * c.s], c.H[i + (int64_t)j * c.ldh], tv);
+            }
+        } else if (!second) tv = c.Aw[a + (int64_t)(me + j) * c.s];
         else if (j < a) tv = 0.0;
         else if (j == a) tv = c.Rdiag[me + a];
         else tv = c.Aw[(me + a) + (int64_t)(me + j) * c.s];
@@ -448,7 +477,8 @@ __global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c, int nblk_rows
     for (int jcol = lane; jcol < me; jcol += 32) dst[a + (int64_t)jcol * c.m] = x[jcol];
 }
 
-// B = M + M^T, C = M^T M (+ R2^T R2), c = ||b|| R_11 e_1, M^T c.
+// B = M + M^T, C = M^T M (+ R2^T R2; relation form: + gamma^2 e_m e_m^T),
+// c = ||b|| R_11 e_1, M^T c.
 __global__ void __launch_bounds__(kThreads) k_tail_prep(TailCtx c) {
     const int me = c.iscal[1];
     const int64_t tot = (int64_t)me * me;
@@ -458,8 +488,13 @@ __global__ void __launch_bounds__(kThreads) k_tail_prep(TailCtx c) {
         if (j > i) continue;
         double acc = 0.0;
         for (int a = 0; a < me; ++a) acc = fma(c.M[a + (int64_t)i * c.m], c.M[a + (int64_t)j * c.m], acc);
-        if (c.method == SKF_METHOD_SGMRES)
-            for (int a = 0; a <= j; ++a) acc = fma(c.R2[a + (int64_t)i * c.m], c.R2[a + (int64_t)j * c.m], acc);
+        if (c.method == SKF_METHOD_SGMRES) {
+            if (c.rel) {
+                if (i == me - 1 && j == me - 1) acc = fma(c.qstate[6], c.qstate[6], acc);
+            } else {
+                for (int a = 0; a <= j; ++a) acc = fma(c.R2[a + (int64_t)i * c.m], c.R2[a + (int64_t)j * c.m], acc);
+            }
+        }
         c.C[i + (int64_t)j * c.m] = acc;
         c.B[i + (int64_t)j * c.m] = c.M[i + (int64_t)j * c.m] + c.M[j + (int64_t)i * c.m];
     }
@@ -467,7 +502,7 @@ __global__ void __launch_bounds__(kThreads) k_tail_prep(TailCtx c) {
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(idx % me), j = (int)(idx / me);
         c.MT[j + (int64_t)i * c.m] = c.M[i + (int64_t)j * c.m];
-        if (c.method == SKF_METHOD_SGMRES) c.R2T[j + (int64_t)i * c.m] = c.R2[i + (int64_t)j * c.m];
+        if (c.method == SKF_METHOD_SGMRES && !c.rel) c.R2T[j + (int64_t)i * c.m] = c.R2[i + (int64_t)j * c.m];
     }
     if (blockIdx.x == 0) {
         const double c0 = (1.0 / c.vscale[0]) * c.Rdiag[0];
@@ -544,6 +579,22 @@ __device__ __forceinline__ void packed_solve_warp(const float *L, const float *r
 // (semi-normal equations with iterative refinement), so the result has the
 // accuracy of an FP64 least-squares solve whenever cond(X)^2 u_fp32 < 1.
 // Nodes that do not converge are flagged for the FP64 kernel.
+// Row a of -R2 y, and row j of R2^T r (r of length m_eff), for the node
+// residuals (the second added to v): R2 upper triangular (ld m, transpose
+// R2T), or, in the relation form, the single row gamma e_m^T.
+__device__ __forceinline__ double r2_row(const TailCtx &c, int a, int me, const double *y) {
+    if (c.rel) return a == 0 ? -c.qstate[6] * y[me - 1] : 0.0;
+    double u = 0.0;
+    for (int j = a; j < me; ++j) u = fma(-c.R2[a + (int64_t)j * c.m], y[j], u);
+    return u;
+}
+
+__device__ __forceinline__ double r2t_row(const TailCtx &c, int j, int me, const double *r, double v) {
+    if (c.rel) return j == me - 1 ? fma(c.qstate[6], r[0], v) : v;
+    for (int a = 0; a <= j; ++a) v = fma(c.R2T[j + (int64_t)a * c.m], r[a], v);
+    return v;
+}
+
 // Stopping test of the FP64 refinement of a node solve, on the squared norms
 // of the correction d and the iterate y (partials loc[0], loc[1] of each of
 // the NT threads): converged when ||d|| <= 1e-14 ||y||; given up when, from
@@ -696,19 +747,14 @@ __global__ void __launch_bounds__(kThreads) k_nodes_mixed(TailCtx c, int n0, int
                 double v = c.cvec[a] - t * y[a];
                 for (int j = 0; j < me; ++j) v = fma(-c.M[a + (int64_t)j * m], y[j], v);
                 rt[a] = v;
-                if (gm) {
-                    double u = 0.0;
-                    for (int j = a; j < me; ++j) u = fma(-c.R2[a + (int64_t)j * m], y[j], u);
-                    rb[a] = u;
-                }
+                if (gm) rb[a] = r2_row(c, a, me, y);
             }
             __syncthreads();
             // g = [t I + M; R2]^T r
             for (int j = threadIdx.x; j < me; j += blockDim.x) {
                 double v = t * rt[j];
                 for (int a = 0; a < me; ++a) v = fma(c.MT[j + (int64_t)a * m], rt[a], v);
-                if (gm)
-                    for (int a = 0; a <= j; ++a) v = fma(c.R2T[j + (int64_t)a * m], rb[a], v);
+                if (gm) v = r2t_row(c, j, me, rb, v);
                 g[j] = v;
             }
             __syncthreads();
@@ -909,18 +955,13 @@ __device__ void node_residual(const TailCtx &c, double t, int me, const double *
         double v = c.cvec[a] - t * y[a];
         for (int j = 0; j < me; ++j) v = fma(-c.M[a + (int64_t)j * m], y[j], v);
         rt[a] = v;
-        if (gm) {
-            double u = 0.0;
-            for (int j = a; j < me; ++j) u = fma(-c.R2[a + (int64_t)j * m], y[j], u);
-            rb[a] = u;
-        }
+        if (gm) rb[a] = r2_row(c, a, me, y);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < me; j += blockDim.x) {
         double v = t * rt[j];
         for (int a = 0; a < me; ++a) v = fma(c.MT[j + (int64_t)a * m], rt[a], v);
-        if (gm)
-            for (int a = 0; a <= j; ++a) v = fma(c.R2T[j + (int64_t)a * m], rb[a], v);
+        if (gm) v = r2t_row(c, j, me, rb, v);
         g[j] = v;
     }
     __syncthreads();
@@ -1009,13 +1050,8 @@ __device__ void node_residual_cplx(const TailCtx &c, double al, double be, int m
         rt[a] = c.cvec[a] - al * u[a] - mu + be * v[a];      // r1
         rt[me + a] = -be * u[a] - al * v[a] - mv;            // r2
         if (gm) {
-            double ru = 0.0, rv = 0.0;
-            for (int j = a; j < me; ++j) {
-                ru = fma(-c.R2[a + (int64_t)j * m], u[j], ru);
-                rv = fma(-c.R2[a + (int64_t)j * m], v[j], rv);
-            }
-            rb[a] = ru;        // r3
-            rb[me + a] = rv;   // r4
+            rb[a] = r2_row(c, a, me, u);        // r3
+            rb[me + a] = r2_row(c, a, me, v);   // r4
         }
     }
     __syncthreads();
@@ -1026,12 +1062,10 @@ __device__ void node_residual_cplx(const TailCtx &c, double al, double be, int m
             g1 = fma(mt, rt[a], g1);
             g2 = fma(mt, rt[me + a], g2);
         }
-        if (gm)
-            for (int a = 0; a <= j; ++a) {
-                const double r2t = c.R2T[j + (int64_t)a * m];
-                g1 = fma(r2t, rb[a], g1);
-                g2 = fma(r2t, rb[me + a], g2);
-            }
+        if (gm) {
+            g1 = r2t_row(c, j, me, rb, g1);
+            g2 = r2t_row(c, j, me, rb + me, g2);
+        }
         g[j] = g1;
         g[me + j] = g2;
     }
@@ -1416,13 +1450,21 @@ __global__ void k_write_info(TailCtx c, skf_info *info, const double *stop_state
 static int g_qr_mode = 0;   // 0 automatic (cooperative QR where it fits), 1 per-reflector launches
 void set_qr_mode(int mode) { g_qr_mode = mode; }
 int qr_mode() { return g_qr_mode; }
+static int g_tail_form = 0;   // 0 automatic (relation form with an FP64 basis), 1 full QR of [S V_m, S A V_m]
+void set_tail_form(int form) { g_tail_form = form; }
+int tail_form() { return g_tail_form; }
 
 skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
                     const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
                     double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out,
-                    const double *stop_state, double *z_out, double cond_max) {
+                    const double *stop_state, double *z_out, double cond_max, const double *H, int ldh, int kt) {
     TailCtx c{};
     c.cond_max = cond_max;
+    // relation form where the basis is FP64 and H is given (see the top of the file)
+    c.rel = (tail_form() != 1 && H != nullptr && vdt == SKF_F64 && m >= 1) ? 1 : 0;
+    c.H = H;
+    c.ldh = ldh;
+    c.kt = kt;
     c.s = s;
     c.m = m;
     c.method = method;
@@ -1458,7 +1500,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                             sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * m,
                             sizeof(double) * m, sizeof(double) * chunk * mm * (rule.cplx ? 4 : 1), sizeof(double) * (size_t)cap * m,
                             sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
-                            sizeof(double) * 6, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
+                            sizeof(double) * 8, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
                             sizeof(double) * 2 * (size_t)m, sizeof(unsigned) * 4};
     constexpr int kNbuf = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
@@ -1482,12 +1524,13 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     long long nlaunch = 0;
     k_tail_copy<<<G, kThreads, 0, st>>>(SV, SAV, c);
     ++nlaunch;
-    const int nref = (method == SKF_METHOD_SGMRES) ? 2 * m : m;
+    const int ncols_max = c.rel ? m + 1 : 2 * m;   // columns of the factored matrix at m_eff = m
+    const int nref = (method == SKF_METHOD_SGMRES) ? ncols_max : m;
     // the QR in one cooperative launch (k_qr_persist): every column's owner
     // CTA must be resident, with at most kQrOwn columns per CTA
     bool qr_done = false;
     if (qr_mode() != 1) {
-        const int cols = std::max(1, 2 * m);   // every column has an owner CTA holding it
+        const int cols = std::max(1, ncols_max);   // every column has an owner CTA holding it
         int Gq = std::min(cols, num_sms());
         if ((cols + kQrOwn - 1) / kQrOwn > Gq) Gq = (cols + kQrOwn - 1) / kQrOwn;
         int dev = 0, per_sm = 0, coop = 0;
@@ -1523,7 +1566,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     pdl[0].val.programmaticStreamSerializationAllowed = 1;
     for (int jj = 0; !qr_done && jj < nref; ++jj) {
-        const int ntrail = std::max(1, 2 * m - jj - 1);
+        const int ntrail = std::max(1, ncols_max - jj - 1);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)ntrail);
         cfg.blockDim = dim3(kHhThreads);
@@ -1535,7 +1578,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     }
     if (!qr_done) nlaunch += nref;
     {
-        const int rows = (method == SKF_METHOD_SGMRES) ? 2 * m : m;
+        const int rows = (method == SKF_METHOD_SGMRES && !c.rel) ? 2 * m : m;
         const int blocks = (rows + (kThreads / 32) - 1) / (kThreads / 32);
         const size_t smem = sizeof(double) * (2 * (kThreads / 32) + 1) * (size_t)m;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k_tri_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
