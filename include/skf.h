@@ -241,6 +241,14 @@ skf_status skf_set_arnoldi_mode(int32_t mode);
  * Returns INVALID_ARG for another mode. */
 skf_status skf_set_qr_mode(int32_t mode);
 
+/* skf_workspace_trim: return the device memory that the library's
+ * workspace pools keep mapped between calls.  Each solve takes its
+ * stream-ordered workspace (about 8 m N bytes for an F64 basis, plus O(s m)
+ * and O(m^2) buffers) from a per-device pool that keeps freed blocks, so
+ * that repeated solves re-use them; call this (after the streams that used
+ * them have finished) to release them.  Errors: CUDA. */
+skf_status skf_workspace_trim(void);
+
 /* skf_set_tail_form: what the tail factors to whiten the sketched problem
  * (Sec. 3; process-wide; results agree to rounding):
  *   0  automatic (default): with an F64 basis the relation form, the QR of

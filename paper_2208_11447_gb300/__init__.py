@@ -114,12 +114,13 @@ def lib():
         L.skf_set_arnoldi_mode.argtypes = [i32]
         L.skf_set_qr_mode.argtypes = [i32]
         L.skf_set_tail_form.argtypes = [i32]
+        L.skf_workspace_trim.argtypes = []
         L.skf_barrier_selftest.argtypes = [i32, i64, vp, vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
                      "skf_solve", "skf_solve_batched", "skf_sfom",
                      "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c", "skf_set_arnoldi_mode",
-                     "skf_set_qr_mode", "skf_set_tail_form", "skf_barrier_selftest"]:
+                     "skf_set_qr_mode", "skf_set_tail_form", "skf_workspace_trim", "skf_barrier_selftest"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -413,6 +414,12 @@ class qr_mode:
 
 
 TAIL_AUTO, TAIL_FULL = 0, 1
+
+
+def workspace_trim() -> None:
+    """skf_workspace_trim: release the workspace blocks the library keeps
+    mapped between calls (synchronise the streams that used them first)."""
+    _check(lib().skf_workspace_trim())
 
 
 def set_tail_form(form: int) -> None:

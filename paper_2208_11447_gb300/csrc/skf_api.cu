@@ -42,14 +42,62 @@ int num_sms() {
     return cached;
 }
 
+// Stream-ordered workspace comes from a memory pool owned by the library, one
+// per device, whose release threshold keeps freed blocks mapped across
+// synchronisations: the workspace of one solve (mostly the m basis columns,
+// 8 m N bytes in FP64) is then taken over by the next solve instead of being
+// mapped again.  skf_workspace_trim returns the cached blocks.  Allocations
+// made while the stream is being captured into a graph use the graph's own
+// memory nodes (cudaMallocAsync) instead.
+static std::mutex &pool_mutex() {
+    static std::mutex *mu = new std::mutex();
+    return *mu;
+}
+
+static std::map<int, cudaMemPool_t> &pools() {
+    static std::map<int, cudaMemPool_t> *p = new std::map<int, cudaMemPool_t>();
+    return *p;
+}
+
+static cudaMemPool_t workspace_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(pool_mutex());
+    auto it = pools().find(dev);
+    if (it != pools().end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;
+    } else {
+        uint64_t keep = ~(uint64_t)0;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pools()[dev] = pool;
+    return pool;
+}
+
 skf_status dalloc(void **p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) bytes = 256;
-    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusNone;
+    }
+    cudaMemPool_t pool = cap == cudaStreamCaptureStatusNone ? workspace_pool() : nullptr;
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
-        return cuda_fail(e, "cudaMallocAsync");
+        return cuda_fail(e, "stream-ordered allocation");
     }
     return SKF_OK;
 }
@@ -702,6 +750,16 @@ skf_status skf_set_arnoldi_mode(int32_t mode) {
 skf_status skf_set_qr_mode(int32_t mode) {
     if (mode < 0 || mode > 1) return fail(SKF_ERR_INVALID_ARG, "QR mode must be 0 or 1");
     set_qr_mode(mode);
+    return SKF_OK;
+}
+
+skf_status skf_workspace_trim(void) {
+    std::lock_guard<std::mutex> lk(pool_mutex());
+    for (auto &kv : pools()) {
+        if (!kv.second) continue;
+        const cudaError_t e = cudaMemPoolTrimTo(kv.second, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolTrimTo");
+    }
     return SKF_OK;
 }
 

@@ -53,10 +53,13 @@ struct TailCtx {
     double *qacc;      // [m]
     double *z;         // [m] coefficients for V (scaled by vscale)
     double *qstate;    // [0] converged, [1] ell, [2] quad_err, [3] rdiag_ratio, [4] FP64 node solves, [5] cond(R) estimate,
-                       // [6] gamma of the relation form (R2 = gamma e_m^T)
+                       // [6] gamma of the relation form (R2 = gamma e_m^T), [7] 1 if R_11 has a zero pivot
     const double *H;   // relation form: Arnoldi coefficients h_ij = H[i + j ldh]
     int ldh, kt;       // leading dimension of H, truncation length k
     int rel;           // 1: relation form (QR of [S V_m, S A v_m]), 0: QR of [S V_m, S A V_m]
+    int hess;          // 1: real node solves by Givens reduction of the Hessenberg node matrix (relation form)
+    double *Rc, *RT;   // R_11 column-major and row-major (ld m), from k_r_pack
+    double *rinv;      // [m] 1 / R_jj
     double cond_max;   // ILL_CONDITIONED above this cond(R) estimate (0: no test)
     double *hsig;      // [2m] ||x(jj+1:)||^2 of each pivot column, from the previous reflector launch
     const double *t, *w;      // node table
@@ -369,42 +372,193 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_persist(TailCtx c, unsigned *
         for (int i = tid; i < s; i += kQrThreads) c.Aw[i + (int64_t)(g + k * G) * s] = cols[(size_t)k * s + i];
 }
 
-constexpr int kMaxRegCol = 16;    // register slots per lane for one column of R (m <= 512)
+// ---------------------------------------------------------------------------
+// Sequential triangular solves with the whitening factor R = R_11 by one
+// warp: lane l holds entries l, l + 32, ... of the vector in K register
+// groups (K = ceil(m / 32) rounded up to 2, 4, 8 or 16).  R comes in compact
+// form (k_r_pack): Rc column-major and RT row-major, ld m, and rinv = 1 / R_jj.
+// Both solves are axpy-oriented (no reduction inside a step: the new entry
+// is broadcast, every lane updates its own entries), and the row or column
+// that a step needs is loaded three steps ahead, so the dependent chain of a
+// step is one multiply, one shuffle and one FMA.
 
-__device__ double warp_rinv_norm_est(const double *Aw, int s, const double *rinv, int me);
+template <int K>
+__device__ __forceinline__ double hsel(const double (&x)[K], int k) {
+    double v = x[0];
+#pragma unroll
+    for (int q = 1; q < K; ++q) v = (q == k) ? x[q] : v;
+    return v;
+}
 
-// Rows of X R = T for T = R12 (-> M) and T = R22 (-> R2); one warp per row,
-// (relation form: T = [R_11 H(1:m, 1:m-1), R(1:m, m+1)] -> M only, and
-// gamma = R(m+1, m+1) / R(m, m) by the cond(R) CTA)
-// x_j = (t_j - sum_{i<j} x_i R_ij) / R_jj.  The row of T and the reciprocals
-// 1 / R_jj are staged in shared memory first, and column j + 1 of R is
-// loaded into registers while column j is reduced, so a step waits on no
-// global load.  The last CTA computes the estimate of cond(R) (qstate[5])
-// meanwhile: ||R^{-1}|| LINPACK-style times the largest column norm of R.
-__global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c, int nblk_rows) {
-    extern __shared__ double xs[];   // [warps][m] solutions, [warps][m] rows of T, [m] 1 / R_jj
+// x R = t (row vector; t in x on entry): x_j = t_j / R_jj, then
+// t_l -= x_j R_jl for l > j, row j of R read from RT.  EST: the forward solve
+// of the LINPACK condition estimator, R^T z = b with b_j = +-1 chosen step by
+// step against the sign of the accumulated sum (x starts at 0).
+template <int K, bool EST>
+__device__ void warp_row_solve(const double *RT, const double *rinv, int me, int m, double (&x)[K]) {
+    const int lane = threadIdx.x & 31;
+    const int ka = (me + 31) >> 5;
+    auto load = [&](double (&bv)[K], double &r, int j) {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int l = lane + 32 * kk;
+            bv[kk] = (j < me && kk < ka && l > j && l < me) ? RT[(int64_t)j * m + l] : 0.0;
+        }
+        r = j < me ? rinv[j] : 0.0;
+    };
+    auto step = [&](const double (&bv)[K], double r, int j) {
+        if (j >= me) return;
+        const int k0 = j >> 5, L = j & 31;
+        double tj = __shfl_sync(0xffffffffu, hsel(x, k0), L);
+        if (EST) tj += (tj < 0.0) ? -1.0 : 1.0;
+        const double xj = tj * r;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            if (kk >= k0 && kk < ka) {
+                const int l = lane + 32 * kk;
+                if (l > j) x[kk] = fma(-xj, bv[kk], x[kk]);
+                else if (l == j) x[kk] = xj;
+            }
+        }
+    };
+    double b0[K], b1[K], b2[K], r0, r1, r2;
+    load(b0, r0, 0);
+    load(b1, r1, 1);
+    load(b2, r2, 2);
+    for (int j = 0; j < me; j += 3) {
+        step(b0, r0, j);
+        load(b0, r0, j + 3);
+        step(b1, r1, j + 1);
+        load(b1, r1, j + 4);
+        step(b2, r2, j + 2);
+        load(b2, r2, j + 5);
+    }
+}
+
+// R y = x in place: y_p = x_p / R_pp, then x_i -= R_ip y_p for i < p,
+// column p of R read from Rc.
+template <int K>
+__device__ void warp_back_solve(const double *Rc, const double *rinv, int me, int m, double (&x)[K]) {
+    const int lane = threadIdx.x & 31;
+    const int ka = (me + 31) >> 5;
+    auto load = [&](double (&bv)[K], double &r, int p) {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int i = lane + 32 * kk;
+            bv[kk] = (p >= 0 && kk < ka && i < p) ? Rc[i + (int64_t)p * m] : 0.0;
+        }
+        r = p >= 0 ? rinv[p] : 0.0;
+    };
+    auto step = [&](const double (&bv)[K], double r, int p) {
+        if (p < 0) return;
+        const int k0 = p >> 5, L = p & 31;
+        const double yp = __shfl_sync(0xffffffffu, hsel(x, k0), L) * r;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            if (kk <= k0) {
+                const int i = lane + 32 * kk;
+                if (i < p) x[kk] = fma(-bv[kk], yp, x[kk]);
+                else if (i == p) x[kk] = yp;
+            }
+        }
+    };
+    double b0[K], b1[K], b2[K], r0, r1, r2;
+    load(b0, r0, me - 1);
+    load(b1, r1, me - 2);
+    load(b2, r2, me - 3);
+    for (int p = me - 1; p >= 0; p -= 3) {
+        step(b0, r0, p);
+        load(b0, r0, p - 3);
+        step(b1, r1, p - 1);
+        load(b1, r1, p - 4);
+        step(b2, r2, p - 2);
+        load(b2, r2, p - 5);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ double warp_sumsq(const double (&x)[K]) {
+    double v = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) v = fma(x[kk], x[kk], v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// R_11 in compact form: Rc (column-major) and RT (row-major), ld m, upper
+// triangle with the diagonal; rinv = 1 / R_jj (0 for a zero pivot, which
+// sets qstate[7]).
+__global__ void __launch_bounds__(kThreads) k_r_pack(TailCtx c) {
+    const int me = c.iscal[1];
+    const int m = c.m;
+    const int64_t tot = (int64_t)me * me;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % me), q = (int)(idx / me);
+        double v = 0.0;
+        if (i < q) {
+            v = c.Aw[i + (int64_t)q * c.s];
+        } else if (i == q) {
+            v = c.Rdiag[q];
+            c.rinv[q] = v != 0.0 ? 1.0 / v : 0.0;
+            if (!(v != 0.0)) c.qstate[7] = 1.0;
+        }
+        c.Rc[i + (int64_t)q * m] = v;
+        c.RT[q + (int64_t)i * m] = v;
+    }
+}
+
+// Rows of X R = T for T = R12 (-> M) and T = R22 (-> R2), one warp per row
+// (relation form: T = [R_11 H(1:m, 1:m-1), R(1:m, m+1)] -> M only).  Two
+// warps per CTA, so that the rows spread over the SMs (each step is a few
+// FP64 instructions per warp; more warps per SM would queue on the FP64
+// pipe).  The last CTA computes meanwhile the estimate of cond(R) (qstate[5]):
+// ||R^{-1}|| LINPACK-style (warp 0) times the largest column norm of R (warp
+// 1), and, in the relation form, gamma = R(m+1, m+1) / R(m, m) (qstate[6]).
+template <int K>
+__global__ void __launch_bounds__(64) k_tri_right(TailCtx c, int nblk_rows) {
     const int me = c.iscal[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double *rinv = xs + (size_t)2 * (kThreads / 32) * c.m;
-    for (int j = threadIdx.x; j < me; j += blockDim.x) rinv[j] = c.Rdiag[j] != 0.0 ? 1.0 / c.Rdiag[j] : 0.0;
-    __syncthreads();
+    const int m = c.m;
+    const int ka = (me + 31) >> 5;
+    const bool gm = c.method == SKF_METHOD_SGMRES;
     if ((int)blockIdx.x == nblk_rows) {   // the cond(R) estimate
         __shared__ double res[2];
+        const bool zp = c.qstate[7] != 0.0;
         if (warp == 0) {
-            bool zp = false;
-            for (int j = lane; j < me; j += 32) zp |= !(c.Rdiag[j] != 0.0);
-            zp = __any_sync(0xffffffffu, zp);
-            const double r = zp ? INFINITY : warp_rinv_norm_est(c.Aw, c.s, rinv, me);
-            if (lane == 0) res[0] = r;
-        } else if (warp == 1) {
-            double mx = 0.0;
-            for (int j = 0; j < me; ++j) {
-                double a2 = (lane == 0) ? c.Rdiag[j] * c.Rdiag[j] : 0.0;
-                for (int i = lane; i < j; i += 32) a2 = fma(c.Aw[i + (int64_t)j * c.s], c.Aw[i + (int64_t)j * c.s], a2);
+            double z[K];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-                mx = fmax(mx, a2);
+            for (int kk = 0; kk < K; ++kk) z[kk] = 0.0;
+            double r = INFINITY;
+            if (!zp && me > 0) {
+                warp_row_solve<K, true>(c.RT, c.rinv, me, m, z);
+                const double zn = warp_sumsq(z);
+                warp_back_solve<K>(c.Rc, c.rinv, me, m, z);
+                const double yn = warp_sumsq(z);
+                r = zn > 0.0 ? sqrt(yn / zn) : 0.0;
             }
+            if (lane == 0) res[0] = r;
+        } else {
+            // column norms of R, lanes over columns, rows of RT in turn
+            double a2[K];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) a2[kk] = 0.0;
+            for (int i = 0; i < me; ++i) {
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const int q = lane + 32 * kk;
+                    if (kk < ka && q >= i && q < me) {
+                        const double v = c.RT[(int64_t)i * m + q];
+                        a2[kk] = fma(v, v, a2[kk]);
+                    }
+                }
+            }
+            double mx = 0.0;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) mx = fmax(mx, a2[kk]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             if (lane == 0) res[1] = sqrt(mx);
         }
         __syncthreads();
@@ -417,72 +571,55 @@ __global__ void __launch_bounds__(kThreads) k_tri_right(TailCtx c, int nblk_rows
             c.qstate[3] = mxd > 0.0 ? mn / mxd : 0.0;
             // never less than the diagonal ratio, a lower bound of cond(R)
             c.qstate[5] = me == 0 ? 0.0 : fmax(res[0] * res[1], mn > 0.0 ? mxd / mn : INFINITY);
-            c.qstate[6] = (c.rel && c.method == SKF_METHOD_SGMRES && me > 0 && c.Rdiag[me - 1] != 0.0)
-                              ? c.Rdiag[me] / c.Rdiag[me - 1] : 0.0;
+            c.qstate[6] = (c.rel && gm && me > 0 && c.Rdiag[me - 1] != 0.0) ? c.Rdiag[me] / c.Rdiag[me - 1] : 0.0;
         }
         return;
     }
-    const int row = blockIdx.x * (kThreads / 32) + warp;
-    const int nrows = (c.method == SKF_METHOD_SGMRES && !c.rel) ? 2 * me : me;
+    const int row = blockIdx.x * 2 + warp;
+    const int nrows = (gm && !c.rel) ? 2 * me : me;
     if (row >= nrows) return;
-    double *x = xs + (size_t)warp * c.m;
-    double *tr = xs + (size_t)((kThreads / 32) + warp) * c.m;
     const bool second = row >= me;
     const int a = second ? row - me : row;
-    for (int j = lane; j < me; j += 32) {
-        double tv;
-        if (c.rel) {
-            if (j == me - 1) {
-                tv = c.Aw[a + (int64_t)me * c.s];   // R(a, m+1)
-            } else {                                // (R_11 H)(a, j): rows max(a, j-k+1) .. j+1 of column j of H
-                tv = 0.0;
-                const int i1 = min(j + 1, me - 1);
-                for (int i = max(a, j - c.kt + 1); i <= i1; ++i)
-                    tv = fma(i == a ? c.Rdiag[a] : c.Aw[a + (int64_t)i * c.s], c.H[i + (int64_t)j * c.ldh], tv);
-            }
-        } else if (!second) tv = c.Aw[a + (int64_t)(me + j) * c.s];
-        else if (j < a) tv = 0.0;
-        else if (j == a) tv = c.Rdiag[me + a];
-        else tv = c.Aw[(me + a) + (int64_t)(me + j) * c.s];
-        tr[j] = tv;
-    }
-    __syncwarp();
-    double cur[kMaxRegCol], nxt[kMaxRegCol];
+    double x[K];
 #pragma unroll
-    for (int t = 0; t < kMaxRegCol; ++t) cur[t] = 0.0;   // column 0 has no entries above the diagonal
-    for (int jcol = 0; jcol < me; ++jcol) {
-        const int jn = jcol + 1;
-#pragma unroll
-        for (int t = 0; t < kMaxRegCol; ++t) {
-            const int i = lane + 32 * t;
-            nxt[t] = (jn < me && i < jn) ? c.Aw[i + (int64_t)jn * c.s] : 0.0;
-        }
-        double part = 0.0;
-        const int nt = (jcol + 31) >> 5;   // warp-uniform: no predicated-off FP64 work
-#pragma unroll
-        for (int t = 0; t < kMaxRegCol; ++t) {
-            if (t < nt) {
-                const int i = lane + 32 * t;
-                part = fma(i < jcol ? x[i] : 0.0, cur[t], part);
+    for (int kk = 0; kk < K; ++kk) {
+        const int j = lane + 32 * kk;
+        double tv = 0.0;
+        if (kk < ka && j < me) {
+            if (c.rel) {
+                if (j == me - 1) {
+                    tv = c.Aw[a + (int64_t)me * c.s];   // R(a, m+1)
+                } else {   // (R_11 H)(a, j): rows max(a, j-k+1) .. j+1 of column j of H
+                    const int i1 = min(j + 1, me - 1);
+                    for (int i = max(a, j - c.kt + 1); i <= i1; ++i)
+                        tv = fma(c.RT[(int64_t)a * m + i], c.H[i + (int64_t)j * c.ldh], tv);
+                }
+            } else if (!second) {
+                tv = c.Aw[a + (int64_t)(me + j) * c.s];
+            } else if (j == a) {
+                tv = c.Rdiag[me + a];
+            } else if (j > a) {
+                tv = c.Aw[(me + a) + (int64_t)(me + j) * c.s];
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) x[jcol] = (tr[jcol] - part) * rinv[jcol];
-        __syncwarp();
-#pragma unroll
-        for (int t = 0; t < kMaxRegCol; ++t) cur[t] = nxt[t];
+        x[kk] = tv;
     }
+    warp_row_solve<K, false>(c.RT, c.rinv, me, m, x);
     double *dst = second ? c.R2 : c.M;
-    for (int jcol = lane; jcol < me; jcol += 32) dst[a + (int64_t)jcol * c.m] = x[jcol];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) {
+        const int j = lane + 32 * kk;
+        if (kk < ka && j < me) dst[a + (int64_t)j * m] = x[kk];
+    }
 }
 
-// B = M + M^T, C = M^T M (+ R2^T R2; relation form: + gamma^2 e_m e_m^T),
-// c = ||b|| R_11 e_1, M^T c.
+// B = M + M^T, C = M^T M (+ R2^T R2; relation form: + gamma^2 e_m e_m^T)
+// for the Cholesky node solves (not needed by the Givens ones), the
+// transposes, c = ||b|| R_11 e_1, M^T c.
 __global__ void __launch_bounds__(kThreads) k_tail_prep(TailCtx c) {
     const int me = c.iscal[1];
     const int64_t tot = (int64_t)me * me;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; !c.hess && idx < tot;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(idx % me), j = (int)(idx / me);
         if (j > i) continue;
@@ -1024,6 +1161,148 @@ __global__ void __launch_bounds__(kNodeThreads) k_nodes_g(TailCtx c, int n0, int
         for (int a = threadIdx.x; a < me; a += blockDim.x) c.out[(size_t)row * m + a] = wt * y[a];
 }
 
+// Real node solves of the relation form.  There M = T R_11^{-1} with T upper
+// Hessenberg (T = [R_11 H(1:m, 1:m-1), R(1:m, m+1)]), so M is upper
+// Hessenberg, and so are t I + M (sFOM) and [t I + M; gamma e_m^T] (sGMRES,
+// (m+1) x m); the right-hand side is c = c_0 e_1.  One warp per node reduces
+// the node matrix to triangular form by Givens rotations of rows (j, j+1),
+// j = 0, 1, ... (row j+1 of t I + M is read when it enters; the rotated row j
+// is final), rotating c along, then solves the triangle by column-oriented
+// back substitution: a backward stable QR solve in FP64, without normal
+// equations or refinement, O(m^2) work per node.  The rows of the triangle
+// go to the node's scratch slot in packed column-major order (column q at
+// q (q + 1) / 2, rows 0 .. q, the diagonal slot holding 1 / R_qq) so that the
+// back substitution reads each column contiguously.  Lane l holds columns
+// (and rows) l, l + 32, ... in K register groups.
+constexpr int kHessWarps = 4;   // nodes (warps) per CTA
+
+template <int K>
+__global__ void __launch_bounds__(32 * kHessWarps) k_nodes_hess(TailCtx c, int n0, int off, int nn, double *Rs,
+                                                                 size_t rstride) {
+    const int me = c.iscal[1];
+    if (c.qstate[0] != 0.0 || me == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * kHessWarps + warp;
+    if (slot >= nn) return;
+    const int row = off + slot;
+    const int nd = n0 + row;
+    const double t = c.t[nd], wt = c.w[nd];
+    const bool gm = c.method == SKF_METHOD_SGMRES;
+    const double gam = gm ? c.qstate[6] : 0.0;
+    const int m = c.m;
+    const int ka = (me + 31) >> 5;   // register groups in use (warp-uniform)
+    double *R = Rs + (size_t)slot * rstride;
+    const double *MT = c.MT;         // row a of M at MT + a m
+    double cr[K], nw[K], u[K];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) {
+        const int col = lane + 32 * kk;
+        const bool in = kk < ka && col < me;
+        cr[kk] = in ? __ldg(MT + col) + (col == 0 ? t : 0.0) : 0.0;   // row 0 of t I + M
+        nw[kk] = (in && me > 1) ? __ldg(MT + m + col) : 0.0;            // row 1 of M
+        u[kk] = 0.0;
+    }
+    double gc = c.cvec[0];   // the rotated right-hand side below the rows done
+    bool bad = false;
+    for (int j = 0; j < me; ++j) {
+        const int k0 = j >> 5, L = j & 31;
+        const bool enter = j + 1 < me || gm;
+        if (j + 1 < me) {   // shift of row j + 1
+            const int k1 = (j + 1) >> 5;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk)
+                if (kk == k1) nw[kk] += (lane == ((j + 1) & 31)) ? t : 0.0;
+        } else if (gm) {    // the row gamma e_m^T of the sGMRES problem
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) nw[kk] = (lane + 32 * kk == me - 1) ? gam : 0.0;
+        }
+        // row j + 2 of M (columns >= j + 1), for the next step
+        double pf[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int col = lane + 32 * kk;
+            pf[kk] = (kk < ka && j + 2 < me && col > j && col < me) ? __ldg(MT + (size_t)(j + 2) * m + col) : 0.0;
+        }
+        double a = hsel(cr, k0), b = hsel(nw, k0);
+        a = __shfl_sync(0xffffffffu, a, L);
+        b = __shfl_sync(0xffffffffu, b, L);
+        double cs = 1.0, sn = 0.0, rinv = 0.0;
+        if (enter) {
+            const double q = fma(a, a, b * b);
+            if (q > 0.0 && q < INFINITY) {
+                const double ri = rsqrt(q);   // r = q ri = R_jj
+                cs = a * ri;
+                sn = b * ri;
+                rinv = ri;
+            } else {
+                bad = true;
+            }
+        } else if (a != 0.0 && fabs(a) < INFINITY) {   // sFOM, last row: R_jj = a
+            rinv = 1.0 / a;
+        } else {
+            bad = true;
+        }
+        // row j of R and the rotated carried row (columns >= j)
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            if (kk >= k0 && kk < ka) {
+                const int col = lane + 32 * kk;
+                if (col >= j && col < me) {
+                    const double rj = fma(cs, cr[kk], sn * nw[kk]);
+                    cr[kk] = fma(cs, nw[kk], -(sn * cr[kk]));
+                    R[(size_t)col * (col + 1) / 2 + j] = (col == j) ? rinv : rj;
+                }
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk)
+            if (kk == k0) u[kk] = (lane == L) ? cs * gc : u[kk];
+        gc = -sn * gc;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) nw[kk] = pf[kk];
+    }
+    __syncwarp();
+    // R y = u, column by column from the last; column j - 1 is loaded while
+    // column j is applied
+    double cur[K];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) {
+        const int i = lane + 32 * kk;
+        cur[kk] = (kk < ka && i < me - 1) ? R[(size_t)(me - 1) * me / 2 + i] : 0.0;
+    }
+    double rj = R[(size_t)(me - 1) * me / 2 + me - 1];
+    for (int j = me - 1; j >= 0; --j) {
+        const int k0 = j >> 5, L = j & 31;
+        double nx[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int i = lane + 32 * kk;
+            nx[kk] = (kk <= k0 && j >= 1 && i < j - 1) ? R[(size_t)(j - 1) * j / 2 + i] : 0.0;
+        }
+        const double rn = j >= 1 ? R[(size_t)(j - 1) * j / 2 + j - 1] : 0.0;
+        double yj = hsel(u, k0);
+        yj = __shfl_sync(0xffffffffu, yj, L) * rj;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            if (kk <= k0) {
+                const int i = lane + 32 * kk;
+                if (i < j) u[kk] = fma(-cur[kk], yj, u[kk]);
+                else if (i == j) u[kk] = yj;
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) cur[kk] = nx[kk];
+        rj = rn;
+    }
+    bad = __any_sync(0xffffffffu, bad);
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) {
+        const int i = lane + 32 * kk;
+        if (kk < ka && i < me) c.out[(size_t)row * m + i] = bad ? 0.0 : wt * u[kk];
+    }
+    if (bad && lane == 0) atomicExch(&c.iscal[2], gm ? (int)SKF_ERR_ILL_CONDITIONED : (int)SKF_ERR_BRANCH_CUT);
+}
+
 // Complex nodes (contour rules for a non-Stieltjes f, Algorithm 2): for
 // t = alpha + i beta the node problem min || [t I + M; R2] y - [c; 0] || (or
 // (t I + M) y = c for sFOM) is solved in real arithmetic for y = u + i v:
@@ -1162,125 +1441,22 @@ __global__ void __launch_bounds__(kThreads) k_levels(TailCtx c, int lev0, int nl
     }
 }
 
-// Triangular solves with the whitening factor R (upper; R_ij = Aw[i + j s]
-// for i < j, R_jj = Rdiag[j]) by one warp, vectors of length me <= 32 kRv
-// held in registers (lane l: entries l, l + 32, ...).  rinv: 1 / R_jj.
-constexpr int kRv = 16;   // m <= 512
-
-__device__ __forceinline__ double warp_pick(const double (&x)[kRv], int p) {
-    const int kp = p >> 5;
-    double v = x[0];
-#pragma unroll
-    for (int k = 1; k < kRv; ++k) v = (k == kp) ? x[k] : v;
-    return __shfl_sync(0xffffffffu, v, p & 31);
-}
-
-// back substitution R z = x in place, column-oriented: step p reads column p
-// of R (contiguous) and updates the rows above it
-__device__ void warp_back_subst(const double *Aw, int s, const double *rinv, int me, double (&x)[kRv]) {
-    const int lane = threadIdx.x & 31;
-    double cur[kRv], nxt[kRv];   // column p of R (rows < p), column p - 1 prefetched
-#pragma unroll
-    for (int k = 0; k < kRv; ++k) {
-        const int i = lane + 32 * k;
-        cur[k] = (me > 0 && i < me - 1) ? Aw[i + (int64_t)(me - 1) * s] : 0.0;
-    }
-    for (int p = me - 1; p >= 0; --p) {
-#pragma unroll
-        for (int k = 0; k < kRv; ++k) {
-            const int i = lane + 32 * k;
-            nxt[k] = (p >= 1 && i < p - 1) ? Aw[i + (int64_t)(p - 1) * s] : 0.0;
-        }
-        const double zp = warp_pick(x, p) * rinv[p];
-        const int nk = (p >> 5) + 1;   // warp-uniform: registers that hold rows <= p
-#pragma unroll
-        for (int k = 0; k < kRv; ++k) {
-            if (k < nk) {
-                const int i = lane + 32 * k;
-                if (i < p) x[k] = fma(-cur[k], zp, x[k]);
-                else if (i == p) x[k] = zp;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kRv; ++k) cur[k] = nxt[k];
-    }
-}
-
-// Estimate of ||R^{-1}||_2 in the manner of the LINPACK condition estimator:
-// solve R^T z = b with b_p = +-1 chosen, step by step, to make |z_p| as large
-// as possible, then R y = z; ||y|| / ||z|| approximates ||R^{-1}|| (from
-// below, usually within a small factor).  Returns the estimate in every lane.
-__device__ double warp_rinv_norm_est(const double *Aw, int s, const double *rinv, int me) {
-    const int lane = threadIdx.x & 31;
-    double z[kRv], cur[kRv], nxt[kRv];   // column p of R, column p + 1 prefetched
-#pragma unroll
-    for (int k = 0; k < kRv; ++k) {
-        z[k] = 0.0;
-        cur[k] = 0.0;   // column 0 has no entries above the diagonal
-    }
-    for (int p = 0; p < me; ++p) {   // R^T z = b: z_p = (b_p - sum_{i<p} R_ip z_i) / R_pp
-#pragma unroll
-        for (int k = 0; k < kRv; ++k) {
-            const int i = lane + 32 * k;
-            nxt[k] = (p + 1 < me && i < p + 1) ? Aw[i + (int64_t)(p + 1) * s] : 0.0;
-        }
-        const int nk = (p >> 5) + 1;
-        double part = 0.0;
-#pragma unroll
-        for (int k = 0; k < kRv; ++k) {
-            if (k < nk) {
-                const int i = lane + 32 * k;
-                if (i < p) part = fma(cur[k], z[k], part);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kRv; ++k) cur[k] = nxt[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        const double bp = part > 0.0 ? -1.0 : 1.0;
-        const double zp = (bp - part) * rinv[p];
-#pragma unroll
-        for (int k = 0; k < kRv; ++k)
-            if (k == (p >> 5) && lane == (p & 31)) z[k] = zp;
-    }
-    double zn = 0.0;
-#pragma unroll
-    for (int k = 0; k < kRv; ++k) zn = fma(z[k], z[k], zn);
-    warp_back_subst(Aw, s, rinv, me, z);
-    double yn = 0.0;
-#pragma unroll
-    for (int k = 0; k < kRv; ++k) yn = fma(z[k], z[k], yn);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        zn += __shfl_xor_sync(0xffffffffu, zn, o);
-        yn += __shfl_xor_sync(0xffffffffu, yn, o);
-    }
-    return zn > 0.0 ? sqrt(yn / zn) : 0.0;
-}
-
-// y = R^{-1} q_acc, z = vscale .* y: one warp, back substitution with the
-// column of R prefetched (warp_back_subst); ILL_CONDITIONED when R has a zero
-// pivot or the estimate of cond(R) (k_tri_right) exceeds cond_max.
+// y = R^{-1} q_acc, z = vscale .* y: one warp (warp_back_solve);
+// ILL_CONDITIONED when R has a zero pivot or the estimate of cond(R)
+// (k_tri_right) exceeds cond_max.
+template <int K>
 __global__ void __launch_bounds__(32) k_coeffs(TailCtx c) {
-    extern __shared__ double rinv[];   // [me]
     const int me = c.iscal[1];
     const int lane = threadIdx.x & 31;
-    bool zero_pivot = false;
-    for (int a = lane; a < me; a += 32) {
-        const double d = c.Rdiag[a];
-        zero_pivot |= !(d != 0.0);
-        rinv[a] = d != 0.0 ? 1.0 / d : 0.0;
-    }
-    zero_pivot = __any_sync(0xffffffffu, zero_pivot);
-    __syncwarp();
-    double x[kRv];
+    const bool zero_pivot = c.qstate[7] != 0.0;
+    double x[K];
 #pragma unroll
-    for (int k = 0; k < kRv; ++k) x[k] = (lane + 32 * k < me) ? c.qacc[lane + 32 * k] : 0.0;
-    if (!zero_pivot) warp_back_subst(c.Aw, c.s, rinv, me, x);
+    for (int kk = 0; kk < K; ++kk) x[kk] = (lane + 32 * kk < me) ? c.qacc[lane + 32 * kk] : 0.0;
+    if (!zero_pivot) warp_back_solve<K>(c.Rc, c.rinv, me, c.m, x);
 #pragma unroll
-    for (int k = 0; k < kRv; ++k) {
-        const int i = lane + 32 * k;
-        if (i < me) c.z[i] = zero_pivot ? 0.0 : c.vscale[i] * x[k];
+    for (int kk = 0; kk < K; ++kk) {
+        const int i = lane + 32 * kk;
+        if (i < me) c.z[i] = zero_pivot ? 0.0 : c.vscale[i] * x[kk];
     }
     if (lane == 0 && me > 0 && c.iscal[2] == SKF_OK &&
         (zero_pivot || (c.cond_max > 0.0 && c.qstate[5] > c.cond_max)))
@@ -1465,6 +1641,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     c.H = H;
     c.ldh = ldh;
     c.kt = kt;
+    c.hess = (c.rel && !rule.cplx) ? 1 : 0;
     c.s = s;
     c.m = m;
     c.method = method;
@@ -1478,8 +1655,9 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     int max_level = 0;
     for (int l = 0; l < rule.nlevels; ++l) max_level = std::max(max_level, rule.h_start[l + 1] - rule.h_start[l]);
     // batches of consecutive levels filling at most one wave of node CTAs
-    // (2 per SM); a larger level forms a batch of its own (never split)
-    const int wave = 2 * num_sms();
+    // (2 per SM; Givens node solves: 4 warps per SM); a larger level forms a
+    // batch of its own (never split)
+    const int wave = (c.hess ? 4 : 2) * num_sms();
     const int cap = std::max(wave, max_level);
     std::vector<std::pair<int, int>> batches;   // (first level, count)
     for (int l = 0; l < rule.nlevels;) {
@@ -1493,15 +1671,19 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
         batches.push_back({l, cnt});
         l += cnt;
     }
-    const int chunk = 2 * num_sms();
+    const int chunk = wave;   // node solves per launch (scratch slots)
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t mm = (size_t)m * m;
+    const size_t rstride = (size_t)m * (m + 1) / 2;   // Givens node solves: packed triangle per slot
+    const size_t nw_bytes = c.hess ? sizeof(double) * chunk * rstride
+                                   : sizeof(double) * chunk * mm * (rule.cplx ? 4 : 1);
     const size_t sizes[] = {sizeof(double) * (size_t)s * 2 * m, sizeof(double) * 2 * m, sizeof(double) * mm,
                             sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * m,
-                            sizeof(double) * m, sizeof(double) * chunk * mm * (rule.cplx ? 4 : 1), sizeof(double) * (size_t)cap * m,
+                            sizeof(double) * m, nw_bytes, sizeof(double) * (size_t)cap * m,
                             sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
                             sizeof(double) * 8, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
-                            sizeof(double) * 2 * (size_t)m, sizeof(unsigned) * 4};
+                            sizeof(double) * 2 * (size_t)m, sizeof(unsigned) * 4, sizeof(double) * mm,
+                            sizeof(double) * mm, sizeof(double) * m};
     constexpr int kNbuf = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
     for (size_t v : sizes) total += al(v);
@@ -1519,6 +1701,9 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     c.z = ptrs[12]; c.qstate = ptrs[13]; c.MT = ptrs[14]; c.R2T = ptrs[15]; c.nodebad = (int *)ptrs[16];
     c.hsig = ptrs[17];
     unsigned *qr_ready = (unsigned *)ptrs[18];   // [0] published pivot columns, [1] timeout flag
+    c.Rc = ptrs[19];
+    c.RT = ptrs[20];
+    c.rinv = ptrs[21];
 
     const int G = std::min(2 * num_sms(), 1024);
     long long nlaunch = 0;
@@ -1577,12 +1762,17 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
         cudaLaunchKernelEx(&cfg, k_householder, c, jj);
     }
     if (!qr_done) nlaunch += nref;
+    k_r_pack<<<(unsigned)std::max<size_t>(1, std::min<size_t>((mm + kThreads - 1) / kThreads, 4 * num_sms())),
+               kThreads, 0, st>>>(c);
+    ++nlaunch;
     {
         const int rows = (method == SKF_METHOD_SGMRES && !c.rel) ? 2 * m : m;
-        const int blocks = (rows + (kThreads / 32) - 1) / (kThreads / 32);
-        const size_t smem = sizeof(double) * (2 * (kThreads / 32) + 1) * (size_t)m;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k_tri_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_tri_right<<<blocks + 1, kThreads, smem, st>>>(c, blocks);   // + 1: the cond(R) estimate
+        const unsigned blocks = (unsigned)((rows + 1) / 2);
+        // + 1 CTA: the cond(R) estimate
+        if (m <= 64) k_tri_right<2><<<blocks + 1, 64, 0, st>>>(c, (int)blocks);
+        else if (m <= 128) k_tri_right<4><<<blocks + 1, 64, 0, st>>>(c, (int)blocks);
+        else if (m <= 256) k_tri_right<8><<<blocks + 1, 64, 0, st>>>(c, (int)blocks);
+        else k_tri_right<16><<<blocks + 1, 64, 0, st>>>(c, (int)blocks);
         ++nlaunch;
     }
     k_tail_prep<<<G, kThreads, 0, st>>>(c);
@@ -1606,6 +1796,15 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
         const int nn = rule.h_start[l0 + nl] - n0;
         for (int o = 0; o < nn; o += chunk) {
             const int nb = std::min(chunk, nn - o);
+            if (c.hess) {
+                const unsigned g = (unsigned)((nb + kHessWarps - 1) / kHessWarps);
+                if (m <= 64) k_nodes_hess<2><<<g, 32 * kHessWarps, 0, st>>>(c, n0, o, nb, c.Nw, rstride);
+                else if (m <= 128) k_nodes_hess<4><<<g, 32 * kHessWarps, 0, st>>>(c, n0, o, nb, c.Nw, rstride);
+                else if (m <= 256) k_nodes_hess<8><<<g, 32 * kHessWarps, 0, st>>>(c, n0, o, nb, c.Nw, rstride);
+                else k_nodes_hess<16><<<g, 32 * kHessWarps, 0, st>>>(c, n0, o, nb, c.Nw, rstride);
+                nlaunch += 1;
+                continue;
+            }
             if (rule.cplx) {
                 k_nodes_cplx<<<nb, kNodeThreads, gsmC, st>>>(c, n0, o);
             } else {
@@ -1619,7 +1818,10 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                                          bi + 1 == batches.size() ? 1 : 0);
         ++nlaunch;
     }
-    k_coeffs<<<1, 32, sizeof(double) * m, st>>>(c);
+    if (m <= 64) k_coeffs<2><<<1, 32, 0, st>>>(c);
+    else if (m <= 128) k_coeffs<4><<<1, 32, 0, st>>>(c);
+    else if (m <= 256) k_coeffs<8><<<1, 32, 0, st>>>(c);
+    else k_coeffs<16><<<1, 32, 0, st>>>(c);
     const int64_t rb = std::min<int64_t>((n + kThreads - 1) / kThreads, 16 * num_sms());
     const unsigned rgrid = (unsigned)std::max<int64_t>(rb, 1);
     const size_t zsm = sizeof(float) * 2 * (size_t)m;
