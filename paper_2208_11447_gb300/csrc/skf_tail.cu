@@ -58,8 +58,11 @@ struct TailCtx {
     int ldh, kt;       // leading dimension of H, truncation length k
     int rel;           // 1: relation form (QR of [S V_m, S A v_m]), 0: QR of [S V_m, S A V_m]
     int hess;          // 1: real node solves by Givens reduction of the Hessenberg node matrix (relation form)
-    double *Rc, *RT;   // R_11 column-major and row-major (ld m), from k_r_pack
+    double *RT, *RTs;  // R_11 row-major, and D^{-1} R_11 row-major (D = diag(R_11)), ld m, from k_r_pack
+    double *Rcs;       // R_11 D^{-1} column-major, ld m
     double *rinv;      // [m] 1 / R_jj
+    double *cn2;       // [m] squared column norms of R_11
+    unsigned *lev_cnt; // CTAs of the current k_levels launch that have finished their level
     double cond_max;   // ILL_CONDITIONED above this cond(R) estimate (0: no test)
     double *hsig;      // [2m] ||x(jj+1:)||^2 of each pivot column, from the previous reflector launch
     const double *t, *w;      // node table
@@ -82,6 +85,7 @@ __global__ void k_tail_copy(const double *__restrict__ SV, const double *__restr
         c.Aw[idx] = v;
     }
     if (blockIdx.x == 0 && threadIdx.x < 8) c.qstate[threadIdx.x] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *c.lev_cnt = 0u;
 }
 
 // Householder reflector for column jj (LAPACK convention: beta = -sign(x0)
@@ -375,12 +379,15 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_persist(TailCtx c, unsigned *
 // ---------------------------------------------------------------------------
 // Sequential triangular solves with the whitening factor R = R_11 by one
 // warp: lane l holds entries l, l + 32, ... of the vector in K register
-// groups (K = ceil(m / 32) rounded up to 2, 4, 8 or 16).  R comes in compact
-// form (k_r_pack): Rc column-major and RT row-major, ld m, and rinv = 1 / R_jj.
-// Both solves are axpy-oriented (no reduction inside a step: the new entry
-// is broadcast, every lane updates its own entries), and the row or column
-// that a step needs is loaded three steps ahead, so the dependent chain of a
-// step is one multiply, one shuffle and one FMA.
+// groups (K = ceil(m / 32) rounded up to 2, 4, 8 or 16).  An FP64 warp
+// instruction keeps its SM sub-partition's FP64 unit busy for many cycles on
+// this part, so a step issues as few as possible: the factors come with
+// unit diagonals (k_r_pack: RTs = D^{-1} R row-major, Rcs = R D^{-1}
+// column-major, D = diag(R)), a step is one broadcast and one FMA per
+// register group still in play (the group of the next pivot first), the
+// outer loop over register groups is unrolled so that the pivot's register
+// is known at compile time, and the row or column a step needs is loaded
+// four steps ahead.
 
 template <int K>
 __device__ __forceinline__ double hsel(const double (&x)[K], int k) {
@@ -390,89 +397,102 @@ __device__ __forceinline__ double hsel(const double (&x)[K], int k) {
     return v;
 }
 
-// x R = t (row vector; t in x on entry): x_j = t_j / R_jj, then
-// t_l -= x_j R_jl for l > j, row j of R read from RT.  EST: the forward solve
-// of the LINPACK condition estimator, R^T z = b with b_j = +-1 chosen step by
-// step against the sign of the accumulated sum (x starts at 0).
+// x' RTs = t with x' = x D, i.e. x R = t (row vector; t in x on entry, x'
+// on exit: the caller scales by 1 / R_jj): x'_j = t_j, then
+// t_l -= x'_j RTs_jl for l > j.  EST: the forward solve of the LINPACK
+// condition estimator, z'^T = (b - v)^T with b_j = +-1 chosen step by step
+// against the sign of the accumulated v (x starts at 0).
 template <int K, bool EST>
-__device__ void warp_row_solve(const double *RT, const double *rinv, int me, int m, double (&x)[K]) {
+__device__ void warp_row_solve(const double *RTs, int me, int m, double (&x)[K]) {
     const int lane = threadIdx.x & 31;
     const int ka = (me + 31) >> 5;
-    auto load = [&](double (&bv)[K], double &r, int j) {
+    auto load = [&](double (&bv)[K], int j) {
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) {
             const int l = lane + 32 * kk;
-            bv[kk] = (j < me && kk < ka && l > j && l < me) ? RT[(int64_t)j * m + l] : 0.0;
+            bv[kk] = (j < me && kk < ka && l > j && l < me) ? RTs[(int64_t)j * m + l] : 0.0;
         }
-        r = j < me ? rinv[j] : 0.0;
     };
-    auto step = [&](const double (&bv)[K], double r, int j) {
-        if (j >= me) return;
-        const int k0 = j >> 5, L = j & 31;
-        double tj = __shfl_sync(0xffffffffu, hsel(x, k0), L);
-        if (EST) tj += (tj < 0.0) ? -1.0 : 1.0;
-        const double xj = tj * r;
+    double b0[K], b1[K], b2[K], b3[K];
+    load(b0, 0);
+    load(b1, 1);
+    load(b2, 2);
+    load(b3, 3);
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-            if (kk >= k0 && kk < ka) {
-                const int l = lane + 32 * kk;
-                if (l > j) x[kk] = fma(-xj, bv[kk], x[kk]);
-                else if (l == j) x[kk] = xj;
-            }
+    for (int k0 = 0; k0 < K; ++k0) {
+        if (k0 >= ka) break;
+        auto step = [&](const double (&bv)[K], int L) {
+            const int j = 32 * k0 + L;
+            double tj = __shfl_sync(0xffffffffu, x[k0], L);
+            if (EST) tj += (tj < 0.0) ? -1.0 : 1.0;
+            const int l0 = lane + 32 * k0;
+            if (l0 == j) x[k0] = tj;
+            else if (l0 > j) x[k0] = fma(-tj, bv[k0], x[k0]);
+#pragma unroll
+            for (int kk = k0 + 1; kk < K; ++kk)
+                if (kk < ka) x[kk] = fma(-tj, bv[kk], x[kk]);
+        };
+        for (int L = 0; L < 32; L += 4) {
+            const int j = 32 * k0 + L;
+            if (j >= me) break;
+            step(b0, L);
+            load(b0, j + 4);
+            if (j + 1 >= me) break;
+            step(b1, L + 1);
+            load(b1, j + 5);
+            if (j + 2 >= me) break;
+            step(b2, L + 2);
+            load(b2, j + 6);
+            if (j + 3 >= me) break;
+            step(b3, L + 3);
+            load(b3, j + 7);
         }
-    };
-    double b0[K], b1[K], b2[K], r0, r1, r2;
-    load(b0, r0, 0);
-    load(b1, r1, 1);
-    load(b2, r2, 2);
-    for (int j = 0; j < me; j += 3) {
-        step(b0, r0, j);
-        load(b0, r0, j + 3);
-        step(b1, r1, j + 1);
-        load(b1, r1, j + 4);
-        step(b2, r2, j + 2);
-        load(b2, r2, j + 5);
     }
 }
 
-// R y = x in place: y_p = x_p / R_pp, then x_i -= R_ip y_p for i < p,
-// column p of R read from Rc.
+// Rcs y' = x with y' = D y, i.e. R y = x, in place (x' on exit: the caller
+// scales by 1 / R_pp): y'_p = x_p, then x_i -= Rcs_ip y'_p for i < p.
 template <int K>
-__device__ void warp_back_solve(const double *Rc, const double *rinv, int me, int m, double (&x)[K]) {
+__device__ void warp_back_solve(const double *Rcs, int me, int m, double (&x)[K]) {
     const int lane = threadIdx.x & 31;
     const int ka = (me + 31) >> 5;
-    auto load = [&](double (&bv)[K], double &r, int p) {
+    auto load = [&](double (&bv)[K], int p) {
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) {
             const int i = lane + 32 * kk;
-            bv[kk] = (p >= 0 && kk < ka && i < p) ? Rc[i + (int64_t)p * m] : 0.0;
+            bv[kk] = (p >= 0 && p < me && kk < ka && i < p) ? Rcs[i + (int64_t)p * m] : 0.0;
         }
-        r = p >= 0 ? rinv[p] : 0.0;
     };
-    auto step = [&](const double (&bv)[K], double r, int p) {
-        if (p < 0) return;
-        const int k0 = p >> 5, L = p & 31;
-        const double yp = __shfl_sync(0xffffffffu, hsel(x, k0), L) * r;
+    double b0[K], b1[K], b2[K], b3[K];
+    const int top = 32 * ka - 1;   // ring position of p is (top - p) mod 4
+    load(b0, top);
+    load(b1, top - 1);
+    load(b2, top - 2);
+    load(b3, top - 3);
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-            if (kk <= k0) {
-                const int i = lane + 32 * kk;
-                if (i < p) x[kk] = fma(-bv[kk], yp, x[kk]);
-                else if (i == p) x[kk] = yp;
+    for (int k0 = K - 1; k0 >= 0; --k0) {
+        if (k0 < ka) {
+            auto step = [&](const double (&bv)[K], int L) {
+                const int p = 32 * k0 + L;
+                if (p >= me) return;
+                const double yp = __shfl_sync(0xffffffffu, x[k0], L);
+                const int i0 = lane + 32 * k0;
+                if (i0 < p) x[k0] = fma(-bv[k0], yp, x[k0]);
+#pragma unroll
+                for (int kk = 0; kk < k0; ++kk) x[kk] = fma(-bv[kk], yp, x[kk]);
+            };
+            for (int L = 31; L >= 0; L -= 4) {
+                const int p = 32 * k0 + L;
+                step(b0, L);
+                load(b0, p - 4);
+                step(b1, L - 1);
+                load(b1, p - 5);
+                step(b2, L - 2);
+                load(b2, p - 6);
+                step(b3, L - 3);
+                load(b3, p - 7);
             }
         }
-    };
-    double b0[K], b1[K], b2[K], r0, r1, r2;
-    load(b0, r0, me - 1);
-    load(b1, r1, me - 2);
-    load(b2, r2, me - 3);
-    for (int p = me - 1; p >= 0; p -= 3) {
-        step(b0, r0, p);
-        load(b0, r0, p - 3);
-        step(b1, r1, p - 1);
-        load(b1, r1, p - 4);
-        step(b2, r2, p - 2);
-        load(b2, r2, p - 5);
     }
 }
 
@@ -486,26 +506,36 @@ __device__ __forceinline__ double warp_sumsq(const double (&x)[K]) {
     return v;
 }
 
-// R_11 in compact form: Rc (column-major) and RT (row-major), ld m, upper
-// triangle with the diagonal; rinv = 1 / R_jj (0 for a zero pivot, which
-// sets qstate[7]).
+// R_11 in compact form: RT (row-major), RTs = D^{-1} R (row-major) and
+// Rcs = R D^{-1} (column-major), ld m, upper triangles with the diagonal;
+// rinv = 1 / R_jj (0 for a zero pivot, which sets qstate[7]); cn2[q] =
+// ||R(:, q)||^2 (thread q, in row order).
 __global__ void __launch_bounds__(kThreads) k_r_pack(TailCtx c) {
     const int me = c.iscal[1];
     const int m = c.m;
     const int64_t tot = (int64_t)me * me;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t idx = gid; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(idx % me), q = (int)(idx / me);
-        double v = 0.0;
-        if (i < q) {
-            v = c.Aw[i + (int64_t)q * c.s];
-        } else if (i == q) {
-            v = c.Rdiag[q];
-            c.rinv[q] = v != 0.0 ? 1.0 / v : 0.0;
-            if (!(v != 0.0)) c.qstate[7] = 1.0;
+        double v = 0.0, vr = 0.0, vc = 0.0;
+        if (i <= q) {
+            v = i < q ? c.Aw[i + (int64_t)q * c.s] : c.Rdiag[q];
+            const double di = c.Rdiag[i], dq = c.Rdiag[q];
+            vr = di != 0.0 ? v / di : 0.0;
+            vc = dq != 0.0 ? v / dq : 0.0;
         }
-        c.Rc[i + (int64_t)q * m] = v;
         c.RT[q + (int64_t)i * m] = v;
+        c.RTs[q + (int64_t)i * m] = vr;
+        c.Rcs[i + (int64_t)q * m] = vc;
+    }
+    if (gid < me) {
+        const int q = (int)gid;
+        const double d = c.Rdiag[q];
+        c.rinv[q] = d != 0.0 ? 1.0 / d : 0.0;
+        if (!(d != 0.0)) c.qstate[7] = 1.0;
+        double a2 = 0.0;
+        for (int i = 0; i < q; ++i) a2 = fma(c.Aw[i + (int64_t)q * c.s], c.Aw[i + (int64_t)q * c.s], a2);
+        c.cn2[q] = fma(d, d, a2);
     }
 }
 
@@ -532,31 +562,26 @@ __global__ void __launch_bounds__(64) k_tri_right(TailCtx c, int nblk_rows) {
             for (int kk = 0; kk < K; ++kk) z[kk] = 0.0;
             double r = INFINITY;
             if (!zp && me > 0) {
-                warp_row_solve<K, true>(c.RT, c.rinv, me, m, z);
+                warp_row_solve<K, true>(c.RTs, me, m, z);   // z' = D z, R^T z = b
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const int i = lane + 32 * kk;
+                    z[kk] = (kk < ka && i < me) ? z[kk] * c.rinv[i] : 0.0;
+                }
                 const double zn = warp_sumsq(z);
-                warp_back_solve<K>(c.Rc, c.rinv, me, m, z);
+                warp_back_solve<K>(c.Rcs, me, m, z);         // y' = D y, R y = z
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const int i = lane + 32 * kk;
+                    z[kk] = (kk < ka && i < me) ? z[kk] * c.rinv[i] : 0.0;
+                }
                 const double yn = warp_sumsq(z);
                 r = zn > 0.0 ? sqrt(yn / zn) : 0.0;
             }
             if (lane == 0) res[0] = r;
         } else {
-            // column norms of R, lanes over columns, rows of RT in turn
-            double a2[K];
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) a2[kk] = 0.0;
-            for (int i = 0; i < me; ++i) {
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    const int q = lane + 32 * kk;
-                    if (kk < ka && q >= i && q < me) {
-                        const double v = c.RT[(int64_t)i * m + q];
-                        a2[kk] = fma(v, v, a2[kk]);
-                    }
-                }
-            }
             double mx = 0.0;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) mx = fmax(mx, a2[kk]);
+            for (int q = lane; q < me; q += 32) mx = fmax(mx, c.cn2[q]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             if (lane == 0) res[1] = sqrt(mx);
@@ -604,12 +629,12 @@ __global__ void __launch_bounds__(64) k_tri_right(TailCtx c, int nblk_rows) {
         }
         x[kk] = tv;
     }
-    warp_row_solve<K, false>(c.RT, c.rinv, me, m, x);
+    warp_row_solve<K, false>(c.RTs, me, m, x);
     double *dst = second ? c.R2 : c.M;
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
         const int j = lane + 32 * kk;
-        if (kk < ka && j < me) dst[a + (int64_t)j * m] = x[kk];
+        if (kk < ka && j < me) dst[a + (int64_t)j * m] = x[kk] * c.rinv[j];
     }
 }
 
@@ -1169,11 +1194,14 @@ __global__ void __launch_bounds__(kNodeThreads) k_nodes_g(TailCtx c, int n0, int
 // j = 0, 1, ... (row j+1 of t I + M is read when it enters; the rotated row j
 // is final), rotating c along, then solves the triangle by column-oriented
 // back substitution: a backward stable QR solve in FP64, without normal
-// equations or refinement, O(m^2) work per node.  The rows of the triangle
-// go to the node's scratch slot in packed column-major order (column q at
-// q (q + 1) / 2, rows 0 .. q, the diagonal slot holding 1 / R_qq) so that the
-// back substitution reads each column contiguously.  Lane l holds columns
-// (and rows) l, l + 32, ... in K register groups.
+// equations or refinement, O(m^2) work per node.  Row j of the triangle is
+// stored divided by its diagonal (R_jj = r = (a^2 + b^2)^{1/2}, so the stored
+// row is (a x + b y) / r^2 and the right-hand side entry c_j / r), which gives
+// the back substitution a unit diagonal; the rows go to the node's scratch
+// slot in packed column-major order (column q at q (q + 1) / 2, rows 0 .. q-1)
+// so that the back substitution reads each column contiguously.  Lane l holds
+// columns (and rows) l, l + 32, ... in K register groups; the loops over the
+// groups are unrolled, so the pivot's register is known at compile time.
 constexpr int kHessWarps = 4;   // nodes (warps) per CTA
 
 template <int K>
@@ -1204,95 +1232,107 @@ __global__ void __launch_bounds__(32 * kHessWarps) k_nodes_hess(TailCtx c, int n
     }
     double gc = c.cvec[0];   // the rotated right-hand side below the rows done
     bool bad = false;
-    for (int j = 0; j < me; ++j) {
-        const int k0 = j >> 5, L = j & 31;
-        const bool enter = j + 1 < me || gm;
-        if (j + 1 < me) {   // shift of row j + 1
-            const int k1 = (j + 1) >> 5;
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk)
-                if (kk == k1) nw[kk] += (lane == ((j + 1) & 31)) ? t : 0.0;
-        } else if (gm) {    // the row gamma e_m^T of the sGMRES problem
+    for (int k0 = 0; k0 < K; ++k0) {
+        if (k0 >= ka) break;
+        for (int L = 0; L < 32; ++L) {
+            const int j = 32 * k0 + L;
+            if (j >= me) break;
+            const bool enter = j + 1 < me || gm;
+            if (j + 1 < me) {   // shift of row j + 1
+                if (L < 31) nw[k0] += (lane == L + 1) ? t : 0.0;
+                else if (k0 + 1 < K) nw[k0 + 1] += (lane == 0) ? t : 0.0;
+            } else if (gm) {    // the row gamma e_m^T of the sGMRES problem
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) nw[kk] = (lane + 32 * kk == me - 1) ? gam : 0.0;
-        }
-        // row j + 2 of M (columns >= j + 1), for the next step
-        double pf[K];
+                for (int kk = 0; kk < K; ++kk) nw[kk] = (lane + 32 * kk == me - 1) ? gam : 0.0;
+            }
+            // row j + 2 of M (columns > j), for the next step
+            double pf[K];
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-            const int col = lane + 32 * kk;
-            pf[kk] = (kk < ka && j + 2 < me && col > j && col < me) ? __ldg(MT + (size_t)(j + 2) * m + col) : 0.0;
-        }
-        double a = hsel(cr, k0), b = hsel(nw, k0);
-        a = __shfl_sync(0xffffffffu, a, L);
-        b = __shfl_sync(0xffffffffu, b, L);
-        double cs = 1.0, sn = 0.0, rinv = 0.0;
-        if (enter) {
-            const double q = fma(a, a, b * b);
-            if (q > 0.0 && q < INFINITY) {
-                const double ri = rsqrt(q);   // r = q ri = R_jj
-                cs = a * ri;
-                sn = b * ri;
-                rinv = ri;
+            for (int kk = 0; kk < K; ++kk) {
+                const int col = lane + 32 * kk;
+                pf[kk] = (kk >= k0 && kk < ka && j + 2 < me && col > j && col < me)
+                             ? __ldg(MT + (size_t)(j + 2) * m + col) : 0.0;
+            }
+            const double a = __shfl_sync(0xffffffffu, cr[k0], L);
+            const double b = __shfl_sync(0xffffffffu, nw[k0], L);
+            double cs = 1.0, sn = 0.0, cs2 = 0.0, sn2 = 0.0, ri = 0.0;
+            if (enter) {
+                const double q = fma(a, a, b * b);
+                if (q > 0.0 && q < INFINITY) {
+                    ri = rsqrt(q);   // 1 / R_jj
+                    cs = a * ri;
+                    sn = b * ri;
+                    cs2 = cs * ri;
+                    sn2 = sn * ri;
+                } else {
+                    bad = true;
+                }
+            } else if (a != 0.0 && fabs(a) < INFINITY) {   // sFOM, last row: R_jj = a
+                ri = 1.0 / a;
+                cs2 = ri;
             } else {
                 bad = true;
             }
-        } else if (a != 0.0 && fabs(a) < INFINITY) {   // sFOM, last row: R_jj = a
-            rinv = 1.0 / a;
-        } else {
-            bad = true;
-        }
-        // row j of R and the rotated carried row (columns >= j)
+            // row j of R / R_jj and the rotated carried row (columns > j);
+            // the group of column j + 1 first
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-            if (kk >= k0 && kk < ka) {
-                const int col = lane + 32 * kk;
-                if (col >= j && col < me) {
-                    const double rj = fma(cs, cr[kk], sn * nw[kk]);
-                    cr[kk] = fma(cs, nw[kk], -(sn * cr[kk]));
-                    R[(size_t)col * (col + 1) / 2 + j] = (col == j) ? rinv : rj;
+            for (int kk = k0; kk < K; ++kk) {
+                if (kk < ka) {
+                    const int col = lane + 32 * kk;
+                    if (col > j && col < me) {
+                        const double rj = fma(cs2, cr[kk], sn2 * nw[kk]);
+                        cr[kk] = fma(cs, nw[kk], -(sn * cr[kk]));
+                        R[(size_t)col * (col + 1) / 2 + j] = rj;
+                    }
                 }
             }
+            u[k0] = (lane == L) ? cs * gc * ri : u[k0];
+            gc = -sn * gc;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) nw[kk] = pf[kk];
         }
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk)
-            if (kk == k0) u[kk] = (lane == L) ? cs * gc : u[kk];
-        gc = -sn * gc;
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) nw[kk] = pf[kk];
     }
     __syncwarp();
-    // R y = u, column by column from the last; column j - 1 is loaded while
-    // column j is applied
-    double cur[K];
-#pragma unroll
-    for (int kk = 0; kk < K; ++kk) {
-        const int i = lane + 32 * kk;
-        cur[kk] = (kk < ka && i < me - 1) ? R[(size_t)(me - 1) * me / 2 + i] : 0.0;
-    }
-    double rj = R[(size_t)(me - 1) * me / 2 + me - 1];
-    for (int j = me - 1; j >= 0; --j) {
-        const int k0 = j >> 5, L = j & 31;
-        double nx[K];
+    // R y = u with the unit-diagonal rows: y_p = u_p, then u_i -= R_ip y_p for
+    // i < p; column p - 4 is loaded while column p is applied
+    auto load = [&](double (&bv)[K], int p) {
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) {
             const int i = lane + 32 * kk;
-            nx[kk] = (kk <= k0 && j >= 1 && i < j - 1) ? R[(size_t)(j - 1) * j / 2 + i] : 0.0;
+            bv[kk] = (p >= 0 && p < me && kk < ka && i < p) ? R[(size_t)p * (p + 1) / 2 + i] : 0.0;
         }
-        const double rn = j >= 1 ? R[(size_t)(j - 1) * j / 2 + j - 1] : 0.0;
-        double yj = hsel(u, k0);
-        yj = __shfl_sync(0xffffffffu, yj, L) * rj;
+    };
+    double b0[K], b1[K], b2[K], b3[K];
+    const int top = 32 * ka - 1;
+    load(b0, top);
+    load(b1, top - 1);
+    load(b2, top - 2);
+    load(b3, top - 3);
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-            if (kk <= k0) {
-                const int i = lane + 32 * kk;
-                if (i < j) u[kk] = fma(-cur[kk], yj, u[kk]);
-                else if (i == j) u[kk] = yj;
+    for (int k0 = K - 1; k0 >= 0; --k0) {
+        if (k0 < ka) {
+            auto step = [&](const double (&bv)[K], int L) {
+                const int p = 32 * k0 + L;
+                if (p >= me) return;
+                const double yp = __shfl_sync(0xffffffffu, u[k0], L);
+                const int i0 = lane + 32 * k0;
+                if (i0 < p) u[k0] = fma(-bv[k0], yp, u[k0]);
+#pragma unroll
+                for (int kk = 0; kk < k0; ++kk) u[kk] = fma(-bv[kk], yp, u[kk]);
+            };
+            for (int L = 31; L >= 0; L -= 4) {
+                const int p = 32 * k0 + L;
+                step(b0, L);
+                load(b0, p - 4);
+                step(b1, L - 1);
+                load(b1, p - 5);
+                step(b2, L - 2);
+                load(b2, p - 6);
+                step(b3, L - 3);
+                load(b3, p - 7);
             }
         }
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) cur[kk] = nx[kk];
-        rj = rn;
     }
     bad = __any_sync(0xffffffffu, bad);
 #pragma unroll
@@ -1389,23 +1429,42 @@ __global__ void __launch_bounds__(kNodeThreads) k_nodes_cplx(TailCtx c, int n0, 
         c.out[(size_t)row * m + a] = wr * (y[a] + g[a]) - wim * (y[me + a] + g[me + a]);
 }
 
-// Sum the node solutions of each level of the batch, then run the
-// acceptance test of Sec. 4.1 level by level.  One CTA.
+// Sum the node solutions of each level of the batch (CTA i: level lev0 + i,
+// four interleaved partial sums over its nodes, added in a fixed order), then
+// the last CTA to finish runs the acceptance test of Sec. 4.1 level by level.
 __global__ void __launch_bounds__(kThreads) k_levels(TailCtx c, int lev0, int nlev, const int *lev_start,
                                                      const int *lev_ell, int n0, double tol, int last_batch) {
     __shared__ double red[64];
+    __shared__ int is_last;
     const int me = c.iscal[1];
     if (c.qstate[0] != 0.0 || me == 0) return;
     const int m = c.m;
-    for (int l = lev0; l < lev0 + nlev; ++l) {
+    {
+        const int l = lev0 + (int)blockIdx.x;
         const int a0 = lev_start[l] - n0, a1 = lev_start[l + 1] - n0;
         double *ql = c.qbuf + (size_t)l * m;
         for (int a = threadIdx.x; a < me; a += blockDim.x) {
-            double acc = 0.0;
-            for (int nd = a0; nd < a1; ++nd) acc += c.out[(size_t)nd * m + a];
-            ql[a] = acc;
+            double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+            int nd = a0;
+            for (; nd + 3 < a1; nd += 4) {
+                p0 += c.out[(size_t)nd * m + a];
+                p1 += c.out[(size_t)(nd + 1) * m + a];
+                p2 += c.out[(size_t)(nd + 2) * m + a];
+                p3 += c.out[(size_t)(nd + 3) * m + a];
+            }
+            for (; nd < a1; ++nd) p0 += c.out[(size_t)nd * m + a];
+            ql[a] = (p0 + p1) + (p2 + p3);
         }
-        __syncthreads();
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(c.lev_cnt, 1u) == (unsigned)(nlev - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) *c.lev_cnt = 0u;   // ready for the next batch
+    for (int l = lev0; l < lev0 + nlev; ++l) {
+        const double *ql = c.qbuf + (size_t)l * m;
         bool accept = false;
         double rel = 0.0;
         if (c.nlevels == 1) {
@@ -1414,9 +1473,10 @@ __global__ void __launch_bounds__(kThreads) k_levels(TailCtx c, int lev0, int nl
             const double *qp = c.qbuf + (size_t)(l - 1) * m;
             double v[2] = {0.0, 0.0};
             for (int a = threadIdx.x; a < me; a += blockDim.x) {
-                const double d = ql[a] - qp[a];
+                const double qa = __ldcg(ql + a);
+                const double d = qa - __ldcg(qp + a);
                 v[0] = fma(d, d, v[0]);
-                v[1] = fma(ql[a], ql[a], v[1]);
+                v[1] = fma(qa, qa, v[1]);
             }
             block_sum<2>(v, red);
             __shared__ double sv2[2];
@@ -1427,7 +1487,7 @@ __global__ void __launch_bounds__(kThreads) k_levels(TailCtx c, int lev0, int nl
         }
         const bool final_level = last_batch && (l == lev0 + nlev - 1);
         if (accept || final_level) {
-            for (int a = threadIdx.x; a < me; a += blockDim.x) c.qacc[a] = ql[a];
+            for (int a = threadIdx.x; a < me; a += blockDim.x) c.qacc[a] = __ldcg(ql + a);
             if (threadIdx.x == 0) {
                 c.qstate[0] = 1.0;
                 c.qstate[1] = (double)lev_ell[l];
@@ -1452,11 +1512,11 @@ __global__ void __launch_bounds__(32) k_coeffs(TailCtx c) {
     double x[K];
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) x[kk] = (lane + 32 * kk < me) ? c.qacc[lane + 32 * kk] : 0.0;
-    if (!zero_pivot) warp_back_solve<K>(c.Rc, c.rinv, me, c.m, x);
+    if (!zero_pivot) warp_back_solve<K>(c.Rcs, me, c.m, x);
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
         const int i = lane + 32 * kk;
-        if (i < me) c.z[i] = zero_pivot ? 0.0 : c.vscale[i] * x[kk];
+        if (i < me) c.z[i] = zero_pivot ? 0.0 : c.vscale[i] * (x[kk] * c.rinv[i]);
     }
     if (lane == 0 && me > 0 && c.iscal[2] == SKF_OK &&
         (zero_pivot || (c.cond_max > 0.0 && c.qstate[5] > c.cond_max)))
@@ -1683,7 +1743,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                             sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
                             sizeof(double) * 8, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
                             sizeof(double) * 2 * (size_t)m, sizeof(unsigned) * 4, sizeof(double) * mm,
-                            sizeof(double) * mm, sizeof(double) * m};
+                            sizeof(double) * mm, sizeof(double) * m, sizeof(double) * mm, sizeof(double) * m};
     constexpr int kNbuf = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
     for (size_t v : sizes) total += al(v);
@@ -1701,9 +1761,12 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     c.z = ptrs[12]; c.qstate = ptrs[13]; c.MT = ptrs[14]; c.R2T = ptrs[15]; c.nodebad = (int *)ptrs[16];
     c.hsig = ptrs[17];
     unsigned *qr_ready = (unsigned *)ptrs[18];   // [0] published pivot columns, [1] timeout flag
-    c.Rc = ptrs[19];
-    c.RT = ptrs[20];
+    c.RT = ptrs[19];
+    c.RTs = ptrs[20];
     c.rinv = ptrs[21];
+    c.Rcs = ptrs[22];
+    c.cn2 = ptrs[23];
+    c.lev_cnt = qr_ready + 2;
 
     const int G = std::min(2 * num_sms(), 1024);
     long long nlaunch = 0;
@@ -1814,7 +1877,7 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
             }
             nlaunch += 2;
         }
-        k_levels<<<1, kThreads, 0, st>>>(c, l0, nl, rule.lev_start, rule.lev_ell, n0, tol,
+        k_levels<<<(unsigned)nl, kThreads, 0, st>>>(c, l0, nl, rule.lev_start, rule.lev_ell, n0, tol,
                                          bi + 1 == batches.size() ? 1 : 0);
         ++nlaunch;
     }
