@@ -8,9 +8,12 @@ N(0,1) right-hand side normalised, f(z) = log(1+z)/z, m = 200, k = 2,
 sparse-sign sketch s = 800, zeta = 8.
 
 One step = one pass of the whole path over one right-hand side through the
-public API: skf_sfom and skf_sgmres (each: truncated Arnoldi with fused
-sketches, whitening QR, adaptive quadrature, V_m y).  value = solves/s over
-all GPUs (2 solves per step per GPU).  Under torchrun each rank runs an
+public API: skf_sfom_sgmres, both approximants of f(A) b from one truncated
+Arnoldi process with fused sketches (the basis both methods use, as in the
+reference arm's pair), one whitening QR, both adaptive-quadrature tails and
+one pass over V_m for both recombinations (--separate: skf_sfom and
+skf_sgmres, two Arnoldi processes).  value = solves/s over all GPUs (2
+solves per step per GPU).  Under torchrun each rank runs an
 independent replica (the path has no data-path exchange; scaling "weak").
 Rank 0 prints one JSON line.
 """
@@ -31,9 +34,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_PEAK_FALLBACK = 6800.0
-# FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA
-# throughput on this part: 1.20 TFLOP/s, i.e. the same unit count).
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes (read + write) per Arnoldi step, summed over the spmv and update
 # kernels of one ncu capture of those kernels as they stand; keyed by workload,
 # basis dtype and sketch, and removed whenever those kernels change.
@@ -673,6 +673,9 @@ def main():
                          "batch: the batched workload (8 operators, 64 right-hand sides) as one CUDA graph")
     ap.add_argument("--lanes", default="auto",
                     help="concurrent streams of the batched solve (batch mode): a count, or auto (timed choice of 4/8/16)")
+    ap.add_argument("--separate", action="store_true",
+                    help="time each pair as two independent solves (skf_sfom + skf_sgmres, two Arnoldi processes) "
+                         "instead of skf_sfom_sgmres")
     ap.add_argument("--two-pass", action="store_true",
                     help="two-pass truncated Arnoldi (Sec. 4.2): basis ring of k + 2 vectors, twice the SpMVs")
     ap.add_argument("--batch-rhs", type=int, default=64, help="right-hand sides of the batched workload")
@@ -746,9 +749,20 @@ def main():
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
 
+    # one pair = both approximants of f(A) b; they share one Arnoldi process
+    # (skf_sfom_sgmres), as the reference arm's pair does, unless --separate
+    # (or the two-pass mode, which the pair call does not offer)
+    paired = not (args.separate or args.two_pass)
+
+    def solve_pair(bv):
+        if paired:
+            skf.sfom_sgmres(op.csr, S, bv, f, p, x_fom=x_fom, x_gmres=x_gm, info_fom=info_f, info_gmres=info_g)
+        else:
+            skf.sfom(op.csr, S, bv, f, p, x=x_fom, info=info_f)
+            skf.sgmres(op.csr, S, bv, f, p, x=x_gm, info=info_g)
+
     def step():
-        skf.sfom(op.csr, S, b_dev, f, p, x=x_fom, info=info_f)
-        skf.sgmres(op.csr, S, b_dev, f, p, x=x_gm, info=info_g)
+        solve_pair(b_dev)
 
     for _ in range(args.warmup):
         step()
@@ -806,14 +820,15 @@ def main():
     alg_bytes = nnz * (bv + 4) + 4 * (N + 1) + (k + 1) * N * bb      # per step: A once, window, new vector
     alg_flops = 2 * nnz + (4 * k + 3) * N                             # SpMV + k dots + k axpys + norm + scale
     hbm_peak, hbm_src = measured_peaks()
+    fp64_peak = skf.fp64_peak(stream)   # measured FMA throughput of this GPU (outside the timed region)
     achieved_gflops = alg_flops / (step_us * 1e-6) / 1e9
     achieved_gbs = alg_bytes / (step_us * 1e-6) / 1e9
-    fp64_bound_us = alg_flops / (FP64_PEAK_GFLOPS * 1e9) * 1e6
+    fp64_bound_us = alg_flops / (fp64_peak * 1e9) * 1e6
     hbm_bound_us = alg_bytes / (hbm_peak * 1e9) * 1e6
     if basis == "f64" and fp64_bound_us >= hbm_bound_us:
-        roof = {"bound": "alu", "achieved": round(achieved_gflops, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
-                "unit": "GFLOP/s", "frac": round(achieved_gflops / FP64_PEAK_GFLOPS, 4), "traffic": None,
-                "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)"}
+        roof = {"bound": "alu", "achieved": round(achieved_gflops, 1), "peak": round(fp64_peak, 1),
+                "unit": "GFLOP/s", "frac": round(achieved_gflops / fp64_peak, 4), "traffic": None,
+                "peak_source": "measured: skf_fp64_peak (independent FP64 FMA chains on every SM, this run)"}
     else:
         roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src}
@@ -842,8 +857,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b_e2e.copy_(b_host, non_blocking=True)
-        skf.sfom(op.csr, S, b_e2e, f, p, x=x_fom, info=info_f)
-        skf.sgmres(op.csr, S, b_e2e, f, p, x=x_gm, info=info_g)
+        solve_pair(b_e2e)
         xf_host.copy_(x_fom, non_blocking=True)
         xg_host.copy_(x_gm, non_blocking=True)
         torch.cuda.synchronize()
@@ -887,6 +901,9 @@ def main():
                                                                                      st_g["status_name"]],
                        "basis": basis, "values": "f64" if A.values.dtype == np.float64 else "f32",
                        "two_pass": bool(args.two_pass),
+                       "pair": ("skf_sfom_sgmres: one Arnoldi process, one whitening QR, both tails, one pass "
+                                "over V_m for both recombinations" if paired else
+                                "skf_sfom + skf_sgmres: two Arnoldi processes"),
                        "basis_bytes": int(BASIS_BYTES[basis] * ((A.n + 63) // 64 * 64)
                                           * (min(wl.m, wl.k + 2) if args.two_pass else wl.m))},
             "accuracy": accuracy,

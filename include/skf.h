@@ -241,6 +241,13 @@ skf_status skf_set_arnoldi_mode(int32_t mode);
  * Returns INVALID_ARG for another mode. */
 skf_status skf_set_qr_mode(int32_t mode);
 
+/* skf_fp64_peak: measured FP64 FMA throughput of the current device in
+ * GFLOP/s (2 flops per FMA): two CTAs of 512 threads per SM, eight
+ * independent FMA chains per thread, 4096 iterations, timed with events on
+ * `stream` after one warm-up launch (synchronises the stream).  The
+ * denominator of the FP64 roofline fraction.  Errors: INVALID_ARG, OOM, CUDA. */
+skf_status skf_fp64_peak(double *gflops, skf_stream_t stream);
+
 /* skf_workspace_trim: return the device memory that the library's
  * workspace pools keep mapped between calls.  Each solve takes its
  * stream-ordered workspace (about 8 m N bytes for an F64 basis, plus O(s m)
@@ -399,8 +406,10 @@ skf_status skf_arnoldi_trunc(const skf_csr *A, const skf_sketch *S, const void *
  * SKF_ERR_QUAD_NOT_CONVERGED (the rule does not settle), with x from the
  * last order.  sGMRES solves least-squares problems, which stay defined.
  *   b  device F64 [N];   x  device F64 [N] (output)
- *   workspace is allocated stream-ordered (cudaMallocAsync) and released
- *   before return, so the call can be captured into a CUDA graph.
+ *   workspace is taken stream-ordered from the library's pool (cached
+ *   between calls, see skf_workspace_trim) and released before return; under
+ *   stream capture it comes from the graph's memory nodes, so the call can be
+ *   captured into a CUDA graph.
  * Errors: INVALID_ARG, OOM, CUDA, SKETCH_TOO_SMALL, NOT_SUPPORTED. */
 skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, const void *b,
                      skf_dtype bdtype, const skf_func *f, const skf_params *p, void *x, skf_dtype xdtype,
@@ -413,6 +422,20 @@ skf_status skf_sfom(const skf_csr *A, const skf_sketch *S, const void *b, skf_dt
 skf_status skf_sgmres(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype,
                       const skf_func *f, const skf_params *p, void *x, skf_dtype xdtype, skf_info *info,
                       skf_stream_t stream);
+
+/* skf_sfom_sgmres: both approximants of the same f(A) b, which share one
+ * truncated Arnoldi process (V_m, S V_m, S A V_m and H are the same for the
+ * two methods, Sec. 3): one Arnoldi run, one whitening QR (with M, cond(R)
+ * and, in the relation form, gamma), then each method's quadrature tail, and
+ * both recombinations x = V_m z in one pass over V_m.  Each result equals
+ * the corresponding skf_sfom / skf_sgmres call bit for bit.  Arguments as
+ * skf_solve (s >= 2m as for SGMRES); x_fom, x_gmres: device F64 [N];
+ * info_fom, info_gmres nullable.  The stopping criterion (check_every > 0)
+ * and the two-pass mode are not offered here (NOT_SUPPORTED).
+ * Errors: INVALID_ARG, OOM, CUDA, SKETCH_TOO_SMALL, NOT_SUPPORTED. */
+skf_status skf_sfom_sgmres(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype,
+                           const skf_func *f, const skf_params *p, void *x_fom, void *x_gmres, skf_dtype xdtype,
+                           skf_info *info_fom, skf_info *info_gmres, skf_stream_t stream);
 
 /* ------------------------------------------------------------- batches */
 /* One independent problem of a batch: the arguments of one skf_solve call. */

@@ -107,6 +107,8 @@ def lib():
         L.skf_solve.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int, ctypes.POINTER(Func),
                                 ctypes.POINTER(Params), vp, ctypes.c_int, vp, vp]
         L.skf_sfom.argtypes = L.skf_solve.argtypes[1:]
+        L.skf_sfom_sgmres.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(Func), ctypes.POINTER(Params), vp, vp,
+                                      ctypes.c_int, vp, vp, vp]
         L.skf_sgmres.argtypes = L.skf_solve.argtypes[1:]
         L.skf_quadrature_rule.argtypes = [ctypes.POINTER(Func), i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
         L.skf_quadrature_rule_c.argtypes = [ctypes.POINTER(Func), i32] + [ctypes.POINTER(dbl)] * 4
@@ -115,12 +117,13 @@ def lib():
         L.skf_set_qr_mode.argtypes = [i32]
         L.skf_set_tail_form.argtypes = [i32]
         L.skf_workspace_trim.argtypes = []
+        L.skf_fp64_peak.argtypes = [ctypes.POINTER(dbl), vp]
         L.skf_barrier_selftest.argtypes = [i32, i64, vp, vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
-                     "skf_solve", "skf_solve_batched", "skf_sfom",
+                     "skf_solve", "skf_solve_batched", "skf_sfom", "skf_sfom_sgmres",
                      "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c", "skf_set_arnoldi_mode",
-                     "skf_set_qr_mode", "skf_set_tail_form", "skf_workspace_trim", "skf_barrier_selftest"]:
+                     "skf_set_qr_mode", "skf_set_tail_form", "skf_workspace_trim", "skf_fp64_peak", "skf_barrier_selftest"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -315,6 +318,19 @@ def sgmres(A, S, b, f, p, x=None, info=None, stream=None):
     return solve(SGMRES, A, S, b, f, p, x, info, stream)
 
 
+def sfom_sgmres(A, S, b, f, p, x_fom=None, x_gmres=None, info_fom=None, info_gmres=None, stream=None):
+    """skf_sfom_sgmres: both approximants from one Arnoldi process.  Returns
+    (x_fom, x_gmres)."""
+    if x_fom is None:
+        x_fom = torch.empty_like(b)
+    if x_gmres is None:
+        x_gmres = torch.empty_like(b)
+    _check(lib().skf_sfom_sgmres(A.handle, S.handle, _ptr(b), _DTYPE[b.dtype], ctypes.byref(f), ctypes.byref(p),
+                                 _ptr(x_fom), _ptr(x_gmres), _DTYPE[x_fom.dtype], _ptr(info_fom), _ptr(info_gmres),
+                                 _stream(stream)))
+    return x_fom, x_gmres
+
+
 def solve_batched(problems, lanes: int = 4, stream=None):
     """skf_solve_batched.  problems: sequence of (method, A, S, b, f, p, x,
     info) with x a preallocated F64 tensor and info a buffer from new_info()
@@ -414,6 +430,13 @@ class qr_mode:
 
 
 TAIL_AUTO, TAIL_FULL = 0, 1
+
+
+def fp64_peak(stream=None) -> float:
+    """skf_fp64_peak: measured FP64 FMA throughput in GFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(lib().skf_fp64_peak(ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def workspace_trim() -> None:

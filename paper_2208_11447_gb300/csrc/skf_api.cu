@@ -753,6 +753,51 @@ skf_status skf_set_qr_mode(int32_t mode) {
     return SKF_OK;
 }
 
+// FP64 FMA throughput of this device: every SM runs 32 warps, each thread
+// eight independent FMA chains (enough to keep the FP64 units of all four
+// sub-partitions busy), timed with events.
+__global__ void __launch_bounds__(512) k_fp64_rate(double *sink, double a, double b, int iters) {
+    double x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = a + c * 1e-3 * threadIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = fma(x[c], b, a);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) t += x[c];
+    if (t == 12345.678) sink[0] = t;   // keeps the chains live; never true for these inputs
+}
+
+skf_status skf_fp64_peak(double *gflops, skf_stream_t stream) {
+    if (!gflops) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    double *sink = nullptr;
+    skf_status s = dalloc((void **)&sink, sizeof(double), st);
+    if (s != SKF_OK) return s;
+    const int grid = 2 * num_sms(), iters = 4096;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        dfree(sink, st);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    k_fp64_rate<<<grid, 512, 0, st>>>(sink, 0.5, 0.999, iters);   // warm-up
+    cudaEventRecord(e0, st);
+    k_fp64_rate<<<grid, 512, 0, st>>>(sink, 0.5, 0.999, iters);
+    cudaEventRecord(e1, st);
+    count_launches(2);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(sink, st);
+    if (e != cudaSuccess) return cuda_fail(e, "FP64 rate probe");
+    *gflops = 2.0 * 8.0 * iters * (double)grid * 512.0 / (ms * 1e-3) / 1e9;
+    return SKF_OK;
+}
+
 skf_status skf_workspace_trim(void) {
     std::lock_guard<std::mutex> lk(pool_mutex());
     for (auto &kv : pools()) {
@@ -998,6 +1043,58 @@ skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, c
     skf_status st = solve_check(method, A, S, b, bdtype, f, p, x, xdtype, &rule);
     if (st != SKF_OK) return st;
     return solve_enqueue(method, A, S, b, *p, x, info, *rule, (cudaStream_t)stream);
+}
+
+// Both methods on one Arnoldi process (skf_sfom_sgmres).
+static skf_status solve_enqueue_pair(const skf_csr *A, const skf_sketch *S, const void *b, const skf_params &p,
+                                     void *x_fom, void *x_gmres, skf_info *info_fom, skf_info *info_gmres,
+                                     const RuleDev &rule, cudaStream_t cs) {
+    const int m = p.m;
+    const int64_t n = A->n;
+    const int s = S->s;
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const skf_dtype bt = p.basis_dtype;
+    const int64_t ldv = (n + 63) / 64 * 64;   // 256-byte aligned columns
+    const size_t szV = dtype_size(bt) * (size_t)ldv * m;
+    const size_t szS = sizeof(double) * (size_t)s * m;
+    const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
+    const size_t total = al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + 2 * al(sizeof(int) * 4);
+    char *ws = nullptr;
+    skf_status st = dalloc((void **)&ws, total, cs);
+    if (st != SKF_OK) return st;
+    size_t off = 0;
+    void *V = (void *)(ws + off); off += al(szV);
+    double *SV = (double *)(ws + off); off += al(szS);
+    double *SAV = (double *)(ws + off); off += al(szS);
+    double *H = (double *)(ws + off); off += al(szH);
+    double *vscale = (double *)(ws + off); off += al(sizeof(double) * m);
+    int *iscal = (int *)(ws + off); off += al(sizeof(int) * 4);
+    int *iscal2 = (int *)(ws + off); off += al(sizeof(int) * 4);
+    st = run_arnoldi(A, S, (const double *)b, m, p.k, bt, V, ldv, vscale, SV, SAV, H, iscal, info_fom, cs, nullptr, 0);
+    if (st == SKF_OK) {
+        // the second method starts from the same Arnoldi record
+        cudaMemcpyAsync(iscal2, iscal, sizeof(int) * 4, cudaMemcpyDeviceToDevice, cs);
+        if (info_fom && info_gmres)
+            cudaMemcpyAsync(info_gmres, info_fom, sizeof(skf_info), cudaMemcpyDefault, cs);
+        TailOut outs[2] = {{SKF_METHOD_SFOM, (double *)x_fom, info_fom, nullptr, iscal},
+                           {SKF_METHOD_SGMRES, (double *)x_gmres, info_gmres, nullptr, iscal2}};
+        st = tail_run_multi(2, outs, s, m, n, V, bt, ldv, vscale, SV, SAV, rule, p.tol, cs, nullptr, nullptr,
+                            p.cond_max == 0.0 ? 1e12 : (p.cond_max < 0.0 ? 0.0 : p.cond_max), H, m + 1, p.k);
+    }
+    dfree(ws, cs);
+    return st;
+}
+
+skf_status skf_sfom_sgmres(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, const skf_func *f,
+                           const skf_params *p, void *x_fom, void *x_gmres, skf_dtype xdtype, skf_info *info_fom,
+                           skf_info *info_gmres, skf_stream_t stream) {
+    if (!x_gmres) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    const RuleDev *rule = nullptr;
+    skf_status st = solve_check(SKF_METHOD_SGMRES, A, S, b, bdtype, f, p, x_fom, xdtype, &rule);
+    if (st != SKF_OK) return st;
+    if (p->check_every > 0 || p->two_pass)
+        return fail(SKF_ERR_NOT_SUPPORTED, "the pair solve offers neither the stopping criterion nor two passes");
+    return solve_enqueue_pair(A, S, b, *p, x_fom, x_gmres, info_fom, info_gmres, *rule, (cudaStream_t)stream);
 }
 
 skf_status skf_solve_batched(int32_t nprob, const skf_problem *probs, int32_t lanes, skf_stream_t stream) {

@@ -480,6 +480,25 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
                     double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out = nullptr,
                     const double *stop_state = nullptr, double *z_out = nullptr, double cond_max = 0.0,
                     const double *H = nullptr, int ldh = 0, int kt = 0);
+// One method's outputs of a tail: the recombined f (nullable), the result
+// record (nullable), the coefficients (nullable) and its status words
+// (iscal[1] = m_eff is read, iscal[2] written).
+struct TailOut {
+    skf_method method;
+    double *x;
+    skf_info *info;
+    double *z_out;
+    int *iscal;
+};
+// The tails of one or two methods on the same Arnoldi output: the whitening
+// QR, M, cond(R) and gamma once (for the most demanding method), then each
+// method's node solves, level sums and coefficients; with two FP64 outputs
+// both recombinations share one pass over V.  The iscal of outs[1] must hold
+// a copy of outs[0]'s (same m_eff).
+skf_status tail_run_multi(int nout, const TailOut *outs, int s, int m, int64_t n, const void *V, skf_dtype vdt,
+                          int64_t ldv, const double *vscale, const double *SV, const double *SAV, const RuleDev &rule,
+                          double tol, cudaStream_t st, double *sketch_out, const double *stop_state, double cond_max,
+                          const double *H, int ldh, int kt);
 // Two-pass mode: x (+)= z_j w_j for basis column w_j (type vdt), j < m_eff =
 // iscal[1]; j = 0 starts x (x = 0 when m_eff = 0).  The FMA sequence per row
 // is that of the one-pass FP64 recombination.

@@ -1535,6 +1535,45 @@ __global__ void __launch_bounds__(kThreads) k_recombine(const double *__restrict
     }
 }
 
+// Two recombinations in one pass over V: x0 = V z0, x1 = V z1 (the sFOM and
+// sGMRES approximants of one Arnoldi process); each sum in the order of
+// k_recombine, so each output equals the one-method result bit for bit.
+__global__ void __launch_bounds__(kThreads) k_recombine2(const double *__restrict__ V, int64_t ldv, int64_t n,
+                                                         const double *__restrict__ z0,
+                                                         const double *__restrict__ z1, const int *iscal,
+                                                         double *__restrict__ x0, double *__restrict__ x1) {
+    extern __shared__ double zz[];   // [2 me]
+    const int me = iscal[1];
+    for (int j = threadIdx.x; j < me; j += blockDim.x) {
+        zz[2 * j] = z0[j];
+        zz[2 * j + 1] = z1[j];
+    }
+    __syncthreads();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int j = 0; j < me; ++j) {
+            const double v = V[r + (int64_t)j * ldv];
+            a0 = fma(v, zz[2 * j], a0);
+            a1 = fma(v, zz[2 * j + 1], a1);
+        }
+        x0[r] = a0;
+        x1[r] = a1;
+    }
+}
+
+// A second method's tail on the shared whitening: its state starts from the
+// first method's (rdiag ratio, cond(R) estimate, gamma, zero-pivot flag;
+// convergence fields cleared), and a failure of the shared part (a QR
+// timeout) is carried over to its status.
+__global__ void k_fork_state(const double *__restrict__ q0, double *__restrict__ q1, const int *__restrict__ isc0,
+                             int *__restrict__ isc1) {
+    if (threadIdx.x < 8) {
+        const int i = threadIdx.x;
+        q1[i] = (i == 3 || i >= 5) ? q0[i] : 0.0;
+    }
+    if (threadIdx.x == 0 && isc1[2] == SKF_OK && isc0[2] == SKF_ERR_TIMEOUT) isc1[2] = SKF_ERR_TIMEOUT;
+}
+
 // f = V_m z for an FP32 or BF16 basis.  Each product v z_j is formed exactly
 // as a float pair (z_j = zh + zl, Dekker product through fmaf) and summed in
 // double-float arithmetic (Knuth's TwoSum), so the sum keeps about 44 bits
@@ -1690,10 +1729,16 @@ static int g_tail_form = 0;   // 0 automatic (relation form with an FP64 basis),
 void set_tail_form(int form) { g_tail_form = form; }
 int tail_form() { return g_tail_form; }
 
-skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
-                    const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
-                    double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out,
-                    const double *stop_state, double *z_out, double cond_max, const double *H, int ldh, int kt) {
+skf_status tail_run_multi(int nout, const TailOut *outs, int s, int m, int64_t n, const void *V, skf_dtype vdt,
+                          int64_t ldv, const double *vscale, const double *SV, const double *SAV, const RuleDev &rule,
+                          double tol, cudaStream_t st, double *sketch_out, const double *stop_state, double cond_max,
+                          const double *H, int ldh, int kt) {
+    if (nout < 1 || nout > 2) return fail(SKF_ERR_INVALID_ARG, "tail: one or two methods");
+    // the shared part (QR, M, cond(R), gamma) is that of the most demanding method
+    skf_method method = outs[0].method;
+    for (int i = 1; i < nout; ++i)
+        if (outs[i].method == SKF_METHOD_SGMRES) method = SKF_METHOD_SGMRES;
+    int *iscal = outs[0].iscal;
     TailCtx c{};
     c.cond_max = cond_max;
     // relation form where the basis is FP64 and H is given (see the top of the file)
@@ -1740,10 +1785,11 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     const size_t sizes[] = {sizeof(double) * (size_t)s * 2 * m, sizeof(double) * 2 * m, sizeof(double) * mm,
                             sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * m,
                             sizeof(double) * m, nw_bytes, sizeof(double) * (size_t)cap * m,
-                            sizeof(double) * (size_t)rule.nlevels * m, sizeof(double) * m, sizeof(double) * m,
-                            sizeof(double) * 8, sizeof(double) * mm, sizeof(double) * mm, sizeof(int) * (size_t)cap,
-                            sizeof(double) * 2 * (size_t)m, sizeof(unsigned) * 4, sizeof(double) * mm,
-                            sizeof(double) * mm, sizeof(double) * m, sizeof(double) * mm, sizeof(double) * m};
+                            sizeof(double) * (size_t)rule.nlevels * m * nout, sizeof(double) * m * nout,
+                            sizeof(double) * m * nout, sizeof(double) * 8 * nout, sizeof(double) * mm,
+                            sizeof(double) * mm, sizeof(int) * (size_t)cap, sizeof(double) * 2 * (size_t)m,
+                            sizeof(unsigned) * 4, sizeof(double) * mm, sizeof(double) * mm, sizeof(double) * m,
+                            sizeof(double) * mm, sizeof(double) * m};
     constexpr int kNbuf = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
     for (size_t v : sizes) total += al(v);
@@ -1767,7 +1813,6 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
     c.Rcs = ptrs[22];
     c.cn2 = ptrs[23];
     c.lev_cnt = qr_ready + 2;
-
     const int G = std::min(2 * num_sms(), 1024);
     long long nlaunch = 0;
     k_tail_copy<<<G, kThreads, 0, st>>>(SV, SAV, c);
@@ -1838,8 +1883,6 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
         else k_tri_right<16><<<blocks + 1, 64, 0, st>>>(c, (int)blocks);
         ++nlaunch;
     }
-    k_tail_prep<<<G, kThreads, 0, st>>>(c);
-    ++nlaunch;
     // FP32 factor: packed in shared memory up to kMixedMaxM, else a global slot
     const bool packed = m <= kMixedMaxM;
     const size_t msmem = sizeof(double) * 4 * m + sizeof(float) * ((size_t)m + (size_t)m * (m + 1) / 2);
@@ -1853,60 +1896,109 @@ skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, s
         cudaFuncSetAttribute(k_nodes_g<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm32);
     if (gsm64 > 48 * 1024)
         cudaFuncSetAttribute(k_nodes_g<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm64);
-    for (size_t bi = 0; bi < batches.size(); ++bi) {
-        const int l0 = batches[bi].first, nl = batches[bi].second;
-        const int n0 = rule.h_start[l0];
-        const int nn = rule.h_start[l0 + nl] - n0;
-        for (int o = 0; o < nn; o += chunk) {
-            const int nb = std::min(chunk, nn - o);
-            if (c.hess) {
-                const unsigned g = (unsigned)((nb + kHessWarps - 1) / kHessWarps);
-                if (m <= 64) k_nodes_hess<2><<<g, 32 * kHessWarps, 0, st>>>(c, n0, o, nb, c.Nw, rstride);
-                else if (m <= 128) k_nodes_hess<4><<<g, 32 * kHessWarps, 0, st>>>(c, n0, o, nb, c.Nw, rstride);
-                else if (m <= 256) k_nodes_hess<8><<<g, 32 * kHessWarps, 0, st>>>(c, n0, o, nb, c.Nw, rstride);
-                else k_nodes_hess<16><<<g, 32 * kHessWarps, 0, st>>>(c, n0, o, nb, c.Nw, rstride);
-                nlaunch += 1;
-                continue;
-            }
-            if (rule.cplx) {
-                k_nodes_cplx<<<nb, kNodeThreads, gsmC, st>>>(c, n0, o);
-            } else {
-                if (packed) k_nodes_mixed<<<nb, kThreads, msmem, st>>>(c, n0, o);
-                else k_nodes_g<float, true><<<nb, kNodeThreads, gsm32, st>>>(c, n0, o);
-                k_nodes_g<double, false><<<nb, kNodeThreads, gsm64, st>>>(c, n0, o);
-            }
-            nlaunch += 2;
-        }
-        k_levels<<<(unsigned)nl, kThreads, 0, st>>>(c, l0, nl, rule.lev_start, rule.lev_ell, n0, tol,
-                                         bi + 1 == batches.size() ? 1 : 0);
-        ++nlaunch;
+    // per method: its context (own qstate, quadrature buffers, coefficients,
+    // status), node solves, level sums and coefficients
+    TailCtx cm[2];
+    for (int i = 0; i < nout; ++i) {
+        cm[i] = c;
+        cm[i].method = outs[i].method;
+        cm[i].iscal = outs[i].iscal;
+        cm[i].qbuf = c.qbuf + (size_t)i * rule.nlevels * m;
+        cm[i].qacc = c.qacc + (size_t)i * m;
+        cm[i].z = c.z + (size_t)i * m;
+        cm[i].qstate = c.qstate + (size_t)i * 8;
     }
-    if (m <= 64) k_coeffs<2><<<1, 32, 0, st>>>(c);
-    else if (m <= 128) k_coeffs<4><<<1, 32, 0, st>>>(c);
-    else if (m <= 256) k_coeffs<8><<<1, 32, 0, st>>>(c);
-    else k_coeffs<16><<<1, 32, 0, st>>>(c);
+    for (int mi = 0; mi < nout; ++mi) {
+        const TailCtx &cc = cm[mi];
+        if (mi > 0) {
+            k_fork_state<<<1, 32, 0, st>>>(c.qstate, cc.qstate, iscal, cc.iscal);
+            ++nlaunch;
+        }
+        // the normal matrices of the Cholesky node solves depend on the method
+        if (mi == 0 || !c.hess) {
+            k_tail_prep<<<G, kThreads, 0, st>>>(cc);
+            ++nlaunch;
+        }
+        for (size_t bi = 0; bi < batches.size(); ++bi) {
+            const int l0 = batches[bi].first, nl = batches[bi].second;
+            const int n0 = rule.h_start[l0];
+            const int nn = rule.h_start[l0 + nl] - n0;
+            for (int o = 0; o < nn; o += chunk) {
+                const int nb = std::min(chunk, nn - o);
+                if (cc.hess) {
+                    const unsigned g = (unsigned)((nb + kHessWarps - 1) / kHessWarps);
+                    if (m <= 64) k_nodes_hess<2><<<g, 32 * kHessWarps, 0, st>>>(cc, n0, o, nb, cc.Nw, rstride);
+                    else if (m <= 128) k_nodes_hess<4><<<g, 32 * kHessWarps, 0, st>>>(cc, n0, o, nb, cc.Nw, rstride);
+                    else if (m <= 256) k_nodes_hess<8><<<g, 32 * kHessWarps, 0, st>>>(cc, n0, o, nb, cc.Nw, rstride);
+                    else k_nodes_hess<16><<<g, 32 * kHessWarps, 0, st>>>(cc, n0, o, nb, cc.Nw, rstride);
+                    nlaunch += 1;
+                    continue;
+                }
+                if (rule.cplx) {
+                    k_nodes_cplx<<<nb, kNodeThreads, gsmC, st>>>(cc, n0, o);
+                } else {
+                    if (packed) k_nodes_mixed<<<nb, kThreads, msmem, st>>>(cc, n0, o);
+                    else k_nodes_g<float, true><<<nb, kNodeThreads, gsm32, st>>>(cc, n0, o);
+                    k_nodes_g<double, false><<<nb, kNodeThreads, gsm64, st>>>(cc, n0, o);
+                }
+                nlaunch += 2;
+            }
+            k_levels<<<(unsigned)nl, kThreads, 0, st>>>(cc, l0, nl, rule.lev_start, rule.lev_ell, n0, tol,
+                                             bi + 1 == batches.size() ? 1 : 0);
+            ++nlaunch;
+        }
+        if (m <= 64) k_coeffs<2><<<1, 32, 0, st>>>(cc);
+        else if (m <= 128) k_coeffs<4><<<1, 32, 0, st>>>(cc);
+        else if (m <= 256) k_coeffs<8><<<1, 32, 0, st>>>(cc);
+        else k_coeffs<16><<<1, 32, 0, st>>>(cc);
+        ++nlaunch;
+        if (outs[mi].z_out) {
+            k_copy_z<<<(m + kThreads - 1) / kThreads, kThreads, 0, st>>>(cc, outs[mi].z_out);
+            ++nlaunch;
+        }
+    }
     const int64_t rb = std::min<int64_t>((n + kThreads - 1) / kThreads, 16 * num_sms());
     const unsigned rgrid = (unsigned)std::max<int64_t>(rb, 1);
     const size_t zsm = sizeof(float) * 2 * (size_t)m;
-    if (z_out) k_copy_z<<<(m + kThreads - 1) / kThreads, kThreads, 0, st>>>(c, z_out);
     if (sketch_out) {
-        k_sketch_f<<<(s + kThreads - 1) / kThreads, kThreads, 0, st>>>(c, SV, sketch_out);
-    } else if (x == nullptr) {
-        // coefficients only (two-pass mode)
-    } else if (vdt == SKF_F64) {
-        k_recombine<<<rgrid, kThreads, 0, st>>>((const double *)V, ldv, n, c.z, iscal, x);
-    } else if (vdt == SKF_F32) {
-        k_recombine_lp<float><<<rgrid, kThreads, zsm, st>>>((const float *)V, ldv, n, c.z, iscal, x);
+        k_sketch_f<<<(s + kThreads - 1) / kThreads, kThreads, 0, st>>>(cm[0], SV, sketch_out);
+        ++nlaunch;
+    } else if (nout == 2 && vdt == SKF_F64 && outs[0].x && outs[1].x) {
+        k_recombine2<<<rgrid, kThreads, sizeof(double) * 2 * m, st>>>((const double *)V, ldv, n, cm[0].z, cm[1].z,
+                                                                        iscal, outs[0].x, outs[1].x);
+        ++nlaunch;
     } else {
-        k_recombine_lp<__nv_bfloat16><<<rgrid, kThreads, zsm, st>>>((const __nv_bfloat16 *)V, ldv, n, c.z, iscal, x);
+        for (int mi = 0; mi < nout; ++mi) {
+            double *x = outs[mi].x;
+            if (x == nullptr) continue;   // coefficients only (two-pass mode)
+            if (vdt == SKF_F64)
+                k_recombine<<<rgrid, kThreads, 0, st>>>((const double *)V, ldv, n, cm[mi].z, iscal, x);
+            else if (vdt == SKF_F32)
+                k_recombine_lp<float><<<rgrid, kThreads, zsm, st>>>((const float *)V, ldv, n, cm[mi].z, iscal, x);
+            else
+                k_recombine_lp<__nv_bfloat16><<<rgrid, kThreads, zsm, st>>>((const __nv_bfloat16 *)V, ldv, n,
+                                                                            cm[mi].z, iscal, x);
+            ++nlaunch;
+        }
     }
-    k_write_info<<<1, 32, 0, st>>>(c, info, stop_state);
-    nlaunch += 3;
+    for (int mi = 0; mi < nout; ++mi) {
+        k_write_info<<<1, 32, 0, st>>>(cm[mi], outs[mi].info, stop_state);
+        ++nlaunch;
+    }
     count_launches(nlaunch);
     cudaError_t e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "tail kernels");
     return SKF_OK;
+}
+
+skf_status tail_run(skf_method method, int s, int m, int64_t n, const void *V, skf_dtype vdt, int64_t ldv,
+                    const double *vscale, const double *SV, const double *SAV, int *iscal, const RuleDev &rule,
+                    double tol, double *x, skf_info *info, cudaStream_t st, double *sketch_out,
+                    const double *stop_state, double *z_out, double cond_max, const double *H, int ldh, int kt) {
+    TailOut o{method, x, info, z_out, iscal};
+    return tail_run_multi(1, &o, s, m, n, V, vdt, ldv, vscale, SV, SAV, rule, tol, st, sketch_out, stop_state,
+                          cond_max, H, ldh, kt);
 }
 
 skf_status stop_check(skf_method method, int s, int p, const double *vscale, const double *SV, const double *SAV,

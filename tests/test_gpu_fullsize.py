@@ -67,3 +67,21 @@ def test_default_workload_full_size_matches_oracle(skf, full, method, mode):
     # tracks cond(V_m) within the embedding's distortion)
     assert full["condR"] * U <= 1e-12
     assert err <= 1e-10
+
+
+def test_default_workload_pair_matches_oracle(skf, full):
+    """The pair call bench.py times: both approximants from one Arnoldi
+    process (persistent form), each against the oracle."""
+    wl = full["wl"]
+    f = skf.make_func(wl.func, full["c"])
+    S = skf.Sketch(skf.SPARSE_SIGN, full["A"].n, wl.s, wl.zeta, 13)
+    p = skf.make_params(wl.m, wl.k, tol=1e-10)
+    i_f, i_g = skf.new_info(), skf.new_info()
+    xf, xg = skf.sfom_sgmres(full["op"].csr, S, torch.as_tensor(full["b"], device="cuda"), f, p,
+                             info_fom=i_f, info_gmres=i_g)
+    torch.cuda.synchronize()
+    for x, info, method in ((xf, i_f, "sfom"), (xg, i_g, "sgmres")):
+        gi = skf.read_info(info)
+        xo, ell = full["ref"][method]
+        assert gi["status"] == 0 and gi["m_eff"] == wl.m and gi["ell"] == ell
+        assert rel(x.cpu().numpy(), xo) <= 1e-10
