@@ -405,24 +405,31 @@ __global__ void k_row_abs_sum(const int32_t *__restrict__ rp, const int32_t *__r
 }
 
 // SELL-32 layout: slice widths, then entries (see skf_csr).
-__global__ void k_sell_width(const int32_t *__restrict__ rp, int64_t n, int64_t nslices, int32_t *__restrict__ w) {
+// Rows longer than `cut` entries count as empty (they take the row-split path).
+__global__ void k_sell_width(const int32_t *__restrict__ rp, int64_t n, int64_t nslices, int cut,
+                             int32_t *__restrict__ w) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nslices; t += (int64_t)gridDim.x * blockDim.x) {
         int mx = 0;
-        for (int64_t r = 32 * t; r < min(n, 32 * t + 32); ++r) mx = max(mx, rp[r + 1] - rp[r]);
+        for (int64_t r = 32 * t; r < min(n, 32 * t + 32); ++r) {
+            const int len = rp[r + 1] - rp[r];
+            if (len <= cut) mx = max(mx, len);
+        }
         w[t] = mx;
     }
 }
 
 template <typename TV>
 __global__ void k_sell_fill(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const TV *__restrict__ v,
-                            int64_t n, int64_t nslices, const int64_t *__restrict__ off, const int32_t *__restrict__ w,
-                            TV *__restrict__ sv, int32_t *__restrict__ sc) {
+                            int64_t n, int64_t nslices, int cut, const int64_t *__restrict__ off,
+                            const int32_t *__restrict__ w, TV *__restrict__ sv, int32_t *__restrict__ sc) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < 32 * nslices;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = r >> 5;
         const int l = (int)(r & 31);
         const int wt = w[t];
-        const int b = r < n ? rp[r] : 0, len = r < n ? rp[r + 1] - b : 0;
+        const int b = r < n ? rp[r] : 0;
+        int len = r < n ? rp[r + 1] - b : 0;
+        if (len > cut) len = 0;   // a long row: row-split path
         const int self = r < n ? (int)r : 0;
         for (int p = 0; p < wt; ++p) {
             const int64_t o = off[t] + 32ll * p + l;
@@ -902,7 +909,49 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
         cudaGetLastError();
         return cleanup(fail(SKF_ERR_OOM, "SELL allocation"));
     }
-    k_sell_width<<<blocks, 256, 0, st>>>(A->rowptr, n, A->nslices, A->sell_w);
+    // row split: long rows, their segments and the per-slice masks (host)
+    {
+        std::vector<int32_t> hrp((size_t)n + 1);
+        cudaMemcpyAsync(hrp.data(), A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, st);
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "row lengths"));
+        std::vector<uint2> hl((size_t)A->nslices, make_uint2(0u, 0u));
+        std::vector<int32_t> seg0{0}, sb, se;
+        int64_t nl = 0;
+        for (int64_t t = 0; t < A->nslices; ++t) {
+            hl[t].y = (unsigned)nl;
+            for (int l = 0; l < 32 && 32 * t + l < n; ++l) {
+                const int64_t r = 32 * t + l;
+                const int32_t b0 = hrp[r], b1 = hrp[r + 1];
+                if (b1 - b0 <= kLongRow) continue;
+                hl[t].x |= 1u << l;
+                for (int32_t p0 = b0; p0 < b1; p0 += kSegLen) {
+                    sb.push_back(p0);
+                    se.push_back(std::min(b1, p0 + kSegLen));
+                }
+                seg0.push_back((int32_t)sb.size());
+                ++nl;
+            }
+        }
+        A->nlong = nl;
+        A->nseg = (int64_t)sb.size();
+        if (nl > 0) {
+            if (cudaMalloc(&A->sell_long, sizeof(uint2) * A->nslices) != cudaSuccess ||
+                cudaMalloc(&A->long_seg0, sizeof(int32_t) * seg0.size()) != cudaSuccess ||
+                cudaMalloc(&A->seg_beg, sizeof(int32_t) * sb.size()) != cudaSuccess ||
+                cudaMalloc(&A->seg_end, sizeof(int32_t) * se.size()) != cudaSuccess) {
+                cudaGetLastError();
+                return cleanup(fail(SKF_ERR_OOM, "row-split allocation"));
+            }
+            cudaMemcpyAsync(A->sell_long, hl.data(), sizeof(uint2) * A->nslices, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(A->long_seg0, seg0.data(), sizeof(int32_t) * seg0.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(A->seg_beg, sb.data(), sizeof(int32_t) * sb.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(A->seg_end, se.data(), sizeof(int32_t) * se.size(), cudaMemcpyHostToDevice, st);
+            e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cleanup(cuda_fail(e, "row-split upload"));
+        }
+    }
+    k_sell_width<<<blocks, 256, 0, st>>>(A->rowptr, n, A->nslices, kLongRow, A->sell_w);
     count_launches(1);
     cudaMemcpyAsync(hw.data(), A->sell_w, sizeof(int32_t) * A->nslices, cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
@@ -925,10 +974,10 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
     cudaMemcpyAsync(A->sell_off, hoff.data(), sizeof(int64_t) * (A->nslices + 1), cudaMemcpyHostToDevice, st);
     if (vdtype == SKF_F64)
         k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, A->nslices,
-                                            A->sell_off, A->sell_w, (double *)A->sell_val, A->sell_col);
+                                            kLongRow, A->sell_off, A->sell_w, (double *)A->sell_val, A->sell_col);
     else
         k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const float *)A->values, n, A->nslices,
-                                            A->sell_off, A->sell_w, (float *)A->sell_val, A->sell_col);
+                                            kLongRow, A->sell_off, A->sell_w, (float *)A->sell_val, A->sell_col);
     count_launches(1);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "SELL fill"));
@@ -947,6 +996,10 @@ skf_status skf_destroy_csr(skf_csr *A) {
     if (A->sell_w) cudaFree(A->sell_w);
     if (A->sell_val) cudaFree(A->sell_val);
     if (A->sell_col) cudaFree(A->sell_col);
+    if (A->sell_long) cudaFree(A->sell_long);
+    if (A->long_seg0) cudaFree(A->long_seg0);
+    if (A->seg_beg) cudaFree(A->seg_beg);
+    if (A->seg_end) cudaFree(A->seg_end);
     delete A;
     return SKF_OK;
 }

@@ -79,6 +79,8 @@ struct ArnCtx {
     int64_t rows_per_cta;      // row partition of the update kernel (sized the sketch tables)
     int64_t spmv_rows;         // rows per CTA of the SpMV kernel (multiple of 32)
     int G_upd;                 // CTAs of the update kernel = number of sketch partials
+    RowSplit rs;               // long rows of a skewed operator (row split)
+    double *seg_part;          // [rs.nseg] partial sums of the long rows' segments
 };
 
 namespace {
@@ -143,6 +145,25 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_init(ArnCtx c, const doubl
     }
 }
 
+// Row split: one warp per segment of a long row, lane-strided products over
+// its CSR entries, then a butterfly whose lane-0 result (a fixed order) is the
+// segment's partial sum of A w_j.
+__global__ void __launch_bounds__(256) k_spmv_long(ArnCtx c, int j) {
+    if (c.iscal[0] && c.iscal[3] < j) return;
+    const double *x = c.V + vcol(c, j);
+    const double *vals = (const double *)c.rs.values;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < c.rs.nseg; g += nwarps) {
+        const int b = __ldg(c.rs.seg_beg + g), e = __ldg(c.rs.seg_end + g);
+        double acc = 0.0;
+        for (int p = b + lane; p < e; p += 32) acc = fma(__ldg(vals + p), x[__ldg(c.rs.colind + p)], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) c.seg_part[g] = acc;
+    }
+}
+
 template <int KW, int WMAX>
 __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int j) {
     __shared__ double red[BlockSumTraits<KW, kSpmvThreads>::kSmem];
@@ -193,12 +214,16 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
         const int64_t t = rw >> 5;
         int wt = 0;
         long long so = 0;
+        uint2 sl = make_uint2(0u, 0u);
         if (lane == 0) {
             wt = __ldg(c.sell_w + t);
             so = __ldg(c.sell_off + t);
+            if (c.rs.sell_long) sl = __ldg(c.rs.sell_long + t);
         }
         wt = __shfl_sync(0xffffffffu, wt, 0);
         so = __shfl_sync(0xffffffffu, so, 0);
+        sl.x = __shfl_sync(0xffffffffu, sl.x, 0);
+        sl.y = __shfl_sync(0xffffffffu, sl.y, 0);
         const int64_t r = rw + lane;
         if (r >= r1) continue;
         const int64_t base = so + lane;
@@ -222,6 +247,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
                 y = fma(__ldg(c.sell_val + o), wj[__ldg(c.sell_col + o)], y);
             }
         }
+        if (sl.x) y = add_long_row(c.rs, c.seg_part, sl, lane, y);
         c.Y[r] = y;
 #pragma unroll
         for (int a = 0; a < KW; ++a)
@@ -689,7 +715,7 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
     // slices up to 8 wide take the pipelined SpMV; wider ones the generic
     // kernel (16 unrolled product slots, an entry loop past 16)
     auto spmv = k_arnoldi_spmv<KW, 16>;
-    const bool pipe = c.max_width <= 8;
+    const bool pipe = c.max_width <= 8 && c.rs.sell_long == nullptr;   // a row split takes the generic SpMV
     // product slots of the pipelined SpMV: the widest slice rounded up to 5, 7
     // or 8 (a slot past a slice's width is a predicated-off FP64 instruction)
     auto spmv_pipe = c.max_width <= 5 ? k_arnoldi_spmv_pipe<KW, 5>
@@ -717,6 +743,7 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
     for (int j = 0; j < c.m; ++j) {
         ArnCtx cj = c;
         window_offsets(cj, j);
+        if (c.rs.sell_long) k_spmv_long<<<long_ctas(c.rs.nseg, num_sms()), 256, 0, st>>>(cj, j);
         if (pipe) cudaLaunchKernelEx(&cfg_s, spmv_pipe, cj, j);
         else spmv<<<Gs, kSpmvThreads, 0, st>>>(cj, j);
         call_hook(hook, j, st);   // S v_i, S A v_i final for i < j
@@ -835,8 +862,10 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     const size_t szGram = sizeof(double) * (size_t)m * kMaxK;
     const size_t szE = sizeof(int) * (size_t)m;
     const size_t szEps = sizeof(double) * (size_t)m;
+    c.rs = row_split_of(A);
+    const size_t szSeg = sizeof(double) * (size_t)std::max<int64_t>(c.rs.nseg, 1);
     const size_t total = al(szY) + al(szP1) + al(szP2) + al(szFd) + al(szFw) + al(szSc) + al(szCnt) + 2 * al(szSk) +
-                         al(szGram) + 2 * al(szE) + al(szEps);
+                         al(szGram) + 2 * al(szE) + al(szEps) + al(szSeg);
     skf_status stt = dalloc((void **)&ws, total, st);
     if (stt != SKF_OK) return stt;
     size_t off = 0;
@@ -858,6 +887,7 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     c.eys = (int *)take(szE);
     c.ews = (int *)take(szE);
     c.epscol = (double *)take(szEps);
+    c.seg_part = (double *)take(szSeg);
     cudaMemsetAsync(c.cnt, 0, szCnt, st);
 
     const size_t smem = c.sparse ? sizeof(int) * 4 * S->s : 0;   // two limbs for each of S v_j, S A v_j
@@ -871,7 +901,7 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     call_hook(hook, m, st);
     k_arnoldi_eps<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);
     k_arnoldi_info<<<1, kThreads, 0, st>>>(c, info);
-    count_launches(4 + 2ll * m);
+    count_launches(4 + (c.rs.sell_long ? 3ll : 2ll) * m);
     cudaError_t e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "arnoldi kernels");

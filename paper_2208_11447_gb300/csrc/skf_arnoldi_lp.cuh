@@ -120,6 +120,8 @@ __device__ __forceinline__ void limbs_f32(float x, const LimbScale &ls, int &l0,
 }
 
 struct LpCtx {
+    RowSplit rs;               // long rows of a skewed operator (row split)
+    float *seg_part;           // [rs.nseg] partial sums of the long rows' segments
     int64_t n;
     const int64_t *sell_off;   // SELL-32 operator with FP32 values (see skf_csr)
     const int32_t *sell_w;
@@ -389,6 +391,25 @@ __device__ __forceinline__ int last_y_exponent(const LpCtx &c, int j) {
     return ey;
 }
 
+// Row split: one warp per segment of a long row, FP32 products and sums
+// (lane-strided, then a butterfly whose lane-0 result is the partial).
+template <typename TB>
+__global__ void __launch_bounds__(256) k_spmv_long_lp(LpCtx c, int j) {
+    if (c.iscal[0] && c.iscal[3] < j) return;
+    const TB *x = (const TB *)c.V + vcol(c, j);
+    const float *vals = (const float *)c.rs.values;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < c.rs.nseg; g += nwarps) {
+        const int b = __ldg(c.rs.seg_beg + g), e = __ldg(c.rs.seg_end + g);
+        float acc = 0.f;
+        for (int p = b + lane; p < e; p += 32) acc = fmaf(__ldg(vals + p), Store<TB>::ld(x + __ldg(c.rs.colind + p)), acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) c.seg_part[g] = acc;
+    }
+}
+
 // SpMV with the SELL values and columns loaded per row (any slice width).
 template <int KW, int ZCAP, typename TB>
 __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, int j) {
@@ -424,12 +445,16 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, in
         if (rw >= c.n) continue;                                                                // whole warp
         int wt = 0;
         long long so = 0;
+        uint2 sl = make_uint2(0u, 0u);
         if (lane == 0) {
             wt = __ldg(c.sell_w + (rw >> 5));
             so = __ldg(c.sell_off + (rw >> 5));
+            if (c.rs.sell_long) sl = __ldg(c.rs.sell_long + (rw >> 5));
         }
         wt = __shfl_sync(0xffffffffu, wt, 0);
         so = __shfl_sync(0xffffffffu, so, 0);
+        sl.x = __shfl_sync(0xffffffffu, sl.x, 0);
+        sl.y = __shfl_sync(0xffffffffu, sl.y, 0);
         const int64_t r = rw + lane;
         if (r >= c.n) continue;   // no warp-collective operation below
         // window values first: independent of the SpMV, their latency overlaps it
@@ -456,6 +481,7 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, in
             for (int p = 0; p < 8; ++p)
                 if (p0 + p < wt) y = fmaf(av[p], xv[p], y);
         }
+        if (sl.x) y = add_long_row(c.rs, c.seg_part, sl, lane, y);
         c.Y[r] = y;
 #pragma unroll
         for (int a = 0; a < KW; ++a)
@@ -906,6 +932,7 @@ void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, 
     for (int j = 0; j < c.m; ++j) {
         LpCtx cj = c;
         window_offsets(cj, j);
+        if (c.rs.sell_long) k_spmv_long_lp<TB><<<long_ctas(c.rs.nseg, num_sms()), 256, 0, st>>>(cj, j);
         spmv<<<c.G, kSpmvThreads, smem_spmv, st>>>(cj, j);
         if (j >= 1) call_hook(hook, j - 1, st);   // S v_i, S A v_i final for i < j - 1
         if (c.identity) k_identity_cols_lp<TB><<<gid, kThreads, 0, st>>>(cj, j);
@@ -977,7 +1004,9 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     const size_t smem_spmv = c.identity ? 0 : sizeof(int) * 2 * (size_t)s;
     if (smem_upd + static_upd > (size_t)optin || smem_spmv > (size_t)optin)
         return fail(SKF_ERR_NOT_SUPPORTED, "sketch size s too large for the shared-memory bins");
-    const bool pipe = A->max_width <= 8;   // slices at most 8 wide: the pipelined SpMV
+    // slices at most 8 wide: the pipelined SpMV (a row split takes the generic one)
+    const bool pipe = A->max_width <= 8 && A->nlong == 0;
+    c.rs = row_split_of(A);
 
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t szY = sizeof(float) * A->n;
@@ -994,9 +1023,10 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     const size_t szEx = sizeof(int) * (size_t)(2 * m + 1);
     const size_t szEps = sizeof(double) * (size_t)m;
     const size_t szCnt = sizeof(unsigned) * 4;
+    const size_t szSeg = sizeof(float) * (size_t)std::max<int64_t>(c.rs.nseg, 1);
     const size_t total = al(szY) + al(szP1) + al(szP2) + al(szFd) + al(szFw) + al(szSc) + al(szGram) + al(szCoef) +
                          al(szSk) + al(szSd) + al(2 * szPart) + al(szPart) + (bf ? al(szPart) : 0) + al(szEx) +
-                         al(szEps) + al(szCnt);
+                         al(szEps) + al(szCnt) + al(szSeg);
     char *ws = nullptr;
     skf_status stt = dalloc((void **)&ws, total, st);
     if (stt != SKF_OK) return stt;
@@ -1007,6 +1037,7 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
         return p;
     };
     c.Y = (float *)take(szY);
+    c.seg_part = (float *)take(szSeg);
     c.p1 = (double *)take(szP1);
     c.p2 = (double *)take(szP2);
     c.fin_d = (double *)take(szFd);
@@ -1032,7 +1063,7 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     call_hook(hook, m, st);
     k_arnoldi_eps_lp<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);
     k_arnoldi_info_lp<<<1, kThreads, 0, st>>>(c, info);
-    count_launches(4 + (c.identity ? 3ll : 2ll) * m);
+    count_launches(4 + ((c.identity ? 3ll : 2ll) + (c.rs.sell_long ? 1 : 0)) * m);
     cudaError_t e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "reduced-precision Arnoldi kernels");

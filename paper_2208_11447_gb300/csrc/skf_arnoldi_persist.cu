@@ -804,7 +804,8 @@ int step_mode() { return g_step_mode; }
 skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V,
                                   int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
                                   skf_info *info, cudaStream_t st) {
-    if (S->kind != SKF_SKETCH_SPARSE_SIGN || S->binmax_persist == nullptr || k > 4 || A->vdtype != SKF_F64)
+    if (S->kind != SKF_SKETCH_SPARSE_SIGN || S->binmax_persist == nullptr || k > 4 || A->vdtype != SKF_F64 ||
+        A->nlong > 0)   // a row split (skewed rows) takes the two-kernel form
         return SKF_ERR_NOT_SUPPORTED;
     int G;
     int64_t R64;

@@ -63,7 +63,63 @@ struct skf_csr {
     int32_t *sell_col = nullptr;
     int max_width = 0;                // widest slice
     int64_t max_chunk_entries = 0;    // most SELL entries in one chunk of 1024 rows (32 slices)
+    // Row split for skewed degree distributions: rows with more than
+    // kLongRow entries are left out of the slices (they count as empty there)
+    // and cut into segments of at most kSegLen consecutive CSR entries; each
+    // segment is reduced by one warp (k_spmv_long) into a partial sum, and the
+    // SpMV adds a long row's partials in segment order.  sell_long[t] = (bit
+    // mask of the long rows of slice t, index of its first long row); the
+    // segments of long row q are long_seg0[q] .. long_seg0[q+1] - 1.
+    int64_t nlong = 0, nseg = 0;
+    uint2 *sell_long = nullptr;       // [nslices], nullptr without long rows
+    int32_t *long_seg0 = nullptr;     // [nlong + 1]
+    int32_t *seg_beg = nullptr;       // [nseg] first CSR entry of the segment
+    int32_t *seg_end = nullptr;       // [nseg] one past its last entry
 };
+constexpr int kLongRow = 32;          // longest row kept in the SELL slices
+constexpr int kSegLen = 1024;         // entries per segment of a long row (32 per lane)
+
+// The row split of an operator as the step kernels see it (see skf_csr).
+struct RowSplit {
+    const uint2 *sell_long = nullptr;     // nullptr: no long rows
+    const int32_t *long_seg0 = nullptr;
+    const int32_t *seg_beg = nullptr, *seg_end = nullptr;
+    const int32_t *colind = nullptr;      // the operator's CSR
+    const void *values = nullptr;
+    int64_t nseg = 0;
+};
+
+inline RowSplit row_split_of(const skf_csr *A) {
+    RowSplit r;
+    if (A->nlong > 0) {
+        r.sell_long = A->sell_long;
+        r.long_seg0 = A->long_seg0;
+        r.seg_beg = A->seg_beg;
+        r.seg_end = A->seg_end;
+        r.colind = A->colind;
+        r.values = A->values;
+        r.nseg = A->nseg;
+    }
+    return r;
+}
+
+// y of a long row: its segment partials added to y (0 from the empty slice
+// row) in segment order.  sl = sell_long of the lane's slice.
+template <typename TA>
+__device__ __forceinline__ TA add_long_row(const RowSplit &rs, const TA *__restrict__ part, uint2 sl, int lane, TA y) {
+    if ((sl.x >> lane) & 1u) {
+        const int q = (int)sl.y + __popc(sl.x & ((1u << lane) - 1u));
+        const int g1 = rs.long_seg0[q + 1];
+        for (int g = rs.long_seg0[q]; g < g1; ++g) y += part[g];
+    }
+    return y;
+}
+
+// CTAs of k_spmv_long: eight segments (warps) per CTA, at most 8 CTAs per SM.
+inline unsigned long_ctas(int64_t nseg, int sms) {
+    const int64_t c = (nseg + 7) / 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(c, 8ll * sms));
+}
 
 struct skf_sketch {
     skf_sketch_kind kind = SKF_SKETCH_SPARSE_SIGN;
