@@ -654,6 +654,63 @@ def precision_extras(dev, reps: int = 3):
     return res
 
 
+def graph_extras(dev, reps: int = 2):
+    """The quadrature-batched graph workloads (N = 4e6 directed power-law
+    graph, FP32 values and basis, m = 150, k = 3, s = 600, 128 fixed
+    Gauss-Jacobi nodes of z^-1/2): rows carrying in-degrees (graph_n4m) and
+    rows carrying the power-law out-degrees (graph_n4m_t, row split).  Per
+    workload the FP32 truncated-Arnoldi step (CUDA events around
+    skf_arnoldi_trunc, median of reps, L2 flushed), its fraction of the
+    measured HBM copy rate for the algorithmic bytes, and the relative error
+    of the FP32 sGMRES solve against the FP64 GPU path on the same operator
+    (values widened exactly), sketch and rule."""
+    import numpy as np
+    import torch
+    import paper_2208_11447_gb300 as skf
+    from workloads.configs import quad_scale
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hbm_peak, hbm_src = measured_peaks()
+    res = {}
+    for name in ("graph_n4m", "graph_n4m_t"):
+        wl, A, b = build_inputs(name)
+        L = np.diff(A.rowptr)
+        A32 = A.astype(np.float32)
+        op32 = skf.upload_csr(A32.rowptr, A32.colind, A32.values, device=dev)
+        S = skf.Sketch(skf.SPARSE_SIGN, A.n, wl.s, wl.zeta, 13)
+        c = quad_scale(wl.func, wl.lam_lo or 0.0, op32.csr.norm_inf())
+        t_nodes, w_nodes = skf.quadrature_rule(skf.make_func(wl.func, c), int(wl.extra["ell"]))
+        f = skf.make_func(wl.func, c, nodes=t_nodes, weights=w_nodes)
+        b_dev = torch.as_tensor(b, device=dev)
+        ts = []
+        for r in range(reps + 1):
+            flush.zero_()
+            ev0.record(stream)
+            skf.arnoldi_trunc(op32.csr, S, b_dev, wl.m, wl.k, basis_dtype=torch.float32)
+            ev1.record(stream)
+            ev1.synchronize()
+            if r > 0:
+                ts.append(ev0.elapsed_time(ev1))
+        us = statistics.median(ts) * 1e3 / wl.m
+        alg = A.nnz * 8 + 4 * (A.n + 1) + (wl.k + 1) * A.n * 4
+        x32 = skf.sgmres(op32.csr, S, b_dev, f, skf.make_params(wl.m, wl.k, basis_dtype=torch.float32, tol=1e-10))
+        torch.cuda.synchronize()
+        del op32
+        op64 = skf.upload_csr(A.rowptr, A.colind, A.values.astype(np.float64), device=dev)
+        x64 = skf.sgmres(op64.csr, S, b_dev, f, skf.make_params(wl.m, wl.k, tol=1e-10))
+        torch.cuda.synchronize()
+        res[name] = {"rows": "power-law out-degrees (row split)" if name.endswith("_t") else "in-degrees",
+                     "N": int(A.n), "nnz": int(A.nnz), "max_row": int(L.max()), "rows_over_32": int((L > 32).sum()),
+                     "us_per_step": round(us, 2), "alg_bytes_per_step": int(alg),
+                     "hbm_frac": round(alg / (us * 1e-6) / 1e9 / hbm_peak, 4), "of": hbm_src,
+                     "rel_err_vs_fp64_gpu": float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))}
+        del op64, x32, x64, S
+        torch.cuda.empty_cache()
+    res["workload"] = "graph N = 4e6, FP32 values and basis, m = 150, k = 3, s = 600, 128 nodes, sGMRES z^-1/2"
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -878,6 +935,7 @@ def main():
         torch.cuda.empty_cache()
         t_ex = time.perf_counter()
         extras = {"precision": precision_extras(dev)}
+        extras["graph"] = graph_extras(dev)
         bo = batch_arms(dev, 1, 1, "16")
         extras["batch"] = {"workload": "batch_cd_8x64 (8 operators, 64 right-hand sides, m_r in [50, 400], "
                                        "sGMRES z^-1/2; one replay per arm after one warm-up)",

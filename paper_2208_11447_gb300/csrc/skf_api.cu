@@ -404,29 +404,19 @@ __global__ void k_row_abs_sum(const int32_t *__restrict__ rp, const int32_t *__r
     atomicMax(maxbits, (unsigned long long)__double_as_longlong(mx));
 }
 
-// SELL-32 layout: slice widths, then entries (see skf_csr).
-// Rows longer than `cut` entries count as empty (they take the row-split path).
-__global__ void k_sell_width(const int32_t *__restrict__ rp, int64_t n, int64_t nslices, int cut,
-                             int32_t *__restrict__ w) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nslices; t += (int64_t)gridDim.x * blockDim.x) {
-        int mx = 0;
-        for (int64_t r = 32 * t; r < min(n, 32 * t + 32); ++r) {
-            const int len = rp[r + 1] - rp[r];
-            if (len <= cut) mx = max(mx, len);
-        }
-        w[t] = mx;
-    }
-}
-
+// SELL-32 entries (see skf_csr); rows longer than `cut` entries are left
+// empty (they take the row-split path).
 template <typename TV>
 __global__ void k_sell_fill(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const TV *__restrict__ v,
-                            int64_t n, int64_t nslices, int cut, const int64_t *__restrict__ off,
-                            const int32_t *__restrict__ w, TV *__restrict__ sv, int32_t *__restrict__ sc) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < 32 * nslices;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = r >> 5;
-        const int l = (int)(r & 31);
+                            int64_t n, int64_t nslices, int cut, const int32_t *__restrict__ perm,
+                            const int64_t *__restrict__ off, const int32_t *__restrict__ w, TV *__restrict__ sv,
+                            int32_t *__restrict__ sc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 32 * nslices;
+         i += (int64_t)gridDim.x * blockDim.x) {   // slot i: row perm[i]
+        const int64_t t = i >> 5;
+        const int l = (int)(i & 31);
         const int wt = w[t];
+        const int64_t r = i < n ? (perm ? (int64_t)perm[i] : i) : n;
         const int b = r < n ? rp[r] : 0;
         int len = r < n ? rp[r + 1] - b : 0;
         if (len > cut) len = 0;   // a long row: row-split path
@@ -915,13 +905,52 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
         cudaMemcpyAsync(hrp.data(), A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, st);
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "row lengths"));
+        // slice widths with and without sorting by length in windows
+        auto eff = [&](int64_t r) {
+            const int32_t len = hrp[r + 1] - hrp[r];
+            return len > kLongRow ? 0 : len;
+        };
+        std::vector<int32_t> hperm((size_t)n);
+        for (int64_t i = 0; i < n; ++i) hperm[i] = (int32_t)i;
+        int64_t pad_plain = 0, pad_sorted = 0;
+        for (int64_t t = 0; t < A->nslices; ++t) {
+            int mx = 0;
+            for (int64_t r = 32 * t; r < std::min<int64_t>(n, 32 * t + 32); ++r) mx = std::max(mx, eff(r));
+            pad_plain += 32ll * mx;
+        }
+        for (int64_t w0 = 0; w0 < n; w0 += kSortWin) {
+            const int64_t w1 = std::min<int64_t>(n, w0 + kSortWin);
+            std::stable_sort(hperm.begin() + w0, hperm.begin() + w1,
+                             [&](int32_t x, int32_t y) { return eff(x) > eff(y); });
+        }
+        for (int64_t t = 0; t < A->nslices; ++t) {
+            int mx = 0;
+            for (int64_t i = 32 * t; i < std::min<int64_t>(n, 32 * t + 32); ++i) mx = std::max(mx, eff(hperm[i]));
+            pad_sorted += 32ll * mx;
+        }
+        const bool sorted = pad_sorted * 5 < pad_plain * 4;
+        if (!sorted)
+            for (int64_t i = 0; i < n; ++i) hperm[i] = (int32_t)i;
+        for (int64_t t = 0; t < A->nslices; ++t) {
+            int mx = 0;
+            for (int64_t i = 32 * t; i < std::min<int64_t>(n, 32 * t + 32); ++i) mx = std::max(mx, eff(hperm[i]));
+            hw[t] = mx;
+        }
+        if (sorted) {
+            if (cudaMalloc(&A->perm, sizeof(int32_t) * n) != cudaSuccess) {
+                cudaGetLastError();
+                return cleanup(fail(SKF_ERR_OOM, "slice permutation allocation"));
+            }
+            cudaMemcpyAsync(A->perm, hperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+        }
+        cudaMemcpyAsync(A->sell_w, hw.data(), sizeof(int32_t) * A->nslices, cudaMemcpyHostToDevice, st);
         std::vector<uint2> hl((size_t)A->nslices, make_uint2(0u, 0u));
         std::vector<int32_t> seg0{0}, sb, se;
         int64_t nl = 0;
         for (int64_t t = 0; t < A->nslices; ++t) {
             hl[t].y = (unsigned)nl;
             for (int l = 0; l < 32 && 32 * t + l < n; ++l) {
-                const int64_t r = 32 * t + l;
+                const int64_t r = hperm[32 * t + l];
                 const int32_t b0 = hrp[r], b1 = hrp[r + 1];
                 if (b1 - b0 <= kLongRow) continue;
                 hl[t].x |= 1u << l;
@@ -951,11 +980,6 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
             if (e != cudaSuccess) return cleanup(cuda_fail(e, "row-split upload"));
         }
     }
-    k_sell_width<<<blocks, 256, 0, st>>>(A->rowptr, n, A->nslices, kLongRow, A->sell_w);
-    count_launches(1);
-    cudaMemcpyAsync(hw.data(), A->sell_w, sizeof(int32_t) * A->nslices, cudaMemcpyDeviceToHost, st);
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "SELL widths"));
     hoff[0] = 0;
     for (int64_t t = 0; t < A->nslices; ++t) {
         hoff[t + 1] = hoff[t] + 32ll * hw[t];
@@ -974,10 +998,12 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
     cudaMemcpyAsync(A->sell_off, hoff.data(), sizeof(int64_t) * (A->nslices + 1), cudaMemcpyHostToDevice, st);
     if (vdtype == SKF_F64)
         k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, A->nslices,
-                                            kLongRow, A->sell_off, A->sell_w, (double *)A->sell_val, A->sell_col);
+                                            kLongRow, A->perm, A->sell_off, A->sell_w, (double *)A->sell_val,
+                                            A->sell_col);
     else
         k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const float *)A->values, n, A->nslices,
-                                            kLongRow, A->sell_off, A->sell_w, (float *)A->sell_val, A->sell_col);
+                                            kLongRow, A->perm, A->sell_off, A->sell_w, (float *)A->sell_val,
+                                            A->sell_col);
     count_launches(1);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "SELL fill"));
@@ -997,6 +1023,7 @@ skf_status skf_destroy_csr(skf_csr *A) {
     if (A->sell_val) cudaFree(A->sell_val);
     if (A->sell_col) cudaFree(A->sell_col);
     if (A->sell_long) cudaFree(A->sell_long);
+    if (A->perm) cudaFree(A->perm);
     if (A->long_seg0) cudaFree(A->long_seg0);
     if (A->seg_beg) cudaFree(A->seg_beg);
     if (A->seg_end) cudaFree(A->seg_end);

@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv(ArnCtx c, int 
         so = __shfl_sync(0xffffffffu, so, 0);
         sl.x = __shfl_sync(0xffffffffu, sl.x, 0);
         sl.y = __shfl_sync(0xffffffffu, sl.y, 0);
-        const int64_t r = rw + lane;
-        if (r >= r1) continue;
+        const int64_t slot = rw + lane;
+        if (slot >= r1) continue;
+        const int64_t r = c.rs.perm ? (int64_t)__ldg(c.rs.perm + slot) : slot;   // the lane's row
         const int64_t base = so + lane;
         double y = 0.0;
         if (wt <= WMAX) {
@@ -715,7 +716,8 @@ void launch_steps(const ArnCtx &c, int G, int Gs, size_t smem, const SrhtDev *sd
     // slices up to 8 wide take the pipelined SpMV; wider ones the generic
     // kernel (16 unrolled product slots, an entry loop past 16)
     auto spmv = k_arnoldi_spmv<KW, 16>;
-    const bool pipe = c.max_width <= 8 && c.rs.sell_long == nullptr;   // a row split takes the generic SpMV
+    // a row split or a sorted slice layout takes the generic SpMV
+    const bool pipe = c.max_width <= 8 && c.rs.sell_long == nullptr && c.rs.perm == nullptr;
     // product slots of the pipelined SpMV: the widest slice rounded up to 5, 7
     // or 8 (a slot past a slice's width is a predicated-off FP64 instruction)
     auto spmv_pipe = c.max_width <= 5 ? k_arnoldi_spmv_pipe<KW, 5>

@@ -455,8 +455,8 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, in
         so = __shfl_sync(0xffffffffu, so, 0);
         sl.x = __shfl_sync(0xffffffffu, sl.x, 0);
         sl.y = __shfl_sync(0xffffffffu, sl.y, 0);
-        const int64_t r = rw + lane;
-        if (r >= c.n) continue;   // no warp-collective operation below
+        if (rw + lane >= c.n) continue;   // no warp-collective operation below
+        const int64_t r = c.rs.perm ? (int64_t)__ldg(c.rs.perm + rw + lane) : rw + lane;   // the lane's row
         // window values first: independent of the SpMV, their latency overlaps it
         float wv[KW];
 #pragma unroll
@@ -1005,7 +1005,7 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     if (smem_upd + static_upd > (size_t)optin || smem_spmv > (size_t)optin)
         return fail(SKF_ERR_NOT_SUPPORTED, "sketch size s too large for the shared-memory bins");
     // slices at most 8 wide: the pipelined SpMV (a row split takes the generic one)
-    const bool pipe = A->max_width <= 8 && A->nlong == 0;
+    const bool pipe = A->max_width <= 8 && A->nlong == 0 && A->perm == nullptr;
     c.rs = row_split_of(A);
 
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };

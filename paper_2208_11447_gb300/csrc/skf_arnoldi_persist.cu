@@ -805,7 +805,7 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
                                   int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
                                   skf_info *info, cudaStream_t st) {
     if (S->kind != SKF_SKETCH_SPARSE_SIGN || S->binmax_persist == nullptr || k > 4 || A->vdtype != SKF_F64 ||
-        A->nlong > 0)   // a row split (skewed rows) takes the two-kernel form
+        A->nlong > 0 || A->perm != nullptr)   // a row split or sorted slices take the two-kernel form
         return SKF_ERR_NOT_SUPPORTED;
     int G;
     int64_t R64;

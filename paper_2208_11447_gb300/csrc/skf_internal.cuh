@@ -71,6 +71,12 @@ struct skf_csr {
     // mask of the long rows of slice t, index of its first long row); the
     // segments of long row q are long_seg0[q] .. long_seg0[q+1] - 1.
     int64_t nlong = 0, nseg = 0;
+    // Sorted slices (irregular row lengths): within aligned windows of
+    // kSortWin rows the rows are taken in order of decreasing length, so that
+    // a slice holds rows of similar length and pads little; slot i of the
+    // slice layout holds row perm[i] (nullptr: slot i holds row i).  Chosen
+    // when it saves more than a fifth of the padded entries.
+    int32_t *perm = nullptr;          // [n] or nullptr
     uint2 *sell_long = nullptr;       // [nslices], nullptr without long rows
     int32_t *long_seg0 = nullptr;     // [nlong + 1]
     int32_t *seg_beg = nullptr;       // [nseg] first CSR entry of the segment
@@ -78,9 +84,11 @@ struct skf_csr {
 };
 constexpr int kLongRow = 32;          // longest row kept in the SELL slices
 constexpr int kSegLen = 1024;         // entries per segment of a long row (32 per lane)
+constexpr int kSortWin = 256;         // rows per sorting window of the sorted slice layout
 
 // The row split of an operator as the step kernels see it (see skf_csr).
 struct RowSplit {
+    const int32_t *perm = nullptr;        // slot -> row of the sorted slice layout, or nullptr
     const uint2 *sell_long = nullptr;     // nullptr: no long rows
     const int32_t *long_seg0 = nullptr;
     const int32_t *seg_beg = nullptr, *seg_end = nullptr;
@@ -91,6 +99,7 @@ struct RowSplit {
 
 inline RowSplit row_split_of(const skf_csr *A) {
     RowSplit r;
+    r.perm = A->perm;
     if (A->nlong > 0) {
         r.sell_long = A->sell_long;
         r.long_seg0 = A->long_seg0;

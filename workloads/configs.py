@@ -87,6 +87,12 @@ WORKLOADS = {
     "graph_n4m": Workload("graph_n4m", lambda: powerlaw_graph_operator(4_000_000, 2.1, 10.0, SEEDS["matrix"]),
                           "invsqrt", m=150, k=3, s=600, value_dtype="f32", basis_dtype="f32",
                           lam_lo=0.1, extra={"ell": 128}),
+    # the same graph with rows carrying the power-law out-degrees (hubs of up
+    # to ~1e5 entries: the row-split SpMV)
+    "graph_n4m_t": Workload("graph_n4m_t", lambda: powerlaw_graph_operator(4_000_000, 2.1, 10.0, SEEDS["matrix"],
+                                                                          transpose=True),
+                            "invsqrt", m=150, k=3, s=600, value_dtype="f32", basis_dtype="f32",
+                            lam_lo=0.1, extra={"ell": 128}),
     # the paper's own first experiment operator (upwind, D = 1e-3), n = 100
     "upwind_n100": Workload("upwind_n100", lambda: upwind_2d(100, 1e-3), "invsqrt", m=200, k=4, s=400,
                             lam_lo=None),

@@ -155,7 +155,8 @@ def powerlaw_graph_operator(N: int, alpha: float = 2.1, mean_degree: float = 10.
     src = np.repeat(np.arange(N, dtype=np.int64), deg)
     dst = rng.integers(0, N - 1, size=src.size, dtype=np.int64)
     dst = dst + (dst >= src)                       # skip the self-loop
-    key = np.unique(src * N + dst)                 # drop duplicates
+    key = np.sort(src * N + dst)                   # drop duplicates (sorted distinct keys)
+    key = key[np.concatenate([[True], key[1:] != key[:-1]])]
     src = key // N
     dst = key % N
     out_deg = np.bincount(src, minlength=N).astype(np.float64)
@@ -165,11 +166,12 @@ def powerlaw_graph_operator(N: int, alpha: float = 2.1, mean_degree: float = 10.
         rows, cols = src, dst      # row i holds -W[i, j]
     else:
         rows, cols = dst, src      # row i holds -W^T[i, j] = -W[j, i]
-    rows = np.concatenate([rows, np.arange(N, dtype=np.int64)])
-    cols = np.concatenate([cols, np.arange(N, dtype=np.int64)])
-    vals = np.concatenate([-np.ones(key.size), diag])
-    order = np.lexsort((cols, rows))
-    rows, cols, vals = rows[order], cols[order], vals[order]
+    # entries in (row, column) order: one sort of the distinct keys row N + col;
+    # the diagonal entries carry diag, the edges -1
+    diag_i = np.arange(N, dtype=np.int64)
+    keys = np.sort(np.concatenate([rows * N + cols, diag_i * N + diag_i]))
+    rows, cols = keys // N, keys % N
+    vals = np.where(rows == cols, diag[rows], -1.0)
     rowptr = np.zeros(N + 1, dtype=np.int64)
     np.cumsum(np.bincount(rows, minlength=N), out=rowptr[1:])
     return CSR(N, rowptr, cols.astype(np.int32), vals)
