@@ -885,7 +885,7 @@ def main():
     if basis == "f64" and fp64_bound_us >= hbm_bound_us:
         roof = {"bound": "alu", "achieved": round(achieved_gflops, 1), "peak": round(fp64_peak, 1),
                 "unit": "GFLOP/s", "frac": round(achieved_gflops / fp64_peak, 4), "traffic": None,
-                "peak_source": "measured: skf_fp64_peak (independent FP64 FMA chains on every SM, this run)"}
+                "peak_source": "measured: skf_fp64_peak (independent FP64 FMA accumulations on every SM, this run)"}
     else:
         roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src}

@@ -242,10 +242,12 @@ skf_status skf_set_arnoldi_mode(int32_t mode);
 skf_status skf_set_qr_mode(int32_t mode);
 
 /* skf_fp64_peak: measured FP64 FMA throughput of the current device in
- * GFLOP/s (2 flops per FMA): two CTAs of 512 threads per SM, eight
- * independent FMA chains per thread, 4096 iterations, timed with events on
- * `stream` after one warm-up launch (synchronises the stream).  The
- * denominator of the FP64 roofline fraction.  Errors: INVALID_ARG, OOM, CUDA. */
+ * GFLOP/s (2 flops per FMA): two CTAs of 512 threads per SM, four
+ * independent accumulations x += y b per thread (the operand pattern of a dot
+ * product, the fastest FMA form measured on this part), 8192 iterations,
+ * timed with events on `stream` after one warm-up launch (synchronises the
+ * stream).  The denominator of the FP64 roofline fraction.
+ * Errors: INVALID_ARG, OOM, CUDA. */
 skf_status skf_fp64_peak(double *gflops, skf_stream_t stream);
 
 /* skf_workspace_trim: return the device memory that the library's
