@@ -663,7 +663,8 @@ def graph_extras(dev, reps: int = 2):
     skf_arnoldi_trunc, median of reps, L2 flushed), its fraction of the
     measured HBM copy rate for the algorithmic bytes, and the relative error
     of the FP32 sGMRES solve against the FP64 GPU path on the same operator
-    (values widened exactly), sketch and rule."""
+    (values widened exactly), sketch and rule.  The slice layout is chosen
+    first by skf_csr_autotune (its per-candidate step times are reported)."""
     import numpy as np
     import torch
     import paper_2208_11447_gb300 as skf
@@ -683,6 +684,7 @@ def graph_extras(dev, reps: int = 2):
         t_nodes, w_nodes = skf.quadrature_rule(skf.make_func(wl.func, c), int(wl.extra["ell"]))
         f = skf.make_func(wl.func, c, nodes=t_nodes, weights=w_nodes)
         b_dev = torch.as_tensor(b, device=dev)
+        tune = skf.csr_autotune(op32.csr, S, wl.k, basis_dtype=torch.float32, m_probe=6)   # the slice layout
         ts = []
         for r in range(reps + 1):
             flush.zero_()
@@ -702,6 +704,7 @@ def graph_extras(dev, reps: int = 2):
         torch.cuda.synchronize()
         res[name] = {"rows": "power-law out-degrees (row split)" if name.endswith("_t") else "in-degrees",
                      "N": int(A.n), "nnz": int(A.nnz), "max_row": int(L.max()), "rows_over_32": int((L > 32).sum()),
+                     "layout": tune["choice"], "layout_us_per_step": [round(x, 1) for x in tune["times_us"]],
                      "us_per_step": round(us, 2), "alg_bytes_per_step": int(alg),
                      "hbm_frac": round(alg / (us * 1e-6) / 1e9 / hbm_peak, 4), "of": hbm_src,
                      "rel_err_vs_fp64_gpu": float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))}

@@ -300,6 +300,30 @@ skf_status skf_destroy_csr(skf_csr *A);
 /* Host copy of the matrix's max absolute row sum (an upper bound for |lambda|). */
 skf_status skf_csr_norm_inf(const skf_csr *A, double *out_host);
 
+/* skf_csr_autotune: choose the operator's slice layout by timing.  The
+ * kernels read A in SELL-32 slices; rows longer than a cut leave the slices
+ * and are reduced in segments of at most 1024 entries (row split), and the
+ * rows may be sorted by length inside windows of 256 rows (less padding for
+ * irregular row lengths).  skf_create_csr picks cut 32, unsorted.  This call
+ * builds each of six
+ * candidates (cut 16, 32, 64; unsorted, then sorted), times m_probe steps of
+ * the truncated Arnoldi process with sketch S, truncation k and basis type
+ * `basis` on a fixed probe vector (the minimum of two runs after a warm-up;
+ * m_probe <= 0 selects 8), and keeps the fastest layout in A.
+ * times_us (nullable, host double[6]): microseconds per step of each
+ * candidate in that order; choice (nullable, host): the index kept.
+ * Synchronises `stream`; A must not be in use on another stream meanwhile.
+ * Results of later solves change only by the order of the long rows' sums.
+ * Errors: INVALID_ARG, OOM, CUDA, NOT_SUPPORTED (as skf_arnoldi_trunc). */
+skf_status skf_csr_autotune(skf_csr *A, const skf_sketch *S, int32_t k, skf_dtype basis, int32_t m_probe,
+                            double *times_us, int32_t *choice, skf_stream_t stream);
+
+/* skf_csr_set_layout: rebuild A's slice layout with rows longer than `cut`
+ * entries split off (cut >= 1) and sorted = 1 (sorted slices), 0 (unsorted)
+ * or -1 (sorted when that saves over a fifth of the padding, the default).
+ * Synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA. */
+skf_status skf_csr_set_layout(skf_csr *A, int32_t cut, int32_t sorted, skf_stream_t stream);
+
 /* -------------------------------------------------------------- sketch */
 /* skf_sketch_create: draw the embedding S in R^{s x N} (Algorithm 1, line 1;
  * eq. (1.1)).  The sparse-sign pattern is expanded once on the device from

@@ -118,12 +118,15 @@ def lib():
         L.skf_set_tail_form.argtypes = [i32]
         L.skf_workspace_trim.argtypes = []
         L.skf_fp64_peak.argtypes = [ctypes.POINTER(dbl), vp]
+        L.skf_csr_autotune.argtypes = [vp, vp, i32, ctypes.c_int, i32, ctypes.POINTER(dbl), ctypes.POINTER(i32), vp]
+        L.skf_csr_set_layout.argtypes = [vp, i32, i32, vp]
         L.skf_barrier_selftest.argtypes = [i32, i64, vp, vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
                      "skf_solve", "skf_solve_batched", "skf_sfom", "skf_sfom_sgmres",
                      "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c", "skf_set_arnoldi_mode",
-                     "skf_set_qr_mode", "skf_set_tail_form", "skf_workspace_trim", "skf_fp64_peak", "skf_barrier_selftest"]:
+                     "skf_set_qr_mode", "skf_set_tail_form", "skf_workspace_trim", "skf_fp64_peak", "skf_csr_autotune", "skf_csr_set_layout",
+                     "skf_barrier_selftest"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -430,6 +433,24 @@ class qr_mode:
 
 
 TAIL_AUTO, TAIL_FULL = 0, 1
+
+
+AUTOTUNE_CANDIDATES = [{"cut": c, "sorted": s} for s in (False, True) for c in (16, 32, 64)]
+
+
+def csr_autotune(A: "Csr", S: "Sketch", k: int, basis_dtype=torch.float64, m_probe: int = 8, stream=None) -> dict:
+    """skf_csr_autotune: time the six slice layouts and keep the fastest in A.
+    Returns {"choice": {...}, "times_us": [...per candidate]}."""
+    t = (ctypes.c_double * 6)()
+    ch = ctypes.c_int32(-1)
+    _check(lib().skf_csr_autotune(A.handle, S.handle, k, _DTYPE[basis_dtype], m_probe, t, ctypes.byref(ch),
+                                  _stream(stream)))
+    return {"choice": dict(AUTOTUNE_CANDIDATES[ch.value]), "times_us": [float(x) for x in t]}
+
+
+def csr_set_layout(A: "Csr", cut: int, sorted_: int = -1, stream=None) -> None:
+    """skf_csr_set_layout: rows over `cut` entries split off; sorted_ 1, 0 or -1 (automatic)."""
+    _check(lib().skf_csr_set_layout(A.handle, cut, sorted_, _stream(stream)))
 
 
 def fp64_peak(stream=None) -> float:

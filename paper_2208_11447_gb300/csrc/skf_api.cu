@@ -824,6 +824,144 @@ skf_status skf_barrier_selftest(int32_t ctas, int64_t budget_cycles, int32_t *st
     return barrier_selftest(ctas, budget_cycles, (int *)status_device, (cudaStream_t)stream);
 }
 
+// The slice layout of A (see skf_csr): rows longer than `cut` entries take
+// the row-split path; sort: 1 rows sorted by length in windows of kSortWin,
+// 0 not sorted, -1 sorted when that saves over a fifth of the padded entries.
+// Replaces any earlier layout (sell_w and sell_off stay allocated).
+static void free_layout(skf_csr *A) {
+    if (A->sell_val) cudaFree(A->sell_val);
+    if (A->sell_col) cudaFree(A->sell_col);
+    if (A->perm) cudaFree(A->perm);
+    if (A->sell_long) cudaFree(A->sell_long);
+    if (A->long_seg0) cudaFree(A->long_seg0);
+    if (A->seg_beg) cudaFree(A->seg_beg);
+    if (A->seg_end) cudaFree(A->seg_end);
+    A->sell_val = nullptr;
+    A->sell_col = nullptr;
+    A->perm = nullptr;
+    A->sell_long = nullptr;
+    A->long_seg0 = A->seg_beg = A->seg_end = nullptr;
+    A->nlong = A->nseg = 0;
+    A->max_width = 0;
+    A->max_chunk_entries = 0;
+}
+
+static skf_status build_layout(skf_csr *A, int cut, int sort, cudaStream_t st) {
+    const int64_t n = A->n;
+    const size_t esz = A->vdtype == SKF_F64 ? 8 : 4;
+    cudaError_t e = cudaStreamSynchronize(st);   // an earlier layout may still be in use on st
+    if (e != cudaSuccess) return cuda_fail(e, "layout");
+    free_layout(A);
+    A->long_cut = cut;
+    std::vector<int32_t> hw(A->nslices);
+    std::vector<int64_t> hoff(A->nslices + 1);
+    std::vector<int32_t> hrp((size_t)n + 1);
+    cudaMemcpyAsync(hrp.data(), A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "row lengths");
+    auto eff = [&](int64_t r) {
+        const int32_t len = hrp[r + 1] - hrp[r];
+        return len > cut ? 0 : len;
+    };
+    std::vector<int32_t> hperm((size_t)n);
+    for (int64_t i = 0; i < n; ++i) hperm[i] = (int32_t)i;
+    auto padded_of = [&]() {
+        int64_t pad = 0;
+        for (int64_t t = 0; t < A->nslices; ++t) {
+            int mx = 0;
+            for (int64_t i = 32 * t; i < std::min<int64_t>(n, 32 * t + 32); ++i) mx = std::max(mx, eff(hperm[i]));
+            pad += 32ll * mx;
+        }
+        return pad;
+    };
+    bool sorted = false;
+    if (sort != 0) {
+        const int64_t pad_plain = padded_of();
+        for (int64_t w0 = 0; w0 < n; w0 += kSortWin) {
+            const int64_t w1 = std::min<int64_t>(n, w0 + kSortWin);
+            std::stable_sort(hperm.begin() + w0, hperm.begin() + w1,
+                             [&](int32_t x, int32_t y) { return eff(x) > eff(y); });
+        }
+        sorted = sort == 1 || padded_of() * 5 < pad_plain * 4;
+        if (!sorted)
+            for (int64_t i = 0; i < n; ++i) hperm[i] = (int32_t)i;
+    }
+    for (int64_t t = 0; t < A->nslices; ++t) {
+        int mx = 0;
+        for (int64_t i = 32 * t; i < std::min<int64_t>(n, 32 * t + 32); ++i) mx = std::max(mx, eff(hperm[i]));
+        hw[t] = mx;
+    }
+    if (sorted) {
+        if (cudaMalloc(&A->perm, sizeof(int32_t) * n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SKF_ERR_OOM, "slice permutation allocation");
+        }
+        cudaMemcpyAsync(A->perm, hperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+    }
+    cudaMemcpyAsync(A->sell_w, hw.data(), sizeof(int32_t) * A->nslices, cudaMemcpyHostToDevice, st);
+    // row split: long rows, their segments and the per-slice masks
+    std::vector<uint2> hl((size_t)A->nslices, make_uint2(0u, 0u));
+    std::vector<int32_t> seg0{0}, sb, se;
+    int64_t nl = 0;
+    for (int64_t t = 0; t < A->nslices; ++t) {
+        hl[t].y = (unsigned)nl;
+        for (int l = 0; l < 32 && 32 * t + l < n; ++l) {
+            const int64_t r = hperm[32 * t + l];
+            const int32_t b0 = hrp[r], b1 = hrp[r + 1];
+            if (b1 - b0 <= cut) continue;
+            hl[t].x |= 1u << l;
+            for (int32_t p0 = b0; p0 < b1; p0 += kSegLen) {
+                sb.push_back(p0);
+                se.push_back(std::min(b1, p0 + kSegLen));
+            }
+            seg0.push_back((int32_t)sb.size());
+            ++nl;
+        }
+    }
+    A->nlong = nl;
+    A->nseg = (int64_t)sb.size();
+    if (nl > 0) {
+        if (cudaMalloc(&A->sell_long, sizeof(uint2) * A->nslices) != cudaSuccess ||
+            cudaMalloc(&A->long_seg0, sizeof(int32_t) * seg0.size()) != cudaSuccess ||
+            cudaMalloc(&A->seg_beg, sizeof(int32_t) * sb.size()) != cudaSuccess ||
+            cudaMalloc(&A->seg_end, sizeof(int32_t) * se.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SKF_ERR_OOM, "row-split allocation");
+        }
+        cudaMemcpyAsync(A->sell_long, hl.data(), sizeof(uint2) * A->nslices, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(A->long_seg0, seg0.data(), sizeof(int32_t) * seg0.size(), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(A->seg_beg, sb.data(), sizeof(int32_t) * sb.size(), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(A->seg_end, se.data(), sizeof(int32_t) * se.size(), cudaMemcpyHostToDevice, st);
+    }
+    hoff[0] = 0;
+    for (int64_t t = 0; t < A->nslices; ++t) {
+        hoff[t + 1] = hoff[t] + 32ll * hw[t];
+        A->max_width = std::max(A->max_width, hw[t]);
+    }
+    for (int64_t t0 = 0; t0 < A->nslices; t0 += kChunkRows / 32) {
+        const int64_t t1 = std::min<int64_t>(A->nslices, t0 + kChunkRows / 32);
+        A->max_chunk_entries = std::max<int64_t>(A->max_chunk_entries, hoff[t1] - hoff[t0]);
+    }
+    const int64_t padded = hoff[A->nslices];
+    if (cudaMalloc(&A->sell_val, esz * std::max<int64_t>(padded, 1)) != cudaSuccess ||
+        cudaMalloc(&A->sell_col, sizeof(int32_t) * std::max<int64_t>(padded, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SKF_ERR_OOM, "SELL allocation");
+    }
+    cudaMemcpyAsync(A->sell_off, hoff.data(), sizeof(int64_t) * (A->nslices + 1), cudaMemcpyHostToDevice, st);
+    const int blocks = (int)std::min<int64_t>((n + 256) / 256, 8 * num_sms());
+    if (A->vdtype == SKF_F64)
+        k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, A->nslices, cut,
+                                            A->perm, A->sell_off, A->sell_w, (double *)A->sell_val, A->sell_col);
+    else
+        k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const float *)A->values, n, A->nslices, cut,
+                                            A->perm, A->sell_off, A->sell_w, (float *)A->sell_val, A->sell_col);
+    count_launches(1);
+    e = cudaStreamSynchronize(st);   // the host vectors above are released on return
+    if (e != cudaSuccess) return cuda_fail(e, "SELL fill");
+    return SKF_OK;
+}
+
 skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind, const void *values,
                           skf_dtype vdtype, skf_copy_mode mode, skf_stream_t stream, skf_csr **A_out) {
     if (!A_out) return fail(SKF_ERR_INVALID_ARG, "A_out is NULL");
@@ -895,123 +1033,19 @@ skf_status skf_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const i
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "skf_create_csr"));
     if (hbad) return cleanup(fail(SKF_ERR_INVALID_ARG, "column index out of range"));
     memcpy(&A->norm_inf, &hmax, sizeof(double));
-    // SELL-32 copy for the kernels
+    // SELL-32 copy for the kernels: rows over kLongRow entries split off,
+    // slices unsorted (sorting paid on neither graph workload when timed:
+    // skf_csr_autotune chooses it where it does)
     A->nslices = (n + 31) / 32;
-    std::vector<int32_t> hw(A->nslices);
-    std::vector<int64_t> hoff(A->nslices + 1);
     if (cudaMalloc(&A->sell_w, sizeof(int32_t) * A->nslices) != cudaSuccess ||
         cudaMalloc(&A->sell_off, sizeof(int64_t) * (A->nslices + 1)) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(fail(SKF_ERR_OOM, "SELL allocation"));
     }
-    // row split: long rows, their segments and the per-slice masks (host)
     {
-        std::vector<int32_t> hrp((size_t)n + 1);
-        cudaMemcpyAsync(hrp.data(), A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, st);
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, "row lengths"));
-        // slice widths with and without sorting by length in windows
-        auto eff = [&](int64_t r) {
-            const int32_t len = hrp[r + 1] - hrp[r];
-            return len > kLongRow ? 0 : len;
-        };
-        std::vector<int32_t> hperm((size_t)n);
-        for (int64_t i = 0; i < n; ++i) hperm[i] = (int32_t)i;
-        int64_t pad_plain = 0, pad_sorted = 0;
-        for (int64_t t = 0; t < A->nslices; ++t) {
-            int mx = 0;
-            for (int64_t r = 32 * t; r < std::min<int64_t>(n, 32 * t + 32); ++r) mx = std::max(mx, eff(r));
-            pad_plain += 32ll * mx;
-        }
-        for (int64_t w0 = 0; w0 < n; w0 += kSortWin) {
-            const int64_t w1 = std::min<int64_t>(n, w0 + kSortWin);
-            std::stable_sort(hperm.begin() + w0, hperm.begin() + w1,
-                             [&](int32_t x, int32_t y) { return eff(x) > eff(y); });
-        }
-        for (int64_t t = 0; t < A->nslices; ++t) {
-            int mx = 0;
-            for (int64_t i = 32 * t; i < std::min<int64_t>(n, 32 * t + 32); ++i) mx = std::max(mx, eff(hperm[i]));
-            pad_sorted += 32ll * mx;
-        }
-        const bool sorted = pad_sorted * 5 < pad_plain * 4;
-        if (!sorted)
-            for (int64_t i = 0; i < n; ++i) hperm[i] = (int32_t)i;
-        for (int64_t t = 0; t < A->nslices; ++t) {
-            int mx = 0;
-            for (int64_t i = 32 * t; i < std::min<int64_t>(n, 32 * t + 32); ++i) mx = std::max(mx, eff(hperm[i]));
-            hw[t] = mx;
-        }
-        if (sorted) {
-            if (cudaMalloc(&A->perm, sizeof(int32_t) * n) != cudaSuccess) {
-                cudaGetLastError();
-                return cleanup(fail(SKF_ERR_OOM, "slice permutation allocation"));
-            }
-            cudaMemcpyAsync(A->perm, hperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
-        }
-        cudaMemcpyAsync(A->sell_w, hw.data(), sizeof(int32_t) * A->nslices, cudaMemcpyHostToDevice, st);
-        std::vector<uint2> hl((size_t)A->nslices, make_uint2(0u, 0u));
-        std::vector<int32_t> seg0{0}, sb, se;
-        int64_t nl = 0;
-        for (int64_t t = 0; t < A->nslices; ++t) {
-            hl[t].y = (unsigned)nl;
-            for (int l = 0; l < 32 && 32 * t + l < n; ++l) {
-                const int64_t r = hperm[32 * t + l];
-                const int32_t b0 = hrp[r], b1 = hrp[r + 1];
-                if (b1 - b0 <= kLongRow) continue;
-                hl[t].x |= 1u << l;
-                for (int32_t p0 = b0; p0 < b1; p0 += kSegLen) {
-                    sb.push_back(p0);
-                    se.push_back(std::min(b1, p0 + kSegLen));
-                }
-                seg0.push_back((int32_t)sb.size());
-                ++nl;
-            }
-        }
-        A->nlong = nl;
-        A->nseg = (int64_t)sb.size();
-        if (nl > 0) {
-            if (cudaMalloc(&A->sell_long, sizeof(uint2) * A->nslices) != cudaSuccess ||
-                cudaMalloc(&A->long_seg0, sizeof(int32_t) * seg0.size()) != cudaSuccess ||
-                cudaMalloc(&A->seg_beg, sizeof(int32_t) * sb.size()) != cudaSuccess ||
-                cudaMalloc(&A->seg_end, sizeof(int32_t) * se.size()) != cudaSuccess) {
-                cudaGetLastError();
-                return cleanup(fail(SKF_ERR_OOM, "row-split allocation"));
-            }
-            cudaMemcpyAsync(A->sell_long, hl.data(), sizeof(uint2) * A->nslices, cudaMemcpyHostToDevice, st);
-            cudaMemcpyAsync(A->long_seg0, seg0.data(), sizeof(int32_t) * seg0.size(), cudaMemcpyHostToDevice, st);
-            cudaMemcpyAsync(A->seg_beg, sb.data(), sizeof(int32_t) * sb.size(), cudaMemcpyHostToDevice, st);
-            cudaMemcpyAsync(A->seg_end, se.data(), sizeof(int32_t) * se.size(), cudaMemcpyHostToDevice, st);
-            e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return cleanup(cuda_fail(e, "row-split upload"));
-        }
+        const skf_status ls = build_layout(A, kLongRow, 0, st);
+        if (ls != SKF_OK) return cleanup(ls);
     }
-    hoff[0] = 0;
-    for (int64_t t = 0; t < A->nslices; ++t) {
-        hoff[t + 1] = hoff[t] + 32ll * hw[t];
-        A->max_width = std::max(A->max_width, hw[t]);
-    }
-    for (int64_t t0 = 0; t0 < A->nslices; t0 += kChunkRows / 32) {
-        const int64_t t1 = std::min<int64_t>(A->nslices, t0 + kChunkRows / 32);
-        A->max_chunk_entries = std::max<int64_t>(A->max_chunk_entries, hoff[t1] - hoff[t0]);
-    }
-    const int64_t padded = hoff[A->nslices];
-    if (cudaMalloc(&A->sell_val, esz * std::max<int64_t>(padded, 1)) != cudaSuccess ||
-        cudaMalloc(&A->sell_col, sizeof(int32_t) * std::max<int64_t>(padded, 1)) != cudaSuccess) {
-        cudaGetLastError();
-        return cleanup(fail(SKF_ERR_OOM, "SELL allocation"));
-    }
-    cudaMemcpyAsync(A->sell_off, hoff.data(), sizeof(int64_t) * (A->nslices + 1), cudaMemcpyHostToDevice, st);
-    if (vdtype == SKF_F64)
-        k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const double *)A->values, n, A->nslices,
-                                            kLongRow, A->perm, A->sell_off, A->sell_w, (double *)A->sell_val,
-                                            A->sell_col);
-    else
-        k_sell_fill<<<blocks, 256, 0, st>>>(A->rowptr, A->colind, (const float *)A->values, n, A->nslices,
-                                            kLongRow, A->perm, A->sell_off, A->sell_w, (float *)A->sell_val,
-                                            A->sell_col);
-    count_launches(1);
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "SELL fill"));
     cudaFree(dbad);
     cudaFree(dmax);
     *A_out = A;
@@ -1033,6 +1067,103 @@ skf_status skf_destroy_csr(skf_csr *A) {
     if (A->seg_beg) cudaFree(A->seg_beg);
     if (A->seg_end) cudaFree(A->seg_end);
     delete A;
+    return SKF_OK;
+}
+
+// Deterministic probe vector for the layout autotuner: entries in [-1, 1)
+// from SplitMix64 of the row index (no meaning beyond "dense and signed").
+__global__ void k_probe_rhs(double *b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        b[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+}
+
+skf_status skf_csr_set_layout(skf_csr *A, int32_t cut, int32_t sorted, skf_stream_t stream) {
+    if (!A) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    if (cut < 1 || sorted < -1 || sorted > 1) return fail(SKF_ERR_INVALID_ARG, "need cut >= 1 and sorted in -1..1");
+    return build_layout(A, cut, sorted, (cudaStream_t)stream);
+}
+
+// Layout candidates of skf_csr_autotune: (row-split cut, sorted slices).
+static const int kTuneCut[] = {16, 32, 64, 16, 32, 64};
+static const int kTuneSort[] = {0, 0, 0, 1, 1, 1};
+constexpr int kTuneCandidates = 6;
+
+skf_status skf_csr_autotune(skf_csr *A, const skf_sketch *S, int32_t k, skf_dtype basis, int32_t m_probe,
+                            double *times_us, int32_t *choice, skf_stream_t stream) {
+    if (!A || !S) return fail(SKF_ERR_INVALID_ARG, "NULL argument");
+    if (m_probe <= 0) m_probe = 8;
+    const double dummy = 0.0;
+    skf_status stt = check_common(A, S, &dummy, SKF_F64, m_probe, k, basis);
+    if (stt != SKF_OK) return stt;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = A->n;
+    const int m = m_probe;
+    const int s = S->s;
+    const int64_t ldv = (n + 63) / 64 * 64;
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t szV = dtype_size(basis) * (size_t)ldv * m;
+    const size_t total = al(sizeof(double) * n) + al(szV) + 2 * al(sizeof(double) * (size_t)s * m) +
+                         al(sizeof(double) * (size_t)(m + 1) * m) + al(sizeof(double) * m) + al(sizeof(int) * 4);
+    char *ws = nullptr;
+    stt = dalloc((void **)&ws, total, st);
+    if (stt != SKF_OK) return stt;
+    size_t off = 0;
+    auto take = [&](size_t sz) {
+        char *p = ws + off;
+        off += al(sz);
+        return p;
+    };
+    double *b = (double *)take(sizeof(double) * n);
+    void *V = take(szV);
+    double *SV = (double *)take(sizeof(double) * (size_t)s * m);
+    double *SAV = (double *)take(sizeof(double) * (size_t)s * m);
+    double *H = (double *)take(sizeof(double) * (size_t)(m + 1) * m);
+    double *vscale = (double *)take(sizeof(double) * m);
+    int *iscal = (int *)take(sizeof(int) * 4);
+    k_probe_rhs<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8ll * num_sms()), 256, 0, st>>>(b, n);
+    count_launches(1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        dfree(ws, st);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    double t[kTuneCandidates];
+    int best = -1;
+    for (int c = 0; c < kTuneCandidates && stt == SKF_OK; ++c) {
+        stt = build_layout(A, kTuneCut[c], kTuneSort[c], st);
+        double tmin = INFINITY;
+        for (int rep = 0; rep < 3 && stt == SKF_OK; ++rep) {   // the first run warms up
+            cudaEventRecord(e0, st);
+            stt = run_arnoldi(A, S, b, m, k, basis, V, ldv, vscale, SV, SAV, H, iscal, nullptr, st);
+            cudaEventRecord(e1, st);
+            if (stt != SKF_OK) break;
+            float ms = 0.f;
+            const cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                stt = cuda_fail(ce != cudaSuccess ? ce : cudaGetLastError(), "autotune timing");
+                break;
+            }
+            if (rep > 0) tmin = std::min(tmin, (double)ms * 1e3 / m);
+        }
+        t[c] = tmin;
+        if (stt == SKF_OK && (best < 0 || t[c] < t[best])) best = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(ws, st);
+    // keep the fastest layout (or restore the default one after a failure)
+    const skf_status ls = best >= 0 && stt == SKF_OK ? build_layout(A, kTuneCut[best], kTuneSort[best], st)
+                                                     : build_layout(A, kLongRow, 0, st);
+    if (stt != SKF_OK) return stt;
+    if (ls != SKF_OK) return ls;
+    if (times_us)
+        for (int c = 0; c < kTuneCandidates; ++c) times_us[c] = t[c];
+    if (choice) *choice = best;
     return SKF_OK;
 }
 

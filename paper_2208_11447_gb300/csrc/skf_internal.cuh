@@ -71,11 +71,12 @@ struct skf_csr {
     // mask of the long rows of slice t, index of its first long row); the
     // segments of long row q are long_seg0[q] .. long_seg0[q+1] - 1.
     int64_t nlong = 0, nseg = 0;
+    int long_cut = 0;                 // rows longer than this take the row split (kLongRow unless tuned)
     // Sorted slices (irregular row lengths): within aligned windows of
     // kSortWin rows the rows are taken in order of decreasing length, so that
     // a slice holds rows of similar length and pads little; slot i of the
-    // slice layout holds row perm[i] (nullptr: slot i holds row i).  Chosen
-    // when it saves more than a fifth of the padded entries.
+    // slice layout holds row perm[i] (nullptr: slot i holds row i).  Built by
+    // skf_csr_set_layout / skf_csr_autotune, not by default.
     int32_t *perm = nullptr;          // [n] or nullptr
     uint2 *sell_long = nullptr;       // [nslices], nullptr without long rows
     int32_t *long_seg0 = nullptr;     // [nlong + 1]

@@ -52,21 +52,6 @@ def test_operator_widths():
     assert sell_max_width(OPS["graph"]) > 16
 
 
-def sorted_layout(A):
-    """Whether the library takes the sorted slice layout for A (rows sorted
-    by length in windows of 256 when that saves over a fifth of the padded
-    entries); such operators run the two-kernel form only."""
-    L = np.diff(A.rowptr)
-    e = np.where(L > 32, 0, L)
-    n = len(L)
-
-    def padded(order):
-        return 32 * np.pad(e[order], (0, (-n) % 32)).reshape(-1, 32).max(axis=1).sum()
-
-    o = np.concatenate([w0 + np.argsort(-e[w0:w0 + 256], kind="stable") for w0 in range(0, n, 256)])
-    return padded(o) * 5 < padded(np.arange(n)) * 4
-
-
 def arnoldi_both(skf, A, b, m, k, s, mode):
     op = upload(skf, A)
     S = skf.Sketch(skf.SPARSE_SIGN, A.n, s, 8, 13)
@@ -113,8 +98,6 @@ def cond_R(ar, S):
                                     if not (nm == "graph" and k == 1)])
 def test_wide_rows_per_column(skf, name, mode, k):
     A = OPS[name]
-    if mode == "persistent" and sorted_layout(A):
-        pytest.skip("sorted slice layout: two-kernel form only (test_sorted_layout_refuses_persistent)")
     b = gaussian_rhs(A.n, 12)
     m = M_OF[name]
     s = 4 * m
@@ -124,9 +107,10 @@ def test_wide_rows_per_column(skf, name, mode, k):
 
 
 def test_sorted_layout_refuses_persistent(skf):
+    """Sorted slices (skf_csr_set_layout) take the two-kernel form only."""
     A = OPS["graph"]
-    assert sorted_layout(A) and not sorted_layout(OPS["ninepoint"])
     op = upload(skf, A)
+    skf.csr_set_layout(op.csr, 32, 1)
     S = skf.Sketch(skf.SPARSE_SIGN, A.n, 40, 8, 13)
     with skf.arnoldi_mode(skf.ARNOLDI_PERSISTENT):
         with pytest.raises(skf.SkfError, match="NOT_SUPPORTED"):
@@ -138,8 +122,6 @@ def test_sorted_layout_refuses_persistent(skf):
 @pytest.mark.parametrize("method", ["sgmres", "sfom"])
 def test_wide_rows_solve(skf, name, mode, method):
     A = OPS[name]
-    if mode == "persistent" and sorted_layout(A):
-        pytest.skip("sorted slice layout: two-kernel form only")
     b = gaussian_rhs(A.n, 12)
     m, k = (40 if name != "graph" else M_OF[name]), 2
     s = 4 * m
