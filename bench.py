@@ -514,6 +514,27 @@ def batch_arms(dev, steps: int, warmup: int, lanes_arg, world: int = 1, n_rhs: i
     out["errs32"] = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(x32, x64)]
     out["flags32"] = [skf.read_info(inf32[r])["nodes_fp64"] > 0 for r in range(nprob)]
     out["status32"] = statuses(inf32)
+    # mixed precision: the library's plan (one pilot Arnoldi process per
+    # operator) picks an FP32 basis where cond(R) 2^-24 <= 1e-6, FP64 elsewhere
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cond, use32 = skf.plan_basis_precision(probs32, BATCH_TOL)
+    out["plan_ms"] = (time.perf_counter() - t0) * 1e3
+    xmx = [torch.empty_like(b) for b in b_dev]
+    infmx = torch.zeros_like(inf64)
+    probsmx = [(skf.SGMRES, (op32 if use32[r] else op64)[q.mat].csr, sketches[r], b_dev[r], funcs[r],
+                (p32 if use32[r] else p64)[r], xmx[r], infmx[r]) for r, q in enumerate(layout.rhs)]
+    graphmx = skf.BatchGraph(probsmx, lanes=lanes)
+    for _ in range(warmup):
+        graphmx.replay()
+    torch.cuda.synchronize()
+    replica_barrier(world)
+    out["tmx"] = replica_max(timed(graphmx.replay, steps), world, dev)
+    del graphmx
+    out["errsmx"] = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(xmx, x64)]
+    out["usemx"] = use32
+    out["condmx"] = cond
+    out["statusmx"] = statuses(infmx)
     return out
 
 
@@ -524,6 +545,7 @@ def batch_summary(o, steps: int, world: int = 1):
     v64b = replica_value(world, nprob * steps, o["t64b"])
     v64 = replica_value(world, nprob * steps, o["t64"])
     v32 = replica_value(world, nprob * steps, o["t32"])
+    vmx = replica_value(world, nprob * steps, o["tmx"])
     errs, flags = o["errs32"], o["flags32"]
     return {
         "fp64_one_at_a_time": {"value": round(v64, 3), "unit": "solves/s",
@@ -542,6 +564,17 @@ def batch_summary(o, steps: int, world: int = 1):
                              "flagged_err_le_tol": sum(1 for f, e in zip(flags, errs) if f and e <= tol),
                              "unflagged_err_gt_tol": sum(1 for f, e in zip(flags, errs) if not f and e > tol),
                              "unflagged_err_le_tol": sum(1 for f, e in zip(flags, errs) if not f and e <= tol)}},
+        "mixed_batched": {"value": round(vmx, 3), "unit": "solves/s", "ms_per_batch": round(o["tmx"] / steps, 3),
+                          "speedup_vs_fp64_one_at_a_time": round(vmx / v64, 3),
+                          "speedup_vs_fp64_batched": round(vmx / v64b, 3),
+                          "fp32_problems": sum(1 for u in o["usemx"] if u), "of": nprob,
+                          "max_rel_err": max(o["errsmx"]), "within_1e-6": sum(1 for e in o["errsmx"] if e <= tol),
+                          "max_rel_err_fp32_problems": max([e for e, u in zip(o["errsmx"], o["usemx"]) if u],
+                                                           default=0.0),
+                          "status": o["statusmx"], "plan_ms": round(o["plan_ms"], 1),
+                          "policy": "skf_plan_basis_precision: FP32 basis where cond(R) 2^-24 <= 1e-6 (cond(R) "
+                                    "of the whitening of a pilot basis, one pilot Arnoldi process per operator), "
+                                    "FP64 elsewhere; planned once outside the timed region"},
         "errors_vs": "FP64 one-at-a-time GPU path, same problems; gate 1e-6",
     }
 
@@ -585,6 +618,7 @@ def run_batch(args, rank, world, local, dev):
             "fp64_one_at_a_time": summ["fp64_one_at_a_time"],
             "speedup_vs_fp64_one_at_a_time": summ["fp64_batched"]["speedup_vs_fp64_one_at_a_time"],
             "fp32_batched": summ["fp32_batched"],
+            "mixed_batched": summ["mixed_batched"],
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src,
                          "kernel": "whole FP64 batch: algorithmic Arnoldi bytes (sum_r m_r (B_A + 3 N 8)) over the "
@@ -696,18 +730,26 @@ def graph_extras(dev, reps: int = 2):
                 ts.append(ev0.elapsed_time(ev1))
         us = statistics.median(ts) * 1e3 / wl.m
         alg = A.nnz * 8 + 4 * (A.n + 1) + (wl.k + 1) * A.n * 4
-        x32 = skf.sgmres(op32.csr, S, b_dev, f, skf.make_params(wl.m, wl.k, basis_dtype=torch.float32, tol=1e-10))
+        i32 = skf.new_info(dev)
+        x32 = skf.sgmres(op32.csr, S, b_dev, f, skf.make_params(wl.m, wl.k, basis_dtype=torch.float32, tol=1e-10),
+                         info=i32)
         torch.cuda.synchronize()
         del op32
         op64 = skf.upload_csr(A.rowptr, A.colind, A.values.astype(np.float64), device=dev)
-        x64 = skf.sgmres(op64.csr, S, b_dev, f, skf.make_params(wl.m, wl.k, tol=1e-10))
+        i64 = skf.new_info(dev)
+        x64 = skf.sgmres(op64.csr, S, b_dev, f, skf.make_params(wl.m, wl.k, tol=1e-10), info=i64)
         torch.cuda.synchronize()
+        cond64 = skf.read_info(i64)["cond_est"]
+        err = float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))
         res[name] = {"rows": "power-law out-degrees (row split)" if name.endswith("_t") else "in-degrees",
                      "N": int(A.n), "nnz": int(A.nnz), "max_row": int(L.max()), "rows_over_32": int((L > 32).sum()),
                      "layout": tune["choice"], "layout_us_per_step": [round(x, 1) for x in tune["times_us"]],
                      "us_per_step": round(us, 2), "alg_bytes_per_step": int(alg),
                      "hbm_frac": round(alg / (us * 1e-6) / 1e9 / hbm_peak, 4), "of": hbm_src,
-                     "rel_err_vs_fp64_gpu": float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))}
+                     "rel_err_vs_fp64_gpu": err, "cond_R_fp64": cond64,
+                     "tolerance": {"rule": "max(1e-6, 2^-24 cond(R)) (FP32 basis against FP64, cond(R) of the "
+                                           "FP64 whitening)", "value": max(1e-6, 2.0 ** -24 * cond64),
+                                   "met": err <= max(1e-6, 2.0 ** -24 * cond64)}}
         del op64, x32, x64, S
         torch.cuda.empty_cache()
     res["workload"] = "graph N = 4e6, FP32 values and basis, m = 150, k = 3, s = 600, 128 nodes, sGMRES z^-1/2"

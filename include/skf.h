@@ -374,8 +374,9 @@ skf_status skf_sketch_apply(const skf_sketch *S, const void *X, skf_dtype xdtype
  * sparse-sign sketch and F64 X, computed without allocating any device
  * memory.  The paper has no counterpart; this entry point exists for callers
  * that cannot call cudaMalloc/cudaMallocAsync at the point of use (a runtime
- * that owns and budgets every device allocation, or a path that must not
- * synchronise or touch the allocator).  Its scratch is a fixed 4 MiB array
+ * that owns and budgets every device allocation, or a path that must leave
+ * the allocator and its memory pools untouched): this call makes no allocator
+ * or memory-pool call at all.  Its scratch is a fixed 4 MiB array
  * inside this library, which every GPU that loads the library keeps until
  * the process exits; it must hold G * ncols * (s + 1) doubles, G being the
  * kernels' CTA count (at most 2 per SM), otherwise the call returns
@@ -502,6 +503,27 @@ typedef struct {
  * Errors: INVALID_ARG (also nprob < 0, lanes outside 1..16), OOM, CUDA,
  *   SKETCH_TOO_SMALL, NOT_SUPPORTED. */
 skf_status skf_solve_batched(int32_t nprob, const skf_problem *probs, int32_t lanes, skf_stream_t stream);
+
+/* skf_plan_basis_precision: per problem, whether an FP32 Krylov basis is
+ * expected to stay within `tol` (relative 2-norm) of the FP64-basis result.
+ * This is the precision policy of the batched form; the paper has no
+ * counterpart (it stores every basis in double precision).  Reasoning: an
+ * FP32 basis perturbs every stored vector by a relative 2^-24, and the
+ * approximant, computed from the sketched basis S V_m through its whitening
+ * S V_m = Q R (Sec. 2.1, Sec. 3), moves by about 2^-24 cond(R); the rule is
+ * FP32 iff cond(R) 2^-24 <= tol.  cond(R) is taken from a pilot: for each
+ * distinct operator A among `probs`, the problem with the largest m runs
+ * its Arnoldi process (its sketch, b, k and basis dtype, F64 or F32), and
+ * for every problem r on that operator the whitening of the pilot's
+ * leading m_r columns gives the estimate skf_info::cond_est describes (the
+ * condition number of a sketched Krylov basis is a property of A, k and m
+ * far more than of b or of the sketch's seed).  Outputs (host): cond_host[r]
+ * and f32_host[r] (1: FP32 basis, 0: FP64).  The problems are validated as
+ * by skf_solve_batched; their x and info are not touched.  Synchronises
+ * `stream`.  Errors: INVALID_ARG, NOT_SUPPORTED (a BF16 pilot), OOM, CUDA,
+ * SKETCH_TOO_SMALL. */
+skf_status skf_plan_basis_precision(int32_t nprob, const skf_problem *probs, double tol, double *cond_host,
+                                    int32_t *f32_host, skf_stream_t stream);
 
 /* skf_quadrature_rule: host copy of the rule of order ell for f (the same
  * nodes and weights the solvers use).  t_host, w_host: host double[ell].

@@ -121,12 +121,14 @@ def lib():
         L.skf_csr_autotune.argtypes = [vp, vp, i32, ctypes.c_int, i32, ctypes.POINTER(dbl), ctypes.POINTER(i32), vp]
         L.skf_csr_set_layout.argtypes = [vp, i32, i32, vp]
         L.skf_barrier_selftest.argtypes = [i32, i64, vp, vp]
+        L.skf_plan_basis_precision.argtypes = [i32, ctypes.POINTER(Problem), dbl, ctypes.POINTER(dbl),
+                                               ctypes.POINTER(i32), vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
                      "skf_solve", "skf_solve_batched", "skf_sfom", "skf_sfom_sgmres",
                      "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c", "skf_set_arnoldi_mode",
                      "skf_set_qr_mode", "skf_set_tail_form", "skf_workspace_trim", "skf_fp64_peak", "skf_csr_autotune", "skf_csr_set_layout",
-                     "skf_barrier_selftest"]:
+                     "skf_barrier_selftest", "skf_plan_basis_precision"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -197,11 +199,21 @@ def sketch_create(kind, n, s, zeta=8, seed=13, stream=None) -> Sketch:
     return Sketch(kind, n, s, zeta, seed, stream)
 
 
-def sketch_apply(S: Sketch, X: torch.Tensor, SX: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """SX = S X for X of shape (N,) or (N, ncols) (column-major storage: X.T contiguous)."""
+def _column_major(X: torch.Tensor) -> torch.Tensor:
+    """(ncols, N) view whose rows are the columns of X, contiguous; no copy when
+    X (N,) or (N, ncols) already stores its columns one after another."""
     Xc = X.reshape(X.shape[0], -1)
-    ncols = Xc.shape[1]
-    Xcm = Xc.t().contiguous()           # column-major: column c at offset c*N
+    Xt = Xc.t()
+    return Xt if Xt.is_contiguous() else Xt.contiguous()
+
+
+def sketch_apply(S: Sketch, X: torch.Tensor, SX: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """SX = S X for X of shape (N,) or (N, ncols).  The C ABI reads X column-major
+    (column c at offset c*N); a tensor already laid out that way (X.t() contiguous,
+    as for X = Y.t() with Y contiguous) is passed as it is, any other is copied
+    into that order first."""
+    Xcm = _column_major(X)
+    ncols = Xcm.shape[0]
     if SX is None:
         SX = torch.empty((ncols, S.s), dtype=torch.float64, device=X.device)
     _check(lib().skf_sketch_apply(S.handle, _ptr(Xcm), _DTYPE[X.dtype], X.shape[0], ncols, _ptr(SX),
@@ -211,11 +223,12 @@ def sketch_apply(S: Sketch, X: torch.Tensor, SX: torch.Tensor | None = None, str
 
 
 def sketch_apply_noalloc(S: Sketch, X: torch.Tensor, SX: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """As sketch_apply, through the allocation-free entry point (the output
-    tensor is allocated here, by the caller of the C ABI, as the ABI requires)."""
-    Xc = X.reshape(X.shape[0], -1)
-    ncols = Xc.shape[1]
-    Xcm = Xc.t().contiguous()
+    """As sketch_apply, through the allocation-free entry point.  The library
+    call allocates nothing; this binding may: it creates SX when none is given,
+    and copies X into column-major order when it is not already in it (pass a
+    column-major X and an SX to allocate nothing at all)."""
+    Xcm = _column_major(X)
+    ncols = Xcm.shape[0]
     if SX is None:
         SX = torch.empty((ncols, S.s), dtype=torch.float64, device=X.device)
     _check(lib().skf_sketch_apply_noalloc(S.handle, _ptr(Xcm), _DTYPE[X.dtype], X.shape[0], ncols, _ptr(SX),
@@ -334,16 +347,31 @@ def sfom_sgmres(A, S, b, f, p, x_fom=None, x_gmres=None, info_fom=None, info_gmr
     return x_fom, x_gmres
 
 
-def solve_batched(problems, lanes: int = 4, stream=None):
-    """skf_solve_batched.  problems: sequence of (method, A, S, b, f, p, x,
-    info) with x a preallocated F64 tensor and info a buffer from new_info()
-    or None.  Returns the list of x."""
+def _problem_array(problems):
     arr = (Problem * len(problems))()
     for i, (method, A, S, b, f, p, x, info) in enumerate(problems):
         arr[i] = Problem(method, A.handle, S.handle, b.data_ptr(), _DTYPE[b.dtype], ctypes.pointer(f),
                          ctypes.pointer(p), x.data_ptr(), _DTYPE[x.dtype], info.data_ptr() if info is not None else 0)
+    return arr
+
+
+def solve_batched(problems, lanes: int = 4, stream=None):
+    """skf_solve_batched.  problems: sequence of (method, A, S, b, f, p, x,
+    info) with x a preallocated F64 tensor and info a buffer from new_info()
+    or None.  Returns the list of x."""
+    arr = _problem_array(problems)
     _check(lib().skf_solve_batched(len(problems), arr, lanes, _stream(stream)))
     return [q[6] for q in problems]
+
+
+def plan_basis_precision(problems, tol: float, stream=None):
+    """skf_plan_basis_precision: (cond, use_f32) per problem, two lists."""
+    n = len(problems)
+    arr = _problem_array(problems)
+    cond = (ctypes.c_double * max(n, 1))()
+    f32 = (ctypes.c_int32 * max(n, 1))()
+    _check(lib().skf_plan_basis_precision(n, arr, tol, cond, f32, _stream(stream)))
+    return [cond[i] for i in range(n)], [bool(f32[i]) for i in range(n)]
 
 
 class BatchGraph:

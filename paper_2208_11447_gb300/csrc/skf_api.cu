@@ -1360,6 +1360,101 @@ skf_status skf_solve_batched(int32_t nprob, const skf_problem *probs, int32_t la
     return SKF_OK;
 }
 
+// ---------------------------------------------------------------- precision plan
+// iscal of one query of skf_plan_basis_precision: the leading min(m_q, m_eff)
+// columns of the pilot basis, status OK, not stopped.
+__global__ void k_plan_query(const int *__restrict__ pilot_iscal, int mq, int *__restrict__ iscal) {
+    if (threadIdx.x == 0) {
+        const int me = pilot_iscal[1] < mq ? pilot_iscal[1] : mq;
+        iscal[0] = 0;
+        iscal[1] = me;
+        iscal[2] = SKF_OK;
+        iscal[3] = me;
+    }
+}
+
+skf_status skf_plan_basis_precision(int32_t nprob, const skf_problem *probs, double tol, double *cond_host,
+                                    int32_t *f32_host, skf_stream_t stream) {
+    if (nprob < 0 || (nprob > 0 && (!probs || !cond_host || !f32_host)))
+        return fail(SKF_ERR_INVALID_ARG, "bad problem or output array");
+    if (!(tol > 0.0)) return fail(SKF_ERR_INVALID_ARG, "tol must be > 0");
+    std::vector<const RuleDev *> rules((size_t)nprob, nullptr);
+    for (int i = 0; i < nprob; ++i) {
+        const skf_problem &q = probs[i];
+        const skf_status st = solve_check(q.method, q.A, q.S, q.b, q.bdtype, q.f, q.p, q.x, q.xdtype, &rules[i]);
+        if (st != SKF_OK) return fail(st, "problem " + std::to_string(i) + ": " + skf_last_error());
+        if (q.p->basis_dtype == SKF_BF16)
+            return fail(SKF_ERR_NOT_SUPPORTED, "problem " + std::to_string(i) + ": plan from an FP64 or FP32 basis");
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    const double u32 = 5.9604644775390625e-08;   // 2^-24
+    std::vector<bool> done((size_t)nprob, false);
+    for (int i = 0; i < nprob; ++i) {
+        if (done[i]) continue;
+        // the problems on this operator; the pilot is the one with the largest m
+        std::vector<int> grp;
+        int pl = i;
+        for (int r = i; r < nprob; ++r)
+            if (!done[r] && probs[r].A == probs[i].A) {
+                grp.push_back(r);
+                if (probs[r].p->m > probs[pl].p->m) pl = r;
+            }
+        const skf_problem &q = probs[pl];
+        const skf_params &pp = *q.p;
+        const int m = pp.m, s = q.S->s;
+        const int64_t n = q.A->n;
+        const int64_t ldv = (n + 63) / 64 * 64;
+        auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+        const size_t szV = dtype_size(pp.basis_dtype) * (size_t)ldv * m;
+        const size_t szS = sizeof(double) * (size_t)s * m;
+        const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
+        const size_t nq = grp.size();
+        const size_t total = al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4) +
+                             nq * (al(sizeof(int) * 4) + al(sizeof(skf_info)));
+        char *ws = nullptr;
+        skf_status st = dalloc((void **)&ws, total, cs);
+        if (st != SKF_OK) return st;
+        size_t off = 0;
+        void *V = (void *)(ws + off); off += al(szV);
+        double *SV = (double *)(ws + off); off += al(szS);
+        double *SAV = (double *)(ws + off); off += al(szS);
+        double *H = (double *)(ws + off); off += al(szH);
+        double *vscale = (double *)(ws + off); off += al(sizeof(double) * m);
+        int *iscal = (int *)(ws + off); off += al(sizeof(int) * 4);
+        std::vector<int *> qis(nq);
+        std::vector<skf_info *> qinf(nq);
+        for (size_t t = 0; t < nq; ++t) {
+            qis[t] = (int *)(ws + off); off += al(sizeof(int) * 4);
+            qinf[t] = (skf_info *)(ws + off); off += al(sizeof(skf_info));
+        }
+        st = run_arnoldi(q.A, q.S, (const double *)q.b, m, pp.k, pp.basis_dtype, V, ldv, vscale, SV, SAV, H, iscal,
+                         nullptr, cs);
+        // the whitening of the leading m_r columns: its cond(R) estimate
+        for (size_t t = 0; t < nq && st == SKF_OK; ++t) {
+            k_plan_query<<<1, 32, 0, cs>>>(iscal, probs[grp[t]].p->m, qis[t]);
+            count_launches(1);
+            st = tail_run(SKF_METHOD_SGMRES, s, probs[grp[t]].p->m, 0, nullptr, SKF_F64, 0, vscale, SV, SAV, qis[t],
+                          *rules[pl], pp.tol, nullptr, qinf[t], cs, nullptr, nullptr, nullptr, 0.0, H, m + 1, pp.k);
+        }
+        std::vector<skf_info> hinf(nq);
+        cudaError_t e = cudaSuccess;
+        for (size_t t = 0; t < nq && st == SKF_OK && e == cudaSuccess; ++t)
+            e = cudaMemcpyAsync(&hinf[t], qinf[t], sizeof(skf_info), cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        dfree(ws, cs);
+        if (st != SKF_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "precision plan");
+        for (size_t t = 0; t < nq; ++t) {
+            const int r = grp[t];
+            done[r] = true;
+            const double cnd = hinf[t].cond_est;
+            cond_host[r] = cnd;
+            f32_host[r] = (cnd > 0.0 && cnd * u32 <= tol) ? 1 : 0;
+        }
+    }
+    return SKF_OK;
+}
+
 skf_status skf_sfom(const skf_csr *A, const skf_sketch *S, const void *b, skf_dtype bdtype, const skf_func *f,
                     const skf_params *p, void *x, skf_dtype xdtype, skf_info *info, skf_stream_t stream) {
     return skf_solve(SKF_METHOD_SFOM, A, S, b, bdtype, f, p, x, xdtype, info, stream);

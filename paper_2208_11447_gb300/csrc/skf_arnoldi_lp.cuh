@@ -312,7 +312,14 @@ template <typename TB>
 __device__ __forceinline__ bool spmv_begin(const LpCtx &c, int j, bool &stopping) {
     if (c.iscal[0] && c.iscal[3] < j) return false;   // stopped at an earlier step
     const double *sc_j = c.stepsc + 4 * (size_t)j;
-    if (j >= 1 && blockIdx.x == 0 && threadIdx.x == 0) c.H[j + (size_t)(j - 1) * (c.m + 1)] = sc_j[1];
+    // h_{j,j-1} of the relation the stored basis satisfies: update j - 1 formed
+    // w_j = sigf y_{j-1} - ... with sigf = cf[0], the FP32 value of sigma_{j-1},
+    // so A v_{j-1} = sigma_{j-1} y_{j-1} has the coefficient
+    // sigma_{j-1} ||w_j|| / sigf on v_j = w_j / ||w_j|| (||w_j|| up to one FP32
+    // rounding of sigma_{j-1})
+    if (j >= 1 && blockIdx.x == 0 && threadIdx.x == 0)
+        c.H[j + (size_t)(j - 1) * (c.m + 1)] =
+            c.stepsc[4 * (size_t)(j - 1)] * sc_j[1] / c.coef[(size_t)(j - 1) * kCoef];
     // zero right-hand side (j = 0) or happy breakdown, decided by the previous
     // launch: m_eff = j.  S w_j is still formed (S y_{j-1} needs it).
     stopping = sc_j[2] != 0.0;
@@ -698,8 +705,15 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
         double *cf = c.coef + (size_t)j * kCoef;
         cf[0] = (double)sigf;
         for (int a = 0; a < nw; ++a) cf[1 + a] = (double)scf[a];
+        // H holds the coefficients of the relation the stored basis satisfies
+        // with the FP32 coefficients applied (the one S A v_j is formed from):
+        // A v_j = (sigma_j / sigf) (v_{j+1} / sigma_{j+1} + sum_a scf_a v_{i0+a} / sigma_{i0+a}),
+        // each within one FP32 rounding of the MGS coefficient h_a
         if (do_update)
-            for (int a = 0; a < nw; ++a) c.H[(i0 + a) + (size_t)j * (c.m + 1)] = sh[a];
+            for (int a = 0; a < nw; ++a) {
+                const double sa = (i0 + a == j) ? sigma : c.vscale[i0 + a];
+                c.H[(i0 + a) + (size_t)j * (c.m + 1)] = sigma * (double)scf[a] / ((double)sigf * sa);
+            }
         c.ex[j] = ew;
     }
     // one-limb fixed point for the BF16 residual: |bf16(w) - w| <= 2^-8 |w|

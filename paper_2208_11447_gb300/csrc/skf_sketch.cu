@@ -291,9 +291,10 @@ skf_status sketch_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, i
 //
 // Some callers cannot allocate device memory at the point where they need a
 // sketch: code running inside a memory-budgeted runtime that owns every
-// allocation, callers that must not synchronise (cudaMalloc/cudaFree can
-// synchronise the device), or code paths that are forbidden to change the
-// allocator's state.  For them the scratch of the column-max / scatter /
+// allocation, or code paths that must not touch the allocator or its memory
+// pools at all (the allocating path goes through cudaMallocAsync and
+// cudaFreeAsync on the library's pool; this one makes no allocator or pool
+// call of any kind).  For them the scratch of the column-max / scatter /
 // reduce pipeline (per-CTA column maxima and per-CTA integer partial sums)
 // lives in the fixed array below instead of coming from cudaMallocAsync.
 //

@@ -12,7 +12,7 @@
 // Each node is solved from its normal equations by Cholesky with one step of
 // FP64 iterative refinement on the original residual.
 //
-// With an FP64 basis the tail factors only the s x (m+1) matrix
+// With an FP64 or FP32 basis the tail factors only the s x (m+1) matrix
 // [S V_m, S A v_m] instead (relation form): the Arnoldi relation
 // A v_j = sum_i h_ij v_i (i <= j + 1, eq. (2.1)) sketched gives
 // S A v_j = S V_m H(1:m, j) for j < m, so with [S V_m, S A v_m] = Q R,
@@ -1741,8 +1741,12 @@ skf_status tail_run_multi(int nout, const TailOut *outs, int s, int m, int64_t n
     int *iscal = outs[0].iscal;
     TailCtx c{};
     c.cond_max = cond_max;
-    // relation form where the basis is FP64 and H is given (see the top of the file)
-    c.rel = (tail_form() != 1 && H != nullptr && vdt == SKF_F64 && m >= 1) ? 1 : 0;
+    // relation form where H is given and the sketched relation holds for the
+    // stored basis: FP64, and FP32 (whose S A v_j, j < m - 1, are formed from
+    // that relation with the coefficients the update applied).  A BF16 basis
+    // keeps the full form: its relation is off by the storage rounding of
+    // w_{j+1}, which S A v_j takes off.
+    c.rel = (tail_form() != 1 && H != nullptr && (vdt == SKF_F64 || vdt == SKF_F32) && m >= 1) ? 1 : 0;
     c.H = H;
     c.ldh = ldh;
     c.kt = kt;

@@ -284,3 +284,35 @@ def test_graph_fixed_rule_128_nodes(skf):
     print(f"graph 128-node sgmres: err f32 {e32:.3e}, err f64 {e64:.3e}, f32 vs f64 {d:.3e}, "
           f"rdiag_ratio {st['rdiag_ratio']:.3e}")
     assert e32 <= 2.0 * e64 + 1e-6
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("method", ["sgmres", "sfom"])
+def test_f32_relation_form_equals_full_form(skf, k, method):
+    """FP32 basis: its S A v_j (j < m - 1) are formed from the sketched Arnoldi
+    relation with the coefficients the update applied, so the relation-form
+    tail (QR of [S V_m, S A v_m], M = [R_11 H, r] R_11^{-1}) and the full form
+    (QR of [S V_m, S A V_m]) factor the same sketched relation and agree to
+    FP64 rounding times cond(R); both stay within max(1e-6, 2^-24 cond(R)) of
+    the FP64 oracle."""
+    A = convdiff_2d(100, (100.0, 50.0))
+    b = gaussian_rhs(A.n, 12)
+    c = quad_scale("invsqrt", laplacian_lambda_min(100, 2), float(abs(csr_to_scipy(A)).sum(1).max()))
+    m = 16 if k == 1 else 40
+    s = 4 * m
+    meth = skf.SGMRES if method == "sgmres" else skf.SFOM
+    x_rel, i_rel = solve_lp(skf, A, b, "invsqrt", m, k, s, c, meth, "f32")
+    with skf.tail_form(skf.TAIL_FULL):
+        x_full, i_full = solve_lp(skf, A, b, "invsqrt", m, k, s, c, meth, "f32")
+    xo, oi = osk.solve(csr_to_scipy(A), b, "invsqrt", m, k, OSketch("sparse_sign", A.n, s, 8, 13), c,
+                       method="sgmres" if method == "sgmres" else "sfom_quad", tol=1e-12)
+    assert i_rel["status"] == 0 and i_full["status"] == 0
+    assert i_rel["ell"] == i_full["ell"]
+    d = rel(x_rel, x_full)
+    print(f"f32 k={k} {method}: relation vs full {d:.3e}, cond_est {i_rel['cond_est']:.3e}, "
+          f"vs oracle {rel(x_rel, xo):.3e}")
+    assert d <= max(1e-10, 1e-14 * i_rel["cond_est"])
+    # against the FP64 oracle: the FP32 basis moves the approximant by about
+    # 2^-24 cond(R) (k = 1 loses basis independence fastest: cond(R) ~ 9e2 here)
+    bound = max(BOUND["f32"], 2.0 ** -24 * i_rel["cond_est"])
+    assert rel(x_rel, xo) <= bound and rel(x_full, xo) <= bound
