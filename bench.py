@@ -53,7 +53,8 @@ METRIC = {"f64": "f(A)b solves/s (sFOM + sGMRES, FP64)",
           "bf16": "f(A)b solves/s (sFOM + sGMRES, BF16 basis, FP32 arithmetic, FP64 tail)"}
 
 
-SKETCH_KIND = {"sparse_sign": lambda skf: skf.SPARSE_SIGN, "srht": lambda skf: skf.SRHT}
+SKETCH_KIND = {"sparse_sign": lambda skf: skf.SPARSE_SIGN, "srht": lambda skf: skf.SRHT,
+               "srdct": lambda skf: skf.SRDCT}
 
 
 def basis_torch(name: str):
@@ -688,6 +689,36 @@ def precision_extras(dev, reps: int = 3):
     return res
 
 
+def sketch_extras(dev, op, A, b_dev, wl, m: int = 12, reps: int = 3):
+    """Truncated-Arnoldi step of the default operator (FP64 basis, the
+    two-kernel form) with each sketch kind: sparse-sign, SRHT and the
+    paper's SRDCT (N = 1e6 = 2^6 5^6: the FFT form of the DCT-II).  CUDA
+    events around skf_arnoldi_trunc over m steps, median of reps, L2
+    flushed; sparse-sign in the two-kernel form for a like comparison."""
+    import torch
+    import paper_2208_11447_gb300 as skf
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    with skf.arnoldi_mode(skf.ARNOLDI_TWO_KERNEL):
+        for kind in ("sparse_sign", "srht", "srdct"):
+            S = skf.Sketch(SKETCH_KIND[kind](skf), A.n, wl.s, wl.zeta if kind == "sparse_sign" else 0, 13)
+            ts = []
+            for r in range(reps + 1):
+                flush.zero_()
+                ev0.record(stream)
+                skf.arnoldi_trunc(op.csr, S, b_dev, m, wl.k)
+                ev1.record(stream)
+                ev1.synchronize()
+                if r > 0:
+                    ts.append(ev0.elapsed_time(ev1))
+            out[kind] = {"us_per_step": round(statistics.median(ts) * 1e3 / m, 2)}
+            del S
+    out["workload"] = f"cd3d_n100 (N = 1e6), FP64 basis, k = {wl.k}, s = {wl.s}, m = {m}, two-kernel Arnoldi form"
+    return out
+
+
 def graph_extras(dev, reps: int = 2):
     """The quadrature-batched graph workloads (N = 4e6 directed power-law
     graph, FP32 values and basis, m = 150, k = 3, s = 600, 128 fixed
@@ -979,7 +1010,8 @@ def main():
         del V, SV, SAV, H
         torch.cuda.empty_cache()
         t_ex = time.perf_counter()
-        extras = {"precision": precision_extras(dev)}
+        extras = {"sketch_kinds": sketch_extras(dev, op, A, b_dev, wl)}
+        extras["precision"] = precision_extras(dev)
         extras["graph"] = graph_extras(dev)
         bo = batch_arms(dev, 1, 1, "16")
         extras["batch"] = {"workload": "batch_cd_8x64 (8 operators, 64 right-hand sides, m_r in [50, 400], "

@@ -1216,6 +1216,8 @@ skf_status skf_sketch_destroy(skf_sketch *S) {
     if (S->pattern8) cudaFree(S->pattern8);
     if (S->E) cudaFree(S->E);
     if (S->costab) cudaFree(S->costab);
+    if (S->tw) cudaFree(S->tw);
+    if (S->twist) cudaFree(S->twist);
     delete S;
     return SKF_OK;
 }

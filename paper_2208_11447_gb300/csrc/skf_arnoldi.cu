@@ -866,8 +866,9 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     const size_t szEps = sizeof(double) * (size_t)m;
     c.rs = row_split_of(A);
     const size_t szSeg = sizeof(double) * (size_t)std::max<int64_t>(c.rs.nseg, 1);
+    const size_t szDct = c.direct ? srdct_work_bytes(S) : 0;   // FFT form of the SRDCT: its complex buffers
     const size_t total = al(szY) + al(szP1) + al(szP2) + al(szFd) + al(szFw) + al(szSc) + al(szCnt) + 2 * al(szSk) +
-                         al(szGram) + 2 * al(szE) + al(szEps) + al(szSeg);
+                         al(szGram) + 2 * al(szE) + al(szEps) + al(szSeg) + al(szDct);
     skf_status stt = dalloc((void **)&ws, total, st);
     if (stt != SKF_OK) return stt;
     size_t off = 0;
@@ -890,6 +891,7 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
     c.ews = (int *)take(szE);
     c.epscol = (double *)take(szEps);
     c.seg_part = (double *)take(szSeg);
+    if (szDct) dd.work = (double2 *)take(szDct);
     cudaMemsetAsync(c.cnt, 0, szCnt, st);
 
     const size_t smem = c.sparse ? sizeof(int) * 4 * S->s : 0;   // two limbs for each of S v_j, S A v_j

@@ -402,6 +402,8 @@ __device__ __forceinline__ int last_y_exponent(const LpCtx &c, int j) {
 // (lane-strided, then a butterfly whose lane-0 result is the partial).
 template <typename TB>
 __global__ void __launch_bounds__(256) k_spmv_long_lp(LpCtx c, int j) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent (see k_arnoldi_spmv_lp)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (c.iscal[0] && c.iscal[3] < j) return;
     const TB *x = (const TB *)c.V + vcol(c, j);
     const float *vals = (const float *)c.rs.values;
@@ -422,6 +424,11 @@ template <int KW, int ZCAP, typename TB>
 __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp(LpCtx c, int j) {
     extern __shared__ int bins[];   // [2 s]: limbs of S w_j (stopping step) or of S y_{m-1} (last step)
     __shared__ double red[32 * KW];
+    // programmatic dependent of the previous launch: every CTA waits for it
+    // in full before reading anything (and before any exit), then releases
+    // the next launch so that its CTAs are placed while this one runs
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     bool stopping;
     if (!spmv_begin<TB>(c, j, stopping)) return;
     if (stopping) {
@@ -509,6 +516,8 @@ template <int KW, int ZCAP, typename TB>
 __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp_pipe(LpCtx c, int j) {
     extern __shared__ int bins[];   // [2 s]: limbs of S w_j (stopping step) or of S y_{m-1} (last step)
     __shared__ double red[32 * KW];
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent (see k_arnoldi_spmv_lp)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     bool stopping;
     if (!spmv_begin<TB>(c, j, stopping)) return;
     if (stopping) {
@@ -655,6 +664,8 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_arnoldi_update_lp(LpCtx c, i
     __shared__ double sh[kMaxK];     // MGS coefficients h_ij
     __shared__ float scf[kMaxK];     // h_ij sigma_i in FP32, as applied
     __shared__ float sigf_s;
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent (see k_arnoldi_spmv_lp)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (c.iscal[0] && c.iscal[3] <= j) return;   // stopped at this step (set by its spmv launch) or earlier
     TB *V = (TB *)c.V;
     const int G = gridDim.x;
@@ -943,14 +954,32 @@ void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, 
     if (smem_upd > 48 * 1024)
         cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_upd);
     const unsigned gid = (unsigned)std::min<int64_t>((c.n + kThreads - 1) / kThreads, 8ll * c.G);
+    // the step kernels are launched as programmatic dependents of the launch
+    // before them (each waits for it in full; only the placement overlaps)
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    auto config = [&](unsigned grid, unsigned block, size_t smem) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(block);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = pdl;
+        cfg.numAttrs = 1;
+        return cfg;
+    };
+    const cudaLaunchConfig_t cfg_l = config((unsigned)long_ctas(c.rs.nseg, num_sms()), 256, 0);
+    const cudaLaunchConfig_t cfg_s = config((unsigned)c.G, kSpmvThreads, smem_spmv);
+    const cudaLaunchConfig_t cfg_u = config((unsigned)c.G, kUpdThreads, smem_upd);
     for (int j = 0; j < c.m; ++j) {
         LpCtx cj = c;
         window_offsets(cj, j);
-        if (c.rs.sell_long) k_spmv_long_lp<TB><<<long_ctas(c.rs.nseg, num_sms()), 256, 0, st>>>(cj, j);
-        spmv<<<c.G, kSpmvThreads, smem_spmv, st>>>(cj, j);
+        if (c.rs.sell_long) cudaLaunchKernelEx(&cfg_l, k_spmv_long_lp<TB>, cj, j);
+        cudaLaunchKernelEx(&cfg_s, spmv, cj, j);
         if (j >= 1) call_hook(hook, j - 1, st);   // S v_i, S A v_i final for i < j - 1
         if (c.identity) k_identity_cols_lp<TB><<<gid, kThreads, 0, st>>>(cj, j);
-        update<<<c.G, kUpdThreads, smem_upd, st>>>(cj, j);
+        cudaLaunchKernelEx(&cfg_u, update, cj, j);
         if (j + 1 < c.m) call_col_hook(hook, j + 1, st);
     }
 }

@@ -139,7 +139,15 @@ struct skf_sketch {
     int64_t np = 0;                   // SRHT: padded length N' (SRDCT: N)
     int32_t *P = nullptr;             // SRHT, SRDCT: s sampled rows (device)
     double *E = nullptr;              // SRDCT: the N signs (device)
-    double *costab = nullptr;         // SRDCT: cos(pi j / (2N)), j = 0 .. 4N-1 (device)
+    double *costab = nullptr;         // SRDCT, direct form: cos(pi j / (2N)), j = 0 .. 4N-1 (device)
+    // SRDCT through a length-N FFT (N with no prime factor above 7): the
+    // radices of its Stockham passes, e^{-2 pi i t / N} for t < N, and per
+    // sampled row k the DCT twist e^{-i pi k / (2N)} times the row's scale
+    // (device); nrad = 0: the direct form
+    int nrad = 0;
+    int rad[64] = {};
+    double2 *tw = nullptr;
+    double2 *twist = nullptr;
     // Sparse-sign pattern, expanded once from the seed: entry [c * zeta + q]
     // holds the row of nonzero q of column c inside stripe q (bits 0-14) and
     // its sign (bit 15).  2 zeta bytes per column.
@@ -606,14 +614,20 @@ skf_status build_srht_tables(skf_sketch *S);
 void srht_launch(const SrhtDev &d, const SrhtCols &cols, cudaStream_t st);
 skf_status srht_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX, cudaStream_t st);
 
-// SRDCT sketch (see skf_srdct.cu): direct O(sN) evaluation of the sampled
-// rows of the orthonormal DCT-II.
+// SRDCT sketch (see skf_srdct.cu): the sampled rows of the orthonormal
+// DCT-II, through a length-N FFT (O(N log N) per vector) when N has no prime
+// factor above 7, else by direct O(sN) evaluation.
 struct SrdctDev {
     int64_t n;
     int s;
     const int32_t *P;       // [s] sampled rows
     const double *E;        // [n] signs
-    const double *costab;   // [4n] cos(pi j / (2n))
+    const double *costab;   // [4n] cos(pi j / (2n)) (direct form)
+    int nrad;               // FFT form: Stockham passes (0: direct form)
+    int rad[64];
+    const double2 *tw;      // [n] e^{-2 pi i t / n}
+    const double2 *twist;   // [s] e^{-i pi k / (2n)} a_k sqrt(n / s), k = P[i]
+    double2 *work;          // FFT form: [2][2][n] scratch of the caller
 };
 // Up to two columns: out[q][i] = colscale * (S x[q])_i (colscale a device
 // scalar or nullptr for 1); iscal/step as for SrhtCols.
@@ -625,6 +639,8 @@ struct SrdctCols {
     const int *iscal;
     int step;
 };
+// bytes of the FFT form's scratch (0 for the direct form)
+size_t srdct_work_bytes(const skf_sketch *S);
 SrdctDev make_srdct(const skf_sketch *S);
 skf_status build_srdct_tables(skf_sketch *S);
 void srdct_launch(const SrdctDev &d, const SrdctCols &cols, cudaStream_t st);

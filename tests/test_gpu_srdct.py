@@ -21,7 +21,12 @@ from gpu_helpers import rel
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("N,s,ncols", [(1, 1, 1), (7, 5, 3), (1000, 200, 2), (10000, 400, 4)])
+# N with no prime factor above 7 takes the FFT form (Makhoul's reordering and
+# Stockham passes of radices 4, 2, 3, 5, 7: 7 = [7], 1000 = [4, 2, 5, 5, 5],
+# 4725 = [3, 3, 3, 5, 5, 7] (odd N), 125000 = [4, 2, 5 x 6]); 1013 (prime) and
+# 9409 = 97^2 the direct form
+@pytest.mark.parametrize("N,s,ncols", [(1, 1, 1), (7, 5, 3), (1000, 200, 2), (10000, 400, 4), (4725, 300, 2),
+                                       (125000, 800, 2), (1013, 300, 2), (9409, 400, 2)])
 def test_srdct_apply_matches_oracle(skf, N, s, ncols):
     X = np.random.default_rng(N + s).standard_normal((N, ncols))
     S = skf.Sketch(skf.SRDCT, N, s, 0, 17)
@@ -54,6 +59,32 @@ def test_srdct_arnoldi_and_solve_match_oracle(skf):
         torch.cuda.synchronize()
         assert skf.read_info(info)["status"] == 0
         assert rel(x.cpu().numpy(), xo) <= 1e-10
+
+
+def test_srdct_fft_form_arnoldi_3d(skf):
+    """The FFT form inside the Arnoldi process at N = 125000 (3D, n = 50):
+    S v_j and S A v_j against the oracle's DCT-II sketch, then sGMRES."""
+    from workloads import convdiff_3d
+    A = convdiff_3d(50, (50.0, 50.0, 50.0))
+    As = csr_to_scipy(A)
+    b = gaussian_rhs(A.n, 4)
+    m, k, s = 24, 2, 96
+    op = skf.upload_csr(A.rowptr, A.colind, A.values, device="cuda")
+    S = skf.Sketch(skf.SRDCT, A.n, s, 0, 29)
+    OS = OSketch("srdct", A.n, s, seed=29)
+    bt = torch.as_tensor(b, device="cuda")
+    V, vsc, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, bt, m, k)
+    ar = arnoldi_trunc(As, b, m, k, OS)
+    assert rel(SV.cpu().numpy().T, ar["SV"]) <= 1e-12
+    assert rel(SAV.cpu().numpy().T, ar["SAV"]) <= 1e-12
+    c = quad_scale("invsqrt", laplacian_lambda_min(50, 3), float(abs(As).sum(1).max()))
+    f = skf.make_func("invsqrt", c)
+    info = skf.new_info()
+    x = skf.solve(skf.SGMRES, op.csr, S, bt, f, skf.make_params(m, k, tol=1e-12), info=info)
+    xo, oi = osk.solve(As, b, "invsqrt", m, k, OS, c, method="sgmres", tol=1e-12)
+    torch.cuda.synchronize()
+    assert skf.read_info(info)["status"] == 0
+    assert rel(x.cpu().numpy(), xo) <= 1e-10
 
 
 def test_paper_convection_diffusion_experiment(skf):
