@@ -5,7 +5,11 @@ solves of eq. (sFOM) over the adaptive quadrature of Sec. 4.1) applied to the
 same basis and sketches the GPU Arnoldi process produced.  Fixing the basis
 isolates the tail: the node solves (FP32 Cholesky factor with FP64 iterative
 refinement, FP64 factor where that does not converge) must agree with the
-oracle's dense least-squares solutions to 1e-10."""
+oracle's dense least-squares solutions to 1e-10.  These node kernels belong
+to the full form of the tail (QR of [S V_m, S A V_m]): the form of a BF16
+basis and of skf_set_tail_form(1).  An FP32 basis takes the relation form by
+default (Givens node solves in FP64), so the cases here select the full form;
+the same cases in the relation form are checked at the end."""
 import math
 
 import numpy as np
@@ -20,7 +24,8 @@ from gpu_helpers import rel
 pytestmark = pytest.mark.gpu
 
 
-def tail_case(skf, A, lam_lo, m, s, basis, method, seed=7, ell=None):
+def tail_case(skf, A, lam_lo, m, s, basis, method, seed=7, ell=None, form=None):
+    form = skf.TAIL_FULL if form is None else form
     from oracle import quadrature as oq
     vals = A.values.astype(np.float32 if basis == torch.float32 else np.float64)
     op = skf.upload_csr(A.rowptr, A.colind, vals, device="cuda")
@@ -34,7 +39,8 @@ def tail_case(skf, A, lam_lo, m, s, basis, method, seed=7, ell=None):
         f = skf.make_func("invsqrt", c, nodes=t_, weights=w_)
     p = skf.make_params(m, 2, basis_dtype=basis, tol=1e-10)
     info = skf.new_info()
-    x = skf.solve(method, op.csr, S, b, f, p, info=info)
+    with skf.tail_form(form):
+        x = skf.solve(method, op.csr, S, b, f, p, info=info)
     V, vsc, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, b, m, 2, basis_dtype=basis)
     torch.cuda.synchronize()
     inf = skf.read_info(info)
@@ -119,7 +125,8 @@ def test_tail_ill_conditioned_nodes_use_fp64_factor(skf, n, m):
     f = skf.make_func("invsqrt", c, nodes=t_, weights=w_)
     p = skf.make_params(m, 2, basis_dtype=torch.float32, tol=1e-10)
     info = skf.new_info()
-    x = skf.solve(skf.SGMRES, op.csr, S, b, f, p, info=info)
+    with skf.tail_form(skf.TAIL_FULL):
+        x = skf.solve(skf.SGMRES, op.csr, S, b, f, p, info=info)
     torch.cuda.synchronize()
     inf = skf.read_info(info)
     q = sum(wi * np.linalg.lstsq(ti * W["Q"] + W["Z"], W["Sb"], rcond=None)[0] for ti, wi in zip(t_, w_))
@@ -133,3 +140,20 @@ def test_tail_ill_conditioned_nodes_use_fp64_factor(skf, n, m):
     assert 1 <= inf["nodes_fp64"] <= 32     # the small shifts of the rule and t*; most nodes stay FP32
     assert kappa ** 2 * 2.0 ** -52 <= 1e-8
     assert err <= max(1e-10, kappa ** 2 * 2.0 ** -52)
+
+
+@pytest.mark.parametrize("m,method", [(352, "sgmres"), (352, "sfom")])
+def test_tail_relation_form_fp32_basis(skf, m, method):
+    """The default tail of an FP32 basis (relation form, Givens node solves in
+    FP64) on the first case above: the same gate against the oracle's tail on
+    the GPU's basis, and no node needs the FP64 fallback factor."""
+    n = 250
+    A = convdiff_2d(n, (100.0, 50.0))
+    meth = skf.SGMRES if method == "sgmres" else skf.SFOM
+    x, xo, inf, ell, kappa = tail_case(skf, A, laplacian_lambda_min(n, 2), m, 4 * m, torch.float32, meth, ell=64,
+                                       form=skf.TAIL_AUTO)
+    assert inf["status"] == 0 and inf["m_eff"] == m and inf["nodes_fp64"] == 0
+    gate = max(1e-10, kappa ** 2 * 2.0 ** -52)
+    print(f"relation form m {m} {method}: kappa {kappa:.3e}, err {rel(x, xo):.2e}")
+    assert kappa ** 2 * 2.0 ** -52 <= 1e-8
+    assert rel(x, xo) <= gate
