@@ -442,8 +442,9 @@ static skf_status check_common(const skf_csr *A, const skf_sketch *S, const void
         if (A->vdtype != SKF_F64) return fail(SKF_ERR_NOT_SUPPORTED, "an F64 basis needs F64 matrix values");
     } else if (basis == SKF_F32 || basis == SKF_BF16) {
         if (A->vdtype != SKF_F32) return fail(SKF_ERR_NOT_SUPPORTED, "an F32 or BF16 basis needs F32 matrix values");
-        if (S->kind != SKF_SKETCH_SPARSE_SIGN && S->kind != SKF_SKETCH_IDENTITY)
-            return fail(SKF_ERR_NOT_SUPPORTED, "sketch kind not implemented");
+        const bool dense = S->kind == SKF_SKETCH_SRHT || S->kind == SKF_SKETCH_SRDCT;
+        if (S->kind != SKF_SKETCH_SPARSE_SIGN && S->kind != SKF_SKETCH_IDENTITY && !(dense && basis == SKF_F32))
+            return fail(SKF_ERR_NOT_SUPPORTED, "sketch kind not implemented for this basis type");
     } else {
         return fail(SKF_ERR_INVALID_ARG, "unknown basis dtype");
     }

@@ -943,7 +943,7 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_info_lp(LpCtx c, skf_info 
 
 template <int KW, int ZCAP, typename TB>
 void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, cudaStream_t st,
-                  const StepHook *hook) {
+                  const StepHook *hook, const skf_sketch *dense, void *dwork) {
     auto spmv = pipe ? k_arnoldi_spmv_lp_pipe<KW, ZCAP, TB> : k_arnoldi_spmv_lp<KW, ZCAP, TB>;
     auto update = k_arnoldi_update_lp<KW, ZCAP, TB, 0>;
     if constexpr (ZCAP == 8) {
@@ -978,18 +978,32 @@ void launch_steps(const LpCtx &c, bool pipe, size_t smem_spmv, size_t smem_upd, 
         if (c.rs.sell_long) cudaLaunchKernelEx(&cfg_l, k_spmv_long_lp<TB>, cj, j);
         cudaLaunchKernelEx(&cfg_s, spmv, cj, j);
         if (j >= 1) call_hook(hook, j - 1, st);   // S v_i, S A v_i final for i < j - 1
-        if (c.identity) k_identity_cols_lp<TB><<<gid, kThreads, 0, st>>>(cj, j);
+        if (dense) {   // SRHT / SRDCT: SV[:, j] = sigma_j S w_j, SAV[:, j] = sigma_j S y_j
+            DenseCols dc{};
+            dc.ncols = 2;
+            dc.x[0] = (const float *)c.V + vcol(c, j);
+            dc.x[1] = c.Y;
+            dc.out[0] = c.SV + (size_t)j * c.sp.s;
+            dc.out[1] = c.SAV + (size_t)j * c.sp.s;
+            dc.colscale = c.stepsc + 4 * (size_t)j;
+            dc.iscal = c.iscal;
+            dc.step = j;
+            dense_sketch_f32(dense, dc, dwork, st);
+        } else if (c.identity) {
+            k_identity_cols_lp<TB><<<gid, kThreads, 0, st>>>(cj, j);
+        }
         cudaLaunchKernelEx(&cfg_u, update, cj, j);
         if (j + 1 < c.m) call_col_hook(hook, j + 1, st);
     }
 }
 
 template <int ZCAP, typename TB>
-void launch_steps_k(const LpCtx &c, bool pipe, size_t s1, size_t s2, cudaStream_t st, const StepHook *hook) {
-    if (c.k <= 2) launch_steps<2, ZCAP, TB>(c, pipe, s1, s2, st, hook);
-    else if (c.k <= 4) launch_steps<4, ZCAP, TB>(c, pipe, s1, s2, st, hook);
-    else if (c.k <= 8) launch_steps<8, ZCAP, TB>(c, pipe, s1, s2, st, hook);
-    else launch_steps<16, ZCAP, TB>(c, pipe, s1, s2, st, hook);
+void launch_steps_k(const LpCtx &c, bool pipe, size_t s1, size_t s2, cudaStream_t st, const StepHook *hook,
+                    const skf_sketch *dense, void *dwork) {
+    if (c.k <= 2) launch_steps<2, ZCAP, TB>(c, pipe, s1, s2, st, hook, dense, dwork);
+    else if (c.k <= 4) launch_steps<4, ZCAP, TB>(c, pipe, s1, s2, st, hook, dense, dwork);
+    else if (c.k <= 8) launch_steps<8, ZCAP, TB>(c, pipe, s1, s2, st, hook, dense, dwork);
+    else launch_steps<16, ZCAP, TB>(c, pipe, s1, s2, st, hook, dense, dwork);
 }
 
 // Host driver: init, m x (spmv, update), finish, eps, info on `st`.
@@ -1004,7 +1018,11 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     c.sell_val = (const float *)A->sell_val;
     c.sell_col = A->sell_col;
     c.norm_inf = A->norm_inf;
-    c.identity = S->kind == SKF_SKETCH_IDENTITY;
+    // an SRHT or SRDCT (F32 basis) is applied by its own kernels to w_j and
+    // y_j after each SpMV; the step kernels then run as for S = I (no
+    // fixed-point sketch work of their own)
+    const skf_sketch *dense = (S->kind == SKF_SKETCH_SRHT || S->kind == SKF_SKETCH_SRDCT) ? S : nullptr;
+    c.identity = S->kind == SKF_SKETCH_IDENTITY || dense != nullptr;
     if (!c.identity) {
         c.sp = make_sparse_sign(S);
         c.pattern = S->pattern;
@@ -1067,9 +1085,10 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     const size_t szEps = sizeof(double) * (size_t)m;
     const size_t szCnt = sizeof(unsigned) * 4;
     const size_t szSeg = sizeof(float) * (size_t)std::max<int64_t>(c.rs.nseg, 1);
+    const size_t szDense = dense ? dense_sketch_work_bytes(S) : 0;
     const size_t total = al(szY) + al(szP1) + al(szP2) + al(szFd) + al(szFw) + al(szSc) + al(szGram) + al(szCoef) +
                          al(szSk) + al(szSd) + al(2 * szPart) + al(szPart) + (bf ? al(szPart) : 0) + al(szEx) +
-                         al(szEps) + al(szCnt) + al(szSeg);
+                         al(szEps) + al(szCnt) + al(szSeg) + al(szDense);
     char *ws = nullptr;
     skf_status stt = dalloc((void **)&ws, total, st);
     if (stt != SKF_OK) return stt;
@@ -1096,17 +1115,18 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     c.ex = (int *)take(szEx);
     c.epscol = (double *)take(szEps);
     c.cnt = (unsigned *)take(szCnt);
+    void *dwork = szDense ? (void *)take(szDense) : nullptr;
     cudaMemsetAsync(c.cnt, 0, szCnt, st);
 
     k_arnoldi_init_lp<TB><<<G, kChunkRows, 0, st>>>(c, b);
     call_col_hook(hook, 0, st);
-    if (c.sp.zeta <= 8) launch_steps_k<8, TB>(c, pipe, smem_spmv, smem_upd, st, hook);
-    else launch_steps_k<16, TB>(c, pipe, smem_spmv, smem_upd, st, hook);
+    if (c.sp.zeta <= 8) launch_steps_k<8, TB>(c, pipe, smem_spmv, smem_upd, st, hook, dense, dwork);
+    else launch_steps_k<16, TB>(c, pipe, smem_spmv, smem_upd, st, hook, dense, dwork);
     k_arnoldi_finish_lp<TB><<<G, kThreads, 0, st>>>(c);
     call_hook(hook, m, st);
     k_arnoldi_eps_lp<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);
     k_arnoldi_info_lp<<<1, kThreads, 0, st>>>(c, info);
-    count_launches(4 + ((c.identity ? 3ll : 2ll) + (c.rs.sell_long ? 1 : 0)) * m);
+    count_launches(4 + ((c.identity && !dense ? 3ll : 2ll) + (c.rs.sell_long ? 1 : 0)) * m);   // + dense_sketch_f32's own
     cudaError_t e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "reduced-precision Arnoldi kernels");

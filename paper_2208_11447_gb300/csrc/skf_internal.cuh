@@ -140,10 +140,12 @@ struct skf_sketch {
     int32_t *P = nullptr;             // SRHT, SRDCT: s sampled rows (device)
     double *E = nullptr;              // SRDCT: the N signs (device)
     double *costab = nullptr;         // SRDCT, direct form: cos(pi j / (2N)), j = 0 .. 4N-1 (device)
-    // SRDCT through a length-N FFT (N with no prime factor above 7): the
-    // radices of its Stockham passes, e^{-2 pi i t / N} for t < N, and per
-    // sampled row k the DCT twist e^{-i pi k / (2N)} times the row's scale
-    // (device); nrad = 0: the direct form
+    // SRDCT through an FFT (N with no prime factor above 7): the FFT length
+    // (N / 2 for even N, the real input packed two to a complex entry; N for
+    // odd N; 0: the direct form), the radices of its Stockham passes,
+    // e^{-2 pi i t / N} for t < N, and per sampled row k the DCT twist
+    // e^{-i pi k / (2N)} times the row's scale (device)
+    int64_t fft_len = 0;
     int nrad = 0;
     int rad[64] = {};
     double2 *tw = nullptr;
@@ -602,12 +604,13 @@ struct SrhtDev {
 // partials part[c][nblk][s]; with iscal non-null the launch does nothing once
 // the Arnoldi process has stopped at or before `step`.
 struct SrhtCols {
-    const double *x[2];
+    const void *x[2];    // F64 columns, or F32 with f32 = 1 (widened exactly)
     const int *e[2];
     long long *part[2];
     int ncols;
     const int *iscal;
     int step;
+    int f32;
 };
 SrhtDev make_srht(const skf_sketch *S);
 skf_status build_srht_tables(skf_sketch *S);
@@ -623,21 +626,23 @@ struct SrdctDev {
     const int32_t *P;       // [s] sampled rows
     const double *E;        // [n] signs
     const double *costab;   // [4n] cos(pi j / (2n)) (direct form)
-    int nrad;               // FFT form: Stockham passes (0: direct form)
+    int64_t fft_len;        // FFT form: n / 2 (even n) or n (odd n); 0: direct form
+    int nrad;               // Stockham passes of the FFT
     int rad[64];
     const double2 *tw;      // [n] e^{-2 pi i t / n}
     const double2 *twist;   // [s] e^{-i pi k / (2n)} a_k sqrt(n / s), k = P[i]
-    double2 *work;          // FFT form: [2][2][n] scratch of the caller
+    double2 *work;          // FFT form: [2][2][fft_len] scratch of the caller
 };
 // Up to two columns: out[q][i] = colscale * (S x[q])_i (colscale a device
 // scalar or nullptr for 1); iscal/step as for SrhtCols.
 struct SrdctCols {
-    const double *x[2];
+    const void *x[2];    // F64 columns, or F32 with f32 = 1 (widened exactly)
     double *out[2];
     const double *colscale;
     int ncols;
     const int *iscal;
     int step;
+    int f32;
 };
 // bytes of the FFT form's scratch (0 for the direct form)
 size_t srdct_work_bytes(const skf_sketch *S);
@@ -645,6 +650,21 @@ SrdctDev make_srdct(const skf_sketch *S);
 skf_status build_srdct_tables(skf_sketch *S);
 void srdct_launch(const SrdctDev &d, const SrdctCols &cols, cudaStream_t st);
 skf_status srdct_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, int ncols, double *SX, cudaStream_t st);
+
+// An SRHT or SRDCT applied to up to two F32 columns of a reduced-precision
+// Arnoldi step (the stored w_j and y_j = A w_j): out[q] = colscale S x[q],
+// computed in FP64 from the exactly widened values (SRHT: exact fixed point);
+// nothing is done once the Arnoldi process stopped at or before `step`.
+struct DenseCols {
+    const float *x[2];
+    double *out[2];
+    const double *colscale;
+    int ncols;
+    const int *iscal;
+    int step;
+};
+size_t dense_sketch_work_bytes(const skf_sketch *S);   // scratch of dense_sketch_f32
+void dense_sketch_f32(const skf_sketch *S, const DenseCols &cols, void *work, cudaStream_t st);
 // P: the first s entries of the partial Fisher-Yates shuffle of [0, np) (device).
 skf_status build_sampled_rows(skf_sketch *S, int64_t np);
 

@@ -41,14 +41,14 @@ __global__ void __launch_bounds__(kSrhtThreads) k_srht_blocks(SrhtDev d, SrhtCol
         for (int o = threadIdx.x; o < d.s; o += blockDim.x) part[o] = 0;
         return;
     }
-    const double *x = cols.x[c];
     const int shift = d.frac - E;
     const int64_t r0 = (int64_t)blk * B;
     for (int i = threadIdx.x; i < B; i += blockDim.x) {
         const int64_t r = r0 + i;
         long long v = 0;
         if (r < d.n) {
-            v = fixed_point(x[r], shift);
+            const double xr = cols.f32 ? (double)((const float *)cols.x[c])[r] : ((const double *)cols.x[c])[r];
+            v = fixed_point(xr, shift);
             if (splitmix_word(d.seed, (uint64_t)r) & 1ull) v = -v;
         }
         z[i] = v;
@@ -106,6 +106,36 @@ __global__ void k_colmax_srht(const double *__restrict__ X, int64_t ldx, int64_t
         mx = block_max(mx, red);
         if (threadIdx.x == 0) part[(size_t)c * gridDim.x + blockIdx.x] = mx;
     }
+}
+
+// Per-CTA partial max |x| of up to two F32 columns (rows g, g + G, ...),
+// nothing once the Arnoldi process stopped.
+__global__ void k_colmax_f32(DenseCols cols, int64_t n, double *__restrict__ part) {
+    __shared__ double red[32];
+    if (cols.iscal && cols.iscal[0] && cols.iscal[3] <= cols.step) return;
+    for (int c = 0; c < cols.ncols; ++c) {
+        double mx = 0.0;
+        for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+            mx = fmax(mx, fabs((double)cols.x[c][r]));
+        mx = block_max(mx, red);
+        if (threadIdx.x == 0) part[(size_t)c * gridDim.x + blockIdx.x] = mx;
+    }
+}
+
+// out[c][o] = colscale s^{-1/2} (sum of the block partials), as k_srht_reduce
+__global__ void k_srht_reduce_cols(SrhtDev d, DenseCols cols, const long long *__restrict__ part,
+                                   const int *__restrict__ E) {
+    if (cols.iscal && cols.iscal[0] && cols.iscal[3] <= cols.step) return;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)d.s * cols.ncols) return;
+    const int c = (int)(idx / d.s), o = (int)(idx % d.s);
+    const double cs = cols.colscale ? *cols.colscale : 1.0;
+    if (E[c] == kNoExp) {
+        cols.out[c][o] = 0.0;
+        return;
+    }
+    const double tot = sum_i64_exact(part + (size_t)c * d.nblk * d.s + o, d.nblk, (size_t)d.s);
+    cols.out[c][o] = scale_pow2(tot, E[c] - d.frac) * (1.0 / sqrt((double)d.s)) * cs;
 }
 
 }  // namespace
@@ -201,6 +231,57 @@ skf_status srht_apply_f64(const skf_sketch *S, const double *X, int64_t ldx, int
     if (stt != SKF_OK) return stt;
     if (e != cudaSuccess) return cuda_fail(e, "SRHT kernels");
     return SKF_OK;
+}
+
+size_t dense_sketch_work_bytes(const skf_sketch *S) {
+    if (S->kind == SKF_SKETCH_SRDCT) return srdct_work_bytes(S);
+    if (S->kind != SKF_SKETCH_SRHT) return 0;
+    const SrhtDev d = make_srht(S);
+    const int G = std::max(1, std::min(2 * num_sms(), (int)((S->n + kThreads - 1) / kThreads)));
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    return al(sizeof(double) * 2 * G) + al(sizeof(int) * 2) + al(sizeof(long long) * 2 * (size_t)d.nblk * d.s);
+}
+
+void dense_sketch_f32(const skf_sketch *S, const DenseCols &cols, void *work, cudaStream_t st) {
+    if (S->kind == SKF_SKETCH_SRDCT) {
+        SrdctDev d = make_srdct(S);
+        d.work = (double2 *)work;
+        SrdctCols sc{};
+        sc.ncols = cols.ncols;
+        for (int q = 0; q < cols.ncols; ++q) {
+            sc.x[q] = cols.x[q];
+            sc.out[q] = cols.out[q];
+        }
+        sc.colscale = cols.colscale;
+        sc.iscal = cols.iscal;
+        sc.step = cols.step;
+        sc.f32 = 1;
+        srdct_launch(d, sc, st);
+        return;
+    }
+    // SRHT: column maxima, exponent bounds, exact block transforms, reduction
+    const SrhtDev d = make_srht(S);
+    const int G = std::max(1, std::min(2 * num_sms(), (int)((S->n + kThreads - 1) / kThreads)));
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    double *maxpart = (double *)work;
+    int *E = (int *)((char *)work + al(sizeof(double) * 2 * G));
+    long long *part = (long long *)((char *)E + al(sizeof(int) * 2));
+    k_colmax_f32<<<G, kThreads, 0, st>>>(cols, S->n, maxpart);
+    k_col_exponent<<<1, 128, 0, st>>>(maxpart, G, cols.ncols, E);
+    SrhtCols hc{};
+    hc.ncols = cols.ncols;
+    for (int q = 0; q < cols.ncols; ++q) {
+        hc.x[q] = cols.x[q];
+        hc.e[q] = E + q;
+        hc.part[q] = part + (size_t)q * d.nblk * d.s;
+    }
+    hc.iscal = cols.iscal;
+    hc.step = cols.step;
+    hc.f32 = 1;
+    srht_launch(d, hc, st);
+    const int64_t tot = (int64_t)d.s * cols.ncols;
+    k_srht_reduce_cols<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(d, cols, part, E);
+    count_launches(3);
 }
 
 }  // namespace skf

@@ -86,7 +86,7 @@ __device__ __forceinline__ bool last_to_arrive(unsigned *cnt) {
 // or, when the basis is kept as a ring of vring slots (two-pass mode, only
 // the columns the recurrence still reads are alive), slot j mod vring.
 template <class Ctx>
-__device__ __forceinline__ size_t vcol(const Ctx &c, int j) {
+__host__ __device__ __forceinline__ size_t vcol(const Ctx &c, int j) {
     return (size_t)(c.vring ? j % c.vring : j) * (size_t)c.ldv;
 }
 

@@ -316,3 +316,55 @@ def test_f32_relation_form_equals_full_form(skf, k, method):
     # 2^-24 cond(R) (k = 1 loses basis independence fastest: cond(R) ~ 9e2 here)
     bound = max(BOUND["f32"], 2.0 ** -24 * i_rel["cond_est"])
     assert rel(x_rel, xo) <= bound and rel(x_full, xo) <= bound
+
+
+@pytest.mark.parametrize("kind", ["srht", "srdct"])
+def test_f32_basis_dense_sketches(skf, kind):
+    """An FP32 basis with the SRHT or the paper's SRDCT (Sec. 5.1): S v_j is the
+    sketch of the stored basis (computed in FP64 from the widened FP32 values,
+    the SRHT exactly), S A v_j the sketch of the FP32 SpMV result (within the
+    FP32 rounding of A v_j), and both solves stay within
+    max(1e-6, 2^-24 cond(R)) of the FP64 oracle with the same sketch."""
+    A = convdiff_2d(100, (100.0, 50.0))          # N = 1e4 = 2^4 5^4: the SRDCT takes its FFT form
+    b = gaussian_rhs(A.n, 12)
+    m, k, s = 40, 2, 160
+    op = upload32(skf, A)
+    kinds = {"srht": skf.SRHT, "srdct": skf.SRDCT}
+    S = skf.Sketch(kinds[kind], A.n, s, 0, 13)
+    OS = OSketch(kind, A.n, s, seed=13)
+    bt = torch.as_tensor(b, device="cuda")
+    info = skf.new_info()
+    V, vs, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, bt, m, k, basis_dtype=torch.float32, info=info)
+    torch.cuda.synchronize()
+    assert skf.read_info(info)["status"] == 0
+    Vn = (V.double() * vs[:, None]).cpu().numpy().T
+    SVg, SAVg = SV.cpu().numpy().T, SAV.cpu().numpy().T
+    assert rel(SVg, OS @ Vn) < 1e-12
+    M = a32(A)
+    AV = M @ Vn
+    width = int(np.diff(A.rowptr).max())
+    for j in range(m):
+        err = np.linalg.norm(SAVg[:, j] - OS @ AV[:, j]) / np.linalg.norm(OS @ AV[:, j])
+        bound = 4 * (width + k + 2) * U32 * np.linalg.norm(abs(M) @ np.abs(Vn[:, j])) / np.linalg.norm(AV[:, j])
+        assert err <= bound, (j, err, bound)
+    c = quad_scale("invsqrt", laplacian_lambda_min(100, 2), float(abs(csr_to_scipy(A)).sum(1).max()))
+    f = skf.make_func("invsqrt", c)
+    for meth, om in ((skf.SGMRES, "sgmres"), (skf.SFOM, "sfom_quad")):
+        inf = skf.new_info()
+        x = skf.solve(meth, op.csr, S, bt, f, skf.make_params(m, k, basis_dtype=torch.float32, tol=1e-12), info=inf)
+        xo, _ = osk.solve(csr_to_scipy(A), b, "invsqrt", m, k, OS, c, method=om, tol=1e-12)
+        torch.cuda.synchronize()
+        st = skf.read_info(inf)
+        err = rel(x.cpu().numpy(), xo)
+        print(f"f32 {kind} {om}: rel err vs FP64 oracle {err:.3e}, cond_est {st['cond_est']:.3e}")
+        assert st["status"] == 0
+        assert err <= max(BOUND["f32"], U32 * st["cond_est"])
+
+
+def test_bf16_basis_dense_sketch_not_supported(skf):
+    A = convdiff_2d(20)
+    op = upload32(skf, A)
+    S = skf.Sketch(skf.SRHT, A.n, 40, 0, 13)
+    with pytest.raises(skf.SkfError, match="NOT_SUPPORTED"):
+        skf.arnoldi_trunc(op.csr, S, torch.as_tensor(gaussian_rhs(A.n, 1), device="cuda"), 8, 2,
+                          basis_dtype=torch.bfloat16)

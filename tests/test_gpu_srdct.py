@@ -21,12 +21,15 @@ from gpu_helpers import rel
 pytestmark = pytest.mark.gpu
 
 
-# N with no prime factor above 7 takes the FFT form (Makhoul's reordering and
-# Stockham passes of radices 4, 2, 3, 5, 7: 7 = [7], 1000 = [4, 2, 5, 5, 5],
-# 4725 = [3, 3, 3, 5, 5, 7] (odd N), 125000 = [4, 2, 5 x 6]); 1013 (prime) and
-# 9409 = 97^2 the direct form
-@pytest.mark.parametrize("N,s,ncols", [(1, 1, 1), (7, 5, 3), (1000, 200, 2), (10000, 400, 4), (4725, 300, 2),
-                                       (125000, 800, 2), (1013, 300, 2), (9409, 400, 2)])
+# N with no prime factor above 7 takes the FFT form (Makhoul's reordering;
+# even N packs the real input two to an entry and transforms N / 2 entries;
+# Stockham passes of radices 4, 2, 3, 5, 7): 2 (one entry, no pass),
+# 12 -> 6 = [2, 3], 210 -> 105 = [3, 5, 7], 1000 -> 500 = [4, 5, 5, 5],
+# 125000 -> 62500 = [4, 5 x 6]; odd N transforms N entries: 7 = [7],
+# 4725 = [3, 3, 3, 5, 5, 7].  1013 (prime) and 9409 = 97^2 take the direct form
+@pytest.mark.parametrize("N,s,ncols", [(1, 1, 1), (2, 2, 1), (7, 5, 3), (12, 7, 2), (210, 50, 2), (1000, 200, 2),
+                                       (10000, 400, 4), (4725, 300, 2), (125000, 800, 2), (1013, 300, 2),
+                                       (9409, 400, 2)])
 def test_srdct_apply_matches_oracle(skf, N, s, ncols):
     X = np.random.default_rng(N + s).standard_normal((N, ncols))
     S = skf.Sketch(skf.SRDCT, N, s, 0, 17)
