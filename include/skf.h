@@ -140,7 +140,10 @@ typedef struct {
     int32_t k;              /* truncation length of MGS, 1 <= k <= 16    */
     skf_dtype basis_dtype;  /* storage of V_m: F64 (F64 matrix values), or F32
                                or BF16 (F32 matrix values; FP32 arithmetic in
-                               the Arnoldi process, FP64 tail)              */
+                               the Arnoldi process, FP64 tail).  F32: every
+                               sketch kind; BF16: sparse-sign and identity.
+                               skf_plan_basis_precision picks F32 or F64
+                               per problem                                 */
     int32_t ell1, ell2;     /* first two quadrature orders (Sec. 4.1)    */
     int32_t ell_max;        /* give up past this order                   */
     double tol;             /* relative tolerance ||q1-q2|| <= tol ||q2|| */
@@ -264,9 +267,11 @@ skf_status skf_workspace_trim(void);
  *      the s x (m+1) matrix [S V_m, S A v_m]: the sketched Arnoldi relation
  *      S A v_j = S V_m H(1:m, j) (j < m, eq. (2.1)) gives
  *      M = [R_11 H(1:m, 1:m-1), R(1:m, m+1)] R_11^{-1} and the sGMRES term
- *      orthogonal to S V_m, R(m+1, m+1) / R(m, m) e_m^T; with an F32 or BF16
- *      basis (whose stored columns satisfy the relation only to their own
- *      precision) the full form;
+ *      orthogonal to S V_m, R(m+1, m+1) / R(m, m) e_m^T; the same with an F32
+ *      basis (its H holds the FP32 coefficients its update applied, so the
+ *      relation holds for the stored columns); with a BF16 basis (whose
+ *      stored columns satisfy the relation only to BF16 precision) the full
+ *      form;
  *   1  the full form: the QR of the s x 2m matrix [S V_m, S A V_m].
  * The stopping criterion's checkpoints always take the full form.
  * Returns INVALID_ARG for another form. */
@@ -345,9 +350,12 @@ skf_status skf_csr_set_layout(skf_csr *A, int32_t cut, int32_t sorted, skf_strea
  *   SRDCT: S x = sqrt(N/s) (F E x)[P], F the orthonormal DCT-II of order N
  *     ((F y)_k = a_k sum_n y_n cos(pi k (2n+1) / (2N)), a_0 = sqrt(1/N),
  *     a_k = sqrt(2/N)), E as for SRHT, P the first s entries of the same
- *     partial Fisher-Yates shuffle, of [0, N).  Requires s <= N.  Applied as
- *     s direct dot products against a table of cos(pi j / (2N)), j < 4N
- *     (O(s N) work per vector: meant for the paper's N ~ 1e4 examples).
+ *     partial Fisher-Yates shuffle, of [0, N).  Requires s <= N.  When N has
+ *     no prime factor above 7 it is applied through one FFT of length N/2
+ *     (even N, real input packed) or N (odd N) in FP64, O(N log N) per
+ *     vector (Makhoul's reordering; creation keeps e^{-2 pi i t/N}, t < N,
+ *     16 N bytes); otherwise as s direct dot products against a table of
+ *     cos(pi j / (2N)), j < 4N (32 N bytes, O(s N) work per vector).
  *   IDENTITY: requires s == N.
  * Errors: INVALID_ARG, OOM, CUDA, NOT_SUPPORTED. */
 skf_status skf_sketch_create(skf_sketch_kind kind, int64_t n, int32_t s, int32_t zeta, uint64_t seed,
@@ -364,8 +372,8 @@ skf_status skf_sketch_destroy(skf_sketch *S);
  * entries (H_{N'} = H_{N'/B} (x) H_B), inputs rounded at 2^-(62 - log2 B) of
  * the column max, and the block contributions to each sampled row are summed
  * exactly.  The SRHT is available for F64 X and, in the Arnoldi process and
- * the solvers, for an F64 basis.  SRDCT sums in FP64 in a fixed order
- * (deterministic, not exact); F64 X and an F64 basis, like the SRHT.
+ * the solvers, for an F64 or F32 basis.  SRDCT sums in FP64 in a fixed order
+ * (deterministic, not exact); F64 X and an F64 or F32 basis, like the SRHT.
  * Errors: INVALID_ARG, OOM, CUDA. */
 skf_status skf_sketch_apply(const skf_sketch *S, const void *X, skf_dtype xdtype, int64_t ldx,
                             int32_t ncols, double *SX, skf_stream_t stream);
