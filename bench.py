@@ -275,6 +275,54 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def run_block(args, wl, A, op, dev, rank):
+    """skf_solve_block in its lockstep SpMM form (nrhs right-hand sides, one
+    operator and sketch) against nrhs skf_solve calls on the same inputs:
+    CUDA events, median of the steps, L2 flushed; the results must be
+    bit-identical."""
+    import numpy as np
+    import torch
+    import paper_2208_11447_gb300 as skf
+    from workloads.configs import quad_scale
+    m = args.m or wl.m
+    bdt = basis_torch(args.basis)
+    S = skf.Sketch(SKETCH_KIND[args.sketch](skf), A.n, wl.s, wl.zeta, 13)
+    f = skf.make_func(wl.func, quad_scale(wl.func, wl.lam_lo or 0.0, op.csr.norm_inf()))
+    p = skf.make_params(m, wl.k, basis_dtype=bdt, tol=1e-10)
+    B = torch.as_tensor(np.stack([wl.rhs(A.n) * (1.0 + 0.1 * q) + 1e-3 * q for q in range(args.nrhs)]),
+                        device=dev).contiguous()
+    Xb, Xs = torch.empty_like(B), torch.empty_like(B)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def block():
+        with skf.block_mode(1):   # the lockstep SpMM form
+            skf.solve_block(skf.SGMRES, op.csr, S, B, f, p, X=Xb)
+
+    def singles():
+        for q in range(args.nrhs):
+            skf.solve(skf.SGMRES, op.csr, S, B[q], f, p, x=Xs[q])
+
+    res = {"mode": "block", "workload": args.workload, "basis": args.basis, "m": m, "nrhs": args.nrhs}
+    for name, fn in (("block", block), ("singles", singles)):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record()
+            fn()
+            ev1.record()
+            ev1.synchronize()
+            ts.append(ev0.elapsed_time(ev1))
+        res[name + "_ms"] = round(statistics.median(ts), 3)
+    res["speedup"] = round(res["singles_ms"] / res["block_ms"], 3)
+    res["bitwise_equal"] = bool(torch.equal(Xb, Xs))
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
 def run_arnoldi_only(args, wl, A, b, op, dev, rank, world):
     """Time skf_arnoldi_trunc alone (m steps of the two step kernels)."""
     import torch
@@ -303,6 +351,7 @@ def run_arnoldi_only(args, wl, A, b, op, dev, rank, world):
 
 # ----------------------------------------------------------------- batched workload
 BATCH_TOL = 1e-6          # error gate of a batched FP32-basis solve against the FP64 one
+FP32_STEP_TRAFFIC = 1511.9e6   # DRAM bytes per FP32 step at N = 16.8M (spmv 1125.4 MB + update 386.4 MB, ncu)
 BATCH_FUNC = "invsqrt"
 
 
@@ -671,7 +720,10 @@ def precision_extras(dev, reps: int = 3):
         p = skf.make_params(wl.m, wl.k, basis_dtype=bdt, tol=1e-10)
         xs[name] = (skf.sfom(op32.csr, S, b_dev, f, p), skf.sgmres(op32.csr, S, b_dev, f, p))
         res[name] = {"us_per_step": round(us, 2), "alg_bytes_per_step": int(alg),
-                     "hbm_frac": round(alg / (us * 1e-6) / 1e9 / hbm_peak, 4), "of": hbm_src}
+                     "hbm_frac": round(alg / (us * 1e-6) / 1e9 / hbm_peak, 4), "of": hbm_src,
+                     # ncu DRAM bytes of the two step kernels per step (one capture of the
+                     # current kernels); FP32 basis only
+                     "traffic": FP32_STEP_TRAFFIC if name == "f32" else None}
     torch.cuda.synchronize()
     del op32
     op64 = skf.upload_csr(A.rowptr, A.colind, A.values.astype(np.float64), device=dev)
@@ -801,7 +853,8 @@ def main():
                     help="form of the FP64 Arnoldi process (skf_set_arnoldi_mode)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the extra keys of the default line (reduced-precision workload, batch arms)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi", "batch"],
+    ap.add_argument("--nrhs", type=int, default=4, help="right-hand sides of the block (block mode)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "arnoldi", "batch", "block"],
                     help="arnoldi: time only skf_arnoldi_trunc (the dominant kernels), e.g. under ncu; "
                          "batch: the batched workload (8 operators, 64 right-hand sides) as one CUDA graph")
     ap.add_argument("--lanes", default="auto",
@@ -865,6 +918,9 @@ def main():
     op = skf.upload_csr(A.rowptr, A.colind, A.values, device=dev)
     if args.mode == "arnoldi":
         run_arnoldi_only(args, wl, A, b, op, dev, rank, world)
+        return
+    if args.mode == "block":
+        run_block(args, wl, A, op, dev, rank)
         return
     S = skf.Sketch(SKETCH_KIND[args.sketch](skf), A.n, wl.s, wl.zeta, 13)
     c = quad_scale(wl.func, wl.lam_lo or 0.0, op.csr.norm_inf())

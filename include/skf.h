@@ -234,6 +234,12 @@ int64_t skf_kernel_launch_count(void);
  * Returns INVALID_ARG for another mode. */
 skf_status skf_set_arnoldi_mode(int32_t mode);
 
+/* skf_set_block_mode: form of skf_solve_block (process-wide; results are
+ * bit-identical in both): 0 (default) the columns one after another,
+ * 1 the lockstep form with one SpMM per step (see skf_solve_block).
+ * Returns INVALID_ARG for another mode. */
+skf_status skf_set_block_mode(int32_t mode);
+
 /* skf_set_qr_mode: form of the whitening QR of [S V_m, S A V_m] in the tail
  * (process-wide; results agree to rounding):
  *   0  automatic (default): one cooperative launch, column q updated by CTA
@@ -486,6 +492,32 @@ typedef struct {
     skf_dtype xdtype;
     skf_info *info;         /* device-writable, or NULL */
 } skf_problem;
+
+/* skf_solve_block: f(A) b_q for a block B = [b_1 .. b_nrhs] of right-hand
+ * sides on one operator, with one sketch, one f, one parameter set and one
+ * method (Algorithm 2 and the tail of skf_solve for every column; the paper
+ * solves one right-hand side at a time).  B and X are device F64 N x nrhs,
+ * column q at B + q ldb and X + q ldx (ldb, ldx >= N); info is a device
+ * array of nrhs skf_info or NULL.  Every column's result is bit-identical to
+ * the skf_solve call for it.  By default the columns are solved one after
+ * another.  skf_set_block_mode(1) selects the lockstep form for an F32 basis
+ * with one pass and no stopping criterion: the nrhs Arnoldi processes advance
+ * together and each step reads A once per group of four right-hand sides (an
+ * SpMM: the products of a chunk of A with the four w_j share one load of the
+ * chunk); each process keeps its own update, sketch partials and tail.  It
+ * applies to slices at most 8 wide without a row split, sparse-sign sketches
+ * with zeta <= 8 and k <= 2 (otherwise, and for other basis types, the
+ * columns go one after another).  Measured on a GB300 it is not faster than
+ * the columns one after another for 7-point stencils (0.96-0.98x at
+ * N = 2.4M and 16.8M): with one row per thread in 1024-thread CTAs (64
+ * registers) the four columns' gathers cannot all be in flight, and the
+ * kernel waits on them (27% of the DRAM peak against 72% for one column).
+ * Device memory: the workspace of all nrhs processes at once in the lockstep
+ * form (V_m in F32 and the sketches per column).  Errors: as skf_solve;
+ * INVALID_ARG also for nrhs < 0 or ld < N. */
+skf_status skf_solve_block(skf_method method, const skf_csr *A, const skf_sketch *S, const double *B, int64_t ldb,
+                           int32_t nrhs, const skf_func *f, const skf_params *p, double *X, int64_t ldx,
+                           skf_info *info, skf_stream_t stream);
 
 /* skf_solve_batched: nprob independent f(A)b problems (each one exactly the
  * approximant skf_solve computes for its arguments; the paper solves one

@@ -123,12 +123,15 @@ def lib():
         L.skf_barrier_selftest.argtypes = [i32, i64, vp, vp]
         L.skf_plan_basis_precision.argtypes = [i32, ctypes.POINTER(Problem), dbl, ctypes.POINTER(dbl),
                                                ctypes.POINTER(i32), vp]
+        L.skf_set_block_mode.argtypes = [i32]
+        L.skf_solve_block.argtypes = [ctypes.c_int, vp, vp, vp, i64, i32, ctypes.POINTER(Func),
+                                      ctypes.POINTER(Params), vp, i64, vp, vp]
         for name in ["skf_create_csr", "skf_destroy_csr", "skf_csr_norm_inf", "skf_sketch_create",
                      "skf_sketch_destroy", "skf_sketch_apply", "skf_sketch_apply_noalloc", "skf_arnoldi_trunc",
                      "skf_solve", "skf_solve_batched", "skf_sfom", "skf_sfom_sgmres",
                      "skf_sgmres", "skf_quadrature_rule", "skf_quadrature_rule_c", "skf_set_arnoldi_mode",
                      "skf_set_qr_mode", "skf_set_tail_form", "skf_workspace_trim", "skf_fp64_peak", "skf_csr_autotune", "skf_csr_set_layout",
-                     "skf_barrier_selftest", "skf_plan_basis_precision"]:
+                     "skf_barrier_selftest", "skf_plan_basis_precision", "skf_solve_block", "skf_set_block_mode"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -326,6 +329,24 @@ def solve(method: int, A: Csr, S: Sketch, b: torch.Tensor, f: Func, p: Params, x
     return x
 
 
+def solve_block(method: int, A: Csr, S: Sketch, B: torch.Tensor, f: Func, p: Params, X: torch.Tensor | None = None,
+                info=None, stream=None) -> torch.Tensor:
+    """skf_solve_block for B of shape (nrhs, N) (row q = right-hand side q,
+    i.e. the column-major N x nrhs block); returns X of the same shape.
+    info: a buffer of nrhs skf_info (new_info_block) or None."""
+    assert B.dim() == 2 and B.is_contiguous()
+    if X is None:
+        X = torch.empty_like(B)
+    nrhs, N = B.shape
+    _check(lib().skf_solve_block(method, A.handle, S.handle, _ptr(B), N, nrhs, ctypes.byref(f), ctypes.byref(p),
+                                 _ptr(X), N, _ptr(info), _stream(stream)))
+    return X
+
+
+def new_info_block(nrhs: int, device="cuda") -> torch.Tensor:
+    return torch.zeros((nrhs, ctypes.sizeof(Info)), dtype=torch.uint8, device=device)
+
+
 def sfom(A, S, b, f, p, x=None, info=None, stream=None):
     return solve(SFOM, A, S, b, f, p, x, info, stream)
 
@@ -457,6 +478,22 @@ class qr_mode:
 
     def __exit__(self, *exc):
         set_qr_mode(0)
+        return False
+
+
+class block_mode:
+    """Context manager: skf_set_block_mode(mode) for the enclosed calls (1: the
+    lockstep SpMM form of skf_solve_block), then back to the default 0."""
+
+    def __init__(self, mode: int):
+        self.mode = mode
+
+    def __enter__(self):
+        _check(lib().skf_set_block_mode(self.mode))
+        return self
+
+    def __exit__(self, *exc):
+        _check(lib().skf_set_block_mode(0))
         return False
 
 

@@ -745,6 +745,14 @@ skf_status skf_set_arnoldi_mode(int32_t mode) {
     return SKF_OK;
 }
 
+static int g_block_mode = 0;   // 0 columns one after another, 1 lockstep with one SpMM per step
+
+skf_status skf_set_block_mode(int32_t mode) {
+    if (mode < 0 || mode > 1) return fail(SKF_ERR_INVALID_ARG, "block mode must be 0 or 1");
+    g_block_mode = mode;
+    return SKF_OK;
+}
+
 skf_status skf_set_qr_mode(int32_t mode) {
     if (mode < 0 || mode > 1) return fail(SKF_ERR_INVALID_ARG, "QR mode must be 0 or 1");
     set_qr_mode(mode);
@@ -1265,6 +1273,67 @@ skf_status skf_solve(skf_method method, const skf_csr *A, const skf_sketch *S, c
 }
 
 // Both methods on one Arnoldi process (skf_sfom_sgmres).
+skf_status skf_solve_block(skf_method method, const skf_csr *A, const skf_sketch *S, const double *B, int64_t ldb,
+                           int32_t nrhs, const skf_func *f, const skf_params *p, double *X, int64_t ldx,
+                           skf_info *info, skf_stream_t stream) {
+    if (nrhs < 0 || (nrhs > 0 && (!B || !X))) return fail(SKF_ERR_INVALID_ARG, "bad block arguments");
+    if (nrhs == 0) return SKF_OK;
+    if (!A || ldb < A->n || ldx < A->n) return fail(SKF_ERR_INVALID_ARG, "need ldb, ldx >= N");
+    const RuleDev *rule = nullptr;
+    skf_status st = solve_check(method, A, S, B, SKF_F64, f, p, X, SKF_F64, &rule);
+    if (st != SKF_OK) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int m = p->m, s = S->s;
+    const int64_t n = A->n;
+    auto col = [](const double *base, int64_t ld, int q) { return base + (size_t)q * ld; };
+    // the lockstep form (skf_set_block_mode(1)): F32 basis, one pass, no
+    // stopping criterion
+    const bool lockstep = g_block_mode == 1 && p->basis_dtype == SKF_F32 && p->two_pass == 0 &&
+                          !(p->check_every > 0 && p->check_every < m) && nrhs > 1;
+    if (!lockstep) {
+        for (int q = 0; q < nrhs; ++q) {
+            st = solve_enqueue(method, A, S, col(B, ldb, q), *p, X + (size_t)q * ldx, info ? info + q : nullptr,
+                               *rule, cs);
+            if (st != SKF_OK) return st;
+        }
+        return SKF_OK;
+    }
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const int64_t ldv = (n + 63) / 64 * 64;
+    const size_t szV = sizeof(float) * (size_t)ldv * m;
+    const size_t szS = sizeof(double) * (size_t)s * m;
+    const size_t szH = sizeof(double) * (size_t)(m + 1) * m;
+    const size_t per = al(szV) + 2 * al(szS) + al(szH) + al(sizeof(double) * m) + al(sizeof(int) * 4);
+    char *ws = nullptr;
+    st = dalloc((void **)&ws, per * (size_t)nrhs, cs);
+    if (st != SKF_OK) return st;
+    std::vector<const double *> bq(nrhs);
+    std::vector<float *> Vq(nrhs);
+    std::vector<double *> vs(nrhs), SVq(nrhs), SAVq(nrhs), Hq(nrhs);
+    std::vector<int *> isc(nrhs);
+    std::vector<skf_info *> inf(nrhs);
+    for (int q = 0; q < nrhs; ++q) {
+        char *w = ws + per * (size_t)q;
+        size_t off = 0;
+        Vq[q] = (float *)(w + off); off += al(szV);
+        SVq[q] = (double *)(w + off); off += al(szS);
+        SAVq[q] = (double *)(w + off); off += al(szS);
+        Hq[q] = (double *)(w + off); off += al(szH);
+        vs[q] = (double *)(w + off); off += al(sizeof(double) * m);
+        isc[q] = (int *)(w + off);
+        bq[q] = col(B, ldb, q);
+        inf[q] = info ? info + q : nullptr;
+    }
+    st = arnoldi_run_f32_block(A, S, nrhs, bq.data(), m, p->k, Vq.data(), ldv, vs.data(), SVq.data(), SAVq.data(),
+                               Hq.data(), isc.data(), inf.data(), cs);
+    const double cond_max = p->cond_max == 0.0 ? 1e12 : (p->cond_max < 0.0 ? 0.0 : p->cond_max);
+    for (int q = 0; q < nrhs && st == SKF_OK; ++q)
+        st = tail_run(method, s, m, n, Vq[q], SKF_F32, ldv, vs[q], SVq[q], SAVq[q], isc[q], *rule, p->tol,
+                      X + (size_t)q * ldx, inf[q], cs, nullptr, nullptr, nullptr, cond_max, Hq[q], m + 1, p->k);
+    dfree(ws, cs);
+    return st;
+}
+
 static skf_status solve_enqueue_pair(const skf_csr *A, const skf_sketch *S, const void *b, const skf_params &p,
                                      void *x_fom, void *x_gmres, skf_info *info_fom, skf_info *info_gmres,
                                      const RuleDev &rule, cudaStream_t cs) {

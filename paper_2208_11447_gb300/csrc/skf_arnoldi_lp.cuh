@@ -622,6 +622,149 @@ __global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmv_lp_pipe(LpCtx 
     spmv_end<KW>(c, j, nw, last, L, bins, acc, ykey, red);
 }
 
+// Several right-hand sides on one operator (a block B = [b_1 .. b_r] of
+// Arnoldi processes in lockstep, same m, k and sketch): the SpMV of step j
+// for up to RB of them in one launch, reading each chunk of A once.  Per
+// right-hand side q everything is as in k_arnoldi_spmv_lp_pipe: the same
+// prologue, the same rows per thread, products and dots in the same order
+// (results bitwise equal to its own launch), its own partials, counter and
+// last-CTA reduction.  Not for the last step (S y_{m-1} is scattered there
+// by the single-vector kernel) nor for a row split.
+template <int RB>
+struct SpmmArgs {
+    LpCtx c[RB];
+    int nr;
+};
+
+template <int KW, int ZCAP, typename TB, int RB>
+__global__ void __launch_bounds__(kSpmvThreads, 1) k_arnoldi_spmm_lp(SpmmArgs<RB> g, int j) {
+    extern __shared__ int bins[];   // [2 s]: limbs of S w_j at a stopping step
+    __shared__ double red[32 * KW];
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // programmatic dependent (see k_arnoldi_spmv_lp)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    bool act[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+        act[q] = false;
+        if (q < g.nr) {
+            bool stopping = false;
+            act[q] = spmv_begin<TB>(g.c[q], j, stopping);
+            if (act[q] && stopping) {   // a stop at this step: S w_j only, as the single-vector kernel does
+                __syncthreads();
+                spmv_stop_sketch<ZCAP, TB>(g.c[q], j, bins);
+                act[q] = false;
+            }
+        }
+    }
+    const LpCtx &c0 = g.c[0];   // operator and partition: common to the block
+    const int i0 = max(0, j - c0.k + 1);
+    const int nw = j - i0 + 1;
+    float acc[RB][KW];
+    unsigned ykey[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+        ykey[q] = 0;
+#pragma unroll
+        for (int a = 0; a < KW; ++a) acc[q][a] = 0.f;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t nc = chunks_of_cta(c0);
+    const int64_t step = (int64_t)c0.G * kChunkRows;
+    const int64_t rw0 = (int64_t)blockIdx.x * kChunkRows + (threadIdx.x & ~31);   // warp's slice in chunk 0
+    int wt_c = 0, mw_raw = 0;
+    long long so_c = 0, mo_raw = 0;
+    if (lane == 0 && nc > 0 && rw0 < c0.n) {
+        wt_c = __ldg(c0.sell_w + (rw0 >> 5));
+        so_c = __ldg(c0.sell_off + (rw0 >> 5));
+    }
+    wt_c = __shfl_sync(0xffffffffu, wt_c, 0);
+    so_c = __shfl_sync(0xffffffffu, so_c, 0);
+    if (lane == 0 && nc > 1 && rw0 + step < c0.n) {
+        mw_raw = __ldg(c0.sell_w + ((rw0 + step) >> 5));
+        mo_raw = __ldg(c0.sell_off + ((rw0 + step) >> 5));
+    }
+    int cv[8];
+    {
+        const int32_t *pc = c0.sell_col + so_c + lane;
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+            if (p < wt_c) cv[p] = __ldcs(pc + 32 * p);
+    }
+    for (int64_t i = 0; i < nc; ++i) {
+        const int64_t rw = rw0 + i * step;
+        const int64_t r = rw + lane;
+        const bool ok = rw < c0.n && r < c0.n;
+        float av[8];
+        {
+            const float *pv = c0.sell_val + so_c + lane;
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < wt_c) av[p] = __ldcs(pv + 32 * p);
+        }
+        const int wt_n = __shfl_sync(0xffffffffu, mw_raw, 0);
+        const long long so_n = __shfl_sync(0xffffffffu, mo_raw, 0);
+        int cvn[8];
+        {
+            const int32_t *pc = c0.sell_col + so_n + lane;
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+                if (p < wt_n) cvn[p] = __ldcs(pc + 32 * p);
+        }
+        mw_raw = 0;
+        mo_raw = 0;
+        if (lane == 0 && i + 2 < nc && rw + 2 * step < c0.n) {
+            mw_raw = __ldg(c0.sell_w + ((rw + 2 * step) >> 5));
+            mo_raw = __ldg(c0.sell_off + ((rw + 2 * step) >> 5));
+        }
+        // per right-hand side: gathers of w_j and the window, y, dots (the
+        // chunk of A is in registers for all of them); the loads of column
+        // q + 1 are issued before the products of column q
+        if (ok) {
+            float xa[8], wa[KW];
+            auto load_col = [&](int q, float (&x)[8], float (&w)[KW]) {
+                const TB *__restrict__ V = (const TB *)g.c[q].V;
+                const TB *__restrict__ wj = V + vcol(g.c[q], j);
+#pragma unroll
+                for (int p = 0; p < 8; ++p) x[p] = p < wt_c ? Store<TB>::ld(wj + cv[p]) : 0.f;
+#pragma unroll
+                for (int a = 0; a < KW; ++a) w[a] = a < nw ? Store<TB>::ld(V + g.c[q].woff[a] + r) : 0.f;
+            };
+            load_col(0, xa, wa);
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                if (q >= g.nr) break;
+                float xb[8], wb[KW];
+                if (q + 1 < RB && q + 1 < g.nr) load_col(q + 1, xb, wb);
+                if (act[q]) {
+                    float y = 0.f;
+#pragma unroll
+                    for (int p = 0; p < 8; ++p)
+                        if (p < wt_c) y = fmaf(av[p], xa[p], y);
+                    float *__restrict__ Yq = g.c[q].Y;
+                    Yq[r] = y;
+#pragma unroll
+                    for (int a = 0; a < KW; ++a)
+                        if (a < nw) acc[q][a] = fmaf(wa[a], y, acc[q][a]);
+                    ykey[q] = max(ykey[q], abs_key_f32(y));
+                }
+                if (q + 1 < RB && q + 1 < g.nr) {
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) xa[p] = xb[p];
+#pragma unroll
+                    for (int a = 0; a < KW; ++a) wa[a] = wb[a];
+                }
+            }
+        }
+        wt_c = wt_n;
+        so_c = so_n;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) cv[p] = cvn[p];
+    }
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+        if (act[q]) spmv_end<KW>(g.c[q], j, nw, false, 0, bins, acc[q], ykey[q], red);
+}
+
 // S = I (tests): SV[:, j] = sigma_j w_j, SAV[:, j] = sigma_j y_j.
 template <typename TB>
 __global__ void __launch_bounds__(kThreads) k_identity_cols_lp(LpCtx c, int j) {
@@ -1006,11 +1149,20 @@ void launch_steps_k(const LpCtx &c, bool pipe, size_t s1, size_t s2, cudaStream_
     else launch_steps<16, ZCAP, TB>(c, pipe, s1, s2, st, hook, dense, dwork);
 }
 
-// Host driver: init, m x (spmv, update), finish, eps, info on `st`.
+// Context, launch shapes and workspace of one reduced-precision Arnoldi
+// process (the workspace is the caller's to release with dfree).
+struct LpRun {
+    LpCtx c;
+    bool pipe;
+    size_t smem_spmv, smem_upd;
+    const skf_sketch *dense;
+    void *dwork;
+    char *ws;
+};
+
 template <typename TB>
-skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, TB *V, int64_t ldv,
-                          double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
-                          cudaStream_t st, const StepHook *hook = nullptr, int vring = 0) {
+skf_status lp_setup(const skf_csr *A, const skf_sketch *S, int m, int k, TB *V, int64_t ldv, double *vscale,
+                    double *SV, double *SAV, double *H, int *iscal, cudaStream_t st, int vring, LpRun &run) {
     LpCtx c{};
     c.n = A->n;
     c.sell_off = A->sell_off;
@@ -1117,6 +1269,31 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     c.cnt = (unsigned *)take(szCnt);
     void *dwork = szDense ? (void *)take(szDense) : nullptr;
     cudaMemsetAsync(c.cnt, 0, szCnt, st);
+    run.c = c;
+    run.pipe = pipe;
+    run.smem_spmv = smem_spmv;
+    run.smem_upd = smem_upd;
+    run.dense = dense;
+    run.dwork = dwork;
+    run.ws = ws;
+    return SKF_OK;
+}
+
+// Host driver: init, m x (spmv, update), finish, eps, info on `st`.
+template <typename TB>
+skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, TB *V, int64_t ldv,
+                          double *vscale, double *SV, double *SAV, double *H, int *iscal, skf_info *info,
+                          cudaStream_t st, const StepHook *hook = nullptr, int vring = 0) {
+    LpRun run{};
+    skf_status stt = lp_setup<TB>(A, S, m, k, V, ldv, vscale, SV, SAV, H, iscal, st, vring, run);
+    if (stt != SKF_OK) return stt;
+    const LpCtx &c = run.c;
+    const int G = c.G;
+    const bool pipe = run.pipe;
+    const size_t smem_spmv = run.smem_spmv, smem_upd = run.smem_upd;
+    const skf_sketch *dense = run.dense;
+    void *dwork = run.dwork;
+    char *ws = run.ws;
 
     k_arnoldi_init_lp<TB><<<G, kChunkRows, 0, st>>>(c, b);
     call_col_hook(hook, 0, st);
@@ -1130,6 +1307,104 @@ skf_status arnoldi_run_lp(const skf_csr *A, const skf_sketch *S, const double *b
     cudaError_t e = cudaGetLastError();
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "reduced-precision Arnoldi kernels");
+    return SKF_OK;
+}
+
+// A block of nr Arnoldi processes on one operator and one sketch (same m
+// and k, right-hand sides b[q]), in lockstep: per step one SpMM launch per
+// group of kSpmmBlock right-hand sides (each chunk of A read once per group),
+// then each process's own update.  Every process computes exactly what its
+// own arnoldi_run_lp computes.  Falls back to one process after another
+// where the SpMM kernel does not apply (slices wider than 8, a row split,
+// sorted slices, sketches other than sparse-sign with zeta <= 8, k > 2).
+constexpr int kSpmmBlock = 4;
+
+template <typename TB>
+skf_status arnoldi_run_lp_block(const skf_csr *A, const skf_sketch *S, int nr, const double *const *b, int m, int k,
+                                TB *const *V, int64_t ldv, double *const *vscale, double *const *SV,
+                                double *const *SAV, double *const *H, int *const *iscal, skf_info *const *info,
+                                cudaStream_t st) {
+    const bool fits = S->kind == SKF_SKETCH_SPARSE_SIGN && S->zeta <= 8 && k <= 2 && A->max_width <= 8 &&
+                      A->nlong == 0 && A->perm == nullptr;
+    if (!fits || nr <= 1) {
+        for (int q = 0; q < nr; ++q) {
+            const skf_status e = arnoldi_run_lp<TB>(A, S, b[q], m, k, V[q], ldv, vscale[q], SV[q], SAV[q], H[q],
+                                                    iscal[q], info[q], st);
+            if (e != SKF_OK) return e;
+        }
+        return SKF_OK;
+    }
+    std::vector<LpRun> runs((size_t)nr);
+    skf_status stt = SKF_OK;
+    int made = 0;
+    for (; made < nr && stt == SKF_OK; ++made)
+        stt = lp_setup<TB>(A, S, m, k, V[made], ldv, vscale[made], SV[made], SAV[made], H[made], iscal[made], st, 0,
+                           runs[made]);
+    if (stt != SKF_OK) {
+        for (int q = 0; q + 1 < made; ++q) dfree(runs[q].ws, st);
+        return stt;
+    }
+    const int G = runs[0].c.G;
+    for (int q = 0; q < nr; ++q) k_arnoldi_init_lp<TB><<<G, kChunkRows, 0, st>>>(runs[q].c, b[q]);
+    auto spmm = k_arnoldi_spmm_lp<2, 8, TB, kSpmmBlock>;
+    auto spmv = k_arnoldi_spmv_lp_pipe<2, 8, TB>;
+    auto update = k_arnoldi_update_lp<2, 8, TB, 0>;
+    if (runs[0].c.split)
+        update = runs[0].c.p8_block == 64 ? k_arnoldi_update_lp<2, 8, TB, 64> : k_arnoldi_update_lp<2, 8, TB, 128>;
+    const size_t smem_spmv = runs[0].smem_spmv, smem_upd = runs[0].smem_upd;
+    if (smem_spmv > 48 * 1024) {
+        cudaFuncSetAttribute(spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_spmv);
+        cudaFuncSetAttribute(spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_spmv);
+    }
+    if (smem_upd > 48 * 1024) cudaFuncSetAttribute(update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_upd);
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    auto config = [&](unsigned grid, unsigned block, size_t smem) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(block);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = pdl;
+        cfg.numAttrs = 1;
+        return cfg;
+    };
+    const cudaLaunchConfig_t cfg_s = config((unsigned)G, kSpmvThreads, smem_spmv);
+    const cudaLaunchConfig_t cfg_u = config((unsigned)G, kUpdThreads, smem_upd);
+    long long nlaunch = nr;
+    std::vector<LpCtx> cj((size_t)nr);
+    for (int j = 0; j < m; ++j) {
+        for (int q = 0; q < nr; ++q) {
+            cj[q] = runs[q].c;
+            window_offsets(cj[q], j);
+        }
+        if (j < m - 1) {
+            for (int q0 = 0; q0 < nr; q0 += kSpmmBlock) {
+                SpmmArgs<kSpmmBlock> args{};
+                args.nr = std::min(kSpmmBlock, nr - q0);
+                for (int q = 0; q < args.nr; ++q) args.c[q] = cj[q0 + q];
+                cudaLaunchKernelEx(&cfg_s, spmm, args, j);
+                ++nlaunch;
+            }
+        } else {
+            for (int q = 0; q < nr; ++q) cudaLaunchKernelEx(&cfg_s, spmv, cj[q], j);
+            nlaunch += nr;
+        }
+        for (int q = 0; q < nr; ++q) cudaLaunchKernelEx(&cfg_u, update, cj[q], j);
+        nlaunch += nr;
+    }
+    for (int q = 0; q < nr; ++q) {
+        const LpCtx &c = runs[q].c;
+        k_arnoldi_finish_lp<TB><<<G, kThreads, 0, st>>>(c);
+        k_arnoldi_eps_lp<<<(m + (kThreads / 32) - 1) / (kThreads / 32), kThreads, 0, st>>>(c);
+        k_arnoldi_info_lp<<<1, kThreads, 0, st>>>(c, info[q]);
+        nlaunch += 3;
+    }
+    count_launches(nlaunch);
+    const cudaError_t e = cudaGetLastError();
+    for (int q = 0; q < nr; ++q) dfree(runs[q].ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reduced-precision block Arnoldi kernels");
     return SKF_OK;
 }
 

@@ -540,6 +540,12 @@ skf_status arnoldi_run(const skf_csr *A, const skf_sketch *S, const double *b, i
 skf_status arnoldi_run_f32(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, float *V,
                            int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
                            skf_info *info, cudaStream_t st, const StepHook *hook = nullptr, int vring = 0);
+// nr FP32-basis Arnoldi processes on one operator and one sketch in lockstep
+// (one SpMM per step for each group of right-hand sides; skf_arnoldi_lp.cuh)
+skf_status arnoldi_run_f32_block(const skf_csr *A, const skf_sketch *S, int nr, const double *const *b, int m, int k,
+                                 float *const *V, int64_t ldv, double *const *vscale, double *const *SV,
+                                 double *const *SAV, double *const *H, int *const *iscal, skf_info *const *info,
+                                 cudaStream_t st);
 skf_status arnoldi_run_bf16(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, void *V,
                             int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
                             skf_info *info, cudaStream_t st, const StepHook *hook = nullptr, int vring = 0);

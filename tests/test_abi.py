@@ -58,6 +58,7 @@ def test_host_side_validation(skf):
     assert L.skf_set_arnoldi_mode(0) == 0
     assert L.skf_set_qr_mode(2) == 1 and L.skf_set_qr_mode(0) == 0
     assert L.skf_set_tail_form(2) == 1 and L.skf_set_tail_form(-1) == 1 and L.skf_set_tail_form(0) == 0
+    assert L.skf_set_block_mode(2) == 1 and L.skf_set_block_mode(-1) == 1 and L.skf_set_block_mode(0) == 0
     assert L.skf_barrier_selftest(1, 10**6, None, None) == 1          # NULL status pointer
 
 

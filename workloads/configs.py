@@ -83,6 +83,10 @@ WORKLOADS = {
     "cd3d_n256_fp32": Workload("cd3d_n256_fp32", _cd(3, 256, (50.0, 50.0, 50.0)), "invsqrt", m=120,
                                k=2, s=480, value_dtype="f32", basis_dtype="f32",
                                lam_lo=laplacian_lambda_min(256, 3)),
+    # mid-size FP32 step (N = 512,000; the batched workload's sizes), for profiles
+    "cd3d_n80_fp32": Workload("cd3d_n80_fp32", _cd(3, 80, (50.0, 50.0, 50.0)), "invsqrt", m=20,
+                              k=2, s=80, value_dtype="f32", basis_dtype="f32",
+                              lam_lo=laplacian_lambda_min(80, 3)),
     # directed power-law graph, N = 4e6, FP32, k = 3, z^{-1/2}, 128 nodes
     "graph_n4m": Workload("graph_n4m", lambda: powerlaw_graph_operator(4_000_000, 2.1, 10.0, SEEDS["matrix"]),
                           "invsqrt", m=150, k=3, s=600, value_dtype="f32", basis_dtype="f32",
