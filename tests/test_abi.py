@@ -60,6 +60,14 @@ def test_host_side_validation(skf):
     assert L.skf_set_tail_form(2) == 1 and L.skf_set_tail_form(-1) == 1 and L.skf_set_tail_form(0) == 0
     assert L.skf_set_block_mode(2) == 1 and L.skf_set_block_mode(-1) == 1 and L.skf_set_block_mode(0) == 0
     assert L.skf_barrier_selftest(1, 10**6, None, None) == 1          # NULL status pointer
+    # block solve and precision plan: argument checks before any device work
+    assert L.skf_solve_block(1, None, None, None, 10, -1, None, None, None, 10, None, None) == 1
+    assert L.skf_solve_block(1, None, None, None, 10, 0, None, None, None, 10, None, None) == 0   # empty block
+    cond = (ctypes.c_double * 1)()
+    f32 = (ctypes.c_int32 * 1)()
+    assert L.skf_plan_basis_precision(-1, None, 1e-6, cond, f32, None) == 1
+    assert L.skf_plan_basis_precision(0, None, 0.0, cond, f32, None) == 1                      # tol <= 0
+    assert L.skf_plan_basis_precision(0, None, 1e-6, cond, f32, None) == 0
 
 
 @pytest.mark.parametrize("func,ell,c", [("invsqrt", 45, 1.0), ("invsqrt", 300, 1885.0),
