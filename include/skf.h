@@ -228,8 +228,10 @@ int64_t skf_kernel_launch_count(void);
  * and of A v_j in shared memory.  It applies to an F64 basis with a
  * sparse-sign sketch, k <= 4, one-pass storage without the stopping
  * criterion, and (k + 1) * ceil(N / SMs) * 8 bytes (plus the sketch bins)
- * within the per-CTA shared memory (N up to about 1e6 at k = 2 on a
- * 152-SM GB300).  Its grid barriers wait at most about one second each and
+ * within the per-CTA shared memory (N up to about 1.1e6 at k = 2 on a
+ * 152-SM GB300); for k <= 2 and slices at most 7 wide it also runs with
+ * A v_j in global memory (L2) when only the k window vectors fit (N up to
+ * about 1.6e6).  Its grid barriers wait at most about one second each and
  * then report SKF_ERR_TIMEOUT in skf_info::status.
  * Returns INVALID_ARG for another mode. */
 skf_status skf_set_arnoldi_mode(int32_t mode);

@@ -71,6 +71,7 @@ struct PCtx {
     unsigned long long *accw;  // [m][2][s]: limb sums of S w_j
     unsigned long long *accy;  // [2][s]: limb sums of the directly sketched y~
     double *Sw;                // s x m: S w_j (unnormalised)
+    double *ysg;               // y~ in global memory ([G][R]) when the rows do not fit with it on chip
     unsigned *bar;             // barrier arrival counter (zeroed before launch)
     int *flag;                 // 1 once a barrier wait ran out
     long long budget;
@@ -326,7 +327,7 @@ __device__ __forceinline__ void spmv_rows(const PCtx &c, const double *__restric
     }
 }
 
-template <int KW, int W, int ZCAP>
+template <int KW, int W, int ZCAP, bool YG>
 __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
     extern __shared__ __align__(16) unsigned char psm[];
     constexpr int kRed = KW * kPT + 4 * KW + kPNW;   // block_reduce_t0<KW>
@@ -338,8 +339,10 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
     const int nr = (int)min((int64_t)R, c.n - r0);          // rows of this CTA (>= 1)
     const int nsl = (nr + 31) >> 5;                          // slices of this CTA
     double *win = (double *)psm;                             // [k][R]: w_i at slot i % k
-    double *ys = win + (size_t)k * R;                        // [R]
-    double *red = ys + R;                                    // block reductions
+    // [R] y~ of this CTA's rows: shared memory, or (YG) this CTA's slice of a
+    // global array, read back by the same CTA after a block barrier (L2)
+    double *ys = YG ? c.ysg + r0 : win + (size_t)k * R;
+    double *red = YG ? win + (size_t)k * R : ys + R;         // block reductions
     double *tp = red + kRed;                                 // [KW][kPT] per-thread norm / Gram partials
     unsigned long long *tk = (unsigned long long *)(tp + KW * kPT);   // [kPT] per-thread max|w| keys
     long long *meta_o = (long long *)(tk + kPT);             // [nsl] slice offsets
@@ -741,9 +744,9 @@ __global__ void __launch_bounds__(32) k_barrier_selftest(unsigned *bar, int *fla
     if (blockIdx.x == 0 && threadIdx.x == 0) *status = ok ? SKF_OK : SKF_ERR_TIMEOUT;
 }
 
-template <int KW, int W, int ZCAP>
+template <int KW, int W, int ZCAP, bool YG>
 cudaError_t launch_persist(const PCtx &c, int G, size_t smem, cudaStream_t st) {
-    auto kern = k_arnoldi_persist<KW, W, ZCAP>;
+    auto kern = k_arnoldi_persist<KW, W, ZCAP, YG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -763,24 +766,33 @@ cudaError_t launch_persist(const PCtx &c, int G, size_t smem, cudaStream_t st) {
     return cudaLaunchKernelEx(&cfg, kern, c);
 }
 
-template <int KW, int W>
+template <int KW, int W, bool YG>
 cudaError_t launch_persist_z(const PCtx &c, int G, size_t smem, cudaStream_t st) {
-    return c.sp.zeta <= 8 ? launch_persist<KW, W, 8>(c, G, smem, st) : launch_persist<KW, W, 16>(c, G, smem, st);
+    return c.sp.zeta <= 8 ? launch_persist<KW, W, 8, YG>(c, G, smem, st)
+                          : launch_persist<KW, W, 16, YG>(c, G, smem, st);
 }
 
 template <int KW>
 cudaError_t launch_persist_w(const PCtx &c, int maxw, int G, size_t smem, cudaStream_t st) {
-    if (maxw <= 5) return launch_persist_z<KW, 5>(c, G, smem, st);
-    if (maxw <= 7) return launch_persist_z<KW, 7>(c, G, smem, st);
-    if (maxw <= 8) return launch_persist_z<KW, 8>(c, G, smem, st);
-    return launch_persist_z<KW, 0>(c, G, smem, st);
+    if (maxw <= 5) return launch_persist_z<KW, 5, false>(c, G, smem, st);
+    if (maxw <= 7) return launch_persist_z<KW, 7, false>(c, G, smem, st);
+    if (maxw <= 8) return launch_persist_z<KW, 8, false>(c, G, smem, st);
+    return launch_persist_z<KW, 0, false>(c, G, smem, st);
 }
 
-// Dynamic shared memory of the persistent kernel for R rows per CTA.
-size_t persist_smem(int R, int k, int KW, int s) {
+// y~ in global memory: instantiated for k <= 2 and slices at most 7 wide (the
+// 5- and 7-point stencils) only
+cudaError_t launch_persist_yg(const PCtx &c, int maxw, int G, size_t smem, cudaStream_t st) {
+    if (maxw <= 5) return launch_persist_z<2, 5, true>(c, G, smem, st);
+    return launch_persist_z<2, 7, true>(c, G, smem, st);
+}
+
+// Dynamic shared memory of the persistent kernel for R rows per CTA (yg: y~
+// kept in global memory instead).
+size_t persist_smem(int R, int k, int KW, int s, bool yg) {
     const size_t red = (size_t)KW * kPT + 4 * KW + kPNW;
     const size_t thread_partials = (size_t)(KW + 1) * kPT;
-    return sizeof(double) * ((size_t)(k + 1) * R + red + thread_partials) +
+    return sizeof(double) * ((size_t)(k + (yg ? 0 : 1)) * R + red + thread_partials) +
            (sizeof(long long) + sizeof(int)) * (size_t)(R / 32) + sizeof(int) * 6 * (size_t)s;
 }
 
@@ -814,15 +826,21 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     const int R = (int)R64;
     const int KW = k <= 2 ? 2 : 4;
     const int s = S->s;
-    const size_t smem = persist_smem(R, k, KW, s);
+    size_t smem = persist_smem(R, k, KW, s, false);
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
         cudaGetLastError();
         return SKF_ERR_NOT_SUPPORTED;
     }
-    // static shared arrays of the kernel take about 3 KB
-    if (smem + 4096 > (size_t)optin) return SKF_ERR_NOT_SUPPORTED;
+    // static shared arrays of the kernel take about 3 KB; past the per-CTA
+    // shared memory the window alone may still fit, with y~ in global memory
+    bool yg = false;
+    if (smem + 4096 > (size_t)optin) {
+        yg = true;
+        smem = persist_smem(R, k, KW, s, true);
+        if (KW != 2 || A->max_width > 7 || smem + 4096 > (size_t)optin) return SKF_ERR_NOT_SUPPORTED;
+    }
     int coop = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
         cudaGetLastError();
@@ -863,7 +881,8 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     const size_t szAy = sizeof(unsigned long long) * 2 * (size_t)s;
     const size_t szSw = sizeof(double) * (size_t)s * m;
     const size_t szBar = 2 * sizeof(int) + sizeof(unsigned long long);   // counter, flag, eps maximum
-    const size_t total = 2 * al(szP) + al(szAw) + al(szAy) + al(szSw) + al(szBar);
+    const size_t szYs = yg ? sizeof(double) * (size_t)G * R : 0;
+    const size_t total = 2 * al(szP) + al(szAw) + al(szAy) + al(szSw) + al(szBar) + al(szYs);
     char *ws = nullptr;
     skf_status stt = dalloc((void **)&ws, total, st);
     if (stt != SKF_OK) return stt;
@@ -879,13 +898,15 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     c.accy = (unsigned long long *)take(szAy);
     c.Sw = (double *)take(szSw);
     c.bar = (unsigned *)take(szBar);
+    c.ysg = yg ? (double *)take(szYs) : nullptr;
     c.flag = (int *)(c.bar + 1);
     unsigned long long *epsmax = (unsigned long long *)(c.bar + 2);
     // accumulators and the barrier start at zero (one memset: they are adjacent)
     cudaMemsetAsync(c.accw, 0, (size_t)((char *)c.Sw - (char *)c.accw), st);
     cudaMemsetAsync(c.bar, 0, szBar, st);
     cudaError_t e;
-    if (KW == 2) e = launch_persist_w<2>(c, A->max_width, G, smem, st);
+    if (yg) e = launch_persist_yg(c, A->max_width, G, smem, st);
+    else if (KW == 2) e = launch_persist_w<2>(c, A->max_width, G, smem, st);
     else e = launch_persist_w<4>(c, A->max_width, G, smem, st);
     if (e != cudaSuccess) {
         cudaGetLastError();

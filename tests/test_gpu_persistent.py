@@ -177,3 +177,32 @@ def test_solves_in_both_forms_match_oracle(skf, method):
         assert rel(x.cpu().numpy(), xo) <= 1e-10, mode
         xs.append(x.cpu().numpy())
     assert rel(xs[0], xs[1]) <= 1e-11
+
+
+def test_persistent_form_with_y_in_global_memory(skf):
+    """N = 1,404,225 (2D, n = 1185): 9,248 rows per CTA, so the window and A w_j
+    no longer fit in the shared memory of a CTA together; the persistent form
+    keeps the window on chip and A w_j in global memory (L2).  Per column
+    against the oracle and the two-kernel form, and an sGMRES solve."""
+    n = 1185
+    A = convdiff_2d(n, (100.0, 50.0))
+    b = gaussian_rhs(A.n, 5)
+    m, k, s = 24, 2, 96
+    gp = gpu_arnoldi(skf, A, b, m, k, s, "persistent")      # the persistent form is required here
+    gt = gpu_arnoldi(skf, A, b, m, k, s, "two_kernel")
+    ar = o_arnoldi(csr_to_scipy(A), b, m, k, OSketch("sparse_sign", A.n, s, 8, 13))
+    check_against_oracle(gp, ar, m)
+    assert rel(gp["V"], gt["V"]) < 1e-12
+    assert rel(gp["SV"], gt["SV"]) < 1e-12 and rel(gp["SAV"], gt["SAV"]) < 1e-12
+    c = quad_scale("invsqrt", laplacian_lambda_min(n, 2), float(abs(csr_to_scipy(A)).sum(1).max()))
+    op = upload(skf, A)
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, s, 8, 13)
+    info = skf.new_info()
+    with skf.arnoldi_mode(skf.ARNOLDI_PERSISTENT):
+        x = skf.sgmres(op.csr, S, torch.as_tensor(b, device="cuda"), skf.make_func("invsqrt", c),
+                       skf.make_params(m, k, tol=1e-12), info=info)
+        torch.cuda.synchronize()
+    xo, _ = osk.solve(csr_to_scipy(A), b, "invsqrt", m, k, OSketch("sparse_sign", A.n, s, 8, 13), c,
+                      method="sgmres", tol=1e-12)
+    assert skf.read_info(info)["status"] == 0
+    assert rel(x.cpu().numpy(), xo) <= 1e-10
