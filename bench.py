@@ -37,13 +37,14 @@ HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) per Arnoldi step, summed over the spmv and update
 # kernels of one ncu capture of those kernels as they stand; keyed by workload,
 # basis dtype and sketch, and removed whenever those kernels change.
+FP32_STEP_TRAFFIC = 1511.9e6   # DRAM bytes per FP32 step at N = 16.8M (ncu, the current kernels)
 # ncu dram bytes per Arnoldi step, for step kernels unchanged since their capture;
-# the FP32 kernels changed after theirs (1516.3 MB per step), so their entry is null
 # k_arnoldi_persist is one launch for all m steps: per-step bytes are the
-# difference of two captures (m = 40 and m = 12) over 28 steps
-NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64", "sparse_sign", True): 91.7e6,
+# difference of two captures (m = 40 and m = 12) over 28 steps; the FP32 entry
+# is the two step kernels of one step (spmv 1125.4 MB + update 386.4 MB)
+NCU_TRAFFIC_PER_STEP = {("cd3d_n100", "f64", "sparse_sign", True): 91.4e6,
                         ("cd3d_n100", "f64", "sparse_sign", False): None,
-                        ("cd3d_n256_fp32", "f32", "sparse_sign", False): None}
+                        ("cd3d_n256_fp32", "f32", "sparse_sign", False): FP32_STEP_TRAFFIC}
 
 
 BASIS_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
@@ -351,7 +352,6 @@ def run_arnoldi_only(args, wl, A, b, op, dev, rank, world):
 
 # ----------------------------------------------------------------- batched workload
 BATCH_TOL = 1e-6          # error gate of a batched FP32-basis solve against the FP64 one
-FP32_STEP_TRAFFIC = 1511.9e6   # DRAM bytes per FP32 step at N = 16.8M (spmv 1125.4 MB + update 386.4 MB, ncu)
 BATCH_FUNC = "invsqrt"
 
 
