@@ -368,3 +368,43 @@ def test_bf16_basis_dense_sketch_not_supported(skf):
     with pytest.raises(skf.SkfError, match="NOT_SUPPORTED"):
         skf.arnoldi_trunc(op.csr, S, torch.as_tensor(gaussian_rhs(A.n, 1), device="cuda"), 8, 2,
                           basis_dtype=torch.bfloat16)
+
+
+@pytest.mark.parametrize("basis", ["f64", "f32"])
+def test_returned_h_is_the_relation_of_the_stored_basis(skf, basis):
+    """H as skf_arnoldi_trunc returns it holds the Arnoldi relation (eq. (2.1))
+    of the stored, normalised basis: S A v_j = S V_{j+2} H(:, j) for j < m - 1
+    to FP64 rounding (the FP32 path forms those S A v_j from that very
+    relation), and A v_j = V H(:, j) to the basis precision (FP64: rounding of
+    the recurrence; FP32: the FP32 SpMV and update)."""
+    A = convdiff_2d(60, (80.0, 20.0))
+    b = gaussian_rhs(A.n, 9)
+    m, k, s = 30, 2, 120
+    if basis == "f32":
+        op = upload32(skf, A)
+        M = a32(A)
+    else:
+        op = skf.upload_csr(A.rowptr, A.colind, A.values, device="cuda")
+        M = csr_to_scipy(A)
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, s, 8, 13)
+    V, vs, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, torch.as_tensor(b, device="cuda"), m, k,
+                                          basis_dtype=torch.float32 if basis == "f32" else torch.float64)
+    torch.cuda.synchronize()
+    Vn = (V.double() * vs[:, None]).cpu().numpy().T
+    SVn, SAVn, Hn = SV.cpu().numpy().T, SAV.cpu().numpy().T, H.cpu().numpy().T   # H: (m + 1) x m
+    sk = SVn[:, :m] @ Hn[:m, : m - 1]
+    d_sk = np.linalg.norm(sk - SAVn[:, : m - 1]) / np.linalg.norm(SAVn[:, : m - 1])
+    AV = M @ Vn[:, : m - 1]
+    R = AV - Vn[:, :m] @ Hn[:m, : m - 1]
+    d_rel = np.linalg.norm(R) / np.linalg.norm(AV)
+    print(f"{basis}: sketched relation {d_sk:.2e}, relation {d_rel:.2e}")
+    assert d_sk <= 1e-12
+    if basis == "f64":
+        assert d_rel <= 1e-13
+    else:
+        # per column: the FP32 SpMV and update roundings, as in check_sketches
+        width = int(np.diff(A.rowptr).max())
+        absAV = abs(M) @ np.abs(Vn[:, : m - 1])
+        for j in range(m - 1):
+            bound = 4 * (width + k + 2) * U32 * np.linalg.norm(absAV[:, j]) / np.linalg.norm(AV[:, j])
+            assert np.linalg.norm(R[:, j]) / np.linalg.norm(AV[:, j]) <= bound, j
