@@ -225,7 +225,8 @@ int64_t skf_kernel_launch_count(void);
  *      apply.
  * The persistent form runs all m steps of Algorithm 2 in one cooperative
  * launch, one CTA per SM, each CTA keeping its rows of the window vectors
- * and of A v_j in shared memory.  It applies to an F64 basis with a
+ * and of A v_j in shared memory.  It applies to an F64 basis (and to an F32
+ * basis with k <= 2 and slices at most 7 wide, N up to about 2e6) with a
  * sparse-sign sketch, k <= 4, one-pass storage without the stopping
  * criterion, and (k + 1) * ceil(N / SMs) * 8 bytes (plus the sketch bins)
  * within the per-CTA shared memory (N up to about 1.1e6 at k = 2 on a

@@ -458,8 +458,17 @@ static skf_status run_arnoldi(const skf_csr *A, const skf_sketch *S, const doubl
                               skf_info *info, cudaStream_t cs, const StepHook *hook = nullptr, int vring = 0) {
     if (basis == SKF_F64)
         return arnoldi_run(A, S, b, m, k, (double *)V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook, vring);
-    if (basis == SKF_F32)
+    if (basis == SKF_F32) {
+        // the persistent form where it applies (as for FP64: no per-step hooks,
+        // one-pass storage), else the two-kernel form
+        if (step_mode() != 1 && hook == nullptr && vring == 0) {
+            const skf_status ps =
+                arnoldi_run_persistent_f32(A, S, b, m, k, (float *)V, ldv, vscale, SV, SAV, H, iscal, info, cs);
+            if (ps != SKF_ERR_NOT_SUPPORTED) return ps;
+            if (step_mode() == 2) return fail(SKF_ERR_NOT_SUPPORTED, "persistent Arnoldi form does not apply here");
+        }
         return arnoldi_run_f32(A, S, b, m, k, (float *)V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook, vring);
+    }
     return arnoldi_run_bf16(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, cs, hook, vring);
 }
 

@@ -52,7 +52,7 @@ struct PCtx {
     int R;                     // rows per CTA (multiple of 32)
     const int64_t *sell_off;
     const int32_t *sell_w;
-    const double *sell_val;
+    const void *sell_val;      // T values (T = double, or float for an FP32 basis)
     const int32_t *sell_col;
     SparseSign sp;
     const uint16_t *pattern;   // [n][zeta]
@@ -62,7 +62,7 @@ struct PCtx {
     double sk_scale;           // 1 / sqrt(zeta)
     int m, k;
     const double *b;
-    double *V;
+    void *V;                   // T [m][ldv]
     int64_t ldv;
     double *vscale, *SV, *SAV, *H;
     int *iscal;
@@ -71,7 +71,7 @@ struct PCtx {
     unsigned long long *accw;  // [m][2][s]: limb sums of S w_j
     unsigned long long *accy;  // [2][s]: limb sums of the directly sketched y~
     double *Sw;                // s x m: S w_j (unnormalised)
-    double *ysg;               // y~ in global memory ([G][R]) when the rows do not fit with it on chip
+    void *ysg;                 // T y~ in global memory ([G][R]) when the rows do not fit with it on chip
     unsigned *bar;             // barrier arrival counter (zeroed before launch)
     int *flag;                 // 1 once a barrier wait ran out
     long long budget;
@@ -226,11 +226,12 @@ __device__ __forceinline__ void scatter_row(const PCtx &c, int64_t r, uint2 pv, 
 // offsets of the window in win[], nw of them) and the magnitude key of
 // max|y~|.  Entries of one row are summed in their SELL (= CSR) order.
 constexpr int kSpmvWarps = kPNW - 1;   // the last warp serves the reductions
-template <int KW, int W>
-__device__ __forceinline__ void spmv_rows(const PCtx &c, const double *__restrict__ wsrc, const double *win,
-                                          const int (&soff)[KW], int nw, double *ys, const long long *meta_o,
-                                          const int *meta_w, int nsl, int nr, double (&acc)[KW],
+template <int KW, int W, typename T>
+__device__ __forceinline__ void spmv_rows(const PCtx &c, const T *__restrict__ wsrc, const T *win,
+                                          const int (&soff)[KW], int nw, T *ys, const long long *meta_o,
+                                          const int *meta_w, int nsl, int nr, T (&acc)[KW],
                                           unsigned long long &ykey) {
+    const T *sell_val = (const T *)c.sell_val;
     const int lane = threadIdx.x & 31;
     int next_t = threadIdx.x >> 5;
     auto grab = [&]() {
@@ -249,13 +250,13 @@ __device__ __forceinline__ void spmv_rows(const PCtx &c, const double *__restric
 #pragma unroll
             for (int p = 0; p < W; ++p) cv[p] = p < wt ? __ldcs(pc + 32 * p) : 0;
         }
-        double av[W], xv[W];
+        T av[W], xv[W];
         {
-            const double *pv = c.sell_val + (t < nsl ? meta_o[t] : 0) + lane;
+            const T *pv = sell_val + (t < nsl ? meta_o[t] : 0) + lane;
 #pragma unroll
             for (int p = 0; p < W; ++p) {
-                av[p] = p < wt ? __ldcs(pv + 32 * p) : 0.0;
-                xv[p] = p < wt ? __ldcg(wsrc + cv[p]) : 0.0;
+                av[p] = p < wt ? __ldcs(pv + 32 * p) : T(0);
+                xv[p] = p < wt ? __ldcg(wsrc + cv[p]) : T(0);
             }
         }
         int tn = t < nsl ? grab() : nsl;
@@ -267,13 +268,13 @@ __device__ __forceinline__ void spmv_rows(const PCtx &c, const double *__restric
             for (int p = 0; p < W; ++p) cvn[p] = p < wtn ? __ldcs(pc + 32 * p) : 0;
         }
         while (t < nsl) {
-            double avn[W], xvn[W];
+            T avn[W], xvn[W];
             {
-                const double *pv = c.sell_val + (tn < nsl ? meta_o[tn] : 0) + lane;
+                const T *pv = sell_val + (tn < nsl ? meta_o[tn] : 0) + lane;
 #pragma unroll
                 for (int p = 0; p < W; ++p) {
-                    avn[p] = p < wtn ? __ldcs(pv + 32 * p) : 0.0;
-                    xvn[p] = p < wtn ? __ldcg(wsrc + cvn[p]) : 0.0;
+                    avn[p] = p < wtn ? __ldcs(pv + 32 * p) : T(0);
+                    xvn[p] = p < wtn ? __ldcg(wsrc + cvn[p]) : T(0);
                 }
             }
             const int tnn = tn < nsl ? grab() : nsl;
@@ -286,7 +287,7 @@ __device__ __forceinline__ void spmv_rows(const PCtx &c, const double *__restric
             }
             const int lr = t * 32 + lane;
             if (lr < nr) {
-                double y = 0.0;
+                T y = T(0);
 #pragma unroll
                 for (int p = 0; p < W; ++p)
                     if (p < wt) y = fma(av[p], xv[p], y);
@@ -294,7 +295,7 @@ __device__ __forceinline__ void spmv_rows(const PCtx &c, const double *__restric
 #pragma unroll
                 for (int a = 0; a < KW; ++a)
                     if (a < nw) acc[a] = fma(win[soff[a] + lr], y, acc[a]);
-                ykey = max(ykey, abs_key(y));
+                ykey = max(ykey, abs_key((double)y));
             }
             t = tn;
             wt = wtn;
@@ -313,22 +314,27 @@ __device__ __forceinline__ void spmv_rows(const PCtx &c, const double *__restric
             const int lr = t * 32 + lane;
             const int wt = meta_w[t];
             const long long o = meta_o[t] + lane;
-            double y = 0.0;
+            T y = T(0);
             for (int p = 0; p < wt; ++p)
-                y = fma(__ldcs(c.sell_val + o + 32 * p), __ldcg(wsrc + __ldcs(c.sell_col + o + 32 * p)), y);
+                y = fma(__ldcs(sell_val + o + 32 * p), __ldcg(wsrc + __ldcs(c.sell_col + o + 32 * p)), y);
             if (lr < nr) {
                 ys[lr] = y;
 #pragma unroll
                 for (int a = 0; a < KW; ++a)
                     if (a < nw) acc[a] = fma(win[soff[a] + lr], y, acc[a]);
-                ykey = max(ykey, abs_key(y));
+                ykey = max(ykey, abs_key((double)y));
             }
         }
     }
 }
 
-template <int KW, int W, int ZCAP, bool YG>
+// T = double: the FP64 basis; T = float: an FP32 basis with FP32 SpMV,
+// orthogonalisation and accumulation, the update applying the FP32 values of
+// sigma_j and of the MGS coefficients (H and S A v_j are those of the relation
+// with the applied values), everything else FP64.
+template <int KW, int W, int ZCAP, bool YG, typename T>
 __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
+    constexpr bool F32 = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char psm[];
     constexpr int kRed = KW * kPT + 4 * KW + kPNW;   // block_reduce_t0<KW>
     constexpr int kSvc = kPNW - 1;                   // the service warp
@@ -338,11 +344,12 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
     const int64_t r0 = (int64_t)g * R;
     const int nr = (int)min((int64_t)R, c.n - r0);          // rows of this CTA (>= 1)
     const int nsl = (nr + 31) >> 5;                          // slices of this CTA
-    double *win = (double *)psm;                             // [k][R]: w_i at slot i % k
+    T *win = (T *)psm;                                       // [k][R]: w_i at slot i % k
+    T *Vb = (T *)c.V;
     // [R] y~ of this CTA's rows: shared memory, or (YG) this CTA's slice of a
     // global array, read back by the same CTA after a block barrier (L2)
-    double *ys = YG ? c.ysg + r0 : win + (size_t)k * R;
-    double *red = YG ? win + (size_t)k * R : ys + R;         // block reductions
+    T *ys = YG ? (T *)c.ysg + r0 : win + (size_t)k * R;
+    double *red = (double *)(YG ? win + (size_t)k * R : ys + R);   // block reductions (R: multiple of 32)
     double *tp = red + kRed;                                 // [KW][kPT] per-thread norm / Gram partials
     unsigned long long *tk = (unsigned long long *)(tp + KW * kPT);   // [kPT] per-thread max|w| keys
     long long *meta_o = (long long *)(tk + kPT);             // [nsl] slice offsets
@@ -354,6 +361,7 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
 
     // per-step scalars, in rings indexed by step & 3 (k <= 4)
     __shared__ double sig[4];                // sigma_i = 1 / ||w_i||
+    __shared__ double sap[4];                // the sigma_i the update of step i applied (FP32: rounded)
     __shared__ double grm[4][kMaxK];         // grm[i & 3][d] = <w_i, w_{i-d}>
     __shared__ double coef[4][kMaxK];        // c_b for w_{i-b} (newest first) of the update of step i
     __shared__ int cnw[4];                   // window length of step i
@@ -384,6 +392,8 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
             double v = swv;
             for (int b2 = pn - 1; b2 >= 0; --b2)
                 v = fma(coef[(i - 1) & 3][b2], __ldcg(c.Sw + is + (size_t)(i - 1 - b2) * s), v);
+            // the update applied sap y~ (= sigma y~ in FP64): S A v = (sigma / sap) (...)
+            if constexpr (F32) v *= sig[(i - 1) & 3] / sap[(i - 1) & 3];
             c.SAV[is + (size_t)(i - 1) * s] = v;
         }
     };
@@ -434,9 +444,10 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
         double nrm[1] = {0.0};
         unsigned long long key = 0;
         for (int lr = tid; lr < nr; lr += kPT) {
-            const double x = c.b[r0 + lr];
-            c.V[r0 + lr] = x;
-            win[lr] = x;    // slot 0
+            const T xt = (T)c.b[r0 + lr];
+            const double x = (double)xt;
+            Vb[r0 + lr] = xt;
+            win[lr] = xt;    // slot 0
             nrm[0] = fma(x, x, nrm[0]);
             key = max(key, abs_key(x));
         }
@@ -463,6 +474,7 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
     }
     if (tid == 0) {
         sig[0] = rsqrt(sb[0]);
+        sap[0] = F32 ? (double)(float)sig[0] : sig[0];
         ews[0] = positive_finite(sb[1]) ? bound_exponent(sb[1]) : kNoExp;
         if (g == 0) c.vscale[0] = sig[0];
     }
@@ -479,9 +491,9 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
         // bins to the global sums and finalises the sketch columns of step
         // j - 2: none of it is needed before the barrier, and phase A does not
         // need the norm of w_j (stored unnormalised).
-        double acc[KW];
+        T acc[KW];
 #pragma unroll
-        for (int a = 0; a < KW; ++a) acc[a] = 0.0;
+        for (int a = 0; a < KW; ++a) acc[a] = T(0);
         unsigned long long ykey = 0;
         if (warp == kSvc && j >= 1) {
             double v[KW];
@@ -516,13 +528,16 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
 #pragma unroll
             for (int a = 0; a < KW; ++a) soff[a] = a < nw ? ((i0 + a) % k) * R : 0;
             if (warp < kSpmvWarps)
-                spmv_rows<KW, W>(c, c.V + (size_t)j * c.ldv, win, soff, nw, ys, meta_o, meta_w, nsl, nr, acc, ykey);
+                spmv_rows<KW, W, T>(c, Vb + (size_t)j * c.ldv, win, soff, nw, ys, meta_o, meta_w, nsl, nr, acc, ykey);
         }
-        ykey = block_reduce_t0<KW>(acc, ykey, red);
+        double accd[KW];
+#pragma unroll
+        for (int a = 0; a < KW; ++a) accd[a] = (double)acc[a];
+        ykey = block_reduce_t0<KW>(accd, ykey, red);
         if (tid == 0) {
 #pragma unroll
             for (int a = 0; a < KW; ++a)
-                if (a < nw) c.pA[(size_t)a * G + g] = acc[a];
+                if (a < nw) c.pA[(size_t)a * G + g] = accd[a];
             c.pA[(size_t)KW * G + g] = key_to_abs(ykey);
         }
         if (!grid_barrier(c.bar, c.flag, ++nb, c.budget)) goto timeout;
@@ -548,16 +563,20 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
                 const double n2 = sb[0];
                 double hs = 0.0;
                 for (int a = 0; a < cnw[(j - 1) & 3]; ++a) hs = fma(sh[a], sh[a], hs);
-                sbreak = (n2 > 1e-24 * (hs + n2)) ? 0 : 1;
+                // (FP32: ||w_j|| <= 2^-17 ||A v_{j-1}||, 64 FP32 unit roundoffs)
+                sbreak = (n2 > (F32 ? 5.820766091346741e-11 : 1e-24) * (hs + n2)) ? 0 : 1;
                 const double sgm = n2 > 0.0 ? rsqrt(n2) : 0.0;
                 const double hn = n2 * sgm;
                 if (!sbreak) {   // w_j enters the window
                     sig[j & 3] = sgm;
+                    sap[j & 3] = F32 ? (double)(float)sgm : sgm;
                     for (int d = 1; d <= ngj; ++d) grm[j & 3][d] = sb[1 + d];
                     ews[j & 3] = positive_finite(sb[1]) ? bound_exponent(sb[1]) : kNoExp;
                 }
                 if (g == 0) {
-                    c.H[j + (size_t)(j - 1) * (m + 1)] = hn;
+                    // FP32: the coefficient of v_j in A v_{j-1} with the applied sigma_{j-1}
+                    c.H[j + (size_t)(j - 1) * (m + 1)] =
+                        F32 ? sig[(j - 1) & 3] * hn / sap[(j - 1) & 3] : hn;
                     if (!sbreak) c.vscale[j] = sgm;
                 }
             }
@@ -574,12 +593,17 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
                         h -= sh[b2] * sa * sig[ib & 3] * grm[ia & 3][ia - ib];
                     }
                     sh[a] = h;
-                    coef[j & 3][nw - 1 - a] = h * sa;
+                    coef[j & 3][nw - 1 - a] = F32 ? (double)(float)(h * sa) : h * sa;
                 }
                 cnw[j & 3] = nw;
                 eys[j & 3] = positive_finite(sd[KW]) ? bound_exponent(sd[KW]) : kNoExp;
+                // FP32: the relation with the applied (rounded) sigma_j and coefficients
                 if (g == 0 && !last)
-                    for (int a = 0; a < nw; ++a) c.H[(i0 + a) + (size_t)j * (m + 1)] = sh[a];
+                    for (int a = 0; a < nw; ++a) {
+                        const int ia = i0 + a;
+                        c.H[ia + (size_t)j * (m + 1)] =
+                            F32 ? sj * coef[j & 3][nw - 1 - a] / (sap[j & 3] * sig[ia & 3]) : sh[a];
+                    }
             }
         }
         __syncthreads();
@@ -592,12 +616,12 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
             int soff[KW];
 #pragma unroll
             for (int a = 0; a < KW; ++a) soff[a] = a < nwb ? ((i0b + a) % k) * R : 0;
-            double accb[KW];
+            T accb[KW];
 #pragma unroll
-            for (int a = 0; a < KW; ++a) accb[a] = 0.0;
+            for (int a = 0; a < KW; ++a) accb[a] = T(0);
             unsigned long long kb = 0;
             if (warp < kSpmvWarps)
-                spmv_rows<KW, W>(c, c.V + (size_t)jb * c.ldv, win, soff, 0, ys, meta_o, meta_w, nsl, nr, accb, kb);
+                spmv_rows<KW, W, T>(c, Vb + (size_t)jb * c.ldv, win, soff, 0, ys, meta_o, meta_w, nsl, nr, accb, kb);
             __syncthreads();
             const int ey = eys[jb & 3];
             const int shift_y = c.frac - (ey == kNoExp ? 0 : ey);
@@ -626,24 +650,24 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
         // ---- phase B: w_{j+1} and this thread's partials of its norm, Gram
         // entries and max; sketch of w_j (and of y~ in the last step)
         {
-            const double sj = sig[j & 3];
+            const T sj = (T)sap[j & 3];   // sigma_j as applied
             const int ew = ews[j & 3], ey = eys[j & 3];
             const int shift_w = c.frac - (ew == kNoExp ? 0 : ew);
             const int shift_y = c.frac - (ey == kNoExp ? 0 : ey);
             const int ng = min(j + 1, k - 1);
             int *bw0 = bins + (j & 1) * 2 * s, *bw1 = bw0 + s;
-            double cf[KW];   // c_b for w_{j-b}
+            T cf[KW];        // c_b for w_{j-b} (as applied)
             int soffr[KW];   // slot offsets, newest first
 #pragma unroll
             for (int b2 = 0; b2 < KW; ++b2) {
-                cf[b2] = b2 < nw ? coef[j & 3][b2] : 0.0;
+                cf[b2] = b2 < nw ? (T)coef[j & 3][b2] : T(0);
                 soffr[b2] = b2 < nw ? ((j - b2) % k) * R : 0;
             }
             const int snew = ((j + 1) % k) * R;
-            double *wn = c.V + (size_t)(j + 1) * c.ldv;
-            double part[KW];
+            T *wn = Vb + (size_t)(j + 1) * c.ldv;
+            T part[KW];
 #pragma unroll
-            for (int a = 0; a < KW; ++a) part[a] = 0.0;
+            for (int a = 0; a < KW; ++a) part[a] = T(0);
             unsigned long long nkey = 0;
             uint2 pv_next = make_uint2(0u, 0u);
             if (p8 && tid < nr) pv_next = __ldg((const uint2 *)(c.pattern8 + (r0 + tid) * 8));
@@ -651,19 +675,19 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
                 const int64_t r = r0 + lr;
                 const uint2 pv = pv_next;
                 if (p8 && lr + kPT < nr) pv_next = __ldg((const uint2 *)(c.pattern8 + (r + kPT) * 8));
-                const double y = ys[lr];
-                double wv[KW];
+                const T y = ys[lr];
+                T wv[KW];
 #pragma unroll
-                for (int b2 = 0; b2 < KW; ++b2) wv[b2] = b2 < nw ? win[soffr[b2] + lr] : 0.0;
+                for (int b2 = 0; b2 < KW; ++b2) wv[b2] = b2 < nw ? win[soffr[b2] + lr] : T(0);
                 if (!last) {
-                    double w = sj * y;
+                    T w = sj * y;
 #pragma unroll
                     for (int b2 = KW - 1; b2 >= 0; --b2)
                         if (b2 < nw) w = fma(-cf[b2], wv[b2], w);   // oldest first
                     wn[r] = w;
                     win[snew + lr] = w;
                     part[0] = fma(w, w, part[0]);
-                    nkey = max(nkey, abs_key(w));
+                    nkey = max(nkey, abs_key((double)w));
 #pragma unroll
                     for (int d = 1; d < KW; ++d)
                         if (d <= ng) part[d] = fma(w, wv[d - 1], part[d]);
@@ -677,7 +701,7 @@ __global__ void __launch_bounds__(kPT, 1) k_arnoldi_persist(PCtx c) {
             }
             if (!last) {
 #pragma unroll
-                for (int a = 0; a < KW; ++a) tp[a * kPT + tid] = part[a];
+                for (int a = 0; a < KW; ++a) tp[a * kPT + tid] = (double)part[a];
                 tk[tid] = nkey;
             } else {
                 __syncthreads();
@@ -744,9 +768,9 @@ __global__ void __launch_bounds__(32) k_barrier_selftest(unsigned *bar, int *fla
     if (blockIdx.x == 0 && threadIdx.x == 0) *status = ok ? SKF_OK : SKF_ERR_TIMEOUT;
 }
 
-template <int KW, int W, int ZCAP, bool YG>
+template <int KW, int W, int ZCAP, bool YG, typename T>
 cudaError_t launch_persist(const PCtx &c, int G, size_t smem, cudaStream_t st) {
-    auto kern = k_arnoldi_persist<KW, W, ZCAP, YG>;
+    auto kern = k_arnoldi_persist<KW, W, ZCAP, YG, T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -766,33 +790,39 @@ cudaError_t launch_persist(const PCtx &c, int G, size_t smem, cudaStream_t st) {
     return cudaLaunchKernelEx(&cfg, kern, c);
 }
 
-template <int KW, int W, bool YG>
+template <int KW, int W, bool YG, typename T>
 cudaError_t launch_persist_z(const PCtx &c, int G, size_t smem, cudaStream_t st) {
-    return c.sp.zeta <= 8 ? launch_persist<KW, W, 8, YG>(c, G, smem, st)
-                          : launch_persist<KW, W, 16, YG>(c, G, smem, st);
+    return c.sp.zeta <= 8 ? launch_persist<KW, W, 8, YG, T>(c, G, smem, st)
+                          : launch_persist<KW, W, 16, YG, T>(c, G, smem, st);
 }
 
 template <int KW>
 cudaError_t launch_persist_w(const PCtx &c, int maxw, int G, size_t smem, cudaStream_t st) {
-    if (maxw <= 5) return launch_persist_z<KW, 5, false>(c, G, smem, st);
-    if (maxw <= 7) return launch_persist_z<KW, 7, false>(c, G, smem, st);
-    if (maxw <= 8) return launch_persist_z<KW, 8, false>(c, G, smem, st);
-    return launch_persist_z<KW, 0, false>(c, G, smem, st);
+    if (maxw <= 5) return launch_persist_z<KW, 5, false, double>(c, G, smem, st);
+    if (maxw <= 7) return launch_persist_z<KW, 7, false, double>(c, G, smem, st);
+    if (maxw <= 8) return launch_persist_z<KW, 8, false, double>(c, G, smem, st);
+    return launch_persist_z<KW, 0, false, double>(c, G, smem, st);
 }
 
 // y~ in global memory: instantiated for k <= 2 and slices at most 7 wide (the
 // 5- and 7-point stencils) only
 cudaError_t launch_persist_yg(const PCtx &c, int maxw, int G, size_t smem, cudaStream_t st) {
-    if (maxw <= 5) return launch_persist_z<2, 5, true>(c, G, smem, st);
-    return launch_persist_z<2, 7, true>(c, G, smem, st);
+    if (maxw <= 5) return launch_persist_z<2, 5, true, double>(c, G, smem, st);
+    return launch_persist_z<2, 7, true, double>(c, G, smem, st);
 }
 
-// Dynamic shared memory of the persistent kernel for R rows per CTA (yg: y~
-// kept in global memory instead).
-size_t persist_smem(int R, int k, int KW, int s, bool yg) {
+// FP32 basis: k <= 2, slices at most 7 wide, y~ on chip
+cudaError_t launch_persist_f32(const PCtx &c, int maxw, int G, size_t smem, cudaStream_t st) {
+    if (maxw <= 5) return launch_persist_z<2, 5, false, float>(c, G, smem, st);
+    return launch_persist_z<2, 7, false, float>(c, G, smem, st);
+}
+
+// Dynamic shared memory of the persistent kernel for R rows per CTA with
+// elements of vb bytes (yg: y~ kept in global memory instead).
+size_t persist_smem(int R, int k, int KW, int s, bool yg, size_t vb = sizeof(double)) {
     const size_t red = (size_t)KW * kPT + 4 * KW + kPNW;
     const size_t thread_partials = (size_t)(KW + 1) * kPT;
-    return sizeof(double) * ((size_t)(k + (yg ? 0 : 1)) * R + red + thread_partials) +
+    return vb * (size_t)(k + (yg ? 0 : 1)) * R + sizeof(double) * (red + thread_partials) +
            (sizeof(long long) + sizeof(int)) * (size_t)(R / 32) + sizeof(int) * 6 * (size_t)s;
 }
 
@@ -813,12 +843,18 @@ static int g_step_mode = 0;   // 0 auto, 1 two-kernel path only, 2 persistent pa
 void set_step_mode(int mode) { g_step_mode = mode; }
 int step_mode() { return g_step_mode; }
 
-skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V,
-                                  int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
-                                  skf_info *info, cudaStream_t st) {
-    if (S->kind != SKF_SKETCH_SPARSE_SIGN || S->binmax_persist == nullptr || k > 4 || A->vdtype != SKF_F64 ||
-        A->nlong > 0 || A->perm != nullptr)   // a row split or sorted slices take the two-kernel form
+// The persistent form for an FP64 basis (f32 = false) or an FP32 one (f32:
+// FP32 values, k <= 2, slices at most 7 wide, the window and y~ both on chip:
+// N up to about 2e6).
+static skf_status run_persistent(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, void *V,
+                                 int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
+                                 skf_info *info, cudaStream_t st, bool f32) {
+    if (S->kind != SKF_SKETCH_SPARSE_SIGN || S->binmax_persist == nullptr || k > 4 ||
+        A->vdtype != (f32 ? SKF_F32 : SKF_F64) || A->nlong > 0 ||
+        A->perm != nullptr)   // a row split or sorted slices take the two-kernel form
         return SKF_ERR_NOT_SUPPORTED;
+    if (f32 && (k > 2 || A->max_width > 7)) return SKF_ERR_NOT_SUPPORTED;
+    const size_t vb = f32 ? sizeof(float) : sizeof(double);
     int G;
     int64_t R64;
     persist_partition(A->n, &G, &R64);
@@ -826,7 +862,7 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     const int R = (int)R64;
     const int KW = k <= 2 ? 2 : 4;
     const int s = S->s;
-    size_t smem = persist_smem(R, k, KW, s, false);
+    size_t smem = persist_smem(R, k, KW, s, false, vb);
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
@@ -837,8 +873,9 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     // shared memory the window alone may still fit, with y~ in global memory
     bool yg = false;
     if (smem + 4096 > (size_t)optin) {
+        if (f32) return SKF_ERR_NOT_SUPPORTED;   // an FP32 basis keeps y~ on chip
         yg = true;
-        smem = persist_smem(R, k, KW, s, true);
+        smem = persist_smem(R, k, KW, s, true, vb);
         if (KW != 2 || A->max_width > 7 || smem + 4096 > (size_t)optin) return SKF_ERR_NOT_SUPPORTED;
     }
     int coop = 0;
@@ -852,7 +889,7 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     c.R = R;
     c.sell_off = A->sell_off;
     c.sell_w = A->sell_w;
-    c.sell_val = (const double *)A->sell_val;
+    c.sell_val = A->sell_val;
     c.sell_col = A->sell_col;
     c.sp = make_sparse_sign(S);
     c.pattern = S->pattern;
@@ -881,7 +918,7 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     const size_t szAy = sizeof(unsigned long long) * 2 * (size_t)s;
     const size_t szSw = sizeof(double) * (size_t)s * m;
     const size_t szBar = 2 * sizeof(int) + sizeof(unsigned long long);   // counter, flag, eps maximum
-    const size_t szYs = yg ? sizeof(double) * (size_t)G * R : 0;
+    const size_t szYs = yg ? vb * (size_t)G * R : 0;
     const size_t total = 2 * al(szP) + al(szAw) + al(szAy) + al(szSw) + al(szBar) + al(szYs);
     char *ws = nullptr;
     skf_status stt = dalloc((void **)&ws, total, st);
@@ -898,14 +935,15 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     c.accy = (unsigned long long *)take(szAy);
     c.Sw = (double *)take(szSw);
     c.bar = (unsigned *)take(szBar);
-    c.ysg = yg ? (double *)take(szYs) : nullptr;
+    c.ysg = yg ? (void *)take(szYs) : nullptr;
     c.flag = (int *)(c.bar + 1);
     unsigned long long *epsmax = (unsigned long long *)(c.bar + 2);
     // accumulators and the barrier start at zero (one memset: they are adjacent)
     cudaMemsetAsync(c.accw, 0, (size_t)((char *)c.Sw - (char *)c.accw), st);
     cudaMemsetAsync(c.bar, 0, szBar, st);
     cudaError_t e;
-    if (yg) e = launch_persist_yg(c, A->max_width, G, smem, st);
+    if (f32) e = launch_persist_f32(c, A->max_width, G, smem, st);
+    else if (yg) e = launch_persist_yg(c, A->max_width, G, smem, st);
     else if (KW == 2) e = launch_persist_w<2>(c, A->max_width, G, smem, st);
     else e = launch_persist_w<4>(c, A->max_width, G, smem, st);
     if (e != cudaSuccess) {
@@ -921,6 +959,18 @@ skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const d
     dfree(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "persistent Arnoldi kernels");
     return SKF_OK;
+}
+
+skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V,
+                                  int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
+                                  skf_info *info, cudaStream_t st) {
+    return run_persistent(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, st, false);
+}
+
+skf_status arnoldi_run_persistent_f32(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, float *V,
+                                      int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
+                                      skf_info *info, cudaStream_t st) {
+    return run_persistent(A, S, b, m, k, V, ldv, vscale, SV, SAV, H, iscal, info, st, true);
 }
 
 // Self-test of the bounded barrier wait: a grid of `ctas` co-resident CTAs

@@ -516,6 +516,10 @@ inline void call_col_hook(const StepHook *h, int j, cudaStream_t st) {
 skf_status arnoldi_run_persistent(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, double *V,
                                   int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
                                   skf_info *info, cudaStream_t st);
+// the persistent form with an FP32 basis (FP32 values, k <= 2, slices at most 7 wide)
+skf_status arnoldi_run_persistent_f32(const skf_csr *A, const skf_sketch *S, const double *b, int m, int k, float *V,
+                                      int64_t ldv, double *vscale, double *SV, double *SAV, double *H, int *iscal,
+                                      skf_info *info, cudaStream_t st);
 // Which FP64 step form arnoldi_run uses: 0 automatic (persistent where it
 // fits), 1 the two-kernel form only, 2 the persistent form or
 // SKF_ERR_NOT_SUPPORTED.

@@ -1,8 +1,9 @@
 """skf_solve_block: a block of right-hand sides on one operator (Algorithm 2
 and the tail for every column).  In the lockstep form (skf_set_block_mode(1))
 with an FP32 basis the Arnoldi processes advance together, one SpMM per step
-and group of four columns; in both forms every column must be bit-identical
-to its own skf_solve call, including a zero column (stopped at step 0 while
+and group of four columns (the two-kernel Arnoldi form of each column); in
+both forms every column must be bit-identical to its own skf_solve call in
+the same Arnoldi form, including a zero column (stopped at step 0 while
 the others go on), a block of five (groups of four and one) and both methods;
 the FP32 results stay within max(1e-6, 2^-24 cond(R)) of the FP64 oracle; an
 FP64 basis solves the columns one after another (also bit-identical)."""
@@ -45,10 +46,13 @@ def test_block_fp32_bitwise_equals_single_solves(skf, method, mode):
         X = skf.solve_block(meth, op.csr, S, B, f, p, info=info)
         torch.cuda.synchronize()
     OS = OSketch("sparse_sign", A.n, 4 * m, 8, 13)
+    # the lockstep form runs the two-kernel Arnoldi form of every column
+    form = skf.ARNOLDI_TWO_KERNEL if mode == 1 else skf.ARNOLDI_AUTO
     for q in range(nrhs):
         iq = skf.new_info()
-        xq = skf.solve(meth, op.csr, S, B[q].clone(), f, p, info=iq)
-        torch.cuda.synchronize()
+        with skf.arnoldi_mode(form):
+            xq = skf.solve(meth, op.csr, S, B[q].clone(), f, p, info=iq)
+            torch.cuda.synchronize()
         bq = skf.read_info(info[q])
         sq = skf.read_info(iq)
         assert torch.equal(X[q], xq), q
@@ -72,8 +76,9 @@ def test_block_fp32_3d_many_chunks(skf):
         X = skf.solve_block(skf.SGMRES, op.csr, S, B, f, p)
         torch.cuda.synchronize()
     for q in range(nrhs):
-        xq = skf.solve(skf.SGMRES, op.csr, S, B[q].clone(), f, p)
-        torch.cuda.synchronize()
+        with skf.arnoldi_mode(skf.ARNOLDI_TWO_KERNEL):
+            xq = skf.solve(skf.SGMRES, op.csr, S, B[q].clone(), f, p)
+            torch.cuda.synchronize()
         assert torch.equal(X[q], xq), q
 
 

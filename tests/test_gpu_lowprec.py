@@ -408,3 +408,39 @@ def test_returned_h_is_the_relation_of_the_stored_basis(skf, basis):
         for j in range(m - 1):
             bound = 4 * (width + k + 2) * U32 * np.linalg.norm(absAV[:, j]) / np.linalg.norm(AV[:, j])
             assert np.linalg.norm(R[:, j]) / np.linalg.norm(AV[:, j]) <= bound, j
+
+
+@pytest.mark.parametrize("method", ["sgmres", "sfom"])
+def test_f32_persistent_and_two_kernel_forms(skf, method):
+    """An FP32 basis in the persistent Arnoldi form (FP32 SpMV and update in one
+    cooperative launch, the window on chip) and in the two-kernel form: the
+    sketches are those of each stored basis, and both solves stay within
+    max(1e-6, 2^-24 cond(R)) of the FP64 oracle."""
+    A = convdiff_2d(100, (100.0, 50.0))
+    b = gaussian_rhs(A.n, 12)
+    c = quad_scale("invsqrt", laplacian_lambda_min(100, 2), float(abs(csr_to_scipy(A)).sum(1).max()))
+    m, k, s = 40, 2, 160
+    op = upload32(skf, A)
+    S = skf.Sketch(skf.SPARSE_SIGN, A.n, s, 8, 13)
+    f = skf.make_func("invsqrt", c)
+    xo, _ = osk.solve(csr_to_scipy(A), b, "invsqrt", m, k, OSketch("sparse_sign", A.n, s, 8, 13), c,
+                      method="sgmres" if method == "sgmres" else "sfom_quad", tol=1e-12)
+    xs = {}
+    for form in (skf.ARNOLDI_PERSISTENT, skf.ARNOLDI_TWO_KERNEL):
+        with skf.arnoldi_mode(form):
+            V, vs, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, torch.as_tensor(b, device="cuda"), m, k,
+                                                  basis_dtype=torch.float32)
+            info = skf.new_info()
+            x = skf.solve(skf.SGMRES if method == "sgmres" else skf.SFOM, op.csr, S,
+                          torch.as_tensor(b, device="cuda"), f,
+                          skf.make_params(m, k, basis_dtype=torch.float32, tol=1e-12), info=info)
+            torch.cuda.synchronize()
+        Vn = (V.double() * vs[:, None]).cpu().numpy().T
+        check_sketches(A, Vn, SV.cpu().numpy().T, SAV.cpu().numpy().T, k, s, m)
+        st = skf.read_info(info)
+        err = rel(x.cpu().numpy(), xo)
+        print(f"f32 form {form} {method}: rel err vs FP64 oracle {err:.3e}, cond_est {st['cond_est']:.3e}")
+        assert st["status"] == 0
+        assert err <= max(BOUND["f32"], U32 * st["cond_est"])
+        xs[form] = x.cpu().numpy()
+    assert rel(xs[skf.ARNOLDI_PERSISTENT], xs[skf.ARNOLDI_TWO_KERNEL]) <= 2e-6

@@ -39,9 +39,11 @@ def tail_case(skf, A, lam_lo, m, s, basis, method, seed=7, ell=None, form=None):
         f = skf.make_func("invsqrt", c, nodes=t_, weights=w_)
     p = skf.make_params(m, 2, basis_dtype=basis, tol=1e-10)
     info = skf.new_info()
-    with skf.tail_form(form):
+    # the cases are calibrated (kappa of the worst node system) on the basis of
+    # the two-kernel Arnoldi form
+    with skf.tail_form(form), skf.arnoldi_mode(skf.ARNOLDI_TWO_KERNEL):
         x = skf.solve(method, op.csr, S, b, f, p, info=info)
-    V, vsc, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, b, m, 2, basis_dtype=basis)
+        V, vsc, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, b, m, 2, basis_dtype=basis)
     torch.cuda.synchronize()
     inf = skf.read_info(info)
     # the oracle's tail on the GPU's basis: S b is the sketch of the stored
@@ -106,8 +108,9 @@ def test_tail_ill_conditioned_nodes_use_fp64_factor(skf, n, m):
     b = torch.as_tensor(gaussian_rhs(A.n, 7), device="cuda")
     S = skf.Sketch(skf.SPARSE_SIGN, A.n, s, 8, 13)
     c = quad_scale("invsqrt", laplacian_lambda_min(n, 2), float(abs(csr_to_scipy(A)).sum(1).max()))
-    V, vsc, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, b, m, 2, basis_dtype=torch.float32)
-    torch.cuda.synchronize()
+    with skf.arnoldi_mode(skf.ARNOLDI_TWO_KERNEL):   # the form the case was built on
+        V, vsc, SV, SAV, H = skf.arnoldi_trunc(op.csr, S, b, m, 2, basis_dtype=torch.float32)
+        torch.cuda.synchronize()
     SVn, SAVn, vs = SV.cpu().numpy().T, SAV.cpu().numpy().T, vsc.cpu().numpy()
     W = osk.whiten(SVn, SAVn, SVn[:, 0] / vs[0])
     kappa_of = lambda t: float(np.linalg.cond(t * W["Q"] + W["Z"]))
@@ -125,9 +128,9 @@ def test_tail_ill_conditioned_nodes_use_fp64_factor(skf, n, m):
     f = skf.make_func("invsqrt", c, nodes=t_, weights=w_)
     p = skf.make_params(m, 2, basis_dtype=torch.float32, tol=1e-10)
     info = skf.new_info()
-    with skf.tail_form(skf.TAIL_FULL):
+    with skf.tail_form(skf.TAIL_FULL), skf.arnoldi_mode(skf.ARNOLDI_TWO_KERNEL):
         x = skf.solve(skf.SGMRES, op.csr, S, b, f, p, info=info)
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
     inf = skf.read_info(info)
     q = sum(wi * np.linalg.lstsq(ti * W["Q"] + W["Z"], W["Sb"], rcond=None)[0] for ti, wi in zip(t_, w_))
     import scipy.linalg as sla
