@@ -1,5 +1,10 @@
-// Persistent single-launch form of the FP64 k-truncated Arnoldi process
-// (Algorithm 2, Sec. 2.2) for sparse-sign sketches.
+// Persistent single-launch form of the k-truncated Arnoldi process
+// (Algorithm 2, Sec. 2.2) for sparse-sign sketches, with an FP64 basis or
+// (k <= 2) an FP32 one: the kernel is instantiated on the value type T of the
+// operator, the basis and the on-chip rows; with T = float the SpMV, the
+// update and the per-thread sums run in FP32 (block and grid sums, scalars,
+// sketches and H stay FP64), and the update applies the FP32 values of sigma_j
+// and of its coefficients, which H and the relation for S A v_j then use.
 //
 // The whole recurrence (all m steps) runs in one cooperative launch of one
 // CTA per SM.  CTA g owns R consecutive rows (whole SELL-32 slices) and keeps
@@ -15,7 +20,10 @@
 //      sum_i h_ij sigma_i w_i, partial ||w_{j+1}||^2, Gram entries of the
 //      next window and max|w_{j+1}|; exact fixed-point sketch of w_j.
 // Storage is that of the two-kernel path: column j of V holds w_j, a
-// positive multiple of v_j, and vscale[j] = 1 / ||w_j||.
+// positive multiple of v_j, and vscale[j] = 1 / ||w_j||.  When the rows of the
+// window and of y~ do not fit in shared memory together but the window does
+// (FP64, k <= 2), y~ lives in a global array instead, written in phase A and
+// read back in phase B by the same CTA (L2-resident).
 //
 // S A v_j is not scattered row by row.  The update of step j applied
 //   w_{j+1} = sigma_j y~_j - sum_i c_i w_i,
