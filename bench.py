@@ -301,8 +301,10 @@ def run_block(args, wl, A, op, dev, rank):
             skf.solve_block(skf.SGMRES, op.csr, S, B, f, p, X=Xb)
 
     def singles():
-        for q in range(args.nrhs):
-            skf.solve(skf.SGMRES, op.csr, S, B[q], f, p, x=Xs[q])
+        # the Arnoldi form of the lockstep columns (two-kernel), for a like comparison
+        with skf.arnoldi_mode(skf.ARNOLDI_TWO_KERNEL):
+            for q in range(args.nrhs):
+                skf.solve(skf.SGMRES, op.csr, S, B[q], f, p, x=Xs[q])
 
     res = {"mode": "block", "workload": args.workload, "basis": args.basis, "m": m, "nrhs": args.nrhs}
     for name, fn in (("block", block), ("singles", singles)):
