@@ -80,3 +80,48 @@ def test_relation_form_sgmres_residual_norms():
         top = (t * np.eye(m) + M) @ y - c
         rhs = np.sqrt(top @ top + (gamma * y[-1]) ** 2 + (np.linalg.norm(Sb) ** 2 - c @ c))
         assert abs(lhs - rhs) <= 1e-10 * max(lhs, 1.0)
+
+
+def test_fp32_update_relation_coefficients():
+    """Reading 14 for an FP32 basis: an update that applies the FP32 values
+    sigma~ = fl32(sigma_j) and c~_i = fl32(h_ij sigma_i),
+        w_{j+1} = sigma~ y_j - sum_i c~_i w_i,
+    satisfies A v_j = V H(:, j) exactly for the stored columns with
+        H(j+1, j) = sigma_j ||w_{j+1}|| / sigma~,  H(i, j) = sigma_j c~_i / (sigma~ sigma_i),
+    whereas the unrounded MGS coefficients h_ij leave a residual of order
+    2^-24 ||A v_j||.  Checked in FP64 on a short recurrence with FP32-rounded
+    coefficients (the stored columns kept in FP64 so that only the
+    coefficients differ)."""
+    A = csr_to_scipy(convdiff_2d(20, (30.0, 10.0)))
+    b = gaussian_rhs(A.shape[0], 4)
+    m, k = 12, 2
+    W = [b / np.linalg.norm(b)]          # stored columns w_j (here already normalised at j = 0)
+    sig = [1.0 / np.linalg.norm(W[0])]
+    H_cons = np.zeros((m + 1, m))
+    H_mgs = np.zeros((m + 1, m))
+    for j in range(m):
+        y = A @ W[j]                     # y_j = A w_j
+        vj = sig[j] * y                  # A v_j
+        i0 = max(0, j - k + 1)
+        w = vj.copy()
+        h = {}
+        for i in range(i0, j + 1):       # MGS against the normalised window
+            vi = sig[i] * W[i]
+            h[i] = vi @ w
+            w = w - h[i] * vi
+        st = float(np.float32(sig[j]))
+        ct = {i: float(np.float32(h[i] * sig[i])) for i in h}
+        wn = st * y - sum(ct[i] * W[i] for i in h)   # the update as applied
+        W.append(wn)
+        sig.append(1.0 / np.linalg.norm(wn))
+        for i in h:
+            H_cons[i, j] = sig[j] * ct[i] / (st * sig[i])
+            H_mgs[i, j] = h[i]
+        H_cons[j + 1, j] = sig[j] * np.linalg.norm(wn) / st
+        H_mgs[j + 1, j] = np.linalg.norm(w)     # the unrounded MGS norm
+    V = np.column_stack([s_ * w_ for s_, w_ in zip(sig, W)])        # normalised stored basis, m + 1 columns
+    AV = A @ V[:, :m]
+    r_cons = np.linalg.norm(AV - V @ H_cons) / np.linalg.norm(AV)
+    r_mgs = np.linalg.norm(AV - V @ H_mgs) / np.linalg.norm(AV)
+    assert r_cons < 1e-14
+    assert r_mgs > 1e-9     # the FP32 rounding of the applied coefficients shows
