@@ -163,3 +163,21 @@ def test_custom_rule_closure(skf):
     bad = skf.make_func("custom", rule=lambda ell: ([1.0], [1.0]))      # wrong length
     with pytest.raises(skf.SkfError, match="NOT_SUPPORTED"):
         skf.quadrature_rule(bad, 3)
+
+
+def test_column_major_view_without_copy(skf):
+    """The sketch bindings pass X to the C ABI column-major (column c at offset
+    c N): a tensor already laid out that way goes through as a view, any other
+    layout is copied once."""
+    import torch
+    N = 7
+    x = torch.arange(N, dtype=torch.float64)
+    v = skf._column_major(x)
+    assert v.shape == (1, N) and v.data_ptr() == x.data_ptr()
+    Y = torch.arange(3 * N, dtype=torch.float64).reshape(3, N)      # rows = columns of X = Y.t()
+    v = skf._column_major(Y.t())
+    assert v.shape == (3, N) and v.data_ptr() == Y.data_ptr() and torch.equal(v, Y)
+    X = torch.arange(3 * N, dtype=torch.float64).reshape(N, 3)      # row-major (N, 3): needs a copy
+    v = skf._column_major(X)
+    assert v.shape == (3, N) and v.is_contiguous() and v.data_ptr() != X.data_ptr()
+    assert torch.equal(v, X.t())
